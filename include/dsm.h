@@ -1,0 +1,192 @@
+/*
+ * dsm.h -- C ABI of the differentiable variance-shadow-mapping library (sm_103a).
+ *
+ * Method: Worchel & Alexa, "Differentiable Shadow Mapping for Efficient Inverse
+ * Graphics" (CVPR 2023).  Per light, Alg. 1 renders the light-view depth map f
+ * (Eq. 1), smooths f and f^2 by edge antialiasing (Sec. 4/5) and filters them
+ * into the moment maps m1 = G f~, m2 = G (f^2)~ (Eqs. moment1, moment2).  The
+ * camera pass shades every pixel with Lambert times the visibility of Alg. 2
+ * (Chebyshev bound of Sec. 3) per light, and the image is antialiased again.
+ * The backward pass returns dL/d vertices, dL/d light (position, direction) and
+ * dL/d albedo (Sec. 4: chain rule through G, the moments and the visibility).
+ *
+ * Conventions shared by every call
+ *  - Matrices are row-major 4x4 float: clip = M [x y z 1]^T.
+ *  - Screen: sx = (0.5 ndc_x + 0.5) W, sy = (0.5 - 0.5 ndc_y) H, row 0 at the top.
+ *    Pixel (i, j) is column i, row j; its centre is (i + 0.5, j + 0.5).
+ *  - Images and maps are row-major, pixel (i, j) at index j * W + i.
+ *  - All pointers named "device" are CUDA device pointers on the current device;
+ *    the caller owns them.  The context owns its scratch memory and the state
+ *    saved by dsm_render for dsm_render_backward; that state stays valid until
+ *    the next dsm_render on the same context.
+ *  - Every call enqueues work on params->stream (the stream given to the last
+ *    dsm_render for dsm_render_backward) and returns without waiting, except
+ *    where stated.  Errors found on the device are reported by dsm_sync.
+ *  - Nothing throws across this boundary; every call returns a dsm_status and
+ *    dsm_last_error() gives a one-line description of the last failure.
+ */
+#ifndef DSM_H
+#define DSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSM_MAX_LIGHTS 8
+
+typedef enum dsm_status {
+  DSM_OK = 0,
+  DSM_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range          */
+  DSM_ERR_CAPACITY = 2,      /* an internal list overflowed; the result is invalid     */
+  DSM_ERR_CUDA = 3,          /* a CUDA runtime call failed                             */
+  DSM_ERR_TIMEOUT = 4,       /* a bounded device wait gave up                          */
+  DSM_ERR_NO_FORWARD = 5,    /* backward called without a matching forward             */
+  DSM_ERR_OOM = 6,           /* device allocation failed                               */
+  DSM_ERR_NO_TOPOLOGY = 7    /* dsm_set_topology was not called for this mesh          */
+} dsm_status;
+
+typedef struct dsm_ctx dsm_ctx;   /* opaque */
+
+/* Triangle mesh.  verts: device, n_verts x 3 float, world space.  tris: device,
+ * n_tris x 3 int32 vertex indices.  tri_material: device, n_tris int32 indices
+ * into albedo (NULL: material 0 everywhere).  albedo: device, n_materials x 3
+ * float Lambert albedo (supplementary Sec. A). */
+typedef struct dsm_mesh {
+  const float*   verts;
+  int32_t        n_verts;
+  const int32_t* tris;
+  int32_t        n_tris;
+  const int32_t* tri_material;
+  const float*   albedo;
+  int32_t        n_materials;
+} dsm_mesh;
+
+/* Constant description of one light (supplementary Sec. A).  The differentiable
+ * light parameters are NOT here: they are passed as a device array
+ * light_params[l * 6 + 0..2] = position, [l * 6 + 3..5] = direction of travel.
+ *  type 0, directional: orthographic shadow camera at -dist * normalize(dir),
+ *          looking along dir, window +-ortho_half;
+ *  type 1, spot: perspective shadow camera at the position looking along dir,
+ *          full vertical field of view fov_y_deg.
+ * The map stores the normalised depth d = (z_view - near) / (far - near), with
+ * z_view the distance along normalize(dir) (Sec. 3: distance from a plane for a
+ * directional light).  Up vector +Y, or +Z when |dir_y| > 0.99 |dir|. */
+typedef struct dsm_light {
+  int32_t type;
+  int32_t res;            /* shadow-map side in texels, 1..16384                   */
+  float   fov_y_deg;      /* spot only                                             */
+  float   ortho_half;     /* directional only                                      */
+  float   dist;           /* directional only                                      */
+  float   near_plane;
+  float   far_plane;
+  float   intensity[3];
+  float   sigma;          /* Gaussian filter sigma in texels                       */
+  int32_t radius;         /* filter radius r (kernel size k = 2r + 1); <= 0: ceil(2 sigma) */
+} dsm_light;
+
+/* Camera: row-major world -> clip matrix (OpenGL-style: ndc z grows with depth)
+ * and the image size. */
+typedef struct dsm_camera {
+  float   clip[16];
+  int32_t width;
+  int32_t height;
+} dsm_camera;
+
+typedef struct dsm_params {
+  float   min_variance;     /* floor of sigma^2 in the Chebyshev bound (normalised depth^2) */
+  int32_t filter_kind;      /* 0 Gaussian, 1 box (kernel size 2r + 1)                        */
+  int32_t filter_boundary;  /* 0 clamp to edge, 1 zero outside                              */
+  int32_t aa_shadow;        /* 1: antialias (f, f^2) before filtering (Sec. 5 ablation: 0)  */
+  int32_t aa_final;         /* 1: antialias the shaded image                                */
+  int32_t recompute_in_backward; /* reserved, must be 0                                     */
+  void*   stream;           /* cudaStream_t; NULL = legacy default stream                   */
+} dsm_params;
+
+/* Create / destroy a context bound to the current CUDA device.  dsm_create
+ * returns DSM_ERR_CUDA when no device is usable. */
+dsm_status dsm_create(dsm_ctx** out);
+void       dsm_destroy(dsm_ctx* ctx);
+
+/* Mesh topology (edge adjacency for the silhouette test of the antialiasing,
+ * vertex -> face lists for the vertex normals).  tris: device, n_tris x 3.
+ * Synchronous: copies tris to the host and builds the tables there.  Call once
+ * per topology, before dsm_render; it may allocate. */
+dsm_status dsm_set_topology(dsm_ctx* ctx, const int32_t* tris, int32_t n_tris, int32_t n_verts);
+
+/* Forward pass (Alg. 1 per light, Alg. 2 + Lambert per camera pixel, final
+ * antialiasing).  light_params: device, n_lights x 6 float (see dsm_light).
+ * image: device, height x width x 4 float, RGB and coverage alpha, overwritten.
+ * Synchronises once with the stream on the first call for a new scene size (to
+ * size the tile lists); later calls do not wait. */
+dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* lights,
+                      const float* light_params, int32_t n_lights,
+                      const dsm_camera* camera, const dsm_params* params, float* image);
+
+/* Backward pass of the last dsm_render on ctx.  dL_dimage: device, H x W x 4.
+ * Outputs (device, overwritten, any may be NULL to skip): dL_dverts n_verts x 3,
+ * dL_dlight n_lights x 6 (position, direction; zero position gradient for
+ * directional lights), dL_dalbedo n_materials x 3.  The mesh, light and
+ * albedo buffers of that dsm_render must still hold the same values. */
+dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_dverts,
+                               float* dL_dlight, float* dL_dalbedo);
+
+/* L = mean((image - target)^2) over n floats and dL/dimage = 2 (image - target) / n.
+ * image, target, dL_dimage: device, n floats; loss: device, one float (overwritten).
+ * stream: cudaStream_t. */
+dsm_status dsm_l2_loss_grad(const float* image, const float* target, int64_t n,
+                            float* loss, float* dL_dimage, void* stream);
+
+/* Separable filter of a two-channel map (Eqs. moment1/moment2: m = G g), the
+ * same arithmetic as inside dsm_render.  in, out: device, res x res float2
+ * (row-major, 8-byte aligned), must not overlap.  Uses ctx scratch for the
+ * intermediate row-filtered map (may allocate). */
+dsm_status dsm_filter_moments(dsm_ctx* ctx, const float* in, float* out, int32_t res,
+                              float sigma, int32_t radius, int32_t kind, int32_t boundary,
+                              void* stream);
+
+/* Wait for the context's stream and report device-side errors (capacity
+ * overflow, timeouts) raised since the last dsm_sync. */
+dsm_status dsm_sync(dsm_ctx* ctx);
+
+/* One-line description of the last error on ctx (static storage, never NULL). */
+const char* dsm_last_error(dsm_ctx* ctx);
+
+/* Copy an internal buffer of the last dsm_render / dsm_render_backward into a
+ * caller device buffer (stage-wise testing and profiling).  what:
+ *  0 G-buffer of view index (lights 0..n-1, camera n): per pixel int32 id+1
+ *    (0 = background), float b0, float b1, float depth key; 16 B per pixel
+ *  1 f, f^2 before antialiasing (light index), float2 per texel
+ *  2 f~, (f^2)~ after antialiasing (light), float2
+ *  3 m1, m2 moment maps (light), float2
+ *  4 camera colour before the final antialiasing, float4 per pixel
+ *  5 light matrices Q (20 floats per light: clip rows 0-3, depth row 4)
+ *  6 snapped vertices of view index: int32 X, Y (24.8 fixed point), float ndc z,
+ *    int32 valid; 16 B per vertex
+ *  7 dL/d(m1, m2) texel gradients (light), float2
+ *  8 dL/d clip coordinates of view index, float4 per vertex
+ *  9 dL/d(f~, (f^2)~) (light), float2
+ * 10 dL/d camera colour before the final antialiasing, float4 per pixel
+ * bytes must equal the buffer size; returns DSM_ERR_INVALID_ARG otherwise. */
+dsm_status dsm_debug_copy(dsm_ctx* ctx, int32_t what, int32_t index, void* dst, size_t bytes);
+
+/* Per-stage device timing: while enabled, dsm_render and dsm_render_backward
+ * record a CUDA event pair on their stream around every stage (stage names:
+ * dsm_profile_stage_name).  dsm_profile_read waits for the recorded events,
+ * writes the accumulated milliseconds and the number of timed calls of each
+ * of the first n stages (ms, calls: host arrays of n entries) and clears the
+ * records.  Enabling costs two event records per stage and call. */
+dsm_status  dsm_profile_enable(dsm_ctx* ctx, int32_t enable);
+int32_t     dsm_profile_stage_count(void);
+const char* dsm_profile_stage_name(int32_t stage);   /* NULL when out of range */
+dsm_status  dsm_profile_read(dsm_ctx* ctx, double* ms, int64_t* calls, int32_t n);
+
+/* Number of kernels this library has launched in this process (all contexts). */
+uint64_t dsm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSM_H */

@@ -67,6 +67,10 @@ def _normalize(a):
     return torch.stack([a[0] / n, a[1] / n, a[2] / n])
 
 
+def _f32(x) -> float:
+    return float(np.float32(x))
+
+
 def light_matrix(light: dict, pos: torch.Tensor, direction: torch.Tensor) -> torch.Tensor:
     """Light camera of Supplementary Sec. A as a 5x4 float64 matrix Q.
 
@@ -88,9 +92,11 @@ def light_matrix(light: dict, pos: torch.Tensor, direction: torch.Tensor) -> tor
         up = torch.tensor([0.0, 1.0, 0.0], dtype=F64)
     r = _normalize(_cross(f, up))
     u = _cross(r, f)
-    near, far = float(light["near"]), float(light["far"])
+    # the light's scalar constants are float32 values (as a renderer stores them)
+    near, far = _f32(light["near"]), _f32(light["far"])
     if int(light["type"]) == 0:
-        e = torch.stack([-float(light["dist"]) * f[0], -float(light["dist"]) * f[1], -float(light["dist"]) * f[2]])
+        dist = _f32(light["dist"])
+        e = torch.stack([-dist * f[0], -dist * f[1], -dist * f[2]])
     else:
         e = pos
     fe = _dot(f, e)
@@ -99,13 +105,13 @@ def light_matrix(light: dict, pos: torch.Tensor, direction: torch.Tensor) -> tor
     zero = torch.zeros((), dtype=F64)
     one = torch.ones((), dtype=F64)
     if int(light["type"]) == 0:
-        h = float(light["ortho_half"])
+        h = _f32(light["ortho_half"])
         row0 = torch.stack([r[0] / h, r[1] / h, r[2] / h, -_dot(r, e) / h])
         row1 = torch.stack([u[0] / h, u[1] / h, u[2] / h, -_dot(u, e) / h])
         row2 = depth
         row3 = torch.stack([zero, zero, zero, one])
     else:
-        c = 1.0 / math.tan(float(light["fov_y_deg"]) * math.pi / 360.0)
+        c = 1.0 / math.tan(_f32(light["fov_y_deg"]) * math.pi / 360.0)
         A = far / rng
         B = -(far * near) / rng
         row0 = torch.stack([c * r[0], c * r[1], c * r[2], -(c * _dot(r, e))])

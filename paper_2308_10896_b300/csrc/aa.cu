@@ -1,0 +1,295 @@
+// Shadow-map depth interpolation (f, f^2) and the analytic edge antialiasing
+// that makes silhouettes differentiable (Sec. 4/5: f, f^2 -> f~, (f^2)~; the
+// same pass smooths the final image), with their adjoints.
+#include "dsm.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dsm {
+
+// Crossing of a silhouette edge of triangle `tri` with the segment between the
+// centres of the occluder pixel O = (io, jo) and its neighbour N = (in, jn).
+// Decisions on the exact snapped coordinates; t from the unsnapped edge.
+struct Cross {
+  int found;
+  int va, vb;
+  float t;          // crossing parameter from O towards N, clamped to [0, 1]
+  int active;       // t strictly inside (0, 1): it depends on the edge
+  float dt[4];      // dt / d(xa, ya, xb, yb) in screen pixels (when active)
+};
+
+template <bool kGrad>
+__device__ __forceinline__ Cross find_crossing(const AAArgs& a, int tri, int io, int jo, int in, int jn,
+                                               bool vertical) {
+  Cross c;
+  c.found = 0;
+  const int m = a.sil[tri];
+  if (!m) return c;
+  long long line, lo;
+  if (vertical) {
+    line = (long long)io * kSubpix + 128;
+    lo = (long long)min(jo, jn) * kSubpix + 128;
+  } else {
+    line = (long long)jo * kSubpix + 128;
+    lo = (long long)min(io, in) * kSubpix + 128;
+  }
+  const long long hi = lo + kSubpix;
+  for (int e = 0; e < 3; ++e) {
+    if (!((m >> e) & 1)) continue;
+    const int va = a.tris[3 * tri + edge_p(e)], vb = a.tris[3 * tri + edge_q(e)];
+    const VertSnap A = a.snap[va], B = a.snap[vb];
+    long long ua, ub, wa, wb;
+    if (vertical) { ua = A.X; ub = B.X; wa = A.Y; wb = B.Y; }
+    else          { ua = A.Y; ub = B.Y; wa = A.X; wb = B.X; }
+    if ((ua >= line) == (ub >= line)) continue;
+    const long long D = ub - ua;
+    const long long along = llabs(wb - wa);
+    if (vertical ? !(llabs(D) >= along) : !(llabs(D) > along)) continue;   // one axis per edge
+    const long long num = wa * D + (line - ua) * (wb - wa);
+    const bool inside = D > 0 ? (lo * D <= num && num <= hi * D) : (lo * D >= num && num >= hi * D);
+    if (!inside) continue;
+    c.found = 1;
+    c.va = va;
+    c.vb = vb;
+    const float2 sa = screen_of(a.clip[va], a.W, a.H), sb = screen_of(a.clip[vb], a.W, a.H);
+    // along-coordinate p, across-coordinate q (q = const line)
+    float pa, qa, pb, qb, lc, opos, step;
+    if (vertical) {
+      pa = sa.y; qa = sa.x; pb = sb.y; qb = sb.x;
+      lc = io + 0.5f; opos = jo + 0.5f; step = (jn > jo) ? 1.f : -1.f;
+    } else {
+      pa = sa.x; qa = sa.y; pb = sb.x; qb = sb.y;
+      lc = jo + 0.5f; opos = io + 0.5f; step = (in > io) ? 1.f : -1.f;
+    }
+    const float dq = qb - qa;
+    if (dq == 0.f) {
+      c.t = 0.5f;
+      c.active = 0;
+      return c;
+    }
+    const float s = (lc - qa) / dq;
+    const float r = (pb - pa) / dq;
+    const float cross = pa + s * (pb - pa);
+    const float traw = (cross - opos) * step;
+    c.t = fminf(fmaxf(traw, 0.f), 1.f);
+    c.active = (traw > 0.f && traw < 1.f);
+    if (kGrad) {
+      // d cross / d(pa, qa, pb, qb)
+      const float dpa = 1.f - s, dpb = s, dqa = -r * (1.f - s), dqb = -r * s;
+      if (vertical) {  // p = y, q = x
+        c.dt[0] = step * dqa; c.dt[1] = step * dpa; c.dt[2] = step * dqb; c.dt[3] = step * dpb;
+      } else {
+        c.dt[0] = step * dpa; c.dt[1] = step * dqa; c.dt[2] = step * dpb; c.dt[3] = step * dqb;
+      }
+    }
+    return c;
+  }
+  return c;
+}
+
+// dL/d clip of a vertex from dL/d of its screen position (sx, sy).
+__device__ __forceinline__ float4 screen_to_clip_grad(float4 c, float gx, float gy, int W, int H) {
+  const float iw = 1.0f / c.w;
+  const float ax = 0.5f * W * iw, ay = -0.5f * H * iw;
+  return make_float4(gx * ax, gy * ay, 0.f, -(gx * ax * c.x + gy * ay * c.y) * iw);
+}
+
+__device__ __forceinline__ int gid(float4 g) { return __float_as_int(g.x); }
+
+// Pair bookkeeping for pixel p=(i,j) and its neighbour q.  Returns false when
+// the pair has no antialiasing crossing.
+struct PairInfo {
+  bool p_occ;       // p is the occluder pixel O
+  bool p_is_first;  // p is the left / top pixel of the pair
+  Cross c;
+};
+
+template <bool kGrad>
+__device__ __forceinline__ bool pair_info(const AAArgs& a, int i, int j, int ni, int nj, float4 gp, float4 gq,
+                                          PairInfo& pi) {
+  const int idp = gid(gp), idq = gid(gq);
+  if (idp == idq) return false;
+  const bool p_first = (ni > i) || (nj > j);
+  const int idA = p_first ? idp : idq, idB = p_first ? idq : idp;
+  const float zA = p_first ? gp.w : gq.w, zB = p_first ? gq.w : gp.w;
+  const bool a_occ = (idB == 0) || (idA != 0 && depth_key(zA, idA - 1) < depth_key(zB, idB - 1));
+  const bool p_occ = p_first ? a_occ : !a_occ;
+  const int tri = (p_occ ? idp : idq) - 1;
+  const int io = p_occ ? i : ni, jo = p_occ ? j : nj, in = p_occ ? ni : i, jn = p_occ ? nj : j;
+  pi.c = find_crossing<kGrad>(a, tri, io, jo, in, jn, nj != j);
+  pi.p_occ = p_occ;
+  pi.p_is_first = p_first;
+  return pi.c.found;
+}
+
+__constant__ int kDI[4] = {-1, 1, 0, 0};
+__constant__ int kDJ[4] = {0, 0, -1, 1};
+
+// ------------------------------------------------------------------ forward
+// Every pixel gathers the gains of the (up to 4) pairs it belongs to: if t > 1/2
+// the neighbour-side pixel N gains (t - 1/2)(c_O - c_N), else O gains
+// (1/2 - t)(c_N - c_O).
+template <typename V>
+__global__ void aa_forward_kernel(AAArgs a, const V* __restrict__ color, V* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= a.W || j >= a.H) return;
+  const size_t p = (size_t)j * a.W + i;
+  const float4 gp = a.gbuf[p];
+  const V cp = color[p];
+  V acc = cp;
+  for (int d = 0; d < 4; ++d) {
+    const int ni = i + kDI[d], nj = j + kDJ[d];
+    if (ni < 0 || nj < 0 || ni >= a.W || nj >= a.H) continue;
+    const size_t q = (size_t)nj * a.W + ni;
+    const float4 gq = a.gbuf[q];
+    PairInfo pi;
+    if (!pair_info<false>(a, i, j, ni, nj, gp, gq, pi)) continue;
+    const V cq = color[q];
+    const float t = pi.c.t;
+    if (t > 0.5f) {
+      if (!pi.p_occ) acc = vadd(acc, vscale(vsub(cq, cp), t - 0.5f));        // p = N, cq = c_O
+    } else {
+      if (pi.p_occ) acc = vadd(acc, vscale(vsub(cq, cp), 0.5f - t));         // p = O, cq = c_N
+    }
+  }
+  out[p] = acc;
+}
+
+// ------------------------------------------------------------------ adjoint
+// dL/dc_p = g_p + the pair terms; the t-gradient of each pair is scattered once
+// (by its left / top pixel) onto the clip coordinates of the edge endpoints.
+template <typename V>
+__device__ __forceinline__ V aa_adjoint_pixel(const AAArgs& a, int i, int j, const V* color, const V* gout,
+                                              float4* gclip) {
+  const size_t p = (size_t)j * a.W + i;
+  const float4 gp = a.gbuf[p];
+  const V g_p = gout[p];
+  V acc = g_p;
+  for (int d = 0; d < 4; ++d) {
+    const int ni = i + kDI[d], nj = j + kDJ[d];
+    if (ni < 0 || nj < 0 || ni >= a.W || nj >= a.H) continue;
+    const size_t q = (size_t)nj * a.W + ni;
+    const float4 gq = a.gbuf[q];
+    PairInfo pi;
+    if (!pair_info<true>(a, i, j, ni, nj, gp, gq, pi)) continue;
+    const V g_q = gout[q];
+    const float t = pi.c.t;
+    const V gO = pi.p_occ ? g_p : g_q, gN = pi.p_occ ? g_q : g_p;
+    float dLdt;
+    if (t > 0.5f) {            // Delta_N = (t - 1/2)(c_O - c_N)
+      acc = vadd(acc, vscale(gN, pi.p_occ ? (t - 0.5f) : -(t - 0.5f)));
+      dLdt = 0.f;
+      if (pi.p_is_first && pi.c.active) {
+        const V cp = color[p], cq = color[q];
+        const V cO = pi.p_occ ? cp : cq, cN = pi.p_occ ? cq : cp;
+        dLdt = dotv(gN, vsub(cO, cN));
+      }
+    } else {                   // Delta_O = (1/2 - t)(c_N - c_O)
+      acc = vadd(acc, vscale(gO, pi.p_occ ? -(0.5f - t) : (0.5f - t)));
+      dLdt = 0.f;
+      if (pi.p_is_first && pi.c.active) {
+        const V cp = color[p], cq = color[q];
+        const V cO = pi.p_occ ? cp : cq, cN = pi.p_occ ? cq : cp;
+        dLdt = dotv(gO, vsub(cO, cN));
+      }
+    }
+    if (dLdt != 0.f) {
+      const float4 ca = a.clip[pi.c.va], cb = a.clip[pi.c.vb];
+      atomic_add4(&gclip[pi.c.va], screen_to_clip_grad(ca, dLdt * pi.c.dt[0], dLdt * pi.c.dt[1], a.W, a.H));
+      atomic_add4(&gclip[pi.c.vb], screen_to_clip_grad(cb, dLdt * pi.c.dt[2], dLdt * pi.c.dt[3], a.W, a.H));
+    }
+  }
+  return acc;
+}
+
+__global__ void aa_backward4_kernel(AAArgs a, const float4* __restrict__ color, const float4* __restrict__ gout,
+                                    float4* __restrict__ gcolor, float4* __restrict__ gclip, int aa) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= a.W || j >= a.H) return;
+  const size_t p = (size_t)j * a.W + i;
+  gcolor[p] = aa ? aa_adjoint_pixel<float4>(a, i, j, color, gout, gclip) : gout[p];
+}
+
+// ------------------------------------------------------------------ shadow-map interpolation
+// f = sum_k b_k d_k of the covering triangle (background: f = 1), f^2 = f f.
+__global__ void sm_interp_kernel(const float4* __restrict__ gbuf, int R, const int* __restrict__ tris,
+                                 const float* __restrict__ depth, float2* __restrict__ fmap) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= R || j >= R) return;
+  const size_t p = (size_t)j * R + i;
+  const float4 g = gbuf[p];
+  const int id = gid(g);
+  float f = 1.f;
+  if (id) {
+    const int t = id - 1;
+    const float b2 = 1.f - g.y - g.z;
+    f = g.y * depth[tris[3 * t]] + g.z * depth[tris[3 * t + 1]] + b2 * depth[tris[3 * t + 2]];
+  }
+  fmap[p] = make_float2(f, f * f);
+}
+
+// Adjoint of antialiasing + interpolation on the shadow map: dL/d(f, f^2) per
+// texel, then dL/df = g.x + 2 f g.y onto the vertex depths and (through the
+// barycentrics) onto the light-space clip coordinates.
+__global__ void sm_backward_kernel(AAArgs a, const float2* __restrict__ fmap, const float2* __restrict__ gft,
+                                   const float* __restrict__ depth, float4* __restrict__ gclip,
+                                   float* __restrict__ gdepth, int aa) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= a.W || j >= a.H) return;
+  const size_t p = (size_t)j * a.W + i;
+  const float2 gc = aa ? aa_adjoint_pixel<float2>(a, i, j, fmap, gft, gclip) : gft[p];
+  const float4 g = a.gbuf[p];
+  const int id = gid(g);
+  if (!id) return;
+  const float f = fmap[p].x;
+  const float gf = gc.x + 2.f * f * gc.y;
+  if (gf == 0.f) return;
+  const int t = id - 1;
+  const int v[3] = {a.tris[3 * t], a.tris[3 * t + 1], a.tris[3 * t + 2]};
+  const float4 c0 = a.clip[v[0]], c1 = a.clip[v[1]], c2 = a.clip[v[2]];
+  const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
+  const Bary r = bary_at(c0, c1, c2, px, py);
+  const float b[3] = {g.y, g.z, 1.f - g.y - g.z};
+  float gb[3];
+  for (int k = 0; k < 3; ++k) {
+    atomicAdd(&gdepth[v[k]], b[k] * gf);
+    gb[k] = depth[v[k]] * gf;
+  }
+  float4 gcv[3];
+  bary_backward(r, gb, px, py, gcv);
+  for (int k = 0; k < 3; ++k) atomic_add4(&gclip[v[k]], gcv[k]);
+}
+
+// ------------------------------------------------------------------ launchers
+static inline dim3 grid2(int W, int H, dim3 b) { return dim3((W + b.x - 1) / b.x, (H + b.y - 1) / b.y); }
+
+void launch_sm_interp(const float4* gbuf, int R, const int* tris, const float* depth, float2* fmap,
+                      cudaStream_t st) {
+  dim3 b(32, 8);
+  count_launches(1);
+  sm_interp_kernel<<<grid2(R, R, b), b, 0, st>>>(gbuf, R, tris, depth, fmap);
+}
+void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, cudaStream_t st) {
+  dim3 b(32, 8);
+  count_launches(1);
+  aa_forward_kernel<float2><<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, out);
+}
+void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, cudaStream_t st) {
+  dim3 b(32, 8);
+  count_launches(1);
+  aa_forward_kernel<float4><<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, out);
+}
+void launch_sm_backward(const AAArgs& a, const float2* fmap, const float2* gft, const float* depth, float4* gclip,
+                        float* gdepth, int aa, cudaStream_t st) {
+  dim3 b(32, 8);
+  count_launches(1);
+  sm_backward_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, fmap, gft, depth, gclip, gdepth, aa);
+}
+void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
+                         int aa, cudaStream_t st) {
+  dim3 b(32, 8);
+  count_launches(1);
+  aa_backward4_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, gout, gcolor, gclip, aa);
+}
+
+}  // namespace dsm

@@ -1,0 +1,141 @@
+// Device-side definitions shared by the kernels of the shadow-mapping library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dsm {
+
+constexpr int kSubpix = 256;          // 8 sub-pixel bits: 24.8 fixed point
+constexpr int kGuard = 1 << 28;       // |snapped coordinate| limit; beyond it a triangle is culled
+constexpr float kWMin = 1e-6f;        // clip w below this culls the triangle
+constexpr int kTile = 16;             // raster tile side in pixels
+constexpr int kTileLog2 = 4;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Snapped vertex of one view: 24.8 fixed-point screen position, ndc depth,
+// validity (w >= kWMin and inside the guard band).
+struct __align__(16) VertSnap {
+  int X, Y;
+  float z;
+  int ok;
+};
+
+// Per-triangle raster record of one view (64 bytes, loaded whole into shared
+// memory by the tile rasteriser).
+struct __align__(16) TriSetup {
+  int X[3], Y[3];     // snapped vertices
+  float z[3];         // ndc depth of the vertices
+  float a2f;          // float(2A), 2A > 0 after orientation normalisation
+  int ibox, jbox;     // pixel bbox: i0 | i1 << 16, j0 | j1 << 16 (empty: i0 > i1)
+  int tri;            // triangle index
+  int flags;          // bit 0..2: top-left flag of edge k; bit 3: s = -1; bit 4: visible
+  int pad[2];
+};
+static_assert(sizeof(TriSetup) == 64, "TriSetup must be 64 bytes");
+
+// Light record written by the light-camera kernel: Q rows 0-3 = clip matrix,
+// row 4 = depth row; J = dQ/d(pos, dir) (20 x 6, row-major).
+struct LightDev {
+  float Q[20];
+  float J[120];
+  float fwd[3];       // normalised travel direction
+  float dir_norm;     // |dir|
+  float pos[3];
+  int type;
+  int res;
+  float intensity[3];
+};
+
+// Device status word (errors raised by kernels, read by dsm_sync).
+struct DevStatus {
+  int capacity_overflow;
+  int timeout;
+  int needed_pairs[DSM_MAX_LIGHTS + 1];
+};
+
+__device__ __forceinline__ uint32_t order_bits(float z) {
+  uint32_t u = __float_as_uint(z);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ uint64_t depth_key(float z, int tri) {
+  return (static_cast<uint64_t>(order_bits(z)) << 32) | static_cast<uint32_t>(tri);
+}
+
+// Edge vertex pairs in the order the antialiasing scans them: v0v1, v1v2, v2v0.
+__device__ __forceinline__ int edge_p(int e) { return e; }
+__device__ __forceinline__ int edge_q(int e) { return e == 2 ? 0 : e + 1; }
+
+// Unsnapped screen position (pixels, y down) of a clip-space vertex.
+__device__ __forceinline__ float2 screen_of(float4 c, int W, int H) {
+  float iw = 1.0f / c.w;
+  return make_float2((0.5f * c.x * iw + 0.5f) * W, (0.5f - 0.5f * c.y * iw) * H);
+}
+
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f2scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ float4 f4scale(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
+__device__ __forceinline__ float dotv(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
+__device__ __forceinline__ float dotv(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return f2add(a, b); }
+__device__ __forceinline__ float4 vadd(float4 a, float4 b) { return f4add(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return f2sub(a, b); }
+__device__ __forceinline__ float4 vsub(float4 a, float4 b) { return f4sub(a, b); }
+__device__ __forceinline__ float2 vscale(float2 a, float s) { return f2scale(a, s); }
+__device__ __forceinline__ float4 vscale(float4 a, float s) { return f4scale(a, s); }
+template <typename V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// Perspective-correct barycentrics at ndc point (px, py) of the triangle with
+// clip vertices c0..c2: b ~ a x c with a_k = x_k - px w_k, c_k = y_k - py w_k.
+struct Bary {
+  float b[3];
+  float a[3], c[3];
+  float beta[3];
+  float S;
+};
+
+__device__ __forceinline__ Bary bary_at(float4 c0, float4 c1, float4 c2, float px, float py) {
+  Bary r;
+  r.a[0] = fmaf(-px, c0.w, c0.x); r.a[1] = fmaf(-px, c1.w, c1.x); r.a[2] = fmaf(-px, c2.w, c2.x);
+  r.c[0] = fmaf(-py, c0.w, c0.y); r.c[1] = fmaf(-py, c1.w, c1.y); r.c[2] = fmaf(-py, c2.w, c2.y);
+  r.beta[0] = r.a[1] * r.c[2] - r.a[2] * r.c[1];
+  r.beta[1] = r.a[2] * r.c[0] - r.a[0] * r.c[2];
+  r.beta[2] = r.a[0] * r.c[1] - r.a[1] * r.c[0];
+  r.S = r.beta[0] + r.beta[1] + r.beta[2];
+  float iS = 1.0f / r.S;
+  r.b[0] = r.beta[0] * iS; r.b[1] = r.beta[1] * iS; r.b[2] = r.beta[2] * iS;
+  return r;
+}
+
+// Adjoint of bary_at: given dL/db_k, the gradient of the three clip vertices.
+__device__ __forceinline__ void bary_backward(const Bary& r, const float gb[3], float px, float py,
+                                              float4 gc[3]) {
+  float iS = 1.0f / r.S;
+  float mean = gb[0] * r.b[0] + gb[1] * r.b[1] + gb[2] * r.b[2];
+  float gbeta[3] = {(gb[0] - mean) * iS, (gb[1] - mean) * iS, (gb[2] - mean) * iS};
+  // beta = a x c:  dL/da = c x gbeta,  dL/dc = gbeta x a
+  float ga[3] = {r.c[1] * gbeta[2] - r.c[2] * gbeta[1], r.c[2] * gbeta[0] - r.c[0] * gbeta[2],
+                 r.c[0] * gbeta[1] - r.c[1] * gbeta[0]};
+  float gcc[3] = {gbeta[1] * r.a[2] - gbeta[2] * r.a[1], gbeta[2] * r.a[0] - gbeta[0] * r.a[2],
+                  gbeta[0] * r.a[1] - gbeta[1] * r.a[0]};
+  for (int k = 0; k < 3; ++k)
+    gc[k] = make_float4(ga[k], gcc[k], 0.f, -px * ga[k] - py * gcc[k]);
+}
+
+// ndc of the pixel centre: (2i + 1 - W) / W and (H - 2j - 1) / H.
+__device__ __forceinline__ float pix_ndc_x(int i, int W) { return (float)(2 * i + 1 - W) / (float)W; }
+__device__ __forceinline__ float pix_ndc_y(int j, int H) { return (float)(H - 2 * j - 1) / (float)H; }
+
+__device__ __forceinline__ void atomic_add4(float4* p, float4 v) {
+  atomicAdd(p, v);
+}
+__device__ __forceinline__ void atomic_add2(float2* p, float2 v) {
+  atomicAdd(p, v);
+}
+
+}  // namespace dsm

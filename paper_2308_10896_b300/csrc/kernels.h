@@ -1,0 +1,124 @@
+// Launchers of the device kernels (host-callable).  Every launcher enqueues on
+// the given stream and returns immediately.
+#pragma once
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "dsm.h"
+#include "common.cuh"
+
+namespace dsm {
+
+// Process-wide count of launched kernels (reported by dsm_kernel_launches).
+extern std::atomic<unsigned long long> g_kernel_launches;
+inline void count_launches(int n) { g_kernel_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+struct LightConst {
+  int type;
+  int res;
+  double dist, ortho_half, near_plane, far_plane;
+  double persp_c;          // 1 / tan(fov / 2), computed on the host in float64
+  float intensity[3];
+};
+
+struct Mat20 {
+  float v[20];
+};
+
+struct LightSetupArgs {
+  LightConst c[DSM_MAX_LIGHTS];
+  int n;
+};
+
+// Filter weights and the clamp-boundary fold coefficients of the adjoint.
+struct FilterArgs {
+  float w[65];             // taps w[k + r], |k| <= r
+  float fold[33];          // fold[i] = sum of w over taps that leave the map by more than i texels
+  int r;
+  int boundary;            // 0 clamp, 1 zero
+};
+
+struct ShadeArgs {
+  const float4* gbuf;
+  int W, H;
+  const float* verts;
+  const int* tris;
+  const int* tri_mat;
+  const float* albedo;
+  int n_mat;
+  const float* vnormal;    // V x 3, unit vertex normals
+  const float4* cam_clip;  // V, camera clip coordinates
+  const LightDev* lights;
+  int L;
+  const float2* mom[DSM_MAX_LIGHTS];
+  int res[DSM_MAX_LIGHTS];
+  float min_variance;
+};
+
+struct ShadeGradArgs {
+  const float4* gcolor;               // dL/d colour before the final antialiasing
+  float* dverts;                      // V x 3
+  float* gnormal;                     // V x 3, dL/d unit vertex normal
+  float4* gclip;                      // V, dL/d camera clip
+  float* dalbedo;                     // M x 3
+  float2* gm[DSM_MAX_LIGHTS];         // dL/d(m1, m2) texel maps
+  float* gQ;                          // L x 20
+  float* gdirect;                     // L x 3
+};
+
+struct VertGradPtrs {
+  const float4* gclip[DSM_MAX_LIGHTS + 1];   // per view (lights, then camera)
+  const float* gdepth[DSM_MAX_LIGHTS];       // per light
+};
+
+struct AAArgs {
+  const float4* gbuf;
+  int W, H;
+  const int* tris;
+  const uint8_t* sil;
+  const VertSnap* snap;
+  const float4* clip;
+};
+
+void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, cudaStream_t st);
+void launch_transform(const float* verts, int V, const float* M20, int W, int H, float4* clip, VertSnap* snap,
+                      float* depth, cudaStream_t st);
+void launch_tri_setup(const int* tris, int T, const VertSnap* snap, int W, int H, TriSetup* setup, int8_t* orient,
+                      const int* adj, uint8_t* sil, cudaStream_t st);
+void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, cudaStream_t st);
+void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st);
+void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
+                     int capacity, DevStatus* status, cudaStream_t st);
+void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
+                   int W, int H, const float4* clip, const int* tris, float4* gbuf, cudaStream_t st);
+
+// shadow-map interpolation and antialiasing
+void launch_sm_interp(const float4* gbuf, int R, const int* tris, const float* depth, float2* fmap, cudaStream_t st);
+void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, cudaStream_t st);
+void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, cudaStream_t st);
+void launch_sm_backward(const AAArgs& a, const float2* fmap, const float2* gft, const float* depth, float4* gclip,
+                        float* gdepth, int aa, cudaStream_t st);
+void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
+                         int aa, cudaStream_t st);
+
+// separable filter
+void make_filter_args(double sigma, int radius, int kind, int boundary, FilterArgs* fa);
+void launch_filter(const float2* in, float2* tmp, float2* out, int R, const FilterArgs& fa, cudaStream_t st);
+void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, const FilterArgs& fa,
+                           cudaStream_t st);
+
+// normals, shading, vertex gradients
+void launch_vertex_normals(const float* verts, int V, const int* tris, const int* vf_off, const int* vf_list,
+                           float* vnormal, cudaStream_t st);
+void launch_normals_backward(const float* verts, int V, const int* tris, int T, const int* vf_off,
+                             const int* vf_list, const float* gnormal, float* gN, float* gface, float* dverts,
+                             cudaStream_t st);
+void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st);
+void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);
+void launch_vertex_backward(const float* verts, int V, const float* viewM, int n_views, int n_lights,
+                            const VertGradPtrs& gp, float* dverts, float* gQ, cudaStream_t st);
+void launch_light_grad(const LightDev* lights, int L, const float* gQ, const float* gdirect, float* dlight,
+                       cudaStream_t st);
+void launch_l2(const float* img, const float* tgt, int64_t n, float* loss, float* grad, cudaStream_t st);
+
+}  // namespace dsm

@@ -1,0 +1,435 @@
+// Light cameras, pinned vertex transform, triangle setup, binning and the tile
+// rasteriser (Eq. 1: nearest surface per pixel centre).
+#include "dsm.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dsm {
+
+// ------------------------------------------------------------------ light camera
+// Float64 value with its derivative w.r.t. the 6 light parameters
+// (pos xyz, dir xyz).  The value part uses explicitly rounded operations so
+// that the float32 light matrix is reproducible bit for bit.
+struct D6 {
+  double v;
+  double d[6];
+};
+__device__ __forceinline__ D6 dc(double v) {
+  D6 r; r.v = v;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) r.d[i] = 0.0;
+  return r;
+}
+__device__ __forceinline__ D6 dvar(double v, int k) { D6 r = dc(v); r.d[k] = 1.0; return r; }
+__device__ __forceinline__ D6 operator+(const D6& a, const D6& b) {
+  D6 r; r.v = __dadd_rn(a.v, b.v);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+__device__ __forceinline__ D6 operator-(const D6& a, const D6& b) {
+  D6 r; r.v = __dsub_rn(a.v, b.v);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+__device__ __forceinline__ D6 operator-(const D6& a) {
+  D6 r; r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+__device__ __forceinline__ D6 operator*(const D6& a, const D6& b) {
+  D6 r; r.v = __dmul_rn(a.v, b.v);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+__device__ __forceinline__ D6 operator/(const D6& a, const D6& b) {
+  D6 r; r.v = __ddiv_rn(a.v, b.v);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+  return r;
+}
+__device__ __forceinline__ D6 dsqrt(const D6& a) {
+  D6 r; r.v = __dsqrt_rn(a.v);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
+  return r;
+}
+struct V3 { D6 x, y, z; };
+__device__ __forceinline__ D6 dot3(const V3& a, const V3& b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+__device__ __forceinline__ V3 cross3(const V3& a, const V3& b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V3 normalize3(const V3& a) {
+  D6 n = dsqrt((a.x * a.x + a.y * a.y) + a.z * a.z);
+  return {a.x / n, a.y / n, a.z / n};
+}
+
+// One thread per light: Q (clip rows 0-3, depth row 4) in float64, rounded to
+// float32, and J = dQ/d(pos, dir) (supplementary Sec. A light cameras).
+__global__ void light_setup_kernel(const float* __restrict__ params, LightSetupArgs a, LightDev* out,
+                                   float* viewM) {
+  int l = threadIdx.x;
+  if (l >= a.n) return;
+  const LightConst& L = a.c[l];
+  V3 pos = {dvar(params[l * 6 + 0], 0), dvar(params[l * 6 + 1], 1), dvar(params[l * 6 + 2], 2)};
+  V3 dir = {dvar(params[l * 6 + 3], 3), dvar(params[l * 6 + 4], 4), dvar(params[l * 6 + 5], 5)};
+  V3 f = normalize3(dir);
+  V3 up = fabs(f.y.v) > 0.99 ? V3{dc(0.0), dc(0.0), dc(1.0)} : V3{dc(0.0), dc(1.0), dc(0.0)};
+  V3 r = normalize3(cross3(f, up));
+  V3 u = cross3(r, f);
+  D6 nearp = dc(L.near_plane), farp = dc(L.far_plane);
+  V3 e;
+  if (L.type == 0) {
+    D6 md = dc(-(double)L.dist);
+    e = {md * f.x, md * f.y, md * f.z};
+  } else {
+    e = pos;
+  }
+  D6 fe = dot3(f, e);
+  D6 rng = farp - nearp;
+  D6 Q[20];
+  Q[16] = f.x / rng; Q[17] = f.y / rng; Q[18] = f.z / rng; Q[19] = (-fe - nearp) / rng;
+  if (L.type == 0) {
+    D6 h = dc(L.ortho_half);
+    Q[0] = r.x / h; Q[1] = r.y / h; Q[2] = r.z / h; Q[3] = (-dot3(r, e)) / h;
+    Q[4] = u.x / h; Q[5] = u.y / h; Q[6] = u.z / h; Q[7] = (-dot3(u, e)) / h;
+    Q[8] = Q[16]; Q[9] = Q[17]; Q[10] = Q[18]; Q[11] = Q[19];
+    Q[12] = dc(0.0); Q[13] = dc(0.0); Q[14] = dc(0.0); Q[15] = dc(1.0);
+  } else {
+    D6 c = dc(L.persp_c);
+    D6 A = farp / rng;
+    D6 B = (-(farp * nearp)) / rng;
+    Q[0] = c * r.x; Q[1] = c * r.y; Q[2] = c * r.z; Q[3] = -(c * dot3(r, e));
+    Q[4] = c * u.x; Q[5] = c * u.y; Q[6] = c * u.z; Q[7] = -(c * dot3(u, e));
+    Q[8] = A * f.x; Q[9] = A * f.y; Q[10] = A * f.z; Q[11] = (-(A * fe)) + B;
+    Q[12] = f.x; Q[13] = f.y; Q[14] = f.z; Q[15] = -fe;
+  }
+  LightDev& o = out[l];
+  for (int k = 0; k < 20; ++k) {
+    o.Q[k] = __double2float_rn(Q[k].v);
+    viewM[l * 20 + k] = o.Q[k];
+    for (int j = 0; j < 6; ++j) o.J[k * 6 + j] = (float)Q[k].d[j];
+  }
+  o.fwd[0] = (float)f.x.v; o.fwd[1] = (float)f.y.v; o.fwd[2] = (float)f.z.v;
+  o.dir_norm = (float)sqrt(dir.x.v * dir.x.v + dir.y.v * dir.y.v + dir.z.v * dir.z.v);
+  o.pos[0] = params[l * 6 + 0]; o.pos[1] = params[l * 6 + 1]; o.pos[2] = params[l * 6 + 2];
+  o.type = L.type;
+  o.res = L.res;
+  o.intensity[0] = L.intensity[0]; o.intensity[1] = L.intensity[1]; o.intensity[2] = L.intensity[2];
+}
+
+// ------------------------------------------------------------------ vertex transform
+__device__ __forceinline__ float pinned_row(const float* M, float x, float y, float z) {
+  return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], x), __fmul_rn(M[1], y)), __fmul_rn(M[2], z)), M[3]);
+}
+
+// clip = M [v, 1] with separately rounded float32 operations, snapped 24.8
+// screen position, and (lights) the depth row.
+__global__ void transform_kernel(const float* __restrict__ verts, int V, const float* __restrict__ M20,
+                                 int W, int H, float4* __restrict__ clip, VertSnap* __restrict__ snap,
+                                 float* __restrict__ depth) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  float x = verts[3 * v], y = verts[3 * v + 1], z = verts[3 * v + 2];
+  float c0 = pinned_row(M20 + 0, x, y, z);
+  float c1 = pinned_row(M20 + 4, x, y, z);
+  float c2 = pinned_row(M20 + 8, x, y, z);
+  float c3 = pinned_row(M20 + 12, x, y, z);
+  clip[v] = make_float4(c0, c1, c2, c3);
+  if (depth) depth[v] = pinned_row(M20 + 16, x, y, z);
+  float nx = __fdiv_rn(c0, c3), ny = __fdiv_rn(c1, c3), nz = __fdiv_rn(c2, c3);
+  float sx = __fmul_rn(__fadd_rn(__fmul_rn(0.5f, nx), 0.5f), (float)W);
+  float sy = __fmul_rn(__fsub_rn(0.5f, __fmul_rn(0.5f, ny)), (float)H);
+  float fx = __fmul_rn(sx, (float)kSubpix), fy = __fmul_rn(sy, (float)kSubpix);
+  bool ok = (c3 >= kWMin) && (fabsf(fx) <= (float)kGuard) && (fabsf(fy) <= (float)kGuard);
+  VertSnap s;
+  s.X = ok ? __float2int_rn(fx) : 0;
+  s.Y = ok ? __float2int_rn(fy) : 0;
+  s.z = nz;
+  s.ok = ok ? 1 : 0;
+  snap[v] = s;
+}
+
+// ------------------------------------------------------------------ triangle setup
+__global__ void tri_setup_kernel(const int* __restrict__ tris, int T, const VertSnap* __restrict__ snap,
+                                 int W, int H, TriSetup* __restrict__ setup, int8_t* __restrict__ orient) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
+  VertSnap s0 = snap[v0], s1 = snap[v1], s2 = snap[v2];
+  long long area2 = (long long)(s1.X - s0.X) * (s2.Y - s0.Y) - (long long)(s1.Y - s0.Y) * (s2.X - s0.X);
+  bool culled = !(s0.ok && s1.ok && s2.ok) || area2 == 0;
+  int sg = area2 > 0 ? 1 : -1;
+  orient[t] = culled ? 0 : (int8_t)sg;
+  TriSetup r;
+  r.X[0] = s0.X; r.X[1] = s1.X; r.X[2] = s2.X;
+  r.Y[0] = s0.Y; r.Y[1] = s1.Y; r.Y[2] = s2.Y;
+  r.z[0] = s0.z; r.z[1] = s1.z; r.z[2] = s2.z;
+  r.a2f = __ll2float_rn((long long)sg * area2);
+  r.tri = t;
+  r.pad[0] = r.pad[1] = 0;
+  int i0 = 1, i1 = 0, j0 = 1, j1 = 0;
+  int flags = (sg < 0) ? 8 : 0;
+  if (!culled) {
+    long long mnx = min(s0.X, min(s1.X, s2.X)), mxx = max(s0.X, max(s1.X, s2.X));
+    long long mny = min(s0.Y, min(s1.Y, s2.Y)), mxy = max(s0.Y, max(s1.Y, s2.Y));
+    long long a0 = -((128 - mnx) >> 8), a1 = (mxx - 128) >> 8;
+    long long b0 = -((128 - mny) >> 8), b1 = (mxy - 128) >> 8;
+    i0 = (int)max(a0, 0LL); i1 = (int)min(a1, (long long)(W - 1));
+    j0 = (int)max(b0, 0LL); j1 = (int)min(b1, (long long)(H - 1));
+    const int ea[3] = {1, 2, 0}, eb[3] = {2, 0, 1};
+    for (int k = 0; k < 3; ++k) {
+      int Xa = r.X[ea[k]], Ya = r.Y[ea[k]], Xb = r.X[eb[k]], Yb = r.Y[eb[k]];
+      long long ca = -(long long)sg * (Yb - Ya), cb = (long long)sg * (Xb - Xa);
+      if (ca > 0 || (ca == 0 && cb > 0)) flags |= 1 << k;
+    }
+    if (i0 <= i1 && j0 <= j1) flags |= 16;
+  }
+  if (!(flags & 16)) { i0 = 1; i1 = 0; j0 = 1; j1 = 0; }
+  r.ibox = (i0 & 0xffff) | (i1 << 16);
+  r.jbox = (j0 & 0xffff) | (j1 << 16);
+  r.flags = flags;
+  setup[t] = r;
+}
+
+// Silhouette edge mask per triangle: bit e set when edge e (v0v1, v1v2, v2v0)
+// is a boundary / non-manifold edge, the triangle across it is culled, or the
+// two triangles have opposite screen orientation.
+__global__ void silhouette_kernel(const int* __restrict__ adj, int T, const int8_t* __restrict__ orient,
+                                  uint8_t* __restrict__ sil) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  int m = 0;
+  int8_t o = orient[t];
+  for (int e = 0; e < 3; ++e) {
+    int a = adj[3 * t + e];
+    if (a < 0) { m |= 1 << e; continue; }
+    int8_t oa = orient[a];
+    if (oa == 0 || oa != o) m |= 1 << e;
+  }
+  sil[t] = (uint8_t)m;
+}
+
+// ------------------------------------------------------------------ binning
+// Warp-cooperative emission of (triangle, tile) pairs: the 32 triangles of a
+// warp pool their tile ranges and the lanes stride over the pooled pairs, so a
+// triangle spanning thousands of tiles is spread over 32 lanes.
+template <bool kFill>
+__global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX, int* __restrict__ counter,
+                           const int* __restrict__ offset, int* __restrict__ list, int capacity,
+                           DevStatus* status) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = threadIdx.x & 31;
+  int n = 0, tx0 = 0, ty0 = 0, ntx = 1;
+  if (t < T) {
+    int flags = setup[t].flags;
+    if (flags & 16) {
+      int ib = setup[t].ibox, jb = setup[t].jbox;
+      int i0 = ib & 0xffff, i1 = (unsigned)ib >> 16, j0 = jb & 0xffff, j1 = (unsigned)jb >> 16;
+      tx0 = i0 >> kTileLog2; ty0 = j0 >> kTileLog2;
+      ntx = (i1 >> kTileLog2) - tx0 + 1;
+      n = ntx * ((j1 >> kTileLog2) - ty0 + 1);
+    }
+  }
+  int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  int total = __shfl_sync(kFull, incl, 31);
+  int excl = incl - n;
+  for (int base = 0; base < total; base += 32) {
+    int p = base + lane;
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {
+      int e = __shfl_sync(kFull, excl, lo + step);
+      if (e <= p) lo += step;
+    }
+    int o_excl = __shfl_sync(kFull, excl, lo);
+    int o_tx0 = __shfl_sync(kFull, tx0, lo);
+    int o_ty0 = __shfl_sync(kFull, ty0, lo);
+    int o_ntx = __shfl_sync(kFull, ntx, lo);
+    int o_t = __shfl_sync(kFull, t, lo);
+    if (p < total) {
+      int q = p - o_excl;
+      int tile = (o_ty0 + q / o_ntx) * tilesX + o_tx0 + q % o_ntx;
+      if (!kFill) {
+        atomicAdd(&counter[tile], 1);
+      } else {
+        int slot = offset[tile] + atomicAdd(&counter[tile], 1);
+        if (slot < capacity) list[slot] = o_t;
+        else atomicExch(&status->capacity_overflow, 1);
+      }
+    }
+  }
+}
+
+// Single-CTA exclusive scan of the tile counts; offset[n] = total pairs.  Also
+// records the total for the host and clears the counters for the fill pass.
+__global__ void scan_kernel(int* __restrict__ count, int n, int* __restrict__ offset, DevStatus* status,
+                            int view) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int v = i < n ? count[i] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+      int wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(kFull, wi, o);
+        if (lane >= o) wi += u;
+      }
+      warp_sums[lane] = wi - w;
+    }
+    __syncthreads();
+    int c = carry;
+    if (i < n) {
+      offset[i] = c + warp_sums[warp] + incl - v;
+      count[i] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = c + warp_sums[warp] + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    offset[n] = carry;
+    status->needed_pairs[view] = carry;
+  }
+}
+
+// ------------------------------------------------------------------ tile rasteriser
+// One 256-thread CTA per 16x16 tile, one thread per pixel.  The tile's triangle
+// list is staged through shared memory 256 records at a time; every pixel keeps
+// the smallest (depth key, triangle) of the triangles covering its centre
+// (integer edge functions, top-left rule), then writes one 16-byte G-buffer
+// texel: id + 1, perspective-correct b0, b1, depth key.
+__global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict__ setup,
+                                                     const int* __restrict__ offset,
+                                                     const int* __restrict__ list, int capacity, int tilesX,
+                                                     int W, int H,
+                                                     const float4* __restrict__ clip,
+                                                     const int* __restrict__ tris, float4* __restrict__ gbuf) {
+  __shared__ TriSetup s[256];
+  const int tile = blockIdx.x;
+  const int ti = tile % tilesX, tj = tile / tilesX;
+  const int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
+  const int i = ti * kTile + lx, j = tj * kTile + ly;
+  const int warp_j0 = tj * kTile + ((threadIdx.x >> 5) << 1);
+  const long long Px = (long long)i * kSubpix + 128, Py = (long long)j * kSubpix + 128;
+  uint64_t best = ~0ull;
+  float bestz = 0.f;
+  // slots past the list capacity were never written (the fill pass flagged the overflow)
+  const int beg = min(offset[tile], capacity), end = min(offset[tile + 1], capacity);
+  for (int base = beg; base < end; base += 256) {
+    const int n = min(256, end - base);
+    __syncthreads();
+    if ((int)threadIdx.x < n) s[threadIdx.x] = setup[list[base + threadIdx.x]];
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+      const int jb = s[k].jbox;
+      const int j0 = jb & 0xffff, j1 = (unsigned)jb >> 16;
+      if (j1 < warp_j0 || j0 > warp_j0 + 1) continue;           // warp-uniform row reject
+      const int ib = s[k].ibox;
+      const int i0 = ib & 0xffff, i1 = (unsigned)ib >> 16;
+      if (i < i0 || i > i1 || j < j0 || j > j1) continue;
+      const int flags = s[k].flags;
+      const int sg = (flags & 8) ? -1 : 1;
+      long long E[3];
+      bool inside = true;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const int a = e == 0 ? 1 : (e == 1 ? 2 : 0);
+        const int b = e == 0 ? 2 : (e == 1 ? 0 : 1);
+        const int Xa = s[k].X[a], Ya = s[k].Y[a];
+        const long long dx = (long long)(s[k].X[b] - Xa), dy = (long long)(s[k].Y[b] - Ya);
+        long long v = dx * (Py - Ya) - dy * (Px - Xa);
+        v = sg > 0 ? v : -v;
+        E[e] = v;
+        inside &= (v > 0) || (v == 0 && ((flags >> e) & 1));
+      }
+      if (!inside) continue;
+      float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(__ll2float_rn(E[0]), s[k].z[0]),
+                                              __fmul_rn(__ll2float_rn(E[1]), s[k].z[1])),
+                                    __fmul_rn(__ll2float_rn(E[2]), s[k].z[2])),
+                          s[k].a2f);
+      uint64_t key = depth_key(z, s[k].tri);
+      if (key < best) { best = key; bestz = z; }
+    }
+  }
+  if (i >= W || j >= H) return;
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (best != ~0ull) {
+    int t = (int)(best & 0xffffffffu);
+    float4 c0 = clip[tris[3 * t]], c1 = clip[tris[3 * t + 1]], c2 = clip[tris[3 * t + 2]];
+    Bary r = bary_at(c0, c1, c2, pix_ndc_x(i, W), pix_ndc_y(j, H));
+    out = make_float4(__int_as_float(t + 1), r.b[0], r.b[1], bestz);
+  }
+  gbuf[(size_t)j * W + i] = out;
+}
+
+// ------------------------------------------------------------------ launchers
+void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM,
+                        cudaStream_t st) {
+  count_launches(1);
+  light_setup_kernel<<<1, 32, 0, st>>>(params, a, out, viewM);
+}
+
+void launch_transform(const float* verts, int V, const float* M20, int W, int H, float4* clip, VertSnap* snap,
+                      float* depth, cudaStream_t st) {
+  if (V == 0) return;
+  count_launches(1);
+  transform_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, M20, W, H, clip, snap, depth);
+}
+
+void launch_tri_setup(const int* tris, int T, const VertSnap* snap, int W, int H, TriSetup* setup,
+                      int8_t* orient, const int* adj, uint8_t* sil, cudaStream_t st) {
+  if (T == 0) return;
+  count_launches(1);
+  tri_setup_kernel<<<(T + 255) / 256, 256, 0, st>>>(tris, T, snap, W, H, setup, orient);
+  count_launches(1);
+  silhouette_kernel<<<(T + 255) / 256, 256, 0, st>>>(adj, T, orient, sil);
+}
+
+void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, cudaStream_t st) {
+  if (T == 0) return;
+  count_launches(1);
+  bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, nullptr, nullptr, 0, status);
+}
+
+void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st) {
+  count_launches(1);
+  scan_kernel<<<1, 1024, 0, st>>>(count, n, offset, status, view);
+}
+
+void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
+                     int capacity, DevStatus* status, cudaStream_t st) {
+  if (T == 0) return;
+  count_launches(1);
+  bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, offset, list, capacity, status);
+}
+
+void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
+                   int W, int H, const float4* clip, const int* tris, float4* gbuf, cudaStream_t st) {
+  count_launches(1);
+  raster_kernel<<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf);
+}
+
+}  // namespace dsm

@@ -1,0 +1,510 @@
+// Deferred shading of the camera G-buffer (supplementary Sec. A: Lambert summed
+// over lights) with the visibility of Alg. 2 (Sec. 3 Chebyshev bound), its
+// adjoint (Sec. 4), vertex normals, per-vertex gradient gathers and the light
+// parameter chain rule.
+#include "dsm.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dsm {
+
+// ------------------------------------------------------------------ vertex normals
+__device__ __forceinline__ float3 face_normal(const float* __restrict__ verts, const int* __restrict__ tris, int t) {
+  const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+  const float3 v0 = make_float3(verts[3 * a], verts[3 * a + 1], verts[3 * a + 2]);
+  const float3 e1 = make_float3(verts[3 * b] - v0.x, verts[3 * b + 1] - v0.y, verts[3 * b + 2] - v0.z);
+  const float3 e2 = make_float3(verts[3 * c] - v0.x, verts[3 * c + 1] - v0.y, verts[3 * c + 2] - v0.z);
+  return make_float3(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
+}
+
+// Area-weighted sum of the incident face normals (cross(v1 - v0, v2 - v0)), normalised.
+__global__ void vertex_normals_kernel(const float* __restrict__ verts, int V, const int* __restrict__ tris,
+                                      const int* __restrict__ off, const int* __restrict__ lst,
+                                      float* __restrict__ vn, float* __restrict__ Nraw) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  float3 s = make_float3(0.f, 0.f, 0.f);
+  for (int k = off[v]; k < off[v + 1]; ++k) {
+    const float3 f = face_normal(verts, tris, lst[k]);
+    s.x += f.x; s.y += f.y; s.z += f.z;
+  }
+  const float l = sqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
+  const float il = l > 0.f ? 1.f / l : 1.f;
+  vn[3 * v] = s.x * il; vn[3 * v + 1] = s.y * il; vn[3 * v + 2] = s.z * il;
+  if (Nraw) { Nraw[3 * v] = s.x; Nraw[3 * v + 1] = s.y; Nraw[3 * v + 2] = s.z; }
+}
+
+// dL/d(unnormalised vertex normal) from dL/d(unit normal).
+__global__ void normals_bwd_vertex_kernel(const float* __restrict__ verts, int V, const int* __restrict__ tris,
+                                          const int* __restrict__ off, const int* __restrict__ lst,
+                                          const float* __restrict__ gn, float* __restrict__ gN) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  float3 s = make_float3(0.f, 0.f, 0.f);
+  for (int k = off[v]; k < off[v + 1]; ++k) {
+    const float3 f = face_normal(verts, tris, lst[k]);
+    s.x += f.x; s.y += f.y; s.z += f.z;
+  }
+  const float l = sqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
+  float3 r = make_float3(0.f, 0.f, 0.f);
+  if (l > 0.f) {
+    const float il = 1.f / l;
+    const float3 n = make_float3(s.x * il, s.y * il, s.z * il);
+    const float3 g = make_float3(gn[3 * v], gn[3 * v + 1], gn[3 * v + 2]);
+    const float d = n.x * g.x + n.y * g.y + n.z * g.z;
+    r = make_float3((g.x - n.x * d) * il, (g.y - n.y * d) * il, (g.z - n.z * d) * il);
+  } else {
+    r = make_float3(gn[3 * v], gn[3 * v + 1], gn[3 * v + 2]);
+  }
+  gN[3 * v] = r.x; gN[3 * v + 1] = r.y; gN[3 * v + 2] = r.z;
+}
+
+// G_t = sum of dL/dN over the face's corners.
+__global__ void normals_bwd_face_kernel(const int* __restrict__ tris, int T, const float* __restrict__ gN,
+                                        float* __restrict__ gface) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  float3 s = make_float3(0.f, 0.f, 0.f);
+  for (int k = 0; k < 3; ++k) {
+    const int v = tris[3 * t + k];
+    s.x += gN[3 * v]; s.y += gN[3 * v + 1]; s.z += gN[3 * v + 2];
+  }
+  gface[3 * t] = s.x; gface[3 * t + 1] = s.y; gface[3 * t + 2] = s.z;
+}
+
+// F = e1 x e2 (e1 = v1 - v0, e2 = v2 - v0):  dL/de1 = e2 x G,  dL/de2 = G x e1.
+__global__ void normals_bwd_gather_kernel(const float* __restrict__ verts, int V, const int* __restrict__ tris,
+                                          const int* __restrict__ off, const int* __restrict__ lst,
+                                          const float* __restrict__ gface, float* __restrict__ dverts) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  float3 acc = make_float3(0.f, 0.f, 0.f);
+  for (int k = off[v]; k < off[v + 1]; ++k) {
+    const int t = lst[k];
+    const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+    const float3 v0 = make_float3(verts[3 * a], verts[3 * a + 1], verts[3 * a + 2]);
+    const float3 e1 = make_float3(verts[3 * b] - v0.x, verts[3 * b + 1] - v0.y, verts[3 * b + 2] - v0.z);
+    const float3 e2 = make_float3(verts[3 * c] - v0.x, verts[3 * c + 1] - v0.y, verts[3 * c + 2] - v0.z);
+    const float3 G = make_float3(gface[3 * t], gface[3 * t + 1], gface[3 * t + 2]);
+    const float3 g1 = make_float3(e2.y * G.z - e2.z * G.y, e2.z * G.x - e2.x * G.z, e2.x * G.y - e2.y * G.x);
+    const float3 g2 = make_float3(G.y * e1.z - G.z * e1.y, G.z * e1.x - G.x * e1.z, G.x * e1.y - G.y * e1.x);
+    if (v == b) { acc.x += g1.x; acc.y += g1.y; acc.z += g1.z; }
+    if (v == c) { acc.x += g2.x; acc.y += g2.y; acc.z += g2.z; }
+    if (v == a) { acc.x -= g1.x + g2.x; acc.y -= g1.y + g2.y; acc.z -= g1.z + g2.z; }
+  }
+  dverts[3 * v] += acc.x; dverts[3 * v + 1] += acc.y; dverts[3 * v + 2] += acc.z;
+}
+
+// ------------------------------------------------------------------ shading
+struct Surf {
+  int tri, v[3];
+  float b[3];
+  float3 x, nt, n;     // world position, interpolated normal, unit normal
+  float nlen;
+};
+
+__device__ __forceinline__ bool load_surf(const ShadeArgs& a, size_t p, Surf& s) {
+  const float4 g = a.gbuf[p];
+  const int id = __float_as_int(g.x);
+  if (!id) return false;
+  s.tri = id - 1;
+  s.b[0] = g.y; s.b[1] = g.z; s.b[2] = 1.f - g.y - g.z;
+  s.x = make_float3(0.f, 0.f, 0.f);
+  s.nt = make_float3(0.f, 0.f, 0.f);
+  for (int k = 0; k < 3; ++k) {
+    const int v = a.tris[3 * s.tri + k];
+    s.v[k] = v;
+    s.x.x += s.b[k] * a.verts[3 * v]; s.x.y += s.b[k] * a.verts[3 * v + 1]; s.x.z += s.b[k] * a.verts[3 * v + 2];
+    s.nt.x += s.b[k] * a.vnormal[3 * v]; s.nt.y += s.b[k] * a.vnormal[3 * v + 1]; s.nt.z += s.b[k] * a.vnormal[3 * v + 2];
+  }
+  s.nlen = sqrtf(s.nt.x * s.nt.x + s.nt.y * s.nt.y + s.nt.z * s.nt.z);
+  const float il = s.nlen > 0.f ? 1.f / s.nlen : 0.f;
+  s.n = make_float3(s.nt.x * il, s.nt.y * il, s.nt.z * il);
+  return true;
+}
+
+__device__ __forceinline__ int material_of(const ShadeArgs& a, int tri) {
+  const int m = a.tri_mat ? a.tri_mat[tri] : 0;
+  return min(max(m, 0), a.n_mat - 1);     // out-of-range material ids read the nearest table entry
+}
+
+// Lookup of Alg. 2 for one light at world point x: clip, depth d, texel
+// coordinates, bilinear (m1, m2), visibility.
+struct Look {
+  float4 clip;
+  float d;
+  int inside;
+  int i0, j0;            // floor of the texel coordinates
+  float fs, ft;
+  float2 m;
+  float var;
+  int var_clamped;
+  float delta;
+  float vis;
+};
+
+__device__ __forceinline__ Look lookup(const float* Q, const float2* __restrict__ mom, int R, float3 x,
+                                       float min_var) {
+  Look L;
+  L.clip = make_float4(Q[0] * x.x + Q[1] * x.y + Q[2] * x.z + Q[3], Q[4] * x.x + Q[5] * x.y + Q[6] * x.z + Q[7],
+                       Q[8] * x.x + Q[9] * x.y + Q[10] * x.z + Q[11], Q[12] * x.x + Q[13] * x.y + Q[14] * x.z + Q[15]);
+  L.d = Q[16] * x.x + Q[17] * x.y + Q[18] * x.z + Q[19];
+  L.vis = 1.f;
+  L.inside = 0;
+  if (!(L.clip.w > 0.f)) return L;
+  const float u = L.clip.x / L.clip.w, v = L.clip.y / L.clip.w;
+  if (!(fabsf(u) <= 1.f && fabsf(v) <= 1.f)) return L;
+  L.inside = 1;
+  const float s = (0.5f * u + 0.5f) * R - 0.5f, t = (0.5f - 0.5f * v) * R - 0.5f;
+  const float fi = floorf(s), fj = floorf(t);
+  L.i0 = (int)fi; L.j0 = (int)fj;
+  L.fs = s - fi; L.ft = t - fj;
+  const int i0 = min(max(L.i0, 0), R - 1), i1 = min(max(L.i0 + 1, 0), R - 1);
+  const int j0 = min(max(L.j0, 0), R - 1), j1 = min(max(L.j0 + 1, 0), R - 1);
+  const float2 m00 = mom[(size_t)j0 * R + i0], m01 = mom[(size_t)j0 * R + i1];
+  const float2 m10 = mom[(size_t)j1 * R + i0], m11 = mom[(size_t)j1 * R + i1];
+  const float w00 = (1.f - L.fs) * (1.f - L.ft), w01 = L.fs * (1.f - L.ft), w10 = (1.f - L.fs) * L.ft, w11 = L.fs * L.ft;
+  L.m = make_float2(w00 * m00.x + w01 * m01.x + w10 * m10.x + w11 * m11.x,
+                    w00 * m00.y + w01 * m01.y + w10 * m10.y + w11 * m11.y);
+  const float raw = fmaf(-L.m.x, L.m.x, L.m.y);
+  L.var_clamped = !(raw >= min_var);
+  L.var = L.var_clamped ? min_var : raw;
+  L.delta = L.d - L.m.x;
+  L.vis = L.delta <= 0.f ? 1.f : L.var / (L.var + L.delta * L.delta);
+  return L;
+}
+
+__device__ __forceinline__ float3 light_omega(const LightDev& Ld, float3 x, float& len) {
+  if (Ld.type == 0) {
+    len = 1.f;
+    return make_float3(-Ld.fwd[0], -Ld.fwd[1], -Ld.fwd[2]);
+  }
+  const float3 d = make_float3(Ld.pos[0] - x.x, Ld.pos[1] - x.y, Ld.pos[2] - x.z);
+  len = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+  const float il = 1.f / len;
+  return make_float3(d.x * il, d.y * il, d.z * il);
+}
+
+__global__ void shade_kernel(ShadeArgs a, float4* __restrict__ color) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= a.W || j >= a.H) return;
+  const size_t p = (size_t)j * a.W + i;
+  Surf s;
+  if (!load_surf(a, p, s)) { color[p] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
+  float3 rad = make_float3(0.f, 0.f, 0.f);
+  for (int l = 0; l < a.L; ++l) {
+    const LightDev& Ld = a.lights[l];
+    const Look L = lookup(Ld.Q, a.mom[l], a.res[l], s.x, a.min_variance);
+    float len;
+    const float3 om = light_omega(Ld, s.x, len);
+    const float lam = fmaxf(s.n.x * om.x + s.n.y * om.y + s.n.z * om.z, 0.f);
+    const float k = L.vis * lam;
+    rad.x += k * Ld.intensity[0]; rad.y += k * Ld.intensity[1]; rad.z += k * Ld.intensity[2];
+  }
+  const int mat = material_of(a, s.tri);
+  color[p] = make_float4(a.albedo[3 * mat] * rad.x, a.albedo[3 * mat + 1] * rad.y, a.albedo[3 * mat + 2] * rad.z, 1.f);
+}
+
+// Warp-sum of v, added once per warp into a shared-memory accumulator.
+__device__ __forceinline__ void warp_add_shared(float* dst, float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(dst, v);
+}
+
+constexpr int kMaxSharedMat = 256;
+
+// Adjoint of shade_kernel (and of the camera interpolation): every covered pixel
+// scatters onto the albedo table, the texel maps dL/d(m1, m2), the light
+// matrices Q, the direct light terms (omega), the vertices (x), the vertex
+// normals and the camera clip coordinates (barycentrics).
+__global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g) {
+  __shared__ float sQ[DSM_MAX_LIGHTS * 20];
+  __shared__ float sD[DSM_MAX_LIGHTS * 3];
+  __shared__ float sA[kMaxSharedMat * 3];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const bool mat_shared = a.n_mat <= kMaxSharedMat;
+  for (int k = tid; k < DSM_MAX_LIGHTS * 20; k += 256) sQ[k] = 0.f;
+  for (int k = tid; k < DSM_MAX_LIGHTS * 3; k += 256) sD[k] = 0.f;
+  for (int k = tid; k < kMaxSharedMat * 3; k += 256) sA[k] = 0.f;
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const bool inb = i < a.W && j < a.H;
+  const size_t p = inb ? (size_t)j * a.W + i : 0;
+  Surf s;
+  const bool cov = inb && load_surf(a, p, s);
+  float4 gc4 = cov ? g.gcolor[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool act = cov && (gc4.x != 0.f || gc4.y != 0.f || gc4.z != 0.f);
+  float3 gx = make_float3(0.f, 0.f, 0.f), gn = make_float3(0.f, 0.f, 0.f);
+  int mat = 0;
+  float3 alb = make_float3(0.f, 0.f, 0.f), rad = make_float3(0.f, 0.f, 0.f);
+  if (act) {
+    mat = material_of(a, s.tri);
+    alb = make_float3(a.albedo[3 * mat], a.albedo[3 * mat + 1], a.albedo[3 * mat + 2]);
+  }
+  const float3 grad_rad = make_float3(gc4.x * alb.x, gc4.y * alb.y, gc4.z * alb.z);
+  for (int l = 0; l < a.L; ++l) {
+    float gq[20];
+#pragma unroll
+    for (int k = 0; k < 20; ++k) gq[k] = 0.f;
+    float3 gdir = make_float3(0.f, 0.f, 0.f);
+    if (act) {
+      const LightDev& Ld = a.lights[l];
+      const int R = a.res[l];
+      const Look L = lookup(Ld.Q, a.mom[l], R, s.x, a.min_variance);
+      float len;
+      const float3 om = light_omega(Ld, s.x, len);
+      const float ndo = s.n.x * om.x + s.n.y * om.y + s.n.z * om.z;
+      const float lam = fmaxf(ndo, 0.f);
+      rad.x += L.vis * lam * Ld.intensity[0]; rad.y += L.vis * lam * Ld.intensity[1]; rad.z += L.vis * lam * Ld.intensity[2];
+      const float sl = grad_rad.x * Ld.intensity[0] + grad_rad.y * Ld.intensity[1] + grad_rad.z * Ld.intensity[2];
+      const float gvis = sl * lam, glam = sl * L.vis;
+      if (ndo > 0.f && glam != 0.f) {
+        gn.x += glam * om.x; gn.y += glam * om.y; gn.z += glam * om.z;
+        const float3 gom = make_float3(glam * s.n.x, glam * s.n.y, glam * s.n.z);
+        if (Ld.type == 0) {
+          gdir = gom;                    // dL/d omega, omega = -fwd (chained on the host side kernel)
+        } else {
+          const float d = om.x * gom.x + om.y * gom.y + om.z * gom.z;
+          const float il = 1.f / len;
+          const float3 gp = make_float3((gom.x - om.x * d) * il, (gom.y - om.y * d) * il, (gom.z - om.z * d) * il);
+          gdir = gp;                     // dL/d pos (direct)
+          gx.x -= gp.x; gx.y -= gp.y; gx.z -= gp.z;
+        }
+      }
+      if (L.inside && L.delta > 0.f && gvis != 0.f) {
+        const float S = L.var + L.delta * L.delta;
+        const float iS2 = 1.f / (S * S);
+        const float dv_dvar = L.delta * L.delta * iS2;
+        const float dv_ddelta = -2.f * L.var * L.delta * iS2;
+        const float gd = gvis * dv_ddelta;
+        float gm1 = -gd, gm2 = 0.f;
+        if (!L.var_clamped) {
+          gm1 += gvis * dv_dvar * (-2.f * L.m.x);
+          gm2 = gvis * dv_dvar;
+        }
+        // bilinear adjoint: texel gradients and dL/d(s, t)
+        const int i0 = min(max(L.i0, 0), R - 1), i1 = min(max(L.i0 + 1, 0), R - 1);
+        const int j0 = min(max(L.j0, 0), R - 1), j1 = min(max(L.j0 + 1, 0), R - 1);
+        const float w00 = (1.f - L.fs) * (1.f - L.ft), w01 = L.fs * (1.f - L.ft), w10 = (1.f - L.fs) * L.ft,
+                    w11 = L.fs * L.ft;
+        float2* gm = g.gm[l];
+        atomic_add2(&gm[(size_t)j0 * R + i0], make_float2(w00 * gm1, w00 * gm2));
+        atomic_add2(&gm[(size_t)j0 * R + i1], make_float2(w01 * gm1, w01 * gm2));
+        atomic_add2(&gm[(size_t)j1 * R + i0], make_float2(w10 * gm1, w10 * gm2));
+        atomic_add2(&gm[(size_t)j1 * R + i1], make_float2(w11 * gm1, w11 * gm2));
+        const float2* mom = a.mom[l];
+        const float2 m00 = mom[(size_t)j0 * R + i0], m01 = mom[(size_t)j0 * R + i1];
+        const float2 m10 = mom[(size_t)j1 * R + i0], m11 = mom[(size_t)j1 * R + i1];
+        const float d00 = m00.x * gm1 + m00.y * gm2, d01 = m01.x * gm1 + m01.y * gm2;
+        const float d10 = m10.x * gm1 + m10.y * gm2, d11 = m11.x * gm1 + m11.y * gm2;
+        const float gfs = (1.f - L.ft) * (d01 - d00) + L.ft * (d11 - d10);
+        const float gft = (1.f - L.fs) * (d10 - d00) + L.fs * (d11 - d01);
+        // s = (0.5 u + 0.5) R - 0.5,  t = (0.5 - 0.5 v) R - 0.5,  u = cx / cw,  v = cy / cw
+        const float gu = gfs * 0.5f * R, gv = -gft * 0.5f * R;
+        const float iw = 1.f / L.clip.w;
+        const float u = L.clip.x * iw, v = L.clip.y * iw;
+        const float gcl[4] = {gu * iw, gv * iw, 0.f, -(gu * u + gv * v) * iw};
+        const float xh[4] = {s.x.x, s.x.y, s.x.z, 1.f};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) gq[r * 4 + c] = gcl[r] * xh[c];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) gq[16 + c] = gd * xh[c];
+        const float* Q = Ld.Q;
+        gx.x += Q[0] * gcl[0] + Q[4] * gcl[1] + Q[12] * gcl[3] + Q[16] * gd;
+        gx.y += Q[1] * gcl[0] + Q[5] * gcl[1] + Q[13] * gcl[3] + Q[17] * gd;
+        gx.z += Q[2] * gcl[0] + Q[6] * gcl[1] + Q[14] * gcl[3] + Q[18] * gd;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 20; ++k) warp_add_shared(&sQ[l * 20 + k], gq[k]);
+    warp_add_shared(&sD[l * 3 + 0], gdir.x);
+    warp_add_shared(&sD[l * 3 + 1], gdir.y);
+    warp_add_shared(&sD[l * 3 + 2], gdir.z);
+  }
+  if (act) {
+    const float3 ga = make_float3(gc4.x * rad.x, gc4.y * rad.y, gc4.z * rad.z);
+    if (mat_shared) {
+      atomicAdd(&sA[3 * mat], ga.x); atomicAdd(&sA[3 * mat + 1], ga.y); atomicAdd(&sA[3 * mat + 2], ga.z);
+    } else {
+      atomicAdd(&g.dalbedo[3 * mat], ga.x); atomicAdd(&g.dalbedo[3 * mat + 1], ga.y);
+      atomicAdd(&g.dalbedo[3 * mat + 2], ga.z);
+    }
+    // unit normal n = nt / |nt|
+    float3 gnt = make_float3(0.f, 0.f, 0.f);
+    if (s.nlen > 0.f) {
+      const float d = s.n.x * gn.x + s.n.y * gn.y + s.n.z * gn.z;
+      const float il = 1.f / s.nlen;
+      gnt = make_float3((gn.x - s.n.x * d) * il, (gn.y - s.n.y * d) * il, (gn.z - s.n.z * d) * il);
+    }
+    float gb[3];
+    for (int k = 0; k < 3; ++k) {
+      const int v = s.v[k];
+      atomicAdd(&g.dverts[3 * v], s.b[k] * gx.x);
+      atomicAdd(&g.dverts[3 * v + 1], s.b[k] * gx.y);
+      atomicAdd(&g.dverts[3 * v + 2], s.b[k] * gx.z);
+      atomicAdd(&g.gnormal[3 * v], s.b[k] * gnt.x);
+      atomicAdd(&g.gnormal[3 * v + 1], s.b[k] * gnt.y);
+      atomicAdd(&g.gnormal[3 * v + 2], s.b[k] * gnt.z);
+      gb[k] = a.verts[3 * v] * gx.x + a.verts[3 * v + 1] * gx.y + a.verts[3 * v + 2] * gx.z +
+              a.vnormal[3 * v] * gnt.x + a.vnormal[3 * v + 1] * gnt.y + a.vnormal[3 * v + 2] * gnt.z;
+    }
+    const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
+    const Bary r = bary_at(a.cam_clip[s.v[0]], a.cam_clip[s.v[1]], a.cam_clip[s.v[2]], px, py);
+    float4 gcv[3];
+    bary_backward(r, gb, px, py, gcv);
+    for (int k = 0; k < 3; ++k) atomic_add4(&g.gclip[s.v[k]], gcv[k]);
+  }
+  __syncthreads();
+  for (int k = tid; k < a.L * 20; k += 256)
+    if (sQ[k] != 0.f) atomicAdd(&g.gQ[k], sQ[k]);
+  for (int k = tid; k < a.L * 3; k += 256)
+    if (sD[k] != 0.f) atomicAdd(&g.gdirect[k], sD[k]);
+  if (mat_shared)
+    for (int k = tid; k < a.n_mat * 3; k += 256)
+      if (sA[k] != 0.f) atomicAdd(&g.dalbedo[k], sA[k]);
+}
+
+
+// ------------------------------------------------------------------ per-vertex gathers
+// dL/dv += M^T dL/dclip for every view (+ depth row for lights);
+// dL/dQ_l += dL/dclip (x) [v, 1] and dL/dd (x) [v, 1].
+__global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __restrict__ verts, int V,
+                                                              const float* __restrict__ viewM, int n_views,
+                                                              int n_lights, VertGradPtrs gp,
+                                                              float* __restrict__ dverts, float* __restrict__ gQ) {
+  __shared__ float sQ[DSM_MAX_LIGHTS * 20];
+  for (int k = threadIdx.x; k < DSM_MAX_LIGHTS * 20; k += blockDim.x) sQ[k] = 0.f;
+  __syncthreads();
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = v < V;
+  const float xh[4] = {ok ? verts[3 * v] : 0.f, ok ? verts[3 * v + 1] : 0.f, ok ? verts[3 * v + 2] : 0.f, 1.f};
+  float3 acc = make_float3(0.f, 0.f, 0.f);
+  for (int w = 0; w < n_views; ++w) {
+    const float* M = viewM + 20 * w;
+    const float4 gc = ok ? gp.gclip[w][v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool is_light = w < n_lights;
+    const float gd = (ok && is_light) ? gp.gdepth[w][v] : 0.f;
+    acc.x += M[0] * gc.x + M[4] * gc.y + M[8] * gc.z + M[12] * gc.w + (is_light ? M[16] * gd : 0.f);
+    acc.y += M[1] * gc.x + M[5] * gc.y + M[9] * gc.z + M[13] * gc.w + (is_light ? M[17] * gd : 0.f);
+    acc.z += M[2] * gc.x + M[6] * gc.y + M[10] * gc.z + M[14] * gc.w + (is_light ? M[18] * gd : 0.f);
+    if (is_light) {
+      const float g5[5] = {gc.x, gc.y, gc.z, gc.w, gd};
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) warp_add_shared(&sQ[w * 20 + r * 4 + c], g5[r] * xh[c]);
+    }
+  }
+  if (ok) {
+    dverts[3 * v] += acc.x; dverts[3 * v + 1] += acc.y; dverts[3 * v + 2] += acc.z;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n_lights * 20; k += blockDim.x)
+    if (sQ[k] != 0.f) atomicAdd(&gQ[k], sQ[k]);
+}
+
+// dL/d(pos, dir) = J^T dL/dQ + the direct terms of the shading direction omega:
+// directional omega = -dir / |dir|, spot omega = normalize(pos - x).
+__global__ void light_grad_kernel(const LightDev* __restrict__ lights, int L, const float* __restrict__ gQ,
+                                  const float* __restrict__ gdirect, float* __restrict__ dlight) {
+  const int l = blockIdx.x;
+  const int j = threadIdx.x;
+  if (l >= L || j >= 6) return;
+  const LightDev& Ld = lights[l];
+  float acc = 0.f;
+  for (int k = 0; k < 20; ++k) acc += gQ[l * 20 + k] * Ld.J[k * 6 + j];
+  const float* gd = gdirect + 3 * l;
+  if (Ld.type == 1) {
+    if (j < 3) acc += gd[j];
+  } else if (j >= 3) {
+    const int c = j - 3;
+    const float* f = Ld.fwd;
+    const float fg = f[0] * gd[0] + f[1] * gd[1] + f[2] * gd[2];
+    acc += -(gd[c] - f[c] * fg) / Ld.dir_norm;
+  }
+  dlight[l * 6 + j] = acc;
+}
+
+__global__ void l2_kernel(const float* __restrict__ img, const float* __restrict__ tgt, int64_t n,
+                          float* __restrict__ loss, float* __restrict__ grad) {
+  float acc = 0.f;
+  const float sc = 2.0f / (float)n;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const float d = img[k] - tgt[k];
+    grad[k] = sc * d;
+    acc += d * d;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  __shared__ float ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (threadIdx.x == 0) atomicAdd(loss, v / (float)n);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+static inline dim3 grid2(int W, int H, dim3 b) { return dim3((W + b.x - 1) / b.x, (H + b.y - 1) / b.y); }
+
+void launch_vertex_normals(const float* verts, int V, const int* tris, const int* vf_off, const int* vf_list,
+                           float* vnormal, cudaStream_t st) {
+  if (V == 0) return;
+  count_launches(1);
+  vertex_normals_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, tris, vf_off, vf_list, vnormal, nullptr);
+}
+
+void launch_normals_backward(const float* verts, int V, const int* tris, int T, const int* vf_off,
+                             const int* vf_list, const float* gnormal, float* gN, float* gface, float* dverts,
+                             cudaStream_t st) {
+  if (V == 0 || T == 0) return;
+  count_launches(1);
+  normals_bwd_vertex_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, tris, vf_off, vf_list, gnormal, gN);
+  count_launches(1);
+  normals_bwd_face_kernel<<<(T + 255) / 256, 256, 0, st>>>(tris, T, gN, gface);
+  count_launches(1);
+  normals_bwd_gather_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, tris, vf_off, vf_list, gface, dverts);
+}
+
+void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st) {
+  dim3 b(32, 8);
+  count_launches(1);
+  shade_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, color);
+}
+
+void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st) {
+  dim3 b(32, 8);
+  count_launches(1);
+  shade_backward_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, g);
+}
+
+void launch_vertex_backward(const float* verts, int V, const float* viewM, int n_views, int n_lights,
+                            const VertGradPtrs& gp, float* dverts, float* gQ, cudaStream_t st) {
+  if (V == 0) return;
+  count_launches(1);
+  vertex_backward_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, viewM, n_views, n_lights, gp, dverts, gQ);
+}
+
+void launch_light_grad(const LightDev* lights, int L, const float* gQ, const float* gdirect, float* dlight,
+                       cudaStream_t st) {
+  if (L == 0) return;
+  count_launches(1);
+  light_grad_kernel<<<L, 32, 0, st>>>(lights, L, gQ, gdirect, dlight);
+}
+
+void launch_l2(const float* img, const float* tgt, int64_t n, float* loss, float* grad, cudaStream_t st) {
+  cudaMemsetAsync(loss, 0, sizeof(float), st);
+  if (n == 0) return;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  count_launches(1);
+  l2_kernel<<<blocks, 256, 0, st>>>(img, tgt, n, loss, grad);
+}
+
+}  // namespace dsm

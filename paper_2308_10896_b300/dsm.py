@@ -1,0 +1,293 @@
+"""Thin Python binding of the C ABI in ``include/dsm.h`` (ctypes).
+
+Argument marshalling only: every step of the shadow-mapping path runs in the
+CUDA kernels of ``libdsm.so``.  Torch provides device memory and streams.  The
+library must be built (``python -m paper_2308_10896_b300.build``); there is no
+fallback when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdsm.so")
+
+DSM_OK, DSM_ERR_INVALID_ARG, DSM_ERR_CAPACITY, DSM_ERR_CUDA, DSM_ERR_TIMEOUT, DSM_ERR_NO_FORWARD, DSM_ERR_OOM, \
+    DSM_ERR_NO_TOPOLOGY = range(8)
+MAX_LIGHTS = 8
+
+# debug_copy buffer codes (see include/dsm.h)
+DBG_GBUF, DBG_F, DBG_FTILDE, DBG_MOMENTS, DBG_COLOR, DBG_Q, DBG_SNAP, DBG_GM, DBG_GCLIP, DBG_GFT, DBG_GCOLOR = range(11)
+
+EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_render_backward",
+            "dsm_l2_loss_grad", "dsm_filter_moments", "dsm_sync", "dsm_last_error", "dsm_debug_copy",
+            "dsm_profile_enable", "dsm_profile_stage_count", "dsm_profile_stage_name", "dsm_profile_read",
+            "dsm_kernel_launches"]
+
+
+class DsmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dsm status {status}: {msg}")
+        self.status = status
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("n_verts", ctypes.c_int32), ("tris", ctypes.c_void_p),
+                ("n_tris", ctypes.c_int32), ("tri_material", ctypes.c_void_p), ("albedo", ctypes.c_void_p),
+                ("n_materials", ctypes.c_int32)]
+
+
+class Light(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("res", ctypes.c_int32), ("fov_y_deg", ctypes.c_float),
+                ("ortho_half", ctypes.c_float), ("dist", ctypes.c_float), ("near_plane", ctypes.c_float),
+                ("far_plane", ctypes.c_float), ("intensity", ctypes.c_float * 3), ("sigma", ctypes.c_float),
+                ("radius", ctypes.c_int32)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("clip", ctypes.c_float * 16), ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("min_variance", ctypes.c_float), ("filter_kind", ctypes.c_int32),
+                ("filter_boundary", ctypes.c_int32), ("aa_shadow", ctypes.c_int32), ("aa_final", ctypes.c_int32),
+                ("recompute_in_backward", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libdsm.so (raises when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2308_10896_b300.build`")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, S = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "dsm_create": ([ctypes.POINTER(P)], I32),
+        "dsm_destroy": ([P], None),
+        "dsm_set_topology": ([P, P, I32, I32], I32),
+        "dsm_render": ([P, ctypes.POINTER(Mesh), ctypes.POINTER(Light), P, I32, ctypes.POINTER(Camera),
+                        ctypes.POINTER(Params), P], I32),
+        "dsm_render_backward": ([P, P, P, P, P], I32),
+        "dsm_l2_loss_grad": ([P, P, I64, P, P, P], I32),
+        "dsm_filter_moments": ([P, P, P, I32, ctypes.c_float, I32, I32, I32, P], I32),
+        "dsm_sync": ([P], I32),
+        "dsm_last_error": ([P], ctypes.c_char_p),
+        "dsm_debug_copy": ([P, I32, I32, P, S], I32),
+        "dsm_profile_enable": ([P, I32], I32),
+        "dsm_profile_stage_count": ([], I32),
+        "dsm_profile_stage_name": ([I32], ctypes.c_char_p),
+        "dsm_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), I32], I32),
+        "dsm_kernel_launches": ([], ctypes.c_uint64),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("tensors passed to the library must be contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def light_struct(d: dict) -> Light:
+    L = Light()
+    L.type = int(d["type"])
+    L.res = int(d["res"])
+    L.fov_y_deg = float(d.get("fov_y_deg", 0.0))
+    L.ortho_half = float(d.get("ortho_half", 0.0))
+    L.dist = float(d.get("dist", 0.0))
+    L.near_plane = float(d["near"])
+    L.far_plane = float(d["far"])
+    for k in range(3):
+        L.intensity[k] = float(d["intensity"][k])
+    L.sigma = float(d["sigma"])
+    L.radius = int(d.get("radius", 0))
+    return L
+
+
+def camera_struct(cam: dict) -> Camera:
+    c = Camera()
+    m = np.asarray(cam["clip"], np.float32).reshape(-1)
+    for k in range(16):
+        c.clip[k] = float(m[k])
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    return c
+
+
+def params_struct(p: dict, stream=None) -> Params:
+    q = Params()
+    q.min_variance = float(p.get("min_variance", 1e-6))
+    q.filter_kind = int(p.get("filter_kind", 0))
+    q.filter_boundary = int(p.get("filter_boundary", 0))
+    q.aa_shadow = int(p.get("aa_shadow", 1))
+    q.aa_final = int(p.get("aa_final", 1))
+    q.recompute_in_backward = 0
+    q.stream = _stream_ptr(stream)
+    return q
+
+
+class Context:
+    """Owner of one dsm_ctx (scratch memory and the state of the last forward)."""
+
+    def __init__(self):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        self._check(self.lib.dsm_create(ctypes.byref(h)), None)
+        self.h = h
+
+    def _check(self, status: int, h=None):
+        if status != DSM_OK:
+            msg = self.lib.dsm_last_error(h if h is not None else getattr(self, "h", None))
+            raise DsmError(status, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dsm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_topology(self, tris: torch.Tensor, n_verts: int):
+        self._check(self.lib.dsm_set_topology(self.h, _ptr(tris), tris.shape[0], n_verts), self.h)
+
+    def render(self, mesh: Mesh, lights, light_params: torch.Tensor, camera: Camera, params: Params,
+               image: torch.Tensor):
+        arr = (Light * max(1, len(lights)))(*lights)
+        self._check(self.lib.dsm_render(self.h, ctypes.byref(mesh), arr, _ptr(light_params), len(lights),
+                                        ctypes.byref(camera), ctypes.byref(params), _ptr(image)), self.h)
+
+    def render_backward(self, dL_dimage, dverts=None, dlight=None, dalbedo=None):
+        self._check(self.lib.dsm_render_backward(self.h, _ptr(dL_dimage), _ptr(dverts), _ptr(dlight),
+                                                 _ptr(dalbedo)), self.h)
+
+    def filter_moments(self, inp: torch.Tensor, out: torch.Tensor, sigma: float, radius: int = 0, kind: int = 0,
+                       boundary: int = 0, stream=None):
+        self._check(self.lib.dsm_filter_moments(self.h, _ptr(inp), _ptr(out), inp.shape[0], float(sigma),
+                                                int(radius), int(kind), int(boundary), _stream_ptr(stream)), self.h)
+
+    def sync(self):
+        self._check(self.lib.dsm_sync(self.h), self.h)
+
+    def profile(self, enable: bool):
+        self._check(self.lib.dsm_profile_enable(self.h, 1 if enable else 0), self.h)
+
+    def profile_read(self) -> dict:
+        n = self.lib.dsm_profile_stage_count()
+        ms = (ctypes.c_double * n)()
+        calls = (ctypes.c_int64 * n)()
+        self._check(self.lib.dsm_profile_read(self.h, ms, calls, n), self.h)
+        return {self.lib.dsm_profile_stage_name(i).decode(): (ms[i], calls[i]) for i in range(n)}
+
+    def debug(self, what: int, index: int, shape, dtype=torch.float32) -> torch.Tensor:
+        out = torch.empty(shape, dtype=dtype, device="cuda")
+        self._check(self.lib.dsm_debug_copy(self.h, what, index, _ptr(out), out.numel() * out.element_size()),
+                    self.h)
+        return out
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load_library().dsm_kernel_launches())
+
+
+def l2_loss_grad(image: torch.Tensor, target: torch.Tensor, loss: torch.Tensor, grad: torch.Tensor, stream=None):
+    """Fused L = mean((image - target)^2) and dL/dimage on the device."""
+    lib = load_library()
+    st = lib.dsm_l2_loss_grad(_ptr(image), _ptr(target), image.numel(), _ptr(loss), _ptr(grad), _stream_ptr(stream))
+    if st != DSM_OK:
+        raise DsmError(st, "dsm_l2_loss_grad")
+
+
+class Renderer:
+    """Scene held on the device plus a context: forward / backward of the
+    differentiable shadow-mapping renderer for one camera."""
+
+    def __init__(self, scene: dict, device: str = "cuda"):
+        self.ctx = Context()
+        self.device = device
+        self.verts = torch.as_tensor(scene["verts"], dtype=torch.float32, device=device).contiguous()
+        self.tris = torch.as_tensor(scene["tris"], dtype=torch.int32, device=device).contiguous()
+        self.tri_mat = torch.as_tensor(scene["tri_mat"], dtype=torch.int32, device=device).contiguous()
+        self.albedo = torch.as_tensor(scene["albedo"], dtype=torch.float32, device=device).contiguous()
+        self.light_params = torch.as_tensor(
+            np.stack([np.concatenate([l["pos"], l["dir"]]) for l in scene["lights"]]).astype(np.float32)
+            if scene["lights"] else np.zeros((0, 6), np.float32), device=device).contiguous()
+        self.lights = [light_struct(l) for l in scene["lights"]]
+        self.camera_dict = scene["camera"]
+        self.camera = camera_struct(scene["camera"])
+        self.params_dict = dict(scene["params"])
+        self.W, self.H = int(scene["camera"]["width"]), int(scene["camera"]["height"])
+        self.ctx.set_topology(self.tris, self.verts.shape[0])
+
+    def set_camera(self, cam: dict):
+        self.camera_dict = cam
+        self.camera = camera_struct(cam)
+        self.W, self.H = int(cam["width"]), int(cam["height"])
+
+    def mesh_struct(self, verts=None, albedo=None) -> Mesh:
+        v = self.verts if verts is None else verts
+        a = self.albedo if albedo is None else albedo
+        self._keep = (v, a)
+        return Mesh(_ptr(v), v.shape[0], _ptr(self.tris), self.tris.shape[0], _ptr(self.tri_mat), _ptr(a),
+                    a.shape[0])
+
+    def forward(self, verts=None, light_params=None, albedo=None, image=None, stream=None) -> torch.Tensor:
+        lp = self.light_params if light_params is None else light_params
+        if image is None:
+            image = torch.empty((self.H, self.W, 4), dtype=torch.float32, device=self.device)
+        self.ctx.render(self.mesh_struct(verts, albedo), self.lights, lp, self.camera,
+                        params_struct(self.params_dict, stream), image)
+        return image
+
+    def backward(self, dL_dimage: torch.Tensor, dverts=None, dlight=None, dalbedo=None):
+        V, L, M = self.verts.shape[0], len(self.lights), self.albedo.shape[0]
+        dverts = torch.empty((V, 3), dtype=torch.float32, device=self.device) if dverts is None else dverts
+        dlight = torch.empty((max(L, 1), 6), dtype=torch.float32, device=self.device) if dlight is None else dlight
+        dalbedo = torch.empty((M, 3), dtype=torch.float32, device=self.device) if dalbedo is None else dalbedo
+        self.ctx.render_backward(dL_dimage.contiguous(), dverts, dlight, dalbedo)
+        return dverts, dlight[:L], dalbedo
+
+
+class DSMFunction(torch.autograd.Function):
+    """image = render(verts, light_params, albedo) with the library's own
+    backward.  The renderer's context keeps the forward state: call backward
+    before the next forward on the same renderer."""
+
+    @staticmethod
+    def forward(ctx, verts, light_params, albedo, renderer: Renderer):
+        image = renderer.forward(verts.contiguous(), light_params.contiguous(), albedo.contiguous())
+        ctx.renderer = renderer
+        return image
+
+    @staticmethod
+    def backward(ctx, grad_image):
+        dv, dl, da = ctx.renderer.backward(grad_image.contiguous())
+        return dv, dl, da, None
+
+
+def render(verts, light_params, albedo, renderer: Renderer):
+    return DSMFunction.apply(verts, light_params, albedo, renderer)
