@@ -1,0 +1,464 @@
+#!/usr/bin/env python
+"""Forward+backward throughput of differentiable variance shadow mapping on B300.
+
+One step = the whole hot path on one frame: per light the shadow-map raster,
+the edge antialiasing of (f, f^2) and the moment filter (Alg. 1); the camera
+raster, the moment lookup with Chebyshev visibility times Lambert (Alg. 2) and
+the final antialiasing; the fused L2 loss gradient; and the backward pass to
+dL/d vertices, light position/direction and albedo.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank renders its
+own seeded replica of the workload (no data-path collective: the frames are
+independent), times are the max over ranks, and value = all frames / time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd shadowed frames/s (330k tris, 1024² img, 2048² SM) and % HBM roofline"
+UNIT = "frames/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+
+
+# ----------------------------------------------------------------------------- workload
+def make_workload(name: str, item: int):
+    import scenes
+    if name == "config3":
+        sc = scenes.config3(item)
+        desc = ("330k-triangle scene: 64 SH-displaced icospheres / subdivided boxes on a 20x20 plane, "
+                "one directional + one spot light with 2048^2 moment maps (sigma 2, 9 taps), "
+                "1920x1080 camera, fwd+bwd of an L2 image loss")
+    elif name == "config2":
+        sc = scenes.config2(item)
+        desc = "50k-triangle displaced icosphere, spot light 1024^2 map (sigma 2), 1024^2 camera, fwd+bwd L2"
+    elif name == "config1":
+        sc = scenes.config1(item)
+        desc = "1280-triangle icosphere over a quad, directional light 256^2 map (sigma 1.5), 256^2 camera, fwd+bwd L2"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return sc, desc
+
+
+def workload_config(name, sc, desc):
+    cam = sc["camera"]
+    return {"workload": f"{name}: {desc}", "triangles": int(sc["tris"].shape[0]),
+            "vertices": int(sc["verts"].shape[0]), "lights": len(sc["lights"]),
+            "shadow_maps": [int(l["res"]) for l in sc["lights"]],
+            "image": f"{cam['width']}x{cam['height']}",
+            "l2_policy": "no flush: per-step working set (G-buffers, moment and gradient maps) > 126 MB L2"}
+
+
+# ----------------------------------------------------------------------------- algorithmic bytes per stage
+def stage_bytes(sc) -> dict:
+    """Algorithmic DRAM bytes of one call of each timed stage (every
+    materialised buffer counted once; neighbour re-reads not counted)."""
+    V, T = int(sc["verts"].shape[0]), int(sc["tris"].shape[0])
+    L = len(sc["lights"])
+    Rs = [int(l["res"]) ** 2 for l in sc["lights"]]
+    WH = int(sc["camera"]["width"]) * int(sc["camera"]["height"])
+    views = L + 1
+    texels = sum(Rs)
+    return {
+        # transform (12 V in, 32 V out, +4 V depth) and triangle setup (12 T in, 64 T + 2 T out), binning count
+        "setup": views * (12 * V + 32 * V + 12 * T + 66 * T + 64 * T) + L * 4 * V,
+        "bin_fill": views * (64 * T + 4 * T),
+        # setup records and lists read once, one 16-byte G-buffer texel written per pixel
+        "raster": views * (64 * T + 4 * T) + 16 * (texels + WH),
+        "sm_interp": texels * (16 + 8),
+        "sm_antialias": texels * (16 + 8 + 8),
+        "filter": texels * 2 * (8 + 8),
+        "shade": WH * (16 + 16) + 8 * texels + 24 * V,
+        "final_antialias": WH * (16 + 16 + 16),
+        "bwd_clear": 8 * texels + views * 16 * V + 4 * L * V + 24 * V,
+        "bwd_final_antialias": WH * (16 + 16 + 16 + 16),
+        "bwd_shade": WH * (16 + 16) + 16 * texels + 40 * V,
+        "bwd_filter": texels * 2 * (8 + 8),
+        "bwd_sm": texels * (16 + 8 + 8) + 20 * V * L,
+        "bwd_vertex": views * 16 * V + 4 * L * V + 12 * V + 24 * V + 12 * T,
+    }
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        idx = self._smi_index(device_index)
+        if idx is None:
+            return
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(idx), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    @staticmethod
+    def _smi_index(dev):
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(dev).uuid)
+            out = subprocess.run(["nvidia-smi", "--query-gpu=index,uuid", "--format=csv,noheader"],
+                                 capture_output=True, text=True, timeout=20).stdout
+            for line in out.strip().splitlines():
+                i, u = [x.strip() for x in line.split(",")]
+                if uuid.replace("GPU-", "") in u:
+                    return int(i)
+            return dev
+        except Exception:
+            return None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def aggregate(seconds: float, frames: int, world: int, device=None):
+    """Max of the timed seconds over ranks and the sum of frames (whole job)."""
+    if world == 1:
+        return seconds, frames
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    n = torch.tensor([float(frames)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- oracle timing (CPU baseline)
+def oracle_sample(sc: dict, scale: int, keep_instances: int, seed: int = 0) -> tuple[float, str, int]:
+    """Time the CPU oracle (fwd + bwd) on a bounded sample of the workload and
+    scale it to one full frame.  Sample: the first `keep_instances` objects of
+    the scene plus the ground, shadow maps and camera reduced by `scale` per
+    axis.  Per-triangle raster time scales with the triangle count, the rest
+    with the pixel count.  Returns (estimated seconds per full frame,
+    description, threads)."""
+    import torch
+    from oracle import dsm_oracle as O
+    import scenes  # noqa: F401
+    tri_mat = sc["tri_mat"]
+    keep = np.isin(tri_mat, list(range(0, keep_instances + 1)))
+    tris_full = sc["tris"]
+    tris = tris_full[keep]
+    used = np.unique(tris)
+    remap = -np.ones(sc["verts"].shape[0], np.int64)
+    remap[used] = np.arange(len(used))
+    sub = dict(sc)
+    sub["verts"] = sc["verts"][used]
+    sub["tris"] = remap[tris].astype(np.int32)
+    sub["tri_mat"] = tri_mat[keep]
+    sub["lights"] = [dict(l, res=max(8, l["res"] // scale)) for l in sc["lights"]]
+    cam = dict(sc["camera"])
+    cam["width"], cam["height"] = max(8, cam["width"] // scale), max(8, cam["height"] // scale)
+    sub["camera"] = cam
+    raster_time = [0.0]
+    orig = O.raster
+
+    def timed_raster(*a, **k):
+        t0 = time.perf_counter()
+        r = orig(*a, **k)
+        raster_time[0] += time.perf_counter() - t0
+        return r
+
+    O.raster = timed_raster
+    try:
+        target = np.zeros((cam["height"], cam["width"], 4))
+        t0 = time.perf_counter()
+        O.render_and_grad(sub, target)
+        total = time.perf_counter() - t0
+    finally:
+        O.raster = orig
+    t_tri = raster_time[0]
+    t_pix = max(total - t_tri, 0.0)
+    tri_factor = tris_full.shape[0] / max(1, tris.shape[0])
+    pix_factor = float(scale * scale)
+    est = t_tri * tri_factor + t_pix * pix_factor
+    desc = (f"oracle fwd+bwd on {tris.shape[0]} of {tris_full.shape[0]} triangles (first {keep_instances} objects + "
+            f"ground) at 1/{scale} resolution per axis ({total:.1f} s: raster {t_tri:.1f} s scaled x{tri_factor:.1f}, "
+            f"per-pixel {t_pix:.1f} s scaled x{pix_factor:.0f})")
+    return est, desc, torch.get_num_threads()
+
+
+def choose_sample(budget_s: float):
+    """Sample size for the oracle so that one sample takes about budget_s."""
+    if budget_s >= 20:
+        return 4, 8
+    if budget_s >= 8:
+        return 8, 4
+    return 16, 2
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2308_10896_b300 import dsm
+    sc, desc = make_workload(args.workload, rank)
+    import scenes
+    r = dsm.Renderer(sc, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream(dev)
+    # target: the same scene with vertices jittered (rendered once, before timing)
+    verts_t = torch.as_tensor(scenes.jitter_vertices(sc, 0.01, 99 + rank), device=dev).contiguous()
+    target = r.forward(verts=verts_t).clone()
+    loss = torch.zeros(1, device=dev)
+    gimg = torch.empty_like(target)
+    image = torch.empty_like(target)
+    V, L, M = r.verts.shape[0], len(r.lights), r.albedo.shape[0]
+    dverts = torch.empty((V, 3), device=dev)
+    dlight = torch.empty((max(L, 1), 6), device=dev)
+    dalbedo = torch.empty((M, 3), device=dev)
+
+    def step():
+        r.forward(image=image)
+        dsm.l2_loss_grad(image, target, loss, gimg)
+        r.backward(gimg, dverts, dlight, dalbedo)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    r.ctx.sync()
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region (device time, CUDA events on the render stream)
+    r.ctx.profile(True)
+    r.ctx.profile_read()
+    sampler = ClockSampler(local) if not args.no_clocks else None
+    time.sleep(0.3 if sampler else 0.0)
+    launches0 = dsm.kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    launches = dsm.kernel_launches() - launches0
+    clocks = sampler.stop() if sampler else None
+    prof = r.ctx.profile_read()
+    r.ctx.profile(False)
+    r.ctx.sync()
+    sec = e0.elapsed_time(e1) / 1e3
+    sec_max, frames = aggregate(sec, args.steps, world, dev)
+    value = frames / sec_max
+
+    # ---- end to end through the public API with host buffers (H2D inputs, D2H results)
+    pin = dict(pin_memory=True)
+    h_verts = torch.as_tensor(sc["verts"]).pin_memory()
+    h_lp = r.light_params.cpu().pin_memory()
+    h_alb = r.albedo.cpu().pin_memory()
+    h_loss = torch.empty(1, **pin)
+    h_dv = torch.empty((V, 3), **pin)
+    h_dl = torch.empty((max(L, 1), 6), **pin)
+    h_da = torch.empty((M, 3), **pin)
+    d_verts = torch.empty_like(r.verts)
+    d_lp = torch.empty_like(r.light_params)
+    d_alb = torch.empty_like(r.albedo)
+    h2d = h_verts.numel() * 4 + h_lp.numel() * 4 + h_alb.numel() * 4
+    d2h = 4 + h_dv.numel() * 4 + h_dl.numel() * 4 + h_da.numel() * 4
+
+    def e2e_step():
+        d_verts.copy_(h_verts, non_blocking=True)
+        d_lp.copy_(h_lp, non_blocking=True)
+        d_alb.copy_(h_alb, non_blocking=True)
+        r.forward(verts=d_verts, light_params=d_lp, albedo=d_alb, image=image)
+        dsm.l2_loss_grad(image, target, loss, gimg)
+        r.backward(gimg, dverts, dlight, dalbedo)
+        h_loss.copy_(loss, non_blocking=True)
+        h_dv.copy_(dverts, non_blocking=True)
+        h_dl.copy_(dlight, non_blocking=True)
+        h_da.copy_(dalbedo, non_blocking=True)
+        stream.synchronize()          # the host reads the step's result before the next step
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    k_e2e = max(3, args.steps)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for _ in range(k_e2e):
+        e2e_step()
+    q1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    e2e_sec, e2e_frames = aggregate(q0.elapsed_time(q1) / 1e3, k_e2e, world, dev)
+
+    # ---- roofline of the dominant stage (live event timing above)
+    peak, peak_kind = load_peaks()
+    sb = stage_bytes(sc)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_calls = prof[dom]
+    avg_s = dom_ms / 1e3 / max(dom_calls, 1)
+    achieved = sb[dom] / avg_s / 1e9
+    stages = {k: {"ms_per_step": round(v[0] / max(args.steps, 1), 4),
+                  "share": round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4),
+                  "algorithmic_GBps": round(sb[k] / (v[0] / 1e3 / max(v[1], 1)) / 1e9, 1) if v[1] else None}
+              for k, v in prof.items()}
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get(args.workload, {}).get(dom)
+        except Exception:
+            traffic = None
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(sec_max * 1e3 / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator)",
+        "config": workload_config(args.workload, sc, desc),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                     "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "algorithmic_bytes_per_launch": int(sb[dom]),
+                     "avg_launch_ms": round(avg_s * 1e3, 4)},
+        "stages": stages,
+        "frame_algorithmic_GBps": round(sum(sb.values()) * value / world / 1e9, 1),
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": {"value": round(e2e_frames / e2e_sec, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        scale, keep = choose_sample(args.cpu_budget)
+        est, sdesc, threads = oracle_sample(sc, scale, keep)
+        out["cpu_baseline"] = {"value": round(1.0 / est, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": sdesc}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    sc, desc = make_workload(args.workload, 0)
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    scale, keep = choose_sample(budget)
+    for _ in range(args.warmup):
+        oracle_sample(sc, scale, keep)
+    ests, sdesc = [], ""
+    for _ in range(args.steps):
+        est, sdesc, threads = oracle_sample(sc, scale, keep)
+        ests.append(est)
+    sec = float(np.mean(ests)) if ests else float("nan")
+    value = 1.0 / sec if ests else float("nan")
+    out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+           "config": workload_config(args.workload, sc, desc), "impl": "reference",
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": torch.get_num_threads(),
+                            "kind": "oracle", "sample": sdesc},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="config3", choices=["config1", "config2", "config3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for the CPU baseline")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

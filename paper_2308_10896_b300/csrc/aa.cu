@@ -230,34 +230,70 @@ __global__ void sm_interp_kernel(const float4* __restrict__ gbuf, int R, const i
 
 // Adjoint of antialiasing + interpolation on the shadow map: dL/d(f, f^2) per
 // texel, then dL/df = g.x + 2 f g.y onto the vertex depths and (through the
-// barycentrics) onto the light-space clip coordinates.
-__global__ void sm_backward_kernel(AAArgs a, const float2* __restrict__ fmap, const float2* __restrict__ gft,
-                                   const float* __restrict__ depth, float4* __restrict__ gclip,
-                                   float* __restrict__ gdepth, int aa) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= a.W || j >= a.H) return;
-  const size_t p = (size_t)j * a.W + i;
-  const float2 gc = aa ? aa_adjoint_pixel<float2>(a, i, j, fmap, gft, gclip) : gft[p];
-  const float4 g = a.gbuf[p];
-  const int id = gid(g);
-  if (!id) return;
-  const float f = fmap[p].x;
-  const float gf = gc.x + 2.f * f * gc.y;
-  if (gf == 0.f) return;
-  const int t = id - 1;
-  const int v[3] = {a.tris[3 * t], a.tris[3 * t + 1], a.tris[3 * t + 2]};
-  const float4 c0 = a.clip[v[0]], c1 = a.clip[v[1]], c2 = a.clip[v[2]];
-  const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
-  const Bary r = bary_at(c0, c1, c2, px, py);
-  const float b[3] = {g.y, g.z, 1.f - g.y - g.z};
-  float gb[3];
-  for (int k = 0; k < 3; ++k) {
-    atomicAdd(&gdepth[v[k]], b[k] * gf);
-    gb[k] = depth[v[k]] * gf;
+// barycentrics) onto the light-space clip coordinates.  Each warp walks a strip
+// of kStrip rows over 32 columns; per-triangle sums go through a run
+// accumulator, so the many texels of a large triangle cost one set of atomics
+// per strip instead of one per texel.
+constexpr int kStrip = 16;
+
+struct SmScatter {
+  const int* tris;
+  float4* gclip;
+  float* gdepth;
+  __device__ __forceinline__ void operator()(int t, const float (&c)[15]) const {
+    for (int k = 0; k < 3; ++k) {
+      const int v = tris[3 * t + k];
+      atomicAdd(&gdepth[v], c[k]);
+      atomic_add4(&gclip[v], make_float4(c[3 + 4 * k], c[4 + 4 * k], c[5 + 4 * k], c[6 + 4 * k]));
+    }
   }
-  float4 gcv[3];
-  bary_backward(r, gb, px, py, gcv);
-  for (int k = 0; k < 3; ++k) atomic_add4(&gclip[v[k]], gcv[k]);
+};
+
+__global__ void __launch_bounds__(256) sm_backward_kernel(AAArgs a, const float2* __restrict__ fmap,
+                                                          const float2* __restrict__ gft,
+                                                          const float* __restrict__ depth, float4* __restrict__ gclip,
+                                                          float* __restrict__ gdepth, int aa) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kStrip;
+  SmScatter sc{a.tris, gclip, gdepth};
+  RunAcc<15> run;
+  run_reset(run);
+  for (int s = 0; s < kStrip; ++s) {
+    const int j = j0 + s;
+    float c[15];
+    int t = -1;
+    if (i < a.W && j < a.H) {
+      const size_t p = (size_t)j * a.W + i;
+      const float2 gc = aa ? aa_adjoint_pixel<float2>(a, i, j, fmap, gft, gclip) : gft[p];
+      const float4 g = a.gbuf[p];
+      const int id = gid(g);
+      const float f = fmap[p].x;
+      const float gf = gc.x + 2.f * f * gc.y;
+      if (id && gf != 0.f) {
+        t = id - 1;
+        const int v[3] = {a.tris[3 * t], a.tris[3 * t + 1], a.tris[3 * t + 2]};
+        const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
+        const Bary r = bary_at(a.clip[v[0]], a.clip[v[1]], a.clip[v[2]], px, py);
+        const float b[3] = {g.y, g.z, 1.f - g.y - g.z};
+        float gb[3];
+        for (int k = 0; k < 3; ++k) {
+          c[k] = b[k] * gf;
+          gb[k] = depth[v[k]] * gf;
+        }
+        float4 gcv[3];
+        bary_backward(r, gb, px, py, gcv);
+        for (int k = 0; k < 3; ++k) {
+          c[3 + 4 * k] = gcv[k].x; c[4 + 4 * k] = gcv[k].y; c[5 + 4 * k] = gcv[k].z; c[6 + 4 * k] = gcv[k].w;
+        }
+      }
+    }
+    if (t < 0) {
+#pragma unroll
+      for (int k = 0; k < 15; ++k) c[k] = 0.f;
+    }
+    run_add(run, t, c, sc);
+  }
+  run_flush(run, sc);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -281,9 +317,9 @@ void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, cudaS
 }
 void launch_sm_backward(const AAArgs& a, const float2* fmap, const float2* gft, const float* depth, float4* gclip,
                         float* gdepth, int aa, cudaStream_t st) {
-  dim3 b(32, 8);
+  dim3 b(32, 8), g((a.W + 31) / 32, (a.H + 8 * kStrip - 1) / (8 * kStrip));
   count_launches(1);
-  sm_backward_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, fmap, gft, depth, gclip, gdepth, aa);
+  sm_backward_kernel<<<g, b, 0, st>>>(a, fmap, gft, depth, gclip, gdepth, aa);
 }
 void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
                          int aa, cudaStream_t st) {

@@ -213,11 +213,42 @@ __device__ __forceinline__ void warp_add_shared(float* dst, float v) {
 }
 
 constexpr int kMaxSharedMat = 256;
+constexpr int kShadeStrip = 8;
 
-// Adjoint of shade_kernel (and of the camera interpolation): every covered pixel
-// scatters onto the albedo table, the texel maps dL/d(m1, m2), the light
-// matrices Q, the direct light terms (omega), the vertices (x), the vertex
-// normals and the camera clip coordinates (barycentrics).
+// Per-triangle scatter of the shading adjoint: 9 dL/dv (b_k dL/dx), 9 dL/d unit
+// vertex normal, 12 dL/d camera clip, 3 dL/d albedo.
+struct ShadeScatter {
+  const int* tris;
+  const ShadeArgs* a;
+  float* dverts;
+  float* gnormal;
+  float4* gclip;
+  float* sA;            // shared albedo accumulator, or nullptr
+  float* dalbedo;
+  __device__ __forceinline__ void operator()(int t, const float (&c)[33]) const {
+    for (int k = 0; k < 3; ++k) {
+      const int v = tris[3 * t + k];
+      atomicAdd(&dverts[3 * v], c[3 * k]);
+      atomicAdd(&dverts[3 * v + 1], c[3 * k + 1]);
+      atomicAdd(&dverts[3 * v + 2], c[3 * k + 2]);
+      atomicAdd(&gnormal[3 * v], c[9 + 3 * k]);
+      atomicAdd(&gnormal[3 * v + 1], c[10 + 3 * k]);
+      atomicAdd(&gnormal[3 * v + 2], c[11 + 3 * k]);
+      atomic_add4(&gclip[v], make_float4(c[18 + 4 * k], c[19 + 4 * k], c[20 + 4 * k], c[21 + 4 * k]));
+    }
+    const int mat = material_of(*a, t);
+    float* dst = sA ? sA : dalbedo;
+    atomicAdd(&dst[3 * mat], c[30]);
+    atomicAdd(&dst[3 * mat + 1], c[31]);
+    atomicAdd(&dst[3 * mat + 2], c[32]);
+  }
+};
+
+// Adjoint of shade_kernel (and of the camera interpolation).  Per pixel: the
+// texel maps dL/d(m1, m2) (bilinear adjoint), the light matrices Q and the
+// direct light terms (block-reduced), and a per-triangle contribution (vertex
+// positions, vertex normals, camera clip coordinates, albedo) that goes
+// through a warp run accumulator.  Each warp walks kShadeStrip rows.
 __global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g) {
   __shared__ float sQ[DSM_MAX_LIGHTS * 20];
   __shared__ float sD[DSM_MAX_LIGHTS * 3];
@@ -228,135 +259,138 @@ __global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeG
   for (int k = tid; k < DSM_MAX_LIGHTS * 3; k += 256) sD[k] = 0.f;
   for (int k = tid; k < kMaxSharedMat * 3; k += 256) sA[k] = 0.f;
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  const bool inb = i < a.W && j < a.H;
-  const size_t p = inb ? (size_t)j * a.W + i : 0;
-  Surf s;
-  const bool cov = inb && load_surf(a, p, s);
-  float4 gc4 = cov ? g.gcolor[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const bool act = cov && (gc4.x != 0.f || gc4.y != 0.f || gc4.z != 0.f);
-  float3 gx = make_float3(0.f, 0.f, 0.f), gn = make_float3(0.f, 0.f, 0.f);
-  int mat = 0;
-  float3 alb = make_float3(0.f, 0.f, 0.f), rad = make_float3(0.f, 0.f, 0.f);
-  if (act) {
-    mat = material_of(a, s.tri);
-    alb = make_float3(a.albedo[3 * mat], a.albedo[3 * mat + 1], a.albedo[3 * mat + 2]);
-  }
-  const float3 grad_rad = make_float3(gc4.x * alb.x, gc4.y * alb.y, gc4.z * alb.z);
-  for (int l = 0; l < a.L; ++l) {
-    float gq[20];
-#pragma unroll
-    for (int k = 0; k < 20; ++k) gq[k] = 0.f;
-    float3 gdir = make_float3(0.f, 0.f, 0.f);
+  ShadeScatter sc{a.tris, &a, g.dverts, g.gnormal, g.gclip, mat_shared ? sA : nullptr, g.dalbedo};
+  RunAcc<33> run;
+  run_reset(run);
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kShadeStrip;
+  for (int srow = 0; srow < kShadeStrip; ++srow) {
+    const int j = j0 + srow;
+    const bool inb = i < a.W && j < a.H;
+    const size_t p = inb ? (size_t)j * a.W + i : 0;
+    Surf s;
+    const bool cov = inb && load_surf(a, p, s);
+    const float4 gc4 = cov ? g.gcolor[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool act = cov && (gc4.x != 0.f || gc4.y != 0.f || gc4.z != 0.f);
+    float3 gx = make_float3(0.f, 0.f, 0.f), gn = make_float3(0.f, 0.f, 0.f);
+    float3 alb = make_float3(0.f, 0.f, 0.f), rad = make_float3(0.f, 0.f, 0.f);
     if (act) {
-      const LightDev& Ld = a.lights[l];
-      const int R = a.res[l];
-      const Look L = lookup(Ld.Q, a.mom[l], R, s.x, a.min_variance);
-      float len;
-      const float3 om = light_omega(Ld, s.x, len);
-      const float ndo = s.n.x * om.x + s.n.y * om.y + s.n.z * om.z;
-      const float lam = fmaxf(ndo, 0.f);
-      rad.x += L.vis * lam * Ld.intensity[0]; rad.y += L.vis * lam * Ld.intensity[1]; rad.z += L.vis * lam * Ld.intensity[2];
-      const float sl = grad_rad.x * Ld.intensity[0] + grad_rad.y * Ld.intensity[1] + grad_rad.z * Ld.intensity[2];
-      const float gvis = sl * lam, glam = sl * L.vis;
-      if (ndo > 0.f && glam != 0.f) {
-        gn.x += glam * om.x; gn.y += glam * om.y; gn.z += glam * om.z;
-        const float3 gom = make_float3(glam * s.n.x, glam * s.n.y, glam * s.n.z);
-        if (Ld.type == 0) {
-          gdir = gom;                    // dL/d omega, omega = -fwd (chained on the host side kernel)
-        } else {
-          const float d = om.x * gom.x + om.y * gom.y + om.z * gom.z;
-          const float il = 1.f / len;
-          const float3 gp = make_float3((gom.x - om.x * d) * il, (gom.y - om.y * d) * il, (gom.z - om.z * d) * il);
-          gdir = gp;                     // dL/d pos (direct)
-          gx.x -= gp.x; gx.y -= gp.y; gx.z -= gp.z;
+      const int mat = material_of(a, s.tri);
+      alb = make_float3(a.albedo[3 * mat], a.albedo[3 * mat + 1], a.albedo[3 * mat + 2]);
+    }
+    const float3 grad_rad = make_float3(gc4.x * alb.x, gc4.y * alb.y, gc4.z * alb.z);
+    for (int l = 0; l < a.L; ++l) {
+      float gq[20];
+#pragma unroll
+      for (int k = 0; k < 20; ++k) gq[k] = 0.f;
+      float3 gdir = make_float3(0.f, 0.f, 0.f);
+      if (act) {
+        const LightDev& Ld = a.lights[l];
+        const int R = a.res[l];
+        const Look L = lookup(Ld.Q, a.mom[l], R, s.x, a.min_variance);
+        float len;
+        const float3 om = light_omega(Ld, s.x, len);
+        const float ndo = s.n.x * om.x + s.n.y * om.y + s.n.z * om.z;
+        const float lam = fmaxf(ndo, 0.f);
+        rad.x += L.vis * lam * Ld.intensity[0]; rad.y += L.vis * lam * Ld.intensity[1]; rad.z += L.vis * lam * Ld.intensity[2];
+        const float sl = grad_rad.x * Ld.intensity[0] + grad_rad.y * Ld.intensity[1] + grad_rad.z * Ld.intensity[2];
+        const float gvis = sl * lam, glam = sl * L.vis;
+        if (ndo > 0.f && glam != 0.f) {
+          gn.x += glam * om.x; gn.y += glam * om.y; gn.z += glam * om.z;
+          const float3 gom = make_float3(glam * s.n.x, glam * s.n.y, glam * s.n.z);
+          if (Ld.type == 0) {
+            gdir = gom;                    // dL/d omega with omega = -fwd (chained in light_grad_kernel)
+          } else {
+            const float d = om.x * gom.x + om.y * gom.y + om.z * gom.z;
+            const float il = 1.f / len;
+            const float3 gp = make_float3((gom.x - om.x * d) * il, (gom.y - om.y * d) * il, (gom.z - om.z * d) * il);
+            gdir = gp;                     // dL/d position (direct term)
+            gx.x -= gp.x; gx.y -= gp.y; gx.z -= gp.z;
+          }
+        }
+        if (L.inside && L.delta > 0.f && gvis != 0.f) {
+          const float S = L.var + L.delta * L.delta;
+          const float iS2 = 1.f / (S * S);
+          const float dv_dvar = L.delta * L.delta * iS2;
+          const float dv_ddelta = -2.f * L.var * L.delta * iS2;
+          const float gd = gvis * dv_ddelta;
+          float gm1 = -gd, gm2 = 0.f;
+          if (!L.var_clamped) {
+            gm1 += gvis * dv_dvar * (-2.f * L.m.x);
+            gm2 = gvis * dv_dvar;
+          }
+          const int i0 = min(max(L.i0, 0), R - 1), i1 = min(max(L.i0 + 1, 0), R - 1);
+          const int j0c = min(max(L.j0, 0), R - 1), j1c = min(max(L.j0 + 1, 0), R - 1);
+          const float w00 = (1.f - L.fs) * (1.f - L.ft), w01 = L.fs * (1.f - L.ft), w10 = (1.f - L.fs) * L.ft,
+                      w11 = L.fs * L.ft;
+          float2* gm = g.gm[l];
+          atomic_add2(&gm[(size_t)j0c * R + i0], make_float2(w00 * gm1, w00 * gm2));
+          atomic_add2(&gm[(size_t)j0c * R + i1], make_float2(w01 * gm1, w01 * gm2));
+          atomic_add2(&gm[(size_t)j1c * R + i0], make_float2(w10 * gm1, w10 * gm2));
+          atomic_add2(&gm[(size_t)j1c * R + i1], make_float2(w11 * gm1, w11 * gm2));
+          const float2* mom = a.mom[l];
+          const float2 m00 = mom[(size_t)j0c * R + i0], m01 = mom[(size_t)j0c * R + i1];
+          const float2 m10 = mom[(size_t)j1c * R + i0], m11 = mom[(size_t)j1c * R + i1];
+          const float d00 = m00.x * gm1 + m00.y * gm2, d01 = m01.x * gm1 + m01.y * gm2;
+          const float d10 = m10.x * gm1 + m10.y * gm2, d11 = m11.x * gm1 + m11.y * gm2;
+          const float gfs = (1.f - L.ft) * (d01 - d00) + L.ft * (d11 - d10);
+          const float gft = (1.f - L.fs) * (d10 - d00) + L.fs * (d11 - d01);
+          // s = (0.5 u + 0.5) R - 0.5,  t = (0.5 - 0.5 v) R - 0.5,  u = cx / cw,  v = cy / cw
+          const float gu = gfs * 0.5f * R, gv = -gft * 0.5f * R;
+          const float iw = 1.f / L.clip.w;
+          const float u = L.clip.x * iw, v = L.clip.y * iw;
+          const float gcl[4] = {gu * iw, gv * iw, 0.f, -(gu * u + gv * v) * iw};
+          const float xh[4] = {s.x.x, s.x.y, s.x.z, 1.f};
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) gq[r * 4 + c] = gcl[r] * xh[c];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) gq[16 + c] = gd * xh[c];
+          const float* Q = Ld.Q;
+          gx.x += Q[0] * gcl[0] + Q[4] * gcl[1] + Q[12] * gcl[3] + Q[16] * gd;
+          gx.y += Q[1] * gcl[0] + Q[5] * gcl[1] + Q[13] * gcl[3] + Q[17] * gd;
+          gx.z += Q[2] * gcl[0] + Q[6] * gcl[1] + Q[14] * gcl[3] + Q[18] * gd;
         }
       }
-      if (L.inside && L.delta > 0.f && gvis != 0.f) {
-        const float S = L.var + L.delta * L.delta;
-        const float iS2 = 1.f / (S * S);
-        const float dv_dvar = L.delta * L.delta * iS2;
-        const float dv_ddelta = -2.f * L.var * L.delta * iS2;
-        const float gd = gvis * dv_ddelta;
-        float gm1 = -gd, gm2 = 0.f;
-        if (!L.var_clamped) {
-          gm1 += gvis * dv_dvar * (-2.f * L.m.x);
-          gm2 = gvis * dv_dvar;
-        }
-        // bilinear adjoint: texel gradients and dL/d(s, t)
-        const int i0 = min(max(L.i0, 0), R - 1), i1 = min(max(L.i0 + 1, 0), R - 1);
-        const int j0 = min(max(L.j0, 0), R - 1), j1 = min(max(L.j0 + 1, 0), R - 1);
-        const float w00 = (1.f - L.fs) * (1.f - L.ft), w01 = L.fs * (1.f - L.ft), w10 = (1.f - L.fs) * L.ft,
-                    w11 = L.fs * L.ft;
-        float2* gm = g.gm[l];
-        atomic_add2(&gm[(size_t)j0 * R + i0], make_float2(w00 * gm1, w00 * gm2));
-        atomic_add2(&gm[(size_t)j0 * R + i1], make_float2(w01 * gm1, w01 * gm2));
-        atomic_add2(&gm[(size_t)j1 * R + i0], make_float2(w10 * gm1, w10 * gm2));
-        atomic_add2(&gm[(size_t)j1 * R + i1], make_float2(w11 * gm1, w11 * gm2));
-        const float2* mom = a.mom[l];
-        const float2 m00 = mom[(size_t)j0 * R + i0], m01 = mom[(size_t)j0 * R + i1];
-        const float2 m10 = mom[(size_t)j1 * R + i0], m11 = mom[(size_t)j1 * R + i1];
-        const float d00 = m00.x * gm1 + m00.y * gm2, d01 = m01.x * gm1 + m01.y * gm2;
-        const float d10 = m10.x * gm1 + m10.y * gm2, d11 = m11.x * gm1 + m11.y * gm2;
-        const float gfs = (1.f - L.ft) * (d01 - d00) + L.ft * (d11 - d10);
-        const float gft = (1.f - L.fs) * (d10 - d00) + L.fs * (d11 - d01);
-        // s = (0.5 u + 0.5) R - 0.5,  t = (0.5 - 0.5 v) R - 0.5,  u = cx / cw,  v = cy / cw
-        const float gu = gfs * 0.5f * R, gv = -gft * 0.5f * R;
-        const float iw = 1.f / L.clip.w;
-        const float u = L.clip.x * iw, v = L.clip.y * iw;
-        const float gcl[4] = {gu * iw, gv * iw, 0.f, -(gu * u + gv * v) * iw};
-        const float xh[4] = {s.x.x, s.x.y, s.x.z, 1.f};
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+      for (int k = 0; k < 20; ++k) warp_add_shared(&sQ[l * 20 + k], gq[k]);
+      warp_add_shared(&sD[l * 3 + 0], gdir.x);
+      warp_add_shared(&sD[l * 3 + 1], gdir.y);
+      warp_add_shared(&sD[l * 3 + 2], gdir.z);
+    }
+    float c[33];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) gq[r * 4 + c] = gcl[r] * xh[c];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) gq[16 + c] = gd * xh[c];
-        const float* Q = Ld.Q;
-        gx.x += Q[0] * gcl[0] + Q[4] * gcl[1] + Q[12] * gcl[3] + Q[16] * gd;
-        gx.y += Q[1] * gcl[0] + Q[5] * gcl[1] + Q[13] * gcl[3] + Q[17] * gd;
-        gx.z += Q[2] * gcl[0] + Q[6] * gcl[1] + Q[14] * gcl[3] + Q[18] * gd;
+    for (int k = 0; k < 33; ++k) c[k] = 0.f;
+    int t = -1;
+    if (act) {
+      t = s.tri;
+      c[30] = gc4.x * rad.x; c[31] = gc4.y * rad.y; c[32] = gc4.z * rad.z;
+      float3 gnt = make_float3(0.f, 0.f, 0.f);
+      if (s.nlen > 0.f) {
+        const float d = s.n.x * gn.x + s.n.y * gn.y + s.n.z * gn.z;
+        const float il = 1.f / s.nlen;
+        gnt = make_float3((gn.x - s.n.x * d) * il, (gn.y - s.n.y * d) * il, (gn.z - s.n.z * d) * il);
+      }
+      float gb[3];
+      for (int k = 0; k < 3; ++k) {
+        const int v = s.v[k];
+        c[3 * k] = s.b[k] * gx.x; c[3 * k + 1] = s.b[k] * gx.y; c[3 * k + 2] = s.b[k] * gx.z;
+        c[9 + 3 * k] = s.b[k] * gnt.x; c[10 + 3 * k] = s.b[k] * gnt.y; c[11 + 3 * k] = s.b[k] * gnt.z;
+        gb[k] = a.verts[3 * v] * gx.x + a.verts[3 * v + 1] * gx.y + a.verts[3 * v + 2] * gx.z +
+                a.vnormal[3 * v] * gnt.x + a.vnormal[3 * v + 1] * gnt.y + a.vnormal[3 * v + 2] * gnt.z;
+      }
+      const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
+      const Bary r = bary_at(a.cam_clip[s.v[0]], a.cam_clip[s.v[1]], a.cam_clip[s.v[2]], px, py);
+      float4 gcv[3];
+      bary_backward(r, gb, px, py, gcv);
+      for (int k = 0; k < 3; ++k) {
+        c[18 + 4 * k] = gcv[k].x; c[19 + 4 * k] = gcv[k].y; c[20 + 4 * k] = gcv[k].z; c[21 + 4 * k] = gcv[k].w;
       }
     }
-#pragma unroll
-    for (int k = 0; k < 20; ++k) warp_add_shared(&sQ[l * 20 + k], gq[k]);
-    warp_add_shared(&sD[l * 3 + 0], gdir.x);
-    warp_add_shared(&sD[l * 3 + 1], gdir.y);
-    warp_add_shared(&sD[l * 3 + 2], gdir.z);
+    run_add(run, t, c, sc);
   }
-  if (act) {
-    const float3 ga = make_float3(gc4.x * rad.x, gc4.y * rad.y, gc4.z * rad.z);
-    if (mat_shared) {
-      atomicAdd(&sA[3 * mat], ga.x); atomicAdd(&sA[3 * mat + 1], ga.y); atomicAdd(&sA[3 * mat + 2], ga.z);
-    } else {
-      atomicAdd(&g.dalbedo[3 * mat], ga.x); atomicAdd(&g.dalbedo[3 * mat + 1], ga.y);
-      atomicAdd(&g.dalbedo[3 * mat + 2], ga.z);
-    }
-    // unit normal n = nt / |nt|
-    float3 gnt = make_float3(0.f, 0.f, 0.f);
-    if (s.nlen > 0.f) {
-      const float d = s.n.x * gn.x + s.n.y * gn.y + s.n.z * gn.z;
-      const float il = 1.f / s.nlen;
-      gnt = make_float3((gn.x - s.n.x * d) * il, (gn.y - s.n.y * d) * il, (gn.z - s.n.z * d) * il);
-    }
-    float gb[3];
-    for (int k = 0; k < 3; ++k) {
-      const int v = s.v[k];
-      atomicAdd(&g.dverts[3 * v], s.b[k] * gx.x);
-      atomicAdd(&g.dverts[3 * v + 1], s.b[k] * gx.y);
-      atomicAdd(&g.dverts[3 * v + 2], s.b[k] * gx.z);
-      atomicAdd(&g.gnormal[3 * v], s.b[k] * gnt.x);
-      atomicAdd(&g.gnormal[3 * v + 1], s.b[k] * gnt.y);
-      atomicAdd(&g.gnormal[3 * v + 2], s.b[k] * gnt.z);
-      gb[k] = a.verts[3 * v] * gx.x + a.verts[3 * v + 1] * gx.y + a.verts[3 * v + 2] * gx.z +
-              a.vnormal[3 * v] * gnt.x + a.vnormal[3 * v + 1] * gnt.y + a.vnormal[3 * v + 2] * gnt.z;
-    }
-    const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
-    const Bary r = bary_at(a.cam_clip[s.v[0]], a.cam_clip[s.v[1]], a.cam_clip[s.v[2]], px, py);
-    float4 gcv[3];
-    bary_backward(r, gb, px, py, gcv);
-    for (int k = 0; k < 3; ++k) atomic_add4(&g.gclip[s.v[k]], gcv[k]);
-  }
+  run_flush(run, sc);
   __syncthreads();
   for (int k = tid; k < a.L * 20; k += 256)
     if (sQ[k] != 0.f) atomicAdd(&g.gQ[k], sQ[k]);
@@ -366,7 +400,6 @@ __global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeG
     for (int k = tid; k < a.n_mat * 3; k += 256)
       if (sA[k] != 0.f) atomicAdd(&g.dalbedo[k], sA[k]);
 }
-
 
 // ------------------------------------------------------------------ per-vertex gathers
 // dL/dv += M^T dL/dclip for every view (+ depth row for lights);
@@ -479,9 +512,9 @@ void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st) {
 }
 
 void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st) {
-  dim3 b(32, 8);
+  dim3 b(32, 8), grid((a.W + 31) / 32, (a.H + 8 * kShadeStrip - 1) / (8 * kShadeStrip));
   count_launches(1);
-  shade_backward_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, g);
+  shade_backward_kernel<<<grid, b, 0, st>>>(a, g);
 }
 
 void launch_vertex_backward(const float* verts, int V, const float* viewM, int n_views, int n_lights,
