@@ -31,32 +31,37 @@ def _nvcc():
     return "nvcc"
 
 
-def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+def _sources(src_dir=CSRC):
+    return sorted(glob.glob(os.path.join(src_dir, "*.cu")) + glob.glob(os.path.join(src_dir, "*.cpp")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(OUT):
+def _stale(src_dir=CSRC, out=OUT) -> bool:
+    if not os.path.exists(out):
         return True
-    t = os.path.getmtime(OUT)
-    deps = _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) \
+    t = os.path.getmtime(out)
+    deps = _sources(src_dir) + glob.glob(os.path.join(src_dir, "*.h")) + glob.glob(os.path.join(src_dir, "*.cuh")) \
         + glob.glob(os.path.join(ROOT, "include", "*.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
-    """Compile csrc/*.cu, csrc/*.cpp into libdsm.so (skipped when up to date)."""
-    if not force and not _stale():
-        return OUT
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list | None = None, src_dir: str = CSRC,
+          out: str = OUT) -> str:
+    """Compile src_dir/*.cu, *.cpp into the shared library `out` (skipped when up to date)."""
+    OUTP = out
+    if not force and not _stale(src_dir, OUTP):
+        return OUTP
+    objdir = BUILD if src_dir == CSRC else os.path.join(os.path.dirname(OUTP), "_build")
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
     extra = list(extra or [])
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", src_dir]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *COMMON, *extra, "-c", src, "-o", obj]
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        flags = [f for f in COMMON if f not in ("-I", CSRC, os.path.join(ROOT, "include"))] + inc
+        cmd = [nvcc, *ARCH, *flags, *extra, "-c", src, "-o", obj]
         if src.endswith(".cpp"):
-            cmd = [nvcc, *COMMON, "-x", "c++", "-c", src, "-o", obj]
+            cmd = [nvcc, *flags, "-x", "c++", "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -65,13 +70,13 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
         return obj
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(compile_one, _sources()))
-    tmp = OUT + ".tmp"
+        objs = list(ex.map(compile_one, _sources(src_dir)))
+    tmp = OUTP + ".tmp"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, OUTP)
+    return OUTP
 
 
 if __name__ == "__main__":

@@ -228,19 +228,40 @@ __global__ void sm_interp_kernel(const float4* __restrict__ gbuf, int R, const i
   fmap[p] = make_float2(f, f * f);
 }
 
-// Adjoint of antialiasing + interpolation on the shadow map: dL/d(f, f^2) per
-// texel, then dL/df = g.x + 2 f g.y onto the vertex depths and (through the
-// barycentrics) onto the light-space clip coordinates.  Each warp walks a strip
-// of kStrip rows over 32 columns; per-triangle sums go through a run
-// accumulator, so the many texels of a large triangle cost one set of atomics
-// per strip instead of one per texel.
+// Adjoint of the shadow-map antialiasing: dL/d(f, f^2) per texel (the pair
+// t-gradients go to the light-space clip coordinates of the edge endpoints),
+// folded into dL/df = g.x + 2 f g.y (f^2 = f f).  One thread per texel.
+__global__ void sm_aa_adjoint_kernel(AAArgs a, const float2* __restrict__ fmap, const float2* __restrict__ gft,
+                                     float4* __restrict__ gclip, float* __restrict__ gf_out, int aa) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= a.W || j >= a.H) return;
+  const size_t p = (size_t)j * a.W + i;
+  const float2 gc = aa ? aa_adjoint_pixel<float2>(a, i, j, fmap, gft, gclip) : gft[p];
+  gf_out[p] = gc.x + 2.f * fmap[p].x * gc.y;
+}
+
+// Adjoint of the interpolation f = sum_k b_k d_k: dL/dd_k = b_k dL/df onto the
+// vertex depths and, through the perspective-correct barycentrics, onto the
+// light-space clip coordinates.  Each warp walks a strip of kStrip rows over 32
+// columns; per-triangle sums go through a run accumulator (a large triangle
+// costs one set of atomics per strip), the current triangle's vertex data stay
+// in registers, and the next row's texel data are fetched one row ahead.
 constexpr int kStrip = 16;
 
 struct SmScatter {
   const int* tris;
   float4* gclip;
   float* gdepth;
+  const int* big;        // big-triangle index per triangle (-1: scatter onto the vertices)
+  float* big_acc;        // kMaxBig x kBigSlots x 15
+  int slot;
   __device__ __forceinline__ void operator()(int t, const float (&c)[15]) const {
+    const int b = big[t];
+    if (b >= 0) {
+      float* d = big_acc + ((size_t)b * kBigSlots + slot) * 15;
+      for (int k = 0; k < 15; ++k) atomicAdd(&d[k], c[k]);
+      return;
+    }
     for (int k = 0; k < 3; ++k) {
       const int v = tris[3 * t + k];
       atomicAdd(&gdepth[v], c[k]);
@@ -249,51 +270,91 @@ struct SmScatter {
   }
 };
 
-__global__ void __launch_bounds__(256) sm_backward_kernel(AAArgs a, const float2* __restrict__ fmap,
-                                                          const float2* __restrict__ gft,
-                                                          const float* __restrict__ depth, float4* __restrict__ gclip,
-                                                          float* __restrict__ gdepth, int aa) {
+__global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const float* __restrict__ gf_map,
+                                                                const float* __restrict__ depth,
+                                                                float4* __restrict__ gclip,
+                                                                float* __restrict__ gdepth,
+                                                                const int* __restrict__ big,
+                                                                float* __restrict__ big_acc) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kStrip;
-  SmScatter sc{a.tris, gclip, gdepth};
+  const bool col_ok = i < a.W;
+  SmScatter sc{a.tris, gclip, gdepth, big, big_acc, scatter_slot(kBigSlots)};
   RunAcc<15> run;
   run_reset(run);
+  int ct = -1;                      // triangle whose vertex data are cached
+  float4 cc[3];
+  float cd[3];
+  // prefetch of row j0
+  float4 g_next = make_float4(0.f, 0.f, 0.f, 0.f);
+  float gf_next = 0.f;
+  if (col_ok && j0 < a.H) {
+    g_next = a.gbuf[(size_t)j0 * a.W + i];
+    gf_next = gf_map[(size_t)j0 * a.W + i];
+  }
   for (int s = 0; s < kStrip; ++s) {
     const int j = j0 + s;
+    const float4 g = g_next;
+    const float gf = gf_next;
+    if (col_ok && j + 1 < a.H && s + 1 < kStrip) {
+      g_next = a.gbuf[(size_t)(j + 1) * a.W + i];
+      gf_next = gf_map[(size_t)(j + 1) * a.W + i];
+    }
     float c[15];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) c[k] = 0.f;
     int t = -1;
-    if (i < a.W && j < a.H) {
-      const size_t p = (size_t)j * a.W + i;
-      const float2 gc = aa ? aa_adjoint_pixel<float2>(a, i, j, fmap, gft, gclip) : gft[p];
-      const float4 g = a.gbuf[p];
-      const int id = gid(g);
-      const float f = fmap[p].x;
-      const float gf = gc.x + 2.f * f * gc.y;
-      if (id && gf != 0.f) {
-        t = id - 1;
-        const int v[3] = {a.tris[3 * t], a.tris[3 * t + 1], a.tris[3 * t + 2]};
-        const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
-        const Bary r = bary_at(a.clip[v[0]], a.clip[v[1]], a.clip[v[2]], px, py);
-        const float b[3] = {g.y, g.z, 1.f - g.y - g.z};
-        float gb[3];
+    const int id = gid(g);
+    if (col_ok && j < a.H && id && gf != 0.f) {
+      t = id - 1;
+      if (t != ct) {
+        ct = t;
         for (int k = 0; k < 3; ++k) {
-          c[k] = b[k] * gf;
-          gb[k] = depth[v[k]] * gf;
-        }
-        float4 gcv[3];
-        bary_backward(r, gb, px, py, gcv);
-        for (int k = 0; k < 3; ++k) {
-          c[3 + 4 * k] = gcv[k].x; c[4 + 4 * k] = gcv[k].y; c[5 + 4 * k] = gcv[k].z; c[6 + 4 * k] = gcv[k].w;
+          const int v = a.tris[3 * t + k];
+          cc[k] = a.clip[v];
+          cd[k] = depth[v];
         }
       }
-    }
-    if (t < 0) {
-#pragma unroll
-      for (int k = 0; k < 15; ++k) c[k] = 0.f;
+      const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
+      const Bary r = bary_at(cc[0], cc[1], cc[2], px, py);
+      const float b[3] = {g.y, g.z, 1.f - g.y - g.z};
+      float gb[3];
+      for (int k = 0; k < 3; ++k) {
+        c[k] = b[k] * gf;
+        gb[k] = cd[k] * gf;
+      }
+      float4 gcv[3];
+      bary_backward(r, gb, px, py, gcv);
+      for (int k = 0; k < 3; ++k) {
+        c[3 + 4 * k] = gcv[k].x; c[4 + 4 * k] = gcv[k].y; c[5 + 4 * k] = gcv[k].z; c[6 + 4 * k] = gcv[k].w;
+      }
     }
     run_add(run, t, c, sc);
   }
   run_flush(run, sc);
+}
+
+// Sum the kBigSlots copies of each big triangle and scatter the result onto its
+// vertex depths and light-space clip coordinates.
+__global__ void sm_big_resolve_kernel(const int* __restrict__ tris, const int* __restrict__ big_tri,
+                                      const DevStatus* __restrict__ status, int view,
+                                      const float* __restrict__ big_acc, float4* __restrict__ gclip,
+                                      float* __restrict__ gdepth) {
+  const int b = blockIdx.x;
+  if (b >= min(status->big_count[view], kMaxBig)) return;
+  __shared__ float sum[15];
+  const int k = threadIdx.x;
+  if (k < 15) {
+    float acc = 0.f;
+    for (int q = 0; q < kBigSlots; ++q) acc += big_acc[((size_t)b * kBigSlots + q) * 15 + k];
+    sum[k] = acc;
+  }
+  __syncthreads();
+  if (k < 3) {
+    const int v = tris[3 * big_tri[b] + k];
+    atomicAdd(&gdepth[v], sum[k]);
+    atomic_add4(&gclip[v], make_float4(sum[3 + 4 * k], sum[4 + 4 * k], sum[5 + 4 * k], sum[6 + 4 * k]));
+  }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -316,10 +377,15 @@ void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, cudaS
   aa_forward_kernel<float4><<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, out);
 }
 void launch_sm_backward(const AAArgs& a, const float2* fmap, const float2* gft, const float* depth, float4* gclip,
-                        float* gdepth, int aa, cudaStream_t st) {
-  dim3 b(32, 8), g((a.W + 31) / 32, (a.H + 8 * kStrip - 1) / (8 * kStrip));
+                        float* gdepth, float* gf_scratch, const BigArgs& big, int aa, cudaStream_t st) {
+  dim3 b(32, 8);
   count_launches(1);
-  sm_backward_kernel<<<g, b, 0, st>>>(a, fmap, gft, depth, gclip, gdepth, aa);
+  sm_aa_adjoint_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, fmap, gft, gclip, gf_scratch, aa);
+  dim3 g((a.W + 31) / 32, (a.H + 8 * kStrip - 1) / (8 * kStrip));
+  count_launches(1);
+  sm_interp_adjoint_kernel<<<g, b, 0, st>>>(a, gf_scratch, depth, gclip, gdepth, big.index, big.acc);
+  count_launches(1);
+  sm_big_resolve_kernel<<<kMaxBig, 32, 0, st>>>(a.tris, big.tri, big.status, big.view, big.acc, gclip, gdepth);
 }
 void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
                          int aa, cudaStream_t st) {

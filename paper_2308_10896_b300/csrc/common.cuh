@@ -51,7 +51,27 @@ struct DevStatus {
   int capacity_overflow;
   int timeout;
   int needed_pairs[DSM_MAX_LIGHTS + 1];
+  int big_count[DSM_MAX_LIGHTS + 1];   // triangles of each view flagged as big
 };
+
+// Contention control for gradient scatters.  A triangle whose pixel bbox spans
+// at least kBigTiles raster tiles is "big": its per-triangle sums go to
+// kBigSlots private copies (spread over L2) instead of straight onto its three
+// vertices, and a resolve kernel adds the copies up.  Block-level reductions
+// of the light and albedo gradients likewise go to kRedSlots copies.
+constexpr int kBigTiles = 16;
+constexpr int kMaxBig = 1024;
+constexpr int kBigSlots = 32;
+constexpr int kRedSlots = 64;
+constexpr int kMaxSharedMat = 256;      // albedo tables up to this size are reduced in shared memory
+
+__device__ __forceinline__ int block_slot(int n) {
+  return (int)((blockIdx.x * 0x9E3779B1u + blockIdx.y * 0x85EBCA77u) >> 16) & (n - 1);
+}
+
+__device__ __forceinline__ int scatter_slot(int n) {
+  return (int)((blockIdx.x * 0x9E3779B1u + blockIdx.y * 0x85EBCA77u + threadIdx.y * 0xC2B2AE3Du) >> 16) & (n - 1);
+}
 
 __device__ __forceinline__ uint32_t order_bits(float z) {
   uint32_t u = __float_as_uint(z);

@@ -48,6 +48,7 @@ struct Buf {
 struct ViewBufs {
   int W = 0, H = 0, tilesX = 0, tilesY = 0;
   Buf clip, snap, depth, setup, orient, sil, count, offset, list, gbuf, gclip, gdepth;
+  Buf big_index, big_tri, big_acc;
   int list_cap = 0;
 };
 
@@ -68,7 +69,7 @@ struct dsm_ctx {
   Buf adj, vf_off, vf_list;
   ViewBufs view[DSM_MAX_LIGHTS + 1];
   LightBufs light[DSM_MAX_LIGHTS];
-  Buf lights_dev, viewM, status, vnormal, camcolor, gcolor, gnormal, gN, gface, gQ, gdirect;
+  Buf lights_dev, viewM, status, vnormal, camcolor, gcolor, gnormal, gN, gface, gQ, gdirect, red;
   Buf scratch_dverts, scratch_dlight, scratch_dalbedo, filter_tmp;
   DevStatus* hstatus = nullptr;
   // state of the last forward
@@ -179,11 +180,11 @@ void dsm_destroy(dsm_ctx* ctx) {
   Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->status,
                  &ctx->vnormal, &ctx->camcolor, &ctx->gcolor, &ctx->gnormal, &ctx->gN, &ctx->gface, &ctx->gQ,
                  &ctx->gdirect, &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo,
-                 &ctx->filter_tmp};
+                 &ctx->filter_tmp, &ctx->red};
   for (Buf* b : bufs) b->release();
   for (auto& v : ctx->view) {
     Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
-                 &v.gbuf, &v.gclip, &v.gdepth};
+                 &v.gbuf, &v.gclip, &v.gdepth, &v.big_index, &v.big_tri, &v.big_acc};
     for (Buf* b : vb) b->release();
   }
   for (auto& l : ctx->light) {
@@ -273,6 +274,9 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   DSM_CHECK(v.offset.ensure((tiles + 1) * 4));
   DSM_CHECK(v.gbuf.ensure((size_t)W * H * sizeof(float4)));
   DSM_CHECK(v.gclip.ensure(Vn * sizeof(float4)));
+  DSM_CHECK(v.big_index.ensure(Tn * 4));
+  DSM_CHECK(v.big_tri.ensure(kMaxBig * 4));
+  DSM_CHECK(v.big_acc.ensure((size_t)kMaxBig * kBigSlots * (is_light ? 15 : 33) * 4));
   if (is_light) {
     DSM_CHECK(v.depth.ensure(Vn * 4));
     DSM_CHECK(v.gdepth.ensure(Vn * 4));
@@ -346,6 +350,7 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
 
   // ---- per view: transform, setup, bin count, scan
   DevStatus* dstat = ctx->status.as<DevStatus>();
+  DSM_CHECK(cudaMemsetAsync(dstat->big_count, 0, sizeof(dstat->big_count), st));
   for (int w = 0; w <= L; ++w) {
     ViewBufs& v = ctx->view[w];
     const bool is_light = w < L;
@@ -354,7 +359,8 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
     launch_tri_setup(mesh->tris, T, v.snap.as<VertSnap>(), v.W, v.H, v.setup.as<TriSetup>(),
                      v.orient.as<int8_t>(), ctx->adj.as<int>(), v.sil.as<uint8_t>(), st);
     DSM_CHECK(cudaMemsetAsync(v.count.p, 0, (size_t)v.tilesX * v.tilesY * 4, st));
-    launch_bin_count(v.setup.as<TriSetup>(), T, v.tilesX, v.count.as<int>(), dstat, st);
+    launch_bin_count(v.setup.as<TriSetup>(), T, v.tilesX, v.count.as<int>(), dstat, w, v.big_index.as<int>(),
+                     v.big_tri.as<int>(), st);
     launch_scan(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), dstat, w, st);
   }
   DSM_CHECK(cudaGetLastError());
@@ -476,6 +482,9 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   DSM_CHECK(ctx->gface.ensure(sizeof(float) * 3 * std::max(T, 1)));
   DSM_CHECK(ctx->gQ.ensure(sizeof(float) * 20 * DSM_MAX_LIGHTS));
   DSM_CHECK(ctx->gdirect.ensure(sizeof(float) * 3 * DSM_MAX_LIGHTS));
+  const int n_mat_red = mesh.n_materials <= kMaxSharedMat ? mesh.n_materials : 0;
+  const int red_stride = 23 * L + 3 * n_mat_red;
+  DSM_CHECK(ctx->red.ensure(sizeof(float) * kRedSlots * std::max(red_stride, 1)));
   for (int l = 0; l < L; ++l) {
     const size_t R2 = (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2);
     DSM_CHECK(ctx->light[l].gm.ensure(R2));
@@ -495,6 +504,9 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   }
   for (int l = 0; l < L; ++l)
     DSM_CHECK(cudaMemsetAsync(ctx->light[l].gm.p, 0, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2), st));
+  DSM_CHECK(cudaMemsetAsync(ctx->red.p, 0, sizeof(float) * kRedSlots * red_stride, st));
+  for (int w = 0; w <= L; ++w)
+    DSM_CHECK(cudaMemsetAsync(ctx->view[w].big_acc.p, 0, (size_t)kMaxBig * kBigSlots * (w < L ? 15 : 33) * 4, st));
 
   t_clear.stop();
   // ---- final antialiasing adjoint and the shading adjoint
@@ -521,11 +533,14 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   ga.gclip = cv.gclip.as<float4>();
   ga.dalbedo = dL_dalbedo;
   for (int l = 0; l < L; ++l) ga.gm[l] = ctx->light[l].gm.as<float2>();
-  ga.gQ = ctx->gQ.as<float>();
-  ga.gdirect = ctx->gdirect.as<float>();
+  ga.red = ctx->red.as<float>();
+  ga.red_stride = red_stride;
+  ga.big = cv.big_index.as<int>();
+  ga.big_acc = cv.big_acc.as<float>();
   {
     StageTimer t(ctx, ST_BWD_SHADE, st);
     launch_shade_backward(sa, ga, st);
+    launch_shade_big_resolve(sa, ga, cv.big_tri.as<int>(), ctx->status.as<DevStatus>(), L, st);
   }
 
   // ---- per light: G^T, antialiasing adjoint, interpolation adjoint
@@ -541,8 +556,9 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
     ViewBufs& v = ctx->view[l];
     LightBufs& lb = ctx->light[l];
     AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(), v.clip.as<float4>()};
+    BigArgs big{v.big_index.as<int>(), v.big_tri.as<int>(), v.big_acc.as<float>(), ctx->status.as<DevStatus>(), l};
     launch_sm_backward(aa, lb.fmap.as<float2>(), lb.gft.as<float2>(), v.depth.as<float>(), v.gclip.as<float4>(),
-                       v.gdepth.as<float>(), ctx->params.aa_shadow, st);
+                       v.gdepth.as<float>(), lb.tmp.as<float>(), big, ctx->params.aa_shadow, st);
   }
 
   t_sm.stop();
@@ -551,9 +567,12 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   VertGradPtrs gp{};
   for (int w = 0; w <= L; ++w) gp.gclip[w] = ctx->view[w].gclip.as<float4>();
   for (int l = 0; l < L; ++l) gp.gdepth[l] = ctx->view[l].gdepth.as<float>();
-  launch_vertex_backward(mesh.verts, V, ctx->viewM.as<float>(), L + 1, L, gp, dL_dverts, ctx->gQ.as<float>(), st);
+  launch_vertex_backward(mesh.verts, V, ctx->viewM.as<float>(), L + 1, L, gp, dL_dverts, ctx->red.as<float>(),
+                         red_stride, st);
   launch_normals_backward(mesh.verts, V, mesh.tris, T, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
                           ctx->gnormal.as<float>(), ctx->gN.as<float>(), ctx->gface.as<float>(), dL_dverts, st);
+  launch_red_reduce(ctx->red.as<float>(), red_stride, L, n_mat_red, ctx->gQ.as<float>(), ctx->gdirect.as<float>(),
+                    dL_dalbedo, st);
   launch_light_grad(ctx->lights_dev.as<LightDev>(), L, ctx->gQ.as<float>(), ctx->gdirect.as<float>(), dL_dlight, st);
   DSM_CHECK(cudaGetLastError());
   return DSM_OK;

@@ -62,13 +62,24 @@ struct ShadeGradArgs {
   float4* gclip;                      // V, dL/d camera clip
   float* dalbedo;                     // M x 3
   float2* gm[DSM_MAX_LIGHTS];         // dL/d(m1, m2) texel maps
-  float* gQ;                          // L x 20
-  float* gdirect;                     // L x 3
+  float* red;                         // kRedSlots x red_stride: [dQ (L x 20) | direct (L x 3) | albedo (M x 3)]
+  int red_stride;
+  const int* big;                     // camera view big-triangle index per triangle
+  float* big_acc;                     // kMaxBig x kBigSlots x 33
 };
 
 struct VertGradPtrs {
   const float4* gclip[DSM_MAX_LIGHTS + 1];   // per view (lights, then camera)
   const float* gdepth[DSM_MAX_LIGHTS];       // per light
+};
+
+// Big-triangle bookkeeping of one view (see kBigTiles).
+struct BigArgs {
+  const int* index;          // per triangle: big index or -1
+  const int* tri;            // per big index: triangle
+  float* acc;                // kMaxBig x kBigSlots x N accumulators
+  const DevStatus* status;   // holds the number of big triangles
+  int view;
 };
 
 struct AAArgs {
@@ -85,7 +96,8 @@ void launch_transform(const float* verts, int V, const float* M20, int W, int H,
                       float* depth, cudaStream_t st);
 void launch_tri_setup(const int* tris, int T, const VertSnap* snap, int W, int H, TriSetup* setup, int8_t* orient,
                       const int* adj, uint8_t* sil, cudaStream_t st);
-void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, cudaStream_t st);
+void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, int view,
+                      int* big_index, int* big_tri, cudaStream_t st);
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st);
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
                      int capacity, DevStatus* status, cudaStream_t st);
@@ -97,7 +109,7 @@ void launch_sm_interp(const float4* gbuf, int R, const int* tris, const float* d
 void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, cudaStream_t st);
 void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, cudaStream_t st);
 void launch_sm_backward(const AAArgs& a, const float2* fmap, const float2* gft, const float* depth, float4* gclip,
-                        float* gdepth, int aa, cudaStream_t st);
+                        float* gdepth, float* gf_scratch, const BigArgs& big, int aa, cudaStream_t st);
 void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
                          int aa, cudaStream_t st);
 
@@ -116,7 +128,11 @@ void launch_normals_backward(const float* verts, int V, const int* tris, int T, 
 void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st);
 void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);
 void launch_vertex_backward(const float* verts, int V, const float* viewM, int n_views, int n_lights,
-                            const VertGradPtrs& gp, float* dverts, float* gQ, cudaStream_t st);
+                            const VertGradPtrs& gp, float* dverts, float* red, int red_stride, cudaStream_t st);
+void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const int* big_tri,
+                              const DevStatus* status, int view, cudaStream_t st);
+void launch_red_reduce(const float* red, int red_stride, int L, int n_mat_red, float* gQ, float* gdirect,
+                       float* dalbedo, cudaStream_t st);
 void launch_light_grad(const LightDev* lights, int L, const float* gQ, const float* gdirect, float* dlight,
                        cudaStream_t st);
 void launch_l2(const float* img, const float* tgt, int64_t n, float* loss, float* grad, cudaStream_t st);

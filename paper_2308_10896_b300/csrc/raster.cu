@@ -220,7 +220,7 @@ __global__ void silhouette_kernel(const int* __restrict__ adj, int T, const int8
 template <bool kFill>
 __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX, int* __restrict__ counter,
                            const int* __restrict__ offset, int* __restrict__ list, int capacity,
-                           DevStatus* status) {
+                           DevStatus* status, int view, int* __restrict__ big_index, int* __restrict__ big_tri) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int lane = threadIdx.x & 31;
   int n = 0, tx0 = 0, ty0 = 0, ntx = 1;
@@ -233,6 +233,15 @@ __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX
       ntx = (i1 >> kTileLog2) - tx0 + 1;
       n = ntx * ((j1 >> kTileLog2) - ty0 + 1);
     }
+  }
+  if (!kFill && t < T) {
+    int b = -1;
+    if (n >= kBigTiles) {
+      b = atomicAdd(&status->big_count[view], 1);
+      if (b < kMaxBig) big_tri[b] = t;
+      else b = -1;
+    }
+    big_index[t] = b;
   }
   int incl = n;
 #pragma unroll
@@ -408,10 +417,12 @@ void launch_tri_setup(const int* tris, int T, const VertSnap* snap, int W, int H
   silhouette_kernel<<<(T + 255) / 256, 256, 0, st>>>(adj, T, orient, sil);
 }
 
-void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, cudaStream_t st) {
+void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, int view,
+                      int* big_index, int* big_tri, cudaStream_t st) {
   if (T == 0) return;
   count_launches(1);
-  bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, nullptr, nullptr, 0, status);
+  bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, nullptr, nullptr, 0, status, view,
+                                                     big_index, big_tri);
 }
 
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st) {
@@ -423,7 +434,8 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, con
                      int capacity, DevStatus* status, cudaStream_t st) {
   if (T == 0) return;
   count_launches(1);
-  bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, offset, list, capacity, status);
+  bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, offset, list, capacity, status, 0,
+                                                    nullptr, nullptr);
 }
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,

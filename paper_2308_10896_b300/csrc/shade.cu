@@ -128,6 +128,46 @@ __device__ __forceinline__ int material_of(const ShadeArgs& a, int tri) {
   return min(max(m, 0), a.n_mat - 1);     // out-of-range material ids read the nearest table entry
 }
 
+// Vertex data of one triangle, kept in registers while consecutive pixels of a
+// strip hit the same triangle.
+struct TriCache {
+  int tri = -1;
+  int v[3];
+  float3 p[3], n[3];
+  float4 cc[3];
+  int mat;
+  float3 alb;
+};
+
+__device__ __forceinline__ void tri_load(const ShadeArgs& a, int t, TriCache& c) {
+  c.tri = t;
+  for (int k = 0; k < 3; ++k) {
+    const int v = a.tris[3 * t + k];
+    c.v[k] = v;
+    c.p[k] = make_float3(a.verts[3 * v], a.verts[3 * v + 1], a.verts[3 * v + 2]);
+    c.n[k] = make_float3(a.vnormal[3 * v], a.vnormal[3 * v + 1], a.vnormal[3 * v + 2]);
+    c.cc[k] = a.cam_clip[v];
+  }
+  c.mat = material_of(a, t);
+  c.alb = make_float3(a.albedo[3 * c.mat], a.albedo[3 * c.mat + 1], a.albedo[3 * c.mat + 2]);
+}
+
+// Surface point of a covered pixel from its G-buffer texel and the cached triangle.
+__device__ __forceinline__ void surf_from(const float4 g, const TriCache& c, Surf& s) {
+  s.tri = c.tri;
+  s.b[0] = g.y; s.b[1] = g.z; s.b[2] = 1.f - g.y - g.z;
+  s.x = make_float3(0.f, 0.f, 0.f);
+  s.nt = make_float3(0.f, 0.f, 0.f);
+  for (int k = 0; k < 3; ++k) {
+    s.v[k] = c.v[k];
+    s.x.x += s.b[k] * c.p[k].x; s.x.y += s.b[k] * c.p[k].y; s.x.z += s.b[k] * c.p[k].z;
+    s.nt.x += s.b[k] * c.n[k].x; s.nt.y += s.b[k] * c.n[k].y; s.nt.z += s.b[k] * c.n[k].z;
+  }
+  s.nlen = sqrtf(s.nt.x * s.nt.x + s.nt.y * s.nt.y + s.nt.z * s.nt.z);
+  const float il = s.nlen > 0.f ? 1.f / s.nlen : 0.f;
+  s.n = make_float3(s.nt.x * il, s.nt.y * il, s.nt.z * il);
+}
+
 // Lookup of Alg. 2 for one light at world point x: clip, depth d, texel
 // coordinates, bilinear (m1, m2), visibility.
 struct Look {
@@ -212,7 +252,6 @@ __device__ __forceinline__ void warp_add_shared(float* dst, float v) {
   if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(dst, v);
 }
 
-constexpr int kMaxSharedMat = 256;
 constexpr int kShadeStrip = 8;
 
 // Per-triangle scatter of the shading adjoint: 9 dL/dv (b_k dL/dx), 9 dL/d unit
@@ -225,7 +264,16 @@ struct ShadeScatter {
   float4* gclip;
   float* sA;            // shared albedo accumulator, or nullptr
   float* dalbedo;
+  const int* big;
+  float* big_acc;
+  int slot;
   __device__ __forceinline__ void operator()(int t, const float (&c)[33]) const {
+    const int b = big[t];
+    if (b >= 0) {
+      float* d = big_acc + ((size_t)b * kBigSlots + slot) * 33;
+      for (int k = 0; k < 33; ++k) atomicAdd(&d[k], c[k]);
+      return;
+    }
     for (int k = 0; k < 3; ++k) {
       const int v = tris[3 * t + k];
       atomicAdd(&dverts[3 * v], c[3 * k]);
@@ -259,25 +307,37 @@ __global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeG
   for (int k = tid; k < DSM_MAX_LIGHTS * 3; k += 256) sD[k] = 0.f;
   for (int k = tid; k < kMaxSharedMat * 3; k += 256) sA[k] = 0.f;
   __syncthreads();
-  ShadeScatter sc{a.tris, &a, g.dverts, g.gnormal, g.gclip, mat_shared ? sA : nullptr, g.dalbedo};
+  ShadeScatter sc{a.tris, &a, g.dverts, g.gnormal, g.gclip, mat_shared ? sA : nullptr, g.dalbedo,
+                  g.big, g.big_acc, scatter_slot(kBigSlots)};
   RunAcc<33> run;
   run_reset(run);
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kShadeStrip;
+  const bool col_ok = i < a.W;
+  TriCache tc;
+  float4 g_next = make_float4(0.f, 0.f, 0.f, 0.f), gc_next = g_next;
+  if (col_ok && j0 < a.H) {
+    g_next = a.gbuf[(size_t)j0 * a.W + i];
+    gc_next = g.gcolor[(size_t)j0 * a.W + i];
+  }
   for (int srow = 0; srow < kShadeStrip; ++srow) {
     const int j = j0 + srow;
-    const bool inb = i < a.W && j < a.H;
-    const size_t p = inb ? (size_t)j * a.W + i : 0;
-    Surf s;
-    const bool cov = inb && load_surf(a, p, s);
-    const float4 gc4 = cov ? g.gcolor[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const bool act = cov && (gc4.x != 0.f || gc4.y != 0.f || gc4.z != 0.f);
-    float3 gx = make_float3(0.f, 0.f, 0.f), gn = make_float3(0.f, 0.f, 0.f);
-    float3 alb = make_float3(0.f, 0.f, 0.f), rad = make_float3(0.f, 0.f, 0.f);
-    if (act) {
-      const int mat = material_of(a, s.tri);
-      alb = make_float3(a.albedo[3 * mat], a.albedo[3 * mat + 1], a.albedo[3 * mat + 2]);
+    const float4 gb4 = g_next;
+    const float4 gcol = gc_next;
+    if (col_ok && j + 1 < a.H && srow + 1 < kShadeStrip) {
+      g_next = a.gbuf[(size_t)(j + 1) * a.W + i];
+      gc_next = g.gcolor[(size_t)(j + 1) * a.W + i];
     }
+    const int id = __float_as_int(gb4.x);
+    const bool act = col_ok && j < a.H && id && (gcol.x != 0.f || gcol.y != 0.f || gcol.z != 0.f);
+    Surf s;
+    if (act) {
+      if (id - 1 != tc.tri) tri_load(a, id - 1, tc);
+      surf_from(gb4, tc, s);
+    }
+    const float4 gc4 = act ? gcol : make_float4(0.f, 0.f, 0.f, 0.f);
+    float3 gx = make_float3(0.f, 0.f, 0.f), gn = make_float3(0.f, 0.f, 0.f);
+    float3 alb = act ? tc.alb : make_float3(0.f, 0.f, 0.f), rad = make_float3(0.f, 0.f, 0.f);
     const float3 grad_rad = make_float3(gc4.x * alb.x, gc4.y * alb.y, gc4.z * alb.z);
     for (int l = 0; l < a.L; ++l) {
       float gq[20];
@@ -374,14 +434,13 @@ __global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeG
       }
       float gb[3];
       for (int k = 0; k < 3; ++k) {
-        const int v = s.v[k];
         c[3 * k] = s.b[k] * gx.x; c[3 * k + 1] = s.b[k] * gx.y; c[3 * k + 2] = s.b[k] * gx.z;
         c[9 + 3 * k] = s.b[k] * gnt.x; c[10 + 3 * k] = s.b[k] * gnt.y; c[11 + 3 * k] = s.b[k] * gnt.z;
-        gb[k] = a.verts[3 * v] * gx.x + a.verts[3 * v + 1] * gx.y + a.verts[3 * v + 2] * gx.z +
-                a.vnormal[3 * v] * gnt.x + a.vnormal[3 * v + 1] * gnt.y + a.vnormal[3 * v + 2] * gnt.z;
+        gb[k] = tc.p[k].x * gx.x + tc.p[k].y * gx.y + tc.p[k].z * gx.z +
+                tc.n[k].x * gnt.x + tc.n[k].y * gnt.y + tc.n[k].z * gnt.z;
       }
       const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
-      const Bary r = bary_at(a.cam_clip[s.v[0]], a.cam_clip[s.v[1]], a.cam_clip[s.v[2]], px, py);
+      const Bary r = bary_at(tc.cc[0], tc.cc[1], tc.cc[2], px, py);
       float4 gcv[3];
       bary_backward(r, gb, px, py, gcv);
       for (int k = 0; k < 3; ++k) {
@@ -392,13 +451,59 @@ __global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeG
   }
   run_flush(run, sc);
   __syncthreads();
+  float* red = g.red + (size_t)block_slot(kRedSlots) * g.red_stride;
   for (int k = tid; k < a.L * 20; k += 256)
-    if (sQ[k] != 0.f) atomicAdd(&g.gQ[k], sQ[k]);
+    if (sQ[k] != 0.f) atomicAdd(&red[k], sQ[k]);
   for (int k = tid; k < a.L * 3; k += 256)
-    if (sD[k] != 0.f) atomicAdd(&g.gdirect[k], sD[k]);
+    if (sD[k] != 0.f) atomicAdd(&red[a.L * 20 + k], sD[k]);
   if (mat_shared)
     for (int k = tid; k < a.n_mat * 3; k += 256)
-      if (sA[k] != 0.f) atomicAdd(&g.dalbedo[k], sA[k]);
+      if (sA[k] != 0.f) atomicAdd(&red[a.L * 23 + k], sA[k]);
+}
+
+// Sum the kBigSlots copies of each big camera-view triangle and scatter them.
+__global__ void shade_big_resolve_kernel(ShadeArgs a, ShadeGradArgs g, const int* __restrict__ big_tri,
+                                         const DevStatus* __restrict__ status, int view) {
+  const int b = blockIdx.x;
+  if (b >= min(status->big_count[view], kMaxBig)) return;
+  __shared__ float sum[33];
+  const int k = threadIdx.x;
+  if (k < 33) {
+    float acc = 0.f;
+    for (int q = 0; q < kBigSlots; ++q) acc += g.big_acc[((size_t)b * kBigSlots + q) * 33 + k];
+    sum[k] = acc;
+  }
+  __syncthreads();
+  if (k == 0) {
+    const int t = big_tri[b];
+    for (int c = 0; c < 3; ++c) {
+      const int v = a.tris[3 * t + c];
+      atomicAdd(&g.dverts[3 * v], sum[3 * c]);
+      atomicAdd(&g.dverts[3 * v + 1], sum[3 * c + 1]);
+      atomicAdd(&g.dverts[3 * v + 2], sum[3 * c + 2]);
+      atomicAdd(&g.gnormal[3 * v], sum[9 + 3 * c]);
+      atomicAdd(&g.gnormal[3 * v + 1], sum[10 + 3 * c]);
+      atomicAdd(&g.gnormal[3 * v + 2], sum[11 + 3 * c]);
+      atomic_add4(&g.gclip[v], make_float4(sum[18 + 4 * c], sum[19 + 4 * c], sum[20 + 4 * c], sum[21 + 4 * c]));
+    }
+    const int mat = material_of(a, t);
+    atomicAdd(&g.dalbedo[3 * mat], sum[30]);
+    atomicAdd(&g.dalbedo[3 * mat + 1], sum[31]);
+    atomicAdd(&g.dalbedo[3 * mat + 2], sum[32]);
+  }
+}
+
+// Sum of the kRedSlots copies: dQ and the direct light terms (overwritten) and
+// the albedo gradient (added).
+__global__ void red_reduce_kernel(const float* __restrict__ red, int stride, int L, int n_mat_red,
+                                  float* __restrict__ gQ, float* __restrict__ gdirect, float* __restrict__ dalbedo) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= L * 23 + n_mat_red * 3) return;
+  float acc = 0.f;
+  for (int q = 0; q < kRedSlots; ++q) acc += red[(size_t)q * stride + k];
+  if (k < L * 20) gQ[k] = acc;
+  else if (k < L * 23) gdirect[k - L * 20] = acc;
+  else dalbedo[k - L * 23] += acc;
 }
 
 // ------------------------------------------------------------------ per-vertex gathers
@@ -407,7 +512,8 @@ __global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeG
 __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __restrict__ verts, int V,
                                                               const float* __restrict__ viewM, int n_views,
                                                               int n_lights, VertGradPtrs gp,
-                                                              float* __restrict__ dverts, float* __restrict__ gQ) {
+                                                              float* __restrict__ dverts, float* __restrict__ red,
+                                                              int red_stride) {
   __shared__ float sQ[DSM_MAX_LIGHTS * 20];
   for (int k = threadIdx.x; k < DSM_MAX_LIGHTS * 20; k += blockDim.x) sQ[k] = 0.f;
   __syncthreads();
@@ -435,8 +541,9 @@ __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __res
     dverts[3 * v] += acc.x; dverts[3 * v + 1] += acc.y; dverts[3 * v + 2] += acc.z;
   }
   __syncthreads();
+  float* dst = red + (size_t)block_slot(kRedSlots) * red_stride;
   for (int k = threadIdx.x; k < n_lights * 20; k += blockDim.x)
-    if (sQ[k] != 0.f) atomicAdd(&gQ[k], sQ[k]);
+    if (sQ[k] != 0.f) atomicAdd(&dst[k], sQ[k]);
 }
 
 // dL/d(pos, dir) = J^T dL/dQ + the direct terms of the shading direction omega:
@@ -518,10 +625,25 @@ void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStrea
 }
 
 void launch_vertex_backward(const float* verts, int V, const float* viewM, int n_views, int n_lights,
-                            const VertGradPtrs& gp, float* dverts, float* gQ, cudaStream_t st) {
+                            const VertGradPtrs& gp, float* dverts, float* red, int red_stride, cudaStream_t st) {
   if (V == 0) return;
   count_launches(1);
-  vertex_backward_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, viewM, n_views, n_lights, gp, dverts, gQ);
+  vertex_backward_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, viewM, n_views, n_lights, gp, dverts, red,
+                                                          red_stride);
+}
+
+void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const int* big_tri,
+                              const DevStatus* status, int view, cudaStream_t st) {
+  count_launches(1);
+  shade_big_resolve_kernel<<<kMaxBig, 64, 0, st>>>(a, g, big_tri, status, view);
+}
+
+void launch_red_reduce(const float* red, int red_stride, int L, int n_mat_red, float* gQ, float* gdirect,
+                       float* dalbedo, cudaStream_t st) {
+  const int n = L * 23 + n_mat_red * 3;
+  if (n == 0) return;
+  count_launches(1);
+  red_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(red, red_stride, L, n_mat_red, gQ, gdirect, dalbedo);
 }
 
 void launch_light_grad(const LightDev* lights, int L, const float* gQ, const float* gdirect, float* dlight,
