@@ -258,7 +258,7 @@ struct SmScatter {
   __device__ __forceinline__ void operator()(int t, const float (&c)[15]) const {
     const int b = big[t];
     if (b >= 0) {
-      float* d = big_acc + ((size_t)b * kBigSlots + slot) * 15;
+      float* d = big_acc + ((size_t)b * kBigSlots + slot) * kBigStrideSm;
       for (int k = 0; k < 15; ++k) atomicAdd(&d[k], c[k]);
       return;
     }
@@ -346,7 +346,7 @@ __global__ void sm_big_resolve_kernel(const int* __restrict__ tris, const int* _
   const int k = threadIdx.x;
   if (k < 15) {
     float acc = 0.f;
-    for (int q = 0; q < kBigSlots; ++q) acc += big_acc[((size_t)b * kBigSlots + q) * 15 + k];
+    for (int q = 0; q < kBigSlots; ++q) acc += big_acc[((size_t)b * kBigSlots + q) * kBigStrideSm + k];
     sum[k] = acc;
   }
   __syncthreads();

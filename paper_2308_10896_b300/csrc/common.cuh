@@ -60,8 +60,10 @@ struct DevStatus {
 // vertices, and a resolve kernel adds the copies up.  Block-level reductions
 // of the light and albedo gradients likewise go to kRedSlots copies.
 constexpr int kBigTiles = 16;
-constexpr int kMaxBig = 1024;
-constexpr int kBigSlots = 32;
+constexpr int kMaxBig = 64;
+constexpr int kBigSlots = 64;
+constexpr int kBigStrideSm = 32;      // floats per slot copy (15 used), one 128-byte line each
+constexpr int kBigStrideCam = 32;     // floats per slot copy (30 used)
 constexpr int kRedSlots = 64;
 constexpr int kMaxSharedMat = 256;      // albedo tables up to this size are reduced in shared memory
 

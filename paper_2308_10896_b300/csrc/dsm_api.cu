@@ -69,7 +69,7 @@ struct dsm_ctx {
   Buf adj, vf_off, vf_list;
   ViewBufs view[DSM_MAX_LIGHTS + 1];
   LightBufs light[DSM_MAX_LIGHTS];
-  Buf lights_dev, viewM, status, vnormal, camcolor, gcolor, gnormal, gN, gface, gQ, gdirect, red;
+  Buf lights_dev, viewM, status, vnormal, camcolor, gcolor, gnormal, gN, gface, gQ, gdirect, red, pgrad;
   Buf scratch_dverts, scratch_dlight, scratch_dalbedo, filter_tmp;
   DevStatus* hstatus = nullptr;
   // state of the last forward
@@ -180,7 +180,7 @@ void dsm_destroy(dsm_ctx* ctx) {
   Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->status,
                  &ctx->vnormal, &ctx->camcolor, &ctx->gcolor, &ctx->gnormal, &ctx->gN, &ctx->gface, &ctx->gQ,
                  &ctx->gdirect, &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo,
-                 &ctx->filter_tmp, &ctx->red};
+                 &ctx->filter_tmp, &ctx->red, &ctx->pgrad};
   for (Buf* b : bufs) b->release();
   for (auto& v : ctx->view) {
     Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
@@ -276,7 +276,7 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   DSM_CHECK(v.gclip.ensure(Vn * sizeof(float4)));
   DSM_CHECK(v.big_index.ensure(Tn * 4));
   DSM_CHECK(v.big_tri.ensure(kMaxBig * 4));
-  DSM_CHECK(v.big_acc.ensure((size_t)kMaxBig * kBigSlots * (is_light ? 15 : 33) * 4));
+  DSM_CHECK(v.big_acc.ensure((size_t)kMaxBig * kBigSlots * (is_light ? kBigStrideSm : kBigStrideCam) * 4));
   if (is_light) {
     DSM_CHECK(v.depth.ensure(Vn * 4));
     DSM_CHECK(v.gdepth.ensure(Vn * 4));
@@ -385,7 +385,7 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
   for (int w = 0; w <= L; ++w) {
     ViewBufs& v = ctx->view[w];
     launch_bin_fill(v.setup.as<TriSetup>(), T, v.tilesX, v.count.as<int>(), v.offset.as<int>(), v.list.as<int>(),
-                    v.list_cap, dstat, st);
+                    v.list_cap, dstat, w, v.big_index.as<int>(), v.big_tri.as<int>(), st);
   }
   t_fill.stop();
   StageTimer t_raster(ctx, ST_RASTER, st);
@@ -477,6 +477,7 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   if (!dL_dlight) { DSM_CHECK(ctx->scratch_dlight.ensure(sizeof(float) * 6 * DSM_MAX_LIGHTS)); dL_dlight = ctx->scratch_dlight.as<float>(); }
   if (!dL_dalbedo) { DSM_CHECK(ctx->scratch_dalbedo.ensure(sizeof(float) * 3 * mesh.n_materials)); dL_dalbedo = ctx->scratch_dalbedo.as<float>(); }
   DSM_CHECK(ctx->gcolor.ensure((size_t)Wc * Hc * sizeof(float4)));
+  DSM_CHECK(ctx->pgrad.ensure((size_t)Wc * Hc * 2 * sizeof(float4)));
   DSM_CHECK(ctx->gnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->gN.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->gface.ensure(sizeof(float) * 3 * std::max(T, 1)));
@@ -506,7 +507,8 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
     DSM_CHECK(cudaMemsetAsync(ctx->light[l].gm.p, 0, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2), st));
   DSM_CHECK(cudaMemsetAsync(ctx->red.p, 0, sizeof(float) * kRedSlots * red_stride, st));
   for (int w = 0; w <= L; ++w)
-    DSM_CHECK(cudaMemsetAsync(ctx->view[w].big_acc.p, 0, (size_t)kMaxBig * kBigSlots * (w < L ? 15 : 33) * 4, st));
+    DSM_CHECK(cudaMemsetAsync(ctx->view[w].big_acc.p, 0,
+                              (size_t)kMaxBig * kBigSlots * (w < L ? kBigStrideSm : kBigStrideCam) * 4, st));
 
   t_clear.stop();
   // ---- final antialiasing adjoint and the shading adjoint
@@ -537,6 +539,7 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   ga.red_stride = red_stride;
   ga.big = cv.big_index.as<int>();
   ga.big_acc = cv.big_acc.as<float>();
+  ga.pgrad = ctx->pgrad.as<float4>();
   {
     StageTimer t(ctx, ST_BWD_SHADE, st);
     launch_shade_backward(sa, ga, st);

@@ -65,7 +65,8 @@ struct ShadeGradArgs {
   float* red;                         // kRedSlots x red_stride: [dQ (L x 20) | direct (L x 3) | albedo (M x 3)]
   int red_stride;
   const int* big;                     // camera view big-triangle index per triangle
-  float* big_acc;                     // kMaxBig x kBigSlots x 33
+  float* big_acc;                     // kMaxBig x kBigSlots x kBigStrideCam
+  float4* pgrad;                      // per pixel: (dL/dx, dL/dn~ x) (dL/dn~ y, z, active, 0)
 };
 
 struct VertGradPtrs {
@@ -100,7 +101,8 @@ void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, De
                       int* big_index, int* big_tri, cudaStream_t st);
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st);
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
-                     int capacity, DevStatus* status, cudaStream_t st);
+                     int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
+                     cudaStream_t st);
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
                    int W, int H, const float4* clip, const int* tris, float4* gbuf, cudaStream_t st);
 

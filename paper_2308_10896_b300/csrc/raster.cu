@@ -243,6 +243,8 @@ __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX
     }
     big_index[t] = b;
   }
+  // big triangles are binned by bin_big_kernel, spread over the whole grid
+  if (t < T && n >= kBigTiles && big_index[t] >= 0) n = 0;
   int incl = n;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -274,6 +276,52 @@ __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX
         if (slot < capacity) list[slot] = o_t;
         else atomicExch(&status->capacity_overflow, 1);
       }
+    }
+  }
+}
+
+// A tile can hold a covered pixel centre of the triangle only if no edge
+// function is negative at all four corner pixel centres of the tile.
+__device__ __forceinline__ bool tile_may_cover(const TriSetup& r, int tx, int ty) {
+  const long long x0 = (long long)(tx * kTile) * kSubpix + 128, x1 = x0 + (long long)(kTile - 1) * kSubpix;
+  const long long y0 = (long long)(ty * kTile) * kSubpix + 128, y1 = y0 + (long long)(kTile - 1) * kSubpix;
+  const int sg = (r.flags & 8) ? -1 : 1;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int a = e == 0 ? 1 : (e == 1 ? 2 : 0), b = e == 0 ? 2 : (e == 1 ? 0 : 1);
+    const long long dx = (long long)sg * (r.X[b] - r.X[a]), dy = (long long)sg * (r.Y[b] - r.Y[a]);
+    // E = dx (Py - Ya) - dy (Px - Xa): maximise over the corner pixel centres
+    const long long py = dx >= 0 ? y1 : y0, px = dy >= 0 ? x0 : x1;
+    if (dx * (py - r.Y[a]) - dy * (px - r.X[a]) < 0) return false;
+  }
+  return true;
+}
+
+// Binning of the big triangles: blockIdx.y selects the triangle, the tiles of
+// its bbox are spread over gridDim.x blocks; tiles it cannot cover are skipped.
+template <bool kFill>
+__global__ void bin_big_kernel(const TriSetup* __restrict__ setup, const int* __restrict__ big_tri,
+                               const DevStatus* __restrict__ status, int view, int tilesX,
+                               int* __restrict__ counter, const int* __restrict__ offset, int* __restrict__ list,
+                               int capacity, DevStatus* wstatus) {
+  const int b = blockIdx.y;
+  if (b >= min(status->big_count[view], kMaxBig)) return;
+  const int t = big_tri[b];
+  const TriSetup r = setup[t];
+  const int i0 = r.ibox & 0xffff, i1 = (unsigned)r.ibox >> 16, j0 = r.jbox & 0xffff, j1 = (unsigned)r.jbox >> 16;
+  const int tx0 = i0 >> kTileLog2, ty0 = j0 >> kTileLog2;
+  const int ntx = (i1 >> kTileLog2) - tx0 + 1, nty = (j1 >> kTileLog2) - ty0 + 1;
+  const int n = ntx * nty;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const int tx = tx0 + q % ntx, ty = ty0 + q / ntx;
+    if (!tile_may_cover(r, tx, ty)) continue;
+    const int tile = ty * tilesX + tx;
+    if (!kFill) {
+      atomicAdd(&counter[tile], 1);
+    } else {
+      const int slot = offset[tile] + atomicAdd(&counter[tile], 1);
+      if (slot < capacity) list[slot] = t;
+      else atomicExch(&wstatus->capacity_overflow, 1);
     }
   }
 }
@@ -423,6 +471,9 @@ void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, De
   count_launches(1);
   bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, nullptr, nullptr, 0, status, view,
                                                      big_index, big_tri);
+  count_launches(1);
+  bin_big_kernel<false><<<dim3(16, kMaxBig), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, nullptr,
+                                                          nullptr, 0, status);
 }
 
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st) {
@@ -431,11 +482,15 @@ void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cu
 }
 
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
-                     int capacity, DevStatus* status, cudaStream_t st) {
+                     int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
+                     cudaStream_t st) {
   if (T == 0) return;
   count_launches(1);
-  bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, offset, list, capacity, status, 0,
-                                                    nullptr, nullptr);
+  bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, offset, list, capacity, status, view,
+                                                    const_cast<int*>(big_index), const_cast<int*>(big_tri));
+  count_launches(1);
+  bin_big_kernel<true><<<dim3(16, kMaxBig), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, offset, list,
+                                                         capacity, status);
 }
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,

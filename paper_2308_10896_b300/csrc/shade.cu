@@ -254,24 +254,181 @@ __device__ __forceinline__ void warp_add_shared(float* dst, float v) {
 
 constexpr int kShadeStrip = 8;
 
-// Per-triangle scatter of the shading adjoint: 9 dL/dv (b_k dL/dx), 9 dL/d unit
-// vertex normal, 12 dL/d camera clip, 3 dL/d albedo.
-struct ShadeScatter {
+// Adjoint of shade_kernel, one thread per pixel.  Scatters the texel maps
+// dL/d(m1, m2) (bilinear adjoint), reduces dL/dQ, the direct light terms and
+// the albedo gradient per block (slot copies), and writes the per-pixel
+// dL/d world position and dL/d interpolated normal for shade_scatter_kernel.
+__global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g) {
+  __shared__ float sQ[DSM_MAX_LIGHTS * 20];
+  __shared__ float sD[DSM_MAX_LIGHTS * 3];
+  __shared__ float sA[kMaxSharedMat * 3];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const bool mat_shared = a.n_mat <= kMaxSharedMat;
+  for (int k = tid; k < DSM_MAX_LIGHTS * 20; k += 256) sQ[k] = 0.f;
+  for (int k = tid; k < DSM_MAX_LIGHTS * 3; k += 256) sD[k] = 0.f;
+  for (int k = tid; k < kMaxSharedMat * 3; k += 256) sA[k] = 0.f;
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const bool inb = i < a.W && j < a.H;
+  const size_t p = inb ? (size_t)j * a.W + i : 0;
+  const float4 gb4 = inb ? a.gbuf[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 gcol = inb ? g.gcolor[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int id = __float_as_int(gb4.x);
+  const bool act = inb && id && (gcol.x != 0.f || gcol.y != 0.f || gcol.z != 0.f);
+  Surf s;
+  int mat = -1;
+  float3 alb = make_float3(0.f, 0.f, 0.f);
+  if (act) {
+    TriCache tc;
+    tri_load(a, id - 1, tc);
+    surf_from(gb4, tc, s);
+    mat = tc.mat;
+    alb = tc.alb;
+  }
+  const float4 gc4 = act ? gcol : make_float4(0.f, 0.f, 0.f, 0.f);
+  float3 gx = make_float3(0.f, 0.f, 0.f), gn = make_float3(0.f, 0.f, 0.f), rad = make_float3(0.f, 0.f, 0.f);
+  const float3 grad_rad = make_float3(gc4.x * alb.x, gc4.y * alb.y, gc4.z * alb.z);
+  for (int l = 0; l < a.L; ++l) {
+    float gq[20];
+#pragma unroll
+    for (int k = 0; k < 20; ++k) gq[k] = 0.f;
+    float3 gdir = make_float3(0.f, 0.f, 0.f);
+    if (act) {
+      const LightDev& Ld = a.lights[l];
+      const int R = a.res[l];
+      const Look L = lookup(Ld.Q, a.mom[l], R, s.x, a.min_variance);
+      float len;
+      const float3 om = light_omega(Ld, s.x, len);
+      const float ndo = s.n.x * om.x + s.n.y * om.y + s.n.z * om.z;
+      const float lam = fmaxf(ndo, 0.f);
+      rad.x += L.vis * lam * Ld.intensity[0]; rad.y += L.vis * lam * Ld.intensity[1]; rad.z += L.vis * lam * Ld.intensity[2];
+      const float sl = grad_rad.x * Ld.intensity[0] + grad_rad.y * Ld.intensity[1] + grad_rad.z * Ld.intensity[2];
+      const float gvis = sl * lam, glam = sl * L.vis;
+      if (ndo > 0.f && glam != 0.f) {
+        gn.x += glam * om.x; gn.y += glam * om.y; gn.z += glam * om.z;
+        const float3 gom = make_float3(glam * s.n.x, glam * s.n.y, glam * s.n.z);
+        if (Ld.type == 0) {
+          gdir = gom;                    // dL/d omega with omega = -fwd (chained in light_grad_kernel)
+        } else {
+          const float d = om.x * gom.x + om.y * gom.y + om.z * gom.z;
+          const float il = 1.f / len;
+          const float3 gp = make_float3((gom.x - om.x * d) * il, (gom.y - om.y * d) * il, (gom.z - om.z * d) * il);
+          gdir = gp;                     // dL/d position (direct term)
+          gx.x -= gp.x; gx.y -= gp.y; gx.z -= gp.z;
+        }
+      }
+      if (L.inside && L.delta > 0.f && gvis != 0.f) {
+        const float S = L.var + L.delta * L.delta;
+        const float iS2 = 1.f / (S * S);
+        const float dv_dvar = L.delta * L.delta * iS2;
+        const float dv_ddelta = -2.f * L.var * L.delta * iS2;
+        const float gd = gvis * dv_ddelta;
+        float gm1 = -gd, gm2 = 0.f;
+        if (!L.var_clamped) {
+          gm1 += gvis * dv_dvar * (-2.f * L.m.x);
+          gm2 = gvis * dv_dvar;
+        }
+        const int i0 = min(max(L.i0, 0), R - 1), i1 = min(max(L.i0 + 1, 0), R - 1);
+        const int j0c = min(max(L.j0, 0), R - 1), j1c = min(max(L.j0 + 1, 0), R - 1);
+        const float w00 = (1.f - L.fs) * (1.f - L.ft), w01 = L.fs * (1.f - L.ft), w10 = (1.f - L.fs) * L.ft,
+                    w11 = L.fs * L.ft;
+        float2* gm = g.gm[l];
+        atomic_add2(&gm[(size_t)j0c * R + i0], make_float2(w00 * gm1, w00 * gm2));
+        atomic_add2(&gm[(size_t)j0c * R + i1], make_float2(w01 * gm1, w01 * gm2));
+        atomic_add2(&gm[(size_t)j1c * R + i0], make_float2(w10 * gm1, w10 * gm2));
+        atomic_add2(&gm[(size_t)j1c * R + i1], make_float2(w11 * gm1, w11 * gm2));
+        const float2* mom = a.mom[l];
+        const float2 m00 = mom[(size_t)j0c * R + i0], m01 = mom[(size_t)j0c * R + i1];
+        const float2 m10 = mom[(size_t)j1c * R + i0], m11 = mom[(size_t)j1c * R + i1];
+        const float d00 = m00.x * gm1 + m00.y * gm2, d01 = m01.x * gm1 + m01.y * gm2;
+        const float d10 = m10.x * gm1 + m10.y * gm2, d11 = m11.x * gm1 + m11.y * gm2;
+        const float gfs = (1.f - L.ft) * (d01 - d00) + L.ft * (d11 - d10);
+        const float gft = (1.f - L.fs) * (d10 - d00) + L.fs * (d11 - d01);
+        // s = (0.5 u + 0.5) R - 0.5,  t = (0.5 - 0.5 v) R - 0.5,  u = cx / cw,  v = cy / cw
+        const float gu = gfs * 0.5f * R, gv = -gft * 0.5f * R;
+        const float iw = 1.f / L.clip.w;
+        const float u = L.clip.x * iw, v = L.clip.y * iw;
+        const float gcl[4] = {gu * iw, gv * iw, 0.f, -(gu * u + gv * v) * iw};
+        const float xh[4] = {s.x.x, s.x.y, s.x.z, 1.f};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) gq[r * 4 + c] = gcl[r] * xh[c];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) gq[16 + c] = gd * xh[c];
+        const float* Q = Ld.Q;
+        gx.x += Q[0] * gcl[0] + Q[4] * gcl[1] + Q[12] * gcl[3] + Q[16] * gd;
+        gx.y += Q[1] * gcl[0] + Q[5] * gcl[1] + Q[13] * gcl[3] + Q[17] * gd;
+        gx.z += Q[2] * gcl[0] + Q[6] * gcl[1] + Q[14] * gcl[3] + Q[18] * gd;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 20; ++k) warp_add_shared(&sQ[l * 20 + k], gq[k]);
+    warp_add_shared(&sD[l * 3 + 0], gdir.x);
+    warp_add_shared(&sD[l * 3 + 1], gdir.y);
+    warp_add_shared(&sD[l * 3 + 2], gdir.z);
+  }
+  // albedo: warp-reduced when the warp's active pixels share one material
+  const float3 ga = make_float3(gc4.x * rad.x, gc4.y * rad.y, gc4.z * rad.z);
+  const int m0 = __reduce_max_sync(kFull, mat);
+  if (__all_sync(kFull, mat == -1 || mat == m0)) {
+    if (m0 >= 0) {
+      float v0 = ga.x, v1 = ga.y, v2 = ga.z;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        v0 += __shfl_xor_sync(kFull, v0, o);
+        v1 += __shfl_xor_sync(kFull, v1, o);
+        v2 += __shfl_xor_sync(kFull, v2, o);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        float* dst = mat_shared ? sA : g.dalbedo;
+        atomicAdd(&dst[3 * m0], v0); atomicAdd(&dst[3 * m0 + 1], v1); atomicAdd(&dst[3 * m0 + 2], v2);
+      }
+    }
+  } else if (act) {
+    float* dst = mat_shared ? sA : g.dalbedo;
+    atomicAdd(&dst[3 * mat], ga.x); atomicAdd(&dst[3 * mat + 1], ga.y); atomicAdd(&dst[3 * mat + 2], ga.z);
+  }
+  // per-pixel dL/dx and dL/d(interpolated normal) for the scatter pass
+  if (inb) {
+    float3 gnt = make_float3(0.f, 0.f, 0.f);
+    if (act && s.nlen > 0.f) {
+      const float d = s.n.x * gn.x + s.n.y * gn.y + s.n.z * gn.z;
+      const float il = 1.f / s.nlen;
+      gnt = make_float3((gn.x - s.n.x * d) * il, (gn.y - s.n.y * d) * il, (gn.z - s.n.z * d) * il);
+    }
+    g.pgrad[2 * p] = make_float4(gx.x, gx.y, gx.z, gnt.x);
+    g.pgrad[2 * p + 1] = make_float4(gnt.y, gnt.z, act ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  float* red = g.red + (size_t)block_slot(kRedSlots) * g.red_stride;
+  for (int k = tid; k < a.L * 20; k += 256)
+    if (sQ[k] != 0.f) atomicAdd(&red[k], sQ[k]);
+  for (int k = tid; k < a.L * 3; k += 256)
+    if (sD[k] != 0.f) atomicAdd(&red[a.L * 20 + k], sD[k]);
+  if (mat_shared)
+    for (int k = tid; k < a.n_mat * 3; k += 256)
+      if (sA[k] != 0.f) atomicAdd(&red[a.L * 23 + k], sA[k]);
+}
+
+// Per-triangle scatter of the camera interpolation adjoint: from the per-pixel
+// dL/dx and dL/dn, x = sum b_k v_k and n~ = sum b_k n_k give 9 dL/dv (b_k dL/dx),
+// 9 dL/d unit vertex normal (b_k dL/dn~) and, through the barycentrics, 12
+// dL/d camera clip.  Strips of kShadeStrip rows per warp with a run
+// accumulator; big triangles go to their slot copies.
+struct CamScatter {
   const int* tris;
-  const ShadeArgs* a;
   float* dverts;
   float* gnormal;
   float4* gclip;
-  float* sA;            // shared albedo accumulator, or nullptr
-  float* dalbedo;
   const int* big;
   float* big_acc;
   int slot;
-  __device__ __forceinline__ void operator()(int t, const float (&c)[33]) const {
+  __device__ __forceinline__ void operator()(int t, const float (&c)[30]) const {
     const int b = big[t];
     if (b >= 0) {
-      float* d = big_acc + ((size_t)b * kBigSlots + slot) * 33;
-      for (int k = 0; k < 33; ++k) atomicAdd(&d[k], c[k]);
+      float* d = big_acc + ((size_t)b * kBigSlots + slot) * kBigStrideCam;
+      for (int k = 0; k < 30; ++k) atomicAdd(&d[k], c[k]);
       return;
     }
     for (int k = 0; k < 3; ++k) {
@@ -284,181 +441,52 @@ struct ShadeScatter {
       atomicAdd(&gnormal[3 * v + 2], c[11 + 3 * k]);
       atomic_add4(&gclip[v], make_float4(c[18 + 4 * k], c[19 + 4 * k], c[20 + 4 * k], c[21 + 4 * k]));
     }
-    const int mat = material_of(*a, t);
-    float* dst = sA ? sA : dalbedo;
-    atomicAdd(&dst[3 * mat], c[30]);
-    atomicAdd(&dst[3 * mat + 1], c[31]);
-    atomicAdd(&dst[3 * mat + 2], c[32]);
   }
 };
 
-// Adjoint of shade_kernel (and of the camera interpolation).  Per pixel: the
-// texel maps dL/d(m1, m2) (bilinear adjoint), the light matrices Q and the
-// direct light terms (block-reduced), and a per-triangle contribution (vertex
-// positions, vertex normals, camera clip coordinates, albedo) that goes
-// through a warp run accumulator.  Each warp walks kShadeStrip rows.
-__global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g) {
-  __shared__ float sQ[DSM_MAX_LIGHTS * 20];
-  __shared__ float sD[DSM_MAX_LIGHTS * 3];
-  __shared__ float sA[kMaxSharedMat * 3];
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const bool mat_shared = a.n_mat <= kMaxSharedMat;
-  for (int k = tid; k < DSM_MAX_LIGHTS * 20; k += 256) sQ[k] = 0.f;
-  for (int k = tid; k < DSM_MAX_LIGHTS * 3; k += 256) sD[k] = 0.f;
-  for (int k = tid; k < kMaxSharedMat * 3; k += 256) sA[k] = 0.f;
-  __syncthreads();
-  ShadeScatter sc{a.tris, &a, g.dverts, g.gnormal, g.gclip, mat_shared ? sA : nullptr, g.dalbedo,
-                  g.big, g.big_acc, scatter_slot(kBigSlots)};
-  RunAcc<33> run;
-  run_reset(run);
+__global__ void __launch_bounds__(256) shade_scatter_kernel(ShadeArgs a, ShadeGradArgs g) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kShadeStrip;
   const bool col_ok = i < a.W;
+  CamScatter sc{a.tris, g.dverts, g.gnormal, g.gclip, g.big, g.big_acc, scatter_slot(kBigSlots)};
+  RunAcc<30> run;
+  run_reset(run);
   TriCache tc;
-  float4 g_next = make_float4(0.f, 0.f, 0.f, 0.f), gc_next = g_next;
-  if (col_ok && j0 < a.H) {
-    g_next = a.gbuf[(size_t)j0 * a.W + i];
-    gc_next = g.gcolor[(size_t)j0 * a.W + i];
-  }
   for (int srow = 0; srow < kShadeStrip; ++srow) {
     const int j = j0 + srow;
-    const float4 gb4 = g_next;
-    const float4 gcol = gc_next;
-    if (col_ok && j + 1 < a.H && srow + 1 < kShadeStrip) {
-      g_next = a.gbuf[(size_t)(j + 1) * a.W + i];
-      gc_next = g.gcolor[(size_t)(j + 1) * a.W + i];
-    }
-    const int id = __float_as_int(gb4.x);
-    const bool act = col_ok && j < a.H && id && (gcol.x != 0.f || gcol.y != 0.f || gcol.z != 0.f);
-    Surf s;
-    if (act) {
-      if (id - 1 != tc.tri) tri_load(a, id - 1, tc);
-      surf_from(gb4, tc, s);
-    }
-    const float4 gc4 = act ? gcol : make_float4(0.f, 0.f, 0.f, 0.f);
-    float3 gx = make_float3(0.f, 0.f, 0.f), gn = make_float3(0.f, 0.f, 0.f);
-    float3 alb = act ? tc.alb : make_float3(0.f, 0.f, 0.f), rad = make_float3(0.f, 0.f, 0.f);
-    const float3 grad_rad = make_float3(gc4.x * alb.x, gc4.y * alb.y, gc4.z * alb.z);
-    for (int l = 0; l < a.L; ++l) {
-      float gq[20];
+    float c[30];
 #pragma unroll
-      for (int k = 0; k < 20; ++k) gq[k] = 0.f;
-      float3 gdir = make_float3(0.f, 0.f, 0.f);
-      if (act) {
-        const LightDev& Ld = a.lights[l];
-        const int R = a.res[l];
-        const Look L = lookup(Ld.Q, a.mom[l], R, s.x, a.min_variance);
-        float len;
-        const float3 om = light_omega(Ld, s.x, len);
-        const float ndo = s.n.x * om.x + s.n.y * om.y + s.n.z * om.z;
-        const float lam = fmaxf(ndo, 0.f);
-        rad.x += L.vis * lam * Ld.intensity[0]; rad.y += L.vis * lam * Ld.intensity[1]; rad.z += L.vis * lam * Ld.intensity[2];
-        const float sl = grad_rad.x * Ld.intensity[0] + grad_rad.y * Ld.intensity[1] + grad_rad.z * Ld.intensity[2];
-        const float gvis = sl * lam, glam = sl * L.vis;
-        if (ndo > 0.f && glam != 0.f) {
-          gn.x += glam * om.x; gn.y += glam * om.y; gn.z += glam * om.z;
-          const float3 gom = make_float3(glam * s.n.x, glam * s.n.y, glam * s.n.z);
-          if (Ld.type == 0) {
-            gdir = gom;                    // dL/d omega with omega = -fwd (chained in light_grad_kernel)
-          } else {
-            const float d = om.x * gom.x + om.y * gom.y + om.z * gom.z;
-            const float il = 1.f / len;
-            const float3 gp = make_float3((gom.x - om.x * d) * il, (gom.y - om.y * d) * il, (gom.z - om.z * d) * il);
-            gdir = gp;                     // dL/d position (direct term)
-            gx.x -= gp.x; gx.y -= gp.y; gx.z -= gp.z;
-          }
-        }
-        if (L.inside && L.delta > 0.f && gvis != 0.f) {
-          const float S = L.var + L.delta * L.delta;
-          const float iS2 = 1.f / (S * S);
-          const float dv_dvar = L.delta * L.delta * iS2;
-          const float dv_ddelta = -2.f * L.var * L.delta * iS2;
-          const float gd = gvis * dv_ddelta;
-          float gm1 = -gd, gm2 = 0.f;
-          if (!L.var_clamped) {
-            gm1 += gvis * dv_dvar * (-2.f * L.m.x);
-            gm2 = gvis * dv_dvar;
-          }
-          const int i0 = min(max(L.i0, 0), R - 1), i1 = min(max(L.i0 + 1, 0), R - 1);
-          const int j0c = min(max(L.j0, 0), R - 1), j1c = min(max(L.j0 + 1, 0), R - 1);
-          const float w00 = (1.f - L.fs) * (1.f - L.ft), w01 = L.fs * (1.f - L.ft), w10 = (1.f - L.fs) * L.ft,
-                      w11 = L.fs * L.ft;
-          float2* gm = g.gm[l];
-          atomic_add2(&gm[(size_t)j0c * R + i0], make_float2(w00 * gm1, w00 * gm2));
-          atomic_add2(&gm[(size_t)j0c * R + i1], make_float2(w01 * gm1, w01 * gm2));
-          atomic_add2(&gm[(size_t)j1c * R + i0], make_float2(w10 * gm1, w10 * gm2));
-          atomic_add2(&gm[(size_t)j1c * R + i1], make_float2(w11 * gm1, w11 * gm2));
-          const float2* mom = a.mom[l];
-          const float2 m00 = mom[(size_t)j0c * R + i0], m01 = mom[(size_t)j0c * R + i1];
-          const float2 m10 = mom[(size_t)j1c * R + i0], m11 = mom[(size_t)j1c * R + i1];
-          const float d00 = m00.x * gm1 + m00.y * gm2, d01 = m01.x * gm1 + m01.y * gm2;
-          const float d10 = m10.x * gm1 + m10.y * gm2, d11 = m11.x * gm1 + m11.y * gm2;
-          const float gfs = (1.f - L.ft) * (d01 - d00) + L.ft * (d11 - d10);
-          const float gft = (1.f - L.fs) * (d10 - d00) + L.fs * (d11 - d01);
-          // s = (0.5 u + 0.5) R - 0.5,  t = (0.5 - 0.5 v) R - 0.5,  u = cx / cw,  v = cy / cw
-          const float gu = gfs * 0.5f * R, gv = -gft * 0.5f * R;
-          const float iw = 1.f / L.clip.w;
-          const float u = L.clip.x * iw, v = L.clip.y * iw;
-          const float gcl[4] = {gu * iw, gv * iw, 0.f, -(gu * u + gv * v) * iw};
-          const float xh[4] = {s.x.x, s.x.y, s.x.z, 1.f};
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) gq[r * 4 + c] = gcl[r] * xh[c];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) gq[16 + c] = gd * xh[c];
-          const float* Q = Ld.Q;
-          gx.x += Q[0] * gcl[0] + Q[4] * gcl[1] + Q[12] * gcl[3] + Q[16] * gd;
-          gx.y += Q[1] * gcl[0] + Q[5] * gcl[1] + Q[13] * gcl[3] + Q[17] * gd;
-          gx.z += Q[2] * gcl[0] + Q[6] * gcl[1] + Q[14] * gcl[3] + Q[18] * gd;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 20; ++k) warp_add_shared(&sQ[l * 20 + k], gq[k]);
-      warp_add_shared(&sD[l * 3 + 0], gdir.x);
-      warp_add_shared(&sD[l * 3 + 1], gdir.y);
-      warp_add_shared(&sD[l * 3 + 2], gdir.z);
-    }
-    float c[33];
-#pragma unroll
-    for (int k = 0; k < 33; ++k) c[k] = 0.f;
+    for (int k = 0; k < 30; ++k) c[k] = 0.f;
     int t = -1;
-    if (act) {
-      t = s.tri;
-      c[30] = gc4.x * rad.x; c[31] = gc4.y * rad.y; c[32] = gc4.z * rad.z;
-      float3 gnt = make_float3(0.f, 0.f, 0.f);
-      if (s.nlen > 0.f) {
-        const float d = s.n.x * gn.x + s.n.y * gn.y + s.n.z * gn.z;
-        const float il = 1.f / s.nlen;
-        gnt = make_float3((gn.x - s.n.x * d) * il, (gn.y - s.n.y * d) * il, (gn.z - s.n.z * d) * il);
-      }
-      float gb[3];
-      for (int k = 0; k < 3; ++k) {
-        c[3 * k] = s.b[k] * gx.x; c[3 * k + 1] = s.b[k] * gx.y; c[3 * k + 2] = s.b[k] * gx.z;
-        c[9 + 3 * k] = s.b[k] * gnt.x; c[10 + 3 * k] = s.b[k] * gnt.y; c[11 + 3 * k] = s.b[k] * gnt.z;
-        gb[k] = tc.p[k].x * gx.x + tc.p[k].y * gx.y + tc.p[k].z * gx.z +
-                tc.n[k].x * gnt.x + tc.n[k].y * gnt.y + tc.n[k].z * gnt.z;
-      }
-      const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
-      const Bary r = bary_at(tc.cc[0], tc.cc[1], tc.cc[2], px, py);
-      float4 gcv[3];
-      bary_backward(r, gb, px, py, gcv);
-      for (int k = 0; k < 3; ++k) {
-        c[18 + 4 * k] = gcv[k].x; c[19 + 4 * k] = gcv[k].y; c[20 + 4 * k] = gcv[k].z; c[21 + 4 * k] = gcv[k].w;
+    if (col_ok && j < a.H) {
+      const size_t p = (size_t)j * a.W + i;
+      const float4 q1 = g.pgrad[2 * p + 1];
+      if (q1.z != 0.f) {
+        const float4 q0 = g.pgrad[2 * p];
+        const float4 gb4 = a.gbuf[p];
+        t = __float_as_int(gb4.x) - 1;
+        if (t != tc.tri) tri_load(a, t, tc);
+        const float b[3] = {gb4.y, gb4.z, 1.f - gb4.y - gb4.z};
+        const float3 gx = make_float3(q0.x, q0.y, q0.z), gnt = make_float3(q0.w, q1.x, q1.y);
+        float gb[3];
+        for (int k = 0; k < 3; ++k) {
+          c[3 * k] = b[k] * gx.x; c[3 * k + 1] = b[k] * gx.y; c[3 * k + 2] = b[k] * gx.z;
+          c[9 + 3 * k] = b[k] * gnt.x; c[10 + 3 * k] = b[k] * gnt.y; c[11 + 3 * k] = b[k] * gnt.z;
+          gb[k] = tc.p[k].x * gx.x + tc.p[k].y * gx.y + tc.p[k].z * gx.z +
+                  tc.n[k].x * gnt.x + tc.n[k].y * gnt.y + tc.n[k].z * gnt.z;
+        }
+        const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
+        const Bary r = bary_at(tc.cc[0], tc.cc[1], tc.cc[2], px, py);
+        float4 gcv[3];
+        bary_backward(r, gb, px, py, gcv);
+        for (int k = 0; k < 3; ++k) {
+          c[18 + 4 * k] = gcv[k].x; c[19 + 4 * k] = gcv[k].y; c[20 + 4 * k] = gcv[k].z; c[21 + 4 * k] = gcv[k].w;
+        }
       }
     }
     run_add(run, t, c, sc);
   }
   run_flush(run, sc);
-  __syncthreads();
-  float* red = g.red + (size_t)block_slot(kRedSlots) * g.red_stride;
-  for (int k = tid; k < a.L * 20; k += 256)
-    if (sQ[k] != 0.f) atomicAdd(&red[k], sQ[k]);
-  for (int k = tid; k < a.L * 3; k += 256)
-    if (sD[k] != 0.f) atomicAdd(&red[a.L * 20 + k], sD[k]);
-  if (mat_shared)
-    for (int k = tid; k < a.n_mat * 3; k += 256)
-      if (sA[k] != 0.f) atomicAdd(&red[a.L * 23 + k], sA[k]);
 }
 
 // Sum the kBigSlots copies of each big camera-view triangle and scatter them.
@@ -466,30 +494,23 @@ __global__ void shade_big_resolve_kernel(ShadeArgs a, ShadeGradArgs g, const int
                                          const DevStatus* __restrict__ status, int view) {
   const int b = blockIdx.x;
   if (b >= min(status->big_count[view], kMaxBig)) return;
-  __shared__ float sum[33];
+  __shared__ float sum[30];
   const int k = threadIdx.x;
-  if (k < 33) {
+  if (k < 30) {
     float acc = 0.f;
-    for (int q = 0; q < kBigSlots; ++q) acc += g.big_acc[((size_t)b * kBigSlots + q) * 33 + k];
+    for (int q = 0; q < kBigSlots; ++q) acc += g.big_acc[((size_t)b * kBigSlots + q) * kBigStrideCam + k];
     sum[k] = acc;
   }
   __syncthreads();
-  if (k == 0) {
-    const int t = big_tri[b];
-    for (int c = 0; c < 3; ++c) {
-      const int v = a.tris[3 * t + c];
-      atomicAdd(&g.dverts[3 * v], sum[3 * c]);
-      atomicAdd(&g.dverts[3 * v + 1], sum[3 * c + 1]);
-      atomicAdd(&g.dverts[3 * v + 2], sum[3 * c + 2]);
-      atomicAdd(&g.gnormal[3 * v], sum[9 + 3 * c]);
-      atomicAdd(&g.gnormal[3 * v + 1], sum[10 + 3 * c]);
-      atomicAdd(&g.gnormal[3 * v + 2], sum[11 + 3 * c]);
-      atomic_add4(&g.gclip[v], make_float4(sum[18 + 4 * c], sum[19 + 4 * c], sum[20 + 4 * c], sum[21 + 4 * c]));
-    }
-    const int mat = material_of(a, t);
-    atomicAdd(&g.dalbedo[3 * mat], sum[30]);
-    atomicAdd(&g.dalbedo[3 * mat + 1], sum[31]);
-    atomicAdd(&g.dalbedo[3 * mat + 2], sum[32]);
+  if (k < 3) {
+    const int v = a.tris[3 * big_tri[b] + k];
+    atomicAdd(&g.dverts[3 * v], sum[3 * k]);
+    atomicAdd(&g.dverts[3 * v + 1], sum[3 * k + 1]);
+    atomicAdd(&g.dverts[3 * v + 2], sum[3 * k + 2]);
+    atomicAdd(&g.gnormal[3 * v], sum[9 + 3 * k]);
+    atomicAdd(&g.gnormal[3 * v + 1], sum[10 + 3 * k]);
+    atomicAdd(&g.gnormal[3 * v + 2], sum[11 + 3 * k]);
+    atomic_add4(&g.gclip[v], make_float4(sum[18 + 4 * k], sum[19 + 4 * k], sum[20 + 4 * k], sum[21 + 4 * k]));
   }
 }
 
@@ -619,9 +640,12 @@ void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st) {
 }
 
 void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st) {
-  dim3 b(32, 8), grid((a.W + 31) / 32, (a.H + 8 * kShadeStrip - 1) / (8 * kShadeStrip));
+  dim3 b(32, 8);
   count_launches(1);
-  shade_backward_kernel<<<grid, b, 0, st>>>(a, g);
+  shade_backward_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, g);
+  dim3 grid((a.W + 31) / 32, (a.H + 8 * kShadeStrip - 1) / (8 * kShadeStrip));
+  count_launches(1);
+  shade_scatter_kernel<<<grid, b, 0, st>>>(a, g);
 }
 
 void launch_vertex_backward(const float* verts, int V, const float* viewM, int n_views, int n_lights,
@@ -635,7 +659,7 @@ void launch_vertex_backward(const float* verts, int V, const float* viewM, int n
 void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const int* big_tri,
                               const DevStatus* status, int view, cudaStream_t st) {
   count_launches(1);
-  shade_big_resolve_kernel<<<kMaxBig, 64, 0, st>>>(a, g, big_tri, status, view);
+  shade_big_resolve_kernel<<<kMaxBig, 32, 0, st>>>(a, g, big_tri, status, view);
 }
 
 void launch_red_reduce(const float* red, int red_stride, int L, int n_mat_red, float* gQ, float* gdirect,
