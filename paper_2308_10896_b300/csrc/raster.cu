@@ -373,71 +373,106 @@ __global__ void scan_kernel(int* __restrict__ count, int n, int* __restrict__ of
 }
 
 // ------------------------------------------------------------------ tile rasteriser
-// One 256-thread CTA per 16x16 tile, one thread per pixel.  The tile's triangle
-// list is staged through shared memory 256 records at a time; every pixel keeps
-// the smallest (depth key, triangle) of the triangles covering its centre
-// (integer edge functions, top-left rule), then writes one 16-byte G-buffer
-// texel: id + 1, perspective-correct b0, b1, depth key.
+// Coverage of pixel centre (Px, Py) by a setup record: integer edge functions
+// with the top-left rule; returns the depth key or ~0.
+__device__ __forceinline__ uint64_t cover_key(const TriSetup& r, long long Px, long long Py) {
+  const int flags = r.flags;
+  const int sg = (flags & 8) ? -1 : 1;
+  long long E[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int a = e == 0 ? 1 : (e == 1 ? 2 : 0);
+    const int b = e == 0 ? 2 : (e == 1 ? 0 : 1);
+    const int Xa = r.X[a], Ya = r.Y[a];
+    const long long dx = (long long)(r.X[b] - Xa), dy = (long long)(r.Y[b] - Ya);
+    long long v = dx * (Py - Ya) - dy * (Px - Xa);
+    v = sg > 0 ? v : -v;
+    E[e] = v;
+    if (!((v > 0) || (v == 0 && ((flags >> e) & 1)))) return ~0ull;
+  }
+  const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(__ll2float_rn(E[0]), r.z[0]),
+                                                __fmul_rn(__ll2float_rn(E[1]), r.z[1])),
+                                      __fmul_rn(__ll2float_rn(E[2]), r.z[2])),
+                            r.a2f);
+  return depth_key(z, r.tri);
+}
+
+__device__ __forceinline__ float key_depth(uint64_t key) {
+  const uint32_t k = (uint32_t)(key >> 32);
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+constexpr int kSmallArea = 64;   // bbox-in-tile pixels up to which one thread rasterises the triangle
+
+// One 256-thread CTA per 16x16 tile.  The tile's triangle list is read 256
+// records at a time, one record per thread.  A triangle whose bbox covers at
+// most kSmallArea pixels of the tile is rasterised by its thread, which folds
+// (depth key, triangle) into the pixel's shared-memory minimum; larger ones are
+// queued and tested by every pixel in parallel.  The minimum is order
+// independent, so the result is deterministic.  Each pixel then writes one
+// 16-byte G-buffer texel: id + 1, perspective-correct b0, b1, depth key.
 __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict__ setup,
                                                      const int* __restrict__ offset,
                                                      const int* __restrict__ list, int capacity, int tilesX,
-                                                     int W, int H,
-                                                     const float4* __restrict__ clip,
+                                                     int W, int H, const float4* __restrict__ clip,
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf) {
-  __shared__ TriSetup s[256];
+  __shared__ TriSetup sq[256];
+  __shared__ unsigned long long sbest[256];
+  __shared__ int qn;
   const int tile = blockIdx.x;
   const int ti = tile % tilesX, tj = tile / tilesX;
-  const int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
+  const int tid = threadIdx.x;
+  const int lx = tid & 15, ly = tid >> 4;
   const int i = ti * kTile + lx, j = tj * kTile + ly;
-  const int warp_j0 = tj * kTile + ((threadIdx.x >> 5) << 1);
+  const int ti0 = ti * kTile, tj0 = tj * kTile;
   const long long Px = (long long)i * kSubpix + 128, Py = (long long)j * kSubpix + 128;
   uint64_t best = ~0ull;
-  float bestz = 0.f;
+  sbest[tid] = ~0ull;
   // slots past the list capacity were never written (the fill pass flagged the overflow)
   const int beg = min(offset[tile], capacity), end = min(offset[tile + 1], capacity);
   for (int base = beg; base < end; base += 256) {
-    const int n = min(256, end - base);
+    if (tid == 0) qn = 0;
     __syncthreads();
-    if ((int)threadIdx.x < n) s[threadIdx.x] = setup[list[base + threadIdx.x]];
+    const int k = base + tid;
+    if (k < end) {
+      const TriSetup r = setup[list[k]];
+      const int i0 = max(r.ibox & 0xffff, ti0), i1 = min((int)((unsigned)r.ibox >> 16), ti0 + kTile - 1);
+      const int j0 = max(r.jbox & 0xffff, tj0), j1 = min((int)((unsigned)r.jbox >> 16), tj0 + kTile - 1);
+      if (i0 <= i1 && j0 <= j1) {
+        if ((i1 - i0 + 1) * (j1 - j0 + 1) > kSmallArea) {
+          sq[atomicAdd(&qn, 1)] = r;
+        } else {
+          for (int y = j0; y <= j1; ++y)
+            for (int x = i0; x <= i1; ++x) {
+              const uint64_t key = cover_key(r, (long long)x * kSubpix + 128, (long long)y * kSubpix + 128);
+              if (key != ~0ull) atomicMin(&sbest[(y - tj0) * kTile + (x - ti0)], (unsigned long long)key);
+            }
+        }
+      }
+    }
     __syncthreads();
-    for (int k = 0; k < n; ++k) {
-      const int jb = s[k].jbox;
+    const int n = qn;
+    for (int q = 0; q < n; ++q) {
+      const int jb = sq[q].jbox;
       const int j0 = jb & 0xffff, j1 = (unsigned)jb >> 16;
-      if (j1 < warp_j0 || j0 > warp_j0 + 1) continue;           // warp-uniform row reject
-      const int ib = s[k].ibox;
+      const int ib = sq[q].ibox;
       const int i0 = ib & 0xffff, i1 = (unsigned)ib >> 16;
       if (i < i0 || i > i1 || j < j0 || j > j1) continue;
-      const int flags = s[k].flags;
-      const int sg = (flags & 8) ? -1 : 1;
-      long long E[3];
-      bool inside = true;
-#pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        const int a = e == 0 ? 1 : (e == 1 ? 2 : 0);
-        const int b = e == 0 ? 2 : (e == 1 ? 0 : 1);
-        const int Xa = s[k].X[a], Ya = s[k].Y[a];
-        const long long dx = (long long)(s[k].X[b] - Xa), dy = (long long)(s[k].Y[b] - Ya);
-        long long v = dx * (Py - Ya) - dy * (Px - Xa);
-        v = sg > 0 ? v : -v;
-        E[e] = v;
-        inside &= (v > 0) || (v == 0 && ((flags >> e) & 1));
-      }
-      if (!inside) continue;
-      float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(__ll2float_rn(E[0]), s[k].z[0]),
-                                              __fmul_rn(__ll2float_rn(E[1]), s[k].z[1])),
-                                    __fmul_rn(__ll2float_rn(E[2]), s[k].z[2])),
-                          s[k].a2f);
-      uint64_t key = depth_key(z, s[k].tri);
-      if (key < best) { best = key; bestz = z; }
+      const uint64_t key = cover_key(sq[q], Px, Py);
+      if (key < best) best = key;
     }
+    __syncthreads();
   }
+  __syncthreads();
+  const uint64_t sb = sbest[tid];
+  if (sb < best) best = sb;
   if (i >= W || j >= H) return;
   float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
   if (best != ~0ull) {
-    int t = (int)(best & 0xffffffffu);
-    float4 c0 = clip[tris[3 * t]], c1 = clip[tris[3 * t + 1]], c2 = clip[tris[3 * t + 2]];
-    Bary r = bary_at(c0, c1, c2, pix_ndc_x(i, W), pix_ndc_y(j, H));
-    out = make_float4(__int_as_float(t + 1), r.b[0], r.b[1], bestz);
+    const int t = (int)(best & 0xffffffffu);
+    const float4 c0 = clip[tris[3 * t]], c1 = clip[tris[3 * t + 1]], c2 = clip[tris[3 * t + 2]];
+    const Bary r = bary_at(c0, c1, c2, pix_ndc_x(i, W), pix_ndc_y(j, H));
+    out = make_float4(__int_as_float(t + 1), r.b[0], r.b[1], key_depth(best));
   }
   gbuf[(size_t)j * W + i] = out;
 }
