@@ -402,15 +402,14 @@ __device__ __forceinline__ float key_depth(uint64_t key) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-constexpr int kSmallArea = 64;   // bbox-in-tile pixels up to which one thread rasterises the triangle
-
 // One 256-thread CTA per 16x16 tile.  The tile's triangle list is read 256
-// records at a time, one record per thread.  A triangle whose bbox covers at
-// most kSmallArea pixels of the tile is rasterised by its thread, which folds
-// (depth key, triangle) into the pixel's shared-memory minimum; larger ones are
-// queued and tested by every pixel in parallel.  The minimum is order
-// independent, so the result is deterministic.  Each pixel then writes one
-// 16-byte G-buffer texel: id + 1, perspective-correct b0, b1, depth key.
+// records at a time.  Every record contributes its bbox-in-tile pixels as work
+// items; a block prefix sum turns them into one flat list that all threads
+// stride over (balanced whatever the triangle sizes), and each covered pixel
+// centre folds (depth key, triangle) into the pixel's shared-memory 64-bit
+// minimum.  The minimum is order independent, so the result is deterministic.
+// Each pixel then writes one 16-byte G-buffer texel: id + 1,
+// perspective-correct b0, b1, depth key.
 __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict__ setup,
                                                      const int* __restrict__ offset,
                                                      const int* __restrict__ list, int capacity, int tilesX,
@@ -418,54 +417,75 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf) {
   __shared__ TriSetup sq[256];
   __shared__ unsigned long long sbest[256];
-  __shared__ int qn;
+  __shared__ int spre[257];          // exclusive prefix of the work items per record
+  __shared__ int sbox[256];          // bbox in tile: x0 | x1 << 4 | y0 << 8 | y1 << 12 (tile-local)
+  __shared__ int swarp[8];
   const int tile = blockIdx.x;
   const int ti = tile % tilesX, tj = tile / tilesX;
-  const int tid = threadIdx.x;
-  const int lx = tid & 15, ly = tid >> 4;
-  const int i = ti * kTile + lx, j = tj * kTile + ly;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ti0 = ti * kTile, tj0 = tj * kTile;
-  const long long Px = (long long)i * kSubpix + 128, Py = (long long)j * kSubpix + 128;
-  uint64_t best = ~0ull;
   sbest[tid] = ~0ull;
   // slots past the list capacity were never written (the fill pass flagged the overflow)
   const int beg = min(offset[tile], capacity), end = min(offset[tile + 1], capacity);
   for (int base = beg; base < end; base += 256) {
-    if (tid == 0) qn = 0;
-    __syncthreads();
     const int k = base + tid;
+    int area = 0, box = 0;
     if (k < end) {
       const TriSetup r = setup[list[k]];
       const int i0 = max(r.ibox & 0xffff, ti0), i1 = min((int)((unsigned)r.ibox >> 16), ti0 + kTile - 1);
       const int j0 = max(r.jbox & 0xffff, tj0), j1 = min((int)((unsigned)r.jbox >> 16), tj0 + kTile - 1);
       if (i0 <= i1 && j0 <= j1) {
-        if ((i1 - i0 + 1) * (j1 - j0 + 1) > kSmallArea) {
-          sq[atomicAdd(&qn, 1)] = r;
-        } else {
-          for (int y = j0; y <= j1; ++y)
-            for (int x = i0; x <= i1; ++x) {
-              const uint64_t key = cover_key(r, (long long)x * kSubpix + 128, (long long)y * kSubpix + 128);
-              if (key != ~0ull) atomicMin(&sbest[(y - tj0) * kTile + (x - ti0)], (unsigned long long)key);
-            }
-        }
+        area = (i1 - i0 + 1) * (j1 - j0 + 1);
+        box = (i0 - ti0) | ((i1 - ti0) << 4) | ((j0 - tj0) << 8) | ((j1 - tj0) << 12);
       }
+      sq[tid] = r;
+    }
+    sbox[tid] = box;
+    // block exclusive scan of the areas
+    int incl = area;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) swarp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const int w = lane < 8 ? swarp[lane] : 0;
+      int wi = w;
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, wi, o);
+        if (lane >= o) wi += v;
+      }
+      if (lane < 8) swarp[lane] = wi - w;
+      if (lane == 7) spre[256] = wi;
     }
     __syncthreads();
-    const int n = qn;
-    for (int q = 0; q < n; ++q) {
-      const int jb = sq[q].jbox;
-      const int j0 = jb & 0xffff, j1 = (unsigned)jb >> 16;
-      const int ib = sq[q].ibox;
-      const int i0 = ib & 0xffff, i1 = (unsigned)ib >> 16;
-      if (i < i0 || i > i1 || j < j0 || j > j1) continue;
-      const uint64_t key = cover_key(sq[q], Px, Py);
-      if (key < best) best = key;
+    spre[tid] = swarp[warp] + incl - area;
+    __syncthreads();
+    const int total = spre[256];
+    int rec = 0;
+    for (int w = tid; w < total; w += 256) {
+      // record owning work item w: last rec with spre[rec] <= w (records only move forward)
+      int lo = rec, hi = 255;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (spre[mid] <= w) lo = mid; else hi = mid - 1;
+      }
+      rec = lo;
+      const int b = sbox[rec];
+      const int x0 = b & 15, x1 = (b >> 4) & 15, y0 = (b >> 8) & 15;
+      const int q = w - spre[rec], wd = x1 - x0 + 1;
+      const int x = x0 + q % wd, y = y0 + q / wd;
+      const uint64_t key = cover_key(sq[rec], (long long)(ti0 + x) * kSubpix + 128,
+                                     (long long)(tj0 + y) * kSubpix + 128);
+      if (key != ~0ull) atomicMin(&sbest[y * kTile + x], (unsigned long long)key);
     }
     __syncthreads();
   }
-  __syncthreads();
-  const uint64_t sb = sbest[tid];
-  if (sb < best) best = sb;
+  const int i = ti0 + (tid & 15), j = tj0 + (tid >> 4);
+  const uint64_t best = sbest[tid];
   if (i >= W || j >= H) return;
   float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
   if (best != ~0ull) {
