@@ -87,9 +87,14 @@ def stage_bytes(sc) -> dict:
         "final_antialias": WH * (16 + 16 + 16),
         "bwd_clear": 8 * texels + views * 16 * V + 4 * L * V + 24 * V,
         "bwd_final_antialias": WH * (16 + 16 + 16 + 16),
-        "bwd_shade": WH * (16 + 16) + 16 * texels + 40 * V,
+        # per pixel: G-buffer 16 + dL/dcolour 16 in, pgrad 32 out; texel gradient scatter 8 per texel
+        "bwd_shade": WH * (16 + 16 + 32) + 8 * texels + 40 * V,
+        "bwd_shade_scatter": WH * (16 + 32) + 40 * V,
         "bwd_filter": texels * 2 * (8 + 8),
-        "bwd_sm": texels * (16 + 8 + 8) + 20 * V * L,
+        # G-buffer 16 + f 8 + dL/df~ 8 in, dL/df 4 out
+        "bwd_sm_antialias": texels * (16 + 8 + 8 + 4),
+        # G-buffer 16 + dL/df 4 in, vertex gradients
+        "bwd_sm_interp": texels * (16 + 4) + 20 * V * L,
         "bwd_vertex": views * 16 * V + 4 * L * V + 12 * V + 24 * V + 12 * T,
     }
 

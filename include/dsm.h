@@ -166,7 +166,8 @@ const char* dsm_last_error(dsm_ctx* ctx);
  *  6 snapped vertices of view index: int32 X, Y (24.8 fixed point), float ndc z,
  *    int32 valid; 16 B per vertex
  *  7 dL/d(m1, m2) texel gradients (light), float2
- *  8 dL/d clip coordinates of view index, float4 per vertex
+ *  8 dL/d clip coordinates of view index, float4 per vertex (light views: the
+ *    z slot holds dL/d vertex depth d, since clip z carries no gradient there)
  *  9 dL/d(f~, (f^2)~) (light), float2
  * 10 dL/d camera colour before the final antialiasing, float4 per pixel
  * bytes must equal the buffer size; returns DSM_ERR_INVALID_ARG otherwise. */

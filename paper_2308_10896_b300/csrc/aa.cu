@@ -248,39 +248,37 @@ __global__ void sm_aa_adjoint_kernel(AAArgs a, const float2* __restrict__ fmap, 
 // in registers, and the next row's texel data are fetched one row ahead.
 constexpr int kStrip = 16;
 
+// Scatter of 12 per-triangle values: for each vertex (dL/dclip_x, dL/dclip_y,
+// dL/dd, dL/dclip_w).  A light view's barycentrics never depend on clip z, so
+// the z slot of the clip gradient carries the vertex-depth gradient instead.
 struct SmScatter {
   const int* tris;
   float4* gclip;
-  float* gdepth;
   const int* big;        // big-triangle index per triangle (-1: scatter onto the vertices)
-  float* big_acc;        // kMaxBig x kBigSlots x 15
+  float* big_acc;        // kMaxBig x kBigSlots x kBigStrideSm
   int slot;
-  __device__ __forceinline__ void operator()(int t, const float (&c)[15]) const {
+  __device__ __forceinline__ void operator()(int t, const float (&c)[12], int lane) const {
     const int b = big[t];
     if (b >= 0) {
-      float* d = big_acc + ((size_t)b * kBigSlots + slot) * kBigStrideSm;
-      for (int k = 0; k < 15; ++k) atomicAdd(&d[k], c[k]);
+      float* d = big_acc + ((size_t)b * kBigSlots + ((slot + lane) & (kBigSlots - 1))) * kBigStrideSm;
+      for (int k = 0; k < 12; ++k) atomicAdd(&d[k], c[k]);
       return;
     }
-    for (int k = 0; k < 3; ++k) {
-      const int v = tris[3 * t + k];
-      atomicAdd(&gdepth[v], c[k]);
-      atomic_add4(&gclip[v], make_float4(c[3 + 4 * k], c[4 + 4 * k], c[5 + 4 * k], c[6 + 4 * k]));
-    }
+    for (int k = 0; k < 3; ++k)
+      atomic_add4(&gclip[tris[3 * t + k]], make_float4(c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]));
   }
 };
 
 __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const float* __restrict__ gf_map,
                                                                 const float* __restrict__ depth,
                                                                 float4* __restrict__ gclip,
-                                                                float* __restrict__ gdepth,
                                                                 const int* __restrict__ big,
                                                                 float* __restrict__ big_acc) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kStrip;
   const bool col_ok = i < a.W;
-  SmScatter sc{a.tris, gclip, gdepth, big, big_acc, scatter_slot(kBigSlots)};
-  RunAcc<15> run;
+  SmScatter sc{a.tris, gclip, big, big_acc, scatter_slot(kBigSlots)};
+  RunAcc<12> run;
   run_reset(run);
   int ct = -1;                      // triangle whose vertex data are cached
   float4 cc[3];
@@ -300,9 +298,9 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
       g_next = a.gbuf[(size_t)(j + 1) * a.W + i];
       gf_next = gf_map[(size_t)(j + 1) * a.W + i];
     }
-    float c[15];
+    float c[12];
 #pragma unroll
-    for (int k = 0; k < 15; ++k) c[k] = 0.f;
+    for (int k = 0; k < 12; ++k) c[k] = 0.f;
     int t = -1;
     const int id = gid(g);
     if (col_ok && j < a.H && id && gf != 0.f) {
@@ -319,14 +317,11 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
       const Bary r = bary_at(cc[0], cc[1], cc[2], px, py);
       const float b[3] = {g.y, g.z, 1.f - g.y - g.z};
       float gb[3];
-      for (int k = 0; k < 3; ++k) {
-        c[k] = b[k] * gf;
-        gb[k] = cd[k] * gf;
-      }
+      for (int k = 0; k < 3; ++k) gb[k] = cd[k] * gf;
       float4 gcv[3];
       bary_backward(r, gb, px, py, gcv);
       for (int k = 0; k < 3; ++k) {
-        c[3 + 4 * k] = gcv[k].x; c[4 + 4 * k] = gcv[k].y; c[5 + 4 * k] = gcv[k].z; c[6 + 4 * k] = gcv[k].w;
+        c[4 * k] = gcv[k].x; c[4 * k + 1] = gcv[k].y; c[4 * k + 2] = b[k] * gf; c[4 * k + 3] = gcv[k].w;
       }
     }
     run_add(run, t, c, sc);
@@ -335,26 +330,22 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
 }
 
 // Sum the kBigSlots copies of each big triangle and scatter the result onto its
-// vertex depths and light-space clip coordinates.
+// vertices' light-space clip gradients (z slot: vertex depth).
 __global__ void sm_big_resolve_kernel(const int* __restrict__ tris, const int* __restrict__ big_tri,
                                       const DevStatus* __restrict__ status, int view,
-                                      const float* __restrict__ big_acc, float4* __restrict__ gclip,
-                                      float* __restrict__ gdepth) {
+                                      const float* __restrict__ big_acc, float4* __restrict__ gclip) {
   const int b = blockIdx.x;
   if (b >= min(status->big_count[view], kMaxBig)) return;
-  __shared__ float sum[15];
+  __shared__ float sum[12];
   const int k = threadIdx.x;
-  if (k < 15) {
+  if (k < 12) {
     float acc = 0.f;
     for (int q = 0; q < kBigSlots; ++q) acc += big_acc[((size_t)b * kBigSlots + q) * kBigStrideSm + k];
     sum[k] = acc;
   }
   __syncthreads();
-  if (k < 3) {
-    const int v = tris[3 * big_tri[b] + k];
-    atomicAdd(&gdepth[v], sum[k]);
-    atomic_add4(&gclip[v], make_float4(sum[3 + 4 * k], sum[4 + 4 * k], sum[5 + 4 * k], sum[6 + 4 * k]));
-  }
+  if (k < 3)
+    atomic_add4(&gclip[tris[3 * big_tri[b] + k]], make_float4(sum[4 * k], sum[4 * k + 1], sum[4 * k + 2], sum[4 * k + 3]));
 }
 
 // ------------------------------------------------------------------ launchers
@@ -376,17 +367,22 @@ void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, cudaS
   count_launches(1);
   aa_forward_kernel<float4><<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, out);
 }
-void launch_sm_backward(const AAArgs& a, const float2* fmap, const float2* gft, const float* depth, float4* gclip,
-                        float* gdepth, float* gf_scratch, const BigArgs& big, int aa, cudaStream_t st) {
+void launch_sm_aa_adjoint(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
+                          int aa, cudaStream_t st) {
   dim3 b(32, 8);
   count_launches(1);
-  sm_aa_adjoint_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, fmap, gft, gclip, gf_scratch, aa);
-  dim3 g((a.W + 31) / 32, (a.H + 8 * kStrip - 1) / (8 * kStrip));
-  count_launches(1);
-  sm_interp_adjoint_kernel<<<g, b, 0, st>>>(a, gf_scratch, depth, gclip, gdepth, big.index, big.acc);
-  count_launches(1);
-  sm_big_resolve_kernel<<<kMaxBig, 32, 0, st>>>(a.tris, big.tri, big.status, big.view, big.acc, gclip, gdepth);
+  sm_aa_adjoint_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, fmap, gft, gclip, gf_out, aa);
 }
+
+void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* depth, float4* gclip,
+                              const BigArgs& big, cudaStream_t st) {
+  dim3 b(32, 8), g((a.W + 31) / 32, (a.H + 8 * kStrip - 1) / (8 * kStrip));
+  count_launches(1);
+  sm_interp_adjoint_kernel<<<g, b, 0, st>>>(a, gf, depth, gclip, big.index, big.acc);
+  count_launches(1);
+  sm_big_resolve_kernel<<<kMaxBig, 32, 0, st>>>(a.tris, big.tri, big.status, big.view, big.acc, gclip);
+}
+
 void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
                          int aa, cudaStream_t st) {
   dim3 b(32, 8);

@@ -163,8 +163,9 @@ __device__ __forceinline__ void atomic_add2(float2* p, float2 v) {
 // Warp-uniform run accumulator for per-triangle gradient scatters.  While all
 // 32 lanes of a warp add to the same triangle the sums stay in registers; a run
 // is flushed by a butterfly reduction and one set of atomics from lane 0.
-// Lanes of mixed warps scatter their own contribution directly.  Every lane of
-// the warp must call run_add / run_flush together.
+// Lanes of mixed warps scatter their own contribution directly (the flush gets
+// the lane id so that slot copies can be spread).  Every lane of the warp must
+// call run_add / run_flush together.
 template <int N>
 struct RunAcc {
   float v[N];
@@ -188,7 +189,7 @@ __device__ __forceinline__ void run_flush(RunAcc<N>& a, Flush& flush) {
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
     a.v[k] = x;
   }
-  if ((threadIdx.x & 31) == 0) flush(a.tri, a.v);
+  if ((threadIdx.x & 31) == 0) flush(a.tri, a.v, 0);
   run_reset(a);
 }
 
@@ -207,7 +208,7 @@ __device__ __forceinline__ void run_add(RunAcc<N>& a, int t, const float (&c)[N]
     for (int k = 0; k < N; ++k) a.v[k] = c[k];
     return;
   }
-  if (t >= 0) flush(t, c);
+  if (t >= 0) flush(t, c, threadIdx.x & 31);   // lane offset spreads big-triangle slot copies
 }
 
 }  // namespace dsm

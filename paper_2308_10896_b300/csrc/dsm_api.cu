@@ -16,10 +16,12 @@ std::atomic<unsigned long long> g_kernel_launches{0};
 
 static const char* const kStageNames[] = {
     "setup", "bin_fill", "raster", "sm_interp", "sm_antialias", "filter", "shade", "final_antialias",
-    "bwd_clear", "bwd_final_antialias", "bwd_shade", "bwd_filter", "bwd_sm", "bwd_vertex"};
+    "bwd_clear", "bwd_final_antialias", "bwd_shade", "bwd_shade_scatter", "bwd_filter", "bwd_sm_antialias",
+    "bwd_sm_interp", "bwd_vertex"};
 constexpr int kStages = (int)(sizeof(kStageNames) / sizeof(kStageNames[0]));
 enum Stage { ST_SETUP, ST_BIN_FILL, ST_RASTER, ST_SM_INTERP, ST_SM_AA, ST_FILTER, ST_SHADE, ST_FINAL_AA,
-             ST_BWD_CLEAR, ST_BWD_FINAL_AA, ST_BWD_SHADE, ST_BWD_FILTER, ST_BWD_SM, ST_BWD_VERTEX };
+             ST_BWD_CLEAR, ST_BWD_FINAL_AA, ST_BWD_SHADE, ST_BWD_SHADE_SCATTER, ST_BWD_FILTER, ST_BWD_SM_AA,
+             ST_BWD_SM_INTERP, ST_BWD_VERTEX };
 
 void build_adjacency(const int32_t* tris, int T, std::vector<int32_t>& adj);
 void build_vertex_faces(const int32_t* tris, int T, int V, std::vector<int32_t>& off, std::vector<int32_t>& lst);
@@ -47,7 +49,7 @@ struct Buf {
 
 struct ViewBufs {
   int W = 0, H = 0, tilesX = 0, tilesY = 0;
-  Buf clip, snap, depth, setup, orient, sil, count, offset, list, gbuf, gclip, gdepth;
+  Buf clip, snap, depth, setup, orient, sil, count, offset, list, gbuf, gclip;
   Buf big_index, big_tri, big_acc;
   int list_cap = 0;
 };
@@ -184,7 +186,7 @@ void dsm_destroy(dsm_ctx* ctx) {
   for (Buf* b : bufs) b->release();
   for (auto& v : ctx->view) {
     Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
-                 &v.gbuf, &v.gclip, &v.gdepth, &v.big_index, &v.big_tri, &v.big_acc};
+                 &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc};
     for (Buf* b : vb) b->release();
   }
   for (auto& l : ctx->light) {
@@ -279,7 +281,6 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   DSM_CHECK(v.big_acc.ensure((size_t)kMaxBig * kBigSlots * (is_light ? kBigStrideSm : kBigStrideCam) * 4));
   if (is_light) {
     DSM_CHECK(v.depth.ensure(Vn * 4));
-    DSM_CHECK(v.gdepth.ensure(Vn * 4));
   }
   if (v.list_cap == 0) {
     const size_t cap = 2 * Tn + 2 * tiles + 1024;
@@ -501,7 +502,6 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   DSM_CHECK(cudaMemsetAsync(ctx->gdirect.p, 0, sizeof(float) * 3 * DSM_MAX_LIGHTS, st));
   for (int w = 0; w <= L; ++w) {
     DSM_CHECK(cudaMemsetAsync(ctx->view[w].gclip.p, 0, sizeof(float4) * V, st));
-    if (w < L) DSM_CHECK(cudaMemsetAsync(ctx->view[w].gdepth.p, 0, sizeof(float) * V, st));
   }
   for (int l = 0; l < L; ++l)
     DSM_CHECK(cudaMemsetAsync(ctx->light[l].gm.p, 0, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2), st));
@@ -543,6 +543,10 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   {
     StageTimer t(ctx, ST_BWD_SHADE, st);
     launch_shade_backward(sa, ga, st);
+  }
+  {
+    StageTimer t(ctx, ST_BWD_SHADE_SCATTER, st);
+    launch_shade_scatter(sa, ga, st);
     launch_shade_big_resolve(sa, ga, cv.big_tri.as<int>(), ctx->status.as<DevStatus>(), L, st);
   }
 
@@ -554,22 +558,29 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
       launch_filter_adjoint(lb.gm.as<float2>(), lb.tmp.as<float2>(), lb.gft.as<float2>(), ctx->view[l].W, lb.fa, st);
     }
   }
-  StageTimer t_sm(ctx, ST_BWD_SM, st);
+  {
+    StageTimer t(ctx, ST_BWD_SM_AA, st);
+    for (int l = 0; l < L; ++l) {
+      ViewBufs& v = ctx->view[l];
+      LightBufs& lb = ctx->light[l];
+      AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(), v.clip.as<float4>()};
+      launch_sm_aa_adjoint(aa, lb.fmap.as<float2>(), lb.gft.as<float2>(), v.gclip.as<float4>(), lb.tmp.as<float>(),
+                           ctx->params.aa_shadow, st);
+    }
+  }
+  StageTimer t_sm(ctx, ST_BWD_SM_INTERP, st);
   for (int l = 0; l < L; ++l) {
     ViewBufs& v = ctx->view[l];
     LightBufs& lb = ctx->light[l];
     AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(), v.clip.as<float4>()};
     BigArgs big{v.big_index.as<int>(), v.big_tri.as<int>(), v.big_acc.as<float>(), ctx->status.as<DevStatus>(), l};
-    launch_sm_backward(aa, lb.fmap.as<float2>(), lb.gft.as<float2>(), v.depth.as<float>(), v.gclip.as<float4>(),
-                       v.gdepth.as<float>(), lb.tmp.as<float>(), big, ctx->params.aa_shadow, st);
+    launch_sm_interp_adjoint(aa, lb.tmp.as<float>(), v.depth.as<float>(), v.gclip.as<float4>(), big, st);
   }
-
   t_sm.stop();
   // ---- vertices, normals, lights
   StageTimer t_vert(ctx, ST_BWD_VERTEX, st);
   VertGradPtrs gp{};
   for (int w = 0; w <= L; ++w) gp.gclip[w] = ctx->view[w].gclip.as<float4>();
-  for (int l = 0; l < L; ++l) gp.gdepth[l] = ctx->view[l].gdepth.as<float>();
   launch_vertex_backward(mesh.verts, V, ctx->viewM.as<float>(), L + 1, L, gp, dL_dverts, ctx->red.as<float>(),
                          red_stride, st);
   launch_normals_backward(mesh.verts, V, mesh.tris, T, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),

@@ -70,8 +70,7 @@ struct ShadeGradArgs {
 };
 
 struct VertGradPtrs {
-  const float4* gclip[DSM_MAX_LIGHTS + 1];   // per view (lights, then camera)
-  const float* gdepth[DSM_MAX_LIGHTS];       // per light
+  const float4* gclip[DSM_MAX_LIGHTS + 1];   // per view (lights, then camera); lights: z = dL/d vertex depth
 };
 
 // Big-triangle bookkeeping of one view (see kBigTiles).
@@ -110,8 +109,10 @@ void launch_raster(const TriSetup* setup, const int* offset, const int* list, in
 void launch_sm_interp(const float4* gbuf, int R, const int* tris, const float* depth, float2* fmap, cudaStream_t st);
 void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, cudaStream_t st);
 void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, cudaStream_t st);
-void launch_sm_backward(const AAArgs& a, const float2* fmap, const float2* gft, const float* depth, float4* gclip,
-                        float* gdepth, float* gf_scratch, const BigArgs& big, int aa, cudaStream_t st);
+void launch_sm_aa_adjoint(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
+                          int aa, cudaStream_t st);
+void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* depth, float4* gclip,
+                              const BigArgs& big, cudaStream_t st);
 void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
                          int aa, cudaStream_t st);
 
@@ -129,6 +130,7 @@ void launch_normals_backward(const float* verts, int V, const int* tris, int T, 
                              cudaStream_t st);
 void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st);
 void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);
+void launch_shade_scatter(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);
 void launch_vertex_backward(const float* verts, int V, const float* viewM, int n_views, int n_lights,
                             const VertGradPtrs& gp, float* dverts, float* red, int red_stride, cudaStream_t st);
 void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const int* big_tri,

@@ -7,111 +7,84 @@
 namespace dsm {
 
 // ------------------------------------------------------------------ light camera
-// Float64 value with its derivative w.r.t. the 6 light parameters
-// (pos xyz, dir xyz).  The value part uses explicitly rounded operations so
-// that the float32 light matrix is reproducible bit for bit.
-struct D6 {
-  double v;
-  double d[6];
+// Float64 value with its derivative w.r.t. one light parameter.  The value
+// part uses explicitly rounded operations so that the float32 light matrix is
+// reproducible bit for bit; the derivative is ordinary float64 arithmetic.
+struct D1 {
+  double v, d;
 };
-__device__ __forceinline__ D6 dc(double v) {
-  D6 r; r.v = v;
-#pragma unroll
-  for (int i = 0; i < 6; ++i) r.d[i] = 0.0;
-  return r;
+__device__ __forceinline__ D1 dc(double v) { return {v, 0.0}; }
+__device__ __forceinline__ D1 operator+(const D1& a, const D1& b) { return {__dadd_rn(a.v, b.v), a.d + b.d}; }
+__device__ __forceinline__ D1 operator-(const D1& a, const D1& b) { return {__dsub_rn(a.v, b.v), a.d - b.d}; }
+__device__ __forceinline__ D1 operator-(const D1& a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ D1 operator*(const D1& a, const D1& b) { return {__dmul_rn(a.v, b.v), a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ D1 operator/(const D1& a, const D1& b) {
+  const double q = __ddiv_rn(a.v, b.v);
+  return {q, (a.d - q * b.d) / b.v};
 }
-__device__ __forceinline__ D6 dvar(double v, int k) { D6 r = dc(v); r.d[k] = 1.0; return r; }
-__device__ __forceinline__ D6 operator+(const D6& a, const D6& b) {
-  D6 r; r.v = __dadd_rn(a.v, b.v);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) r.d[i] = a.d[i] + b.d[i];
-  return r;
+__device__ __forceinline__ D1 dsqrt(const D1& a) {
+  const double r = __dsqrt_rn(a.v);
+  return {r, a.d / (2.0 * r)};
 }
-__device__ __forceinline__ D6 operator-(const D6& a, const D6& b) {
-  D6 r; r.v = __dsub_rn(a.v, b.v);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) r.d[i] = a.d[i] - b.d[i];
-  return r;
-}
-__device__ __forceinline__ D6 operator-(const D6& a) {
-  D6 r; r.v = -a.v;
-#pragma unroll
-  for (int i = 0; i < 6; ++i) r.d[i] = -a.d[i];
-  return r;
-}
-__device__ __forceinline__ D6 operator*(const D6& a, const D6& b) {
-  D6 r; r.v = __dmul_rn(a.v, b.v);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
-  return r;
-}
-__device__ __forceinline__ D6 operator/(const D6& a, const D6& b) {
-  D6 r; r.v = __ddiv_rn(a.v, b.v);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
-  return r;
-}
-__device__ __forceinline__ D6 dsqrt(const D6& a) {
-  D6 r; r.v = __dsqrt_rn(a.v);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
-  return r;
-}
-struct V3 { D6 x, y, z; };
-__device__ __forceinline__ D6 dot3(const V3& a, const V3& b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+struct V3 { D1 x, y, z; };
+__device__ __forceinline__ D1 dot3(const V3& a, const V3& b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
 __device__ __forceinline__ V3 cross3(const V3& a, const V3& b) {
   return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 __device__ __forceinline__ V3 normalize3(const V3& a) {
-  D6 n = dsqrt((a.x * a.x + a.y * a.y) + a.z * a.z);
+  D1 n = dsqrt((a.x * a.x + a.y * a.y) + a.z * a.z);
   return {a.x / n, a.y / n, a.z / n};
 }
 
-// One thread per light: Q (clip rows 0-3, depth row 4) in float64, rounded to
-// float32, and J = dQ/d(pos, dir) (supplementary Sec. A light cameras).
+// Thread (light l, parameter j) computes Q (clip rows 0-3, depth row 4) in
+// float64 together with dQ/d theta_j (theta = pos xyz, dir xyz); thread j = 0
+// also writes the float32 Q (supplementary Sec. A light cameras).
 __global__ void light_setup_kernel(const float* __restrict__ params, LightSetupArgs a, LightDev* out,
                                    float* viewM) {
-  int l = threadIdx.x;
+  const int l = threadIdx.x / 6, jd = threadIdx.x % 6;
   if (l >= a.n) return;
   const LightConst& L = a.c[l];
-  V3 pos = {dvar(params[l * 6 + 0], 0), dvar(params[l * 6 + 1], 1), dvar(params[l * 6 + 2], 2)};
-  V3 dir = {dvar(params[l * 6 + 3], 3), dvar(params[l * 6 + 4], 4), dvar(params[l * 6 + 5], 5)};
-  V3 f = normalize3(dir);
-  V3 up = fabs(f.y.v) > 0.99 ? V3{dc(0.0), dc(0.0), dc(1.0)} : V3{dc(0.0), dc(1.0), dc(0.0)};
-  V3 r = normalize3(cross3(f, up));
-  V3 u = cross3(r, f);
-  D6 nearp = dc(L.near_plane), farp = dc(L.far_plane);
+  D1 th[6];
+  for (int k = 0; k < 6; ++k) th[k] = {(double)params[l * 6 + k], k == jd ? 1.0 : 0.0};
+  const V3 pos = {th[0], th[1], th[2]};
+  const V3 dir = {th[3], th[4], th[5]};
+  const V3 f = normalize3(dir);
+  const V3 up = fabs(f.y.v) > 0.99 ? V3{dc(0.0), dc(0.0), dc(1.0)} : V3{dc(0.0), dc(1.0), dc(0.0)};
+  const V3 r = normalize3(cross3(f, up));
+  const V3 u = cross3(r, f);
+  const D1 nearp = dc(L.near_plane), farp = dc(L.far_plane);
   V3 e;
   if (L.type == 0) {
-    D6 md = dc(-(double)L.dist);
+    const D1 md = dc(-(double)L.dist);
     e = {md * f.x, md * f.y, md * f.z};
   } else {
     e = pos;
   }
-  D6 fe = dot3(f, e);
-  D6 rng = farp - nearp;
-  D6 Q[20];
+  const D1 fe = dot3(f, e);
+  const D1 rng = farp - nearp;
+  D1 Q[20];
   Q[16] = f.x / rng; Q[17] = f.y / rng; Q[18] = f.z / rng; Q[19] = (-fe - nearp) / rng;
   if (L.type == 0) {
-    D6 h = dc(L.ortho_half);
+    const D1 h = dc(L.ortho_half);
     Q[0] = r.x / h; Q[1] = r.y / h; Q[2] = r.z / h; Q[3] = (-dot3(r, e)) / h;
     Q[4] = u.x / h; Q[5] = u.y / h; Q[6] = u.z / h; Q[7] = (-dot3(u, e)) / h;
     Q[8] = Q[16]; Q[9] = Q[17]; Q[10] = Q[18]; Q[11] = Q[19];
     Q[12] = dc(0.0); Q[13] = dc(0.0); Q[14] = dc(0.0); Q[15] = dc(1.0);
   } else {
-    D6 c = dc(L.persp_c);
-    D6 A = farp / rng;
-    D6 B = (-(farp * nearp)) / rng;
+    const D1 c = dc(L.persp_c);
+    const D1 A = farp / rng;
+    const D1 B = (-(farp * nearp)) / rng;
     Q[0] = c * r.x; Q[1] = c * r.y; Q[2] = c * r.z; Q[3] = -(c * dot3(r, e));
     Q[4] = c * u.x; Q[5] = c * u.y; Q[6] = c * u.z; Q[7] = -(c * dot3(u, e));
     Q[8] = A * f.x; Q[9] = A * f.y; Q[10] = A * f.z; Q[11] = (-(A * fe)) + B;
     Q[12] = f.x; Q[13] = f.y; Q[14] = f.z; Q[15] = -fe;
   }
   LightDev& o = out[l];
+  for (int k = 0; k < 20; ++k) o.J[k * 6 + jd] = (float)Q[k].d;
+  if (jd != 0) return;
   for (int k = 0; k < 20; ++k) {
     o.Q[k] = __double2float_rn(Q[k].v);
     viewM[l * 20 + k] = o.Q[k];
-    for (int j = 0; j < 6; ++j) o.J[k * 6 + j] = (float)Q[k].d[j];
   }
   o.fwd[0] = (float)f.x.v; o.fwd[1] = (float)f.y.v; o.fwd[2] = (float)f.z.v;
   o.dir_norm = (float)sqrt(dir.x.v * dir.x.v + dir.y.v * dir.y.v + dir.z.v * dir.z.v);
@@ -501,7 +474,7 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM,
                         cudaStream_t st) {
   count_launches(1);
-  light_setup_kernel<<<1, 32, 0, st>>>(params, a, out, viewM);
+  light_setup_kernel<<<1, 6 * DSM_MAX_LIGHTS, 0, st>>>(params, a, out, viewM);
 }
 
 void launch_transform(const float* verts, int V, const float* M20, int W, int H, float4* clip, VertSnap* snap,

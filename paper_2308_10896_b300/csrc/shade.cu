@@ -424,10 +424,10 @@ struct CamScatter {
   const int* big;
   float* big_acc;
   int slot;
-  __device__ __forceinline__ void operator()(int t, const float (&c)[30]) const {
+  __device__ __forceinline__ void operator()(int t, const float (&c)[30], int lane) const {
     const int b = big[t];
     if (b >= 0) {
-      float* d = big_acc + ((size_t)b * kBigSlots + slot) * kBigStrideCam;
+      float* d = big_acc + ((size_t)b * kBigSlots + ((slot + lane) & (kBigSlots - 1))) * kBigStrideCam;
       for (int k = 0; k < 30; ++k) atomicAdd(&d[k], c[k]);
       return;
     }
@@ -546,12 +546,14 @@ __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __res
     const float* M = viewM + 20 * w;
     const float4 gc = ok ? gp.gclip[w][v] : make_float4(0.f, 0.f, 0.f, 0.f);
     const bool is_light = w < n_lights;
-    const float gd = (ok && is_light) ? gp.gdepth[w][v] : 0.f;
-    acc.x += M[0] * gc.x + M[4] * gc.y + M[8] * gc.z + M[12] * gc.w + (is_light ? M[16] * gd : 0.f);
-    acc.y += M[1] * gc.x + M[5] * gc.y + M[9] * gc.z + M[13] * gc.w + (is_light ? M[17] * gd : 0.f);
-    acc.z += M[2] * gc.x + M[6] * gc.y + M[10] * gc.z + M[14] * gc.w + (is_light ? M[18] * gd : 0.f);
+    // light views carry dL/d vertex depth in the z slot (clip z has no gradient there)
+    const float gz = is_light ? 0.f : gc.z;
+    const float gd = is_light ? gc.z : 0.f;
+    acc.x += M[0] * gc.x + M[4] * gc.y + M[8] * gz + M[12] * gc.w + (is_light ? M[16] * gd : 0.f);
+    acc.y += M[1] * gc.x + M[5] * gc.y + M[9] * gz + M[13] * gc.w + (is_light ? M[17] * gd : 0.f);
+    acc.z += M[2] * gc.x + M[6] * gc.y + M[10] * gz + M[14] * gc.w + (is_light ? M[18] * gd : 0.f);
     if (is_light) {
-      const float g5[5] = {gc.x, gc.y, gc.z, gc.w, gd};
+      const float g5[5] = {gc.x, gc.y, 0.f, gc.w, gd};
 #pragma unroll
       for (int r = 0; r < 5; ++r)
 #pragma unroll
@@ -643,7 +645,10 @@ void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStrea
   dim3 b(32, 8);
   count_launches(1);
   shade_backward_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, g);
-  dim3 grid((a.W + 31) / 32, (a.H + 8 * kShadeStrip - 1) / (8 * kShadeStrip));
+}
+
+void launch_shade_scatter(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st) {
+  dim3 b(32, 8), grid((a.W + 31) / 32, (a.H + 8 * kShadeStrip - 1) / (8 * kShadeStrip));
   count_launches(1);
   shade_scatter_kernel<<<grid, b, 0, st>>>(a, g);
 }

@@ -1,0 +1,74 @@
+"""Host-side logic of bench.py on CPU: the multi-rank aggregation over a
+world_size-2 gloo group, the algorithmic byte model, and the JSON contract of
+the reference (oracle) arm."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sec, frames = bench.aggregate(1.0 + rank, 10 + rank, world)
+    out.put((rank, sec, frames))
+    bench.barrier(world)
+    dist.destroy_process_group()
+
+
+def test_aggregate_max_time_sum_frames_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = [q.get(timeout=120) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, sec, frames in res:
+        assert sec == 2.0 and frames == 21       # max over ranks, sum of frames
+
+
+def test_stage_bytes_model():
+    sys.path.insert(0, ROOT)
+    import bench
+    import scenes
+    sc = scenes.config1()
+    b = bench.stage_bytes(sc)
+    R2, WH = 256 * 256, 256 * 256
+    assert b["filter"] == R2 * 32 and b["bwd_filter"] == R2 * 32
+    assert b["final_antialias"] == WH * 48
+    assert set(b) >= {"raster", "shade", "bwd_sm_interp", "bwd_sm_antialias", "bwd_shade", "setup"}
+
+
+@pytest.mark.slow
+def test_reference_arm_json_contract():
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "config1", "--steps", "1", "--warmup", "3"], capture_output=True, text=True, env=env,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "config",
+              "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["e2e"]["h2d_bytes_per_step"] == 0 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle"
