@@ -174,11 +174,12 @@ const char* dsm_last_error(dsm_ctx* ctx);
 dsm_status dsm_debug_copy(dsm_ctx* ctx, int32_t what, int32_t index, void* dst, size_t bytes);
 
 /* Per-stage device timing: while enabled, dsm_render and dsm_render_backward
- * record a CUDA event pair on their stream around every stage (stage names:
- * dsm_profile_stage_name).  dsm_profile_read waits for the recorded events,
- * writes the accumulated milliseconds and the number of timed calls of each
- * of the first n stages (ms, calls: host arrays of n entries) and clears the
- * records.  Enabling costs two event records per stage and call. */
+ * run every view on the caller's stream (instead of one internal stream per
+ * view) and record a CUDA event pair around every stage of every view (stage
+ * names: dsm_profile_stage_name).  dsm_profile_read waits for the recorded
+ * events, writes the accumulated milliseconds and the number of timed calls of
+ * each of the first n stages (ms, calls: host arrays of n entries) and clears
+ * the records. */
 dsm_status  dsm_profile_enable(dsm_ctx* ctx, int32_t enable);
 int32_t     dsm_profile_stage_count(void);
 const char* dsm_profile_stage_name(int32_t stage);   /* NULL when out of range */

@@ -83,6 +83,9 @@ struct dsm_ctx {
   dsm_params params{};
   cudaStream_t stream = nullptr;
   uint64_t sized_sig = 0;
+  // internal streams: one per view (lights, then camera), fork/join events
+  cudaStream_t vs[DSM_MAX_LIGHTS + 1] = {};
+  cudaEvent_t ev_fork = nullptr, ev_bfork = nullptr, ev_join[DSM_MAX_LIGHTS + 1] = {};
   // per-stage timing
   bool prof = false;
   struct Rec { int stage; cudaEvent_t a, b; };
@@ -148,6 +151,42 @@ struct StageTimer {
   ~StageTimer() { stop(); }
 };
 
+cudaError_t ensure_streams(dsm_ctx* c) {
+  if (c->ev_fork) return cudaSuccess;
+  cudaError_t e;
+  for (auto& v : c->vs)
+    if ((e = cudaStreamCreateWithFlags(&v, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&c->ev_bfork, cudaEventDisableTiming)) != cudaSuccess) return e;
+  for (auto& ev : c->ev_join)
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+// Stream of view w: its own stream, or the caller's while stage profiling is
+// on (profiling serialises the views so that each stage's events bracket only
+// its own kernels).
+cudaStream_t view_stream(const dsm_ctx* c, int w, cudaStream_t st) { return c->prof ? st : c->vs[w]; }
+
+// All view streams wait for the work enqueued so far on st.
+cudaError_t fork_views(dsm_ctx* c, cudaStream_t st, cudaEvent_t ev, int n_views) {
+  if (c->prof) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(ev, st);
+  for (int w = 0; w < n_views && e == cudaSuccess; ++w) e = cudaStreamWaitEvent(c->vs[w], ev, 0);
+  return e;
+}
+
+// st waits for the work enqueued so far on the first n view streams.
+cudaError_t join_views(dsm_ctx* c, cudaStream_t st, int n_views) {
+  if (c->prof) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  for (int w = 0; w < n_views && e == cudaSuccess; ++w) {
+    e = cudaEventRecord(c->ev_join[w], c->vs[w]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join[w], 0);
+  }
+  return e;
+}
+
 uint64_t mix(uint64_t h, uint64_t v) {
   h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
   return h;
@@ -195,6 +234,10 @@ void dsm_destroy(dsm_ctx* ctx) {
   }
   if (ctx->hstatus) cudaFreeHost(ctx->hstatus);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto v : ctx->vs) if (v) cudaStreamDestroy(v);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_bfork) cudaEventDestroy(ctx->ev_bfork);
+  for (auto e : ctx->ev_join) if (e) cudaEventDestroy(e);
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   delete ctx;
 }
@@ -349,25 +392,31 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
   launch_vertex_normals(mesh->verts, V, mesh->tris, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
                         ctx->vnormal.as<float>(), st);
 
-  // ---- per view: transform, setup, bin count, scan
+  // ---- per view on its own stream: transform, setup, bin count, scan
+  // (the light views and the camera view are independent until shading)
   DevStatus* dstat = ctx->status.as<DevStatus>();
   DSM_CHECK(cudaMemsetAsync(dstat->big_count, 0, sizeof(dstat->big_count), st));
+  t_setup.stop();
+  DSM_CHECK(ensure_streams(ctx));
+  DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, L + 1));
   for (int w = 0; w <= L; ++w) {
     ViewBufs& v = ctx->view[w];
+    cudaStream_t vst = view_stream(ctx, w, st);
     const bool is_light = w < L;
+    StageTimer tw(ctx, ST_SETUP, vst);
     launch_transform(mesh->verts, V, viewM + 20 * w, v.W, v.H, v.clip.as<float4>(), v.snap.as<VertSnap>(),
-                     is_light ? v.depth.as<float>() : nullptr, st);
+                     is_light ? v.depth.as<float>() : nullptr, vst);
     launch_tri_setup(mesh->tris, T, v.snap.as<VertSnap>(), v.W, v.H, v.setup.as<TriSetup>(),
-                     v.orient.as<int8_t>(), ctx->adj.as<int>(), v.sil.as<uint8_t>(), st);
-    DSM_CHECK(cudaMemsetAsync(v.count.p, 0, (size_t)v.tilesX * v.tilesY * 4, st));
+                     v.orient.as<int8_t>(), ctx->adj.as<int>(), v.sil.as<uint8_t>(), vst);
+    DSM_CHECK(cudaMemsetAsync(v.count.p, 0, (size_t)v.tilesX * v.tilesY * 4, vst));
     launch_bin_count(v.setup.as<TriSetup>(), T, v.tilesX, v.count.as<int>(), dstat, w, v.big_index.as<int>(),
-                     v.big_tri.as<int>(), st);
-    launch_scan(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), dstat, w, st);
+                     v.big_tri.as<int>(), vst);
+    launch_scan(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), dstat, w, vst);
   }
   DSM_CHECK(cudaGetLastError());
-  t_setup.stop();
   if (ctx->sized_sig != sig) {
     // first frame of this scene size: read the pair counts once and size the lists
+    DSM_CHECK(join_views(ctx, st, L + 1));
     DSM_CHECK(cudaMemcpyAsync(ctx->hstatus, dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     DSM_CHECK(cudaStreamSynchronize(st));
     for (int w = 0; w <= L; ++w) {
@@ -381,52 +430,46 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
       }
     }
     ctx->sized_sig = sig;
+    DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, L + 1));
   }
-  StageTimer t_fill(ctx, ST_BIN_FILL, st);
+  // ---- per view: bin fill, raster; per light: Alg. 1 (f, f^2 -> antialias -> filter)
   for (int w = 0; w <= L; ++w) {
     ViewBufs& v = ctx->view[w];
-    launch_bin_fill(v.setup.as<TriSetup>(), T, v.tilesX, v.count.as<int>(), v.offset.as<int>(), v.list.as<int>(),
-                    v.list_cap, dstat, w, v.big_index.as<int>(), v.big_tri.as<int>(), st);
-  }
-  t_fill.stop();
-  StageTimer t_raster(ctx, ST_RASTER, st);
-  for (int w = 0; w <= L; ++w) {
-    ViewBufs& v = ctx->view[w];
-    launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY, v.W, v.H,
-                  v.clip.as<float4>(), mesh->tris, v.gbuf.as<float4>(), st);
-  }
-  t_raster.stop();
-
-  // ---- Alg. 1 per light: f, f^2 -> antialias -> filter
-  {
-    StageTimer t(ctx, ST_SM_INTERP, st);
-    for (int l = 0; l < L; ++l) {
-      ViewBufs& v = ctx->view[l];
-      launch_sm_interp(v.gbuf.as<float4>(), v.W, mesh->tris, v.depth.as<float>(), ctx->light[l].fmap.as<float2>(), st);
+    cudaStream_t vst = view_stream(ctx, w, st);
+    {
+      StageTimer t(ctx, ST_BIN_FILL, vst);
+      launch_bin_fill(v.setup.as<TriSetup>(), T, v.tilesX, v.count.as<int>(), v.offset.as<int>(), v.list.as<int>(),
+                      v.list_cap, dstat, w, v.big_index.as<int>(), v.big_tri.as<int>(), vst);
     }
-  }
-  {
-    StageTimer t(ctx, ST_SM_AA, st);
-    for (int l = 0; l < L; ++l) {
-      ViewBufs& v = ctx->view[l];
-      LightBufs& lb = ctx->light[l];
+    {
+      StageTimer t(ctx, ST_RASTER, vst);
+      launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY, v.W,
+                    v.H, v.clip.as<float4>(), mesh->tris, v.gbuf.as<float4>(), vst);
+    }
+    if (w == L) continue;
+    LightBufs& lb = ctx->light[w];
+    {
+      StageTimer t(ctx, ST_SM_INTERP, vst);
+      launch_sm_interp(v.gbuf.as<float4>(), v.W, mesh->tris, v.depth.as<float>(), lb.fmap.as<float2>(), vst);
+    }
+    {
+      StageTimer t(ctx, ST_SM_AA, vst);
       if (params->aa_shadow) {
         AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh->tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(),
                   v.clip.as<float4>()};
-        launch_aa_forward2(aa, lb.fmap.as<float2>(), lb.ftilde.as<float2>(), st);
+        launch_aa_forward2(aa, lb.fmap.as<float2>(), lb.ftilde.as<float2>(), vst);
       } else {
         DSM_CHECK(cudaMemcpyAsync(lb.ftilde.p, lb.fmap.p, (size_t)v.W * v.H * sizeof(float2),
-                                  cudaMemcpyDeviceToDevice, st));
+                                  cudaMemcpyDeviceToDevice, vst));
       }
     }
-  }
-  {
-    StageTimer t(ctx, ST_FILTER, st);
-    for (int l = 0; l < L; ++l) {
-      LightBufs& lb = ctx->light[l];
-      launch_filter(lb.ftilde.as<float2>(), lb.tmp.as<float2>(), lb.mom.as<float2>(), ctx->view[l].W, lb.fa, st);
+    {
+      StageTimer t(ctx, ST_FILTER, vst);
+      launch_filter(lb.ftilde.as<float2>(), lb.tmp.as<float2>(), lb.mom.as<float2>(), v.W, lb.fa, vst);
     }
   }
+  DSM_CHECK(join_views(ctx, st, L + 1));
+  DSM_CHECK(cudaGetLastError());
 
   // ---- camera: shade (Alg. 2 x Lambert) and the final antialiasing
   ViewBufs& cv = ctx->view[L];
@@ -544,39 +587,36 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
     StageTimer t(ctx, ST_BWD_SHADE, st);
     launch_shade_backward(sa, ga, st);
   }
+  // ---- per light on its own stream: G^T, antialiasing adjoint, interpolation
+  // adjoint (they write only that light's buffers), beside the camera scatter
+  DSM_CHECK(ensure_streams(ctx));
+  DSM_CHECK(fork_views(ctx, st, ctx->ev_bfork, L));
+  for (int l = 0; l < L; ++l) {
+    ViewBufs& v = ctx->view[l];
+    LightBufs& lb = ctx->light[l];
+    cudaStream_t vst = view_stream(ctx, l, st);
+    AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(), v.clip.as<float4>()};
+    {
+      StageTimer t(ctx, ST_BWD_FILTER, vst);
+      launch_filter_adjoint(lb.gm.as<float2>(), lb.tmp.as<float2>(), lb.gft.as<float2>(), v.W, lb.fa, vst);
+    }
+    {
+      StageTimer t(ctx, ST_BWD_SM_AA, vst);
+      launch_sm_aa_adjoint(aa, lb.fmap.as<float2>(), lb.gft.as<float2>(), v.gclip.as<float4>(), lb.tmp.as<float>(),
+                           ctx->params.aa_shadow, vst);
+    }
+    {
+      StageTimer t(ctx, ST_BWD_SM_INTERP, vst);
+      BigArgs big{v.big_index.as<int>(), v.big_tri.as<int>(), v.big_acc.as<float>(), ctx->status.as<DevStatus>(), l};
+      launch_sm_interp_adjoint(aa, lb.tmp.as<float>(), v.depth.as<float>(), v.gclip.as<float4>(), big, vst);
+    }
+  }
   {
     StageTimer t(ctx, ST_BWD_SHADE_SCATTER, st);
     launch_shade_scatter(sa, ga, st);
     launch_shade_big_resolve(sa, ga, cv.big_tri.as<int>(), ctx->status.as<DevStatus>(), L, st);
   }
-
-  // ---- per light: G^T, antialiasing adjoint, interpolation adjoint
-  {
-    StageTimer t(ctx, ST_BWD_FILTER, st);
-    for (int l = 0; l < L; ++l) {
-      LightBufs& lb = ctx->light[l];
-      launch_filter_adjoint(lb.gm.as<float2>(), lb.tmp.as<float2>(), lb.gft.as<float2>(), ctx->view[l].W, lb.fa, st);
-    }
-  }
-  {
-    StageTimer t(ctx, ST_BWD_SM_AA, st);
-    for (int l = 0; l < L; ++l) {
-      ViewBufs& v = ctx->view[l];
-      LightBufs& lb = ctx->light[l];
-      AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(), v.clip.as<float4>()};
-      launch_sm_aa_adjoint(aa, lb.fmap.as<float2>(), lb.gft.as<float2>(), v.gclip.as<float4>(), lb.tmp.as<float>(),
-                           ctx->params.aa_shadow, st);
-    }
-  }
-  StageTimer t_sm(ctx, ST_BWD_SM_INTERP, st);
-  for (int l = 0; l < L; ++l) {
-    ViewBufs& v = ctx->view[l];
-    LightBufs& lb = ctx->light[l];
-    AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(), v.clip.as<float4>()};
-    BigArgs big{v.big_index.as<int>(), v.big_tri.as<int>(), v.big_acc.as<float>(), ctx->status.as<DevStatus>(), l};
-    launch_sm_interp_adjoint(aa, lb.tmp.as<float>(), v.depth.as<float>(), v.gclip.as<float4>(), big, st);
-  }
-  t_sm.stop();
+  DSM_CHECK(join_views(ctx, st, L));
   // ---- vertices, normals, lights
   StageTimer t_vert(ctx, ST_BWD_VERTEX, st);
   VertGradPtrs gp{};
