@@ -147,6 +147,25 @@ dsm_status dsm_filter_moments(dsm_ctx* ctx, const float* in, float* out, int32_t
                               float sigma, int32_t radius, int32_t kind, int32_t boundary,
                               void* stream);
 
+/* Allocation-free variant of dsm_filter_moments, for callers that must not
+ * allocate device memory while they run (a real-time loop with a fixed memory
+ * budget, code between the begin and end of a stream capture, or an
+ * application that owns the device memory pool).  The paper has no
+ * counterpart; it is the same separable filter (same result as
+ * dsm_filter_moments for the same arguments).  in, out: device, res x res
+ * float2, must not overlap; the caller owns both.  The intermediate map lives
+ * in a static device array of the library (1024 x 1024 texels, 8 MiB, held
+ * by every GPU that loads the library until the process exits); no call
+ * allocates or frees memory.  The first call on a device looks up that
+ * array's device address once (make it before any stream capture on that
+ * device).  Every call shares the array: calls whose work overlaps on the GPU
+ * (two streams, or two threads) race on it; serialise them.  Returns
+ * DSM_ERR_CAPACITY when res * res exceeds 1024 * 1024, DSM_ERR_INVALID_ARG for
+ * other bad arguments, DSM_ERR_CUDA when the device lookup or the launch
+ * fails.  stream: cudaStream_t (NULL = legacy default stream). */
+dsm_status dsm_filter_moments_noalloc(const float* in, float* out, int32_t res, float sigma,
+                                      int32_t radius, int32_t kind, int32_t boundary, void* stream);
+
 /* Wait for the context's stream and report device-side errors (capacity
  * overflow, timeouts) raised since the last dsm_sync. */
 dsm_status dsm_sync(dsm_ctx* ctx);

@@ -26,7 +26,7 @@ DBG_GBUF, DBG_F, DBG_FTILDE, DBG_MOMENTS, DBG_COLOR, DBG_Q, DBG_SNAP, DBG_GM, DB
 EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_render_backward",
             "dsm_l2_loss_grad", "dsm_filter_moments", "dsm_sync", "dsm_last_error", "dsm_debug_copy",
             "dsm_profile_enable", "dsm_profile_stage_count", "dsm_profile_stage_name", "dsm_profile_read",
-            "dsm_kernel_launches"]
+            "dsm_kernel_launches", "dsm_filter_moments_noalloc"]
 
 
 class DsmError(RuntimeError):
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dsm_profile_stage_name": ([I32], ctypes.c_char_p),
         "dsm_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), I32], I32),
         "dsm_kernel_launches": ([], ctypes.c_uint64),
+        "dsm_filter_moments_noalloc": ([P, P, I32, ctypes.c_float, I32, I32, I32, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
