@@ -78,11 +78,13 @@ def stage_bytes(sc) -> dict:
         # transform (12 V in, 32 V out, +4 V depth) and triangle setup (12 T in, 64 T + 2 T out), binning count
         "setup": views * (12 * V + 32 * V + 12 * T + 66 * T + 64 * T) + L * 4 * V,
         "bin_fill": views * (64 * T + 4 * T),
-        # setup records and lists read once, one 16-byte G-buffer texel written per pixel
-        "raster": views * (64 * T + 4 * T) + 16 * (texels + WH),
-        "sm_interp": texels * (16 + 8),
+        # setup records and lists read once, one 16-byte G-buffer texel written per pixel, and per light
+        # texel the depth sample (f, f^2), 8 bytes
+        "raster": views * (64 * T + 4 * T) + 16 * (texels + WH) + 8 * texels,
+        # G-buffer 16 + (f, f^2) 8 in, (f~, (f^2)~) 8 out
         "sm_antialias": texels * (16 + 8 + 8),
-        "filter": texels * 2 * (8 + 8),
+        # one tiled pass: f~ in, moments out
+        "filter": texels * (8 + 8),
         "shade": WH * (16 + 16) + 8 * texels + 24 * V,
         "final_antialias": WH * (16 + 16 + 16),
         "bwd_clear": 8 * texels + views * 16 * V + 4 * L * V + 24 * V,
@@ -90,7 +92,7 @@ def stage_bytes(sc) -> dict:
         # per pixel: G-buffer 16 + dL/dcolour 16 in, pgrad 32 out; texel gradient scatter 8 per texel
         "bwd_shade": WH * (16 + 16 + 32) + 8 * texels + 40 * V,
         "bwd_shade_scatter": WH * (16 + 32) + 40 * V,
-        "bwd_filter": texels * 2 * (8 + 8),
+        "bwd_filter": texels * (8 + 8),
         # G-buffer 16 + f 8 + dL/df~ 8 in, dL/df 4 out
         "bwd_sm_antialias": texels * (16 + 8 + 8 + 4),
         # G-buffer 16 + dL/df 4 in, vertex gradients

@@ -140,12 +140,28 @@ dsm_status dsm_l2_loss_grad(const float* image, const float* target, int64_t n,
                             float* loss, float* dL_dimage, void* stream);
 
 /* Separable filter of a two-channel map (Eqs. moment1/moment2: m = G g), the
- * same arithmetic as inside dsm_render.  in, out: device, res x res float2
- * (row-major, 8-byte aligned), must not overlap.  Uses ctx scratch for the
- * intermediate row-filtered map (may allocate). */
+ * same arithmetic as inside dsm_render: G filters along x, then along y, with
+ * 2 radius + 1 normalised taps.  in, out: device, res x res float2 (row-major,
+ * 8-byte aligned), caller-owned, must not overlap.  sigma: Gaussian standard
+ * deviation in texels (kind 0); radius: taps on each side, 0 = ceil(2 sigma),
+ * at most 32; kind: 0 Gaussian, 1 box (equal taps); boundary: 0 clamp to the
+ * edge texel, 1 zero outside the map.  Radii up to 15 take one tiled kernel;
+ * larger radii take two 1-D passes through ctx scratch (may allocate).
+ * DSM_ERR_INVALID_ARG for bad arguments, DSM_ERR_CUDA on a launch error.
+ * stream: cudaStream_t (NULL = legacy default stream). */
 dsm_status dsm_filter_moments(dsm_ctx* ctx, const float* in, float* out, int32_t res,
                               float sigma, int32_t radius, int32_t kind, int32_t boundary,
                               void* stream);
+
+/* Transpose of dsm_filter_moments for the same arguments: gin = G^T gout
+ * (Sec. 4: the gradient with respect to the filtered moments is carried back
+ * to the unfiltered texels; for the clamp boundary the weight of the taps that
+ * G clamped onto an edge texel returns to that texel).  gout, gin: device,
+ * res x res float2, caller-owned, must not overlap.  Same errors and scratch
+ * rule as dsm_filter_moments. */
+dsm_status dsm_filter_moments_adjoint(dsm_ctx* ctx, const float* gout, float* gin, int32_t res,
+                                      float sigma, int32_t radius, int32_t kind, int32_t boundary,
+                                      void* stream);
 
 /* Allocation-free variant of dsm_filter_moments, for callers that must not
  * allocate device memory while they run (a real-time loop with a fixed memory

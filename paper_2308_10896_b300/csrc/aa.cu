@@ -128,31 +128,42 @@ __constant__ int kDJ[4] = {0, 0, -1, 1};
 // ------------------------------------------------------------------ forward
 // Every pixel gathers the gains of the (up to 4) pairs it belongs to: if t > 1/2
 // the neighbour-side pixel N gains (t - 1/2)(c_O - c_N), else O gains
-// (1/2 - t)(c_N - c_O).
+// (1/2 - t)(c_N - c_O).  The four neighbours' G-buffer entries are fetched
+// together up front; the neighbour's colour only where a pair blends.
+template <typename V, typename ColorOf>
+__device__ __forceinline__ V aa_pixel(const AAArgs& a, int i, int j, float4 gp, V cp, ColorOf color_of) {
+  float4 gq[4];
+  size_t qi[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const int ni = i + (d == 0 ? -1 : d == 1 ? 1 : 0), nj = j + (d == 2 ? -1 : d == 3 ? 1 : 0);
+    const bool ok = ni >= 0 && nj >= 0 && ni < a.W && nj < a.H;
+    qi[d] = ok ? (size_t)nj * a.W + ni : (size_t)j * a.W + i;   // out of range: the pixel itself (same id)
+    gq[d] = a.gbuf[qi[d]];
+  }
+  V acc = cp;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    if (gid(gq[d]) == gid(gp)) continue;
+    const int ni = i + (d == 0 ? -1 : d == 1 ? 1 : 0), nj = j + (d == 2 ? -1 : d == 3 ? 1 : 0);
+    PairInfo pi;
+    if (!pair_info<false>(a, i, j, ni, nj, gp, gq[d], pi)) continue;
+    const float t = pi.c.t;
+    if (t > 0.5f) {
+      if (!pi.p_occ) acc = vadd(acc, vscale(vsub(color_of(qi[d], gq[d]), cp), t - 0.5f));   // p = N, cq = c_O
+    } else {
+      if (pi.p_occ) acc = vadd(acc, vscale(vsub(color_of(qi[d], gq[d]), cp), 0.5f - t));    // p = O, cq = c_N
+    }
+  }
+  return acc;
+}
+
 template <typename V>
 __global__ void aa_forward_kernel(AAArgs a, const V* __restrict__ color, V* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= a.W || j >= a.H) return;
   const size_t p = (size_t)j * a.W + i;
-  const float4 gp = a.gbuf[p];
-  const V cp = color[p];
-  V acc = cp;
-  for (int d = 0; d < 4; ++d) {
-    const int ni = i + kDI[d], nj = j + kDJ[d];
-    if (ni < 0 || nj < 0 || ni >= a.W || nj >= a.H) continue;
-    const size_t q = (size_t)nj * a.W + ni;
-    const float4 gq = a.gbuf[q];
-    PairInfo pi;
-    if (!pair_info<false>(a, i, j, ni, nj, gp, gq, pi)) continue;
-    const V cq = color[q];
-    const float t = pi.c.t;
-    if (t > 0.5f) {
-      if (!pi.p_occ) acc = vadd(acc, vscale(vsub(cq, cp), t - 0.5f));        // p = N, cq = c_O
-    } else {
-      if (pi.p_occ) acc = vadd(acc, vscale(vsub(cq, cp), 0.5f - t));         // p = O, cq = c_N
-    }
-  }
-  out[p] = acc;
+  out[p] = aa_pixel<V>(a, i, j, a.gbuf[p], color[p], [&](size_t q, float4) { return color[q]; });
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -208,24 +219,6 @@ __global__ void aa_backward4_kernel(AAArgs a, const float4* __restrict__ color, 
   if (i >= a.W || j >= a.H) return;
   const size_t p = (size_t)j * a.W + i;
   gcolor[p] = aa ? aa_adjoint_pixel<float4>(a, i, j, color, gout, gclip) : gout[p];
-}
-
-// ------------------------------------------------------------------ shadow-map interpolation
-// f = sum_k b_k d_k of the covering triangle (background: f = 1), f^2 = f f.
-__global__ void sm_interp_kernel(const float4* __restrict__ gbuf, int R, const int* __restrict__ tris,
-                                 const float* __restrict__ depth, float2* __restrict__ fmap) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= R || j >= R) return;
-  const size_t p = (size_t)j * R + i;
-  const float4 g = gbuf[p];
-  const int id = gid(g);
-  float f = 1.f;
-  if (id) {
-    const int t = id - 1;
-    const float b2 = 1.f - g.y - g.z;
-    f = g.y * depth[tris[3 * t]] + g.z * depth[tris[3 * t + 1]] + b2 * depth[tris[3 * t + 2]];
-  }
-  fmap[p] = make_float2(f, f * f);
 }
 
 // Adjoint of the shadow-map antialiasing: dL/d(f, f^2) per texel (the pair
@@ -351,12 +344,6 @@ __global__ void sm_big_resolve_kernel(const int* __restrict__ tris, const int* _
 // ------------------------------------------------------------------ launchers
 static inline dim3 grid2(int W, int H, dim3 b) { return dim3((W + b.x - 1) / b.x, (H + b.y - 1) / b.y); }
 
-void launch_sm_interp(const float4* gbuf, int R, const int* tris, const float* depth, float2* fmap,
-                      cudaStream_t st) {
-  dim3 b(32, 8);
-  count_launches(1);
-  sm_interp_kernel<<<grid2(R, R, b), b, 0, st>>>(gbuf, R, tris, depth, fmap);
-}
 void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, cudaStream_t st) {
   dim3 b(32, 8);
   count_launches(1);

@@ -15,11 +15,11 @@ namespace dsm {
 std::atomic<unsigned long long> g_kernel_launches{0};
 
 static const char* const kStageNames[] = {
-    "setup", "bin_fill", "raster", "sm_interp", "sm_antialias", "filter", "shade", "final_antialias",
+    "setup", "bin_fill", "raster", "sm_antialias", "filter", "shade", "final_antialias",
     "bwd_clear", "bwd_final_antialias", "bwd_shade", "bwd_shade_scatter", "bwd_filter", "bwd_sm_antialias",
     "bwd_sm_interp", "bwd_vertex"};
 constexpr int kStages = (int)(sizeof(kStageNames) / sizeof(kStageNames[0]));
-enum Stage { ST_SETUP, ST_BIN_FILL, ST_RASTER, ST_SM_INTERP, ST_SM_AA, ST_FILTER, ST_SHADE, ST_FINAL_AA,
+enum Stage { ST_SETUP, ST_BIN_FILL, ST_RASTER, ST_SM_AA, ST_FILTER, ST_SHADE, ST_FINAL_AA,
              ST_BWD_CLEAR, ST_BWD_FINAL_AA, ST_BWD_SHADE, ST_BWD_SHADE_SCATTER, ST_BWD_FILTER, ST_BWD_SM_AA,
              ST_BWD_SM_INTERP, ST_BWD_VERTEX };
 
@@ -444,14 +444,11 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
     {
       StageTimer t(ctx, ST_RASTER, vst);
       launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY, v.W,
-                    v.H, v.clip.as<float4>(), mesh->tris, v.gbuf.as<float4>(), vst);
+                    v.H, v.clip.as<float4>(), mesh->tris, v.gbuf.as<float4>(), w < L ? v.depth.as<float>() : nullptr,
+                    w < L ? ctx->light[w].fmap.as<float2>() : nullptr, vst);
     }
     if (w == L) continue;
     LightBufs& lb = ctx->light[w];
-    {
-      StageTimer t(ctx, ST_SM_INTERP, vst);
-      launch_sm_interp(v.gbuf.as<float4>(), v.W, mesh->tris, v.depth.as<float>(), lb.fmap.as<float2>(), vst);
-    }
     {
       StageTimer t(ctx, ST_SM_AA, vst);
       if (params->aa_shadow) {
@@ -650,6 +647,21 @@ dsm_status dsm_filter_moments(dsm_ctx* ctx, const float* in, float* out, int32_t
   make_filter_args(sigma, radius, kind, boundary, &fa);
   launch_filter(reinterpret_cast<const float2*>(in), ctx->filter_tmp.as<float2>(), reinterpret_cast<float2*>(out), res,
                 fa, (cudaStream_t)stream);
+  DSM_CHECK(cudaGetLastError());
+  return DSM_OK;
+}
+
+dsm_status dsm_filter_moments_adjoint(dsm_ctx* ctx, const float* gout, float* gin, int32_t res, float sigma,
+                                      int32_t radius, int32_t kind, int32_t boundary, void* stream) {
+  if (!ctx) return DSM_ERR_INVALID_ARG;
+  if (!gout || !gin || res < 1 || res > 16384 || (kind != 0 && kind != 1) || (boundary != 0 && boundary != 1) ||
+      radius > 32 || (!(sigma > 0.f) && radius <= 0))
+    return fail(ctx, DSM_ERR_INVALID_ARG, "bad filter arguments");
+  DSM_CHECK(ctx->filter_tmp.ensure((size_t)res * res * sizeof(float2)));
+  FilterArgs fa;
+  make_filter_args(sigma, radius, kind, boundary, &fa);
+  launch_filter_adjoint(reinterpret_cast<const float2*>(gout), ctx->filter_tmp.as<float2>(),
+                        reinterpret_cast<float2*>(gin), res, fa, (cudaStream_t)stream);
   DSM_CHECK(cudaGetLastError());
   return DSM_OK;
 }

@@ -102,11 +102,13 @@ void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cu
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
                      int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
                      cudaStream_t st);
+// Light views (fmap != NULL) also write the shadow-map depth sample (f, f^2)
+// of every texel, f interpolated from the per-vertex light depths.
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
-                   int W, int H, const float4* clip, const int* tris, float4* gbuf, cudaStream_t st);
+                   int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth, float2* fmap,
+                   cudaStream_t st);
 
 // shadow-map interpolation and antialiasing
-void launch_sm_interp(const float4* gbuf, int R, const int* tris, const float* depth, float2* fmap, cudaStream_t st);
 void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, cudaStream_t st);
 void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, cudaStream_t st);
 void launch_sm_aa_adjoint(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,

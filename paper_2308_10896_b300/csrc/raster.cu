@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
                                                      const int* __restrict__ offset,
                                                      const int* __restrict__ list, int capacity, int tilesX,
                                                      int W, int H, const float4* __restrict__ clip,
-                                                     const int* __restrict__ tris, float4* __restrict__ gbuf) {
+                                                     const int* __restrict__ tris, float4* __restrict__ gbuf,
+                                                     const float* __restrict__ depth, float2* __restrict__ fmap) {
   __shared__ TriSetup sq[256];
   __shared__ unsigned long long sbest[256];
   __shared__ int spre[257];          // exclusive prefix of the work items per record
@@ -461,13 +462,21 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
   const uint64_t best = sbest[tid];
   if (i >= W || j >= H) return;
   float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  float f = 1.f;   // shadow-map depth sample; background: 1
   if (best != ~0ull) {
     const int t = (int)(best & 0xffffffffu);
-    const float4 c0 = clip[tris[3 * t]], c1 = clip[tris[3 * t + 1]], c2 = clip[tris[3 * t + 2]];
+    const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
+    const float4 c0 = clip[v0], c1 = clip[v1], c2 = clip[v2];
     const Bary r = bary_at(c0, c1, c2, pix_ndc_x(i, W), pix_ndc_y(j, H));
     out = make_float4(__int_as_float(t + 1), r.b[0], r.b[1], key_depth(best));
+    if (fmap) {
+      // f = sum_k b_k d_k with b_2 = 1 - b_0 - b_1 of the stored barycentrics
+      const float b2 = 1.f - r.b[0] - r.b[1];
+      f = r.b[0] * depth[v0] + r.b[1] * depth[v1] + b2 * depth[v2];
+    }
   }
   gbuf[(size_t)j * W + i] = out;
+  if (fmap) fmap[(size_t)j * W + i] = make_float2(f, f * f);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -522,9 +531,11 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, con
 }
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
-                   int W, int H, const float4* clip, const int* tris, float4* gbuf, cudaStream_t st) {
+                   int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth, float2* fmap,
+                   cudaStream_t st) {
   count_launches(1);
-  raster_kernel<<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf);
+  raster_kernel<<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf, depth,
+                                                 fmap);
 }
 
 }  // namespace dsm

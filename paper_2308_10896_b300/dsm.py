@@ -26,7 +26,7 @@ DBG_GBUF, DBG_F, DBG_FTILDE, DBG_MOMENTS, DBG_COLOR, DBG_Q, DBG_SNAP, DBG_GM, DB
 EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_render_backward",
             "dsm_l2_loss_grad", "dsm_filter_moments", "dsm_sync", "dsm_last_error", "dsm_debug_copy",
             "dsm_profile_enable", "dsm_profile_stage_count", "dsm_profile_stage_name", "dsm_profile_read",
-            "dsm_kernel_launches", "dsm_filter_moments_noalloc"]
+            "dsm_kernel_launches", "dsm_filter_moments_noalloc", "dsm_filter_moments_adjoint"]
 
 
 class DsmError(RuntimeError):
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dsm_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), I32], I32),
         "dsm_kernel_launches": ([], ctypes.c_uint64),
         "dsm_filter_moments_noalloc": ([P, P, I32, ctypes.c_float, I32, I32, I32, P], I32),
+        "dsm_filter_moments_adjoint": ([P, P, P, I32, ctypes.c_float, I32, I32, I32, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +190,12 @@ class Context:
                        boundary: int = 0, stream=None):
         self._check(self.lib.dsm_filter_moments(self.h, _ptr(inp), _ptr(out), inp.shape[0], float(sigma),
                                                 int(radius), int(kind), int(boundary), _stream_ptr(stream)), self.h)
+
+    def filter_moments_adjoint(self, gout: torch.Tensor, gin: torch.Tensor, sigma: float, radius: int = 0,
+                               kind: int = 0, boundary: int = 0, stream=None):
+        self._check(self.lib.dsm_filter_moments_adjoint(self.h, _ptr(gout), _ptr(gin), gout.shape[0], float(sigma),
+                                                        int(radius), int(kind), int(boundary),
+                                                        _stream_ptr(stream)), self.h)
 
     def sync(self):
         self._check(self.lib.dsm_sync(self.h), self.h)

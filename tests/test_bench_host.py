@@ -54,9 +54,9 @@ def test_stage_bytes_model():
     sc = scenes.config1()
     b = bench.stage_bytes(sc)
     R2, WH = 256 * 256, 256 * 256
-    assert b["filter"] == R2 * 32 and b["bwd_filter"] == R2 * 32
+    assert b["filter"] == R2 * 16 and b["bwd_filter"] == R2 * 16
     assert b["final_antialias"] == WH * 48
-    assert set(b) >= {"raster", "shade", "bwd_sm_interp", "bwd_sm_antialias", "bwd_shade", "setup"}
+    assert set(b) >= {"raster", "sm_antialias", "shade", "bwd_sm_interp", "bwd_sm_antialias", "bwd_shade", "setup"}
 
 
 @pytest.mark.slow
