@@ -7,91 +7,143 @@
 namespace dsm {
 
 // ------------------------------------------------------------------ light camera
-// Float64 value with its derivative w.r.t. one light parameter.  The value
-// part uses explicitly rounded operations so that the float32 light matrix is
-// reproducible bit for bit; the derivative is ordinary float64 arithmetic.
-struct D1 {
-  double v, d;
+// The float32 light matrix Q (supplementary Sec. A light cameras: clip rows
+// 0-3, depth row 4) must be reproducible bit for bit, so its entries are
+// formed in float64 with explicitly rounded operations (no contraction) in a
+// fixed order and rounded to float32 once.  The derivatives J = dQ/d theta
+// (theta = pos xyz, dir xyz) only feed gradients and use float32 dual numbers.
+struct R64 {   // float64 value, every operation separately rounded
+  double v;
 };
-__device__ __forceinline__ D1 dc(double v) { return {v, 0.0}; }
-__device__ __forceinline__ D1 operator+(const D1& a, const D1& b) { return {__dadd_rn(a.v, b.v), a.d + b.d}; }
-__device__ __forceinline__ D1 operator-(const D1& a, const D1& b) { return {__dsub_rn(a.v, b.v), a.d - b.d}; }
-__device__ __forceinline__ D1 operator-(const D1& a) { return {-a.v, -a.d}; }
-__device__ __forceinline__ D1 operator*(const D1& a, const D1& b) { return {__dmul_rn(a.v, b.v), a.d * b.v + a.v * b.d}; }
-__device__ __forceinline__ D1 operator/(const D1& a, const D1& b) {
-  const double q = __ddiv_rn(a.v, b.v);
+__device__ __forceinline__ R64 operator+(R64 a, R64 b) { return {__dadd_rn(a.v, b.v)}; }
+__device__ __forceinline__ R64 operator-(R64 a, R64 b) { return {__dsub_rn(a.v, b.v)}; }
+__device__ __forceinline__ R64 operator-(R64 a) { return {-a.v}; }
+__device__ __forceinline__ R64 operator*(R64 a, R64 b) { return {__dmul_rn(a.v, b.v)}; }
+__device__ __forceinline__ R64 operator/(R64 a, R64 b) { return {__ddiv_rn(a.v, b.v)}; }
+__device__ __forceinline__ R64 tsqrt(R64 a) { return {__dsqrt_rn(a.v)}; }
+__device__ __forceinline__ double val(R64 a) { return a.v; }
+
+struct F1 {    // float32 value with its derivative w.r.t. one light parameter
+  float v, d;
+};
+__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ F1 operator-(F1 a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ F1 operator/(F1 a, F1 b) {
+  const float q = a.v / b.v;
   return {q, (a.d - q * b.d) / b.v};
 }
-__device__ __forceinline__ D1 dsqrt(const D1& a) {
-  const double r = __dsqrt_rn(a.v);
-  return {r, a.d / (2.0 * r)};
+__device__ __forceinline__ F1 tsqrt(F1 a) {
+  const float r = sqrtf(a.v);
+  return {r, a.d / (2.f * r)};
 }
-struct V3 { D1 x, y, z; };
-__device__ __forceinline__ D1 dot3(const V3& a, const V3& b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
-__device__ __forceinline__ V3 cross3(const V3& a, const V3& b) {
+__device__ __forceinline__ double val(F1 a) { return a.v; }
+
+template <class T> struct V3 { T x, y, z; };
+template <class T> __device__ __forceinline__ T dot3(const V3<T>& a, const V3<T>& b) {
+  return (a.x * b.x + a.y * b.y) + a.z * b.z;
+}
+template <class T> __device__ __forceinline__ V3<T> cross3(const V3<T>& a, const V3<T>& b) {
   return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
-__device__ __forceinline__ V3 normalize3(const V3& a) {
-  D1 n = dsqrt((a.x * a.x + a.y * a.y) + a.z * a.z);
+template <class T> __device__ __forceinline__ V3<T> normalize3(const V3<T>& a) {
+  const T n = tsqrt((a.x * a.x + a.y * a.y) + a.z * a.z);
   return {a.x / n, a.y / n, a.z / n};
 }
 
-// Thread (light l, parameter j) computes Q (clip rows 0-3, depth row 4) in
-// float64 together with dQ/d theta_j (theta = pos xyz, dir xyz); thread j = 0
-// also writes the float32 Q (supplementary Sec. A light cameras).
+// Light frame: forward f, right r, up u, eye e, and the scalars every entry uses.
+template <class T> struct Frame {
+  V3<T> f, r, u, e;
+  T fe, rng, nfe_near;   // f.e, far - near, -f.e - near
+};
+template <class T> __device__ __forceinline__ Frame<T> light_frame(const T (&th)[6], const LightConst& L, T zero,
+                                                                   T one) {
+  Frame<T> F;
+  const V3<T> dir = {th[3], th[4], th[5]};
+  F.f = normalize3(dir);
+  const V3<T> up = fabs(val(F.f.y)) > 0.99 ? V3<T>{zero, zero, one} : V3<T>{zero, one, zero};
+  F.r = normalize3(cross3(F.f, up));
+  F.u = cross3(F.r, F.f);
+  if (L.type == 0) {
+    const T md = -(one * T{(decltype(one.v))L.dist});
+    F.e = {md * F.f.x, md * F.f.y, md * F.f.z};
+  } else {
+    F.e = {th[0], th[1], th[2]};
+  }
+  F.fe = dot3(F.f, F.e);
+  const T nearp = one * T{(decltype(one.v))L.near_plane}, farp = one * T{(decltype(one.v))L.far_plane};
+  F.rng = farp - nearp;
+  F.nfe_near = -F.fe - nearp;
+  return F;
+}
+
+// Entry k of Q as mult * op (+ add for the spot's [2][3]) / den, in the order
+// the entry is defined: directional rows r/h, u/h, depth row, (0 0 0 1);
+// spot rows c r, c u, A f (+B), f; both: depth row f / (far - near).
+template <class T> __device__ __forceinline__ T q_entry(int k, const Frame<T>& F, const LightConst& L, T zero, T one) {
+  using S = decltype(one.v);
+  const T nearp = one * T{(S)L.near_plane}, farp = one * T{(S)L.far_plane};
+  const V3<T>& f = F.f;
+  if (k >= 16) {
+    const T op = k == 16 ? f.x : k == 17 ? f.y : k == 18 ? f.z : F.nfe_near;
+    return op / F.rng;
+  }
+  const int row = k >> 2, c = k & 3;
+  if (L.type == 0) {
+    const T h = one * T{(S)L.ortho_half};
+    if (row == 0) return (c == 0 ? F.r.x : c == 1 ? F.r.y : c == 2 ? F.r.z : -dot3(F.r, F.e)) / h;
+    if (row == 1) return (c == 0 ? F.u.x : c == 1 ? F.u.y : c == 2 ? F.u.z : -dot3(F.u, F.e)) / h;
+    if (row == 2) return (c == 0 ? f.x : c == 1 ? f.y : c == 2 ? f.z : F.nfe_near) / F.rng;
+    return c == 3 ? one : zero;
+  }
+  const T cc = one * T{(S)L.persp_c};
+  if (row == 0) return c < 3 ? cc * (c == 0 ? F.r.x : c == 1 ? F.r.y : F.r.z) : -(cc * dot3(F.r, F.e));
+  if (row == 1) return c < 3 ? cc * (c == 0 ? F.u.x : c == 1 ? F.u.y : F.u.z) : -(cc * dot3(F.u, F.e));
+  if (row == 2) {
+    const T A = farp / F.rng;
+    if (c < 3) return A * (c == 0 ? f.x : c == 1 ? f.y : f.z);
+    const T B = (-(farp * nearp)) / F.rng;
+    return (-(A * F.fe)) + B;
+  }
+  return c == 0 ? f.x : c == 1 ? f.y : c == 2 ? f.z : -F.fe;
+}
+
+// One CTA per light.  Warp 0: lane k < 20 forms Q[k] in float64 (the frame is
+// computed by every lane at once) and lane 0 writes the light's other fields;
+// warp 1: lane j < 6 forms all of Q with float32 duals in direction theta_j
+// and writes column j of J.
 __global__ void light_setup_kernel(const float* __restrict__ params, LightSetupArgs a, LightDev* out,
                                    float* viewM) {
-  const int l = threadIdx.x / 6, jd = threadIdx.x % 6;
+  const int l = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (l >= a.n) return;
   const LightConst& L = a.c[l];
-  D1 th[6];
-  for (int k = 0; k < 6; ++k) th[k] = {(double)params[l * 6 + k], k == jd ? 1.0 : 0.0};
-  const V3 pos = {th[0], th[1], th[2]};
-  const V3 dir = {th[3], th[4], th[5]};
-  const V3 f = normalize3(dir);
-  const V3 up = fabs(f.y.v) > 0.99 ? V3{dc(0.0), dc(0.0), dc(1.0)} : V3{dc(0.0), dc(1.0), dc(0.0)};
-  const V3 r = normalize3(cross3(f, up));
-  const V3 u = cross3(r, f);
-  const D1 nearp = dc(L.near_plane), farp = dc(L.far_plane);
-  V3 e;
-  if (L.type == 0) {
-    const D1 md = dc(-(double)L.dist);
-    e = {md * f.x, md * f.y, md * f.z};
-  } else {
-    e = pos;
-  }
-  const D1 fe = dot3(f, e);
-  const D1 rng = farp - nearp;
-  D1 Q[20];
-  Q[16] = f.x / rng; Q[17] = f.y / rng; Q[18] = f.z / rng; Q[19] = (-fe - nearp) / rng;
-  if (L.type == 0) {
-    const D1 h = dc(L.ortho_half);
-    Q[0] = r.x / h; Q[1] = r.y / h; Q[2] = r.z / h; Q[3] = (-dot3(r, e)) / h;
-    Q[4] = u.x / h; Q[5] = u.y / h; Q[6] = u.z / h; Q[7] = (-dot3(u, e)) / h;
-    Q[8] = Q[16]; Q[9] = Q[17]; Q[10] = Q[18]; Q[11] = Q[19];
-    Q[12] = dc(0.0); Q[13] = dc(0.0); Q[14] = dc(0.0); Q[15] = dc(1.0);
-  } else {
-    const D1 c = dc(L.persp_c);
-    const D1 A = farp / rng;
-    const D1 B = (-(farp * nearp)) / rng;
-    Q[0] = c * r.x; Q[1] = c * r.y; Q[2] = c * r.z; Q[3] = -(c * dot3(r, e));
-    Q[4] = c * u.x; Q[5] = c * u.y; Q[6] = c * u.z; Q[7] = -(c * dot3(u, e));
-    Q[8] = A * f.x; Q[9] = A * f.y; Q[10] = A * f.z; Q[11] = (-(A * fe)) + B;
-    Q[12] = f.x; Q[13] = f.y; Q[14] = f.z; Q[15] = -fe;
-  }
   LightDev& o = out[l];
-  for (int k = 0; k < 20; ++k) o.J[k * 6 + jd] = (float)Q[k].d;
-  if (jd != 0) return;
-  for (int k = 0; k < 20; ++k) {
-    o.Q[k] = __double2float_rn(Q[k].v);
-    viewM[l * 20 + k] = o.Q[k];
+  if (warp == 0) {
+    if (lane >= 20) return;
+    R64 th[6];
+    for (int k = 0; k < 6; ++k) th[k] = {(double)params[l * 6 + k]};
+    const R64 zero{0.0}, one{1.0};
+    const Frame<R64> F = light_frame(th, L, zero, one);
+    const float q = __double2float_rn(q_entry(lane, F, L, zero, one).v);
+    o.Q[lane] = q;
+    viewM[l * 20 + lane] = q;
+    if (lane == 0) {
+      o.fwd[0] = (float)F.f.x.v; o.fwd[1] = (float)F.f.y.v; o.fwd[2] = (float)F.f.z.v;
+      const double dx = th[3].v, dy = th[4].v, dz = th[5].v;
+      o.dir_norm = (float)sqrt(dx * dx + dy * dy + dz * dz);
+      o.pos[0] = params[l * 6 + 0]; o.pos[1] = params[l * 6 + 1]; o.pos[2] = params[l * 6 + 2];
+      o.type = L.type;
+      o.res = L.res;
+      o.intensity[0] = L.intensity[0]; o.intensity[1] = L.intensity[1]; o.intensity[2] = L.intensity[2];
+    }
+  } else if (warp == 1 && lane < 6) {
+    F1 th[6];
+    for (int k = 0; k < 6; ++k) th[k] = {params[l * 6 + k], k == lane ? 1.f : 0.f};
+    const F1 zero{0.f, 0.f}, one{1.f, 0.f};
+    const Frame<F1> F = light_frame(th, L, zero, one);
+    for (int k = 0; k < 20; ++k) o.J[k * 6 + lane] = q_entry(k, F, L, zero, one).d;
   }
-  o.fwd[0] = (float)f.x.v; o.fwd[1] = (float)f.y.v; o.fwd[2] = (float)f.z.v;
-  o.dir_norm = (float)sqrt(dir.x.v * dir.x.v + dir.y.v * dir.y.v + dir.z.v * dir.z.v);
-  o.pos[0] = params[l * 6 + 0]; o.pos[1] = params[l * 6 + 1]; o.pos[2] = params[l * 6 + 2];
-  o.type = L.type;
-  o.res = L.res;
-  o.intensity[0] = L.intensity[0]; o.intensity[1] = L.intensity[1]; o.intensity[2] = L.intensity[2];
 }
 
 // ------------------------------------------------------------------ vertex transform
@@ -301,42 +353,74 @@ __global__ void bin_big_kernel(const TriSetup* __restrict__ setup, const int* __
 
 // Single-CTA exclusive scan of the tile counts; offset[n] = total pairs.  Also
 // records the total for the host and clears the counters for the fill pass.
-__global__ void scan_kernel(int* __restrict__ count, int n, int* __restrict__ offset, DevStatus* status,
-                            int view) {
+// Each thread owns kScanPer consecutive counts of a chunk (loaded together,
+// scanned in registers); one block scan of the per-thread sums per chunk.
+constexpr int kScanThreads = 1024, kScanPer = 16;
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(int* __restrict__ count, int n, int* __restrict__ offset,
+                                                            DevStatus* status, int view) {
   __shared__ int warp_sums[32];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = 0; base < n; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    int v = i < n ? count[i] : 0;
-    int incl = v;
+  for (int base = 0; base < n; base += kScanThreads * kScanPer) {
+    const int i0 = base + threadIdx.x * kScanPer;
+    int v[kScanPer];
+    if (i0 + kScanPer <= n) {
+#pragma unroll
+      for (int k = 0; k < kScanPer; k += 4) {
+        const int4 q = *reinterpret_cast<const int4*>(count + i0 + k);
+        v[k] = q.x; v[k + 1] = q.y; v[k + 2] = q.z; v[k + 3] = q.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) v[k] = i0 + k < n ? count[i0 + k] : 0;
+    }
+    int tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      const int c = v[k];
+      v[k] = tsum;          // exclusive within the thread
+      tsum += c;
+    }
+    int incl = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int u = __shfl_up_sync(kFull, incl, o);
+      const int u = __shfl_up_sync(kFull, incl, o);
       if (lane >= o) incl += u;
     }
     if (lane == 31) warp_sums[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-      int w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+      const int w = warp_sums[lane];
       int wi = w;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(kFull, wi, o);
+        const int u = __shfl_up_sync(kFull, wi, o);
         if (lane >= o) wi += u;
       }
       warp_sums[lane] = wi - w;
     }
     __syncthreads();
-    int c = carry;
-    if (i < n) {
-      offset[i] = c + warp_sums[warp] + incl - v;
-      count[i] = 0;
+    const int c = carry;
+    const int tbase = c + warp_sums[warp] + incl - tsum;
+    if (i0 + kScanPer <= n) {
+#pragma unroll
+      for (int k = 0; k < kScanPer; k += 4) {
+        *reinterpret_cast<int4*>(offset + i0 + k) =
+            make_int4(tbase + v[k], tbase + v[k + 1], tbase + v[k + 2], tbase + v[k + 3]);
+        *reinterpret_cast<int4*>(count + i0 + k) = make_int4(0, 0, 0, 0);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k)
+        if (i0 + k < n) {
+          offset[i0 + k] = tbase + v[k];
+          count[i0 + k] = 0;
+        }
     }
     __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = c + warp_sums[warp] + incl;
+    if (threadIdx.x == kScanThreads - 1) carry = tbase + tsum;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -483,7 +567,7 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM,
                         cudaStream_t st) {
   count_launches(1);
-  light_setup_kernel<<<1, 6 * DSM_MAX_LIGHTS, 0, st>>>(params, a, out, viewM);
+  light_setup_kernel<<<a.n, 64, 0, st>>>(params, a, out, viewM);
 }
 
 void launch_transform(const float* verts, int V, const float* M20, int W, int H, float4* clip, VertSnap* snap,
@@ -515,7 +599,7 @@ void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, De
 
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st) {
   count_launches(1);
-  scan_kernel<<<1, 1024, 0, st>>>(count, n, offset, status, view);
+  scan_kernel<<<1, kScanThreads, 0, st>>>(count, n, offset, status, view);
 }
 
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
