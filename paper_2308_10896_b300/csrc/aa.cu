@@ -159,7 +159,7 @@ __device__ __forceinline__ V aa_pixel(const AAArgs& a, int i, int j, float4 gp, 
 }
 
 template <typename V>
-__global__ void aa_forward_kernel(AAArgs a, const V* __restrict__ color, V* __restrict__ out) {
+__global__ void __launch_bounds__(256, 6) aa_forward_kernel(AAArgs a, const V* __restrict__ color, V* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= a.W || j >= a.H) return;
   const size_t p = (size_t)j * a.W + i;
@@ -213,7 +213,7 @@ __device__ __forceinline__ V aa_adjoint_pixel(const AAArgs& a, int i, int j, con
   return acc;
 }
 
-__global__ void aa_backward4_kernel(AAArgs a, const float4* __restrict__ color, const float4* __restrict__ gout,
+__global__ void __launch_bounds__(256, 6) aa_backward4_kernel(AAArgs a, const float4* __restrict__ color, const float4* __restrict__ gout,
                                     float4* __restrict__ gcolor, float4* __restrict__ gclip, int aa) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= a.W || j >= a.H) return;
@@ -224,7 +224,7 @@ __global__ void aa_backward4_kernel(AAArgs a, const float4* __restrict__ color, 
 // Adjoint of the shadow-map antialiasing: dL/d(f, f^2) per texel (the pair
 // t-gradients go to the light-space clip coordinates of the edge endpoints),
 // folded into dL/df = g.x + 2 f g.y (f^2 = f f).  One thread per texel.
-__global__ void sm_aa_adjoint_kernel(AAArgs a, const float2* __restrict__ fmap, const float2* __restrict__ gft,
+__global__ void __launch_bounds__(256, 6) sm_aa_adjoint_kernel(AAArgs a, const float2* __restrict__ fmap, const float2* __restrict__ gft,
                                      float4* __restrict__ gclip, float* __restrict__ gf_out, int aa) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= a.W || j >= a.H) return;

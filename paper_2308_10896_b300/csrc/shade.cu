@@ -258,7 +258,7 @@ constexpr int kShadeStrip = 8;
 // dL/d(m1, m2) (bilinear adjoint), reduces dL/dQ, the direct light terms and
 // the albedo gradient per block (slot copies), and writes the per-pixel
 // dL/d world position and dL/d interpolated normal for shade_scatter_kernel.
-__global__ void __launch_bounds__(256) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g) {
+__global__ void __launch_bounds__(256, 5) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g) {
   __shared__ float sQ[DSM_MAX_LIGHTS * 20];
   __shared__ float sD[DSM_MAX_LIGHTS * 3];
   __shared__ float sA[kMaxSharedMat * 3];
