@@ -247,18 +247,17 @@ constexpr int kStrip = 16;
 struct SmScatter {
   const int* tris;
   float4* gclip;
-  const int* big;        // big-triangle index per triangle (-1: scatter onto the vertices)
   float* big_acc;        // kMaxBig x kBigSlots x kBigStrideSm
   int slot;
-  __device__ __forceinline__ void operator()(int t, const float (&c)[12], int lane) const {
-    const int b = big[t];
-    if (b >= 0) {
-      float* d = big_acc + ((size_t)b * kBigSlots + ((slot + lane) & (kBigSlots - 1))) * kBigStrideSm;
-      for (int k = 0; k < 12; ++k) atomicAdd(&d[k], c[k]);
-      return;
-    }
+  // ordinary triangle: onto its vertices
+  __device__ __forceinline__ void vertices(int t, const float (&c)[12]) const {
     for (int k = 0; k < 3; ++k)
       atomic_add4(&gclip[tris[3 * t + k]], make_float4(c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]));
+  }
+  // big triangle b: into one of its slot copies
+  __device__ __forceinline__ void operator()(int b, const float (&c)[12], int lane = 0) const {
+    float* d = big_acc + ((size_t)b * kBigSlots + ((slot + lane) & (kBigSlots - 1))) * kBigStrideSm;
+    for (int k = 0; k < 12; ++k) atomicAdd(&d[k], c[k]);
   }
 };
 
@@ -270,9 +269,9 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kStrip;
   const bool col_ok = i < a.W;
-  SmScatter sc{a.tris, gclip, big, big_acc, scatter_slot(kBigSlots)};
-  RunAcc<12> run;
-  run_reset(run);
+  SmScatter sc{a.tris, gclip, big_acc, scatter_slot(kBigSlots)};
+  BigRun<12, 2> run;
+  big_run_reset(run);
   int ct = -1;                      // triangle whose vertex data are cached
   float4 cc[3];
   float cd[3];
@@ -317,9 +316,11 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
         c[4 * k] = gcv[k].x; c[4 * k + 1] = gcv[k].y; c[4 * k + 2] = b[k] * gf; c[4 * k + 3] = gcv[k].w;
       }
     }
-    run_add(run, t, c, sc);
+    const int bi = t >= 0 ? big[t] : -1;
+    big_run_add(run, bi, c, sc);
+    if (t >= 0 && bi < 0) sc.vertices(t, c);
   }
-  run_flush(run, sc);
+  big_run_flush(run, sc);
 }
 
 // Sum the kBigSlots copies of each big triangle and scatter the result onto its

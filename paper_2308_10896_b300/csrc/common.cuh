@@ -160,6 +160,80 @@ __device__ __forceinline__ void atomic_add2(float2* p, float2 v) {
   atomicAdd(p, v);
 }
 
+// Per-lane register sums for up to K big triangles per warp (a big triangle's
+// texels are spread over most lanes and rows of a strip, so their
+// contributions are summed in registers and reduced across the warp once, at
+// the flush).  The triangles held are the same on every lane; a lane whose big
+// triangle finds no free slot adds it through `direct`.  Every lane of the
+// warp must call add / flush together; add with b < 0 adds nothing.
+template <int N, int K>
+struct BigRun {
+  int big[K];       // big-triangle index held by each slot, -1 = free (warp-uniform)
+  float v[K][N];
+};
+
+template <int N, int K>
+__device__ __forceinline__ void big_run_reset(BigRun<N, K>& r) {
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    r.big[s] = -1;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.v[s][k] = 0.f;
+  }
+}
+
+template <int N, int K, typename Direct>
+__device__ __forceinline__ void big_run_add(BigRun<N, K>& r, int b, const float (&c)[N], Direct& direct) {
+  // claim free slots for big triangles not yet held (warp-uniform decisions)
+  auto held = [&](int x) {
+    bool h = false;
+#pragma unroll
+    for (int s = 0; s < K; ++s) h |= (x == r.big[s]);
+    return h;
+  };
+  unsigned m = __ballot_sync(kFull, b >= 0 && !held(b));
+  while (m) {
+    const int bn = __shfl_sync(kFull, b, __ffs(m) - 1);
+    int free_slot = -1;
+#pragma unroll
+    for (int s = K - 1; s >= 0; --s)
+      if (r.big[s] < 0) free_slot = s;
+    if (free_slot < 0) break;
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+      if (s == free_slot) r.big[s] = bn;
+    m = __ballot_sync(kFull, b >= 0 && !held(b));
+  }
+  if (b < 0) return;
+  bool done = false;
+#pragma unroll
+  for (int s = 0; s < K; ++s)
+    if (b == r.big[s]) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) r.v[s][k] += c[k];
+      done = true;
+    }
+  if (!done) direct(b, c, threadIdx.x & 31);
+}
+
+// flush(big index, sums) is called by lane 0 for each held slot.
+template <int N, int K, typename Flush>
+__device__ __forceinline__ void big_run_flush(BigRun<N, K>& r, Flush& flush) {
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    if (r.big[s] < 0) continue;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      float x = r.v[s][k];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+      r.v[s][k] = x;
+    }
+    if ((threadIdx.x & 31) == 0) flush(r.big[s], r.v[s]);
+  }
+  big_run_reset(r);
+}
+
 // Warp-uniform run accumulator for per-triangle gradient scatters.  While all
 // 32 lanes of a warp add to the same triangle the sums stay in registers; a run
 // is flushed by a butterfly reduction and one set of atomics from lane 0.
