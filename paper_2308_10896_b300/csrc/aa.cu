@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256, 6) sm_aa_adjoint_kernel(AAArgs a, const f
 // columns; per-triangle sums go through a run accumulator (a large triangle
 // costs one set of atomics per strip), the current triangle's vertex data stay
 // in registers, and the next row's texel data are fetched one row ahead.
-constexpr int kStrip = 16;
+constexpr int kStrip = 8;
 
 // Scatter of 12 per-triangle values: for each vertex (dL/dclip_x, dL/dclip_y,
 // dL/dd, dL/dclip_w).  A light view's barycentrics never depend on clip z, so

@@ -234,55 +234,4 @@ __device__ __forceinline__ void big_run_flush(BigRun<N, K>& r, Flush& flush) {
   big_run_reset(r);
 }
 
-// Warp-uniform run accumulator for per-triangle gradient scatters.  While all
-// 32 lanes of a warp add to the same triangle the sums stay in registers; a run
-// is flushed by a butterfly reduction and one set of atomics from lane 0.
-// Lanes of mixed warps scatter their own contribution directly (the flush gets
-// the lane id so that slot copies can be spread).  Every lane of the warp must
-// call run_add / run_flush together.
-template <int N>
-struct RunAcc {
-  float v[N];
-  int tri;   // same on all lanes; -1 when empty
-};
-
-template <int N>
-__device__ __forceinline__ void run_reset(RunAcc<N>& a) {
-  a.tri = -1;
-#pragma unroll
-  for (int k = 0; k < N; ++k) a.v[k] = 0.f;
-}
-
-template <int N, typename Flush>
-__device__ __forceinline__ void run_flush(RunAcc<N>& a, Flush& flush) {
-  if (a.tri < 0) return;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    float x = a.v[k];
-#pragma unroll
-    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    a.v[k] = x;
-  }
-  if ((threadIdx.x & 31) == 0) flush(a.tri, a.v, 0);
-  run_reset(a);
-}
-
-template <int N, typename Flush>
-__device__ __forceinline__ void run_add(RunAcc<N>& a, int t, const float (&c)[N], Flush& flush) {
-  if (a.tri >= 0 && __all_sync(kFull, t == a.tri)) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) a.v[k] += c[k];
-    return;
-  }
-  run_flush(a, flush);
-  const int t0 = __shfl_sync(kFull, t, 0);
-  if (t0 >= 0 && __all_sync(kFull, t == t0)) {
-    a.tri = t0;
-#pragma unroll
-    for (int k = 0; k < N; ++k) a.v[k] = c[k];
-    return;
-  }
-  if (t >= 0) flush(t, c, threadIdx.x & 31);   // lane offset spreads big-triangle slot copies
-}
-
 }  // namespace dsm

@@ -421,16 +421,10 @@ struct CamScatter {
   float* dverts;
   float* gnormal;
   float4* gclip;
-  const int* big;
   float* big_acc;
   int slot;
-  __device__ __forceinline__ void operator()(int t, const float (&c)[30], int lane) const {
-    const int b = big[t];
-    if (b >= 0) {
-      float* d = big_acc + ((size_t)b * kBigSlots + ((slot + lane) & (kBigSlots - 1))) * kBigStrideCam;
-      for (int k = 0; k < 30; ++k) atomicAdd(&d[k], c[k]);
-      return;
-    }
+  // ordinary triangle: onto its vertices
+  __device__ __forceinline__ void vertices(int t, const float (&c)[30]) const {
     for (int k = 0; k < 3; ++k) {
       const int v = tris[3 * t + k];
       atomicAdd(&dverts[3 * v], c[3 * k]);
@@ -442,15 +436,20 @@ struct CamScatter {
       atomic_add4(&gclip[v], make_float4(c[18 + 4 * k], c[19 + 4 * k], c[20 + 4 * k], c[21 + 4 * k]));
     }
   }
+  // big triangle b: into one of its slot copies
+  __device__ __forceinline__ void operator()(int b, const float (&c)[30], int lane = 0) const {
+    float* d = big_acc + ((size_t)b * kBigSlots + ((slot + lane) & (kBigSlots - 1))) * kBigStrideCam;
+    for (int k = 0; k < 30; ++k) atomicAdd(&d[k], c[k]);
+  }
 };
 
 __global__ void __launch_bounds__(256) shade_scatter_kernel(ShadeArgs a, ShadeGradArgs g) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kShadeStrip;
   const bool col_ok = i < a.W;
-  CamScatter sc{a.tris, g.dverts, g.gnormal, g.gclip, g.big, g.big_acc, scatter_slot(kBigSlots)};
-  RunAcc<30> run;
-  run_reset(run);
+  CamScatter sc{a.tris, g.dverts, g.gnormal, g.gclip, g.big_acc, scatter_slot(kBigSlots)};
+  BigRun<30, 2> run;
+  big_run_reset(run);
   TriCache tc;
   for (int srow = 0; srow < kShadeStrip; ++srow) {
     const int j = j0 + srow;
@@ -484,9 +483,11 @@ __global__ void __launch_bounds__(256) shade_scatter_kernel(ShadeArgs a, ShadeGr
         }
       }
     }
-    run_add(run, t, c, sc);
+    const int bi = t >= 0 ? g.big[t] : -1;
+    big_run_add(run, bi, c, sc);
+    if (t >= 0 && bi < 0) sc.vertices(t, c);
   }
-  run_flush(run, sc);
+  big_run_flush(run, sc);
 }
 
 // Sum the kBigSlots copies of each big camera-view triangle and scatter them.
