@@ -117,6 +117,50 @@ __global__ void set_matrix_kernel(Mat20 m, float* dst) {
   if (k < 20) dst[k] = m.v[k];
 }
 
+// One launch that zeroes several buffers: segment blockIdx.y, 16-byte stores
+// over its aligned body, 4-byte stores for an unaligned head and the tail.
+constexpr int kMaxClear = 40;
+struct ClearList {
+  float* p[kMaxClear];
+  long long n[kMaxClear];     // floats
+  int count;
+};
+
+__global__ void clear_kernel(ClearList c) {
+  const int s = blockIdx.y;
+  if (s >= c.count) return;
+  float* p = c.p[s];
+  const long long n = c.n[s];
+  const long long head = min(n, (long long)(((16 - ((uintptr_t)p & 15)) & 15) / 4));
+  const long long body = (n - head) / 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 < head) p[t0] = 0.f;
+  float4* q = reinterpret_cast<float4*>(p + head);
+  for (long long k = t0; k < body; k += stride) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const long long tail0 = head + 4 * body;
+  if (t0 < n - tail0) p[tail0 + t0] = 0.f;
+}
+
+struct Clearer {
+  ClearList list{};
+  long long largest = 0;
+  void add(void* p, size_t bytes) {
+    if (!p || bytes == 0) return;
+    list.p[list.count] = static_cast<float*>(p);
+    list.n[list.count] = (long long)(bytes / 4);
+    largest = std::max(largest, (long long)(bytes / 4));
+    ++list.count;
+  }
+  void launch(cudaStream_t st) {
+    if (!list.count) return;
+    const long long per = 256LL * 4;
+    const int gx = (int)std::min<long long>((largest + per - 1) / per, 1184);
+    count_launches(1);
+    clear_kernel<<<dim3(std::max(gx, 1), list.count), 256, 0, st>>>(list);
+  }
+};
+
 cudaEvent_t take_event(dsm_ctx* c) {
   if (!c->free_events.empty()) {
     cudaEvent_t e = c->free_events.back();
@@ -534,21 +578,24 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   }
   // ---- clear accumulators and outputs
   StageTimer t_clear(ctx, ST_BWD_CLEAR, st);
-  DSM_CHECK(cudaMemsetAsync(dL_dverts, 0, sizeof(float) * 3 * V, st));
-  if (L) DSM_CHECK(cudaMemsetAsync(dL_dlight, 0, sizeof(float) * 6 * L, st));
-  DSM_CHECK(cudaMemsetAsync(dL_dalbedo, 0, sizeof(float) * 3 * mesh.n_materials, st));
-  DSM_CHECK(cudaMemsetAsync(ctx->gnormal.p, 0, sizeof(float) * 3 * V, st));
-  DSM_CHECK(cudaMemsetAsync(ctx->gQ.p, 0, sizeof(float) * 20 * DSM_MAX_LIGHTS, st));
-  DSM_CHECK(cudaMemsetAsync(ctx->gdirect.p, 0, sizeof(float) * 3 * DSM_MAX_LIGHTS, st));
-  for (int w = 0; w <= L; ++w) {
-    DSM_CHECK(cudaMemsetAsync(ctx->view[w].gclip.p, 0, sizeof(float4) * V, st));
+  {
+    Clearer cl;
+    cl.add(dL_dverts, sizeof(float) * 3 * V);
+    if (L) cl.add(dL_dlight, sizeof(float) * 6 * L);
+    cl.add(dL_dalbedo, sizeof(float) * 3 * mesh.n_materials);
+    cl.add(ctx->gnormal.p, sizeof(float) * 3 * V);
+    cl.add(ctx->gQ.p, sizeof(float) * 20 * DSM_MAX_LIGHTS);
+    cl.add(ctx->gdirect.p, sizeof(float) * 3 * DSM_MAX_LIGHTS);
+    for (int w = 0; w <= L; ++w) cl.add(ctx->view[w].gclip.p, sizeof(float4) * V);
+    for (int l = 0; l < L; ++l)
+      cl.add(ctx->light[l].gm.p, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2));
+    cl.add(ctx->red.p, sizeof(float) * kRedSlots * red_stride);
+    for (int w = 0; w <= L; ++w)
+      cl.add(ctx->view[w].big_acc.p, (size_t)kMaxBig * kBigSlots * (w < L ? kBigStrideSm : kBigStrideCam) * 4);
+    static_assert(6 + 3 * (DSM_MAX_LIGHTS + 1) <= kMaxClear, "clear list");
+    cl.launch(st);
   }
-  for (int l = 0; l < L; ++l)
-    DSM_CHECK(cudaMemsetAsync(ctx->light[l].gm.p, 0, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2), st));
-  DSM_CHECK(cudaMemsetAsync(ctx->red.p, 0, sizeof(float) * kRedSlots * red_stride, st));
-  for (int w = 0; w <= L; ++w)
-    DSM_CHECK(cudaMemsetAsync(ctx->view[w].big_acc.p, 0,
-                              (size_t)kMaxBig * kBigSlots * (w < L ? kBigStrideSm : kBigStrideCam) * 4, st));
+  DSM_CHECK(cudaGetLastError());
 
   t_clear.stop();
   // ---- final antialiasing adjoint and the shading adjoint
