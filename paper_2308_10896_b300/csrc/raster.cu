@@ -431,27 +431,30 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(int* __restrict__ co
 
 // ------------------------------------------------------------------ tile rasteriser
 // Coverage of pixel centre (Px, Py) by a setup record: integer edge functions
-// with the top-left rule; returns the depth key or ~0.
-__device__ __forceinline__ uint64_t cover_key(const TriSetup& r, long long Px, long long Py) {
-  const int flags = r.flags;
-  const int sg = (flags & 8) ? -1 : 1;
+// with the top-left rule; returns the depth key or ~0.  The record is read as
+// words in TriSetup order (X[3], Y[3], z[3], a2f, ibox, jbox, tri, flags).
+constexpr int kRecWords = 14;       // words of a record the rasteriser uses
+constexpr int kRecStride = 15;      // shared-memory stride (odd: distinct records hit distinct banks)
+__device__ __forceinline__ uint64_t cover_key(const int* w, long long Px, long long Py) {
+  const int flags = w[13];
+  const bool neg = (flags & 8) != 0;
   long long E[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int a = e == 0 ? 1 : (e == 1 ? 2 : 0);
     const int b = e == 0 ? 2 : (e == 1 ? 0 : 1);
-    const int Xa = r.X[a], Ya = r.Y[a];
-    const long long dx = (long long)(r.X[b] - Xa), dy = (long long)(r.Y[b] - Ya);
+    const int Xa = w[a], Ya = w[3 + a];
+    const long long dx = (long long)(w[b] - Xa), dy = (long long)(w[3 + b] - Ya);
     long long v = dx * (Py - Ya) - dy * (Px - Xa);
-    v = sg > 0 ? v : -v;
+    v = neg ? -v : v;
     E[e] = v;
     if (!((v > 0) || (v == 0 && ((flags >> e) & 1)))) return ~0ull;
   }
-  const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(__ll2float_rn(E[0]), r.z[0]),
-                                                __fmul_rn(__ll2float_rn(E[1]), r.z[1])),
-                                      __fmul_rn(__ll2float_rn(E[2]), r.z[2])),
-                            r.a2f);
-  return depth_key(z, r.tri);
+  const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(__ll2float_rn(E[0]), __int_as_float(w[6])),
+                                                __fmul_rn(__ll2float_rn(E[1]), __int_as_float(w[7]))),
+                                      __fmul_rn(__ll2float_rn(E[2]), __int_as_float(w[8]))),
+                            __int_as_float(w[9]));
+  return depth_key(z, w[12]);
 }
 
 __device__ __forceinline__ float key_depth(uint64_t key) {
@@ -473,10 +476,11 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
                                                      int W, int H, const float4* __restrict__ clip,
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf,
                                                      const float* __restrict__ depth, float2* __restrict__ fmap) {
-  __shared__ TriSetup sq[256];
+  __shared__ int sq[256 * kRecStride];
   __shared__ unsigned long long sbest[256];
   __shared__ int spre[257];          // exclusive prefix of the work items per record
-  __shared__ int sbox[256];          // bbox in tile: x0 | x1 << 4 | y0 << 8 | y1 << 12 (tile-local)
+  __shared__ int sbox[256];          // bbox in tile: x0 | x1 << 4 | y0 << 8 | y1 << 12 (tile-local),
+                                     // ceil(2^16 / width) - 1 << 16
   __shared__ int swarp[8];
   const int tile = blockIdx.x;
   const int ti = tile % tilesX, tj = tile / tilesX;
@@ -493,10 +497,14 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
       const int i0 = max(r.ibox & 0xffff, ti0), i1 = min((int)((unsigned)r.ibox >> 16), ti0 + kTile - 1);
       const int j0 = max(r.jbox & 0xffff, tj0), j1 = min((int)((unsigned)r.jbox >> 16), tj0 + kTile - 1);
       if (i0 <= i1 && j0 <= j1) {
-        area = (i1 - i0 + 1) * (j1 - j0 + 1);
-        box = (i0 - ti0) | ((i1 - ti0) << 4) | ((j0 - tj0) << 8) | ((j1 - tj0) << 12);
+        const int wd = i1 - i0 + 1;
+        area = wd * (j1 - j0 + 1);
+        box = (i0 - ti0) | ((i1 - ti0) << 4) | ((j0 - tj0) << 8) | ((j1 - tj0) << 12) |
+              (((65536 + wd - 1) / wd - 1) << 16);
       }
-      sq[tid] = r;
+      const int* rw = reinterpret_cast<const int*>(&r);
+#pragma unroll
+      for (int c = 0; c < kRecWords; ++c) sq[tid * kRecStride + c] = rw[c];
     }
     sbox[tid] = box;
     // block exclusive scan of the areas
@@ -535,8 +543,9 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
       const int b = sbox[rec];
       const int x0 = b & 15, x1 = (b >> 4) & 15, y0 = (b >> 8) & 15;
       const int q = w - spre[rec], wd = x1 - x0 + 1;
-      const int x = x0 + q % wd, y = y0 + q / wd;
-      const uint64_t key = cover_key(sq[rec], (long long)(ti0 + x) * kSubpix + 128,
+      const int qy = (q * (((unsigned)b >> 16) + 1)) >> 16;   // q / wd (exact for q < 256, wd <= 16)
+      const int x = x0 + (q - qy * wd), y = y0 + qy;
+      const uint64_t key = cover_key(sq + rec * kRecStride, (long long)(ti0 + x) * kSubpix + 128,
                                      (long long)(tj0 + y) * kSubpix + 128);
       if (key != ~0ull) atomicMin(&sbest[y * kTile + x], (unsigned long long)key);
     }
