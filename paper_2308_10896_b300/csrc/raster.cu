@@ -291,13 +291,24 @@ __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX
     int o_ty0 = __shfl_sync(kFull, ty0, lo);
     int o_ntx = __shfl_sync(kFull, ntx, lo);
     int o_t = __shfl_sync(kFull, t, lo);
+    int tile = -1;
     if (p < total) {
       int q = p - o_excl;
-      int tile = (o_ty0 + q / o_ntx) * tilesX + o_tx0 + q % o_ntx;
-      if (!kFill) {
-        atomicAdd(&counter[tile], 1);
-      } else {
-        int slot = offset[tile] + atomicAdd(&counter[tile], 1);
+      tile = (o_ty0 + q / o_ntx) * tilesX + o_tx0 + q % o_ntx;
+    }
+    // lanes that hit the same tile (neighbouring triangles usually share
+    // tiles) take one atomic through their lowest lane
+    const unsigned peers = __match_any_sync(kFull, tile);
+    const int leader = __ffs(peers) - 1;
+    const int cnt = __popc(peers);
+    if (!kFill) {
+      if (tile >= 0 && lane == leader) atomicAdd(&counter[tile], cnt);
+    } else {
+      int base_slot = 0;
+      if (tile >= 0 && lane == leader) base_slot = offset[tile] + atomicAdd(&counter[tile], cnt);
+      base_slot = __shfl_sync(kFull, base_slot, leader);
+      if (tile >= 0) {
+        const int slot = base_slot + __popc(peers & ((1u << lane) - 1));
         if (slot < capacity) list[slot] = o_t;
         else atomicExch(&status->capacity_overflow, 1);
       }
@@ -433,6 +444,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(int* __restrict__ co
 // Coverage of pixel centre (Px, Py) by a setup record: integer edge functions
 // with the top-left rule; returns the depth key or ~0.  The record is read as
 // words in TriSetup order (X[3], Y[3], z[3], a2f, ibox, jbox, tri, flags).
+// Correctly rounded int64 -> float32 without the 64-bit conversion (which
+// runs on the slow double-precision pipe): v = h 2^24 + l with h = v >> 24 and
+// 0 <= l < 2^24 both exact in float32, and one fused multiply-add rounds the
+// exact sum h 2^24 + l once, to nearest even.  Exact for |v| < 2^55.
+__device__ __forceinline__ float ll_to_float(long long v) {
+  const float h = __int2float_rn((int)(v >> 24));
+  const float l = __int2float_rn((int)(v & 0xffffff));
+  return __fmaf_rn(h, 16777216.f, l);
+}
+
 constexpr int kRecWords = 14;       // words of a record the rasteriser uses
 constexpr int kRecStride = 15;      // shared-memory stride (odd: distinct records hit distinct banks)
 __device__ __forceinline__ uint64_t cover_key(const int* w, long long Px, long long Py) {
@@ -450,9 +471,9 @@ __device__ __forceinline__ uint64_t cover_key(const int* w, long long Px, long l
     E[e] = v;
     if (!((v > 0) || (v == 0 && ((flags >> e) & 1)))) return ~0ull;
   }
-  const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(__ll2float_rn(E[0]), __int_as_float(w[6])),
-                                                __fmul_rn(__ll2float_rn(E[1]), __int_as_float(w[7]))),
-                                      __fmul_rn(__ll2float_rn(E[2]), __int_as_float(w[8]))),
+  const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(ll_to_float(E[0]), __int_as_float(w[6])),
+                                                __fmul_rn(ll_to_float(E[1]), __int_as_float(w[7]))),
+                                      __fmul_rn(ll_to_float(E[2]), __int_as_float(w[8]))),
                             __int_as_float(w[9]));
   return depth_key(z, w[12]);
 }
