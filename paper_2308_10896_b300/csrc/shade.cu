@@ -254,11 +254,29 @@ __device__ __forceinline__ void warp_add_shared(float* dst, float v) {
 
 constexpr int kShadeStrip = 8;
 
+// Warp reduce-scatter of 32 values per lane by recursive halving: after five
+// exchange steps (16 + 8 + 4 + 2 + 1 shuffles) lane k holds the warp sum of
+// value k.  Far cheaper than 32 separate butterfly reductions.
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float send = upper ? v[k] : v[k + h];
+      const float keep = upper ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(kFull, send, h);
+    }
+  }
+  return v[0];
+}
+
 // Adjoint of shade_kernel, one thread per pixel.  Scatters the texel maps
 // dL/d(m1, m2) (bilinear adjoint), reduces dL/dQ, the direct light terms and
 // the albedo gradient per block (slot copies), and writes the per-pixel
 // dL/d world position and dL/d interpolated normal for shade_scatter_kernel.
-__global__ void __launch_bounds__(256, 5) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g) {
+__global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g) {
   __shared__ float sQ[DSM_MAX_LIGHTS * 20];
   __shared__ float sD[DSM_MAX_LIGHTS * 3];
   __shared__ float sA[kMaxSharedMat * 3];
@@ -362,11 +380,25 @@ __global__ void __launch_bounds__(256, 5) shade_backward_kernel(ShadeArgs a, Sha
         gx.z += Q[2] * gcl[0] + Q[6] * gcl[1] + Q[14] * gcl[3] + Q[18] * gd;
       }
     }
+    // rows 0, 1, 3 and the depth row of dL/dQ (row 2 is zero: the lookup never
+    // reads clip z) and the direct light term, one warp reduce-scatter
+    {
+      float v[32];
 #pragma unroll
-    for (int k = 0; k < 20; ++k) warp_add_shared(&sQ[l * 20 + k], gq[k]);
-    warp_add_shared(&sD[l * 3 + 0], gdir.x);
-    warp_add_shared(&sD[l * 3 + 1], gdir.y);
-    warp_add_shared(&sD[l * 3 + 2], gdir.z);
+      for (int k = 0; k < 8; ++k) v[k] = gq[k];
+#pragma unroll
+      for (int k = 8; k < 16; ++k) v[k] = gq[k + 4];
+      v[16] = gdir.x; v[17] = gdir.y; v[18] = gdir.z;
+#pragma unroll
+      for (int k = 19; k < 32; ++k) v[k] = 0.f;
+      const float r = warp_reduce_scatter32(v);
+      const int lane = threadIdx.x & 31;
+      if (r != 0.f) {
+        if (lane < 8) atomicAdd(&sQ[l * 20 + lane], r);
+        else if (lane < 16) atomicAdd(&sQ[l * 20 + lane + 4], r);
+        else if (lane < 19) atomicAdd(&sD[l * 3 + lane - 16], r);
+      }
+    }
   }
   // albedo: warp-reduced when the warp's active pixels share one material
   const float3 ga = make_float3(gc4.x * rad.x, gc4.y * rad.y, gc4.z * rad.z);
