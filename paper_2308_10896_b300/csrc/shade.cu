@@ -245,22 +245,18 @@ __global__ void shade_kernel(ShadeArgs a, float4* __restrict__ color) {
   color[p] = make_float4(a.albedo[3 * mat] * rad.x, a.albedo[3 * mat + 1] * rad.y, a.albedo[3 * mat + 2] * rad.z, 1.f);
 }
 
-// Warp-sum of v, added once per warp into a shared-memory accumulator.
-__device__ __forceinline__ void warp_add_shared(float* dst, float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(dst, v);
-}
-
 constexpr int kShadeStrip = 8;
 
-// Warp reduce-scatter of 32 values per lane by recursive halving: after five
-// exchange steps (16 + 8 + 4 + 2 + 1 shuffles) lane k holds the warp sum of
-// value k.  Far cheaper than 32 separate butterfly reductions.
-__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+// Warp reduce-scatter of N (16 or 32) values per lane by recursive halving:
+// after the exchange steps (N/2 + ... + 1 shuffles, plus one across the half
+// warps when N = 16) lane k holds the warp sum of value k mod N.  Far cheaper
+// than N separate butterfly reductions.
+template <int N>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[N]) {
+  static_assert(N == 16 || N == 32, "16 or 32 values");
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
+  for (int h = N / 2; h >= 1; h >>= 1) {
     const bool upper = (lane & h) != 0;
 #pragma unroll
     for (int k = 0; k < h; ++k) {
@@ -269,6 +265,7 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
       v[k] = keep + __shfl_xor_sync(kFull, send, h);
     }
   }
+  if (N == 16) v[0] += __shfl_xor_sync(kFull, v[0], 16);
   return v[0];
 }
 
@@ -391,7 +388,7 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
       v[16] = gdir.x; v[17] = gdir.y; v[18] = gdir.z;
 #pragma unroll
       for (int k = 19; k < 32; ++k) v[k] = 0.f;
-      const float r = warp_reduce_scatter32(v);
+      const float r = warp_reduce_scatter<32>(v);
       const int lane = threadIdx.x & 31;
       if (r != 0.f) {
         if (lane < 8) atomicAdd(&sQ[l * 20 + lane], r);
@@ -586,11 +583,16 @@ __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __res
     acc.y += M[1] * gc.x + M[5] * gc.y + M[9] * gz + M[13] * gc.w + (is_light ? M[17] * gd : 0.f);
     acc.z += M[2] * gc.x + M[6] * gc.y + M[10] * gz + M[14] * gc.w + (is_light ? M[18] * gd : 0.f);
     if (is_light) {
-      const float g5[5] = {gc.x, gc.y, 0.f, gc.w, gd};
+      // dL/dQ rows 0, 1, 3 and the depth row (row 2, clip z, has no gradient)
+      const float g4[4] = {gc.x, gc.y, gc.w, gd};
+      float q[16];
 #pragma unroll
-      for (int r = 0; r < 5; ++r)
+      for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) warp_add_shared(&sQ[w * 20 + r * 4 + c], g5[r] * xh[c]);
+        for (int c = 0; c < 4; ++c) q[r * 4 + c] = g4[r] * xh[c];
+      const float sum = warp_reduce_scatter<16>(q);
+      const int lane = threadIdx.x & 31, r = lane >> 2;
+      if (lane < 16 && sum != 0.f) atomicAdd(&sQ[w * 20 + (r < 2 ? r : r + 1) * 4 + (lane & 3)], sum);
     }
   }
   if (ok) {
