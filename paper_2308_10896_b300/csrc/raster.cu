@@ -454,33 +454,64 @@ __device__ __forceinline__ float ll_to_float(long long v) {
   return __fmaf_rn(h, 16777216.f, l);
 }
 
-constexpr int kRecWords = 14;       // words of a record the rasteriser uses
-constexpr int kRecStride = 15;      // shared-memory stride (odd: distinct records hit distinct banks)
-__device__ __forceinline__ uint64_t cover_key(const int* w, long long Px, long long Py) {
-  const int flags = w[13];
-  const bool neg = (flags & 8) != 0;
-  long long E[3];
+__device__ __forceinline__ float key_depth(uint64_t key) {
+  const uint32_t k = (uint32_t)(key >> 32);
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Shared-memory form of a setup record inside one tile: for each edge e the
+// orientation-normalised edge function at the tile's first pixel centre, E0_e,
+// and its steps per pixel along x and y, A_e = -s dy_e 256 and B_e = s dx_e 256
+// (all int64, so E_e(x, y) = E0_e + x A_e + y B_e is the exact integer edge
+// function of Eq. 1's coverage test), then z[3], 2A (float), triangle, flags.
+// The stride is odd so that records of different lanes sit in different banks.
+constexpr int kRecE0 = 0, kRecA = 6, kRecB = 12, kRecZ = 18, kRecA2 = 21, kRecTri = 22, kRecFlags = 23;
+constexpr int kRecStride = 25;
+
+__device__ __forceinline__ long long rec_ll(const int* w, int o) {
+  return (long long)(((unsigned long long)(unsigned)w[o + 1] << 32) | (unsigned)w[o]);
+}
+__device__ __forceinline__ void rec_set_ll(int* w, int o, long long v) {
+  w[o] = (int)(unsigned)(unsigned long long)v;
+  w[o + 1] = (int)(unsigned)((unsigned long long)v >> 32);
+}
+
+__device__ __forceinline__ void rec_stage(const TriSetup& r, long long Px0, long long Py0, int* w) {
+  const long long sg = (r.flags & 8) ? -1 : 1;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int a = e == 0 ? 1 : (e == 1 ? 2 : 0);
     const int b = e == 0 ? 2 : (e == 1 ? 0 : 1);
-    const int Xa = w[a], Ya = w[3 + a];
-    const long long dx = (long long)(w[b] - Xa), dy = (long long)(w[3 + b] - Ya);
-    long long v = dx * (Py - Ya) - dy * (Px - Xa);
-    v = neg ? -v : v;
+    const long long dx = sg * (long long)(r.X[b] - r.X[a]), dy = sg * (long long)(r.Y[b] - r.Y[a]);
+    rec_set_ll(w, kRecE0 + 2 * e, dx * (Py0 - r.Y[a]) - dy * (Px0 - r.X[a]));
+    rec_set_ll(w, kRecA + 2 * e, -dy * kSubpix);
+    rec_set_ll(w, kRecB + 2 * e, dx * kSubpix);
+  }
+  w[kRecZ] = __float_as_int(r.z[0]);
+  w[kRecZ + 1] = __float_as_int(r.z[1]);
+  w[kRecZ + 2] = __float_as_int(r.z[2]);
+  w[kRecA2] = __float_as_int(r.a2f);
+  w[kRecTri] = r.tri;
+  w[kRecFlags] = r.flags;
+}
+
+// Coverage of tile pixel (x, y) by a staged record: integer edge functions
+// with the top-left rule; returns the depth key or ~0.
+__device__ __forceinline__ uint64_t cover_key(const int* w, int x, int y) {
+  const int flags = w[kRecFlags];
+  long long E[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const long long v = rec_ll(w, kRecE0 + 2 * e) + (long long)x * rec_ll(w, kRecA + 2 * e) +
+                        (long long)y * rec_ll(w, kRecB + 2 * e);
     E[e] = v;
     if (!((v > 0) || (v == 0 && ((flags >> e) & 1)))) return ~0ull;
   }
-  const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(ll_to_float(E[0]), __int_as_float(w[6])),
-                                                __fmul_rn(ll_to_float(E[1]), __int_as_float(w[7]))),
-                                      __fmul_rn(ll_to_float(E[2]), __int_as_float(w[8]))),
-                            __int_as_float(w[9]));
-  return depth_key(z, w[12]);
-}
-
-__device__ __forceinline__ float key_depth(uint64_t key) {
-  const uint32_t k = (uint32_t)(key >> 32);
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+  const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(ll_to_float(E[0]), __int_as_float(w[kRecZ])),
+                                                __fmul_rn(ll_to_float(E[1]), __int_as_float(w[kRecZ + 1]))),
+                                      __fmul_rn(ll_to_float(E[2]), __int_as_float(w[kRecZ + 2]))),
+                            __int_as_float(w[kRecA2]));
+  return depth_key(z, w[kRecTri]);
 }
 
 // One 256-thread CTA per 16x16 tile.  The tile's triangle list is read 256
@@ -489,8 +520,13 @@ __device__ __forceinline__ float key_depth(uint64_t key) {
 // stride over (balanced whatever the triangle sizes), and each covered pixel
 // centre folds (depth key, triangle) into the pixel's shared-memory 64-bit
 // minimum.  The minimum is order independent, so the result is deterministic.
+// Items are handed out kChunk at a time: every record marks the chunk
+// position where it starts (or position 0 when it began earlier), and a block
+// prefix maximum turns the marks into the owning record of every item.
 // Each pixel then writes one 16-byte G-buffer texel: id + 1,
 // perspective-correct b0, b1, depth key.
+constexpr int kChunk = 1024;
+
 __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict__ setup,
                                                      const int* __restrict__ offset,
                                                      const int* __restrict__ list, int capacity, int tilesX,
@@ -502,11 +538,13 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
   __shared__ int spre[257];          // exclusive prefix of the work items per record
   __shared__ int sbox[256];          // bbox in tile: x0 | x1 << 4 | y0 << 8 | y1 << 12 (tile-local),
                                      // ceil(2^16 / width) - 1 << 16
+  __shared__ unsigned short sown[kChunk];   // owning record + 1 of each item of the chunk
   __shared__ int swarp[8];
   const int tile = blockIdx.x;
   const int ti = tile % tilesX, tj = tile / tilesX;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ti0 = ti * kTile, tj0 = tj * kTile;
+  const long long Px0 = (long long)ti0 * kSubpix + 128, Py0 = (long long)tj0 * kSubpix + 128;
   sbest[tid] = ~0ull;
   // slots past the list capacity were never written (the fill pass flagged the overflow)
   const int beg = min(offset[tile], capacity), end = min(offset[tile + 1], capacity);
@@ -522,10 +560,8 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
         area = wd * (j1 - j0 + 1);
         box = (i0 - ti0) | ((i1 - ti0) << 4) | ((j0 - tj0) << 8) | ((j1 - tj0) << 12) |
               (((65536 + wd - 1) / wd - 1) << 16);
+        rec_stage(r, Px0, Py0, sq + tid * kRecStride);
       }
-      const int* rw = reinterpret_cast<const int*>(&r);
-#pragma unroll
-      for (int c = 0; c < kRecWords; ++c) sq[tid * kRecStride + c] = rw[c];
     }
     sbox[tid] = box;
     // block exclusive scan of the areas
@@ -549,28 +585,53 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
       if (lane == 7) spre[256] = wi;
     }
     __syncthreads();
-    spre[tid] = swarp[warp] + incl - area;
+    const int my_start = swarp[warp] + incl - area;
+    spre[tid] = my_start;
     __syncthreads();
     const int total = spre[256];
-    int rec = 0;
-    for (int w = tid; w < total; w += 256) {
-      // record owning work item w: last rec with spre[rec] <= w (records only move forward)
-      int lo = rec, hi = 255;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (spre[mid] <= w) lo = mid; else hi = mid - 1;
+    for (int c0 = 0; c0 < total; c0 += kChunk) {
+      // owner marks: record tid starts at chunk position my_start - c0 (or began before it)
+      for (int q = tid; q < kChunk / 2; q += 256) reinterpret_cast<unsigned*>(sown)[q] = 0u;
+      __syncthreads();
+      if (area > 0 && my_start < c0 + kChunk && my_start + area > c0)
+        sown[max(my_start - c0, 0)] = (unsigned short)(tid + 1);
+      __syncthreads();
+      // block prefix maximum over the chunk (4 consecutive entries per thread)
+      {
+        unsigned short* o = sown + 4 * tid;
+        int m0 = o[0], m1 = max(m0, (int)o[1]), m2 = max(m1, (int)o[2]), m3 = max(m2, (int)o[3]);
+        int inc = m3;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int v = __shfl_up_sync(kFull, inc, d);
+          if (lane >= d) inc = max(inc, v);
+        }
+        __syncthreads();   // every thread has read its entries; swarp is free again
+        if (lane == 31) swarp[warp] = inc;
+        __syncthreads();
+        int before = 0;
+        for (int q = 0; q < warp; ++q) before = max(before, swarp[q]);
+        const int lane_before = __shfl_up_sync(kFull, inc, 1);
+        if (lane > 0) before = max(before, lane_before);
+        o[0] = (unsigned short)max(before, m0);
+        o[1] = (unsigned short)max(before, m1);
+        o[2] = (unsigned short)max(before, m2);
+        o[3] = (unsigned short)max(before, m3);
       }
-      rec = lo;
-      const int b = sbox[rec];
-      const int x0 = b & 15, x1 = (b >> 4) & 15, y0 = (b >> 8) & 15;
-      const int q = w - spre[rec], wd = x1 - x0 + 1;
-      const int qy = (q * (((unsigned)b >> 16) + 1)) >> 16;   // q / wd (exact for q < 256, wd <= 16)
-      const int x = x0 + (q - qy * wd), y = y0 + qy;
-      const uint64_t key = cover_key(sq + rec * kRecStride, (long long)(ti0 + x) * kSubpix + 128,
-                                     (long long)(tj0 + y) * kSubpix + 128);
-      if (key != ~0ull) atomicMin(&sbest[y * kTile + x], (unsigned long long)key);
+      __syncthreads();
+      const int n = min(kChunk, total - c0);
+      for (int q = tid; q < n; q += 256) {
+        const int rec = sown[q] - 1;
+        const int b = sbox[rec];
+        const int x0 = b & 15, x1 = (b >> 4) & 15, y0 = (b >> 8) & 15;
+        const int it = c0 + q - spre[rec], wd = x1 - x0 + 1;
+        const int qy = (it * (((unsigned)b >> 16) + 1)) >> 16;   // it / wd (exact for it < 256, wd <= 16)
+        const int x = x0 + (it - qy * wd), y = y0 + qy;
+        const uint64_t key = cover_key(sq + rec * kRecStride, x, y);
+        if (key != ~0ull) atomicMin(&sbest[y * kTile + x], (unsigned long long)key);
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   const int i = ti0 + (tid & 15), j = tj0 + (tid >> 4);
   const uint64_t best = sbest[tid];
