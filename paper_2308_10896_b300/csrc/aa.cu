@@ -104,16 +104,24 @@ struct PairInfo {
   Cross c;
 };
 
+// Whether p is the occluder O of the pair (p, q) (ids differ): the nearer
+// surface by depth key; the background never occludes.
+__device__ __forceinline__ bool pair_p_occ(int i, int j, int ni, int nj, float4 gp, float4 gq) {
+  const int idp = gid(gp), idq = gid(gq);
+  const bool p_first = (ni > i) || (nj > j);
+  const int idA = p_first ? idp : idq, idB = p_first ? idq : idp;
+  const float zA = p_first ? gp.w : gq.w, zB = p_first ? gq.w : gp.w;
+  const bool a_occ = (idB == 0) || (idA != 0 && depth_key(zA, idA - 1) < depth_key(zB, idB - 1));
+  return p_first ? a_occ : !a_occ;
+}
+
 template <bool kGrad>
 __device__ __forceinline__ bool pair_info(const AAArgs& a, int i, int j, int ni, int nj, float4 gp, float4 gq,
                                           PairInfo& pi) {
   const int idp = gid(gp), idq = gid(gq);
   if (idp == idq) return false;
   const bool p_first = (ni > i) || (nj > j);
-  const int idA = p_first ? idp : idq, idB = p_first ? idq : idp;
-  const float zA = p_first ? gp.w : gq.w, zB = p_first ? gq.w : gp.w;
-  const bool a_occ = (idB == 0) || (idA != 0 && depth_key(zA, idA - 1) < depth_key(zB, idB - 1));
-  const bool p_occ = p_first ? a_occ : !a_occ;
+  const bool p_occ = pair_p_occ(i, j, ni, nj, gp, gq);
   const int tri = (p_occ ? idp : idq) - 1;
   const int io = p_occ ? i : ni, jo = p_occ ? j : nj, in = p_occ ? ni : i, jn = p_occ ? nj : j;
   pi.c = find_crossing<kGrad>(a, tri, io, jo, in, jn, nj != j);
@@ -122,115 +130,294 @@ __device__ __forceinline__ bool pair_info(const AAArgs& a, int i, int j, int ni,
   return pi.c.found;
 }
 
-__constant__ int kDI[4] = {-1, 1, 0, 0};
-__constant__ int kDJ[4] = {0, 0, -1, 1};
+// The G-buffer entries a pair decision needs (triangle id, depth key) for a
+// kAAW x kAAH block of pixels and its one-pixel halo, staged in shared memory
+// with coalesced loads: the four neighbours of every pixel are read from here.
+constexpr int kAAW = 32, kAAH = 8;
+struct GTile {
+  int id[kAAH + 2][kAAW + 2];
+  float z[kAAH + 2][kAAW + 2];
+};
+
+__device__ __forceinline__ void load_gtile(const AAArgs& a, GTile& t, int bx0, int by0) {
+  const int tid = threadIdx.y * kAAW + threadIdx.x;
+  for (int k = tid; k < (kAAH + 2) * (kAAW + 2); k += kAAW * kAAH) {
+    const int r = k / (kAAW + 2), c = k - r * (kAAW + 2);
+    const int gi = bx0 - 1 + c, gj = by0 - 1 + r;
+    int id = 0;
+    float z = 0.f;
+    if (gi >= 0 && gj >= 0 && gi < a.W && gj < a.H) {
+      const float4 g = a.gbuf[(size_t)gj * a.W + gi];
+      id = gid(g);
+      z = g.w;
+    }
+    t.id[r][c] = id;
+    t.z[r][c] = z;
+  }
+}
+
+__device__ __forceinline__ float4 gtile_at(const GTile& t, int lx, int ly) {
+  return make_float4(__int_as_float(t.id[ly][lx]), 0.f, 0.f, t.z[ly][lx]);
+}
+
+// Neighbour d of pixel (i, j): left, right, up, down.
+__device__ __forceinline__ int nb_dx(int d) { return d == 0 ? -1 : d == 1 ? 1 : 0; }
+__device__ __forceinline__ int nb_dy(int d) { return d == 2 ? -1 : d == 3 ? 1 : 0; }
+
+// Two passes per antialiasing step.  Only a pair whose occluder triangle has
+// a silhouette edge can have a crossing, and such pairs are few; the code that
+// finds and differentiates crossings needs many registers.  So a light pass
+// (staged G-buffer tile, high occupancy) finishes every pixel without such a
+// pair and appends the others to a work list, and a second pass runs the full
+// pair logic for the listed pixels only.  The second pass's last CTA resets
+// the list counter for the next use.
+__device__ __forceinline__ bool needs_crossing(const AAArgs& a, const GTile& t, int i, int j, int lx, int ly) {
+  const float4 gp = gtile_at(t, lx, ly);
+  bool heavy = false;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const int ni = i + nb_dx(d), nj = j + nb_dy(d);
+    if (ni < 0 || nj < 0 || ni >= a.W || nj >= a.H) continue;
+    const float4 gq = gtile_at(t, lx + nb_dx(d), ly + nb_dy(d));
+    if (gid(gq) == gid(gp)) continue;
+    const int tri = gid(pair_p_occ(i, j, ni, nj, gp, gq) ? gp : gq) - 1;
+    heavy |= a.sil[tri] != 0;
+  }
+  return heavy;
+}
+
+// Warp-aggregated append of `value` for the lanes with `want`; every lane of
+// the warp must call it.
+__device__ __forceinline__ void list_append(const AAWork& w, bool want, int value) {
+  const unsigned m = __ballot_sync(kFull, want);
+  if (!m) return;
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(w.count, __popc(m));
+  base = __shfl_sync(kFull, base, leader);
+  if (want) w.list[base + __popc(m & ((1u << lane) - 1))] = value;
+}
+
+// End of a second pass: the last CTA to finish clears the counters.
+__device__ __forceinline__ void work_done(const AAWork& w) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(w.done, 1) == (int)gridDim.x - 1) {
+      *w.count = 0;
+      *w.done = 0;
+    }
+  }
+}
 
 // ------------------------------------------------------------------ forward
 // Every pixel gathers the gains of the (up to 4) pairs it belongs to: if t > 1/2
 // the neighbour-side pixel N gains (t - 1/2)(c_O - c_N), else O gains
-// (1/2 - t)(c_N - c_O).  The four neighbours' G-buffer entries are fetched
-// together up front; the neighbour's colour only where a pair blends.
-template <typename V, typename ColorOf>
-__device__ __forceinline__ V aa_pixel(const AAArgs& a, int i, int j, float4 gp, V cp, ColorOf color_of) {
-  float4 gq[4];
-  size_t qi[4];
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    const int ni = i + (d == 0 ? -1 : d == 1 ? 1 : 0), nj = j + (d == 2 ? -1 : d == 3 ? 1 : 0);
-    const bool ok = ni >= 0 && nj >= 0 && ni < a.W && nj < a.H;
-    qi[d] = ok ? (size_t)nj * a.W + ni : (size_t)j * a.W + i;   // out of range: the pixel itself (same id)
-    gq[d] = a.gbuf[qi[d]];
+// (1/2 - t)(c_N - c_O).  aa_pair_gain: the gain of pixel (i, j) from its pair
+// in direction d.
+template <typename V>
+__device__ __forceinline__ V aa_pair_gain(const AAArgs& a, int i, int j, int d, float4 gp, V cp,
+                                          const V* __restrict__ color) {
+  const int ni = i + nb_dx(d), nj = j + nb_dy(d);
+  if (ni < 0 || nj < 0 || ni >= a.W || nj >= a.H) return V{};
+  const size_t q = (size_t)nj * a.W + ni;
+  const float4 gq = a.gbuf[q];
+  PairInfo pi;
+  if (!pair_info<false>(a, i, j, ni, nj, gp, gq, pi)) return V{};
+  const float tt = pi.c.t;
+  if (tt > 0.5f) {
+    if (!pi.p_occ) return vscale(vsub(color[q], cp), tt - 0.5f);   // p = N, cq = c_O
+  } else {
+    if (pi.p_occ) return vscale(vsub(color[q], cp), 0.5f - tt);    // p = O, cq = c_N
   }
-  V acc = cp;
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    if (gid(gq[d]) == gid(gp)) continue;
-    const int ni = i + (d == 0 ? -1 : d == 1 ? 1 : 0), nj = j + (d == 2 ? -1 : d == 3 ? 1 : 0);
-    PairInfo pi;
-    if (!pair_info<false>(a, i, j, ni, nj, gp, gq[d], pi)) continue;
-    const float t = pi.c.t;
-    if (t > 0.5f) {
-      if (!pi.p_occ) acc = vadd(acc, vscale(vsub(color_of(qi[d], gq[d]), cp), t - 0.5f));   // p = N, cq = c_O
-    } else {
-      if (pi.p_occ) acc = vadd(acc, vscale(vsub(color_of(qi[d], gq[d]), cp), 0.5f - t));    // p = O, cq = c_N
-    }
+  return V{};
+}
+
+__device__ __forceinline__ float2 shfl_xor_v(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(kFull, v.x, m), __shfl_xor_sync(kFull, v.y, m));
+}
+__device__ __forceinline__ float4 shfl_xor_v(float4 v, int m) {
+  return make_float4(__shfl_xor_sync(kFull, v.x, m), __shfl_xor_sync(kFull, v.y, m), __shfl_xor_sync(kFull, v.z, m),
+                     __shfl_xor_sync(kFull, v.w, m));
+}
+
+// Second passes: four consecutive lanes take one listed pixel, one pair
+// direction each, and sum their terms with two shuffles.  `body(k, d, act)`
+// runs for every lane (act: the lane has an item).
+template <typename Body>
+__device__ __forceinline__ void for_listed_pairs(const AAWork& w, Body body) {
+  const int n = *(volatile int*)w.count;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per_sweep = gridDim.x * blockDim.x / 4;
+  for (int k0 = 0; k0 < n; k0 += per_sweep) {
+    const int k = k0 + gtid / 4;
+    body(k, gtid & 3, k < n);
   }
-  return acc;
 }
 
 template <typename V>
-__global__ void __launch_bounds__(256, 6) aa_forward_kernel(AAArgs a, const V* __restrict__ color, V* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= a.W || j >= a.H) return;
-  const size_t p = (size_t)j * a.W + i;
-  out[p] = aa_pixel<V>(a, i, j, a.gbuf[p], color[p], [&](size_t q, float4) { return color[q]; });
+__global__ void __launch_bounds__(256) aa_forward_kernel(AAArgs a, const V* __restrict__ color, V* __restrict__ out,
+                                                         AAWork w) {
+  __shared__ GTile t;
+  const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
+  const int i = bx0 + threadIdx.x, j = by0 + threadIdx.y;
+  const bool in = i < a.W && j < a.H;
+  const size_t p = in ? (size_t)j * a.W + i : 0;
+  const V cp = in ? color[p] : V{};
+  load_gtile(a, t, bx0, by0);
+  __syncthreads();
+  const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, threadIdx.y + 1);
+  if (in && !heavy) out[p] = cp;
+  list_append(w, heavy, (int)p);
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) aa_forward_list_kernel(AAArgs a, const V* __restrict__ color,
+                                                              V* __restrict__ out, AAWork w) {
+  for_listed_pairs(w, [&](int k, int d, bool act) {
+    V g{};
+    V cp{};
+    int p = 0;
+    if (act) {
+      p = w.list[k];
+      const int j = p / a.W, i = p - j * a.W;
+      cp = color[p];
+      g = aa_pair_gain<V>(a, i, j, d, a.gbuf[p], cp, color);
+    }
+    g = vadd(g, shfl_xor_v(g, 1));
+    g = vadd(g, shfl_xor_v(g, 2));
+    if (act && d == 0) out[p] = vadd(cp, g);
+  });
+  work_done(w);
 }
 
 // ------------------------------------------------------------------ adjoint
 // dL/dc_p = g_p + the pair terms; the t-gradient of each pair is scattered once
 // (by its left / top pixel) onto the clip coordinates of the edge endpoints.
+// aa_pair_adjoint: the term of pixel (i, j) from its pair in direction d.
 template <typename V>
-__device__ __forceinline__ V aa_adjoint_pixel(const AAArgs& a, int i, int j, const V* color, const V* gout,
-                                              float4* gclip) {
-  const size_t p = (size_t)j * a.W + i;
-  const float4 gp = a.gbuf[p];
-  const V g_p = gout[p];
-  V acc = g_p;
-  for (int d = 0; d < 4; ++d) {
-    const int ni = i + kDI[d], nj = j + kDJ[d];
-    if (ni < 0 || nj < 0 || ni >= a.W || nj >= a.H) continue;
-    const size_t q = (size_t)nj * a.W + ni;
-    const float4 gq = a.gbuf[q];
-    PairInfo pi;
-    if (!pair_info<true>(a, i, j, ni, nj, gp, gq, pi)) continue;
-    const V g_q = gout[q];
-    const float t = pi.c.t;
-    const V gO = pi.p_occ ? g_p : g_q, gN = pi.p_occ ? g_q : g_p;
-    float dLdt;
-    if (t > 0.5f) {            // Delta_N = (t - 1/2)(c_O - c_N)
-      acc = vadd(acc, vscale(gN, pi.p_occ ? (t - 0.5f) : -(t - 0.5f)));
-      dLdt = 0.f;
-      if (pi.p_is_first && pi.c.active) {
-        const V cp = color[p], cq = color[q];
-        const V cO = pi.p_occ ? cp : cq, cN = pi.p_occ ? cq : cp;
-        dLdt = dotv(gN, vsub(cO, cN));
-      }
-    } else {                   // Delta_O = (1/2 - t)(c_N - c_O)
-      acc = vadd(acc, vscale(gO, pi.p_occ ? -(0.5f - t) : (0.5f - t)));
-      dLdt = 0.f;
-      if (pi.p_is_first && pi.c.active) {
-        const V cp = color[p], cq = color[q];
-        const V cO = pi.p_occ ? cp : cq, cN = pi.p_occ ? cq : cp;
-        dLdt = dotv(gO, vsub(cO, cN));
-      }
+__device__ __forceinline__ V aa_pair_adjoint(const AAArgs& a, int i, int j, int d, float4 gp, V g_p, const V* color,
+                                             const V* gout, float4* gclip) {
+  const int ni = i + nb_dx(d), nj = j + nb_dy(d);
+  if (ni < 0 || nj < 0 || ni >= a.W || nj >= a.H) return V{};
+  const size_t p = (size_t)j * a.W + i, q = (size_t)nj * a.W + ni;
+  const float4 gq = a.gbuf[q];
+  PairInfo pi;
+  if (!pair_info<true>(a, i, j, ni, nj, gp, gq, pi)) return V{};
+  const V g_q = gout[q];
+  const float tt = pi.c.t;
+  const V gO = pi.p_occ ? g_p : g_q, gN = pi.p_occ ? g_q : g_p;
+  V term;
+  float dLdt = 0.f;
+  if (tt > 0.5f) {            // Delta_N = (t - 1/2)(c_O - c_N)
+    term = vscale(gN, pi.p_occ ? (tt - 0.5f) : -(tt - 0.5f));
+    if (pi.p_is_first && pi.c.active) {
+      const V cp = color[p], cq = color[q];
+      const V cO = pi.p_occ ? cp : cq, cN = pi.p_occ ? cq : cp;
+      dLdt = dotv(gN, vsub(cO, cN));
     }
-    if (dLdt != 0.f) {
-      const float4 ca = a.clip[pi.c.va], cb = a.clip[pi.c.vb];
-      atomic_add4(&gclip[pi.c.va], screen_to_clip_grad(ca, dLdt * pi.c.dt[0], dLdt * pi.c.dt[1], a.W, a.H));
-      atomic_add4(&gclip[pi.c.vb], screen_to_clip_grad(cb, dLdt * pi.c.dt[2], dLdt * pi.c.dt[3], a.W, a.H));
+  } else {                   // Delta_O = (1/2 - t)(c_N - c_O)
+    term = vscale(gO, pi.p_occ ? -(0.5f - tt) : (0.5f - tt));
+    if (pi.p_is_first && pi.c.active) {
+      const V cp = color[p], cq = color[q];
+      const V cO = pi.p_occ ? cp : cq, cN = pi.p_occ ? cq : cp;
+      dLdt = dotv(gO, vsub(cO, cN));
     }
   }
-  return acc;
+  if (dLdt != 0.f) {
+    const float4 ca = a.clip[pi.c.va], cb = a.clip[pi.c.vb];
+    atomic_add4(&gclip[pi.c.va], screen_to_clip_grad(ca, dLdt * pi.c.dt[0], dLdt * pi.c.dt[1], a.W, a.H));
+    atomic_add4(&gclip[pi.c.vb], screen_to_clip_grad(cb, dLdt * pi.c.dt[2], dLdt * pi.c.dt[3], a.W, a.H));
+  }
+  return term;
 }
 
-__global__ void __launch_bounds__(256, 6) aa_backward4_kernel(AAArgs a, const float4* __restrict__ color, const float4* __restrict__ gout,
-                                    float4* __restrict__ gcolor, float4* __restrict__ gclip, int aa) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= a.W || j >= a.H) return;
-  const size_t p = (size_t)j * a.W + i;
-  gcolor[p] = aa ? aa_adjoint_pixel<float4>(a, i, j, color, gout, gclip) : gout[p];
+// First pass of the colour adjoint (camera view): pixels without a crossing
+// pass dL/dcolour through.
+__global__ void __launch_bounds__(256) aa_backward4_kernel(AAArgs a, const float4* __restrict__ gout,
+                                                           float4* __restrict__ gcolor, AAWork w) {
+  __shared__ GTile t;
+  const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
+  const int i = bx0 + threadIdx.x, j = by0 + threadIdx.y;
+  const bool in = i < a.W && j < a.H;
+  const size_t p = in ? (size_t)j * a.W + i : 0;
+  const float4 g_p = in ? gout[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+  load_gtile(a, t, bx0, by0);
+  __syncthreads();
+  const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, threadIdx.y + 1);
+  if (in && !heavy) gcolor[p] = g_p;
+  list_append(w, heavy, (int)p);
+}
+
+__global__ void __launch_bounds__(256) aa_backward4_list_kernel(AAArgs a, const float4* __restrict__ color,
+                                                                const float4* __restrict__ gout,
+                                                                float4* __restrict__ gcolor,
+                                                                float4* __restrict__ gclip, AAWork w) {
+  for_listed_pairs(w, [&](int k, int d, bool act) {
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f), g_p = g;
+    int p = 0;
+    if (act) {
+      p = w.list[k];
+      const int j = p / a.W, i = p - j * a.W;
+      g_p = gout[p];
+      g = aa_pair_adjoint<float4>(a, i, j, d, a.gbuf[p], g_p, color, gout, gclip);
+    }
+    g = vadd(g, shfl_xor_v(g, 1));
+    g = vadd(g, shfl_xor_v(g, 2));
+    if (act && d == 0) gcolor[p] = vadd(g_p, g);
+  });
+  work_done(w);
 }
 
 // Adjoint of the shadow-map antialiasing: dL/d(f, f^2) per texel (the pair
 // t-gradients go to the light-space clip coordinates of the edge endpoints),
-// folded into dL/df = g.x + 2 f g.y (f^2 = f f).  One thread per texel.
-__global__ void __launch_bounds__(256, 6) sm_aa_adjoint_kernel(AAArgs a, const float2* __restrict__ fmap, const float2* __restrict__ gft,
-                                     float4* __restrict__ gclip, float* __restrict__ gf_out, int aa) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= a.W || j >= a.H) return;
-  const size_t p = (size_t)j * a.W + i;
-  const float2 gc = aa ? aa_adjoint_pixel<float2>(a, i, j, fmap, gft, gclip) : gft[p];
-  gf_out[p] = gc.x + 2.f * fmap[p].x * gc.y;
+// folded into dL/df = g.x + 2 f g.y (f^2 = f f).
+__global__ void __launch_bounds__(256) sm_aa_adjoint_kernel(AAArgs a, const float2* __restrict__ fmap,
+                                                            const float2* __restrict__ gft,
+                                                            float* __restrict__ gf_out, AAWork w) {
+  __shared__ GTile t;
+  const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
+  const int i = bx0 + threadIdx.x, j = by0 + threadIdx.y;
+  const bool in = i < a.W && j < a.H;
+  const size_t p = in ? (size_t)j * a.W + i : 0;
+  const float2 g_p = in ? gft[p] : make_float2(0.f, 0.f);
+  const float f = in ? fmap[p].x : 0.f;
+  load_gtile(a, t, bx0, by0);
+  __syncthreads();
+  const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, threadIdx.y + 1);
+  if (in && !heavy) gf_out[p] = g_p.x + 2.f * f * g_p.y;
+  list_append(w, heavy, (int)p);
+}
+
+__global__ void __launch_bounds__(256) sm_aa_adjoint_list_kernel(AAArgs a, const float2* __restrict__ fmap,
+                                                                 const float2* __restrict__ gft,
+                                                                 float4* __restrict__ gclip,
+                                                                 float* __restrict__ gf_out, AAWork w) {
+  for_listed_pairs(w, [&](int k, int d, bool act) {
+    float2 g = make_float2(0.f, 0.f), g_p = g;
+    int p = 0;
+    if (act) {
+      p = w.list[k];
+      const int j = p / a.W, i = p - j * a.W;
+      g_p = gft[p];
+      g = aa_pair_adjoint<float2>(a, i, j, d, a.gbuf[p], g_p, fmap, gft, gclip);
+    }
+    g = vadd(g, shfl_xor_v(g, 1));
+    g = vadd(g, shfl_xor_v(g, 2));
+    if (act && d == 0) {
+      const float2 gc = vadd(g_p, g);
+      gf_out[p] = gc.x + 2.f * fmap[p].x * gc.y;
+    }
+  });
+  work_done(w);
+}
+
+// Without antialiasing the adjoint only folds dL/d(f, f^2) into dL/df.
+__global__ void sm_fold_kernel(const float2* __restrict__ fmap, const float2* __restrict__ gft,
+                               float* __restrict__ gf_out, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) gf_out[p] = gft[p].x + 2.f * fmap[p].x * gft[p].y;
 }
 
 // Adjoint of the interpolation f = sum_k b_k d_k: dL/dd_k = b_k dL/df onto the
@@ -345,21 +532,33 @@ __global__ void sm_big_resolve_kernel(const int* __restrict__ tris, const int* _
 // ------------------------------------------------------------------ launchers
 static inline dim3 grid2(int W, int H, dim3 b) { return dim3((W + b.x - 1) / b.x, (H + b.y - 1) / b.y); }
 
-void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, cudaStream_t st) {
-  dim3 b(32, 8);
-  count_launches(1);
-  aa_forward_kernel<float2><<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, out);
+constexpr int kListGrid = 148 * 8;   // CTAs of a second pass (grid-stride over the list)
+
+template <typename V>
+static void launch_aa_forward(const AAArgs& a, const V* color, V* out, const AAWork& w, cudaStream_t st) {
+  dim3 b(kAAW, kAAH);
+  count_launches(2);
+  aa_forward_kernel<V><<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, out, w);
+  aa_forward_list_kernel<V><<<kListGrid, 256, 0, st>>>(a, color, out, w);
 }
-void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, cudaStream_t st) {
-  dim3 b(32, 8);
-  count_launches(1);
-  aa_forward_kernel<float4><<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, out);
+void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, const AAWork& w, cudaStream_t st) {
+  launch_aa_forward<float2>(a, color, out, w, st);
+}
+void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, const AAWork& w, cudaStream_t st) {
+  launch_aa_forward<float4>(a, color, out, w, st);
 }
 void launch_sm_aa_adjoint(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
-                          int aa, cudaStream_t st) {
-  dim3 b(32, 8);
-  count_launches(1);
-  sm_aa_adjoint_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, fmap, gft, gclip, gf_out, aa);
+                          int aa, const AAWork& w, cudaStream_t st) {
+  if (!aa) {
+    const int n = a.W * a.H;
+    count_launches(1);
+    sm_fold_kernel<<<(n + 255) / 256, 256, 0, st>>>(fmap, gft, gf_out, n);
+    return;
+  }
+  dim3 b(kAAW, kAAH);
+  count_launches(2);
+  sm_aa_adjoint_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, fmap, gft, gf_out, w);
+  sm_aa_adjoint_list_kernel<<<kListGrid, 256, 0, st>>>(a, fmap, gft, gclip, gf_out, w);
 }
 
 void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* depth, float4* gclip,
@@ -372,10 +571,11 @@ void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* dep
 }
 
 void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
-                         int aa, cudaStream_t st) {
-  dim3 b(32, 8);
-  count_launches(1);
-  aa_backward4_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, gout, gcolor, gclip, aa);
+                         const AAWork& w, cudaStream_t st) {
+  dim3 b(kAAW, kAAH);
+  count_launches(2);
+  aa_backward4_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, gout, gcolor, w);
+  aa_backward4_list_kernel<<<kListGrid, 256, 0, st>>>(a, color, gout, gcolor, gclip, w);
 }
 
 }  // namespace dsm

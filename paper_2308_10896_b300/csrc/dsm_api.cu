@@ -51,7 +51,9 @@ struct ViewBufs {
   int W = 0, H = 0, tilesX = 0, tilesY = 0;
   Buf clip, snap, depth, setup, orient, sil, count, offset, list, gbuf, gclip;
   Buf big_index, big_tri, big_acc;
+  Buf aa_list, aa_ctr;      // antialiasing work list and its two counters
   int list_cap = 0;
+  AAWork aa_work() { return AAWork{aa_list.as<int>(), aa_ctr.as<int>(), aa_ctr.as<int>() + 1}; }
 };
 
 struct LightBufs {
@@ -369,6 +371,13 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   if (is_light) {
     DSM_CHECK(v.depth.ensure(Vn * 4));
   }
+  DSM_CHECK(v.aa_list.ensure((size_t)W * H * 4));
+  if (!v.aa_ctr.p) {
+    // the counters start at zero; every second pass leaves them at zero
+    DSM_CHECK(v.aa_ctr.ensure(2 * sizeof(int)));
+    DSM_CHECK(cudaMemset(v.aa_ctr.p, 0, 2 * sizeof(int)));
+    DSM_CHECK(cudaDeviceSynchronize());
+  }
   if (v.list_cap == 0) {
     const size_t cap = 2 * Tn + 2 * tiles + 1024;
     DSM_CHECK(v.list.ensure(cap * 4));
@@ -498,7 +507,7 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
       if (params->aa_shadow) {
         AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh->tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(),
                   v.clip.as<float4>()};
-        launch_aa_forward2(aa, lb.fmap.as<float2>(), lb.ftilde.as<float2>(), vst);
+        launch_aa_forward2(aa, lb.fmap.as<float2>(), lb.ftilde.as<float2>(), v.aa_work(), vst);
       } else {
         DSM_CHECK(cudaMemcpyAsync(lb.ftilde.p, lb.fmap.p, (size_t)v.W * v.H * sizeof(float2),
                                   cudaMemcpyDeviceToDevice, vst));
@@ -532,7 +541,7 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
   if (params->aa_final) {
     AAArgs aa{cv.gbuf.as<float4>(), Wc, Hc, mesh->tris, cv.sil.as<uint8_t>(), cv.snap.as<VertSnap>(),
               cv.clip.as<float4>()};
-    launch_aa_forward4(aa, ctx->camcolor.as<float4>(), reinterpret_cast<float4*>(image), st);
+    launch_aa_forward4(aa, ctx->camcolor.as<float4>(), reinterpret_cast<float4*>(image), cv.aa_work(), st);
   } else {
     DSM_CHECK(cudaMemcpyAsync(image, ctx->camcolor.p, (size_t)Wc * Hc * sizeof(float4), cudaMemcpyDeviceToDevice, st));
   }
@@ -602,8 +611,13 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   ViewBufs& cv = ctx->view[L];
   StageTimer t_faa(ctx, ST_BWD_FINAL_AA, st);
   AAArgs caa{cv.gbuf.as<float4>(), Wc, Hc, mesh.tris, cv.sil.as<uint8_t>(), cv.snap.as<VertSnap>(), cv.clip.as<float4>()};
-  launch_aa_backward4(caa, ctx->camcolor.as<float4>(), reinterpret_cast<const float4*>(dL_dimage),
-                      ctx->gcolor.as<float4>(), cv.gclip.as<float4>(), ctx->params.aa_final, st);
+  if (ctx->params.aa_final) {
+    launch_aa_backward4(caa, ctx->camcolor.as<float4>(), reinterpret_cast<const float4*>(dL_dimage),
+                        ctx->gcolor.as<float4>(), cv.gclip.as<float4>(), cv.aa_work(), st);
+  } else {
+    DSM_CHECK(cudaMemcpyAsync(ctx->gcolor.p, dL_dimage, (size_t)Wc * Hc * sizeof(float4), cudaMemcpyDeviceToDevice,
+                              st));
+  }
   t_faa.stop();
   ShadeArgs sa{};
   sa.gbuf = cv.gbuf.as<float4>();
@@ -647,7 +661,7 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
     {
       StageTimer t(ctx, ST_BWD_SM_AA, vst);
       launch_sm_aa_adjoint(aa, lb.fmap.as<float2>(), lb.gft.as<float2>(), v.gclip.as<float4>(), lb.tmp.as<float>(),
-                           ctx->params.aa_shadow, vst);
+                           ctx->params.aa_shadow, v.aa_work(), vst);
     }
     {
       StageTimer t(ctx, ST_BWD_SM_INTERP, vst);

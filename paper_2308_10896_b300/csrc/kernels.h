@@ -82,6 +82,14 @@ struct BigArgs {
   int view;
 };
 
+// Work list of a two-pass antialiasing step: pixel indices appended by the
+// first pass, count and done counters (zero between uses).
+struct AAWork {
+  int* list;
+  int* count;
+  int* done;
+};
+
 struct AAArgs {
   const float4* gbuf;
   int W, H;
@@ -109,14 +117,14 @@ void launch_raster(const TriSetup* setup, const int* offset, const int* list, in
                    cudaStream_t st);
 
 // shadow-map interpolation and antialiasing
-void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, cudaStream_t st);
-void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, cudaStream_t st);
+void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, const AAWork& w, cudaStream_t st);
+void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, const AAWork& w, cudaStream_t st);
 void launch_sm_aa_adjoint(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
-                          int aa, cudaStream_t st);
+                          int aa, const AAWork& w, cudaStream_t st);
 void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* depth, float4* gclip,
                               const BigArgs& big, cudaStream_t st);
 void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
-                         int aa, cudaStream_t st);
+                         const AAWork& w, cudaStream_t st);
 
 // separable filter
 void make_filter_args(double sigma, int radius, int kind, int boundary, FilterArgs* fa);
