@@ -442,26 +442,41 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
   for (int k = 0; k < 16; ++k) cm.v[k] = cam->clip[k];
   count_launches(1);
   set_matrix_kernel<<<1, 32, 0, st>>>(cm, viewM + 20 * L);
-  launch_vertex_normals(mesh->verts, V, mesh->tris, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
-                        ctx->vnormal.as<float>(), st);
-
-  // ---- per view on its own stream: transform, setup, bin count, scan
-  // (the light views and the camera view are independent until shading)
+  // every view at once: transform, triangle setup, silhouettes (and zeroed
+  // tile counters for the binning)
   DevStatus* dstat = ctx->status.as<DevStatus>();
-  DSM_CHECK(cudaMemsetAsync(dstat->big_count, 0, sizeof(dstat->big_count), st));
+  {
+    ViewSetupArgs va{};
+    va.n = L + 1;
+    for (int w = 0; w <= L; ++w) {
+      ViewBufs& v = ctx->view[w];
+      va.W[w] = v.W; va.H[w] = v.H; va.tiles[w] = v.tilesX * v.tilesY;
+      va.clip[w] = v.clip.as<float4>();
+      va.snap[w] = v.snap.as<VertSnap>();
+      va.depth[w] = w < L ? v.depth.as<float>() : nullptr;
+      va.setup[w] = v.setup.as<TriSetup>();
+      va.orient[w] = v.orient.as<int8_t>();
+      va.sil[w] = v.sil.as<uint8_t>();
+      va.count[w] = v.count.as<int>();
+    }
+    launch_setup_all(mesh->verts, V, mesh->tris, T, ctx->adj.as<int>(), viewM, va, dstat, st);
+  }
   t_setup.stop();
+
+  // ---- per view on its own stream: bin count, scan (the light views and the
+  // camera view are independent until shading)
   DSM_CHECK(ensure_streams(ctx));
   DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, L + 1));
+  {
+    cudaStream_t cst = view_stream(ctx, L, st);
+    StageTimer tn(ctx, ST_SETUP, cst);
+    launch_vertex_normals(mesh->verts, V, mesh->tris, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
+                          ctx->vnormal.as<float>(), cst);
+  }
   for (int w = 0; w <= L; ++w) {
     ViewBufs& v = ctx->view[w];
     cudaStream_t vst = view_stream(ctx, w, st);
-    const bool is_light = w < L;
     StageTimer tw(ctx, ST_SETUP, vst);
-    launch_transform(mesh->verts, V, viewM + 20 * w, v.W, v.H, v.clip.as<float4>(), v.snap.as<VertSnap>(),
-                     is_light ? v.depth.as<float>() : nullptr, vst);
-    launch_tri_setup(mesh->tris, T, v.snap.as<VertSnap>(), v.W, v.H, v.setup.as<TriSetup>(),
-                     v.orient.as<int8_t>(), ctx->adj.as<int>(), v.sil.as<uint8_t>(), vst);
-    DSM_CHECK(cudaMemsetAsync(v.count.p, 0, (size_t)v.tilesX * v.tilesY * 4, vst));
     launch_bin_count(v.setup.as<TriSetup>(), T, v.tilesX, v.count.as<int>(), dstat, w, v.big_index.as<int>(),
                      v.big_tri.as<int>(), vst);
     launch_scan(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), dstat, w, vst);

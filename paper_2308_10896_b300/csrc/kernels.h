@@ -99,11 +99,24 @@ struct AAArgs {
   const float4* clip;
 };
 
+// Per-view pointers and sizes for the fused setup of all views of a frame.
+constexpr int kMaxViews = DSM_MAX_LIGHTS + 1;
+struct ViewSetupArgs {
+  int n;
+  int W[kMaxViews], H[kMaxViews], tiles[kMaxViews];
+  float4* clip[kMaxViews];
+  VertSnap* snap[kMaxViews];
+  float* depth[kMaxViews];        // light views only (camera: NULL)
+  TriSetup* setup[kMaxViews];
+  int8_t* orient[kMaxViews];
+  uint8_t* sil[kMaxViews];
+  int* count[kMaxViews];          // tile counters, zeroed by the setup
+};
+// Transform, triangle setup and silhouettes of every view; also zeroes the tile
+// counters and the big-triangle counts for the binning that follows.
+void launch_setup_all(const float* verts, int V, const int* tris, int T, const int* adj, const float* viewM,
+                      const ViewSetupArgs& a, DevStatus* status, cudaStream_t st);
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, cudaStream_t st);
-void launch_transform(const float* verts, int V, const float* M20, int W, int H, float4* clip, VertSnap* snap,
-                      float* depth, cudaStream_t st);
-void launch_tri_setup(const int* tris, int T, const VertSnap* snap, int W, int H, TriSetup* setup, int8_t* orient,
-                      const int* adj, uint8_t* sil, cudaStream_t st);
 void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, int view,
                       int* big_index, int* big_tri, cudaStream_t st);
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st);

@@ -1,5 +1,6 @@
 // Light cameras, pinned vertex transform, triangle setup, binning and the tile
 // rasteriser (Eq. 1: nearest surface per pixel centre).
+#include <algorithm>
 #include "dsm.h"
 #include "common.cuh"
 #include "kernels.h"
@@ -151,44 +152,32 @@ __device__ __forceinline__ float pinned_row(const float* M, float x, float y, fl
   return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], x), __fmul_rn(M[1], y)), __fmul_rn(M[2], z)), M[3]);
 }
 
-// clip = M [v, 1] with separately rounded float32 operations, snapped 24.8
-// screen position, and (lights) the depth row.
-__global__ void transform_kernel(const float* __restrict__ verts, int V, const float* __restrict__ M20,
-                                 int W, int H, float4* __restrict__ clip, VertSnap* __restrict__ snap,
-                                 float* __restrict__ depth) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V) return;
-  float x = verts[3 * v], y = verts[3 * v + 1], z = verts[3 * v + 2];
-  float c0 = pinned_row(M20 + 0, x, y, z);
-  float c1 = pinned_row(M20 + 4, x, y, z);
-  float c2 = pinned_row(M20 + 8, x, y, z);
-  float c3 = pinned_row(M20 + 12, x, y, z);
-  clip[v] = make_float4(c0, c1, c2, c3);
-  if (depth) depth[v] = pinned_row(M20 + 16, x, y, z);
-  float nx = __fdiv_rn(c0, c3), ny = __fdiv_rn(c1, c3), nz = __fdiv_rn(c2, c3);
-  float sx = __fmul_rn(__fadd_rn(__fmul_rn(0.5f, nx), 0.5f), (float)W);
-  float sy = __fmul_rn(__fsub_rn(0.5f, __fmul_rn(0.5f, ny)), (float)H);
-  float fx = __fmul_rn(sx, (float)kSubpix), fy = __fmul_rn(sy, (float)kSubpix);
-  bool ok = (c3 >= kWMin) && (fabsf(fx) <= (float)kGuard) && (fabsf(fy) <= (float)kGuard);
+// Screen position of a clip-space vertex snapped to 24.8 fixed point, ndc z,
+// and validity (w >= kWMin and inside the guard band).
+__device__ __forceinline__ VertSnap snap_vertex(float c0, float c1, float c2, float c3, int W, int H) {
+  const float nx = __fdiv_rn(c0, c3), ny = __fdiv_rn(c1, c3), nz = __fdiv_rn(c2, c3);
+  const float sx = __fmul_rn(__fadd_rn(__fmul_rn(0.5f, nx), 0.5f), (float)W);
+  const float sy = __fmul_rn(__fsub_rn(0.5f, __fmul_rn(0.5f, ny)), (float)H);
+  const float fx = __fmul_rn(sx, (float)kSubpix), fy = __fmul_rn(sy, (float)kSubpix);
+  const bool ok = (c3 >= kWMin) && (fabsf(fx) <= (float)kGuard) && (fabsf(fy) <= (float)kGuard);
   VertSnap s;
   s.X = ok ? __float2int_rn(fx) : 0;
   s.Y = ok ? __float2int_rn(fy) : 0;
   s.z = nz;
   s.ok = ok ? 1 : 0;
-  snap[v] = s;
+  return s;
 }
 
 // ------------------------------------------------------------------ triangle setup
-__global__ void tri_setup_kernel(const int* __restrict__ tris, int T, const VertSnap* __restrict__ snap,
-                                 int W, int H, TriSetup* __restrict__ setup, int8_t* __restrict__ orient) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= T) return;
-  int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
-  VertSnap s0 = snap[v0], s1 = snap[v1], s2 = snap[v2];
+// Setup record of triangle t in one view from its snapped corners: bbox,
+// orientation-normalised top-left flags, float 2A; orient = sign of 2A (0:
+// culled).
+__device__ __forceinline__ void setup_triangle(int t, VertSnap s0, VertSnap s1, VertSnap s2, int W, int H,
+                                               TriSetup* __restrict__ out, int8_t* __restrict__ orient) {
   long long area2 = (long long)(s1.X - s0.X) * (s2.Y - s0.Y) - (long long)(s1.Y - s0.Y) * (s2.X - s0.X);
   bool culled = !(s0.ok && s1.ok && s2.ok) || area2 == 0;
   int sg = area2 > 0 ? 1 : -1;
-  orient[t] = culled ? 0 : (int8_t)sg;
+  *orient = culled ? 0 : (int8_t)sg;
   TriSetup r;
   r.X[0] = s0.X; r.X[1] = s1.X; r.X[2] = s2.X;
   r.Y[0] = s0.Y; r.Y[1] = s1.Y; r.Y[2] = s2.Y;
@@ -217,25 +206,77 @@ __global__ void tri_setup_kernel(const int* __restrict__ tris, int T, const Vert
   r.ibox = (i0 & 0xffff) | (i1 << 16);
   r.jbox = (j0 & 0xffff) | (j1 << 16);
   r.flags = flags;
-  setup[t] = r;
+  *out = r;
 }
+
 
 // Silhouette edge mask per triangle: bit e set when edge e (v0v1, v1v2, v2v0)
 // is a boundary / non-manifold edge, the triangle across it is culled, or the
 // two triangles have opposite screen orientation.
-__global__ void silhouette_kernel(const int* __restrict__ adj, int T, const int8_t* __restrict__ orient,
-                                  uint8_t* __restrict__ sil) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= T) return;
+// Silhouette edges of triangle t (bit e): boundary or non-manifold edge, a
+// culled neighbour across it, or the neighbour's opposite screen orientation.
+__device__ __forceinline__ uint8_t silhouette_mask(const int8_t* __restrict__ orient, int t, int a0, int a1, int a2) {
+  const int8_t o = orient[t];
+  const int adj[3] = {a0, a1, a2};
   int m = 0;
-  int8_t o = orient[t];
+#pragma unroll
   for (int e = 0; e < 3; ++e) {
-    int a = adj[3 * t + e];
+    const int a = adj[e];
     if (a < 0) { m |= 1 << e; continue; }
-    int8_t oa = orient[a];
+    const int8_t oa = orient[a];
     if (oa == 0 || oa != o) m |= 1 << e;
   }
-  sil[t] = (uint8_t)m;
+  return (uint8_t)m;
+}
+
+
+// ------------------------------------------------------------------ all views at once
+// The per-view setup kernels above, fused over the views of one frame: each
+// vertex / triangle is read once and processed for every view (the view loop
+// is unrolled so that the per-view pointers stay in parameter space).
+__global__ void transform_all_kernel(const float* __restrict__ verts, int V, const float* __restrict__ viewM,
+                                     ViewSetupArgs a) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const float x = verts[3 * v], y = verts[3 * v + 1], z = verts[3 * v + 2];
+#pragma unroll
+  for (int w = 0; w < kMaxViews; ++w) {
+    if (w >= a.n) break;
+    const float* M20 = viewM + 20 * w;
+    const float c0 = pinned_row(M20 + 0, x, y, z);
+    const float c1 = pinned_row(M20 + 4, x, y, z);
+    const float c2 = pinned_row(M20 + 8, x, y, z);
+    const float c3 = pinned_row(M20 + 12, x, y, z);
+    a.clip[w][v] = make_float4(c0, c1, c2, c3);
+    if (a.depth[w]) a.depth[w][v] = pinned_row(M20 + 16, x, y, z);
+    a.snap[w][v] = snap_vertex(c0, c1, c2, c3, a.W[w], a.H[w]);
+  }
+}
+
+__global__ void tri_setup_all_kernel(const int* __restrict__ tris, int T, ViewSetupArgs a, DevStatus* status) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // the binning's tile counters and big-triangle counts start this frame at zero
+  for (int w = 0; w < a.n; ++w)
+    for (int k = t; k < a.tiles[w]; k += gridDim.x * blockDim.x) a.count[w][k] = 0;
+  if (t < DSM_MAX_LIGHTS + 1) status->big_count[t] = 0;
+  if (t >= T) return;
+  const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
+#pragma unroll
+  for (int w = 0; w < kMaxViews; ++w) {
+    if (w >= a.n) break;
+    setup_triangle(t, a.snap[w][v0], a.snap[w][v1], a.snap[w][v2], a.W[w], a.H[w], a.setup[w] + t, a.orient[w] + t);
+  }
+}
+
+__global__ void silhouette_all_kernel(const int* __restrict__ adj, int T, ViewSetupArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const int a0 = adj[3 * t], a1 = adj[3 * t + 1], a2 = adj[3 * t + 2];
+#pragma unroll
+  for (int w = 0; w < kMaxViews; ++w) {
+    if (w >= a.n) break;
+    a.sil[w][t] = silhouette_mask(a.orient[w], t, a0, a1, a2);
+  }
 }
 
 // ------------------------------------------------------------------ binning
@@ -333,31 +374,34 @@ __device__ __forceinline__ bool tile_may_cover(const TriSetup& r, int tx, int ty
   return true;
 }
 
-// Binning of the big triangles: blockIdx.y selects the triangle, the tiles of
-// its bbox are spread over gridDim.x blocks; tiles it cannot cover are skipped.
+// Binning of the big triangles: blockIdx.y strides over the triangles, the
+// tiles of a bbox are spread over gridDim.x blocks; tiles it cannot cover are
+// skipped.
+constexpr int kBigGridY = 4;
 template <bool kFill>
 __global__ void bin_big_kernel(const TriSetup* __restrict__ setup, const int* __restrict__ big_tri,
                                const DevStatus* __restrict__ status, int view, int tilesX,
                                int* __restrict__ counter, const int* __restrict__ offset, int* __restrict__ list,
                                int capacity, DevStatus* wstatus) {
-  const int b = blockIdx.y;
-  if (b >= min(status->big_count[view], kMaxBig)) return;
-  const int t = big_tri[b];
-  const TriSetup r = setup[t];
-  const int i0 = r.ibox & 0xffff, i1 = (unsigned)r.ibox >> 16, j0 = r.jbox & 0xffff, j1 = (unsigned)r.jbox >> 16;
-  const int tx0 = i0 >> kTileLog2, ty0 = j0 >> kTileLog2;
-  const int ntx = (i1 >> kTileLog2) - tx0 + 1, nty = (j1 >> kTileLog2) - ty0 + 1;
-  const int n = ntx * nty;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const int tx = tx0 + q % ntx, ty = ty0 + q / ntx;
-    if (!tile_may_cover(r, tx, ty)) continue;
-    const int tile = ty * tilesX + tx;
-    if (!kFill) {
-      atomicAdd(&counter[tile], 1);
-    } else {
-      const int slot = offset[tile] + atomicAdd(&counter[tile], 1);
-      if (slot < capacity) list[slot] = t;
-      else atomicExch(&wstatus->capacity_overflow, 1);
+  const int nb = min(status->big_count[view], kMaxBig);
+  for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+    const int t = big_tri[b];
+    const TriSetup r = setup[t];
+    const int i0 = r.ibox & 0xffff, i1 = (unsigned)r.ibox >> 16, j0 = r.jbox & 0xffff, j1 = (unsigned)r.jbox >> 16;
+    const int tx0 = i0 >> kTileLog2, ty0 = j0 >> kTileLog2;
+    const int ntx = (i1 >> kTileLog2) - tx0 + 1, nty = (j1 >> kTileLog2) - ty0 + 1;
+    const int n = ntx * nty;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+      const int tx = tx0 + q % ntx, ty = ty0 + q / ntx;
+      if (!tile_may_cover(r, tx, ty)) continue;
+      const int tile = ty * tilesX + tx;
+      if (!kFill) {
+        atomicAdd(&counter[tile], 1);
+      } else {
+        const int slot = offset[tile] + atomicAdd(&counter[tile], 1);
+        if (slot < capacity) list[slot] = t;
+        else atomicExch(&wstatus->capacity_overflow, 1);
+      }
     }
   }
 }
@@ -661,20 +705,18 @@ void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* 
   light_setup_kernel<<<a.n, 64, 0, st>>>(params, a, out, viewM);
 }
 
-void launch_transform(const float* verts, int V, const float* M20, int W, int H, float4* clip, VertSnap* snap,
-                      float* depth, cudaStream_t st) {
-  if (V == 0) return;
+void launch_setup_all(const float* verts, int V, const int* tris, int T, const int* adj, const float* viewM,
+                      const ViewSetupArgs& a, DevStatus* status, cudaStream_t st) {
+  if (V > 0) {
+    count_launches(1);
+    transform_all_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, viewM, a);
+  }
   count_launches(1);
-  transform_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, M20, W, H, clip, snap, depth);
-}
-
-void launch_tri_setup(const int* tris, int T, const VertSnap* snap, int W, int H, TriSetup* setup,
-                      int8_t* orient, const int* adj, uint8_t* sil, cudaStream_t st) {
-  if (T == 0) return;
-  count_launches(1);
-  tri_setup_kernel<<<(T + 255) / 256, 256, 0, st>>>(tris, T, snap, W, H, setup, orient);
-  count_launches(1);
-  silhouette_kernel<<<(T + 255) / 256, 256, 0, st>>>(adj, T, orient, sil);
+  tri_setup_all_kernel<<<std::max((T + 255) / 256, 64), 256, 0, st>>>(tris, T, a, status);
+  if (T > 0) {
+    count_launches(1);
+    silhouette_all_kernel<<<(T + 255) / 256, 256, 0, st>>>(adj, T, a);
+  }
 }
 
 void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, int view,
@@ -684,7 +726,7 @@ void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, De
   bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, nullptr, nullptr, 0, status, view,
                                                      big_index, big_tri);
   count_launches(1);
-  bin_big_kernel<false><<<dim3(16, kMaxBig), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, nullptr,
+  bin_big_kernel<false><<<dim3(16, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, nullptr,
                                                           nullptr, 0, status);
 }
 
@@ -701,7 +743,7 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, con
   bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, offset, list, capacity, status, view,
                                                     const_cast<int*>(big_index), const_cast<int*>(big_tri));
   count_launches(1);
-  bin_big_kernel<true><<<dim3(16, kMaxBig), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, offset, list,
+  bin_big_kernel<true><<<dim3(16, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, offset, list,
                                                          capacity, status);
 }
 
