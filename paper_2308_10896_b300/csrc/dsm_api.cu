@@ -362,7 +362,7 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   DSM_CHECK(v.orient.ensure(Tn));
   DSM_CHECK(v.sil.ensure(Tn));
   DSM_CHECK(v.count.ensure(tiles * 4));
-  DSM_CHECK(v.offset.ensure((tiles + 1) * 4));
+  DSM_CHECK(v.offset.ensure(2 * tiles * 4));
   DSM_CHECK(v.gbuf.ensure((size_t)W * H * sizeof(float4)));
   DSM_CHECK(v.gclip.ensure(Vn * sizeof(float4)));
   DSM_CHECK(v.big_index.ensure(Tn * 4));

@@ -119,6 +119,8 @@ void launch_setup_all(const float* verts, int V, const int* tris, int T, const i
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, cudaStream_t st);
 void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, int view,
                       int* big_index, int* big_tri, cudaStream_t st);
+// Segment of every tile in the view's triangle list (begin, end) from the
+// per-tile counts; clears the counts for the fill pass.
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st);
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
                      int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,

@@ -255,10 +255,13 @@ __global__ void transform_all_kernel(const float* __restrict__ verts, int V, con
 
 __global__ void tri_setup_all_kernel(const int* __restrict__ tris, int T, ViewSetupArgs a, DevStatus* status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  // the binning's tile counters and big-triangle counts start this frame at zero
+  // the binning's tile counters, big-triangle counts and list totals start this frame at zero
   for (int w = 0; w < a.n; ++w)
     for (int k = t; k < a.tiles[w]; k += gridDim.x * blockDim.x) a.count[w][k] = 0;
-  if (t < DSM_MAX_LIGHTS + 1) status->big_count[t] = 0;
+  if (t < DSM_MAX_LIGHTS + 1) {
+    status->big_count[t] = 0;
+    status->needed_pairs[t] = 0;
+  }
   if (t >= T) return;
   const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
 #pragma unroll
@@ -406,81 +409,28 @@ __global__ void bin_big_kernel(const TriSetup* __restrict__ setup, const int* __
   }
 }
 
-// Single-CTA exclusive scan of the tile counts; offset[n] = total pairs.  Also
-// records the total for the host and clears the counters for the fill pass.
-// Each thread owns kScanPer consecutive counts of a chunk (loaded together,
-// scanned in registers); one block scan of the per-thread sums per chunk.
-constexpr int kScanThreads = 1024, kScanPer = 16;
-__global__ void __launch_bounds__(kScanThreads) scan_kernel(int* __restrict__ count, int n, int* __restrict__ offset,
-                                                            DevStatus* status, int view) {
-  __shared__ int warp_sums[32];
-  __shared__ int carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = 0; base < n; base += kScanThreads * kScanPer) {
-    const int i0 = base + threadIdx.x * kScanPer;
-    int v[kScanPer];
-    if (i0 + kScanPer <= n) {
+// List segments of the tiles: tile k owns [offset[k], offset[n + k]) of the
+// view's triangle list.  Segments are handed out by one atomic per warp on the
+// view's running total (status->needed_pairs, zeroed by the setup), so they
+// are not in tile order (nothing depends on that order).  Also clears the
+// counters for the fill pass; the running total tells the host the list size.
+__global__ void alloc_kernel(int* __restrict__ count, int n, int* __restrict__ offset, DevStatus* status,
+                             int view) {
+  const int tile = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+  const int c = tile < n ? count[tile] : 0;
+  int incl = c;
 #pragma unroll
-      for (int k = 0; k < kScanPer; k += 4) {
-        const int4 q = *reinterpret_cast<const int4*>(count + i0 + k);
-        v[k] = q.x; v[k + 1] = q.y; v[k + 2] = q.z; v[k + 3] = q.w;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < kScanPer; ++k) v[k] = i0 + k < n ? count[i0 + k] : 0;
-    }
-    int tsum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-      const int c = v[k];
-      v[k] = tsum;          // exclusive within the thread
-      tsum += c;
-    }
-    int incl = tsum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += u;
-    }
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      const int w = warp_sums[lane];
-      int wi = w;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(kFull, wi, o);
-        if (lane >= o) wi += u;
-      }
-      warp_sums[lane] = wi - w;
-    }
-    __syncthreads();
-    const int c = carry;
-    const int tbase = c + warp_sums[warp] + incl - tsum;
-    if (i0 + kScanPer <= n) {
-#pragma unroll
-      for (int k = 0; k < kScanPer; k += 4) {
-        *reinterpret_cast<int4*>(offset + i0 + k) =
-            make_int4(tbase + v[k], tbase + v[k + 1], tbase + v[k + 2], tbase + v[k + 3]);
-        *reinterpret_cast<int4*>(count + i0 + k) = make_int4(0, 0, 0, 0);
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < kScanPer; ++k)
-        if (i0 + k < n) {
-          offset[i0 + k] = tbase + v[k];
-          count[i0 + k] = 0;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == kScanThreads - 1) carry = tbase + tsum;
-    __syncthreads();
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
   }
-  if (threadIdx.x == 0) {
-    offset[n] = carry;
-    status->needed_pairs[view] = carry;
+  int base = 0;
+  if (lane == 31 && incl > 0) base = atomicAdd(&status->needed_pairs[view], incl);
+  base = __shfl_sync(kFull, base, 31);
+  if (tile < n) {
+    offset[tile] = base + incl - c;
+    offset[n + tile] = base + incl;
+    count[tile] = 0;
   }
 }
 
@@ -591,7 +541,7 @@ __global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict_
   const long long Px0 = (long long)ti0 * kSubpix + 128, Py0 = (long long)tj0 * kSubpix + 128;
   sbest[tid] = ~0ull;
   // slots past the list capacity were never written (the fill pass flagged the overflow)
-  const int beg = min(offset[tile], capacity), end = min(offset[tile + 1], capacity);
+  const int beg = min(offset[tile], capacity), end = min(offset[gridDim.x + tile], capacity);
   for (int base = beg; base < end; base += 256) {
     const int k = base + tid;
     int area = 0, box = 0;
@@ -732,7 +682,7 @@ void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, De
 
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st) {
   count_launches(1);
-  scan_kernel<<<1, kScanThreads, 0, st>>>(count, n, offset, status, view);
+  alloc_kernel<<<(n + 255) / 256, 256, 0, st>>>(count, n, offset, status, view);
 }
 
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
