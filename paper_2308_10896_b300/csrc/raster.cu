@@ -521,7 +521,7 @@ __device__ __forceinline__ uint64_t cover_key(const int* w, int x, int y) {
 // perspective-correct b0, b1, depth key.
 constexpr int kChunk = 1024;
 
-__global__ void __launch_bounds__(256) raster_kernel(const TriSetup* __restrict__ setup,
+__global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restrict__ setup,
                                                      const int* __restrict__ offset,
                                                      const int* __restrict__ list, int capacity, int tilesX,
                                                      int W, int H, const float4* __restrict__ clip,
