@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(256) shade_scatter_kernel(ShadeArgs a, ShadeGr
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kShadeStrip;
   const bool col_ok = i < a.W;
   CamScatter sc{a.tris, g.dverts, g.gnormal, g.gclip, g.big_acc, scatter_slot(kBigSlots)};
-  BigRun<30, 2> run;
+  BigRun<30, 1> run;
   big_run_reset(run);
   TriCache tc;
   for (int srow = 0; srow < kShadeStrip; ++srow) {
