@@ -457,9 +457,8 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kStrip;
   const bool col_ok = i < a.W;
   SmScatter sc{a.tris, gclip, big_acc, scatter_slot(kBigSlots)};
-  BigRun<12, 2> run;
+  BigRun<12, 1> run;
   big_run_reset(run);
-  int ct = -1;                      // triangle whose vertex data are cached
   float4 cc[3];
   float cd[3];
   // prefetch of row j0
@@ -484,13 +483,12 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
     const int id = gid(g);
     if (col_ok && j < a.H && id && gf != 0.f) {
       t = id - 1;
-      if (t != ct) {
-        ct = t;
-        for (int k = 0; k < 3; ++k) {
-          const int v = a.tris[3 * t + k];
-          cc[k] = a.clip[v];
-          cd[k] = depth[v];
-        }
+      // the triangle's corners are reloaded per texel (L1 hits): keeping them
+      // live across rows costs more in occupancy than the loads
+      for (int k = 0; k < 3; ++k) {
+        const int v = a.tris[3 * t + k];
+        cc[k] = a.clip[v];
+        cd[k] = depth[v];
       }
       const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
       const Bary r = bary_at(cc[0], cc[1], cc[2], px, py);
