@@ -73,7 +73,7 @@ struct dsm_ctx {
   Buf adj, vf_off, vf_list;
   ViewBufs view[DSM_MAX_LIGHTS + 1];
   LightBufs light[DSM_MAX_LIGHTS];
-  Buf lights_dev, viewM, status, vnormal, camcolor, gcolor, gnormal, gN, gface, gQ, gdirect, red, pgrad;
+  Buf lights_dev, viewM, status, vnormal, vnlen, camcolor, gcolor, gnormal, gN, gface, gQ, gdirect, red, pgrad;
   Buf scratch_dverts, scratch_dlight, scratch_dalbedo, filter_tmp;
   DevStatus* hstatus = nullptr;
   // state of the last forward
@@ -265,13 +265,13 @@ void dsm_destroy(dsm_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
   Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->status,
-                 &ctx->vnormal, &ctx->camcolor, &ctx->gcolor, &ctx->gnormal, &ctx->gN, &ctx->gface, &ctx->gQ,
-                 &ctx->gdirect, &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo,
+                 &ctx->vnormal, &ctx->vnlen, &ctx->camcolor, &ctx->gcolor, &ctx->gnormal, &ctx->gN, &ctx->gface,
+                 &ctx->gQ, &ctx->gdirect, &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo,
                  &ctx->filter_tmp, &ctx->red, &ctx->pgrad};
   for (Buf* b : bufs) b->release();
   for (auto& v : ctx->view) {
     Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
-                 &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc};
+                 &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr};
     for (Buf* b : vb) b->release();
   }
   for (auto& l : ctx->light) {
@@ -417,6 +417,7 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
   DSM_CHECK(ctx->lights_dev.ensure(sizeof(LightDev) * DSM_MAX_LIGHTS));
   DSM_CHECK(ctx->viewM.ensure(sizeof(float) * 20 * (DSM_MAX_LIGHTS + 1)));
   DSM_CHECK(ctx->vnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
+  DSM_CHECK(ctx->vnlen.ensure(sizeof(float) * std::max(V, 1)));
   DSM_CHECK(ctx->camcolor.ensure((size_t)Wc * Hc * sizeof(float4)));
 
   // ---- light cameras and the camera matrix
@@ -471,7 +472,7 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
     cudaStream_t cst = view_stream(ctx, L, st);
     StageTimer tn(ctx, ST_SETUP, cst);
     launch_vertex_normals(mesh->verts, V, mesh->tris, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
-                          ctx->vnormal.as<float>(), cst);
+                          ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), cst);
   }
   for (int w = 0; w <= L; ++w) {
     ViewBufs& v = ctx->view[w];
@@ -697,7 +698,8 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   launch_vertex_backward(mesh.verts, V, ctx->viewM.as<float>(), L + 1, L, gp, dL_dverts, ctx->red.as<float>(),
                          red_stride, st);
   launch_normals_backward(mesh.verts, V, mesh.tris, T, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
-                          ctx->gnormal.as<float>(), ctx->gN.as<float>(), ctx->gface.as<float>(), dL_dverts, st);
+                          ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), ctx->gnormal.as<float>(),
+                          ctx->gN.as<float>(), ctx->gface.as<float>(), dL_dverts, st);
   launch_red_reduce(ctx->red.as<float>(), red_stride, L, n_mat_red, ctx->gQ.as<float>(), ctx->gdirect.as<float>(),
                     dL_dalbedo, st);
   launch_light_grad(ctx->lights_dev.as<LightDev>(), L, ctx->gQ.as<float>(), ctx->gdirect.as<float>(), dL_dlight, st);

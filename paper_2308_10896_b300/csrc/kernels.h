@@ -149,10 +149,10 @@ void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, 
 
 // normals, shading, vertex gradients
 void launch_vertex_normals(const float* verts, int V, const int* tris, const int* vf_off, const int* vf_list,
-                           float* vnormal, cudaStream_t st);
+                           float* vnormal, float* vlen, cudaStream_t st);
 void launch_normals_backward(const float* verts, int V, const int* tris, int T, const int* vf_off,
-                             const int* vf_list, const float* gnormal, float* gN, float* gface, float* dverts,
-                             cudaStream_t st);
+                             const int* vf_list, const float* vnormal, const float* vlen, const float* gnormal,
+                             float* gN, float* gface, float* dverts, cudaStream_t st);
 void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st);
 void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);
 void launch_shade_scatter(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);

@@ -380,7 +380,7 @@ __device__ __forceinline__ bool tile_may_cover(const TriSetup& r, int tx, int ty
 // Binning of the big triangles: blockIdx.y strides over the triangles, the
 // tiles of a bbox are spread over gridDim.x blocks; tiles it cannot cover are
 // skipped.
-constexpr int kBigGridY = 4;
+constexpr int kBigGridX = 64, kBigGridY = 2;
 template <bool kFill>
 __global__ void bin_big_kernel(const TriSetup* __restrict__ setup, const int* __restrict__ big_tri,
                                const DevStatus* __restrict__ status, int view, int tilesX,
@@ -676,7 +676,7 @@ void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, De
   bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, nullptr, nullptr, 0, status, view,
                                                      big_index, big_tri);
   count_launches(1);
-  bin_big_kernel<false><<<dim3(16, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, nullptr,
+  bin_big_kernel<false><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, nullptr,
                                                           nullptr, 0, status);
 }
 
@@ -693,7 +693,7 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, con
   bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, offset, list, capacity, status, view,
                                                     const_cast<int*>(big_index), const_cast<int*>(big_tri));
   count_launches(1);
-  bin_big_kernel<true><<<dim3(16, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, offset, list,
+  bin_big_kernel<true><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, offset, list,
                                                          capacity, status);
 }
 

@@ -20,7 +20,7 @@ __device__ __forceinline__ float3 face_normal(const float* __restrict__ verts, c
 // Area-weighted sum of the incident face normals (cross(v1 - v0, v2 - v0)), normalised.
 __global__ void vertex_normals_kernel(const float* __restrict__ verts, int V, const int* __restrict__ tris,
                                       const int* __restrict__ off, const int* __restrict__ lst,
-                                      float* __restrict__ vn, float* __restrict__ Nraw) {
+                                      float* __restrict__ vn, float* __restrict__ vlen) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
   float3 s = make_float3(0.f, 0.f, 0.f);
@@ -31,35 +31,27 @@ __global__ void vertex_normals_kernel(const float* __restrict__ verts, int V, co
   const float l = sqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
   const float il = l > 0.f ? 1.f / l : 1.f;
   vn[3 * v] = s.x * il; vn[3 * v + 1] = s.y * il; vn[3 * v + 2] = s.z * il;
-  if (Nraw) { Nraw[3 * v] = s.x; Nraw[3 * v + 1] = s.y; Nraw[3 * v + 2] = s.z; }
+  vlen[v] = l;
 }
 
 // dL/d(unnormalised vertex normal) from dL/d(unit normal).
-__global__ void normals_bwd_vertex_kernel(const float* __restrict__ verts, int V, const int* __restrict__ tris,
-                                          const int* __restrict__ off, const int* __restrict__ lst,
+// dL/d unnormalised vertex normal N from dL/d unit normal n = N / |N|:
+// (g - n (n.g)) / |N|, with n and |N| saved by the forward.
+__global__ void normals_bwd_vertex_kernel(const float* __restrict__ vn, const float* __restrict__ vlen, int V,
                                           const float* __restrict__ gn, float* __restrict__ gN) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
-  float3 s = make_float3(0.f, 0.f, 0.f);
-  for (int k = off[v]; k < off[v + 1]; ++k) {
-    const float3 f = face_normal(verts, tris, lst[k]);
-    s.x += f.x; s.y += f.y; s.z += f.z;
-  }
-  const float l = sqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
-  float3 r = make_float3(0.f, 0.f, 0.f);
+  const float l = vlen[v];
+  const float3 g = make_float3(gn[3 * v], gn[3 * v + 1], gn[3 * v + 2]);
+  float3 r = g;
   if (l > 0.f) {
     const float il = 1.f / l;
-    const float3 n = make_float3(s.x * il, s.y * il, s.z * il);
-    const float3 g = make_float3(gn[3 * v], gn[3 * v + 1], gn[3 * v + 2]);
+    const float3 n = make_float3(vn[3 * v], vn[3 * v + 1], vn[3 * v + 2]);
     const float d = n.x * g.x + n.y * g.y + n.z * g.z;
     r = make_float3((g.x - n.x * d) * il, (g.y - n.y * d) * il, (g.z - n.z * d) * il);
-  } else {
-    r = make_float3(gn[3 * v], gn[3 * v + 1], gn[3 * v + 2]);
   }
   gN[3 * v] = r.x; gN[3 * v + 1] = r.y; gN[3 * v + 2] = r.z;
 }
-
-// G_t = sum of dL/dN over the face's corners.
 __global__ void normals_bwd_face_kernel(const int* __restrict__ tris, int T, const float* __restrict__ gN,
                                         float* __restrict__ gface) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -652,18 +644,18 @@ __global__ void l2_kernel(const float* __restrict__ img, const float* __restrict
 static inline dim3 grid2(int W, int H, dim3 b) { return dim3((W + b.x - 1) / b.x, (H + b.y - 1) / b.y); }
 
 void launch_vertex_normals(const float* verts, int V, const int* tris, const int* vf_off, const int* vf_list,
-                           float* vnormal, cudaStream_t st) {
+                           float* vnormal, float* vlen, cudaStream_t st) {
   if (V == 0) return;
   count_launches(1);
-  vertex_normals_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, tris, vf_off, vf_list, vnormal, nullptr);
+  vertex_normals_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, tris, vf_off, vf_list, vnormal, vlen);
 }
 
 void launch_normals_backward(const float* verts, int V, const int* tris, int T, const int* vf_off,
-                             const int* vf_list, const float* gnormal, float* gN, float* gface, float* dverts,
-                             cudaStream_t st) {
+                             const int* vf_list, const float* vnormal, const float* vlen, const float* gnormal,
+                             float* gN, float* gface, float* dverts, cudaStream_t st) {
   if (V == 0 || T == 0) return;
   count_launches(1);
-  normals_bwd_vertex_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, tris, vf_off, vf_list, gnormal, gN);
+  normals_bwd_vertex_kernel<<<(V + 255) / 256, 256, 0, st>>>(vnormal, vlen, V, gnormal, gN);
   count_launches(1);
   normals_bwd_face_kernel<<<(T + 255) / 256, 256, 0, st>>>(tris, T, gN, gface);
   count_launches(1);
