@@ -81,20 +81,21 @@ def stage_bytes(sc) -> dict:
         # setup records and lists read once, one 16-byte G-buffer texel written per pixel, and per light
         # texel the depth sample (f, f^2), 8 bytes
         "raster": views * (64 * T + 4 * T) + 16 * (texels + WH) + 8 * texels,
-        # G-buffer 16 + (f, f^2) 8 in, (f~, (f^2)~) 8 out
-        "sm_antialias": texels * (16 + 8 + 8),
-        # one tiled pass: f~ in, moments out
-        "filter": texels * (8 + 8),
+        # detection: G-buffer 16 in, listed-flag byte out (the list pass touches ~1 % of texels: not counted)
+        "sm_antialias": texels * (16 + 1),
+        # one tiled pass: (f, f^2) 8 + flag 1 in, moments 8 out
+        "filter": texels * (8 + 1 + 8),
         "shade": WH * (16 + 16) + 8 * texels + 24 * V,
-        "final_antialias": WH * (16 + 16 + 16),
+        "final_antialias": WH * (16 + 16 + 16 + 1),
         "bwd_clear": 8 * texels + views * 16 * V + 4 * L * V + 24 * V,
-        "bwd_final_antialias": WH * (16 + 16 + 16 + 16),
+        "bwd_final_antialias": WH * (1 + 16 + 16),
         # per pixel: G-buffer 16 + dL/dcolour 16 in, pgrad 32 out; texel gradient scatter 8 per texel
         "bwd_shade": WH * (16 + 16 + 32) + 8 * texels + 40 * V,
         "bwd_shade_scatter": WH * (16 + 32) + 40 * V,
-        "bwd_filter": texels * (8 + 8),
-        # G-buffer 16 + f 8 + dL/df~ 8 in, dL/df 4 out
-        "bwd_sm_antialias": texels * (16 + 8 + 8 + 4),
+        # dm 8 + f 8 in, dL/df~ 8 + dL/df 4 out
+        "bwd_filter": texels * (8 + 8 + 8 + 4),
+        # list pass only (~1 % of texels): not counted
+        "bwd_sm_antialias": 0,
         # G-buffer 16 + dL/df 4 in, vertex gradients
         "bwd_sm_interp": texels * (16 + 4) + 20 * V * L,
         "bwd_vertex": views * 16 * V + 4 * L * V + 12 * V + 24 * V + 12 * T,

@@ -164,13 +164,18 @@ __device__ __forceinline__ float4 gtile_at(const GTile& t, int lx, int ly) {
 __device__ __forceinline__ int nb_dx(int d) { return d == 0 ? -1 : d == 1 ? 1 : 0; }
 __device__ __forceinline__ int nb_dy(int d) { return d == 2 ? -1 : d == 3 ? 1 : 0; }
 
-// Two passes per antialiasing step.  Only a pair whose occluder triangle has
-// a silhouette edge can have a crossing, and such pairs are few; the code that
-// finds and differentiates crossings needs many registers.  So a light pass
-// (staged G-buffer tile, high occupancy) finishes every pixel without such a
-// pair and appends the others to a work list, and a second pass runs the full
-// pair logic for the listed pixels only.  The second pass's last CTA resets
-// the list counter for the next use.
+// Antialiasing runs as a detection pass and a list pass.  Only a pair whose
+// occluder triangle has a silhouette edge can have a crossing, and such pairs
+// are few (about 1 % of pixels in the benchmark scenes); the code that finds
+// and differentiates crossings needs many registers.  So a light detection
+// pass (staged G-buffer tile, high occupancy) flags the pixels with such a
+// pair (hflag) and appends them to the view's work list, and the list passes
+// run the full pair logic for the listed pixels only.  Every other pixel's
+// antialiased value is its own value, so the consumers read the unmodified
+// map there: the moment filter substitutes the list pass's values at flagged
+// texels, and the backward's filter transpose writes dL/df directly.  The list
+// depends only on the G-buffer, so the backward reuses the forward's list; the
+// setup of the next frame clears its counter.
 __device__ __forceinline__ bool needs_crossing(const AAArgs& a, const GTile& t, int i, int j, int lx, int ly) {
   const float4 gp = gtile_at(t, lx, ly);
   bool heavy = false;
@@ -197,18 +202,6 @@ __device__ __forceinline__ void list_append(const AAWork& w, bool want, int valu
   if (lane == leader) base = atomicAdd(w.count, __popc(m));
   base = __shfl_sync(kFull, base, leader);
   if (want) w.list[base + __popc(m & ((1u << lane) - 1))] = value;
-}
-
-// End of a second pass: the last CTA to finish clears the counters.
-__device__ __forceinline__ void work_done(const AAWork& w) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(w.done, 1) == (int)gridDim.x - 1) {
-      *w.count = 0;
-      *w.done = 0;
-    }
-  }
 }
 
 // ------------------------------------------------------------------ forward
@@ -256,9 +249,25 @@ __device__ __forceinline__ void for_listed_pairs(const AAWork& w, Body body) {
   }
 }
 
+// Detection pass (shadow maps): hflag and the work list only.
+__global__ void __launch_bounds__(256) aa_detect_kernel(AAArgs a, uint8_t* __restrict__ hflag, AAWork w) {
+  __shared__ GTile t;
+  const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
+  const int i = bx0 + threadIdx.x, j = by0 + threadIdx.y;
+  const bool in = i < a.W && j < a.H;
+  const size_t p = in ? (size_t)j * a.W + i : 0;
+  load_gtile(a, t, bx0, by0);
+  __syncthreads();
+  const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, threadIdx.y + 1);
+  if (in) hflag[p] = heavy ? 1 : 0;
+  list_append(w, heavy, (int)p);
+}
+
+// Detection pass of the final image: also writes out = colour at the pixels
+// without a crossing.
 template <typename V>
 __global__ void __launch_bounds__(256) aa_forward_kernel(AAArgs a, const V* __restrict__ color, V* __restrict__ out,
-                                                         AAWork w) {
+                                                         uint8_t* __restrict__ hflag, AAWork w) {
   __shared__ GTile t;
   const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
   const int i = bx0 + threadIdx.x, j = by0 + threadIdx.y;
@@ -268,7 +277,10 @@ __global__ void __launch_bounds__(256) aa_forward_kernel(AAArgs a, const V* __re
   load_gtile(a, t, bx0, by0);
   __syncthreads();
   const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, threadIdx.y + 1);
-  if (in && !heavy) out[p] = cp;
+  if (in) {
+    hflag[p] = heavy ? 1 : 0;
+    if (!heavy) out[p] = cp;
+  }
   list_append(w, heavy, (int)p);
 }
 
@@ -289,7 +301,6 @@ __global__ void __launch_bounds__(256) aa_forward_list_kernel(AAArgs a, const V*
     g = vadd(g, shfl_xor_v(g, 2));
     if (act && d == 0) out[p] = vadd(cp, g);
   });
-  work_done(w);
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -333,21 +344,12 @@ __device__ __forceinline__ V aa_pair_adjoint(const AAArgs& a, int i, int j, int 
   return term;
 }
 
-// First pass of the colour adjoint (camera view): pixels without a crossing
-// pass dL/dcolour through.
-__global__ void __launch_bounds__(256) aa_backward4_kernel(AAArgs a, const float4* __restrict__ gout,
-                                                           float4* __restrict__ gcolor, AAWork w) {
-  __shared__ GTile t;
-  const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
-  const int i = bx0 + threadIdx.x, j = by0 + threadIdx.y;
-  const bool in = i < a.W && j < a.H;
-  const size_t p = in ? (size_t)j * a.W + i : 0;
-  const float4 g_p = in ? gout[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-  load_gtile(a, t, bx0, by0);
-  __syncthreads();
-  const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, threadIdx.y + 1);
-  if (in && !heavy) gcolor[p] = g_p;
-  list_append(w, heavy, (int)p);
+// Colour adjoint at the pixels without a crossing (hflag from the forward's
+// detection pass): dL/dcolour passes through.
+__global__ void aa_backward4_kernel(const uint8_t* __restrict__ hflag, const float4* __restrict__ gout,
+                                    float4* __restrict__ gcolor, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n && !hflag[p]) gcolor[p] = gout[p];
 }
 
 __global__ void __launch_bounds__(256) aa_backward4_list_kernel(AAArgs a, const float4* __restrict__ color,
@@ -367,29 +369,12 @@ __global__ void __launch_bounds__(256) aa_backward4_list_kernel(AAArgs a, const 
     g = vadd(g, shfl_xor_v(g, 2));
     if (act && d == 0) gcolor[p] = vadd(g_p, g);
   });
-  work_done(w);
 }
 
-// Adjoint of the shadow-map antialiasing: dL/d(f, f^2) per texel (the pair
-// t-gradients go to the light-space clip coordinates of the edge endpoints),
-// folded into dL/df = g.x + 2 f g.y (f^2 = f f).
-__global__ void __launch_bounds__(256) sm_aa_adjoint_kernel(AAArgs a, const float2* __restrict__ fmap,
-                                                            const float2* __restrict__ gft,
-                                                            float* __restrict__ gf_out, AAWork w) {
-  __shared__ GTile t;
-  const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
-  const int i = bx0 + threadIdx.x, j = by0 + threadIdx.y;
-  const bool in = i < a.W && j < a.H;
-  const size_t p = in ? (size_t)j * a.W + i : 0;
-  const float2 g_p = in ? gft[p] : make_float2(0.f, 0.f);
-  const float f = in ? fmap[p].x : 0.f;
-  load_gtile(a, t, bx0, by0);
-  __syncthreads();
-  const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, threadIdx.y + 1);
-  if (in && !heavy) gf_out[p] = g_p.x + 2.f * f * g_p.y;
-  list_append(w, heavy, (int)p);
-}
-
+// Adjoint of the shadow-map antialiasing at the listed texels: dL/d(f, f^2)
+// (the pair t-gradients go to the light-space clip coordinates of the edge
+// endpoints), folded into dL/df = g.x + 2 f g.y (f^2 = f f).  The filter
+// transpose already wrote dL/df at every other texel.
 __global__ void __launch_bounds__(256) sm_aa_adjoint_list_kernel(AAArgs a, const float2* __restrict__ fmap,
                                                                  const float2* __restrict__ gft,
                                                                  float4* __restrict__ gclip,
@@ -410,15 +395,8 @@ __global__ void __launch_bounds__(256) sm_aa_adjoint_list_kernel(AAArgs a, const
       gf_out[p] = gc.x + 2.f * fmap[p].x * gc.y;
     }
   });
-  work_done(w);
 }
 
-// Without antialiasing the adjoint only folds dL/d(f, f^2) into dL/df.
-__global__ void sm_fold_kernel(const float2* __restrict__ fmap, const float2* __restrict__ gft,
-                               float* __restrict__ gf_out, int n) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) gf_out[p] = gft[p].x + 2.f * fmap[p].x * gft[p].y;
-}
 
 // Adjoint of the interpolation f = sum_k b_k d_k: dL/dd_k = b_k dL/df onto the
 // vertex depths and, through the perspective-correct barycentrics, onto the
@@ -532,30 +510,25 @@ static inline dim3 grid2(int W, int H, dim3 b) { return dim3((W + b.x - 1) / b.x
 
 constexpr int kListGrid = 148 * 8;   // CTAs of a second pass (grid-stride over the list)
 
-template <typename V>
-static void launch_aa_forward(const AAArgs& a, const V* color, V* out, const AAWork& w, cudaStream_t st) {
+void launch_aa_detect(const AAArgs& a, uint8_t* hflag, const AAWork& w, cudaStream_t st) {
+  dim3 b(kAAW, kAAH);
+  count_launches(1);
+  aa_detect_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, hflag, w);
+}
+void launch_aa_forward2_list(const AAArgs& a, const float2* color, float2* out, const AAWork& w, cudaStream_t st) {
+  count_launches(1);
+  aa_forward_list_kernel<float2><<<kListGrid, 256, 0, st>>>(a, color, out, w);
+}
+void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, uint8_t* hflag, const AAWork& w,
+                        cudaStream_t st) {
   dim3 b(kAAW, kAAH);
   count_launches(2);
-  aa_forward_kernel<V><<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, out, w);
-  aa_forward_list_kernel<V><<<kListGrid, 256, 0, st>>>(a, color, out, w);
+  aa_forward_kernel<float4><<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, out, hflag, w);
+  aa_forward_list_kernel<float4><<<kListGrid, 256, 0, st>>>(a, color, out, w);
 }
-void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, const AAWork& w, cudaStream_t st) {
-  launch_aa_forward<float2>(a, color, out, w, st);
-}
-void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, const AAWork& w, cudaStream_t st) {
-  launch_aa_forward<float4>(a, color, out, w, st);
-}
-void launch_sm_aa_adjoint(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
-                          int aa, const AAWork& w, cudaStream_t st) {
-  if (!aa) {
-    const int n = a.W * a.H;
-    count_launches(1);
-    sm_fold_kernel<<<(n + 255) / 256, 256, 0, st>>>(fmap, gft, gf_out, n);
-    return;
-  }
-  dim3 b(kAAW, kAAH);
-  count_launches(2);
-  sm_aa_adjoint_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, fmap, gft, gf_out, w);
+void launch_sm_aa_adjoint_list(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
+                               const AAWork& w, cudaStream_t st) {
+  count_launches(1);
   sm_aa_adjoint_list_kernel<<<kListGrid, 256, 0, st>>>(a, fmap, gft, gclip, gf_out, w);
 }
 
@@ -569,10 +542,10 @@ void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* dep
 }
 
 void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
-                         const AAWork& w, cudaStream_t st) {
-  dim3 b(kAAW, kAAH);
+                         const uint8_t* hflag, const AAWork& w, cudaStream_t st) {
+  const int n = a.W * a.H;
   count_launches(2);
-  aa_backward4_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, gout, gcolor, w);
+  aa_backward4_kernel<<<(n + 255) / 256, 256, 0, st>>>(hflag, gout, gcolor, n);
   aa_backward4_list_kernel<<<kListGrid, 256, 0, st>>>(a, color, gout, gcolor, gclip, w);
 }
 

@@ -51,9 +51,9 @@ struct ViewBufs {
   int W = 0, H = 0, tilesX = 0, tilesY = 0;
   Buf clip, snap, depth, setup, orient, sil, count, offset, list, gbuf, gclip;
   Buf big_index, big_tri, big_acc;
-  Buf aa_list, aa_ctr;      // antialiasing work list and its two counters
+  Buf aa_list, aa_ctr, hflag;   // antialiasing work list, its counter, per-pixel "listed" flag
   int list_cap = 0;
-  AAWork aa_work() { return AAWork{aa_list.as<int>(), aa_ctr.as<int>(), aa_ctr.as<int>() + 1}; }
+  AAWork aa_work() { return AAWork{aa_list.as<int>(), aa_ctr.as<int>()}; }
 };
 
 struct LightBufs {
@@ -271,7 +271,8 @@ void dsm_destroy(dsm_ctx* ctx) {
   for (Buf* b : bufs) b->release();
   for (auto& v : ctx->view) {
     Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
-                 &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr};
+                 &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr,
+                 &v.hflag};
     for (Buf* b : vb) b->release();
   }
   for (auto& l : ctx->light) {
@@ -372,12 +373,8 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
     DSM_CHECK(v.depth.ensure(Vn * 4));
   }
   DSM_CHECK(v.aa_list.ensure((size_t)W * H * 4));
-  if (!v.aa_ctr.p) {
-    // the counters start at zero; every second pass leaves them at zero
-    DSM_CHECK(v.aa_ctr.ensure(2 * sizeof(int)));
-    DSM_CHECK(cudaMemset(v.aa_ctr.p, 0, 2 * sizeof(int)));
-    DSM_CHECK(cudaDeviceSynchronize());
-  }
+  DSM_CHECK(v.aa_ctr.ensure(sizeof(int)));
+  DSM_CHECK(v.hflag.ensure((size_t)W * H));
   if (v.list_cap == 0) {
     const size_t cap = 2 * Tn + 2 * tiles + 1024;
     DSM_CHECK(v.list.ensure(cap * 4));
@@ -459,6 +456,7 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
       va.orient[w] = v.orient.as<int8_t>();
       va.sil[w] = v.sil.as<uint8_t>();
       va.count[w] = v.count.as<int>();
+      va.aa_count[w] = v.aa_ctr.as<int>();
     }
     launch_setup_all(mesh->verts, V, mesh->tris, T, ctx->adj.as<int>(), viewM, va, dstat, st);
   }
@@ -523,15 +521,15 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
       if (params->aa_shadow) {
         AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh->tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(),
                   v.clip.as<float4>()};
-        launch_aa_forward2(aa, lb.fmap.as<float2>(), lb.ftilde.as<float2>(), v.aa_work(), vst);
-      } else {
-        DSM_CHECK(cudaMemcpyAsync(lb.ftilde.p, lb.fmap.p, (size_t)v.W * v.H * sizeof(float2),
-                                  cudaMemcpyDeviceToDevice, vst));
+        launch_aa_detect(aa, v.hflag.as<uint8_t>(), v.aa_work(), vst);
+        launch_aa_forward2_list(aa, lb.fmap.as<float2>(), lb.ftilde.as<float2>(), v.aa_work(), vst);
       }
     }
     {
+      // f~ = f except at the listed texels, whose values the list pass left in ftilde
       StageTimer t(ctx, ST_FILTER, vst);
-      launch_filter(lb.ftilde.as<float2>(), lb.tmp.as<float2>(), lb.mom.as<float2>(), v.W, lb.fa, vst);
+      launch_filter(lb.fmap.as<float2>(), lb.tmp.as<float2>(), lb.mom.as<float2>(), v.W, lb.fa, vst,
+                    params->aa_shadow ? v.hflag.as<uint8_t>() : nullptr, lb.ftilde.as<float2>());
     }
   }
   DSM_CHECK(join_views(ctx, st, L + 1));
@@ -557,7 +555,8 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
   if (params->aa_final) {
     AAArgs aa{cv.gbuf.as<float4>(), Wc, Hc, mesh->tris, cv.sil.as<uint8_t>(), cv.snap.as<VertSnap>(),
               cv.clip.as<float4>()};
-    launch_aa_forward4(aa, ctx->camcolor.as<float4>(), reinterpret_cast<float4*>(image), cv.aa_work(), st);
+    launch_aa_forward4(aa, ctx->camcolor.as<float4>(), reinterpret_cast<float4*>(image), cv.hflag.as<uint8_t>(),
+                       cv.aa_work(), st);
   } else {
     DSM_CHECK(cudaMemcpyAsync(image, ctx->camcolor.p, (size_t)Wc * Hc * sizeof(float4), cudaMemcpyDeviceToDevice, st));
   }
@@ -629,7 +628,7 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   AAArgs caa{cv.gbuf.as<float4>(), Wc, Hc, mesh.tris, cv.sil.as<uint8_t>(), cv.snap.as<VertSnap>(), cv.clip.as<float4>()};
   if (ctx->params.aa_final) {
     launch_aa_backward4(caa, ctx->camcolor.as<float4>(), reinterpret_cast<const float4*>(dL_dimage),
-                        ctx->gcolor.as<float4>(), cv.gclip.as<float4>(), cv.aa_work(), st);
+                        ctx->gcolor.as<float4>(), cv.gclip.as<float4>(), cv.hflag.as<uint8_t>(), cv.aa_work(), st);
   } else {
     DSM_CHECK(cudaMemcpyAsync(ctx->gcolor.p, dL_dimage, (size_t)Wc * Hc * sizeof(float4), cudaMemcpyDeviceToDevice,
                               st));
@@ -672,12 +671,16 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
     AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(), v.clip.as<float4>()};
     {
       StageTimer t(ctx, ST_BWD_FILTER, vst);
-      launch_filter_adjoint(lb.gm.as<float2>(), lb.tmp.as<float2>(), lb.gft.as<float2>(), v.W, lb.fa, vst);
+      // dL/d(f~, (f^2)~) and, folded through f^2 = f f, dL/df (into tmp)
+      launch_filter_adjoint(lb.gm.as<float2>(), lb.tmp.as<float2>(), lb.gft.as<float2>(), v.W, lb.fa, vst,
+                            lb.fmap.as<float2>(), lb.tmp.as<float>());
     }
     {
+      // the listed texels: dL/df through the antialiasing (overwrites tmp there)
       StageTimer t(ctx, ST_BWD_SM_AA, vst);
-      launch_sm_aa_adjoint(aa, lb.fmap.as<float2>(), lb.gft.as<float2>(), v.gclip.as<float4>(), lb.tmp.as<float>(),
-                           ctx->params.aa_shadow, v.aa_work(), vst);
+      if (ctx->params.aa_shadow)
+        launch_sm_aa_adjoint_list(aa, lb.fmap.as<float2>(), lb.gft.as<float2>(), v.gclip.as<float4>(),
+                                  lb.tmp.as<float>(), v.aa_work(), vst);
     }
     {
       StageTimer t(ctx, ST_BWD_SM_INTERP, vst);
@@ -813,6 +816,19 @@ dsm_status dsm_debug_copy(dsm_ctx* ctx, int32_t what, int32_t index, void* dst, 
   }
   if (!src || size == 0) return fail(ctx, DSM_ERR_INVALID_ARG, "unknown or empty debug buffer");
   if (bytes != size) return fail(ctx, DSM_ERR_INVALID_ARG, "debug buffer size mismatch");
+  if (what == 2) {
+    // f~ is held as f plus the antialiased values of the listed texels
+    const LightBufs& lb = ctx->light[index];
+    const int n = lb.res * lb.res;
+    if (ctx->params.aa_shadow)
+      launch_compose(lb.fmap.as<float2>(), ctx->view[index].hflag.as<uint8_t>(), lb.ftilde.as<float2>(),
+                     static_cast<float2*>(dst), n, ctx->stream);
+    else
+      DSM_CHECK(cudaMemcpyAsync(dst, lb.fmap.p, size, cudaMemcpyDeviceToDevice, ctx->stream));
+    DSM_CHECK(cudaGetLastError());
+    DSM_CHECK(cudaStreamSynchronize(ctx->stream));
+    return DSM_OK;
+  }
   DSM_CHECK(cudaMemcpyAsync(dst, src, size, cudaMemcpyDeviceToDevice, ctx->stream));
   DSM_CHECK(cudaStreamSynchronize(ctx->stream));
   return DSM_OK;

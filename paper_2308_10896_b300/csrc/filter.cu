@@ -143,9 +143,20 @@ __device__ __forceinline__ void tap_run(const float2* src, int step, const Filte
   }
 }
 
+// Extras of the shadow-map path (NULL for a plain filter):
+//   forward: the input is (f, f^2) except where hflag marks a texel whose
+//     antialiased value the antialiasing pass wrote into patch;
+//   adjoint: also writes dL/df = g.x + 2 f g.y of the output g (f from fmap).
+struct FilterExtras {
+  const uint8_t* hflag;
+  const float2* patch;
+  const float2* fmap;
+  float* gf;
+};
+
 template <int kR, bool kAdjoint>
 __global__ void __launch_bounds__(256) filter_tile_kernel(const float2* __restrict__ in, float2* __restrict__ out,
-                                                          int R, FilterArgs fa) {
+                                                          int R, FilterArgs fa, FilterExtras ex) {
   using G = TileGeom<kR>;
   constexpr int S = G::S, P = G::P, PM = G::PM;
   extern __shared__ float2 sm[];
@@ -159,12 +170,16 @@ __global__ void __launch_bounds__(256) filter_tile_kernel(const float2* __restri
     const int row = k / S, col = k - row * S;
     int gy = oy - kR + row, gx = ox - kR + col;
     float2 v = make_float2(0.f, 0.f);
+    bool load = true;
     if (!kAdjoint && clamp) {
       gy = min(max(gy, 0), R - 1);
       gx = min(max(gx, 0), R - 1);
-      v = in[(size_t)gy * R + gx];
-    } else if (gy >= 0 && gy < R && gx >= 0 && gx < R) {
-      v = in[(size_t)gy * R + gx];
+    } else {
+      load = gy >= 0 && gy < R && gx >= 0 && gx < R;
+    }
+    if (load) {
+      const size_t q = (size_t)gy * R + gx;
+      v = (!kAdjoint && ex.hflag && ex.hflag[q]) ? ex.patch[q] : in[q];
     }
     tin[row * P + col] = v;
   }
@@ -203,10 +218,26 @@ __global__ void __launch_bounds__(256) filter_tile_kernel(const float2* __restri
 #pragma unroll
       for (int u = 0; u < kYRun; ++u) {
         const int gy = oy + r0 + u;
-        if (gy < R) out[(size_t)gy * R + gx] = acc[u];
+        if (gy < R) {
+          const size_t q = (size_t)gy * R + gx;
+          out[q] = acc[u];
+          if (kAdjoint && ex.gf) ex.gf[q] = acc[u].x + 2.f * ex.fmap[q].x * acc[u].y;
+        }
       }
     }
   }
+}
+
+// The extras on the two-pass path (radius above the tiled kernel's limit).
+__global__ void compose_kernel(const float2* __restrict__ fmap, const uint8_t* __restrict__ hflag,
+                               const float2* __restrict__ patch, float2* __restrict__ out, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) out[p] = hflag[p] ? patch[p] : fmap[p];
+}
+__global__ void fold_kernel(const float2* __restrict__ fmap, const float2* __restrict__ g, float* __restrict__ gf,
+                            int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) gf[p] = g[p].x + 2.f * fmap[p].x * g[p].y;
 }
 static_assert(kFT * kFT == 256 * kYRun, "one y-pass run per thread");
 static_assert(TileGeom<kFRmax>::S * (kFT / kXRun) <= 256, "one x-pass pass over the threads for every radius");
@@ -215,26 +246,36 @@ static_assert(TileGeom<kFRmax>::smem <= 48 * 1024, "filter tile");
 
 template <int kR>
 static bool launch_tiled_r(bool adjoint, const float2* in, float2* out, int R, const FilterArgs& fa,
-                           cudaStream_t st) {
+                           const FilterExtras& ex, cudaStream_t st) {
   if (fa.r != kR) {
-    if constexpr (kR < kFRmax) return launch_tiled_r<kR + 1>(adjoint, in, out, R, fa, st);
+    if constexpr (kR < kFRmax) return launch_tiled_r<kR + 1>(adjoint, in, out, R, fa, ex, st);
     else return false;
   }
   dim3 g((R + kFT - 1) / kFT, (R + kFT - 1) / kFT);
   count_launches(1);
-  if (adjoint) filter_tile_kernel<kR, true><<<g, 256, TileGeom<kR>::smem, st>>>(in, out, R, fa);
-  else filter_tile_kernel<kR, false><<<g, 256, TileGeom<kR>::smem, st>>>(in, out, R, fa);
+  if (adjoint) filter_tile_kernel<kR, true><<<g, 256, TileGeom<kR>::smem, st>>>(in, out, R, fa, ex);
+  else filter_tile_kernel<kR, false><<<g, 256, TileGeom<kR>::smem, st>>>(in, out, R, fa, ex);
   return true;
 }
 
-template <bool kAdjoint>
-static bool launch_tiled(const float2* in, float2* out, int R, const FilterArgs& fa, cudaStream_t st) {
-  return launch_tiled_r<1>(kAdjoint, in, out, R, fa, st);
+void launch_compose(const float2* fmap, const uint8_t* hflag, const float2* patch, float2* out, int n,
+                    cudaStream_t st) {
+  count_launches(1);
+  compose_kernel<<<(n + 255) / 256, 256, 0, st>>>(fmap, hflag, patch, out, n);
 }
 
-void launch_filter(const float2* in, float2* tmp, float2* out, int R, const FilterArgs& fa, cudaStream_t st) {
-  if (launch_tiled<false>(in, out, R, fa, st)) return;
+void launch_filter(const float2* in, float2* tmp, float2* out, int R, const FilterArgs& fa, cudaStream_t st,
+                   const uint8_t* hflag, const float2* patch) {
+  const FilterExtras ex{hflag, patch, nullptr, nullptr};
+  if (launch_tiled_r<1>(false, in, out, R, fa, ex, st)) return;
   dim3 b(32, 8), g((R + 31) / 32, (R + 7) / 8);
+  if (hflag) {
+    // the substituted input is composed into `out` first (the passes read it back)
+    const int n = R * R;
+    count_launches(1);
+    compose_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, hflag, patch, out, n);
+    in = out;
+  }
   count_launches(1);
   filter_pass_kernel<false, false><<<g, b, 0, st>>>(in, tmp, R, fa);
   count_launches(1);
@@ -242,13 +283,19 @@ void launch_filter(const float2* in, float2* tmp, float2* out, int R, const Filt
 }
 
 void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, const FilterArgs& fa,
-                           cudaStream_t st) {
-  if (launch_tiled<true>(gout, gin, R, fa, st)) return;
+                           cudaStream_t st, const float2* fmap, float* gf) {
+  const FilterExtras ex{nullptr, nullptr, fmap, gf};
+  if (launch_tiled_r<1>(true, gout, gin, R, fa, ex, st)) return;
   dim3 b(32, 8), g((R + 31) / 32, (R + 7) / 8);
   count_launches(1);
   filter_pass_kernel<true, true><<<g, b, 0, st>>>(gout, tmp, R, fa);
   count_launches(1);
   filter_pass_kernel<false, true><<<g, b, 0, st>>>(tmp, gin, R, fa);
+  if (gf) {
+    const int n = R * R;
+    count_launches(1);
+    fold_kernel<<<(n + 255) / 256, 256, 0, st>>>(fmap, gin, gf, n);
+  }
 }
 
 }  // namespace dsm

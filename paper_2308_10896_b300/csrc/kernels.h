@@ -82,12 +82,11 @@ struct BigArgs {
   int view;
 };
 
-// Work list of a two-pass antialiasing step: pixel indices appended by the
-// first pass, count and done counters (zero between uses).
+// Antialiasing work list of a view: pixel indices appended by the detection
+// pass; the counter is cleared by the setup of each frame.
 struct AAWork {
   int* list;
   int* count;
-  int* done;
 };
 
 struct AAArgs {
@@ -111,6 +110,7 @@ struct ViewSetupArgs {
   int8_t* orient[kMaxViews];
   uint8_t* sil[kMaxViews];
   int* count[kMaxViews];          // tile counters, zeroed by the setup
+  int* aa_count[kMaxViews];       // antialiasing work-list counters, zeroed by the setup
 };
 // Transform, triangle setup and silhouettes of every view; also zeroes the tile
 // counters and the big-triangle counts for the binning that follows.
@@ -132,20 +132,31 @@ void launch_raster(const TriSetup* setup, const int* offset, const int* list, in
                    cudaStream_t st);
 
 // shadow-map interpolation and antialiasing
-void launch_aa_forward2(const AAArgs& a, const float2* color, float2* out, const AAWork& w, cudaStream_t st);
-void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, const AAWork& w, cudaStream_t st);
-void launch_sm_aa_adjoint(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
-                          int aa, const AAWork& w, cudaStream_t st);
+// Antialiasing (detection + list passes, see aa.cu).
+void launch_aa_detect(const AAArgs& a, uint8_t* hflag, const AAWork& w, cudaStream_t st);
+void launch_aa_forward2_list(const AAArgs& a, const float2* color, float2* out, const AAWork& w, cudaStream_t st);
+void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, uint8_t* hflag, const AAWork& w,
+                        cudaStream_t st);
+void launch_sm_aa_adjoint_list(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
+                               const AAWork& w, cudaStream_t st);
+void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
+                         const uint8_t* hflag, const AAWork& w, cudaStream_t st);
 void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* depth, float4* gclip,
                               const BigArgs& big, cudaStream_t st);
-void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
-                         const AAWork& w, cudaStream_t st);
 
 // separable filter
 void make_filter_args(double sigma, int radius, int kind, int boundary, FilterArgs* fa);
-void launch_filter(const float2* in, float2* tmp, float2* out, int R, const FilterArgs& fa, cudaStream_t st);
-void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, const FilterArgs& fa,
-                           cudaStream_t st);
+// m = G g; with hflag (shadow-map path) g is (f, f^2) except at flagged texels,
+// where the antialiasing pass left (f~, (f^2)~) in patch.
+void launch_filter(const float2* in, float2* tmp, float2* out, int R, const FilterArgs& fa, cudaStream_t st,
+                   const uint8_t* hflag = nullptr, const float2* patch = nullptr);
+// out = hflag ? patch : fmap per texel (the antialiased shadow map, materialised
+// on request).
+void launch_compose(const float2* fmap, const uint8_t* hflag, const float2* patch, float2* out, int n,
+                    cudaStream_t st);
+// gin = G^T gout; with gf (shadow-map path) also dL/df = gin.x + 2 f gin.y.
+void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, const FilterArgs& fa, cudaStream_t st,
+                           const float2* fmap = nullptr, float* gf = nullptr);
 
 // normals, shading, vertex gradients
 void launch_vertex_normals(const float* verts, int V, const int* tris, const int* vf_off, const int* vf_list,

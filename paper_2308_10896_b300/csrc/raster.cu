@@ -255,13 +255,15 @@ __global__ void transform_all_kernel(const float* __restrict__ verts, int V, con
 
 __global__ void tri_setup_all_kernel(const int* __restrict__ tris, int T, ViewSetupArgs a, DevStatus* status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  // the binning's tile counters, big-triangle counts and list totals start this frame at zero
+  // the binning's tile counters, big-triangle counts and list totals, and the
+  // antialiasing work lists, start this frame empty
   for (int w = 0; w < a.n; ++w)
     for (int k = t; k < a.tiles[w]; k += gridDim.x * blockDim.x) a.count[w][k] = 0;
   if (t < DSM_MAX_LIGHTS + 1) {
     status->big_count[t] = 0;
     status->needed_pairs[t] = 0;
   }
+  if (t < a.n && a.aa_count[t]) *a.aa_count[t] = 0;
   if (t >= T) return;
   const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
 #pragma unroll

@@ -54,8 +54,8 @@ def test_stage_bytes_model():
     sc = scenes.config1()
     b = bench.stage_bytes(sc)
     R2, WH = 256 * 256, 256 * 256
-    assert b["filter"] == R2 * 16 and b["bwd_filter"] == R2 * 16
-    assert b["final_antialias"] == WH * 48
+    assert b["filter"] == R2 * 17 and b["bwd_filter"] == R2 * 28
+    assert b["final_antialias"] == WH * 49
     assert set(b) >= {"raster", "sm_antialias", "shade", "bwd_sm_interp", "bwd_sm_antialias", "bwd_shade", "setup"}
 
 
