@@ -133,7 +133,8 @@ __device__ __forceinline__ bool pair_info(const AAArgs& a, int i, int j, int ni,
 // The G-buffer entries a pair decision needs (triangle id, depth key) for a
 // kAAW x kAAH block of pixels and its one-pixel halo, staged in shared memory
 // with coalesced loads: the four neighbours of every pixel are read from here.
-constexpr int kAAW = 32, kAAH = 8;
+constexpr int kAAW = 32, kAAH = 32, kAAThreadsY = 8;   // tile of a CTA; threads: 32 x 8, 4 rows each
+constexpr int kAARows = kAAH / kAAThreadsY;
 struct GTile {
   int id[kAAH + 2][kAAW + 2];
   float z[kAAH + 2][kAAW + 2];
@@ -141,7 +142,7 @@ struct GTile {
 
 __device__ __forceinline__ void load_gtile(const AAArgs& a, GTile& t, int bx0, int by0) {
   const int tid = threadIdx.y * kAAW + threadIdx.x;
-  for (int k = tid; k < (kAAH + 2) * (kAAW + 2); k += kAAW * kAAH) {
+  for (int k = tid; k < (kAAH + 2) * (kAAW + 2); k += kAAW * kAAThreadsY) {
     const int r = k / (kAAW + 2), c = k - r * (kAAW + 2);
     const int gi = bx0 - 1 + c, gj = by0 - 1 + r;
     int id = 0;
@@ -253,14 +254,18 @@ __device__ __forceinline__ void for_listed_pairs(const AAWork& w, Body body) {
 __global__ void __launch_bounds__(256) aa_detect_kernel(AAArgs a, uint8_t* __restrict__ hflag, AAWork w) {
   __shared__ GTile t;
   const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
-  const int i = bx0 + threadIdx.x, j = by0 + threadIdx.y;
-  const bool in = i < a.W && j < a.H;
-  const size_t p = in ? (size_t)j * a.W + i : 0;
   load_gtile(a, t, bx0, by0);
   __syncthreads();
-  const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, threadIdx.y + 1);
-  if (in) hflag[p] = heavy ? 1 : 0;
-  list_append(w, heavy, (int)p);
+  const int i = bx0 + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < kAARows; ++q) {
+    const int ly = threadIdx.y + kAAThreadsY * q, j = by0 + ly;
+    const bool in = i < a.W && j < a.H;
+    const size_t p = in ? (size_t)j * a.W + i : 0;
+    const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, ly + 1);
+    if (in) hflag[p] = heavy ? 1 : 0;
+    list_append(w, heavy, (int)p);
+  }
 }
 
 // Detection pass of the final image: also writes out = colour at the pixels
@@ -270,18 +275,27 @@ __global__ void __launch_bounds__(256) aa_forward_kernel(AAArgs a, const V* __re
                                                          uint8_t* __restrict__ hflag, AAWork w) {
   __shared__ GTile t;
   const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
-  const int i = bx0 + threadIdx.x, j = by0 + threadIdx.y;
-  const bool in = i < a.W && j < a.H;
-  const size_t p = in ? (size_t)j * a.W + i : 0;
-  const V cp = in ? color[p] : V{};
+  const int i = bx0 + threadIdx.x;
+  V cp[kAARows];
+#pragma unroll
+  for (int q = 0; q < kAARows; ++q) {
+    const int j = by0 + threadIdx.y + kAAThreadsY * q;
+    cp[q] = (i < a.W && j < a.H) ? color[(size_t)j * a.W + i] : V{};
+  }
   load_gtile(a, t, bx0, by0);
   __syncthreads();
-  const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, threadIdx.y + 1);
-  if (in) {
-    hflag[p] = heavy ? 1 : 0;
-    if (!heavy) out[p] = cp;
+#pragma unroll
+  for (int q = 0; q < kAARows; ++q) {
+    const int ly = threadIdx.y + kAAThreadsY * q, j = by0 + ly;
+    const bool in = i < a.W && j < a.H;
+    const size_t p = in ? (size_t)j * a.W + i : 0;
+    const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, ly + 1);
+    if (in) {
+      hflag[p] = heavy ? 1 : 0;
+      if (!heavy) out[p] = cp[q];
+    }
+    list_append(w, heavy, (int)p);
   }
-  list_append(w, heavy, (int)p);
 }
 
 template <typename V>
@@ -506,14 +520,14 @@ __global__ void sm_big_resolve_kernel(const int* __restrict__ tris, const int* _
 }
 
 // ------------------------------------------------------------------ launchers
-static inline dim3 grid2(int W, int H, dim3 b) { return dim3((W + b.x - 1) / b.x, (H + b.y - 1) / b.y); }
 
 constexpr int kListGrid = 148 * 8;   // CTAs of a second pass (grid-stride over the list)
 
+static inline dim3 aa_grid(const AAArgs& a) { return dim3((a.W + kAAW - 1) / kAAW, (a.H + kAAH - 1) / kAAH); }
+
 void launch_aa_detect(const AAArgs& a, uint8_t* hflag, const AAWork& w, cudaStream_t st) {
-  dim3 b(kAAW, kAAH);
   count_launches(1);
-  aa_detect_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, hflag, w);
+  aa_detect_kernel<<<aa_grid(a), dim3(kAAW, kAAThreadsY), 0, st>>>(a, hflag, w);
 }
 void launch_aa_forward2_list(const AAArgs& a, const float2* color, float2* out, const AAWork& w, cudaStream_t st) {
   count_launches(1);
@@ -521,9 +535,8 @@ void launch_aa_forward2_list(const AAArgs& a, const float2* color, float2* out, 
 }
 void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, uint8_t* hflag, const AAWork& w,
                         cudaStream_t st) {
-  dim3 b(kAAW, kAAH);
   count_launches(2);
-  aa_forward_kernel<float4><<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, out, hflag, w);
+  aa_forward_kernel<float4><<<aa_grid(a), dim3(kAAW, kAAThreadsY), 0, st>>>(a, color, out, hflag, w);
   aa_forward_list_kernel<float4><<<kListGrid, 256, 0, st>>>(a, color, out, w);
 }
 void launch_sm_aa_adjoint_list(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
