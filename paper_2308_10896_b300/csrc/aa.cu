@@ -141,19 +141,29 @@ struct GTile {
 };
 
 __device__ __forceinline__ void load_gtile(const AAArgs& a, GTile& t, int bx0, int by0) {
+  constexpr int kN = (kAAH + 2) * (kAAW + 2), kThreads = kAAW * kAAThreadsY;
+  constexpr int kIt = (kN + kThreads - 1) / kThreads;
   const int tid = threadIdx.y * kAAW + threadIdx.x;
-  for (int k = tid; k < (kAAH + 2) * (kAAW + 2); k += kAAW * kAAThreadsY) {
+  float2 g[kIt];   // (id bits, depth key); every load issued before the first store
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int k = tid + kThreads * it;
     const int r = k / (kAAW + 2), c = k - r * (kAAW + 2);
     const int gi = bx0 - 1 + c, gj = by0 - 1 + r;
-    int id = 0;
-    float z = 0.f;
-    if (gi >= 0 && gj >= 0 && gi < a.W && gj < a.H) {
-      const float4 g = a.gbuf[(size_t)gj * a.W + gi];
-      id = gid(g);
-      z = g.w;
+    g[it] = make_float2(0.f, 0.f);
+    if (k < kN && gi >= 0 && gj >= 0 && gi < a.W && gj < a.H) {
+      const float4 v = a.gbuf[(size_t)gj * a.W + gi];
+      g[it] = make_float2(v.x, v.w);
     }
-    t.id[r][c] = id;
-    t.z[r][c] = z;
+  }
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int k = tid + kThreads * it;
+    if (k < kN) {
+      const int r = k / (kAAW + 2), c = k - r * (kAAW + 2);
+      t.id[r][c] = __float_as_int(g[it].x);
+      t.z[r][c] = g[it].y;
+    }
   }
 }
 

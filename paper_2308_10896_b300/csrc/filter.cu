@@ -165,23 +165,36 @@ __global__ void __launch_bounds__(256) filter_tile_kernel(const float2* __restri
   const int ox = blockIdx.x * kFT, oy = blockIdx.y * kFT;
   const int tid = threadIdx.x;
   const bool clamp = fa.boundary == 0;
-  // 1. stage the input
-  for (int k = tid; k < S * S; k += 256) {
+  // 1. stage the input: every load of the thread is issued before the first
+  // shared-memory store
+  constexpr int kStage = (S * S + 255) / 256;
+  float2 v[kStage];
+#pragma unroll
+  for (int it = 0; it < kStage; ++it) {
+    const int k = tid + 256 * it;
     const int row = k / S, col = k - row * S;
     int gy = oy - kR + row, gx = ox - kR + col;
-    float2 v = make_float2(0.f, 0.f);
-    bool load = true;
+    v[it] = make_float2(0.f, 0.f);
+    bool load = k < S * S;
     if (!kAdjoint && clamp) {
       gy = min(max(gy, 0), R - 1);
       gx = min(max(gx, 0), R - 1);
     } else {
-      load = gy >= 0 && gy < R && gx >= 0 && gx < R;
+      load = load && gy >= 0 && gy < R && gx >= 0 && gx < R;
     }
     if (load) {
       const size_t q = (size_t)gy * R + gx;
-      v = (!kAdjoint && ex.hflag && ex.hflag[q]) ? ex.patch[q] : in[q];
+      v[it] = in[q];
+      if (!kAdjoint && ex.hflag && ex.hflag[q]) v[it] = ex.patch[q];
     }
-    tin[row * P + col] = v;
+  }
+#pragma unroll
+  for (int it = 0; it < kStage; ++it) {
+    const int k = tid + 256 * it;
+    if (k < S * S) {
+      const int row = k / S, col = k - row * S;
+      tin[row * P + col] = v[it];
+    }
   }
   __syncthreads();
   const bool fold = kAdjoint && clamp;
