@@ -368,21 +368,22 @@ def run_ours(args):
     r.ctx.profile(False)
     r.ctx.sync()
     # ---- end to end through the public API with host buffers (H2D inputs, D2H results)
-    pin = dict(pin_memory=True)
-    h_verts = torch.as_tensor(sc["verts"]).pin_memory()
-    h_lp = r.light_params.cpu().pin_memory()
-    h_alb = r.albedo.cpu().pin_memory()
-    h_loss = torch.empty(1, **pin)
-    d_verts = torch.empty_like(r.verts)
-    d_lp = torch.empty_like(r.light_params)
-    d_alb = torch.empty_like(r.albedo)
-    h2d = h_verts.numel() * 4 + h_lp.numel() * 4 + h_alb.numel() * 4
+    # the step's inputs (vertices, light parameters, albedo) packed in one pinned
+    # host buffer and uploaded with one copy
+    parts = [torch.as_tensor(sc["verts"], dtype=torch.float32).reshape(-1), r.light_params.cpu().reshape(-1),
+             r.albedo.cpu().reshape(-1)]
+    h_in = torch.cat(parts).pin_memory()
+    d_in = torch.empty_like(h_in, device=dev)
+    n0, n1 = parts[0].numel(), parts[0].numel() + parts[1].numel()
+    d_verts = d_in[:n0].view(r.verts.shape)
+    d_lp = d_in[n0:n1].view(r.light_params.shape)
+    d_alb = d_in[n1:].view(r.albedo.shape)
+    h_loss = torch.empty(1, pin_memory=True)
+    h2d = h_in.numel() * 4
     d2h = 4
 
     def e2e_step():
-        d_verts.copy_(h_verts, non_blocking=True)
-        d_lp.copy_(h_lp, non_blocking=True)
-        d_alb.copy_(h_alb, non_blocking=True)
+        d_in.copy_(h_in, non_blocking=True)
         r.forward(verts=d_verts, light_params=d_lp, albedo=d_alb, image=image)
         dsm.l2_loss_grad(image, target, loss, gimg)
         r.backward(gimg, dverts, dlight, dalbedo)
