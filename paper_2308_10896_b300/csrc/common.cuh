@@ -8,8 +8,8 @@ namespace dsm {
 constexpr int kSubpix = 256;          // 8 sub-pixel bits: 24.8 fixed point
 constexpr int kGuard = 1 << 28;       // |snapped coordinate| limit; beyond it a triangle is culled
 constexpr float kWMin = 1e-6f;        // clip w below this culls the triangle
-constexpr int kTile = 16;             // raster tile side in pixels
-constexpr int kTileLog2 = 4;
+constexpr int kTile = 32;             // raster tile side in pixels
+constexpr int kTileLog2 = 5;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Snapped vertex of one view: 24.8 fixed-point screen position, ndc depth,

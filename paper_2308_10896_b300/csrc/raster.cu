@@ -510,7 +510,7 @@ __device__ __forceinline__ uint64_t cover_key(const int* w, int x, int y) {
   return depth_key(z, w[kRecTri]);
 }
 
-// One 256-thread CTA per 16x16 tile.  The tile's triangle list is read 256
+// One 256-thread CTA per 32x32 tile.  The tile's triangle list is read 256
 // records at a time.  Every record contributes its bbox-in-tile pixels as work
 // items; a block prefix sum turns them into one flat list that all threads
 // stride over (balanced whatever the triangle sizes), and each covered pixel
@@ -529,11 +529,12 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
                                                      int W, int H, const float4* __restrict__ clip,
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf,
                                                      const float* __restrict__ depth, float2* __restrict__ fmap) {
+  constexpr int kPix = kTile * kTile;
   __shared__ int sq[256 * kRecStride];
-  __shared__ unsigned long long sbest[256];
+  __shared__ unsigned long long sbest[kPix];
   __shared__ int spre[257];          // exclusive prefix of the work items per record
-  __shared__ int sbox[256];          // bbox in tile: x0 | x1 << 4 | y0 << 8 | y1 << 12 (tile-local),
-                                     // ceil(2^16 / width) - 1 << 16
+  __shared__ int sbox[256];          // bbox in tile: x0 | x1 << 5 | y0 << 10 | y1 << 15 (tile-local)
+  __shared__ int sinv[256];          // ceil(2^16 / bbox width)
   __shared__ unsigned short sown[kChunk];   // owning record + 1 of each item of the chunk
   __shared__ int swarp[8];
   const int tile = blockIdx.x;
@@ -541,12 +542,12 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ti0 = ti * kTile, tj0 = tj * kTile;
   const long long Px0 = (long long)ti0 * kSubpix + 128, Py0 = (long long)tj0 * kSubpix + 128;
-  sbest[tid] = ~0ull;
+  for (int q = tid; q < kPix; q += 256) sbest[q] = ~0ull;
   // slots past the list capacity were never written (the fill pass flagged the overflow)
   const int beg = min(offset[tile], capacity), end = min(offset[gridDim.x + tile], capacity);
   for (int base = beg; base < end; base += 256) {
     const int k = base + tid;
-    int area = 0, box = 0;
+    int area = 0, box = 0, inv = 0;
     if (k < end) {
       const TriSetup r = setup[list[k]];
       const int i0 = max(r.ibox & 0xffff, ti0), i1 = min((int)((unsigned)r.ibox >> 16), ti0 + kTile - 1);
@@ -554,12 +555,13 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
       if (i0 <= i1 && j0 <= j1) {
         const int wd = i1 - i0 + 1;
         area = wd * (j1 - j0 + 1);
-        box = (i0 - ti0) | ((i1 - ti0) << 4) | ((j0 - tj0) << 8) | ((j1 - tj0) << 12) |
-              (((65536 + wd - 1) / wd - 1) << 16);
+        box = (i0 - ti0) | ((i1 - ti0) << 5) | ((j0 - tj0) << 10) | ((j1 - tj0) << 15);
+        inv = (65536 + wd - 1) / wd;
         rec_stage(r, Px0, Py0, sq + tid * kRecStride);
       }
     }
     sbox[tid] = box;
+    sinv[tid] = inv;
     // block exclusive scan of the areas
     int incl = area;
 #pragma unroll
@@ -619,9 +621,9 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
       for (int q = tid; q < n; q += 256) {
         const int rec = sown[q] - 1;
         const int b = sbox[rec];
-        const int x0 = b & 15, x1 = (b >> 4) & 15, y0 = (b >> 8) & 15;
+        const int x0 = b & 31, x1 = (b >> 5) & 31, y0 = (b >> 10) & 31;
         const int it = c0 + q - spre[rec], wd = x1 - x0 + 1;
-        const int qy = (it * (((unsigned)b >> 16) + 1)) >> 16;   // it / wd (exact for it < 256, wd <= 16)
+        const int qy = (it * sinv[rec]) >> 16;   // it / wd (exact for it < 1024, wd <= 32)
         const int x = x0 + (it - qy * wd), y = y0 + qy;
         const uint64_t key = cover_key(sq + rec * kRecStride, x, y);
         if (key != ~0ull) atomicMin(&sbest[y * kTile + x], (unsigned long long)key);
@@ -629,25 +631,27 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
       __syncthreads();
     }
   }
-  const int i = ti0 + (tid & 15), j = tj0 + (tid >> 4);
-  const uint64_t best = sbest[tid];
-  if (i >= W || j >= H) return;
-  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-  float f = 1.f;   // shadow-map depth sample; background: 1
-  if (best != ~0ull) {
-    const int t = (int)(best & 0xffffffffu);
-    const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
-    const float4 c0 = clip[v0], c1 = clip[v1], c2 = clip[v2];
-    const Bary r = bary_at(c0, c1, c2, pix_ndc_x(i, W), pix_ndc_y(j, H));
-    out = make_float4(__int_as_float(t + 1), r.b[0], r.b[1], key_depth(best));
-    if (fmap) {
-      // f = sum_k b_k d_k with b_2 = 1 - b_0 - b_1 of the stored barycentrics
-      const float b2 = 1.f - r.b[0] - r.b[1];
-      f = r.b[0] * depth[v0] + r.b[1] * depth[v1] + b2 * depth[v2];
-    }
+  for (int px = tid; px < kPix; px += 256) {
+    const int i = ti0 + (px & (kTile - 1)), j = tj0 + (px >> kTileLog2);
+    const uint64_t best = sbest[px];
+    if (i >= W || j >= H) continue;
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    float f = 1.f;   // shadow-map depth sample; background: 1
+    if (best != ~0ull) {
+      const int t = (int)(best & 0xffffffffu);
+      const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
+      const float4 c0 = clip[v0], c1 = clip[v1], c2 = clip[v2];
+      const Bary r = bary_at(c0, c1, c2, pix_ndc_x(i, W), pix_ndc_y(j, H));
+      out = make_float4(__int_as_float(t + 1), r.b[0], r.b[1], key_depth(best));
+      if (fmap) {
+        // f = sum_k b_k d_k with b_2 = 1 - b_0 - b_1 of the stored barycentrics
+        const float b2 = 1.f - r.b[0] - r.b[1];
+        f = r.b[0] * depth[v0] + r.b[1] * depth[v1] + b2 * depth[v2];
+      }
   }
   gbuf[(size_t)j * W + i] = out;
   if (fmap) fmap[(size_t)j * W + i] = make_float2(f, f * f);
+  }
 }
 
 // ------------------------------------------------------------------ launchers
