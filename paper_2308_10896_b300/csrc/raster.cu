@@ -648,9 +648,9 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
         const float b2 = 1.f - r.b[0] - r.b[1];
         f = r.b[0] * depth[v0] + r.b[1] * depth[v1] + b2 * depth[v2];
       }
-  }
-  gbuf[(size_t)j * W + i] = out;
-  if (fmap) fmap[(size_t)j * W + i] = make_float2(f, f * f);
+    }
+    gbuf[(size_t)j * W + i] = out;
+    if (fmap) fmap[(size_t)j * W + i] = make_float2(f, f * f);
   }
 }
 
