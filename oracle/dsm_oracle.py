@@ -172,9 +172,14 @@ def _order_bits(z32: np.ndarray) -> np.ndarray:
 
 
 # =============================================================================== a3: brute-force raster
-def raster(setup: dict, tris: np.ndarray) -> dict:
+def raster(setup: dict, tris: np.ndarray, window=None) -> dict:
     """Eq. 1 on the pixel grid: for every pixel centre the nearest covering
     triangle, by brute force over each triangle's bounding box.
+
+    ``window`` = (i0, i1, j0, j1) (inclusive pixel ranges) restricts the work
+    to that window: only triangles whose box meets it are visited, and their
+    boxes are cut to it; pixels outside it are left as background.  This is the
+    same computation on fewer pixels, for spot checks of full-size frames.
 
     Coverage: edge functions E_ab(P) = (X_b - X_a)(P_y - Y_a) - (Y_b - Y_a)(P_x - X_a)
     in exact integers at P = (256 i + 128, 256 j + 128); E_0 = E_12,
@@ -191,15 +196,25 @@ def raster(setup: dict, tris: np.ndarray) -> dict:
     X, Y, zn = setup["X"], setup["Y"], setup["zndc"]
     best = np.full((H, W), np.iinfo(np.uint64).max, np.uint64)
     zbest = np.zeros((H, W), np.float32)
-    for t in range(tris.shape[0]):
+    wi0, wi1, wj0, wj1 = (0, W - 1, 0, H - 1) if window is None else window
+    order = range(tris.shape[0])
+    if window is not None:
+        # triangles whose pixel box meets the window (the same box as below)
+        xs_all, ys_all = X[tris].astype(np.int64), Y[tris].astype(np.int64)
+        bi0 = -((128 - xs_all.min(1)) // SUBPIX)
+        bi1 = (xs_all.max(1) - 128) // SUBPIX
+        bj0 = -((128 - ys_all.min(1)) // SUBPIX)
+        bj1 = (ys_all.max(1) - 128) // SUBPIX
+        order = np.nonzero((bi1 >= wi0) & (bi0 <= wi1) & (bj1 >= wj0) & (bj0 <= wj1))[0].tolist()
+    for t in order:
         if setup["culled"][t]:
             continue
         v = tris[t]
         xs, ys = X[v], Y[v]
-        i0 = max(0, -((128 - int(xs.min())) // SUBPIX))
-        i1 = min(W - 1, (int(xs.max()) - 128) // SUBPIX)
-        j0 = max(0, -((128 - int(ys.min())) // SUBPIX))
-        j1 = min(H - 1, (int(ys.max()) - 128) // SUBPIX)
+        i0 = max(wi0, -((128 - int(xs.min())) // SUBPIX))
+        i1 = min(wi1, (int(xs.max()) - 128) // SUBPIX)
+        j0 = max(wj0, -((128 - int(ys.min())) // SUBPIX))
+        j1 = min(wj1, (int(ys.max()) - 128) // SUBPIX)
         if i0 > i1 or j0 > j1:
             continue
         s = 1 if setup["area2"][t] > 0 else -1
@@ -514,6 +529,41 @@ def _substitute(value: torch.Tensor, teacher) -> torch.Tensor:
     return value + (tv - value).detach()
 
 
+def shade_pixels(scene: dict, verts: torch.Tensor, light_params: torch.Tensor, albedo: torch.Tensor, maps: list,
+                 clipc: torch.Tensor, ids: np.ndarray):
+    """Camera pass of Alg. 2 with Lambert shading (suppl. Sec. A) at the
+    covered pixels of ``ids``: world position x and normal n interpolated with
+    the perspective-correct barycentrics, visibility of every light from its
+    (Q, moment map) in ``maps``, colour = albedo * sum_l I_l v_l max(0, n.omega_l).
+    Returns (rows, cols, rgb, per-light visibility)."""
+    P = scene["params"]
+    tris = torch.as_tensor(scene["tris"].astype(np.int64))
+    jj, ii, tri, b = barycentrics(clipc, tris, ids)
+    tv = tris[tri]
+    x = (b[:, :, None] * verts[tv]).sum(1)
+    vn = vertex_normals(verts, tris)
+    n = (b[:, :, None] * vn[tv]).sum(1)
+    n = n / torch.sqrt((n * n).sum(1, keepdim=True))
+    xh = torch.cat([x, torch.ones((x.shape[0], 1), dtype=F64)], 1)
+    radiance = torch.zeros((x.shape[0], 3), dtype=F64)
+    vis_all = []
+    for li, light in enumerate(scene["lights"]):
+        Q, mom = maps[li]
+        vis = light_visibility(Q, mom, xh, float(P["min_variance"]))
+        if int(light["type"]) == 0:
+            dl = light_params[li, 3:6]
+            omega = -(dl / torch.sqrt((dl * dl).sum()))[None, :].expand_as(x)
+        else:
+            to = light_params[li, 0:3][None, :] - x
+            omega = to / torch.sqrt((to * to).sum(1, keepdim=True))
+        lam = torch.clamp((n * omega).sum(1), min=0.0)
+        I = torch.as_tensor(light["intensity"], dtype=F64)
+        radiance = radiance + (vis * lam)[:, None] * I[None, :]
+        vis_all.append(vis)
+    mat = torch.as_tensor(scene["tri_mat"].astype(np.int64))[tri]
+    return jj, ii, albedo[mat] * radiance, vis_all
+
+
 def render(scene: dict, verts: torch.Tensor = None, light_params: torch.Tensor = None,
            albedo: torch.Tensor = None, teacher: dict = None, keep: bool = True) -> dict:
     """Forward pass: Alg. 1 per light, then the camera pass with Alg. 2 and
@@ -572,31 +622,7 @@ def render(scene: dict, verts: torch.Tensor = None, light_params: torch.Tensor =
     stc = setup_view(clip_pinned(M32, V32), tris_np, Wc, Hc)
     rasc = raster(stc, tris_np)
     clipc = vh @ torch.as_tensor(M32, dtype=F64).T
-    jj, ii, tri, b = barycentrics(clipc, tris, rasc["ids"])
-    tv = tris[tri]
-    x = (b[:, :, None] * verts[tv]).sum(1)
-    vn = vertex_normals(verts, tris)
-    n = (b[:, :, None] * vn[tv]).sum(1)
-    n = n / torch.sqrt((n * n).sum(1, keepdim=True))
-    xh = torch.cat([x, torch.ones((x.shape[0], 1), dtype=F64)], 1)
-    radiance = torch.zeros((x.shape[0], 3), dtype=F64)
-    vis_all = []
-    for li, light in enumerate(scene["lights"]):
-        Q, mom = maps[li]
-        R = int(light["res"])
-        vis = light_visibility(Q, mom, xh, float(P["min_variance"]))
-        if int(light["type"]) == 0:
-            dl = light_params[li, 3:6]
-            omega = -(dl / torch.sqrt((dl * dl).sum()))[None, :].expand_as(x)
-        else:
-            to = light_params[li, 0:3][None, :] - x
-            omega = to / torch.sqrt((to * to).sum(1, keepdim=True))
-        lam = torch.clamp((n * omega).sum(1), min=0.0)
-        I = torch.as_tensor(light["intensity"], dtype=F64)
-        radiance = radiance + (vis * lam)[:, None] * I[None, :]
-        vis_all.append(vis)
-    mat = torch.as_tensor(scene["tri_mat"].astype(np.int64))[tri]
-    rgb = albedo[mat] * radiance
+    jj, ii, rgb, vis_all = shade_pixels(scene, verts, light_params, albedo, maps, clipc, rasc["ids"])
     color = torch.zeros((Hc, Wc, 4), dtype=F64)
     color = color.index_put((torch.as_tensor(jj), torch.as_tensor(ii)),
                             torch.cat([rgb, torch.ones((rgb.shape[0], 1), dtype=F64)], 1))

@@ -1,0 +1,155 @@
+"""Spot checks of full-size frames in the launch configuration the benchmark
+times (the default renderer: per-view streams, the same kernels): config 2
+(50k-triangle displaced icosphere, 1024² spot map and image) and config 3
+(330k triangles in 64 objects, two 2048² maps, 1920x1080 image).
+
+The oracle cannot render these frames whole in seconds, so it checks windows
+of them (its raster cut to a pixel window is the same computation on fewer
+pixels) and, where a stage is cheap at full size (the moment filter), the
+whole map:
+- triangle ids and depth keys in windows of every view: bit-identical;
+- light depth samples f in the windows, the full moment filter fed the GPU's
+  f~, and the camera colour in the windows fed the GPU's moment maps:
+  |g - o| <= 1e-5 + 1e-4 |o|;
+- the albedo gradient: the image is linear in the albedo, so the L2 loss is
+  quadratic in it and a central difference along any direction equals the
+  directional derivative up to rounding."""
+import numpy as np
+import pytest
+import torch
+
+import scenes
+from oracle import dsm_oracle as O
+from parity_util import F64, assert_close
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS = {"config2": scenes.config2, "config3": scenes.config3}
+WIN = 32
+
+
+def _windows(W, H, seed, n=3):
+    rng = np.random.default_rng(seed)
+    wins = [((W - WIN) // 2, (H - WIN) // 2)]
+    wins += [(int(rng.integers(0, W - WIN)), int(rng.integers(0, H - WIN))) for _ in range(n)]
+    return [(i0, i0 + WIN - 1, j0, j0 + WIN - 1) for i0, j0 in wins]
+
+
+@pytest.fixture(scope="module", params=list(CONFIGS))
+def frame(request):
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    sc = CONFIGS[request.param]()
+    r = dsm.Renderer(sc)
+    image = r.forward()
+    r.ctx.sync()
+    L = len(sc["lights"])
+    cam = sc["camera"]
+    W, H = int(cam["width"]), int(cam["height"])
+    d = {"sc": sc, "r": r, "dsm": dsm, "image": image.cpu().numpy(), "gbuf": [], "fmap": [], "ftilde": [], "mom": []}
+    for w in range(L + 1):
+        RW, RH = (sc["lights"][w]["res"],) * 2 if w < L else (W, H)
+        d["gbuf"].append(r.ctx.debug(dsm.DBG_GBUF, w, (RH, RW, 4)).cpu())
+    for l, Lt in enumerate(sc["lights"]):
+        R = Lt["res"]
+        d["fmap"].append(r.ctx.debug(dsm.DBG_F, l, (R, R, 2)).cpu().numpy())
+        d["ftilde"].append(r.ctx.debug(dsm.DBG_FTILDE, l, (R, R, 2)).cpu().numpy())
+        d["mom"].append(r.ctx.debug(dsm.DBG_MOMENTS, l, (R, R, 2)).cpu().numpy())
+    d["color"] = r.ctx.debug(dsm.DBG_COLOR, 0, (H, W, 4)).cpu().numpy()
+    tris = sc["tris"].astype(np.int64)
+    V32 = sc["verts"].astype(np.float32)
+    views = []
+    for l, Lt in enumerate(sc["lights"]):
+        lp = torch.as_tensor(np.concatenate([Lt["pos"], Lt["dir"]]), dtype=F64)
+        Q = O.light_matrix(Lt, lp[:3], lp[3:])
+        views.append((Q, Q.detach().numpy().astype(np.float32)[:4], Lt["res"], Lt["res"]))
+    views.append((None, np.asarray(cam["clip"], np.float32), W, H))
+    d["views"] = [(Q, M, RW, RH, O.setup_view(O.clip_pinned(M, V32), tris, RW, RH)) for Q, M, RW, RH in views]
+    return d
+
+
+def _ids(g):
+    return g[..., 0].contiguous().view(torch.int32).numpy().astype(np.int64)
+
+
+def test_ids_and_depth_keys_bit_exact_in_windows(frame):
+    tris = frame["sc"]["tris"].astype(np.int64)
+    for w, (_, _, RW, RH, st) in enumerate(frame["views"]):
+        ids = _ids(frame["gbuf"][w])
+        zkey = frame["gbuf"][w][..., 3].numpy()
+        for win in _windows(RW, RH, 100 + w):
+            ras = O.raster(st, tris, window=win)
+            i0, i1, j0, j1 = win
+            got, exp = ids[j0:j1 + 1, i0:i1 + 1], ras["ids"][j0:j1 + 1, i0:i1 + 1]
+            assert np.array_equal(got, exp), f"view {w} window {win}: {(got != exp).sum()} ids differ"
+            cov = exp > 0
+            assert np.array_equal(zkey[j0:j1 + 1, i0:i1 + 1][cov], ras["zkey"][j0:j1 + 1, i0:i1 + 1][cov])
+
+
+def test_light_depth_samples_in_windows(frame):
+    sc = frame["sc"]
+    tris_np = sc["tris"].astype(np.int64)
+    tris = torch.as_tensor(tris_np)
+    verts = torch.as_tensor(sc["verts"], dtype=F64)
+    vh = torch.cat([verts, torch.ones((verts.shape[0], 1), dtype=F64)], 1)
+    for l in range(len(sc["lights"])):
+        Q, _, R, _, st = frame["views"][l]
+        clip, depth = vh @ Q[:4].T, vh @ Q[4]
+        for win in _windows(R, R, 200 + l):
+            ras = O.raster(st, tris_np, window=win)
+            jj, ii, tri, b = O.barycentrics(clip, tris, ras["ids"])
+            f = (b * depth[tris[tri]]).sum(1).detach().numpy()
+            assert_close(frame["fmap"][l][jj, ii, 0], f, f"f, light {l}, window {win}")
+            assert_close(frame["fmap"][l][jj, ii, 1], f * f, f"f^2, light {l}, window {win}")
+
+
+def test_moment_filter_full_maps(frame):
+    sc = frame["sc"]
+    P = sc["params"]
+    for l, Lt in enumerate(sc["lights"]):
+        w = O.filter_weights(Lt["sigma"], Lt["radius"], P.get("filter_kind", 0))
+        exp = O.separable_filter(torch.as_tensor(frame["ftilde"][l], dtype=F64), w, P.get("filter_boundary", 0))
+        assert_close(frame["mom"][l], exp.numpy(), f"moments, light {l}")
+
+
+def test_camera_colour_in_windows(frame):
+    sc = frame["sc"]
+    L = len(sc["lights"])
+    tris_np = sc["tris"].astype(np.int64)
+    verts = torch.as_tensor(sc["verts"], dtype=F64)
+    vh = torch.cat([verts, torch.ones((verts.shape[0], 1), dtype=F64)], 1)
+    lp = torch.as_tensor(np.stack([np.concatenate([l["pos"], l["dir"]]) for l in sc["lights"]]), dtype=F64)
+    albedo = torch.as_tensor(sc["albedo"], dtype=F64)
+    maps = [(frame["views"][l][0], torch.as_tensor(frame["mom"][l], dtype=F64)) for l in range(L)]
+    _, M, W, H, st = frame["views"][L]
+    clipc = vh @ torch.as_tensor(M, dtype=F64).T
+    for win in _windows(W, H, 300):
+        ras = O.raster(st, tris_np, window=win)
+        jj, ii, rgb, _ = O.shade_pixels(sc, verts, lp, albedo, maps, clipc, ras["ids"])
+        assert_close(frame["color"][jj, ii, :3], rgb.detach().numpy(), f"colour, window {win}")
+        assert (frame["color"][jj, ii, 3] == 1.0).all()
+
+
+def test_albedo_gradient_matches_exact_central_difference(frame):
+    sc, r, dsm = frame["sc"], frame["r"], frame["dsm"]
+    target = torch.as_tensor(frame["image"], device="cuda") * 0.9
+    loss = torch.zeros(1, device="cuda")
+    img = torch.empty_like(target)
+    gimg = torch.empty_like(target)
+
+    def L_of(alb):
+        r.forward(albedo=alb, image=img)
+        dsm.l2_loss_grad(img, target, loss, gimg)
+        return float(loss.item())
+
+    alb0 = r.albedo.clone()
+    L_of(alb0)
+    _, _, dalb = r.backward(gimg)
+    g = dalb.double().cpu()
+    eps = torch.as_tensor(np.random.default_rng(7).normal(size=tuple(alb0.shape)), dtype=torch.float32,
+                          device="cuda")
+    h = 0.05
+    fd = (L_of((alb0 + h * eps).contiguous()) - L_of((alb0 - h * eps).contiguous())) / (2 * h)
+    dd = float((g * eps.double().cpu()).sum())
+    assert abs(fd - dd) <= 1e-3 * abs(dd) + 1e-9, f"central difference {fd} vs gradient {dd}"
+    r.forward(albedo=alb0, image=img)

@@ -566,3 +566,24 @@ def test_pinned_transform_is_rounded_float64_product():
     c64 = np.concatenate([V, np.ones((500, 1), np.float32)], 1).astype(np.float64) @ M.astype(np.float64).T
     scale = np.abs(M).astype(np.float64) @ np.concatenate([np.abs(V), np.ones((500, 1))], 1).T.astype(np.float64)
     assert (np.abs(c32 - c64) <= 4 * np.finfo(np.float32).eps * scale.T).all()
+
+
+def test_raster_window_matches_full_frame():
+    """The windowed raster used for full-size spot checks is the full raster cut
+    to the window: same ids and depth keys inside, background outside."""
+    import scenes
+    sc = scenes.tiny_scene(4, res=70, img=64, freq=3)
+    tris = sc["tris"].astype(np.int64)
+    L = sc["lights"][0]
+    lp = torch.as_tensor(np.concatenate([L["pos"], L["dir"]]), dtype=O.F64)
+    Q = O.light_matrix(L, lp[:3], lp[3:]).numpy().astype(np.float32)
+    st = O.setup_view(O.clip_pinned(Q[:4], sc["verts"].astype(np.float32)), tris, 70, 70)
+    full = O.raster(st, tris)
+    for win in ((0, 69, 0, 69), (13, 44, 20, 41), (60, 69, 0, 5), (35, 35, 35, 35)):
+        part = O.raster(st, tris, window=win)
+        i0, i1, j0, j1 = win
+        inside = np.zeros((70, 70), bool)
+        inside[j0:j1 + 1, i0:i1 + 1] = True
+        assert np.array_equal(part["ids"][inside], full["ids"][inside])
+        assert np.array_equal(part["zkey"][inside], full["zkey"][inside])
+        assert (part["ids"][~inside] == 0).all()
