@@ -19,8 +19,10 @@ def close(gpu, ref, atol=ATOL, rtol=RTOL):
     g = np.asarray(gpu, np.float64)
     o = np.asarray(ref, np.float64)
     err = np.abs(g - o) - (atol + rtol * np.abs(o))
-    k = int(np.argmax(err)) if err.size else 0
-    return (err.size == 0 or err.max() <= 0), (float(err.max()) if err.size else 0.0), np.unravel_index(k, err.shape)
+    if err.size == 0:
+        return True, 0.0, ()
+    k = int(np.argmax(err))
+    return err.max() <= 0, float(err.max()), np.unravel_index(k, err.shape)
 
 
 def assert_close(gpu, ref, what, atol=ATOL, rtol=RTOL):
