@@ -182,6 +182,56 @@ dsm_status dsm_filter_moments_adjoint(dsm_ctx* ctx, const float* gout, float* gi
 dsm_status dsm_filter_moments_noalloc(const float* in, float* out, int32_t res, float sigma,
                                       int32_t radius, int32_t kind, int32_t boundary, void* stream);
 
+/* ---- Batched frames.  n independent scenes (each a mesh, lights, a camera and
+ * an L2 target) advanced by one call per step: forward, L2 loss
+ * (dsm_l2_loss_grad) and backward of every scene.  The paper renders one view
+ * at a time and has no batch call; per scene the step is exactly dsm_render,
+ * dsm_l2_loss_grad and dsm_render_backward.
+ *
+ * Each scene has its own context (dsm_batch_context: set its topology there
+ * before the first step; its debug copies work as usual) and its own stream,
+ * with the scene's views serialised on that stream; the scenes overlap.  The
+ * first step with a given set of items and params runs eagerly (it sizes
+ * every context; this is the only step with host synchronisation) and then
+ * records the same step into one CUDA graph; a later step whose items
+ * (pointers, sizes, light and camera descriptions) and params are unchanged
+ * replays that graph with one launch.  The contents of the device buffers
+ * (vertices, light parameters, albedo, targets) may change between steps.
+ * One params serves every scene; params->stream must not be the legacy
+ * default stream (graph capture); params->recompute_in_backward must be 0. */
+typedef struct dsm_batch dsm_batch;
+typedef struct dsm_batch_item {
+  dsm_mesh          mesh;
+  const dsm_light*  lights;        /* host, n_lights (read at every step)          */
+  const float*      light_params;  /* device, n_lights x 6 (see dsm_render)        */
+  int32_t           n_lights;
+  dsm_camera        camera;
+  float*            image;         /* device, H x W x 4, written                   */
+  const float*      target;        /* device, H x W x 4                             */
+  float*            loss;          /* device, 1 float, written                      */
+  float*            dL_dimage;     /* device, H x W x 4, caller-owned scratch       */
+  float*            dL_dverts;     /* device, n_verts x 3, written (NULL: skipped)  */
+  float*            dL_dlight;     /* device, n_lights x 6, written (NULL: skipped) */
+  float*            dL_dalbedo;    /* device, n_materials x 3, written (NULL: skip) */
+} dsm_batch_item;
+
+/* Create a batch for up to n scenes (n contexts and streams); destroy frees
+ * them all.  DSM_ERR_CUDA / DSM_ERR_OOM when the device objects cannot be made. */
+dsm_status dsm_batch_create(dsm_batch** out, int32_t n);
+void       dsm_batch_destroy(dsm_batch* b);
+/* The context of scene i (owned by the batch), NULL when i is out of range. */
+dsm_ctx*   dsm_batch_context(dsm_batch* b, int32_t i);
+/* One step of scenes 0..n-1 (n <= the batch size).  Asynchronous on
+ * params->stream except for the eager first step.  Errors: DSM_ERR_INVALID_ARG
+ * for bad items, a scene's own error (dsm_batch_last_error names the scene),
+ * DSM_ERR_CUDA for stream, capture or graph failures. */
+dsm_status dsm_batch_step(dsm_batch* b, const dsm_batch_item* items, int32_t n, const dsm_params* params);
+/* dsm_sync of every scene's context. */
+dsm_status dsm_batch_sync(dsm_batch* b);
+/* Kernels one recorded step launches (counted while recording). */
+uint64_t   dsm_batch_kernels_per_step(dsm_batch* b);
+const char* dsm_batch_last_error(dsm_batch* b);
+
 /* Wait for the context's stream and report device-side errors (capacity
  * overflow, timeouts) raised since the last dsm_sync. */
 dsm_status dsm_sync(dsm_ctx* ctx);

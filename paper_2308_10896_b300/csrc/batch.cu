@@ -1,0 +1,195 @@
+// Batched frames: n independent scenes advanced by one call per step
+// (forward, L2 loss, backward of every scene).  Each scene keeps its own
+// context (its scratch and saved state) and runs on its own stream with its
+// views serialised on that stream; the scenes overlap one another.  The first
+// step with a given set of buffers runs eagerly, which sizes every context,
+// and then records the same step into one CUDA graph; later steps with the
+// same buffers replay the graph with a single launch.
+#include <cstring>
+#include <string>
+#include <vector>
+#include "dsm.h"
+#include "kernels.h"
+
+namespace dsm {
+void set_serial_views(dsm_ctx* ctx, bool serial);
+}
+
+struct dsm_batch {
+  int n = 0;
+  std::vector<dsm_ctx*> ctx;
+  std::vector<cudaStream_t> ss;
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t sig = 0;
+  unsigned long long kernels_per_step = 0;
+  std::string err = "ok";
+};
+
+namespace {
+
+uint64_t mix_bytes(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+// Everything a recorded step bakes in: buffers, sizes, host-side light and
+// camera descriptions, parameters.
+uint64_t step_signature(const dsm_batch_item* items, int n, const dsm_params* params) {
+  uint64_t h = 1469598103934665603ull;
+  h = mix_bytes(h, &n, sizeof(n));
+  h = mix_bytes(h, params, sizeof(dsm_params));
+  for (int i = 0; i < n; ++i) {
+    const dsm_batch_item& it = items[i];
+    h = mix_bytes(h, &it, sizeof(dsm_batch_item));
+    if (it.lights && it.n_lights > 0) h = mix_bytes(h, it.lights, sizeof(dsm_light) * (size_t)it.n_lights);
+  }
+  return h;
+}
+
+dsm_status batch_fail(dsm_batch* b, dsm_status s, const std::string& m) {
+  b->err = m;
+  return s;
+}
+
+// Enqueue one step of every scene on the scene streams, forked from and joined
+// back into `origin`.
+dsm_status issue_step(dsm_batch* b, const dsm_batch_item* items, int n, const dsm_params* params,
+                      cudaStream_t origin) {
+  if (cudaEventRecord(b->ev_fork, origin) != cudaSuccess) return DSM_ERR_CUDA;
+  for (int i = 0; i < n; ++i) {
+    const dsm_batch_item& it = items[i];
+    cudaStream_t s = b->ss[i];
+    if (cudaStreamWaitEvent(s, b->ev_fork, 0) != cudaSuccess) return DSM_ERR_CUDA;
+    dsm_params p = *params;
+    p.stream = s;
+    dsm_status st =
+        dsm_render(b->ctx[i], &it.mesh, it.lights, it.light_params, it.n_lights, &it.camera, &p, it.image);
+    if (st != DSM_OK) return batch_fail(b, st, std::string("scene ") + std::to_string(i) + ": " +
+                                                   dsm_last_error(b->ctx[i]));
+    const int64_t npx = (int64_t)it.camera.width * it.camera.height * 4;
+    st = dsm_l2_loss_grad(it.image, it.target, npx, it.loss, it.dL_dimage, s);
+    if (st != DSM_OK) return batch_fail(b, st, "loss of scene " + std::to_string(i));
+    st = dsm_render_backward(b->ctx[i], it.dL_dimage, it.dL_dverts, it.dL_dlight, it.dL_dalbedo);
+    if (st != DSM_OK) return batch_fail(b, st, std::string("scene ") + std::to_string(i) + ": " +
+                                                   dsm_last_error(b->ctx[i]));
+    if (cudaEventRecord(b->ev_join[i], s) != cudaSuccess) return DSM_ERR_CUDA;
+    if (cudaStreamWaitEvent(origin, b->ev_join[i], 0) != cudaSuccess) return DSM_ERR_CUDA;
+  }
+  return DSM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dsm_status dsm_batch_create(dsm_batch** out, int32_t n) {
+  if (!out || n < 1) return DSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  dsm_batch* b = new dsm_batch();
+  b->n = n;
+  b->ctx.assign(n, nullptr);
+  b->ss.assign(n, nullptr);
+  b->ev_join.assign(n, nullptr);
+  dsm_status st = DSM_OK;
+  for (int i = 0; i < n && st == DSM_OK; ++i) {
+    st = dsm_create(&b->ctx[i]);
+    if (st == DSM_OK) dsm::set_serial_views(b->ctx[i], true);
+    if (st == DSM_OK && cudaStreamCreateWithFlags(&b->ss[i], cudaStreamNonBlocking) != cudaSuccess)
+      st = DSM_ERR_CUDA;
+    if (st == DSM_OK && cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+      st = DSM_ERR_CUDA;
+  }
+  if (st == DSM_OK && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+    st = DSM_ERR_CUDA;
+  if (st != DSM_OK) {
+    dsm_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return DSM_OK;
+}
+
+void dsm_batch_destroy(dsm_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (int i = 0; i < b->n; ++i) {
+    if (b->ctx[i]) dsm_destroy(b->ctx[i]);
+    if (b->ss[i]) cudaStreamDestroy(b->ss[i]);
+    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  delete b;
+}
+
+dsm_ctx* dsm_batch_context(dsm_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= b->n) return nullptr;
+  return b->ctx[i];
+}
+
+dsm_status dsm_batch_step(dsm_batch* b, const dsm_batch_item* items, int32_t n, const dsm_params* params) {
+  if (!b || !items || !params || n < 1 || n > b->n) return DSM_ERR_INVALID_ARG;
+  if (params->recompute_in_backward) return batch_fail(b, DSM_ERR_INVALID_ARG, "recompute_in_backward unsupported");
+  for (int i = 0; i < n; ++i)
+    if (!items[i].image || !items[i].target || !items[i].loss || !items[i].dL_dimage)
+      return batch_fail(b, DSM_ERR_INVALID_ARG, "scene " + std::to_string(i) + ": null image/target/loss buffer");
+  cudaStream_t origin = (cudaStream_t)params->stream;
+  const uint64_t sig = step_signature(items, n, params);
+  if (b->exec && sig == b->sig) {
+    if (cudaGraphLaunch(b->exec, origin) != cudaSuccess) return batch_fail(b, DSM_ERR_CUDA, "graph launch");
+    return DSM_OK;
+  }
+  // eager step: sizes every context (host synchronisations happen here only)
+  dsm_status st = issue_step(b, items, n, params, origin);
+  if (st != DSM_OK) return st;
+  if (cudaStreamSynchronize(origin) != cudaSuccess) return batch_fail(b, DSM_ERR_CUDA, "eager step");
+  for (int i = 0; i < n; ++i) {
+    st = dsm_sync(b->ctx[i]);
+    if (st != DSM_OK) return batch_fail(b, st, std::string("scene ") + std::to_string(i) + ": " +
+                                                   dsm_last_error(b->ctx[i]));
+  }
+  // record the same step into a graph for the next calls
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  const unsigned long long k0 = dsm_kernel_launches();
+  if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return batch_fail(b, DSM_ERR_CUDA, "begin capture (the batch needs a stream other than the legacy default)");
+  st = issue_step(b, items, n, params, origin);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(origin, &graph);
+  if (st != DSM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ce != cudaSuccess || !graph) return batch_fail(b, DSM_ERR_CUDA, "end capture");
+  const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    b->exec = nullptr;
+    return batch_fail(b, DSM_ERR_CUDA, "graph instantiate");
+  }
+  b->kernels_per_step = dsm_kernel_launches() - k0;
+  b->sig = sig;
+  return DSM_OK;
+}
+
+dsm_status dsm_batch_sync(dsm_batch* b) {
+  if (!b) return DSM_ERR_INVALID_ARG;
+  for (int i = 0; i < b->n; ++i) {
+    const dsm_status st = dsm_sync(b->ctx[i]);
+    if (st != DSM_OK) return batch_fail(b, st, std::string("scene ") + std::to_string(i) + ": " +
+                                                   dsm_last_error(b->ctx[i]));
+  }
+  return DSM_OK;
+}
+
+uint64_t dsm_batch_kernels_per_step(dsm_batch* b) { return b ? b->kernels_per_step : 0; }
+
+const char* dsm_batch_last_error(dsm_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+}  // extern "C"

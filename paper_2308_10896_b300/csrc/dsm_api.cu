@@ -90,6 +90,8 @@ struct dsm_ctx {
   cudaEvent_t ev_fork = nullptr, ev_bfork = nullptr, ev_join[DSM_MAX_LIGHTS + 1] = {};
   // per-stage timing
   bool prof = false;
+  // views serialised on the caller's stream (batched scenes overlap one another instead)
+  bool serial = false;
   struct Rec { int stage; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> free_events;
@@ -212,11 +214,13 @@ cudaError_t ensure_streams(dsm_ctx* c) {
 // Stream of view w: its own stream, or the caller's while stage profiling is
 // on (profiling serialises the views so that each stage's events bracket only
 // its own kernels).
-cudaStream_t view_stream(const dsm_ctx* c, int w, cudaStream_t st) { return c->prof ? st : c->vs[w]; }
+cudaStream_t view_stream(const dsm_ctx* c, int w, cudaStream_t st) {
+  return (c->prof || c->serial) ? st : c->vs[w];
+}
 
 // All view streams wait for the work enqueued so far on st.
 cudaError_t fork_views(dsm_ctx* c, cudaStream_t st, cudaEvent_t ev, int n_views) {
-  if (c->prof) return cudaSuccess;
+  if (c->prof || c->serial) return cudaSuccess;
   cudaError_t e = cudaEventRecord(ev, st);
   for (int w = 0; w < n_views && e == cudaSuccess; ++w) e = cudaStreamWaitEvent(c->vs[w], ev, 0);
   return e;
@@ -224,7 +228,7 @@ cudaError_t fork_views(dsm_ctx* c, cudaStream_t st, cudaEvent_t ev, int n_views)
 
 // st waits for the work enqueued so far on the first n view streams.
 cudaError_t join_views(dsm_ctx* c, cudaStream_t st, int n_views) {
-  if (c->prof) return cudaSuccess;
+  if (c->prof || c->serial) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   for (int w = 0; w < n_views && e == cudaSuccess; ++w) {
     e = cudaEventRecord(c->ev_join[w], c->vs[w]);
@@ -239,6 +243,13 @@ uint64_t mix(uint64_t h, uint64_t v) {
 }
 
 }  // namespace
+
+namespace dsm {
+// Batched scenes: each context keeps its views on the caller's stream.
+void set_serial_views(dsm_ctx* ctx, bool serial) {
+  if (ctx) ctx->serial = serial;
+}
+}  // namespace dsm
 
 extern "C" {
 

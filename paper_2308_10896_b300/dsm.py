@@ -26,7 +26,9 @@ DBG_GBUF, DBG_F, DBG_FTILDE, DBG_MOMENTS, DBG_COLOR, DBG_Q, DBG_SNAP, DBG_GM, DB
 EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_render_backward",
             "dsm_l2_loss_grad", "dsm_filter_moments", "dsm_sync", "dsm_last_error", "dsm_debug_copy",
             "dsm_profile_enable", "dsm_profile_stage_count", "dsm_profile_stage_name", "dsm_profile_read",
-            "dsm_kernel_launches", "dsm_filter_moments_noalloc", "dsm_filter_moments_adjoint"]
+            "dsm_kernel_launches", "dsm_filter_moments_noalloc", "dsm_filter_moments_adjoint",
+            "dsm_batch_create", "dsm_batch_destroy", "dsm_batch_context", "dsm_batch_step", "dsm_batch_sync",
+            "dsm_batch_kernels_per_step", "dsm_batch_last_error"]
 
 
 class DsmError(RuntimeError):
@@ -56,6 +58,13 @@ class Params(ctypes.Structure):
     _fields_ = [("min_variance", ctypes.c_float), ("filter_kind", ctypes.c_int32),
                 ("filter_boundary", ctypes.c_int32), ("aa_shadow", ctypes.c_int32), ("aa_final", ctypes.c_int32),
                 ("recompute_in_backward", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("mesh", Mesh), ("lights", ctypes.c_void_p), ("light_params", ctypes.c_void_p),
+                ("n_lights", ctypes.c_int32), ("camera", Camera), ("image", ctypes.c_void_p),
+                ("target", ctypes.c_void_p), ("loss", ctypes.c_void_p), ("dL_dimage", ctypes.c_void_p),
+                ("dL_dverts", ctypes.c_void_p), ("dL_dlight", ctypes.c_void_p), ("dL_dalbedo", ctypes.c_void_p)]
 
 
 _lib = None
@@ -89,6 +98,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dsm_kernel_launches": ([], ctypes.c_uint64),
         "dsm_filter_moments_noalloc": ([P, P, I32, ctypes.c_float, I32, I32, I32, P], I32),
         "dsm_filter_moments_adjoint": ([P, P, P, I32, ctypes.c_float, I32, I32, I32, P], I32),
+        "dsm_batch_create": ([ctypes.POINTER(P), I32], I32),
+        "dsm_batch_destroy": ([P], None),
+        "dsm_batch_context": ([P, I32], P),
+        "dsm_batch_step": ([P, P, I32, P], I32),
+        "dsm_batch_sync": ([P], I32),
+        "dsm_batch_kernels_per_step": ([P], ctypes.c_uint64),
+        "dsm_batch_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -299,3 +315,82 @@ class DSMFunction(torch.autograd.Function):
 
 def render(verts, light_params, albedo, renderer: Renderer):
     return DSMFunction.apply(verts, light_params, albedo, renderer)
+
+
+class Batch:
+    """Batched frames (dsm_batch_*): every scene's forward, L2 loss against its
+    target and backward in one call per step, replayed from a CUDA graph after
+    the first step.  Device copies of each scene and its output buffers are
+    held here; `step` runs on a dedicated non-default stream."""
+
+    def __init__(self, scenes: list, targets: list, device: str = "cuda"):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        st = self.lib.dsm_batch_create(ctypes.byref(h), len(scenes))
+        if st != DSM_OK:
+            raise DsmError(st, "dsm_batch_create")
+        self.h = h
+        self.stream = torch.cuda.Stream()
+        self.params = params_struct(scenes[0]["params"], self.stream)
+        self.scenes = []
+        items = []
+        for i, (sc, tgt) in enumerate(zip(scenes, targets)):
+            d = {"verts": torch.as_tensor(sc["verts"], dtype=torch.float32, device=device).contiguous(),
+                 "tris": torch.as_tensor(sc["tris"], dtype=torch.int32, device=device).contiguous(),
+                 "tri_mat": torch.as_tensor(sc["tri_mat"], dtype=torch.int32, device=device).contiguous(),
+                 "albedo": torch.as_tensor(sc["albedo"], dtype=torch.float32, device=device).contiguous(),
+                 "light_params": torch.as_tensor(
+                     np.stack([np.concatenate([l["pos"], l["dir"]]) for l in sc["lights"]]).astype(np.float32),
+                     device=device).contiguous()}
+            W, H = int(sc["camera"]["width"]), int(sc["camera"]["height"])
+            V, L, M = d["verts"].shape[0], len(sc["lights"]), d["albedo"].shape[0]
+            d["image"] = torch.zeros((H, W, 4), dtype=torch.float32, device=device)
+            d["target"] = torch.as_tensor(tgt, dtype=torch.float32, device=device).contiguous()
+            d["loss"] = torch.zeros(1, dtype=torch.float32, device=device)
+            d["gimg"] = torch.empty((H, W, 4), dtype=torch.float32, device=device)
+            d["dverts"] = torch.empty((V, 3), dtype=torch.float32, device=device)
+            d["dlight"] = torch.empty((max(L, 1), 6), dtype=torch.float32, device=device)
+            d["dalbedo"] = torch.empty((M, 3), dtype=torch.float32, device=device)
+            d["lights"] = (Light * max(1, L))(*[light_struct(l) for l in sc["lights"]])
+            ctx = self.lib.dsm_batch_context(self.h, i)
+            st = self.lib.dsm_set_topology(ctx, _ptr(d["tris"]), d["tris"].shape[0], V)
+            if st != DSM_OK:
+                raise DsmError(st, self.lib.dsm_last_error(ctx).decode())
+            it = BatchItem()
+            it.mesh = Mesh(_ptr(d["verts"]), V, _ptr(d["tris"]), d["tris"].shape[0], _ptr(d["tri_mat"]),
+                           _ptr(d["albedo"]), M)
+            it.lights = ctypes.cast(d["lights"], ctypes.c_void_p)
+            it.light_params, it.n_lights = _ptr(d["light_params"]), L
+            it.camera = camera_struct(sc["camera"])
+            it.image, it.target, it.loss, it.dL_dimage = (_ptr(d["image"]), _ptr(d["target"]), _ptr(d["loss"]),
+                                                          _ptr(d["gimg"]))
+            it.dL_dverts, it.dL_dlight, it.dL_dalbedo = _ptr(d["dverts"]), _ptr(d["dlight"]), _ptr(d["dalbedo"])
+            items.append(it)
+            self.scenes.append(d)
+        self.items = (BatchItem * len(items))(*items)
+        torch.cuda.synchronize()
+
+    def step(self):
+        st = self.lib.dsm_batch_step(self.h, ctypes.cast(self.items, ctypes.c_void_p), len(self.scenes),
+                                     ctypes.byref(self.params))
+        if st != DSM_OK:
+            raise DsmError(st, self.lib.dsm_batch_last_error(self.h).decode())
+
+    def sync(self):
+        st = self.lib.dsm_batch_sync(self.h)
+        if st != DSM_OK:
+            raise DsmError(st, self.lib.dsm_batch_last_error(self.h).decode())
+
+    def kernels_per_step(self) -> int:
+        return int(self.lib.dsm_batch_kernels_per_step(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dsm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
