@@ -36,6 +36,7 @@ extern "C" {
 #endif
 
 #define DSM_MAX_LIGHTS 8
+#define DSM_MAX_CAMERAS 8
 
 typedef enum dsm_status {
   DSM_OK = 0,
@@ -101,7 +102,9 @@ typedef struct dsm_params {
   int32_t filter_boundary;  /* 0 clamp to edge, 1 zero outside                              */
   int32_t aa_shadow;        /* 1: antialias (f, f^2) before filtering (Sec. 5 ablation: 0)  */
   int32_t aa_final;         /* 1: antialias the shaded image                                */
-  int32_t recompute_in_backward; /* reserved, must be 0                                     */
+  int32_t recompute_in_backward; /* 0: keep every view's buffers from forward to backward;
+                                   * 1: views share one light and one camera buffer set and
+                                   * the backward rebuilds what it reads (see dsm_render_cameras) */
   void*   stream;           /* cudaStream_t; NULL = legacy default stream                   */
 } dsm_params;
 
@@ -129,9 +132,50 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
  * Outputs (device, overwritten, any may be NULL to skip): dL_dverts n_verts x 3,
  * dL_dlight n_lights x 6 (position, direction; zero position gradient for
  * directional lights), dL_dalbedo n_materials x 3.  The mesh, light and
- * albedo buffers of that dsm_render must still hold the same values. */
+ * albedo buffers of that dsm_render must still hold the same values.
+ * DSM_ERR_INVALID_ARG when the last forward had several cameras. */
 dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_dverts,
                                float* dL_dlight, float* dL_dalbedo);
+
+/* Forward pass seen by n_cameras cameras (1..DSM_MAX_CAMERAS) under the same
+ * lights: each light's moment maps (Alg. 1) are built once and every camera
+ * is shaded with all of them (Alg. 2 + Lambert, final antialiasing).
+ * cameras: host array of n_cameras; images: host array of n_cameras device
+ * pointers, image c height_c x width_c x 4 (as in dsm_render).  dsm_render is
+ * this call with one camera; the result of camera c equals a dsm_render with
+ * camera c alone.
+ * With params->recompute_in_backward = 1 the views go one at a time through
+ * one light buffer set and one camera buffer set (device memory of one light
+ * view and one camera view instead of all of them, plus every light's moment
+ * maps); the backward then rasterises every view again and filters the
+ * moment maps again instead of reading stored ones.  Results are the same in
+ * both modes; with recomputation the debug copies of per-view buffers are
+ * unavailable. */
+dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* lights,
+                              const float* light_params, int32_t n_lights,
+                              const dsm_camera* cameras, int32_t n_cameras,
+                              const dsm_params* params, float* const* images);
+
+/* Backward pass of the last dsm_render_cameras (or dsm_render) on ctx for the
+ * loss summed over the cameras.  dL_dimages: host array of that call's
+ * n_cameras device pointers, each height_c x width_c x 4.  Outputs as in
+ * dsm_render_backward (gradients summed over the cameras). */
+dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dimages,
+                                       float* dL_dverts, float* dL_dlight, float* dL_dalbedo);
+
+/* Device memory held by ctx (its scratch and saved state), in bytes. */
+uint64_t dsm_memory_bytes(dsm_ctx* ctx);
+
+/* One Adam step (Kingma & Ba 2015, Algorithm 1) in place, for optimising the
+ * vertices (or any float parameters) with the gradients of the backward pass;
+ * the paper optimises its scene parameters with Adam.  params, m, v: device,
+ * n floats, read and overwritten (m, v start at zero before step 1); grads:
+ * device, n floats; step: 1-based step count t (bias corrections 1 - beta^t).
+ * params -= lr * m^ / (sqrt(v^) + eps) with m^ = m / (1 - beta1^t),
+ * v^ = v / (1 - beta2^t).  DSM_ERR_INVALID_ARG for a bad argument (beta outside
+ * [0, 1), eps <= 0, step < 1).  stream: cudaStream_t. */
+dsm_status dsm_adam_step(float* params, const float* grads, float* m, float* v, int64_t n, int32_t step,
+                         float lr, float beta1, float beta2, float eps, void* stream);
 
 /* L = mean((image - target)^2) over n floats and dL/dimage = 2 (image - target) / n.
  * image, target, dL_dimage: device, n floats; loss: device, one float (overwritten).
@@ -198,7 +242,9 @@ dsm_status dsm_filter_moments_noalloc(const float* in, float* out, int32_t res, 
  * replays that graph with one launch.  The contents of the device buffers
  * (vertices, light parameters, albedo, targets) may change between steps.
  * One params serves every scene; params->stream must not be the legacy
- * default stream (graph capture); params->recompute_in_backward must be 0. */
+ * default stream (graph capture).  With params->recompute_in_backward = 1
+ * each scene's context holds one light and one camera buffer set (see
+ * dsm_render_cameras). */
 typedef struct dsm_batch dsm_batch;
 typedef struct dsm_batch_item {
   dsm_mesh          mesh;
@@ -241,12 +287,12 @@ const char* dsm_last_error(dsm_ctx* ctx);
 
 /* Copy an internal buffer of the last dsm_render / dsm_render_backward into a
  * caller device buffer (stage-wise testing and profiling).  what:
- *  0 G-buffer of view index (lights 0..n-1, camera n): per pixel int32 id+1
+ *  0 G-buffer of view index (lights 0..n-1, then cameras n..): per pixel int32 id+1
  *    (0 = background), float b0, float b1, float depth key; 16 B per pixel
  *  1 f, f^2 before antialiasing (light index), float2 per texel
  *  2 f~, (f^2)~ after antialiasing (light), float2
  *  3 m1, m2 moment maps (light), float2
- *  4 camera colour before the final antialiasing, float4 per pixel
+ *  4 colour of camera index (0..n_cameras-1) before the final antialiasing, float4
  *  5 light matrices Q (20 floats per light: clip rows 0-3, depth row 4)
  *  6 snapped vertices of view index: int32 X, Y (24.8 fixed point), float ndc z,
  *    int32 valid; 16 B per vertex
@@ -254,8 +300,9 @@ const char* dsm_last_error(dsm_ctx* ctx);
  *  8 dL/d clip coordinates of view index, float4 per vertex (light views: the
  *    z slot holds dL/d vertex depth d, since clip z carries no gradient there)
  *  9 dL/d(f~, (f^2)~) (light), float2
- * 10 dL/d camera colour before the final antialiasing, float4 per pixel
- * bytes must equal the buffer size; returns DSM_ERR_INVALID_ARG otherwise. */
+ * 10 dL/d colour of camera index before the final antialiasing, float4 per pixel
+ * bytes must equal the buffer size; returns DSM_ERR_INVALID_ARG otherwise.
+ * After a forward with recompute_in_backward = 1 only 3, 5 and 7 are kept. */
 dsm_status dsm_debug_copy(dsm_ctx* ctx, int32_t what, int32_t index, void* dst, size_t bytes);
 
 /* Per-stage device timing: while enabled, dsm_render and dsm_render_backward

@@ -50,6 +50,7 @@ __all__ = [
     "light_matrix", "clip_pinned", "setup_view", "raster", "edge_adjacency", "silhouette_table",
     "barycentrics", "antialias", "filter_weights", "separable_filter", "bilinear",
     "chebyshev", "light_visibility", "vertex_normals", "render", "mse_loss", "render_and_grad",
+    "render_cameras_and_grad", "adam_step",
 ]
 
 
@@ -658,3 +659,38 @@ def render_and_grad(scene: dict, target, teacher: dict = None, verts=None, light
     gv, gl, ga = torch.autograd.grad(loss, [v, lp, al], allow_unused=True)
     out.update({"loss": loss.detach(), "grad_verts": gv, "grad_light": gl, "grad_albedo": ga})
     return out
+
+
+def render_cameras_and_grad(scene: dict, cameras: list, targets: list, verts=None, teachers: list = None) -> dict:
+    """Several cameras under the same lights: the loss is the sum over the
+    cameras of each image's mean squared error; each camera's image is
+    ``render`` with that camera (the light maps do not depend on the camera).
+    ``teachers`` optionally gives ``render``'s teacher per camera.  Returns
+    the images, the summed loss and its gradients."""
+    v = torch.as_tensor(scene["verts"] if verts is None else verts, dtype=F64).clone().requires_grad_(True)
+    lp = torch.as_tensor(np.stack([np.concatenate([l["pos"], l["dir"]]) for l in scene["lights"]]),
+                         dtype=F64).clone().requires_grad_(True)
+    al = torch.as_tensor(scene["albedo"], dtype=F64).clone().requires_grad_(True)
+    images, loss = [], 0.0
+    for c, (cam, tgt) in enumerate(zip(cameras, targets)):
+        sc = dict(scene, camera=cam)
+        img = render(sc, v, lp, al, teacher=teachers[c] if teachers else None, keep=False)["image"]
+        images.append(img.detach())
+        loss = loss + mse_loss(img, tgt)
+    gv, gl, ga = torch.autograd.grad(loss, [v, lp, al], allow_unused=True)
+    return {"images": images, "loss": loss.detach(), "grad_verts": gv, "grad_light": gl, "grad_albedo": ga}
+
+
+# =============================================================================== optimisation
+def adam_step(p, g, m, v, t: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """One Adam update in float64 (Kingma & Ba 2015, Algorithm 1; the paper
+    optimises with Adam, beta1 = 0.9 and beta2 = 0.999, supplementary Sec. B):
+    m <- beta1 m + (1 - beta1) g, v <- beta2 v + (1 - beta2) g^2, then
+    p <- p - lr m^ / (sqrt(v^) + eps) with m^ = m / (1 - beta1^t),
+    v^ = v / (1 - beta2^t).  Returns the new (p, m, v)."""
+    p, g, m, v = (np.asarray(x, np.float64) for x in (p, g, m, v))
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

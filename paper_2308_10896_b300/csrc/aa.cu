@@ -526,7 +526,8 @@ __global__ void sm_big_resolve_kernel(const int* __restrict__ tris, const int* _
   }
   __syncthreads();
   if (k < 3)
-    atomic_add4(&gclip[tris[3 * big_tri[b] + k]], make_float4(sum[4 * k], sum[4 * k + 1], sum[4 * k + 2], sum[4 * k + 3]));
+    atomic_add4(&gclip[tris[3 * big_tri[b] + k]],
+                make_float4(sum[4 * k], sum[4 * k + 1], sum[4 * k + 2], sum[4 * k + 3]));
 }
 
 // ------------------------------------------------------------------ launchers

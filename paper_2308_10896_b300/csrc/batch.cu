@@ -132,7 +132,6 @@ dsm_ctx* dsm_batch_context(dsm_batch* b, int32_t i) {
 
 dsm_status dsm_batch_step(dsm_batch* b, const dsm_batch_item* items, int32_t n, const dsm_params* params) {
   if (!b || !items || !params || n < 1 || n > b->n) return DSM_ERR_INVALID_ARG;
-  if (params->recompute_in_backward) return batch_fail(b, DSM_ERR_INVALID_ARG, "recompute_in_backward unsupported");
   for (int i = 0; i < n; ++i)
     if (!items[i].image || !items[i].target || !items[i].loss || !items[i].dL_dimage)
       return batch_fail(b, DSM_ERR_INVALID_ARG, "scene " + std::to_string(i) + ": null image/target/loss buffer");

@@ -8,6 +8,7 @@ namespace dsm {
 constexpr int kSubpix = 256;          // 8 sub-pixel bits: 24.8 fixed point
 constexpr int kGuard = 1 << 28;       // |snapped coordinate| limit; beyond it a triangle is culled
 constexpr float kWMin = 1e-6f;        // clip w below this culls the triangle
+constexpr int kMaxViews = DSM_MAX_LIGHTS + DSM_MAX_CAMERAS;   // light views, then camera views
 constexpr int kTile = 32;             // raster tile side in pixels
 constexpr int kTileLog2 = 5;
 constexpr unsigned kFull = 0xffffffffu;
@@ -50,8 +51,8 @@ struct LightDev {
 struct DevStatus {
   int capacity_overflow;
   int timeout;
-  int needed_pairs[DSM_MAX_LIGHTS + 1];
-  int big_count[DSM_MAX_LIGHTS + 1];   // triangles of each view flagged as big
+  int needed_pairs[DSM_MAX_LIGHTS + DSM_MAX_CAMERAS];
+  int big_count[DSM_MAX_LIGHTS + DSM_MAX_CAMERAS];   // triangles of each view flagged as big
 };
 
 // Contention control for gradient scatters.  A triangle whose pixel bbox spans
@@ -97,8 +98,12 @@ __device__ __forceinline__ float2 screen_of(float4 c, int W, int H) {
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 f2scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
-__device__ __forceinline__ float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 f4sub(float4 a, float4 b) {
+  return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
 __device__ __forceinline__ float4 f4scale(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
 __device__ __forceinline__ float dotv(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
 __device__ __forceinline__ float dotv(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }

@@ -17,11 +17,11 @@ std::atomic<unsigned long long> g_kernel_launches{0};
 static const char* const kStageNames[] = {
     "setup", "bin_fill", "raster", "sm_antialias", "filter", "shade", "final_antialias",
     "bwd_clear", "bwd_final_antialias", "bwd_shade", "bwd_shade_scatter", "bwd_filter", "bwd_sm_antialias",
-    "bwd_sm_interp", "bwd_vertex"};
+    "bwd_sm_interp", "bwd_vertex", "bwd_recompute"};
 constexpr int kStages = (int)(sizeof(kStageNames) / sizeof(kStageNames[0]));
 enum Stage { ST_SETUP, ST_BIN_FILL, ST_RASTER, ST_SM_AA, ST_FILTER, ST_SHADE, ST_FINAL_AA,
              ST_BWD_CLEAR, ST_BWD_FINAL_AA, ST_BWD_SHADE, ST_BWD_SHADE_SCATTER, ST_BWD_FILTER, ST_BWD_SM_AA,
-             ST_BWD_SM_INTERP, ST_BWD_VERTEX };
+             ST_BWD_SM_INTERP, ST_BWD_VERTEX, ST_BWD_RECOMPUTE };
 
 void build_adjacency(const int32_t* tris, int T, std::vector<int32_t>& adj);
 void build_vertex_faces(const int32_t* tris, int T, int V, std::vector<int32_t>& off, std::vector<int32_t>& lst);
@@ -52,6 +52,7 @@ struct ViewBufs {
   Buf clip, snap, depth, setup, orient, sil, count, offset, list, gbuf, gclip;
   Buf big_index, big_tri, big_acc;
   Buf aa_list, aa_ctr, hflag;   // antialiasing work list, its counter, per-pixel "listed" flag
+  Buf color, gcolor, pgrad;     // camera views: colour before the final antialiasing, its adjoint, pixel gradients
   int list_cap = 0;
   AAWork aa_work() { return AAWork{aa_list.as<int>(), aa_ctr.as<int>()}; }
 };
@@ -71,25 +72,29 @@ struct dsm_ctx {
   std::string err = "ok";
   int topo_T = -1, topo_V = -1;
   Buf adj, vf_off, vf_list;
-  ViewBufs view[DSM_MAX_LIGHTS + 1];
+  ViewBufs view[kMaxViews];
   LightBufs light[DSM_MAX_LIGHTS];
-  Buf lights_dev, viewM, status, vnormal, vnlen, camcolor, gcolor, gnormal, gN, gface, gQ, gdirect, red, pgrad;
+  Buf lights_dev, viewM, status, vnormal, vnlen, gnormal, gN, gface, gQ, gdirect, red;
   Buf scratch_dverts, scratch_dlight, scratch_dalbedo, filter_tmp;
   DevStatus* hstatus = nullptr;
   // state of the last forward
   bool have_fwd = false;
   dsm_mesh mesh{};
   dsm_light lights[DSM_MAX_LIGHTS]{};
-  int L = 0;
-  dsm_camera cam{};
+  int L = 0, C = 0;
+  dsm_camera cams[DSM_MAX_CAMERAS]{};
   dsm_params params{};
+  // recompute_in_backward: the views share two buffer sets (one for the
+  // lights, one for the cameras) and the backward rebuilds what it reads
+  bool recompute = false;
   cudaStream_t stream = nullptr;
   uint64_t sized_sig = 0;
-  // internal streams: one per view (lights, then camera), fork/join events
-  cudaStream_t vs[DSM_MAX_LIGHTS + 1] = {};
-  cudaEvent_t ev_fork = nullptr, ev_bfork = nullptr, ev_join[DSM_MAX_LIGHTS + 1] = {};
-  // per-stage timing
+  // internal streams: one per view (lights, then cameras), fork/join events
+  cudaStream_t vs[kMaxViews] = {};
+  cudaEvent_t ev_fork = nullptr, ev_bfork = nullptr, ev_join[kMaxViews] = {};
+  // per-stage timing (stage_override >= 0 books every stage under that one)
   bool prof = false;
+  int stage_override = -1;
   // views serialised on the caller's stream (batched scenes overlap one another instead)
   bool serial = false;
   struct Rec { int stage; cudaEvent_t a, b; };
@@ -116,14 +121,14 @@ dsm_status cuda_fail(dsm_ctx* c, cudaError_t e, const char* where) {
     if (e__ != cudaSuccess) return cuda_fail(ctx, e__, #call);  \
   } while (0)
 
-__global__ void set_matrix_kernel(Mat20 m, float* dst) {
-  int k = threadIdx.x;
-  if (k < 20) dst[k] = m.v[k];
-}
+// Camera matrices, 20 floats each (the clip matrix, then an unused depth row).
+struct CamMats {
+  float v[20 * DSM_MAX_CAMERAS];
+};
 
 // One launch that zeroes several buffers: segment blockIdx.y, 16-byte stores
 // over its aligned body, 4-byte stores for an unaligned head and the tail.
-constexpr int kMaxClear = 40;
+constexpr int kMaxClear = 64;
 struct ClearList {
   float* p[kMaxClear];
   long long n[kMaxClear];     // floats
@@ -182,7 +187,8 @@ struct StageTimer {
   cudaStream_t st;
   int stage;
   cudaEvent_t a = nullptr;
-  StageTimer(dsm_ctx* c_, int stage_, cudaStream_t st_) : c(c_), st(st_), stage(stage_) {
+  StageTimer(dsm_ctx* c_, int stage_, cudaStream_t st_)
+      : c(c_), st(st_), stage(c_->stage_override >= 0 ? c_->stage_override : stage_) {
     if (c->prof && (a = take_event(c))) cudaEventRecord(a, st);
   }
   void stop() {
@@ -218,19 +224,19 @@ cudaStream_t view_stream(const dsm_ctx* c, int w, cudaStream_t st) {
   return (c->prof || c->serial) ? st : c->vs[w];
 }
 
-// All view streams wait for the work enqueued so far on st.
-cudaError_t fork_views(dsm_ctx* c, cudaStream_t st, cudaEvent_t ev, int n_views) {
-  if (c->prof || c->serial) return cudaSuccess;
+// The streams of views [w0, w1) wait for the work enqueued so far on st.
+cudaError_t fork_views(dsm_ctx* c, cudaStream_t st, cudaEvent_t ev, int w0, int w1) {
+  if (c->prof || c->serial || w1 <= w0) return cudaSuccess;
   cudaError_t e = cudaEventRecord(ev, st);
-  for (int w = 0; w < n_views && e == cudaSuccess; ++w) e = cudaStreamWaitEvent(c->vs[w], ev, 0);
+  for (int w = w0; w < w1 && e == cudaSuccess; ++w) e = cudaStreamWaitEvent(c->vs[w], ev, 0);
   return e;
 }
 
-// st waits for the work enqueued so far on the first n view streams.
-cudaError_t join_views(dsm_ctx* c, cudaStream_t st, int n_views) {
+// st waits for the work enqueued so far on the streams of views [w0, w1).
+cudaError_t join_views(dsm_ctx* c, cudaStream_t st, int w0, int w1) {
   if (c->prof || c->serial) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-  for (int w = 0; w < n_views && e == cudaSuccess; ++w) {
+  for (int w = w0; w < w1 && e == cudaSuccess; ++w) {
     e = cudaEventRecord(c->ev_join[w], c->vs[w]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join[w], 0);
   }
@@ -276,14 +282,13 @@ void dsm_destroy(dsm_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
   Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->status,
-                 &ctx->vnormal, &ctx->vnlen, &ctx->camcolor, &ctx->gcolor, &ctx->gnormal, &ctx->gN, &ctx->gface,
-                 &ctx->gQ, &ctx->gdirect, &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo,
-                 &ctx->filter_tmp, &ctx->red, &ctx->pgrad};
+                 &ctx->vnormal, &ctx->vnlen, &ctx->gnormal, &ctx->gN, &ctx->gface, &ctx->gQ, &ctx->gdirect,
+                 &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo, &ctx->filter_tmp, &ctx->red};
   for (Buf* b : bufs) b->release();
   for (auto& v : ctx->view) {
     Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
                  &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr,
-                 &v.hflag};
+                 &v.hflag, &v.color, &v.gcolor, &v.pgrad};
     for (Buf* b : vb) b->release();
   }
   for (auto& l : ctx->light) {
@@ -308,7 +313,8 @@ const char* dsm_last_error(dsm_ctx* ctx) {
 
 dsm_status dsm_set_topology(dsm_ctx* ctx, const int32_t* tris, int32_t n_tris, int32_t n_verts) {
   if (!ctx) return DSM_ERR_INVALID_ARG;
-  if (n_tris < 0 || n_verts < 0 || (n_tris > 0 && !tris)) return fail(ctx, DSM_ERR_INVALID_ARG, "bad topology arguments");
+  if (n_tris < 0 || n_verts < 0 || (n_tris > 0 && !tris))
+    return fail(ctx, DSM_ERR_INVALID_ARG, "bad topology arguments");
   std::vector<int32_t> h((size_t)n_tris * 3);
   if (n_tris) DSM_CHECK(cudaMemcpy(h.data(), tris, h.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
   for (int32_t v : h)
@@ -330,10 +336,11 @@ dsm_status dsm_set_topology(dsm_ctx* ctx, const int32_t* tris, int32_t n_tris, i
 }
 
 static dsm_status check_args(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* lights,
-                             const float* light_params, int32_t n_lights, const dsm_camera* cam,
-                             const dsm_params* params, float* image) {
-  if (!mesh || !cam || !params || !image) return fail(ctx, DSM_ERR_INVALID_ARG, "null argument");
+                             const float* light_params, int32_t n_lights, const dsm_camera* cams, int32_t n_cams,
+                             const dsm_params* params, float* const* images) {
+  if (!mesh || !cams || !params || !images) return fail(ctx, DSM_ERR_INVALID_ARG, "null argument");
   if (n_lights < 0 || n_lights > DSM_MAX_LIGHTS) return fail(ctx, DSM_ERR_INVALID_ARG, "n_lights out of range");
+  if (n_cams < 1 || n_cams > DSM_MAX_CAMERAS) return fail(ctx, DSM_ERR_INVALID_ARG, "n_cameras out of range");
   if (n_lights > 0 && (!lights || !light_params)) return fail(ctx, DSM_ERR_INVALID_ARG, "null light arrays");
   if (mesh->n_verts < 0 || mesh->n_tris < 0) return fail(ctx, DSM_ERR_INVALID_ARG, "negative mesh size");
   if ((mesh->n_verts > 0 && !mesh->verts) || (mesh->n_tris > 0 && !mesh->tris))
@@ -341,8 +348,12 @@ static dsm_status check_args(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light
   if (mesh->n_materials < 1 || !mesh->albedo) return fail(ctx, DSM_ERR_INVALID_ARG, "no albedo table");
   if (mesh->n_tris != ctx->topo_T || mesh->n_verts != ctx->topo_V)
     return fail(ctx, DSM_ERR_NO_TOPOLOGY, "dsm_set_topology was not called for this mesh size");
-  if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
-    return fail(ctx, DSM_ERR_INVALID_ARG, "camera size out of range");
+  for (int c = 0; c < n_cams; ++c) {
+    if (!images[c]) return fail(ctx, DSM_ERR_INVALID_ARG, "null image");
+    const dsm_camera& cam = cams[c];
+    if (cam.width < 1 || cam.height < 1 || cam.width > 16384 || cam.height > 16384)
+      return fail(ctx, DSM_ERR_INVALID_ARG, "camera size out of range");
+  }
   for (int l = 0; l < n_lights; ++l) {
     const dsm_light& L = lights[l];
     if (L.type != 0 && L.type != 1) return fail(ctx, DSM_ERR_INVALID_ARG, "unknown light type");
@@ -356,7 +367,8 @@ static dsm_status check_args(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light
   if (params->filter_kind != 0 && params->filter_kind != 1) return fail(ctx, DSM_ERR_INVALID_ARG, "filter_kind");
   if (params->filter_boundary != 0 && params->filter_boundary != 1)
     return fail(ctx, DSM_ERR_INVALID_ARG, "filter_boundary");
-  if (params->recompute_in_backward != 0) return fail(ctx, DSM_ERR_INVALID_ARG, "recompute_in_backward unsupported");
+  if (params->recompute_in_backward != 0 && params->recompute_in_backward != 1)
+    return fail(ctx, DSM_ERR_INVALID_ARG, "recompute_in_backward");
   if (!(params->min_variance >= 0.f)) return fail(ctx, DSM_ERR_INVALID_ARG, "min_variance");
   return DSM_OK;
 }
@@ -382,6 +394,8 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   DSM_CHECK(v.big_acc.ensure((size_t)kMaxBig * kBigSlots * (is_light ? kBigStrideSm : kBigStrideCam) * 4));
   if (is_light) {
     DSM_CHECK(v.depth.ensure(Vn * 4));
+  } else {
+    DSM_CHECK(v.color.ensure((size_t)W * H * sizeof(float4)));
   }
   DSM_CHECK(v.aa_list.ensure((size_t)W * H * 4));
   DSM_CHECK(v.aa_ctr.ensure(sizeof(int)));
@@ -394,41 +408,319 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   return DSM_OK;
 }
 
-dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* lights, const float* light_params,
-                      int32_t n_lights, const dsm_camera* cam, const dsm_params* params, float* image) {
+namespace {
+
+// Camera buffer set under recomputation (view[0] is the light set).
+constexpr int kCamSlot = DSM_MAX_LIGHTS;
+
+// Buffers of view w (lights 0..L-1, then cameras L..L+C-1).  Under
+// recomputation every light view uses view[0] and every camera view
+// view[kCamSlot], one after the other.
+ViewBufs& vbuf(dsm_ctx* ctx, int w) {
+  if (!ctx->recompute) return ctx->view[w];
+  return ctx->view[w < ctx->L ? 0 : kCamSlot];
+}
+
+// Working maps of light l (f, the antialiased patch, filter scratch, dL/df~):
+// shared by all lights under recomputation.  The moments and their adjoint
+// stay per light (every camera reads all of them).
+LightBufs& lwork(dsm_ctx* ctx, int l) { return ctx->recompute ? ctx->light[0] : ctx->light[l]; }
+
+bool view_is_light(const dsm_ctx* ctx, int w) { return w < ctx->L; }
+
+// Sizes the buffer set of view w for that view (buffers only grow).
+dsm_status prepare_view(dsm_ctx* ctx, int w) {
+  const int L = ctx->L;
+  const bool light = view_is_light(ctx, w);
+  const int W = light ? ctx->lights[w].res : ctx->cams[w - L].width;
+  const int H = light ? ctx->lights[w].res : ctx->cams[w - L].height;
+  return ensure_view(ctx, vbuf(ctx, w), W, H, ctx->mesh.n_verts, ctx->mesh.n_tris, light);
+}
+
+dsm_status prepare_light(dsm_ctx* ctx, int l) {
+  const int R = ctx->lights[l].res;
+  const size_t R2 = (size_t)R * R * sizeof(float2);
+  LightBufs& wk = lwork(ctx, l);
+  DSM_CHECK(wk.fmap.ensure(R2));
+  DSM_CHECK(wk.ftilde.ensure(R2));
+  DSM_CHECK(wk.tmp.ensure(R2));
+  LightBufs& lb = ctx->light[l];
+  DSM_CHECK(lb.mom.ensure(R2));
+  lb.res = R;
+  make_filter_args(ctx->lights[l].sigma, ctx->lights[l].radius, ctx->params.filter_kind, ctx->params.filter_boundary,
+                   &lb.fa);
+  return DSM_OK;
+}
+
+dsm_status grow_list(dsm_ctx* ctx, ViewBufs& v, long long need) {
+  if (need <= v.list_cap) return DSM_OK;
+  const long long cap = need + need / 2 + 1024;
+  if (cap > 0x7fffffffLL) return fail(ctx, DSM_ERR_CAPACITY, "tile list above 2^31 entries");
+  DSM_CHECK(v.list.ensure((size_t)cap * 4));
+  v.list_cap = (int)cap;
+  return DSM_OK;
+}
+
+AAArgs aa_args(const dsm_ctx* ctx, ViewBufs& v) {
+  return AAArgs{v.gbuf.as<float4>(), v.W, v.H, ctx->mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(),
+                v.clip.as<float4>()};
+}
+
+// Transform, triangle setup and silhouettes of views [w0, w0 + n) in one fused
+// pass, which also empties their tile counters and antialiasing lists.
+void setup_views(dsm_ctx* ctx, int w0, int n, cudaStream_t st) {
+  ViewSetupArgs va{};
+  va.n = n;
+  for (int k = 0; k < n; ++k) {
+    const int w = w0 + k;
+    ViewBufs& v = vbuf(ctx, w);
+    va.W[k] = v.W; va.H[k] = v.H; va.tiles[k] = v.tilesX * v.tilesY;
+    va.clip[k] = v.clip.as<float4>();
+    va.snap[k] = v.snap.as<VertSnap>();
+    va.depth[k] = view_is_light(ctx, w) ? v.depth.as<float>() : nullptr;
+    va.setup[k] = v.setup.as<TriSetup>();
+    va.orient[k] = v.orient.as<int8_t>();
+    va.sil[k] = v.sil.as<uint8_t>();
+    va.count[k] = v.count.as<int>();
+    va.aa_count[k] = v.aa_ctr.as<int>();
+  }
+  const dsm_mesh& m = ctx->mesh;
+  launch_setup_all(m.verts, m.n_verts, m.tris, m.n_tris, ctx->adj.as<int>(), ctx->viewM.as<float>() + 20 * w0, va,
+                   ctx->status.as<DevStatus>(), st);
+}
+
+void bin_count_view(dsm_ctx* ctx, int w, cudaStream_t st) {
+  ViewBufs& v = vbuf(ctx, w);
+  DevStatus* ds = ctx->status.as<DevStatus>();
+  StageTimer t(ctx, ST_SETUP, st);
+  launch_bin_count(v.setup.as<TriSetup>(), ctx->mesh.n_tris, v.tilesX, v.count.as<int>(), ds, w,
+                   v.big_index.as<int>(), v.big_tri.as<int>(), st);
+  launch_scan(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), ds, w, st);
+}
+
+// Bin fill and raster of view w (a light view also writes f, f^2).
+void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
+  ViewBufs& v = vbuf(ctx, w);
+  const bool light = view_is_light(ctx, w);
+  DevStatus* ds = ctx->status.as<DevStatus>();
+  {
+    StageTimer t(ctx, ST_BIN_FILL, st);
+    launch_bin_fill(v.setup.as<TriSetup>(), ctx->mesh.n_tris, v.tilesX, v.count.as<int>(), v.offset.as<int>(),
+                    v.list.as<int>(), v.list_cap, ds, w, v.big_index.as<int>(), v.big_tri.as<int>(), st);
+  }
+  StageTimer t(ctx, ST_RASTER, st);
+  launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY, v.W,
+                v.H, v.clip.as<float4>(), ctx->mesh.tris, v.gbuf.as<float4>(), light ? v.depth.as<float>() : nullptr,
+                light ? lwork(ctx, w).fmap.as<float2>() : nullptr, st);
+}
+
+// Alg. 1 after the raster: antialiasing of f, f^2 at the listed texels, then
+// the moment filter (f~ = f except at the listed texels, whose values the list
+// pass left in ftilde).
+void light_maps(dsm_ctx* ctx, int l, cudaStream_t st) {
+  ViewBufs& v = vbuf(ctx, l);
+  LightBufs& wk = lwork(ctx, l);
+  LightBufs& lb = ctx->light[l];
+  const bool aa = ctx->params.aa_shadow != 0;
+  {
+    StageTimer t(ctx, ST_SM_AA, st);
+    if (aa) {
+      const AAArgs a = aa_args(ctx, v);
+      launch_aa_detect(a, v.hflag.as<uint8_t>(), v.aa_work(), st);
+      launch_aa_forward2_list(a, wk.fmap.as<float2>(), wk.ftilde.as<float2>(), v.aa_work(), st);
+    }
+  }
+  StageTimer t(ctx, ST_FILTER, st);
+  launch_filter(wk.fmap.as<float2>(), wk.tmp.as<float2>(), lb.mom.as<float2>(), v.W, lb.fa, st,
+                aa ? v.hflag.as<uint8_t>() : nullptr, wk.ftilde.as<float2>());
+}
+
+ShadeArgs shade_args(dsm_ctx* ctx, int c) {
+  ViewBufs& cv = vbuf(ctx, ctx->L + c);
+  const dsm_mesh& m = ctx->mesh;
+  ShadeArgs sa{};
+  sa.gbuf = cv.gbuf.as<float4>();
+  sa.W = cv.W; sa.H = cv.H;
+  sa.verts = m.verts; sa.tris = m.tris; sa.tri_mat = m.tri_material;
+  sa.albedo = m.albedo; sa.n_mat = m.n_materials;
+  sa.vnormal = ctx->vnormal.as<float>();
+  sa.cam_clip = cv.clip.as<float4>();
+  sa.lights = ctx->lights_dev.as<LightDev>(); sa.L = ctx->L;
+  for (int l = 0; l < ctx->L; ++l) { sa.mom[l] = ctx->light[l].mom.as<float2>(); sa.res[l] = ctx->light[l].res; }
+  sa.min_variance = ctx->params.min_variance;
+  return sa;
+}
+
+ShadeGradArgs grad_args(dsm_ctx* ctx, int c, float* dverts, float* dalbedo, int red_stride) {
+  ViewBufs& cv = vbuf(ctx, ctx->L + c);
+  ShadeGradArgs ga{};
+  ga.gcolor = cv.gcolor.as<float4>();
+  ga.dverts = dverts;
+  ga.gnormal = ctx->gnormal.as<float>();
+  ga.gclip = cv.gclip.as<float4>();
+  ga.dalbedo = dalbedo;
+  for (int l = 0; l < ctx->L; ++l) ga.gm[l] = ctx->light[l].gm.as<float2>();
+  ga.red = ctx->red.as<float>();
+  ga.red_stride = red_stride;
+  ga.big = cv.big_index.as<int>();
+  ga.big_acc = cv.big_acc.as<float>();
+  ga.pgrad = cv.pgrad.as<float4>();
+  return ga;
+}
+
+// Camera c: Alg. 2 x Lambert into its colour buffer, then (with an image) the
+// final antialiasing into the image.
+dsm_status camera_colour(dsm_ctx* ctx, int c, float* image, cudaStream_t st) {
+  ViewBufs& cv = vbuf(ctx, ctx->L + c);
+  {
+    StageTimer t(ctx, ST_SHADE, st);
+    launch_shade(shade_args(ctx, c), cv.color.as<float4>(), st);
+  }
+  if (!image) return DSM_OK;
+  StageTimer t(ctx, ST_FINAL_AA, st);
+  if (ctx->params.aa_final) {
+    launch_aa_forward4(aa_args(ctx, cv), cv.color.as<float4>(), reinterpret_cast<float4*>(image),
+                       cv.hflag.as<uint8_t>(), cv.aa_work(), st);
+  } else {
+    DSM_CHECK(cudaMemcpyAsync(image, cv.color.p, (size_t)cv.W * cv.H * sizeof(float4), cudaMemcpyDeviceToDevice, st));
+  }
+  return DSM_OK;
+}
+
+// Camera c, backward: final antialiasing adjoint, then the shading adjoint
+// (dL/dm into every light's gm, per-pixel gradients for the scatter).
+dsm_status camera_backward(dsm_ctx* ctx, int c, const float* gimage, float* dverts, float* dalbedo, int red_stride,
+                           cudaStream_t st) {
+  ViewBufs& cv = vbuf(ctx, ctx->L + c);
+  {
+    StageTimer t(ctx, ST_BWD_FINAL_AA, st);
+    if (ctx->params.aa_final) {
+      launch_aa_backward4(aa_args(ctx, cv), cv.color.as<float4>(), reinterpret_cast<const float4*>(gimage),
+                          cv.gcolor.as<float4>(), cv.gclip.as<float4>(), cv.hflag.as<uint8_t>(), cv.aa_work(), st);
+    } else {
+      DSM_CHECK(cudaMemcpyAsync(cv.gcolor.p, gimage, (size_t)cv.W * cv.H * sizeof(float4), cudaMemcpyDeviceToDevice,
+                                st));
+    }
+  }
+  StageTimer t(ctx, ST_BWD_SHADE, st);
+  launch_shade_backward(shade_args(ctx, c), grad_args(ctx, c, dverts, dalbedo, red_stride), st);
+  return DSM_OK;
+}
+
+// Camera c, backward: the per-pixel gradients scattered to the triangle corners.
+void camera_scatter(dsm_ctx* ctx, int c, float* dverts, float* dalbedo, int red_stride, cudaStream_t st) {
+  StageTimer t(ctx, ST_BWD_SHADE_SCATTER, st);
+  const ShadeArgs sa = shade_args(ctx, c);
+  const ShadeGradArgs ga = grad_args(ctx, c, dverts, dalbedo, red_stride);
+  launch_shade_scatter(sa, ga, st);
+  launch_shade_big_resolve(sa, ga, vbuf(ctx, ctx->L + c).big_tri.as<int>(), ctx->status.as<DevStatus>(), ctx->L + c,
+                           st);
+}
+
+// Light l, backward: G^T (filter adjoint, folded through f^2 = f f), the
+// antialiasing adjoint at the listed texels, the interpolation adjoint.
+void light_backward(dsm_ctx* ctx, int l, cudaStream_t st) {
+  ViewBufs& v = vbuf(ctx, l);
+  LightBufs& wk = lwork(ctx, l);
+  LightBufs& lb = ctx->light[l];
+  const AAArgs aa = aa_args(ctx, v);
+  {
+    StageTimer t(ctx, ST_BWD_FILTER, st);
+    launch_filter_adjoint(lb.gm.as<float2>(), wk.tmp.as<float2>(), wk.gft.as<float2>(), v.W, lb.fa, st,
+                          wk.fmap.as<float2>(), wk.tmp.as<float>());
+  }
+  {
+    StageTimer t(ctx, ST_BWD_SM_AA, st);
+    if (ctx->params.aa_shadow)
+      launch_sm_aa_adjoint_list(aa, wk.fmap.as<float2>(), wk.gft.as<float2>(), v.gclip.as<float4>(),
+                                wk.tmp.as<float>(), v.aa_work(), st);
+  }
+  StageTimer t(ctx, ST_BWD_SM_INTERP, st);
+  BigArgs big{v.big_index.as<int>(), v.big_tri.as<int>(), v.big_acc.as<float>(), ctx->status.as<DevStatus>(), l};
+  launch_sm_interp_adjoint(aa, wk.tmp.as<float>(), v.depth.as<float>(), v.gclip.as<float4>(), big, st);
+}
+
+// dL/dv += M^T dL/dclip over views [w0, w0 + n), and dQ of the lights among them.
+void vertex_backward_views(dsm_ctx* ctx, int w0, int n, float* dverts, int red_stride, cudaStream_t st) {
+  VertGradPtrs gp{};
+  for (int k = 0; k < n; ++k) gp.gclip[k] = vbuf(ctx, w0 + k).gclip.as<float4>();
+  const int n_lights = std::max(0, std::min(n, ctx->L - w0));
+  float* red = ctx->red.as<float>() + (n_lights > 0 ? 20 * w0 : 0);
+  launch_vertex_backward(ctx->mesh.verts, ctx->mesh.n_verts, ctx->viewM.as<float>() + 20 * w0, n, n_lights, gp,
+                         dverts, red, red_stride, st);
+}
+
+// Under recomputation: view w through its shared buffer set (setup, binning,
+// raster); `maps` also rebuilds a light's filtered moments, `detect` the
+// antialiasing work list.
+dsm_status rebuild_view(dsm_ctx* ctx, int w, bool sizing, bool maps, bool detect, cudaStream_t st) {
+  dsm_status s = prepare_view(ctx, w);
+  if (s != DSM_OK) return s;
+  {
+    StageTimer t(ctx, ST_SETUP, st);
+    setup_views(ctx, w, 1, st);
+  }
+  bin_count_view(ctx, w, st);
+  if (sizing) {
+    DSM_CHECK(cudaMemcpyAsync(ctx->hstatus, ctx->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    DSM_CHECK(cudaStreamSynchronize(st));
+    s = grow_list(ctx, vbuf(ctx, w), ctx->hstatus->needed_pairs[w]);
+    if (s != DSM_OK) return s;
+  }
+  raster_view(ctx, w, st);
+  if (maps && view_is_light(ctx, w)) light_maps(ctx, w, st);
+  if (detect) {
+    ViewBufs& v = vbuf(ctx, w);
+    StageTimer t(ctx, view_is_light(ctx, w) ? ST_SM_AA : ST_FINAL_AA, st);
+    launch_aa_detect(aa_args(ctx, v), v.hflag.as<uint8_t>(), v.aa_work(), st);
+  }
+  DSM_CHECK(cudaGetLastError());
+  return DSM_OK;
+}
+
+__global__ void set_cameras_kernel(CamMats m, int n, float* dst) {
+  for (int k = threadIdx.x; k < 20 * n; k += blockDim.x) dst[k] = m.v[k];
+}
+
+}  // namespace
+
+dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* lights, const float* light_params,
+                              int32_t n_lights, const dsm_camera* cams, int32_t n_cams, const dsm_params* params,
+                              float* const* images) {
   if (!ctx) return DSM_ERR_INVALID_ARG;
-  dsm_status s = check_args(ctx, mesh, lights, light_params, n_lights, cam, params, image);
+  dsm_status s = check_args(ctx, mesh, lights, light_params, n_lights, cams, n_cams, params, images);
   if (s != DSM_OK) return s;
   ctx->have_fwd = false;
   cudaStream_t st = (cudaStream_t)params->stream;
-  const int V = mesh->n_verts, T = mesh->n_tris, L = n_lights;
-  const int Wc = cam->width, Hc = cam->height;
+  const int V = mesh->n_verts, T = mesh->n_tris, L = n_lights, C = n_cams, NV = L + C;
+  ctx->mesh = *mesh;
+  for (int l = 0; l < L; ++l) ctx->lights[l] = lights[l];
+  for (int c = 0; c < C; ++c) ctx->cams[c] = cams[c];
+  ctx->L = L;
+  ctx->C = C;
+  ctx->params = *params;
+  ctx->stream = st;
+  ctx->recompute = params->recompute_in_backward != 0;
 
-  // ---- buffers
-  uint64_t sig = mix(mix(mix(1, V), T), L);
-  sig = mix(mix(sig, Wc), Hc);
-  for (int l = 0; l < L; ++l) {
-    s = ensure_view(ctx, ctx->view[l], lights[l].res, lights[l].res, V, T, true);
+  // ---- buffers (all growth happens here, before any launch of this frame)
+  uint64_t sig = mix(mix(mix(mix(mix(1, V), T), L), C), ctx->recompute ? 1 : 0);
+  for (int c = 0; c < C; ++c) sig = mix(mix(sig, cams[c].width), cams[c].height);
+  for (int l = 0; l < L; ++l) sig = mix(mix(sig, lights[l].res), lights[l].type);
+  const bool sizing = ctx->sized_sig != sig;
+  for (int w = 0; w < NV; ++w) {
+    s = prepare_view(ctx, w);
     if (s != DSM_OK) return s;
-    LightBufs& lb = ctx->light[l];
-    const size_t R2 = (size_t)lights[l].res * lights[l].res * sizeof(float2);
-    DSM_CHECK(lb.fmap.ensure(R2));
-    DSM_CHECK(lb.ftilde.ensure(R2));
-    DSM_CHECK(lb.tmp.ensure(R2));
-    DSM_CHECK(lb.mom.ensure(R2));
-    lb.res = lights[l].res;
-    make_filter_args(lights[l].sigma, lights[l].radius, params->filter_kind, params->filter_boundary, &lb.fa);
-    sig = mix(mix(sig, lights[l].res), lights[l].type);
   }
-  s = ensure_view(ctx, ctx->view[L], Wc, Hc, V, T, false);
-  if (s != DSM_OK) return s;
+  for (int l = 0; l < L; ++l) {
+    s = prepare_light(ctx, l);
+    if (s != DSM_OK) return s;
+  }
   DSM_CHECK(ctx->lights_dev.ensure(sizeof(LightDev) * DSM_MAX_LIGHTS));
-  DSM_CHECK(ctx->viewM.ensure(sizeof(float) * 20 * (DSM_MAX_LIGHTS + 1)));
+  DSM_CHECK(ctx->viewM.ensure(sizeof(float) * 20 * kMaxViews));
   DSM_CHECK(ctx->vnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->vnlen.ensure(sizeof(float) * std::max(V, 1)));
-  DSM_CHECK(ctx->camcolor.ensure((size_t)Wc * Hc * sizeof(float4)));
 
-  // ---- light cameras and the camera matrix
+  // ---- light cameras and the camera matrices
   LightSetupArgs la{};
   la.n = L;
   for (int l = 0; l < L; ++l) {
@@ -444,160 +736,108 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
     c.intensity[0] = Lh.intensity[0]; c.intensity[1] = Lh.intensity[1]; c.intensity[2] = Lh.intensity[2];
   }
   float* viewM = ctx->viewM.as<float>();
-  LightDev* ldev = ctx->lights_dev.as<LightDev>();
   StageTimer t_setup(ctx, ST_SETUP, st);
-  if (L > 0) launch_light_setup(light_params, la, ldev, viewM, st);
-  Mat20 cm{};
-  for (int k = 0; k < 16; ++k) cm.v[k] = cam->clip[k];
+  if (L > 0) launch_light_setup(light_params, la, ctx->lights_dev.as<LightDev>(), viewM, st);
+  CamMats cm{};
+  for (int c = 0; c < C; ++c)
+    for (int k = 0; k < 16; ++k) cm.v[20 * c + k] = cams[c].clip[k];
   count_launches(1);
-  set_matrix_kernel<<<1, 32, 0, st>>>(cm, viewM + 20 * L);
-  // every view at once: transform, triangle setup, silhouettes (and zeroed
-  // tile counters for the binning)
-  DevStatus* dstat = ctx->status.as<DevStatus>();
-  {
-    ViewSetupArgs va{};
-    va.n = L + 1;
-    for (int w = 0; w <= L; ++w) {
-      ViewBufs& v = ctx->view[w];
-      va.W[w] = v.W; va.H[w] = v.H; va.tiles[w] = v.tilesX * v.tilesY;
-      va.clip[w] = v.clip.as<float4>();
-      va.snap[w] = v.snap.as<VertSnap>();
-      va.depth[w] = w < L ? v.depth.as<float>() : nullptr;
-      va.setup[w] = v.setup.as<TriSetup>();
-      va.orient[w] = v.orient.as<int8_t>();
-      va.sil[w] = v.sil.as<uint8_t>();
-      va.count[w] = v.count.as<int>();
-      va.aa_count[w] = v.aa_ctr.as<int>();
-    }
-    launch_setup_all(mesh->verts, V, mesh->tris, T, ctx->adj.as<int>(), viewM, va, dstat, st);
-  }
-  t_setup.stop();
+  set_cameras_kernel<<<1, 64, 0, st>>>(cm, C, viewM + 20 * L);
 
-  // ---- per view on its own stream: bin count, scan (the light views and the
-  // camera view are independent until shading)
-  DSM_CHECK(ensure_streams(ctx));
-  DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, L + 1));
-  {
-    cudaStream_t cst = view_stream(ctx, L, st);
-    StageTimer tn(ctx, ST_SETUP, cst);
+  if (ctx->recompute) {
+    // ---- one view at a time through the shared buffer sets
     launch_vertex_normals(mesh->verts, V, mesh->tris, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
-                          ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), cst);
-  }
-  for (int w = 0; w <= L; ++w) {
-    ViewBufs& v = ctx->view[w];
-    cudaStream_t vst = view_stream(ctx, w, st);
-    StageTimer tw(ctx, ST_SETUP, vst);
-    launch_bin_count(v.setup.as<TriSetup>(), T, v.tilesX, v.count.as<int>(), dstat, w, v.big_index.as<int>(),
-                     v.big_tri.as<int>(), vst);
-    launch_scan(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), dstat, w, vst);
-  }
-  DSM_CHECK(cudaGetLastError());
-  if (ctx->sized_sig != sig) {
-    // first frame of this scene size: read the pair counts once and size the lists
-    DSM_CHECK(join_views(ctx, st, L + 1));
-    DSM_CHECK(cudaMemcpyAsync(ctx->hstatus, dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-    DSM_CHECK(cudaStreamSynchronize(st));
-    for (int w = 0; w <= L; ++w) {
-      ViewBufs& v = ctx->view[w];
-      const long long need = ctx->hstatus->needed_pairs[w];
-      if (need > v.list_cap) {
-        const long long cap = need + need / 2 + 1024;
-        if (cap > 0x7fffffffLL) return fail(ctx, DSM_ERR_CAPACITY, "tile list above 2^31 entries");
-        DSM_CHECK(v.list.ensure((size_t)cap * 4));
-        v.list_cap = (int)cap;
+                          ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), st);
+    t_setup.stop();
+    for (int w = 0; w < NV; ++w) {
+      s = rebuild_view(ctx, w, sizing, true, false, st);
+      if (s != DSM_OK) return s;
+      if (w >= L) {
+        s = camera_colour(ctx, w - L, images[w - L], st);
+        if (s != DSM_OK) return s;
       }
     }
-    ctx->sized_sig = sig;
-    DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, L + 1));
-  }
-  // ---- per view: bin fill, raster; per light: Alg. 1 (f, f^2 -> antialias -> filter)
-  for (int w = 0; w <= L; ++w) {
-    ViewBufs& v = ctx->view[w];
-    cudaStream_t vst = view_stream(ctx, w, st);
-    {
-      StageTimer t(ctx, ST_BIN_FILL, vst);
-      launch_bin_fill(v.setup.as<TriSetup>(), T, v.tilesX, v.count.as<int>(), v.offset.as<int>(), v.list.as<int>(),
-                      v.list_cap, dstat, w, v.big_index.as<int>(), v.big_tri.as<int>(), vst);
-    }
-    {
-      StageTimer t(ctx, ST_RASTER, vst);
-      launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY, v.W,
-                    v.H, v.clip.as<float4>(), mesh->tris, v.gbuf.as<float4>(), w < L ? v.depth.as<float>() : nullptr,
-                    w < L ? ctx->light[w].fmap.as<float2>() : nullptr, vst);
-    }
-    if (w == L) continue;
-    LightBufs& lb = ctx->light[w];
-    {
-      StageTimer t(ctx, ST_SM_AA, vst);
-      if (params->aa_shadow) {
-        AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh->tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(),
-                  v.clip.as<float4>()};
-        launch_aa_detect(aa, v.hflag.as<uint8_t>(), v.aa_work(), vst);
-        launch_aa_forward2_list(aa, lb.fmap.as<float2>(), lb.ftilde.as<float2>(), v.aa_work(), vst);
-      }
-    }
-    {
-      // f~ = f except at the listed texels, whose values the list pass left in ftilde
-      StageTimer t(ctx, ST_FILTER, vst);
-      launch_filter(lb.fmap.as<float2>(), lb.tmp.as<float2>(), lb.mom.as<float2>(), v.W, lb.fa, vst,
-                    params->aa_shadow ? v.hflag.as<uint8_t>() : nullptr, lb.ftilde.as<float2>());
-    }
-  }
-  DSM_CHECK(join_views(ctx, st, L + 1));
-  DSM_CHECK(cudaGetLastError());
-
-  // ---- camera: shade (Alg. 2 x Lambert) and the final antialiasing
-  ViewBufs& cv = ctx->view[L];
-  ShadeArgs sa{};
-  sa.gbuf = cv.gbuf.as<float4>();
-  sa.W = Wc; sa.H = Hc;
-  sa.verts = mesh->verts; sa.tris = mesh->tris; sa.tri_mat = mesh->tri_material;
-  sa.albedo = mesh->albedo; sa.n_mat = mesh->n_materials;
-  sa.vnormal = ctx->vnormal.as<float>();
-  sa.cam_clip = cv.clip.as<float4>();
-  sa.lights = ldev; sa.L = L;
-  for (int l = 0; l < L; ++l) { sa.mom[l] = ctx->light[l].mom.as<float2>(); sa.res[l] = lights[l].res; }
-  sa.min_variance = params->min_variance;
-  {
-    StageTimer t(ctx, ST_SHADE, st);
-    launch_shade(sa, ctx->camcolor.as<float4>(), st);
-  }
-  StageTimer t_final(ctx, ST_FINAL_AA, st);
-  if (params->aa_final) {
-    AAArgs aa{cv.gbuf.as<float4>(), Wc, Hc, mesh->tris, cv.sil.as<uint8_t>(), cv.snap.as<VertSnap>(),
-              cv.clip.as<float4>()};
-    launch_aa_forward4(aa, ctx->camcolor.as<float4>(), reinterpret_cast<float4*>(image), cv.hflag.as<uint8_t>(),
-                       cv.aa_work(), st);
   } else {
-    DSM_CHECK(cudaMemcpyAsync(image, ctx->camcolor.p, (size_t)Wc * Hc * sizeof(float4), cudaMemcpyDeviceToDevice, st));
+    // every view at once: transform, triangle setup, silhouettes
+    setup_views(ctx, 0, NV, st);
+    t_setup.stop();
+    // ---- per view on its own stream: bin count, scan (the views are independent until shading)
+    DSM_CHECK(ensure_streams(ctx));
+    DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, 0, NV));
+    {
+      cudaStream_t cst = view_stream(ctx, L, st);
+      StageTimer tn(ctx, ST_SETUP, cst);
+      launch_vertex_normals(mesh->verts, V, mesh->tris, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
+                            ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), cst);
+    }
+    for (int w = 0; w < NV; ++w) bin_count_view(ctx, w, view_stream(ctx, w, st));
+    DSM_CHECK(cudaGetLastError());
+    if (sizing) {
+      // first frame of this scene size: read the pair counts once and size the lists
+      DSM_CHECK(join_views(ctx, st, 0, NV));
+      DSM_CHECK(cudaMemcpyAsync(ctx->hstatus, ctx->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+      DSM_CHECK(cudaStreamSynchronize(st));
+      for (int w = 0; w < NV; ++w) {
+        s = grow_list(ctx, ctx->view[w], ctx->hstatus->needed_pairs[w]);
+        if (s != DSM_OK) return s;
+      }
+      DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, 0, NV));
+    }
+    // ---- per view: bin fill, raster; per light: Alg. 1 (f, f^2 -> antialias -> filter)
+    for (int w = 0; w < NV; ++w) {
+      cudaStream_t vst = view_stream(ctx, w, st);
+      raster_view(ctx, w, vst);
+      if (w < L) light_maps(ctx, w, vst);
+    }
+    DSM_CHECK(join_views(ctx, st, 0, NV));
+    DSM_CHECK(cudaGetLastError());
+    // ---- cameras: shade (Alg. 2 x Lambert) and the final antialiasing, each on its stream
+    if (C > 1) DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, L, NV));
+    for (int c = 0; c < C; ++c) {
+      s = camera_colour(ctx, c, images[c], C > 1 ? view_stream(ctx, L + c, st) : st);
+      if (s != DSM_OK) return s;
+    }
+    if (C > 1) DSM_CHECK(join_views(ctx, st, L, NV));
   }
-  t_final.stop();
   DSM_CHECK(cudaGetLastError());
-
-  ctx->mesh = *mesh;
-  for (int l = 0; l < L; ++l) ctx->lights[l] = lights[l];
-  ctx->L = L;
-  ctx->cam = *cam;
-  ctx->params = *params;
-  ctx->stream = st;
+  ctx->sized_sig = sig;
   ctx->have_fwd = true;
   return DSM_OK;
 }
 
-dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_dverts, float* dL_dlight,
-                               float* dL_dalbedo) {
+dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* lights, const float* light_params,
+                      int32_t n_lights, const dsm_camera* cam, const dsm_params* params, float* image) {
+  return dsm_render_cameras(ctx, mesh, lights, light_params, n_lights, cam, 1, params, &image);
+}
+
+dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dimages, float* dL_dverts,
+                                       float* dL_dlight, float* dL_dalbedo) {
   if (!ctx) return DSM_ERR_INVALID_ARG;
-  if (!ctx->have_fwd) return fail(ctx, DSM_ERR_NO_FORWARD, "dsm_render_backward without a forward");
-  if (!dL_dimage) return fail(ctx, DSM_ERR_INVALID_ARG, "null dL_dimage");
+  if (!ctx->have_fwd) return fail(ctx, DSM_ERR_NO_FORWARD, "backward without a forward");
+  if (!dL_dimages) return fail(ctx, DSM_ERR_INVALID_ARG, "null dL_dimages");
+  for (int c = 0; c < ctx->C; ++c)
+    if (!dL_dimages[c]) return fail(ctx, DSM_ERR_INVALID_ARG, "null dL_dimage");
   cudaStream_t st = ctx->stream;
   const dsm_mesh& mesh = ctx->mesh;
-  const int V = mesh.n_verts, T = mesh.n_tris, L = ctx->L;
-  const int Wc = ctx->cam.width, Hc = ctx->cam.height;
-  if (!dL_dverts) { DSM_CHECK(ctx->scratch_dverts.ensure(sizeof(float) * 3 * std::max(V, 1))); dL_dverts = ctx->scratch_dverts.as<float>(); }
-  if (!dL_dlight) { DSM_CHECK(ctx->scratch_dlight.ensure(sizeof(float) * 6 * DSM_MAX_LIGHTS)); dL_dlight = ctx->scratch_dlight.as<float>(); }
-  if (!dL_dalbedo) { DSM_CHECK(ctx->scratch_dalbedo.ensure(sizeof(float) * 3 * mesh.n_materials)); dL_dalbedo = ctx->scratch_dalbedo.as<float>(); }
-  DSM_CHECK(ctx->gcolor.ensure((size_t)Wc * Hc * sizeof(float4)));
-  DSM_CHECK(ctx->pgrad.ensure((size_t)Wc * Hc * 2 * sizeof(float4)));
+  const int V = mesh.n_verts, T = mesh.n_tris, L = ctx->L, C = ctx->C, NV = L + C;
+  if (!dL_dverts) {
+    DSM_CHECK(ctx->scratch_dverts.ensure(sizeof(float) * 3 * std::max(V, 1)));
+    dL_dverts = ctx->scratch_dverts.as<float>();
+  }
+  if (!dL_dlight) {
+    DSM_CHECK(ctx->scratch_dlight.ensure(sizeof(float) * 6 * DSM_MAX_LIGHTS));
+    dL_dlight = ctx->scratch_dlight.as<float>();
+  }
+  if (!dL_dalbedo) {
+    DSM_CHECK(ctx->scratch_dalbedo.ensure(sizeof(float) * 3 * mesh.n_materials));
+    dL_dalbedo = ctx->scratch_dalbedo.as<float>();
+  }
+  for (int c = 0; c < C; ++c) {
+    ViewBufs& cv = vbuf(ctx, L + c);
+    const size_t px = (size_t)ctx->cams[c].width * ctx->cams[c].height;
+    DSM_CHECK(cv.gcolor.ensure(px * sizeof(float4)));
+    DSM_CHECK(cv.pgrad.ensure(px * 2 * sizeof(float4)));
+  }
   DSM_CHECK(ctx->gnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->gN.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->gface.ensure(sizeof(float) * 3 * std::max(T, 1)));
@@ -609,11 +849,16 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   for (int l = 0; l < L; ++l) {
     const size_t R2 = (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2);
     DSM_CHECK(ctx->light[l].gm.ensure(R2));
-    DSM_CHECK(ctx->light[l].gft.ensure(R2));
+    DSM_CHECK(lwork(ctx, l).gft.ensure(R2));
   }
+  auto clear_view = [&](Clearer& cl, int w) {
+    ViewBufs& v = vbuf(ctx, w);
+    cl.add(v.gclip.p, sizeof(float4) * V);
+    cl.add(v.big_acc.p, (size_t)kMaxBig * kBigSlots * (view_is_light(ctx, w) ? kBigStrideSm : kBigStrideCam) * 4);
+  };
   // ---- clear accumulators and outputs
-  StageTimer t_clear(ctx, ST_BWD_CLEAR, st);
   {
+    StageTimer t(ctx, ST_BWD_CLEAR, st);
     Clearer cl;
     cl.add(dL_dverts, sizeof(float) * 3 * V);
     if (L) cl.add(dL_dlight, sizeof(float) * 6 * L);
@@ -621,104 +866,100 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
     cl.add(ctx->gnormal.p, sizeof(float) * 3 * V);
     cl.add(ctx->gQ.p, sizeof(float) * 20 * DSM_MAX_LIGHTS);
     cl.add(ctx->gdirect.p, sizeof(float) * 3 * DSM_MAX_LIGHTS);
-    for (int w = 0; w <= L; ++w) cl.add(ctx->view[w].gclip.p, sizeof(float4) * V);
+    cl.add(ctx->red.p, sizeof(float) * kRedSlots * red_stride);
     for (int l = 0; l < L; ++l)
       cl.add(ctx->light[l].gm.p, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2));
-    cl.add(ctx->red.p, sizeof(float) * kRedSlots * red_stride);
-    for (int w = 0; w <= L; ++w)
-      cl.add(ctx->view[w].big_acc.p, (size_t)kMaxBig * kBigSlots * (w < L ? kBigStrideSm : kBigStrideCam) * 4);
-    static_assert(6 + 3 * (DSM_MAX_LIGHTS + 1) <= kMaxClear, "clear list");
+    if (!ctx->recompute)
+      for (int w = 0; w < NV; ++w) clear_view(cl, w);
+    static_assert(7 + DSM_MAX_LIGHTS + 2 * kMaxViews <= kMaxClear, "clear list");
     cl.launch(st);
   }
   DSM_CHECK(cudaGetLastError());
 
-  t_clear.stop();
-  // ---- final antialiasing adjoint and the shading adjoint
-  ViewBufs& cv = ctx->view[L];
-  StageTimer t_faa(ctx, ST_BWD_FINAL_AA, st);
-  AAArgs caa{cv.gbuf.as<float4>(), Wc, Hc, mesh.tris, cv.sil.as<uint8_t>(), cv.snap.as<VertSnap>(), cv.clip.as<float4>()};
-  if (ctx->params.aa_final) {
-    launch_aa_backward4(caa, ctx->camcolor.as<float4>(), reinterpret_cast<const float4*>(dL_dimage),
-                        ctx->gcolor.as<float4>(), cv.gclip.as<float4>(), cv.hflag.as<uint8_t>(), cv.aa_work(), st);
+  if (ctx->recompute) {
+    // ---- the filtered moment maps again (every camera's shading adjoint reads all of them)
+    ctx->stage_override = ST_BWD_RECOMPUTE;
+    for (int l = 0; l < L; ++l) {
+      dsm_status s = rebuild_view(ctx, l, false, true, false, st);
+      if (s != DSM_OK) { ctx->stage_override = -1; return s; }
+    }
+    ctx->stage_override = -1;
+    // ---- per camera: G-buffer and colour again, then its adjoints and its share of dL/dv
+    for (int c = 0; c < C; ++c) {
+      ctx->stage_override = ST_BWD_RECOMPUTE;
+      dsm_status s = rebuild_view(ctx, L + c, false, false, ctx->params.aa_final != 0, st);
+      if (s == DSM_OK) s = camera_colour(ctx, c, nullptr, st);
+      ctx->stage_override = -1;
+      if (s != DSM_OK) return s;
+      {
+        StageTimer t(ctx, ST_BWD_CLEAR, st);
+        Clearer cl;
+        clear_view(cl, L + c);
+        cl.launch(st);
+      }
+      s = camera_backward(ctx, c, dL_dimages[c], dL_dverts, dL_dalbedo, red_stride, st);
+      if (s != DSM_OK) return s;
+      camera_scatter(ctx, c, dL_dverts, dL_dalbedo, red_stride, st);
+      StageTimer t(ctx, ST_BWD_VERTEX, st);
+      vertex_backward_views(ctx, L + c, 1, dL_dverts, red_stride, st);
+    }
+    // ---- per light: G-buffer, f and the antialiasing list again, then its adjoints
+    for (int l = 0; l < L; ++l) {
+      ctx->stage_override = ST_BWD_RECOMPUTE;
+      dsm_status s = rebuild_view(ctx, l, false, false, ctx->params.aa_shadow != 0, st);
+      ctx->stage_override = -1;
+      if (s != DSM_OK) return s;
+      {
+        StageTimer t(ctx, ST_BWD_CLEAR, st);
+        Clearer cl;
+        clear_view(cl, l);
+        cl.launch(st);
+      }
+      light_backward(ctx, l, st);
+      StageTimer t(ctx, ST_BWD_VERTEX, st);
+      vertex_backward_views(ctx, l, 1, dL_dverts, red_stride, st);
+    }
   } else {
-    DSM_CHECK(cudaMemcpyAsync(ctx->gcolor.p, dL_dimage, (size_t)Wc * Hc * sizeof(float4), cudaMemcpyDeviceToDevice,
-                              st));
+    // ---- per camera: final antialiasing adjoint and the shading adjoint
+    DSM_CHECK(ensure_streams(ctx));
+    if (C > 1) DSM_CHECK(fork_views(ctx, st, ctx->ev_bfork, L, NV));
+    for (int c = 0; c < C; ++c) {
+      dsm_status s = camera_backward(ctx, c, dL_dimages[c], dL_dverts, dL_dalbedo, red_stride,
+                                     C > 1 ? view_stream(ctx, L + c, st) : st);
+      if (s != DSM_OK) return s;
+    }
+    if (C > 1) DSM_CHECK(join_views(ctx, st, L, NV));   // gm is complete
+    // ---- per light on its own stream: G^T, antialiasing adjoint, interpolation
+    // adjoint (they write only that light's buffers), beside the camera scatters
+    DSM_CHECK(fork_views(ctx, st, ctx->ev_bfork, 0, L));
+    for (int l = 0; l < L; ++l) light_backward(ctx, l, view_stream(ctx, l, st));
+    for (int c = 0; c < C; ++c)
+      camera_scatter(ctx, c, dL_dverts, dL_dalbedo, red_stride, C > 1 ? view_stream(ctx, L + c, st) : st);
+    DSM_CHECK(join_views(ctx, st, 0, L));
+    if (C > 1) DSM_CHECK(join_views(ctx, st, L, NV));
+    StageTimer t(ctx, ST_BWD_VERTEX, st);
+    vertex_backward_views(ctx, 0, NV, dL_dverts, red_stride, st);
   }
-  t_faa.stop();
-  ShadeArgs sa{};
-  sa.gbuf = cv.gbuf.as<float4>();
-  sa.W = Wc; sa.H = Hc;
-  sa.verts = mesh.verts; sa.tris = mesh.tris; sa.tri_mat = mesh.tri_material;
-  sa.albedo = mesh.albedo; sa.n_mat = mesh.n_materials;
-  sa.vnormal = ctx->vnormal.as<float>();
-  sa.cam_clip = cv.clip.as<float4>();
-  sa.lights = ctx->lights_dev.as<LightDev>(); sa.L = L;
-  for (int l = 0; l < L; ++l) { sa.mom[l] = ctx->light[l].mom.as<float2>(); sa.res[l] = ctx->light[l].res; }
-  sa.min_variance = ctx->params.min_variance;
-  ShadeGradArgs ga{};
-  ga.gcolor = ctx->gcolor.as<float4>();
-  ga.dverts = dL_dverts;
-  ga.gnormal = ctx->gnormal.as<float>();
-  ga.gclip = cv.gclip.as<float4>();
-  ga.dalbedo = dL_dalbedo;
-  for (int l = 0; l < L; ++l) ga.gm[l] = ctx->light[l].gm.as<float2>();
-  ga.red = ctx->red.as<float>();
-  ga.red_stride = red_stride;
-  ga.big = cv.big_index.as<int>();
-  ga.big_acc = cv.big_acc.as<float>();
-  ga.pgrad = ctx->pgrad.as<float4>();
+  // ---- normals, lights
   {
-    StageTimer t(ctx, ST_BWD_SHADE, st);
-    launch_shade_backward(sa, ga, st);
+    StageTimer t(ctx, ST_BWD_VERTEX, st);
+    launch_normals_backward(mesh.verts, V, mesh.tris, T, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
+                            ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), ctx->gnormal.as<float>(),
+                            ctx->gN.as<float>(), ctx->gface.as<float>(), dL_dverts, st);
+    launch_red_reduce(ctx->red.as<float>(), red_stride, L, n_mat_red, ctx->gQ.as<float>(), ctx->gdirect.as<float>(),
+                      dL_dalbedo, st);
+    launch_light_grad(ctx->lights_dev.as<LightDev>(), L, ctx->gQ.as<float>(), ctx->gdirect.as<float>(), dL_dlight,
+                      st);
   }
-  // ---- per light on its own stream: G^T, antialiasing adjoint, interpolation
-  // adjoint (they write only that light's buffers), beside the camera scatter
-  DSM_CHECK(ensure_streams(ctx));
-  DSM_CHECK(fork_views(ctx, st, ctx->ev_bfork, L));
-  for (int l = 0; l < L; ++l) {
-    ViewBufs& v = ctx->view[l];
-    LightBufs& lb = ctx->light[l];
-    cudaStream_t vst = view_stream(ctx, l, st);
-    AAArgs aa{v.gbuf.as<float4>(), v.W, v.H, mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(), v.clip.as<float4>()};
-    {
-      StageTimer t(ctx, ST_BWD_FILTER, vst);
-      // dL/d(f~, (f^2)~) and, folded through f^2 = f f, dL/df (into tmp)
-      launch_filter_adjoint(lb.gm.as<float2>(), lb.tmp.as<float2>(), lb.gft.as<float2>(), v.W, lb.fa, vst,
-                            lb.fmap.as<float2>(), lb.tmp.as<float>());
-    }
-    {
-      // the listed texels: dL/df through the antialiasing (overwrites tmp there)
-      StageTimer t(ctx, ST_BWD_SM_AA, vst);
-      if (ctx->params.aa_shadow)
-        launch_sm_aa_adjoint_list(aa, lb.fmap.as<float2>(), lb.gft.as<float2>(), v.gclip.as<float4>(),
-                                  lb.tmp.as<float>(), v.aa_work(), vst);
-    }
-    {
-      StageTimer t(ctx, ST_BWD_SM_INTERP, vst);
-      BigArgs big{v.big_index.as<int>(), v.big_tri.as<int>(), v.big_acc.as<float>(), ctx->status.as<DevStatus>(), l};
-      launch_sm_interp_adjoint(aa, lb.tmp.as<float>(), v.depth.as<float>(), v.gclip.as<float4>(), big, vst);
-    }
-  }
-  {
-    StageTimer t(ctx, ST_BWD_SHADE_SCATTER, st);
-    launch_shade_scatter(sa, ga, st);
-    launch_shade_big_resolve(sa, ga, cv.big_tri.as<int>(), ctx->status.as<DevStatus>(), L, st);
-  }
-  DSM_CHECK(join_views(ctx, st, L));
-  // ---- vertices, normals, lights
-  StageTimer t_vert(ctx, ST_BWD_VERTEX, st);
-  VertGradPtrs gp{};
-  for (int w = 0; w <= L; ++w) gp.gclip[w] = ctx->view[w].gclip.as<float4>();
-  launch_vertex_backward(mesh.verts, V, ctx->viewM.as<float>(), L + 1, L, gp, dL_dverts, ctx->red.as<float>(),
-                         red_stride, st);
-  launch_normals_backward(mesh.verts, V, mesh.tris, T, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
-                          ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), ctx->gnormal.as<float>(),
-                          ctx->gN.as<float>(), ctx->gface.as<float>(), dL_dverts, st);
-  launch_red_reduce(ctx->red.as<float>(), red_stride, L, n_mat_red, ctx->gQ.as<float>(), ctx->gdirect.as<float>(),
-                    dL_dalbedo, st);
-  launch_light_grad(ctx->lights_dev.as<LightDev>(), L, ctx->gQ.as<float>(), ctx->gdirect.as<float>(), dL_dlight, st);
   DSM_CHECK(cudaGetLastError());
   return DSM_OK;
+}
+
+dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_dverts, float* dL_dlight,
+                               float* dL_dalbedo) {
+  if (!ctx) return DSM_ERR_INVALID_ARG;
+  if (ctx->have_fwd && ctx->C != 1) return fail(ctx, DSM_ERR_INVALID_ARG, "last forward had several cameras");
+  return dsm_render_cameras_backward(ctx, &dL_dimage, dL_dverts, dL_dlight, dL_dalbedo);
 }
 
 dsm_status dsm_l2_loss_grad(const float* image, const float* target, int64_t n, float* loss, float* dL_dimage,
@@ -807,22 +1048,28 @@ uint64_t dsm_kernel_launches(void) { return (uint64_t)g_kernel_launches.load(); 
 dsm_status dsm_debug_copy(dsm_ctx* ctx, int32_t what, int32_t index, void* dst, size_t bytes) {
   if (!ctx || !dst) return DSM_ERR_INVALID_ARG;
   const int L = ctx->L, V = ctx->mesh.n_verts;
+  if (ctx->recompute && what != 3 && what != 5 && what != 7)
+    return fail(ctx, DSM_ERR_INVALID_ARG, "per-view buffers are not kept under recomputation");
   const void* src = nullptr;
   size_t size = 0;
-  auto light_ok = [&](int i) { return i >= 0 && i < L; };
-  auto view_ok = [&](int i) { return i >= 0 && i <= L; };
+  const bool light_ok = index >= 0 && index < L;
+  const bool view_ok = index >= 0 && index < L + ctx->C;
+  const bool cam_ok = index >= 0 && index < ctx->C;
+  const size_t R2 = light_ok ? (size_t)ctx->light[index].res * ctx->light[index].res * 8 : 0;
+  auto view_px = [&](int w) { return (size_t)ctx->view[w].W * ctx->view[w].H; };
+  auto cam_px = [&](int c) { return (size_t)ctx->cams[c].width * ctx->cams[c].height; };
   switch (what) {
-    case 0: if (view_ok(index)) { src = ctx->view[index].gbuf.p; size = (size_t)ctx->view[index].W * ctx->view[index].H * 16; } break;
-    case 1: if (light_ok(index)) { src = ctx->light[index].fmap.p; size = (size_t)ctx->light[index].res * ctx->light[index].res * 8; } break;
-    case 2: if (light_ok(index)) { src = ctx->light[index].ftilde.p; size = (size_t)ctx->light[index].res * ctx->light[index].res * 8; } break;
-    case 3: if (light_ok(index)) { src = ctx->light[index].mom.p; size = (size_t)ctx->light[index].res * ctx->light[index].res * 8; } break;
-    case 4: src = ctx->camcolor.p; size = (size_t)ctx->cam.width * ctx->cam.height * 16; break;
+    case 0: if (view_ok) { src = ctx->view[index].gbuf.p; size = view_px(index) * 16; } break;
+    case 1: if (light_ok) { src = ctx->light[index].fmap.p; size = R2; } break;
+    case 2: if (light_ok) { src = ctx->light[index].ftilde.p; size = R2; } break;
+    case 3: if (light_ok) { src = ctx->light[index].mom.p; size = R2; } break;
+    case 4: if (cam_ok) { src = ctx->view[L + index].color.p; size = cam_px(index) * 16; } break;
     case 5: src = ctx->viewM.p; size = (size_t)L * 20 * 4; break;
-    case 6: if (view_ok(index)) { src = ctx->view[index].snap.p; size = (size_t)V * 16; } break;
-    case 7: if (light_ok(index)) { src = ctx->light[index].gm.p; size = (size_t)ctx->light[index].res * ctx->light[index].res * 8; } break;
-    case 8: if (view_ok(index)) { src = ctx->view[index].gclip.p; size = (size_t)V * 16; } break;
-    case 9: if (light_ok(index)) { src = ctx->light[index].gft.p; size = (size_t)ctx->light[index].res * ctx->light[index].res * 8; } break;
-    case 10: src = ctx->gcolor.p; size = (size_t)ctx->cam.width * ctx->cam.height * 16; break;
+    case 6: if (view_ok) { src = ctx->view[index].snap.p; size = (size_t)V * 16; } break;
+    case 7: if (light_ok) { src = ctx->light[index].gm.p; size = R2; } break;
+    case 8: if (view_ok) { src = ctx->view[index].gclip.p; size = (size_t)V * 16; } break;
+    case 9: if (light_ok) { src = ctx->light[index].gft.p; size = R2; } break;
+    case 10: if (cam_ok) { src = ctx->view[L + index].gcolor.p; size = cam_px(index) * 16; } break;
     default: break;
   }
   if (!src || size == 0) return fail(ctx, DSM_ERR_INVALID_ARG, "unknown or empty debug buffer");
@@ -843,6 +1090,27 @@ dsm_status dsm_debug_copy(dsm_ctx* ctx, int32_t what, int32_t index, void* dst, 
   DSM_CHECK(cudaMemcpyAsync(dst, src, size, cudaMemcpyDeviceToDevice, ctx->stream));
   DSM_CHECK(cudaStreamSynchronize(ctx->stream));
   return DSM_OK;
+}
+
+uint64_t dsm_memory_bytes(dsm_ctx* ctx) {
+  if (!ctx) return 0;
+  uint64_t n = 0;
+  const Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->status,
+                       &ctx->vnormal, &ctx->vnlen, &ctx->gnormal, &ctx->gN, &ctx->gface, &ctx->gQ, &ctx->gdirect,
+                       &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo, &ctx->filter_tmp,
+                       &ctx->red};
+  for (const Buf* b : bufs) n += b->cap;
+  for (const auto& v : ctx->view) {
+    const Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
+                       &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr,
+                       &v.hflag, &v.color, &v.gcolor, &v.pgrad};
+    for (const Buf* b : vb) n += b->cap;
+  }
+  for (const auto& l : ctx->light) {
+    const Buf* lb[] = {&l.fmap, &l.ftilde, &l.tmp, &l.mom, &l.gm, &l.gft};
+    for (const Buf* b : lb) n += b->cap;
+  }
+  return n;
 }
 
 }  // extern "C"

@@ -70,7 +70,7 @@ struct ShadeGradArgs {
 };
 
 struct VertGradPtrs {
-  const float4* gclip[DSM_MAX_LIGHTS + 1];   // per view (lights, then camera); lights: z = dL/d vertex depth
+  const float4* gclip[kMaxViews];   // per view (lights, then cameras); lights: z = dL/d vertex depth
 };
 
 // Big-triangle bookkeeping of one view (see kBigTiles).
@@ -99,7 +99,6 @@ struct AAArgs {
 };
 
 // Per-view pointers and sizes for the fused setup of all views of a frame.
-constexpr int kMaxViews = DSM_MAX_LIGHTS + 1;
 struct ViewSetupArgs {
   int n;
   int W[kMaxViews], H[kMaxViews], tiles[kMaxViews];

@@ -259,7 +259,7 @@ __global__ void tri_setup_all_kernel(const int* __restrict__ tris, int T, ViewSe
   // antialiasing work lists, start this frame empty
   for (int w = 0; w < a.n; ++w)
     for (int k = t; k < a.tiles[w]; k += gridDim.x * blockDim.x) a.count[w][k] = 0;
-  if (t < DSM_MAX_LIGHTS + 1) {
+  if (t < kMaxViews) {
     status->big_count[t] = 0;
     status->needed_pairs[t] = 0;
   }
@@ -682,8 +682,8 @@ void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, De
   bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, nullptr, nullptr, 0, status, view,
                                                      big_index, big_tri);
   count_launches(1);
-  bin_big_kernel<false><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, nullptr,
-                                                          nullptr, 0, status);
+  bin_big_kernel<false><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter,
+                                                                     nullptr, nullptr, 0, status);
 }
 
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st) {
@@ -699,8 +699,8 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, con
   bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, offset, list, capacity, status, view,
                                                     const_cast<int*>(big_index), const_cast<int*>(big_tri));
   count_launches(1);
-  bin_big_kernel<true><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter, offset, list,
-                                                         capacity, status);
+  bin_big_kernel<true><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter,
+                                                                    offset, list, capacity, status);
 }
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,

@@ -107,7 +107,9 @@ __device__ __forceinline__ bool load_surf(const ShadeArgs& a, size_t p, Surf& s)
     const int v = a.tris[3 * s.tri + k];
     s.v[k] = v;
     s.x.x += s.b[k] * a.verts[3 * v]; s.x.y += s.b[k] * a.verts[3 * v + 1]; s.x.z += s.b[k] * a.verts[3 * v + 2];
-    s.nt.x += s.b[k] * a.vnormal[3 * v]; s.nt.y += s.b[k] * a.vnormal[3 * v + 1]; s.nt.z += s.b[k] * a.vnormal[3 * v + 2];
+    s.nt.x += s.b[k] * a.vnormal[3 * v];
+    s.nt.y += s.b[k] * a.vnormal[3 * v + 1];
+    s.nt.z += s.b[k] * a.vnormal[3 * v + 2];
   }
   s.nlen = sqrtf(s.nt.x * s.nt.x + s.nt.y * s.nt.y + s.nt.z * s.nt.z);
   const float il = s.nlen > 0.f ? 1.f / s.nlen : 0.f;
@@ -195,7 +197,8 @@ __device__ __forceinline__ Look lookup(const float* Q, const float2* __restrict_
   const int j0 = min(max(L.j0, 0), R - 1), j1 = min(max(L.j0 + 1, 0), R - 1);
   const float2 m00 = mom[(size_t)j0 * R + i0], m01 = mom[(size_t)j0 * R + i1];
   const float2 m10 = mom[(size_t)j1 * R + i0], m11 = mom[(size_t)j1 * R + i1];
-  const float w00 = (1.f - L.fs) * (1.f - L.ft), w01 = L.fs * (1.f - L.ft), w10 = (1.f - L.fs) * L.ft, w11 = L.fs * L.ft;
+  const float w00 = (1.f - L.fs) * (1.f - L.ft), w01 = L.fs * (1.f - L.ft);
+  const float w10 = (1.f - L.fs) * L.ft, w11 = L.fs * L.ft;
   L.m = make_float2(w00 * m00.x + w01 * m01.x + w10 * m10.x + w11 * m11.x,
                     w00 * m00.y + w01 * m01.y + w10 * m10.y + w11 * m11.y);
   const float raw = fmaf(-L.m.x, L.m.x, L.m.y);
@@ -308,7 +311,9 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
       const float3 om = light_omega(Ld, s.x, len);
       const float ndo = s.n.x * om.x + s.n.y * om.y + s.n.z * om.z;
       const float lam = fmaxf(ndo, 0.f);
-      rad.x += L.vis * lam * Ld.intensity[0]; rad.y += L.vis * lam * Ld.intensity[1]; rad.z += L.vis * lam * Ld.intensity[2];
+      rad.x += L.vis * lam * Ld.intensity[0];
+      rad.y += L.vis * lam * Ld.intensity[1];
+      rad.z += L.vis * lam * Ld.intensity[2];
       const float sl = grad_rad.x * Ld.intensity[0] + grad_rad.y * Ld.intensity[1] + grad_rad.z * Ld.intensity[2];
       const float gvis = sl * lam, glam = sl * L.vis;
       if (ndo > 0.f && glam != 0.f) {

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libdsm.so")
 DSM_OK, DSM_ERR_INVALID_ARG, DSM_ERR_CAPACITY, DSM_ERR_CUDA, DSM_ERR_TIMEOUT, DSM_ERR_NO_FORWARD, DSM_ERR_OOM, \
     DSM_ERR_NO_TOPOLOGY = range(8)
 MAX_LIGHTS = 8
+MAX_CAMERAS = 8
 
 # debug_copy buffer codes (see include/dsm.h)
 DBG_GBUF, DBG_F, DBG_FTILDE, DBG_MOMENTS, DBG_COLOR, DBG_Q, DBG_SNAP, DBG_GM, DBG_GCLIP, DBG_GFT, DBG_GCOLOR = range(11)
@@ -28,7 +29,8 @@ EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_
             "dsm_profile_enable", "dsm_profile_stage_count", "dsm_profile_stage_name", "dsm_profile_read",
             "dsm_kernel_launches", "dsm_filter_moments_noalloc", "dsm_filter_moments_adjoint",
             "dsm_batch_create", "dsm_batch_destroy", "dsm_batch_context", "dsm_batch_step", "dsm_batch_sync",
-            "dsm_batch_kernels_per_step", "dsm_batch_last_error"]
+            "dsm_batch_kernels_per_step", "dsm_batch_last_error", "dsm_render_cameras",
+            "dsm_render_cameras_backward", "dsm_memory_bytes", "dsm_adam_step"]
 
 
 class DsmError(RuntimeError):
@@ -105,6 +107,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dsm_batch_sync": ([P], I32),
         "dsm_batch_kernels_per_step": ([P], ctypes.c_uint64),
         "dsm_batch_last_error": ([P], ctypes.c_char_p),
+        "dsm_render_cameras": ([P, ctypes.POINTER(Mesh), ctypes.POINTER(Light), P, I32, ctypes.POINTER(Camera), I32,
+                                ctypes.POINTER(Params), ctypes.POINTER(P)], I32),
+        "dsm_render_cameras_backward": ([P, ctypes.POINTER(P), P, P, P], I32),
+        "dsm_memory_bytes": ([P], ctypes.c_uint64),
+        "dsm_adam_step": ([P, P, P, P, I64, I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P],
+                          I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -159,7 +167,7 @@ def params_struct(p: dict, stream=None) -> Params:
     q.filter_boundary = int(p.get("filter_boundary", 0))
     q.aa_shadow = int(p.get("aa_shadow", 1))
     q.aa_final = int(p.get("aa_final", 1))
-    q.recompute_in_backward = 0
+    q.recompute_in_backward = int(p.get("recompute_in_backward", 0))
     q.stream = _stream_ptr(stream)
     return q
 
@@ -201,6 +209,22 @@ class Context:
     def render_backward(self, dL_dimage, dverts=None, dlight=None, dalbedo=None):
         self._check(self.lib.dsm_render_backward(self.h, _ptr(dL_dimage), _ptr(dverts), _ptr(dlight),
                                                  _ptr(dalbedo)), self.h)
+
+    def render_cameras(self, mesh: Mesh, lights, light_params: torch.Tensor, cameras, params: Params, images):
+        arr = (Light * max(1, len(lights)))(*lights)
+        cams = (Camera * len(cameras))(*cameras)
+        ptrs = (ctypes.c_void_p * len(images))(*[_ptr(im) for im in images])
+        self._check(self.lib.dsm_render_cameras(self.h, ctypes.byref(mesh), arr, _ptr(light_params), len(lights),
+                                                cams, len(cameras), ctypes.byref(params), ptrs), self.h)
+
+    def render_cameras_backward(self, dL_dimages, dverts=None, dlight=None, dalbedo=None):
+        ptrs = (ctypes.c_void_p * len(dL_dimages))(*[_ptr(g) for g in dL_dimages])
+        self._check(self.lib.dsm_render_cameras_backward(self.h, ptrs, _ptr(dverts), _ptr(dlight), _ptr(dalbedo)),
+                    self.h)
+
+    def memory_bytes(self) -> int:
+        """Device memory held by this context (scratch and saved state)."""
+        return int(self.lib.dsm_memory_bytes(self.h))
 
     def filter_moments(self, inp: torch.Tensor, out: torch.Tensor, sigma: float, radius: int = 0, kind: int = 0,
                        boundary: int = 0, stream=None):
@@ -246,6 +270,20 @@ def l2_loss_grad(image: torch.Tensor, target: torch.Tensor, loss: torch.Tensor, 
         raise DsmError(st, "dsm_l2_loss_grad")
 
 
+def adam_step(params: torch.Tensor, grads: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int,
+              lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8, stream=None):
+    """In-place Adam step on float32 device tensors (m, v zero before step 1)."""
+    lib = load_library()
+    n = params.numel()
+    for t in (grads, m, v):
+        if t.numel() != n:
+            raise ValueError("adam_step: params, grads, m and v must have the same size")
+    st = lib.dsm_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), n, int(step), float(lr), float(betas[0]),
+                           float(betas[1]), float(eps), _stream_ptr(stream))
+    if st != DSM_OK:
+        raise DsmError(st, "dsm_adam_step")
+
+
 class Renderer:
     """Scene held on the device plus a context: forward / backward of the
     differentiable shadow-mapping renderer for one camera."""
@@ -287,13 +325,35 @@ class Renderer:
                         params_struct(self.params_dict, stream), image)
         return image
 
-    def backward(self, dL_dimage: torch.Tensor, dverts=None, dlight=None, dalbedo=None):
+    def _grads(self, dverts, dlight, dalbedo):
         V, L, M = self.verts.shape[0], len(self.lights), self.albedo.shape[0]
         dverts = torch.empty((V, 3), dtype=torch.float32, device=self.device) if dverts is None else dverts
         dlight = torch.empty((max(L, 1), 6), dtype=torch.float32, device=self.device) if dlight is None else dlight
         dalbedo = torch.empty((M, 3), dtype=torch.float32, device=self.device) if dalbedo is None else dalbedo
+        return dverts, dlight, dalbedo
+
+    def backward(self, dL_dimage: torch.Tensor, dverts=None, dlight=None, dalbedo=None):
+        dverts, dlight, dalbedo = self._grads(dverts, dlight, dalbedo)
         self.ctx.render_backward(dL_dimage.contiguous(), dverts, dlight, dalbedo)
-        return dverts, dlight[:L], dalbedo
+        return dverts, dlight[:len(self.lights)], dalbedo
+
+    def forward_cameras(self, cameras: list, verts=None, light_params=None, albedo=None, images=None,
+                        stream=None) -> list:
+        """One forward seen by several cameras (dicts like scene["camera"]):
+        each light's maps are built once; returns one image per camera."""
+        lp = self.light_params if light_params is None else light_params
+        if images is None:
+            images = [torch.empty((int(c["height"]), int(c["width"]), 4), dtype=torch.float32, device=self.device)
+                      for c in cameras]
+        self.ctx.render_cameras(self.mesh_struct(verts, albedo), self.lights, lp,
+                                [camera_struct(c) for c in cameras], params_struct(self.params_dict, stream), images)
+        return images
+
+    def backward_cameras(self, dL_dimages: list, dverts=None, dlight=None, dalbedo=None):
+        """Backward of the last forward_cameras for the loss summed over the cameras."""
+        dverts, dlight, dalbedo = self._grads(dverts, dlight, dalbedo)
+        self.ctx.render_cameras_backward([g.contiguous() for g in dL_dimages], dverts, dlight, dalbedo)
+        return dverts, dlight[:len(self.lights)], dalbedo
 
 
 class DSMFunction(torch.autograd.Function):

@@ -32,7 +32,7 @@ __all__ = [
     "icosphere", "subdivided_box", "ground_quad", "sh_displace", "random_rotation",
     "look_at_perspective", "directional_light", "spot_light", "merge_meshes",
     "config1", "config2", "config3", "config4", "config5", "config_by_name",
-    "tiny_scene", "jitter_vertices",
+    "tiny_scene", "jitter_vertices", "displaced_target",
 ]
 
 
@@ -379,6 +379,25 @@ def jitter_vertices(scene: dict, sigma: float, seed: int) -> np.ndarray:
     """Seeded vertex perturbation used to make a target render."""
     rng = np.random.default_rng(seed)
     return (scene["verts"] + rng.normal(0.0, sigma, scene["verts"].shape)).astype(np.float32)
+
+
+def displaced_target(scene: dict, amplitude: float = 0.03, seed: int = 0, material: int = 0) -> np.ndarray:
+    """Vertices of a seeded smooth displacement of one object (the vertices
+    of the triangles with the given material): each moves along its
+    direction n from the object's bounding-box centre c,
+    x -> c + (x - c) (1 + A S(n) / max|S|), S a seeded combination of real SH
+    of degree 1..3.  Used to render reconstruction targets."""
+    rng = np.random.default_rng(50_000 + seed)
+    verts = scene["verts"].astype(np.float64)
+    sel = np.unique(scene["tris"][scene["tri_mat"] == material])
+    x = verts[sel]
+    c = 0.5 * (x.min(0) + x.max(0))
+    d = x - c
+    n = d / np.linalg.norm(d, axis=1, keepdims=True)
+    s = _real_sh_basis(n) @ rng.standard_normal(15)
+    out = verts.copy()
+    out[sel] = c + d * (1.0 + amplitude * s / np.abs(s).max())[:, None]
+    return out.astype(np.float32)
 
 
 def config_by_name(name: str):

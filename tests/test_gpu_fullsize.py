@@ -1,7 +1,11 @@
 """Spot checks of full-size frames in the launch configuration the benchmark
 times (the default renderer: per-view streams, the same kernels): config 2
-(50k-triangle displaced icosphere, 1024² spot map and image) and config 3
-(330k triangles in 64 objects, two 2048² maps, 1920x1080 image).
+(50k-triangle displaced icosphere, 1024² spot map and image), config 3
+(330k triangles in 64 objects, two 2048² maps, 1920x1080 image) and config 5
+(1M-triangle displaced icosphere seen by 8 cameras at 1024² under 4
+directional lights with 2048² maps; its benchmark runs the recomputing
+backward, whose images and gradients are checked against the stored mode
+here, which is checked against the oracle).
 
 The oracle cannot render these frames whole in seconds, so it checks windows
 of them (its raster cut to a pixel window is the same computation on fewer
@@ -26,7 +30,7 @@ from parity_util import F64, assert_close
 
 pytestmark = pytest.mark.gpu
 
-CONFIGS = {"config2": scenes.config2, "config3": scenes.config3}
+CONFIGS = {"config2": scenes.config2, "config3": scenes.config3, "config5": scenes.config5}
 WIN = 32
 
 
@@ -42,22 +46,23 @@ def frame(request):
     from paper_2308_10896_b300 import dsm
     torch.cuda.set_device(0)
     sc = CONFIGS[request.param]()
+    cams = sc.get("cameras", [sc["camera"]])
     r = dsm.Renderer(sc)
-    image = r.forward()
+    images = [im.cpu().numpy() for im in r.forward_cameras(cams)]
     r.ctx.sync()
-    L = len(sc["lights"])
-    cam = sc["camera"]
-    W, H = int(cam["width"]), int(cam["height"])
-    d = {"sc": sc, "r": r, "dsm": dsm, "image": image.cpu().numpy(), "gbuf": [], "fmap": [], "ftilde": [], "mom": []}
-    for w in range(L + 1):
-        RW, RH = (sc["lights"][w]["res"],) * 2 if w < L else (W, H)
+    L, C = len(sc["lights"]), len(cams)
+    size = [(int(c["width"]), int(c["height"])) for c in cams]
+    d = {"sc": sc, "r": r, "dsm": dsm, "cams": cams, "images": images, "gbuf": [], "fmap": [], "ftilde": [],
+         "mom": []}
+    for w in range(L + C):
+        RW, RH = (sc["lights"][w]["res"],) * 2 if w < L else size[w - L]
         d["gbuf"].append(r.ctx.debug(dsm.DBG_GBUF, w, (RH, RW, 4)).cpu())
     for l, Lt in enumerate(sc["lights"]):
         R = Lt["res"]
         d["fmap"].append(r.ctx.debug(dsm.DBG_F, l, (R, R, 2)).cpu().numpy())
         d["ftilde"].append(r.ctx.debug(dsm.DBG_FTILDE, l, (R, R, 2)).cpu().numpy())
         d["mom"].append(r.ctx.debug(dsm.DBG_MOMENTS, l, (R, R, 2)).cpu().numpy())
-    d["color"] = r.ctx.debug(dsm.DBG_COLOR, 0, (H, W, 4)).cpu().numpy()
+    d["color"] = [r.ctx.debug(dsm.DBG_COLOR, c, (H, W, 4)).cpu().numpy() for c, (W, H) in enumerate(size)]
     tris = sc["tris"].astype(np.int64)
     V32 = sc["verts"].astype(np.float32)
     views = []
@@ -65,7 +70,7 @@ def frame(request):
         lp = torch.as_tensor(np.concatenate([Lt["pos"], Lt["dir"]]), dtype=F64)
         Q = O.light_matrix(Lt, lp[:3], lp[3:])
         views.append((Q, Q.detach().numpy().astype(np.float32)[:4], Lt["res"], Lt["res"]))
-    views.append((None, np.asarray(cam["clip"], np.float32), W, H))
+    views += [(None, np.asarray(c["clip"], np.float32), W, H) for c, (W, H) in zip(cams, size)]
     d["views"] = [(Q, M, RW, RH, O.setup_view(O.clip_pinned(M, V32), tris, RW, RH)) for Q, M, RW, RH in views]
     return d
 
@@ -114,21 +119,25 @@ def test_moment_filter_full_maps(frame):
         assert_close(frame["mom"][l], exp.numpy(), f"moments, light {l}")
 
 
-def test_camera_colour_in_windows(frame):
+@pytest.mark.parametrize("cam", range(8))
+def test_camera_colour_in_windows(frame, cam):
     sc = frame["sc"]
     L = len(sc["lights"])
+    if cam >= len(frame["cams"]):
+        pytest.skip("the scene has fewer cameras")
     tris_np = sc["tris"].astype(np.int64)
     verts = torch.as_tensor(sc["verts"], dtype=F64)
     vh = torch.cat([verts, torch.ones((verts.shape[0], 1), dtype=F64)], 1)
     lp = torch.as_tensor(np.stack([np.concatenate([l["pos"], l["dir"]]) for l in sc["lights"]]), dtype=F64)
     albedo = torch.as_tensor(sc["albedo"], dtype=F64)
     maps = [(frame["views"][l][0], torch.as_tensor(frame["mom"][l], dtype=F64)) for l in range(L)]
-    _, M, W, H, st = frame["views"][L]
+    _, M, W, H, st = frame["views"][L + cam]
     clipc = vh @ torch.as_tensor(M, dtype=F64).T
-    for win in _windows(W, H, 300):
+    colour = frame["color"][cam]
+    for win in _windows(W, H, 300 + cam):
         ras = O.raster(st, tris_np, window=win)
         jj, ii, rgb, vis = O.shade_pixels(sc, verts, lp, albedo, maps, clipc, ras["ids"])
-        got, exp = frame["color"][jj, ii, :3], rgb.detach().numpy()
+        got, exp = colour[jj, ii, :3], rgb.detach().numpy()
         # Pixels lit by every light (d <= mu, v = 1 exactly) take the stage
         # tolerance.  In a penumbra the lookup's own float32 position feeds a
         # visibility whose slope reaches 0.65 / sigma_min, so those pixels take
@@ -136,29 +145,63 @@ def test_camera_colour_in_windows(frame):
         lit = np.all(np.stack([v.detach().numpy() == 1.0 for v in vis]), 0)
         assert_close(got[lit], exp[lit], f"colour of lit pixels, window {win}")
         assert_close(got[~lit], exp[~lit], f"colour in penumbra, window {win}", atol=2e-3, rtol=1e-3)
-        assert (frame["color"][jj, ii, 3] == 1.0).all()
+        assert (colour[jj, ii, 3] == 1.0).all()
+
+
+def _targets(frame):
+    return [torch.as_tensor(im, device="cuda") * 0.9 for im in frame["images"]]
+
+
+def _loss_and_grads(dsm, r, cams, targets, albedo=None, imgs=None):
+    imgs = r.forward_cameras(cams, albedo=albedo, images=imgs)
+    total, gimgs = 0.0, []
+    for im, tg in zip(imgs, targets):
+        loss = torch.zeros(1, device="cuda")
+        g = torch.empty_like(im)
+        dsm.l2_loss_grad(im, tg, loss, g)
+        total += float(loss.item())
+        gimgs.append(g)
+    return total, gimgs, imgs
 
 
 def test_albedo_gradient_matches_exact_central_difference(frame):
-    sc, r, dsm = frame["sc"], frame["r"], frame["dsm"]
-    target = torch.as_tensor(frame["image"], device="cuda") * 0.9
-    loss = torch.zeros(1, device="cuda")
-    img = torch.empty_like(target)
-    gimg = torch.empty_like(target)
-
-    def L_of(alb):
-        r.forward(albedo=alb, image=img)
-        dsm.l2_loss_grad(img, target, loss, gimg)
-        return float(loss.item())
-
+    r, dsm, cams = frame["r"], frame["dsm"], frame["cams"]
+    targets = _targets(frame)
     alb0 = r.albedo.clone()
-    L_of(alb0)
-    _, _, dalb = r.backward(gimg)
+    _, gimgs, imgs = _loss_and_grads(dsm, r, cams, targets, alb0)
+    _, _, dalb = r.backward_cameras(gimgs)
     g = dalb.double().cpu()
     eps = torch.as_tensor(np.random.default_rng(7).normal(size=tuple(alb0.shape)), dtype=torch.float32,
                           device="cuda")
     h = 0.05
-    fd = (L_of((alb0 + h * eps).contiguous()) - L_of((alb0 - h * eps).contiguous())) / (2 * h)
+    lp = _loss_and_grads(dsm, r, cams, targets, (alb0 + h * eps).contiguous(), imgs)[0]
+    lm = _loss_and_grads(dsm, r, cams, targets, (alb0 - h * eps).contiguous(), imgs)[0]
+    fd = (lp - lm) / (2 * h)
     dd = float((g * eps.double().cpu()).sum())
     assert abs(fd - dd) <= 1e-3 * abs(dd) + 1e-9, f"central difference {fd} vs gradient {dd}"
-    r.forward(albedo=alb0, image=img)
+
+
+def test_recomputing_backward_matches_stored(frame):
+    """The benchmark's recompute-in-backward configuration gives the same
+    images and, up to the order of float atomics, the same gradients."""
+    dsm, sc, cams = frame["dsm"], frame["sc"], frame["cams"]
+    targets = _targets(frame)
+    out = {}
+    for mode in (0, 1):
+        s2 = dict(sc)
+        s2["params"] = dict(sc["params"], recompute_in_backward=mode)
+        r = dsm.Renderer(s2)
+        _, gimgs, imgs = _loss_and_grads(dsm, r, cams, targets)
+        dv, dl, da = r.backward_cameras(gimgs)
+        r.ctx.sync()
+        out[mode] = ([im.cpu() for im in imgs], dv.cpu().double(), dl.cpu().double(), da.cpu().double(),
+                     r.ctx.memory_bytes())
+        r.ctx.close()
+    for c in range(len(cams)):
+        assert torch.equal(out[0][0][c], out[1][0][c]), f"camera {c}: image differs"
+    for k, name in ((1, "verts"), (2, "light"), (3, "albedo")):
+        a, b = out[1][k].reshape(-1), out[0][k].reshape(-1)
+        rel = float((a - b).norm() / max(float(b.norm()), 1e-30))
+        assert rel <= 1e-4, f"dL/d{name}: rel {rel}"
+    if len(cams) + len(sc["lights"]) > 2:
+        assert out[1][4] < out[0][4]

@@ -587,3 +587,54 @@ def test_raster_window_matches_full_frame():
         assert np.array_equal(part["ids"][inside], full["ids"][inside])
         assert np.array_equal(part["zkey"][inside], full["zkey"][inside])
         assert (part["ids"][~inside] == 0).all()
+
+
+def test_adam_constant_gradient_closed_form():
+    """With a constant gradient g the bias-corrected moments are exactly g and
+    g^2 at every step, so each step moves p by lr g / (|g| + eps)."""
+    rng = np.random.default_rng(3)
+    p0 = rng.normal(size=50)
+    g = rng.normal(size=50)
+    p, m, v = p0, np.zeros(50), np.zeros(50)
+    for t in range(1, 8):
+        p, m, v = O.adam_step(p, g, m, v, t, lr=1e-2)
+        np.testing.assert_allclose(p, p0 - t * 1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-13)
+
+
+def test_adam_matches_unrolled_moment_sums():
+    """m_t and v_t equal the closed sums (1 - b) sum_k b^(t-k) g_k (resp. g_k^2),
+    and the parameters move by the sum of the per-step updates."""
+    rng = np.random.default_rng(4)
+    b1, b2, lr, eps = 0.8, 0.95, 3e-3, 1e-6
+    gs = rng.normal(size=(6, 10))
+    p, m, v = np.ones(10), np.zeros(10), np.zeros(10)
+    moved = np.zeros(10)
+    for t in range(1, 7):
+        p_prev = p
+        p, m, v = O.adam_step(p, gs[t - 1], m, v, t, lr, b1, b2, eps)
+        ms = (1 - b1) * sum(b1 ** (t - k) * gs[k - 1] for k in range(1, t + 1))
+        vs = (1 - b2) * sum(b2 ** (t - k) * gs[k - 1] ** 2 for k in range(1, t + 1))
+        np.testing.assert_allclose(m, ms, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(v, vs, rtol=1e-12, atol=1e-15)
+        step = lr * (ms / (1 - b1 ** t)) / (np.sqrt(vs / (1 - b2 ** t)) + eps)
+        np.testing.assert_allclose(p_prev - p, step, rtol=1e-9, atol=1e-15)
+        moved += step
+    np.testing.assert_allclose(1.0 - p, moved, rtol=1e-9, atol=1e-15)
+
+
+def test_multi_camera_loss_is_sum_of_single_camera_losses():
+    """Two cameras: the summed loss and its gradient equal the sum of the
+    single-camera results of render_and_grad."""
+    sc = scenes.tiny_scene(5, res=16, img=12)
+    cam2 = scenes.look_at_perspective((2.5, 2.0, -2.0), (0.0, 0.5, 0.0), 50.0, 10, 14)
+    cams = [sc["camera"], cam2]
+    rng = np.random.default_rng(8)
+    tg = [rng.uniform(0, 1, (c["height"], c["width"], 4)) for c in cams]
+    both = O.render_cameras_and_grad(sc, cams, tg)
+    singles = [O.render_and_grad(dict(sc, camera=c), t) for c, t in zip(cams, tg)]
+    assert abs(float(both["loss"]) - sum(float(s["loss"]) for s in singles)) <= 1e-12
+    for k in ("grad_verts", "grad_light", "grad_albedo"):
+        exp = sum(s[k] for s in singles)
+        assert torch.allclose(both[k], exp, rtol=1e-10, atol=1e-14), k
+    for img, s in zip(both["images"], singles):
+        assert torch.equal(img, s["image"].detach())
