@@ -317,6 +317,8 @@ def run_ours(args):
     # target: the same scene with vertices jittered (rendered once, before timing)
     verts_t = torch.as_tensor(scenes.jitter_vertices(sc, 0.01, 99 + rank), device=dev).contiguous()
     target = r.forward(verts=verts_t).clone()
+    # kernel shapes for this scene (timed outside the measured region)
+    tuning = r.autotune(reps=3)[0] if not args.no_autotune else r.ctx.get_tuning()
     loss = torch.zeros(1, device=dev)
     gimg = torch.empty_like(target)
     image = torch.empty_like(target)
@@ -421,7 +423,7 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(sec_max * 1e3 / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator)",
-        "config": workload_config(args.workload, sc, desc),
+        "config": dict(workload_config(args.workload, sc, desc), tuning=tuning),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "algorithmic_bytes_per_step": int(sb[dom]),
@@ -497,6 +499,10 @@ def run_batch(args):
     n = len(scs)
     # batched
     b = dsm.Batch(scs, targets)
+    if not args.no_autotune:
+        b.step()
+        b.autotune(reps=2)
+    tunings = b.tunings()
     for _ in range(args.warmup):
         b.step()
     b.stream.synchronize()
@@ -513,6 +519,8 @@ def run_batch(args):
     b.close()
     # one render per scene, in turn
     rs = [dsm.Renderer(sc) for sc in scs]
+    for r, t in zip(rs, tunings):   # the same kernel shapes as the batched form
+        r.ctx.set_tuning(**t)
     bufs = []
     for r, tgt in zip(rs, targets):
         img = torch.empty((r.H, r.W, 4), device=dev)
@@ -542,7 +550,12 @@ def run_batch(args):
         "dtype": "f32", "data": "synthetic (seeded generator)",
         "config": {"workload": "config4: 64 scenes, one SH-displaced icosphere of 1k-100k triangles each on a ground "
                                "quad, image 256-1024, shadow maps 512-2048, 1-3 directional lights",
-                   "scenes": n, "triangles_total": sum(tris), "triangles_min_max": [min(tris), max(tris)]},
+                   "scenes": n, "triangles_total": sum(tris), "triangles_min_max": [min(tris), max(tris)],
+                   "tunings": {"autotuned": not args.no_autotune,
+                               "light_tile_16": sum(t["light_tile"] == 16 for t in tunings),
+                               "camera_tile_16": sum(t["camera_tile"] == 16 for t in tunings),
+                               "filter_two_pass": sum(t["filter_shape"] == 1 for t in tunings),
+                               "big_tiles": sorted({t["big_tiles"] for t in tunings})}},
         "one_call_per_scene": {"value": round(n * 1e3 / serial_ms, 2), "unit": "scene-frames/s",
                                "ms_per_step": round(serial_ms, 4)},
         "speedup": round(serial_ms / batch_ms, 3),
@@ -579,6 +592,7 @@ def run_reconstruction(args):
         s2["params"] = dict(sc["params"], recompute_in_backward=mode)
         r = dsm.Renderer(s2)
         targets = [im.clone() for im in r.forward_cameras(cams, verts=tgt_verts)]
+        tuning = r.autotune(cams, reps=2)[0] if not args.no_autotune else r.ctx.get_tuning()
         imgs = [torch.empty_like(t) for t in targets]
         gimgs = [torch.empty_like(t) for t in targets]
         losses = torch.zeros(C, device=dev)
@@ -630,7 +644,7 @@ def run_reconstruction(args):
         for _ in range(args.steps):
             step()
             trace.append(float(losses.sum().item()))
-        res[mode] = {"ms_per_step": round(ms, 3), "library_device_bytes": int(r.ctx.memory_bytes()),
+        res[mode] = {"ms_per_step": round(ms, 3), "tuning": tuning, "library_device_bytes": int(r.ctx.memory_bytes()),
                      "device_used_growth_bytes": int(free0 - free1), "loss_first": trace[0],
                      "loss_last": trace[-1]}
         if mode == 1:
@@ -663,7 +677,8 @@ def run_reconstruction(args):
         "peak_device_memory": {"recompute": {k: rc[k] for k in ("library_device_bytes", "device_used_growth_bytes")},
                                "stored": {k: res[0][k] for k in ("library_device_bytes",
                                                                  "device_used_growth_bytes")}},
-        "stored_mode": {"ms_per_step": res[0]["ms_per_step"]},
+        "stored_mode": {"ms_per_step": res[0]["ms_per_step"], "tuning": res[0]["tuning"]},
+        "tuning": rc["tuning"],
         "loss": {"first_step": rc["loss_first"], "last_step": rc["loss_last"]},
         "stages": stages,
         "gpu_launches": int(launches_per_step * args.steps),
@@ -682,6 +697,7 @@ def main(argv=None):
                     choices=["config1", "config2", "config3", "config4", "config5"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel shapes")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for the CPU baseline")
     args = ap.parse_args(argv)
     if args.warmup < 3:

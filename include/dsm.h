@@ -166,6 +166,40 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
 /* Device memory held by ctx (its scratch and saved state), in bytes. */
 uint64_t dsm_memory_bytes(dsm_ctx* ctx);
 
+/* ---- Kernel shapes of a context.  The results do not depend on them (the
+ * raster is exact and order independent; the filter is the same sums), only
+ * the speed does.  Defaults: 32, 32, 16, 0. */
+typedef struct dsm_tuning {
+  int32_t light_tile;    /* raster tile side of the light views, pixels: 16 or 32                 */
+  int32_t camera_tile;   /* raster tile side of the camera views: 16 or 32                        */
+  int32_t big_tiles;     /* bin depth: a triangle whose bbox spans at least this many tiles is
+                            binned by the big-triangle kernel (tiles spread over many blocks) and
+                            its backward sums go to private copies; 2..4096                       */
+  int32_t filter_shape;  /* 0: both filter passes in one kernel on 32x32 output tiles (radius <=
+                            15, larger radii take two passes); 1: two 1-D passes                  */
+} dsm_tuning;
+
+/* Set / read the shapes used by the next calls on ctx.  DSM_ERR_INVALID_ARG
+ * for a value out of range. */
+dsm_status dsm_set_tuning(dsm_ctx* ctx, const dsm_tuning* tuning);
+dsm_status dsm_get_tuning(dsm_ctx* ctx, dsm_tuning* tuning);
+
+/* Autotuner: times forward + backward steps of the given frame (arguments as
+ * in dsm_render_cameras; the images double as dL/dimage of the timed
+ * backward, whose gradients go to context scratch) for candidate shapes and
+ * keeps the fastest on ctx.  Coordinate search from the current shapes: each
+ * knob in turn (light tile, camera tile, bin depth from {4, 16, 64}, filter
+ * shape) is set to each of its other values and kept when the step gets
+ * faster; each candidate runs one untimed step (sizing) and `reps` timed
+ * steps (1..100) with CUDA events on params->stream.  Synchronous.  best and
+ * best_ms (host, may be NULL) receive the chosen shapes and their time per
+ * step in milliseconds.  The state of the last forward is that of the last
+ * candidate: render again before a backward. */
+dsm_status dsm_autotune(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* lights,
+                        const float* light_params, int32_t n_lights,
+                        const dsm_camera* cameras, int32_t n_cameras, const dsm_params* params,
+                        float* const* images, int32_t reps, dsm_tuning* best, float* best_ms);
+
 /* One Adam step (Kingma & Ba 2015, Algorithm 1) in place, for optimising the
  * vertices (or any float parameters) with the gradients of the backward pass;
  * the paper optimises its scene parameters with Adam.  params, m, v: device,
@@ -276,6 +310,11 @@ dsm_status dsm_batch_step(dsm_batch* b, const dsm_batch_item* items, int32_t n, 
 dsm_status dsm_batch_sync(dsm_batch* b);
 /* Kernels one recorded step launches (counted while recording). */
 uint64_t   dsm_batch_kernels_per_step(dsm_batch* b);
+/* dsm_autotune of every scene on its own context and stream with its item's
+ * buffers (views serialised, as in a step).  Synchronous; the next
+ * dsm_batch_step runs eagerly and records a new graph. */
+dsm_status dsm_batch_autotune(dsm_batch* b, const dsm_batch_item* items, int32_t n, const dsm_params* params,
+                              int32_t reps);
 const char* dsm_batch_last_error(dsm_batch* b);
 
 /* Wait for the context's stream and report device-side errors (capacity

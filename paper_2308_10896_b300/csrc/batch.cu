@@ -137,7 +137,7 @@ dsm_status dsm_batch_step(dsm_batch* b, const dsm_batch_item* items, int32_t n, 
       return batch_fail(b, DSM_ERR_INVALID_ARG, "scene " + std::to_string(i) + ": null image/target/loss buffer");
   cudaStream_t origin = (cudaStream_t)params->stream;
   const uint64_t sig = step_signature(items, n, params);
-  if (b->exec && sig == b->sig) {
+  if (b->exec && b->sig != 0 && sig == b->sig) {
     if (cudaGraphLaunch(b->exec, origin) != cudaSuccess) return batch_fail(b, DSM_ERR_CUDA, "graph launch");
     return DSM_OK;
   }
@@ -174,6 +174,23 @@ dsm_status dsm_batch_step(dsm_batch* b, const dsm_batch_item* items, int32_t n, 
   }
   b->kernels_per_step = dsm_kernel_launches() - k0;
   b->sig = sig;
+  return DSM_OK;
+}
+
+dsm_status dsm_batch_autotune(dsm_batch* b, const dsm_batch_item* items, int32_t n, const dsm_params* params,
+                              int32_t reps) {
+  if (!b || !items || !params || n < 1 || n > b->n) return DSM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const dsm_batch_item& it = items[i];
+    dsm_params p = *params;
+    p.stream = b->ss[i];
+    float* img = it.image;
+    const dsm_status st = dsm_autotune(b->ctx[i], &it.mesh, it.lights, it.light_params, it.n_lights, &it.camera, 1,
+                                       &p, &img, reps, nullptr, nullptr);
+    if (st != DSM_OK) return batch_fail(b, st, std::string("scene ") + std::to_string(i) + ": " +
+                                                 dsm_last_error(b->ctx[i]));
+  }
+  b->sig = 0;   // the shapes changed: the next step records a new graph
   return DSM_OK;
 }
 

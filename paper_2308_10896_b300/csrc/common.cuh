@@ -9,8 +9,9 @@ constexpr int kSubpix = 256;          // 8 sub-pixel bits: 24.8 fixed point
 constexpr int kGuard = 1 << 28;       // |snapped coordinate| limit; beyond it a triangle is culled
 constexpr float kWMin = 1e-6f;        // clip w below this culls the triangle
 constexpr int kMaxViews = DSM_MAX_LIGHTS + DSM_MAX_CAMERAS;   // light views, then camera views
-constexpr int kTile = 32;             // raster tile side in pixels
-constexpr int kTileLog2 = 5;
+// Raster tile side 2^tile_log2 pixels: 16 or 32 per view (chosen by the
+// tuning of the context; 32 by default).
+constexpr int kTileLog2Min = 4, kTileLog2Max = 5, kTileLog2Default = 5;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Snapped vertex of one view: 24.8 fixed-point screen position, ndc depth,
@@ -56,11 +57,13 @@ struct DevStatus {
 };
 
 // Contention control for gradient scatters.  A triangle whose pixel bbox spans
-// at least kBigTiles raster tiles is "big": its per-triangle sums go to
+// at least big_tiles raster tiles (a binning parameter of the view, default
+// kBigTilesDefault) is "big": it is binned by a kernel that spreads its tiles
+// over many blocks, and in the backward its per-triangle sums go to
 // kBigSlots private copies (spread over L2) instead of straight onto its three
 // vertices, and a resolve kernel adds the copies up.  Block-level reductions
 // of the light and albedo gradients likewise go to kRedSlots copies.
-constexpr int kBigTiles = 16;
+constexpr int kBigTilesDefault = 16;
 constexpr int kMaxBig = 64;
 constexpr int kBigSlots = 64;
 constexpr int kBigStrideSm = 32;      // floats per slot copy (15 used), one 128-byte line each

@@ -54,6 +54,7 @@ struct ViewBufs {
   Buf aa_list, aa_ctr, hflag;   // antialiasing work list, its counter, per-pixel "listed" flag
   Buf color, gcolor, pgrad;     // camera views: colour before the final antialiasing, its adjoint, pixel gradients
   int list_cap = 0;
+  BinShape bs{kTileLog2Default, kBigTilesDefault};
   AAWork aa_work() { return AAWork{aa_list.as<int>(), aa_ctr.as<int>()}; }
 };
 
@@ -84,6 +85,8 @@ struct dsm_ctx {
   int L = 0, C = 0;
   dsm_camera cams[DSM_MAX_CAMERAS]{};
   dsm_params params{};
+  // raster tile sides, big-triangle threshold and filter shape (dsm_autotune)
+  dsm_tuning tuning{1 << kTileLog2Default, 1 << kTileLog2Default, kBigTilesDefault, 0};
   // recompute_in_backward: the views share two buffer sets (one for the
   // lights, one for the cameras) and the backward rebuilds what it reads
   bool recompute = false;
@@ -376,8 +379,12 @@ static dsm_status check_args(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light
 static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, int T, bool is_light) {
   v.W = W;
   v.H = H;
-  v.tilesX = (W + kTile - 1) / kTile;
-  v.tilesY = (H + kTile - 1) / kTile;
+  const int side = is_light ? ctx->tuning.light_tile : ctx->tuning.camera_tile;
+  v.bs.tile_log2 = side == 16 ? 4 : 5;
+  v.bs.big_tiles = ctx->tuning.big_tiles;
+  const int tile = 1 << v.bs.tile_log2;
+  v.tilesX = (W + tile - 1) / tile;
+  v.tilesY = (H + tile - 1) / tile;
   const size_t tiles = (size_t)v.tilesX * v.tilesY;
   const size_t Vn = std::max(V, 1), Tn = std::max(T, 1);
   DSM_CHECK(v.clip.ensure(Vn * sizeof(float4)));
@@ -449,6 +456,7 @@ dsm_status prepare_light(dsm_ctx* ctx, int l) {
   lb.res = R;
   make_filter_args(ctx->lights[l].sigma, ctx->lights[l].radius, ctx->params.filter_kind, ctx->params.filter_boundary,
                    &lb.fa);
+  lb.fa.shape = ctx->tuning.filter_shape;
   return DSM_OK;
 }
 
@@ -493,7 +501,7 @@ void bin_count_view(dsm_ctx* ctx, int w, cudaStream_t st) {
   ViewBufs& v = vbuf(ctx, w);
   DevStatus* ds = ctx->status.as<DevStatus>();
   StageTimer t(ctx, ST_SETUP, st);
-  launch_bin_count(v.setup.as<TriSetup>(), ctx->mesh.n_tris, v.tilesX, v.count.as<int>(), ds, w,
+  launch_bin_count(v.setup.as<TriSetup>(), ctx->mesh.n_tris, v.tilesX, v.bs, v.count.as<int>(), ds, w,
                    v.big_index.as<int>(), v.big_tri.as<int>(), st);
   launch_scan(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), ds, w, st);
 }
@@ -505,13 +513,13 @@ void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
   DevStatus* ds = ctx->status.as<DevStatus>();
   {
     StageTimer t(ctx, ST_BIN_FILL, st);
-    launch_bin_fill(v.setup.as<TriSetup>(), ctx->mesh.n_tris, v.tilesX, v.count.as<int>(), v.offset.as<int>(),
+    launch_bin_fill(v.setup.as<TriSetup>(), ctx->mesh.n_tris, v.tilesX, v.bs, v.count.as<int>(), v.offset.as<int>(),
                     v.list.as<int>(), v.list_cap, ds, w, v.big_index.as<int>(), v.big_tri.as<int>(), st);
   }
   StageTimer t(ctx, ST_RASTER, st);
-  launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY, v.W,
-                v.H, v.clip.as<float4>(), ctx->mesh.tris, v.gbuf.as<float4>(), light ? v.depth.as<float>() : nullptr,
-                light ? lwork(ctx, w).fmap.as<float2>() : nullptr, st);
+  launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,
+                v.bs.tile_log2, v.W, v.H, v.clip.as<float4>(), ctx->mesh.tris, v.gbuf.as<float4>(),
+                light ? v.depth.as<float>() : nullptr, light ? lwork(ctx, w).fmap.as<float2>() : nullptr, st);
 }
 
 // Alg. 1 after the raster: antialiasing of f, f^2 at the listed texels, then
@@ -704,6 +712,7 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
 
   // ---- buffers (all growth happens here, before any launch of this frame)
   uint64_t sig = mix(mix(mix(mix(mix(1, V), T), L), C), ctx->recompute ? 1 : 0);
+  sig = mix(mix(mix(sig, ctx->tuning.light_tile), ctx->tuning.camera_tile), ctx->tuning.big_tiles);
   for (int c = 0; c < C; ++c) sig = mix(mix(sig, cams[c].width), cams[c].height);
   for (int l = 0; l < L; ++l) sig = mix(mix(sig, lights[l].res), lights[l].type);
   const bool sizing = ctx->sized_sig != sig;
@@ -960,6 +969,96 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   if (!ctx) return DSM_ERR_INVALID_ARG;
   if (ctx->have_fwd && ctx->C != 1) return fail(ctx, DSM_ERR_INVALID_ARG, "last forward had several cameras");
   return dsm_render_cameras_backward(ctx, &dL_dimage, dL_dverts, dL_dlight, dL_dalbedo);
+}
+
+static bool tuning_ok(const dsm_tuning& t) {
+  return (t.light_tile == 16 || t.light_tile == 32) && (t.camera_tile == 16 || t.camera_tile == 32) &&
+         t.big_tiles >= 2 && t.big_tiles <= 4096 && (t.filter_shape == 0 || t.filter_shape == 1);
+}
+
+dsm_status dsm_set_tuning(dsm_ctx* ctx, const dsm_tuning* tuning) {
+  if (!ctx || !tuning) return DSM_ERR_INVALID_ARG;
+  if (!tuning_ok(*tuning)) return fail(ctx, DSM_ERR_INVALID_ARG, "tuning value out of range");
+  ctx->tuning = *tuning;
+  ctx->have_fwd = false;
+  return DSM_OK;
+}
+
+dsm_status dsm_get_tuning(dsm_ctx* ctx, dsm_tuning* tuning) {
+  if (!ctx || !tuning) return DSM_ERR_INVALID_ARG;
+  *tuning = ctx->tuning;
+  return DSM_OK;
+}
+
+dsm_status dsm_autotune(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* lights, const float* light_params,
+                        int32_t n_lights, const dsm_camera* cams, int32_t n_cams, const dsm_params* params,
+                        float* const* images, int32_t reps, dsm_tuning* best, float* best_ms) {
+  if (!ctx) return DSM_ERR_INVALID_ARG;
+  if (reps < 1 || reps > 100) return fail(ctx, DSM_ERR_INVALID_ARG, "reps out of range");
+  dsm_status s = check_args(ctx, mesh, lights, light_params, n_lights, cams, n_cams, params, images);
+  if (s != DSM_OK) return s;
+  cudaStream_t st = (cudaStream_t)params->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  DSM_CHECK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(ctx, DSM_ERR_CUDA, "event");
+  }
+  const float* const* gimg = const_cast<const float* const*>(images);
+  auto step = [&]() -> dsm_status {
+    dsm_status r = dsm_render_cameras(ctx, mesh, lights, light_params, n_lights, cams, n_cams, params, images);
+    if (r == DSM_OK) r = dsm_render_cameras_backward(ctx, gimg, nullptr, nullptr, nullptr);
+    return r;
+  };
+  // time per step of shapes t (one untimed step first: it sizes the lists)
+  auto measure = [&](const dsm_tuning& t, float* ms) -> dsm_status {
+    ctx->tuning = t;
+    dsm_status r = step();
+    if (r == DSM_OK) r = dsm_sync(ctx);
+    if (r != DSM_OK) return r;
+    if (cudaEventRecord(e0, st) != cudaSuccess) return fail(ctx, DSM_ERR_CUDA, "event record");
+    for (int k = 0; k < reps && r == DSM_OK; ++k) r = step();
+    if (r != DSM_OK) return r;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+      return fail(ctx, DSM_ERR_CUDA, "event wait");
+    r = dsm_sync(ctx);
+    if (r != DSM_OK) return r;
+    float total = 0.f;
+    if (cudaEventElapsedTime(&total, e0, e1) != cudaSuccess) return fail(ctx, DSM_ERR_CUDA, "event time");
+    *ms = total / reps;
+    return DSM_OK;
+  };
+  dsm_tuning cur = ctx->tuning;
+  float cur_ms = 0.f;
+  s = measure(cur, &cur_ms);
+  const int32_t tiles[2] = {16, 32}, bins[3] = {4, 16, 64}, shapes[2] = {0, 1};
+  for (int knob = 0; knob < 4 && s == DSM_OK; ++knob) {
+    const int32_t* vals = knob < 2 ? tiles : (knob == 2 ? bins : shapes);
+    const int nv = knob == 2 ? 3 : 2;
+    const dsm_tuning base = cur;
+    for (int k = 0; k < nv && s == DSM_OK; ++k) {
+      dsm_tuning cand = base;
+      int32_t* field = knob == 0 ? &cand.light_tile
+                     : knob == 1 ? &cand.camera_tile
+                     : knob == 2 ? &cand.big_tiles : &cand.filter_shape;
+      if (*field == vals[k]) continue;
+      *field = vals[k];
+      float ms = 0.f;
+      s = measure(cand, &ms);
+      if (s == DSM_OK && ms < 0.98f * cur_ms) {
+        cur = cand;
+        cur_ms = ms;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tuning = cur;
+  ctx->have_fwd = false;
+  if (s != DSM_OK) return s;
+  if (best) *best = cur;
+  if (best_ms) *best_ms = cur_ms;
+  return DSM_OK;
 }
 
 dsm_status dsm_l2_loss_grad(const float* image, const float* target, int64_t n, float* loss, float* dL_dimage,

@@ -12,6 +12,7 @@ void make_filter_args(double sigma, int radius, int kind, int boundary, FilterAr
   if (r > 32) r = 32;
   fa->r = r;
   fa->boundary = boundary;
+  fa->shape = 0;
   double w[65], s = 0.0;
   for (int k = -r; k <= r; ++k) {
     w[k + r] = (kind == 1) ? 1.0 : std::exp(-(double)k * k / (2.0 * sigma * sigma));
@@ -280,7 +281,7 @@ void launch_compose(const float2* fmap, const uint8_t* hflag, const float2* patc
 void launch_filter(const float2* in, float2* tmp, float2* out, int R, const FilterArgs& fa, cudaStream_t st,
                    const uint8_t* hflag, const float2* patch) {
   const FilterExtras ex{hflag, patch, nullptr, nullptr};
-  if (launch_tiled_r<1>(false, in, out, R, fa, ex, st)) return;
+  if (fa.shape == 0 && launch_tiled_r<1>(false, in, out, R, fa, ex, st)) return;
   dim3 b(32, 8), g((R + 31) / 32, (R + 7) / 8);
   if (hflag) {
     // the substituted input is composed into `out` first (the passes read it back)
@@ -298,7 +299,7 @@ void launch_filter(const float2* in, float2* tmp, float2* out, int R, const Filt
 void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, const FilterArgs& fa,
                            cudaStream_t st, const float2* fmap, float* gf) {
   const FilterExtras ex{nullptr, nullptr, fmap, gf};
-  if (launch_tiled_r<1>(true, gout, gin, R, fa, ex, st)) return;
+  if (fa.shape == 0 && launch_tiled_r<1>(true, gout, gin, R, fa, ex, st)) return;
   dim3 b(32, 8), g((R + 31) / 32, (R + 7) / 8);
   count_launches(1);
   filter_pass_kernel<true, true><<<g, b, 0, st>>>(gout, tmp, R, fa);

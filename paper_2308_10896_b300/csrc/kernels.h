@@ -36,6 +36,14 @@ struct FilterArgs {
   float fold[33];          // fold[i] = sum of w over taps that leave the map by more than i texels
   int r;
   int boundary;            // 0 clamp, 1 zero
+  int shape;               // 0 one fused tile kernel (radius <= 15, else two passes), 1 two 1-D passes
+};
+
+// Binning and raster shape of one view: tile side 2^tile_log2 pixels, and the
+// tile count from which a triangle takes the big-triangle binning.
+struct BinShape {
+  int tile_log2;
+  int big_tiles;
 };
 
 struct ShadeArgs {
@@ -73,7 +81,7 @@ struct VertGradPtrs {
   const float4* gclip[kMaxViews];   // per view (lights, then cameras); lights: z = dL/d vertex depth
 };
 
-// Big-triangle bookkeeping of one view (see kBigTiles).
+// Big-triangle bookkeeping of one view (see kBigTilesDefault).
 struct BigArgs {
   const int* index;          // per triangle: big index or -1
   const int* tri;            // per big index: triangle
@@ -116,19 +124,19 @@ struct ViewSetupArgs {
 void launch_setup_all(const float* verts, int V, const int* tris, int T, const int* adj, const float* viewM,
                       const ViewSetupArgs& a, DevStatus* status, cudaStream_t st);
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, cudaStream_t st);
-void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, int view,
-                      int* big_index, int* big_tri, cudaStream_t st);
+void launch_bin_count(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, DevStatus* status,
+                      int view, int* big_index, int* big_tri, cudaStream_t st);
 // Segment of every tile in the view's triangle list (begin, end) from the
 // per-tile counts; clears the counts for the fill pass.
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st);
-void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
-                     int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
+void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, const int* offset,
+                     int* list, int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
                      cudaStream_t st);
 // Light views (fmap != NULL) also write the shadow-map depth sample (f, f^2)
 // of every texel, f interpolated from the per-vertex light depths.
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
-                   int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth, float2* fmap,
-                   cudaStream_t st);
+                   int tile_log2, int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth,
+                   float2* fmap, cudaStream_t st);
 
 // shadow-map interpolation and antialiasing
 // Antialiasing (detection + list passes, see aa.cu).

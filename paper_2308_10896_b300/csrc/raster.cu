@@ -289,9 +289,11 @@ __global__ void silhouette_all_kernel(const int* __restrict__ adj, int T, ViewSe
 // warp pool their tile ranges and the lanes stride over the pooled pairs, so a
 // triangle spanning thousands of tiles is spread over 32 lanes.
 template <bool kFill>
-__global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX, int* __restrict__ counter,
-                           const int* __restrict__ offset, int* __restrict__ list, int capacity,
-                           DevStatus* status, int view, int* __restrict__ big_index, int* __restrict__ big_tri) {
+__global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX, BinShape bs,
+                           int* __restrict__ counter, const int* __restrict__ offset, int* __restrict__ list,
+                           int capacity, DevStatus* status, int view, int* __restrict__ big_index,
+                           int* __restrict__ big_tri) {
+  const int tl = bs.tile_log2;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int lane = threadIdx.x & 31;
   int n = 0, tx0 = 0, ty0 = 0, ntx = 1;
@@ -300,14 +302,14 @@ __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX
     if (flags & 16) {
       int ib = setup[t].ibox, jb = setup[t].jbox;
       int i0 = ib & 0xffff, i1 = (unsigned)ib >> 16, j0 = jb & 0xffff, j1 = (unsigned)jb >> 16;
-      tx0 = i0 >> kTileLog2; ty0 = j0 >> kTileLog2;
-      ntx = (i1 >> kTileLog2) - tx0 + 1;
-      n = ntx * ((j1 >> kTileLog2) - ty0 + 1);
+      tx0 = i0 >> tl; ty0 = j0 >> tl;
+      ntx = (i1 >> tl) - tx0 + 1;
+      n = ntx * ((j1 >> tl) - ty0 + 1);
     }
   }
   if (!kFill && t < T) {
     int b = -1;
-    if (n >= kBigTiles) {
+    if (n >= bs.big_tiles) {
       b = atomicAdd(&status->big_count[view], 1);
       if (b < kMaxBig) big_tri[b] = t;
       else b = -1;
@@ -315,7 +317,7 @@ __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX
     big_index[t] = b;
   }
   // big triangles are binned by bin_big_kernel, spread over the whole grid
-  if (t < T && n >= kBigTiles && big_index[t] >= 0) n = 0;
+  if (t < T && n >= bs.big_tiles && big_index[t] >= 0) n = 0;
   int incl = n;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -364,9 +366,10 @@ __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX
 
 // A tile can hold a covered pixel centre of the triangle only if no edge
 // function is negative at all four corner pixel centres of the tile.
-__device__ __forceinline__ bool tile_may_cover(const TriSetup& r, int tx, int ty) {
-  const long long x0 = (long long)(tx * kTile) * kSubpix + 128, x1 = x0 + (long long)(kTile - 1) * kSubpix;
-  const long long y0 = (long long)(ty * kTile) * kSubpix + 128, y1 = y0 + (long long)(kTile - 1) * kSubpix;
+__device__ __forceinline__ bool tile_may_cover(const TriSetup& r, int tx, int ty, int tl) {
+  const int tile = 1 << tl;
+  const long long x0 = (long long)(tx << tl) * kSubpix + 128, x1 = x0 + (long long)(tile - 1) * kSubpix;
+  const long long y0 = (long long)(ty << tl) * kSubpix + 128, y1 = y0 + (long long)(tile - 1) * kSubpix;
   const int sg = (r.flags & 8) ? -1 : 1;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
@@ -385,7 +388,7 @@ __device__ __forceinline__ bool tile_may_cover(const TriSetup& r, int tx, int ty
 constexpr int kBigGridX = 64, kBigGridY = 2;
 template <bool kFill>
 __global__ void bin_big_kernel(const TriSetup* __restrict__ setup, const int* __restrict__ big_tri,
-                               const DevStatus* __restrict__ status, int view, int tilesX,
+                               const DevStatus* __restrict__ status, int view, int tilesX, int tl,
                                int* __restrict__ counter, const int* __restrict__ offset, int* __restrict__ list,
                                int capacity, DevStatus* wstatus) {
   const int nb = min(status->big_count[view], kMaxBig);
@@ -393,12 +396,12 @@ __global__ void bin_big_kernel(const TriSetup* __restrict__ setup, const int* __
     const int t = big_tri[b];
     const TriSetup r = setup[t];
     const int i0 = r.ibox & 0xffff, i1 = (unsigned)r.ibox >> 16, j0 = r.jbox & 0xffff, j1 = (unsigned)r.jbox >> 16;
-    const int tx0 = i0 >> kTileLog2, ty0 = j0 >> kTileLog2;
-    const int ntx = (i1 >> kTileLog2) - tx0 + 1, nty = (j1 >> kTileLog2) - ty0 + 1;
+    const int tx0 = i0 >> tl, ty0 = j0 >> tl;
+    const int ntx = (i1 >> tl) - tx0 + 1, nty = (j1 >> tl) - ty0 + 1;
     const int n = ntx * nty;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
       const int tx = tx0 + q % ntx, ty = ty0 + q / ntx;
-      if (!tile_may_cover(r, tx, ty)) continue;
+      if (!tile_may_cover(r, tx, ty, tl)) continue;
       const int tile = ty * tilesX + tx;
       if (!kFill) {
         atomicAdd(&counter[tile], 1);
@@ -510,7 +513,7 @@ __device__ __forceinline__ uint64_t cover_key(const int* w, int x, int y) {
   return depth_key(z, w[kRecTri]);
 }
 
-// One 256-thread CTA per 32x32 tile.  The tile's triangle list is read 256
+// One 256-thread CTA per tile of kTile x kTile pixels (kTile = 2^kTL, 16 or 32).  The tile's triangle list is read 256
 // records at a time.  Every record contributes its bbox-in-tile pixels as work
 // items; a block prefix sum turns them into one flat list that all threads
 // stride over (balanced whatever the triangle sizes), and each covered pixel
@@ -523,13 +526,16 @@ __device__ __forceinline__ uint64_t cover_key(const int* w, int x, int y) {
 // perspective-correct b0, b1, depth key.
 constexpr int kChunk = 1024;
 
+template <int kTL>
 __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restrict__ setup,
                                                      const int* __restrict__ offset,
                                                      const int* __restrict__ list, int capacity, int tilesX,
                                                      int W, int H, const float4* __restrict__ clip,
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf,
                                                      const float* __restrict__ depth, float2* __restrict__ fmap) {
+  constexpr int kTile = 1 << kTL;
   constexpr int kPix = kTile * kTile;
+  static_assert(kTile <= 32, "tile-local coordinates are packed in 5 bits");
   __shared__ int sq[256 * kRecStride];
   __shared__ unsigned long long sbest[kPix];
   __shared__ int spre[257];          // exclusive prefix of the work items per record
@@ -632,7 +638,7 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
     }
   }
   for (int px = tid; px < kPix; px += 256) {
-    const int i = ti0 + (px & (kTile - 1)), j = tj0 + (px >> kTileLog2);
+    const int i = ti0 + (px & (kTile - 1)), j = tj0 + (px >> kTL);
     const uint64_t best = sbest[px];
     if (i >= W || j >= H) continue;
     float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -675,15 +681,16 @@ void launch_setup_all(const float* verts, int V, const int* tris, int T, const i
   }
 }
 
-void launch_bin_count(const TriSetup* setup, int T, int tilesX, int* counter, DevStatus* status, int view,
-                      int* big_index, int* big_tri, cudaStream_t st) {
+void launch_bin_count(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, DevStatus* status,
+                      int view, int* big_index, int* big_tri, cudaStream_t st) {
   if (T == 0) return;
   count_launches(1);
-  bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, nullptr, nullptr, 0, status, view,
-                                                     big_index, big_tri);
+  bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, bs, counter, nullptr, nullptr, 0, status,
+                                                     view, big_index, big_tri);
   count_launches(1);
-  bin_big_kernel<false><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter,
-                                                                     nullptr, nullptr, 0, status);
+  bin_big_kernel<false><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX,
+                                                                     bs.tile_log2, counter, nullptr, nullptr, 0,
+                                                                     status);
 }
 
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st) {
@@ -691,24 +698,29 @@ void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cu
   alloc_kernel<<<(n + 255) / 256, 256, 0, st>>>(count, n, offset, status, view);
 }
 
-void launch_bin_fill(const TriSetup* setup, int T, int tilesX, int* counter, const int* offset, int* list,
-                     int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
+void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, const int* offset,
+                     int* list, int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
                      cudaStream_t st) {
   if (T == 0) return;
   count_launches(1);
-  bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, counter, offset, list, capacity, status, view,
-                                                    const_cast<int*>(big_index), const_cast<int*>(big_tri));
+  bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, bs, counter, offset, list, capacity, status,
+                                                    view, const_cast<int*>(big_index), const_cast<int*>(big_tri));
   count_launches(1);
-  bin_big_kernel<true><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX, counter,
-                                                                    offset, list, capacity, status);
+  bin_big_kernel<true><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX,
+                                                                    bs.tile_log2, counter, offset, list, capacity,
+                                                                    status);
 }
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
-                   int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth, float2* fmap,
-                   cudaStream_t st) {
+                   int tile_log2, int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth,
+                   float2* fmap, cudaStream_t st) {
   count_launches(1);
-  raster_kernel<<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf, depth,
-                                                 fmap);
+  if (tile_log2 == 4)
+    raster_kernel<4><<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf,
+                                                      depth, fmap);
+  else
+    raster_kernel<5><<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf,
+                                                      depth, fmap);
 }
 
 }  // namespace dsm

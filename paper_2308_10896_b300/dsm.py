@@ -30,7 +30,8 @@ EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_
             "dsm_kernel_launches", "dsm_filter_moments_noalloc", "dsm_filter_moments_adjoint",
             "dsm_batch_create", "dsm_batch_destroy", "dsm_batch_context", "dsm_batch_step", "dsm_batch_sync",
             "dsm_batch_kernels_per_step", "dsm_batch_last_error", "dsm_render_cameras",
-            "dsm_render_cameras_backward", "dsm_memory_bytes", "dsm_adam_step"]
+            "dsm_render_cameras_backward", "dsm_memory_bytes", "dsm_adam_step", "dsm_set_tuning",
+            "dsm_get_tuning", "dsm_autotune", "dsm_batch_autotune"]
 
 
 class DsmError(RuntimeError):
@@ -60,6 +61,14 @@ class Params(ctypes.Structure):
     _fields_ = [("min_variance", ctypes.c_float), ("filter_kind", ctypes.c_int32),
                 ("filter_boundary", ctypes.c_int32), ("aa_shadow", ctypes.c_int32), ("aa_final", ctypes.c_int32),
                 ("recompute_in_backward", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("light_tile", ctypes.c_int32), ("camera_tile", ctypes.c_int32), ("big_tiles", ctypes.c_int32),
+                ("filter_shape", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class BatchItem(ctypes.Structure):
@@ -111,6 +120,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                 ctypes.POINTER(Params), ctypes.POINTER(P)], I32),
         "dsm_render_cameras_backward": ([P, ctypes.POINTER(P), P, P, P], I32),
         "dsm_memory_bytes": ([P], ctypes.c_uint64),
+        "dsm_set_tuning": ([P, ctypes.POINTER(Tuning)], I32),
+        "dsm_get_tuning": ([P, ctypes.POINTER(Tuning)], I32),
+        "dsm_autotune": ([P, ctypes.POINTER(Mesh), ctypes.POINTER(Light), P, I32, ctypes.POINTER(Camera), I32,
+                          ctypes.POINTER(Params), ctypes.POINTER(P), I32, ctypes.POINTER(Tuning),
+                          ctypes.POINTER(ctypes.c_float)], I32),
+        "dsm_batch_autotune": ([P, P, I32, P, I32], I32),
         "dsm_adam_step": ([P, P, P, P, I64, I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P],
                           I32),
     }
@@ -225,6 +240,25 @@ class Context:
     def memory_bytes(self) -> int:
         """Device memory held by this context (scratch and saved state)."""
         return int(self.lib.dsm_memory_bytes(self.h))
+
+    def set_tuning(self, light_tile=32, camera_tile=32, big_tiles=16, filter_shape=0):
+        t = Tuning(light_tile, camera_tile, big_tiles, filter_shape)
+        self._check(self.lib.dsm_set_tuning(self.h, ctypes.byref(t)), self.h)
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        self._check(self.lib.dsm_get_tuning(self.h, ctypes.byref(t)), self.h)
+        return t.as_dict()
+
+    def autotune(self, mesh: Mesh, lights, light_params, cameras, params: Params, images, reps: int = 3):
+        arr = (Light * max(1, len(lights)))(*lights)
+        cams = (Camera * len(cameras))(*cameras)
+        ptrs = (ctypes.c_void_p * len(images))(*[_ptr(im) for im in images])
+        best, ms = Tuning(), ctypes.c_float()
+        self._check(self.lib.dsm_autotune(self.h, ctypes.byref(mesh), arr, _ptr(light_params), len(lights), cams,
+                                          len(cameras), ctypes.byref(params), ptrs, int(reps), ctypes.byref(best),
+                                          ctypes.byref(ms)), self.h)
+        return best.as_dict(), float(ms.value)
 
     def filter_moments(self, inp: torch.Tensor, out: torch.Tensor, sigma: float, radius: int = 0, kind: int = 0,
                        boundary: int = 0, stream=None):
@@ -349,6 +383,16 @@ class Renderer:
                                 [camera_struct(c) for c in cameras], params_struct(self.params_dict, stream), images)
         return images
 
+    def autotune(self, cameras: list | None = None, reps: int = 3, stream=None):
+        """Choose the kernel shapes of this renderer's context by timing
+        forward + backward steps of its scene (dsm_autotune); returns the
+        chosen shapes and the time per step in ms."""
+        cams = cameras if cameras is not None else [self.camera_dict]
+        images = [torch.empty((int(c["height"]), int(c["width"]), 4), dtype=torch.float32, device=self.device)
+                  for c in cams]
+        return self.ctx.autotune(self.mesh_struct(), self.lights, self.light_params, [camera_struct(c) for c in cams],
+                                 params_struct(self.params_dict, stream), images, reps)
+
     def backward_cameras(self, dL_dimages: list, dverts=None, dlight=None, dalbedo=None):
         """Backward of the last forward_cameras for the loss summed over the cameras."""
         dverts, dlight, dalbedo = self._grads(dverts, dlight, dalbedo)
@@ -443,6 +487,21 @@ class Batch:
 
     def kernels_per_step(self) -> int:
         return int(self.lib.dsm_batch_kernels_per_step(self.h))
+
+    def autotune(self, reps: int = 2):
+        """dsm_autotune of every scene's context (synchronous)."""
+        st = self.lib.dsm_batch_autotune(self.h, ctypes.cast(self.items, ctypes.c_void_p), len(self.scenes),
+                                         ctypes.byref(self.params), int(reps))
+        if st != DSM_OK:
+            raise DsmError(st, self.lib.dsm_batch_last_error(self.h).decode())
+
+    def tunings(self) -> list:
+        out = []
+        for i in range(len(self.scenes)):
+            t = Tuning()
+            self.lib.dsm_get_tuning(self.lib.dsm_batch_context(self.h, i), ctypes.byref(t))
+            out.append(t.as_dict())
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -69,3 +69,30 @@ def test_batch_matches_single_renders_and_follows_device_data():
                 assert _rel(g, o) <= 1e-4, f"step {step} scene {k}: dL/d{name} rel {_rel(g, o)}"
     assert b.kernels_per_step() > 0
     b.close()
+
+
+def test_batch_autotune_keeps_results():
+    """Per-scene autotuning, then a recorded step: images as single renders
+    with the default shapes, gradients up to atomic order."""
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    scs = _scenes()[:3]
+    targets = []
+    for k, sc in enumerate(scs):
+        r = dsm.Renderer(sc)
+        jit = torch.as_tensor(scenes.jitter_vertices(sc, 0.01, 70 + k), device="cuda")
+        targets.append(r.forward(verts=jit).clone().cpu().numpy())
+    b = dsm.Batch(scs, targets)
+    b.step()
+    b.autotune(reps=1)
+    assert len(b.tunings()) == len(scs)
+    for _ in range(2):
+        b.step()
+    b.stream.synchronize()
+    b.sync()
+    for k, (sc, d) in enumerate(zip(scs, b.scenes)):
+        tgt = torch.as_tensor(targets[k], device="cuda")
+        img, loss, dv, dl, da = _single(dsm, sc, d["verts"].clone(), tgt)
+        assert torch.equal(d["image"].cpu(), img), f"scene {k}: image differs"
+        assert _rel(d["dverts"].cpu(), dv) <= 1e-4
+    b.close()
