@@ -310,9 +310,12 @@ dsm_status dsm_batch_step(dsm_batch* b, const dsm_batch_item* items, int32_t n, 
 dsm_status dsm_batch_sync(dsm_batch* b);
 /* Kernels one recorded step launches (counted while recording). */
 uint64_t   dsm_batch_kernels_per_step(dsm_batch* b);
-/* dsm_autotune of every scene on its own context and stream with its item's
- * buffers (views serialised, as in a step).  Synchronous; the next
- * dsm_batch_step runs eagerly and records a new graph. */
+/* Autotuner of the batch: the same coordinate search as dsm_autotune over
+ * shapes shared by every scene, each candidate timed as whole batched steps
+ * (an eager step that records the graph and one replay untimed, then `reps`
+ * timed replays on params->stream), since the scenes overlap one another in a
+ * step.  Synchronous; leaves the fastest shapes on every scene's context and
+ * its graph recorded. */
 dsm_status dsm_batch_autotune(dsm_batch* b, const dsm_batch_item* items, int32_t n, const dsm_params* params,
                               int32_t reps);
 const char* dsm_batch_last_error(dsm_batch* b);

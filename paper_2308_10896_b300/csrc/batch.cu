@@ -6,6 +6,7 @@
 // and then records the same step into one CUDA graph; later steps with the
 // same buffers replay the graph with a single launch.
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 #include "dsm.h"
@@ -13,6 +14,8 @@
 
 namespace dsm {
 void set_serial_views(dsm_ctx* ctx, bool serial);
+dsm_status tuning_search(dsm_tuning* cur, float* cur_ms,
+                         const std::function<dsm_status(const dsm_tuning&, float*)>& measure);
 }
 
 struct dsm_batch {
@@ -180,18 +183,50 @@ dsm_status dsm_batch_step(dsm_batch* b, const dsm_batch_item* items, int32_t n, 
 dsm_status dsm_batch_autotune(dsm_batch* b, const dsm_batch_item* items, int32_t n, const dsm_params* params,
                               int32_t reps) {
   if (!b || !items || !params || n < 1 || n > b->n) return DSM_ERR_INVALID_ARG;
-  for (int i = 0; i < n; ++i) {
-    const dsm_batch_item& it = items[i];
-    dsm_params p = *params;
-    p.stream = b->ss[i];
-    float* img = it.image;
-    const dsm_status st = dsm_autotune(b->ctx[i], &it.mesh, it.lights, it.light_params, it.n_lights, &it.camera, 1,
-                                       &p, &img, reps, nullptr, nullptr);
-    if (st != DSM_OK) return batch_fail(b, st, std::string("scene ") + std::to_string(i) + ": " +
-                                                 dsm_last_error(b->ctx[i]));
+  if (reps < 1 || reps > 100) return batch_fail(b, DSM_ERR_INVALID_ARG, "reps out of range");
+  cudaStream_t origin = (cudaStream_t)params->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess) return batch_fail(b, DSM_ERR_CUDA, "event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return batch_fail(b, DSM_ERR_CUDA, "event");
   }
-  b->sig = 0;   // the shapes changed: the next step records a new graph
-  return DSM_OK;
+  auto set_all = [&](const dsm_tuning& t) -> dsm_status {
+    for (int i = 0; i < n; ++i) {
+      const dsm_status st = dsm_set_tuning(b->ctx[i], &t);
+      if (st != DSM_OK) return batch_fail(b, st, "tuning");
+    }
+    b->sig = 0;   // the next step records a new graph
+    return DSM_OK;
+  };
+  // whole batched steps with shapes t: the eager step that records the graph
+  // and one replay untimed, then `reps` timed replays
+  auto measure = [&](const dsm_tuning& t, float* ms) -> dsm_status {
+    dsm_status st = set_all(t);
+    for (int k = 0; k < 2 && st == DSM_OK; ++k) st = dsm_batch_step(b, items, n, params);
+    if (st == DSM_OK) st = dsm_batch_sync(b);
+    if (st != DSM_OK) return st;
+    if (cudaEventRecord(e0, origin) != cudaSuccess) return batch_fail(b, DSM_ERR_CUDA, "event record");
+    for (int k = 0; k < reps && st == DSM_OK; ++k) st = dsm_batch_step(b, items, n, params);
+    if (st != DSM_OK) return st;
+    if (cudaEventRecord(e1, origin) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+      return batch_fail(b, DSM_ERR_CUDA, "event wait");
+    st = dsm_batch_sync(b);
+    if (st != DSM_OK) return st;
+    float total = 0.f;
+    if (cudaEventElapsedTime(&total, e0, e1) != cudaSuccess) return batch_fail(b, DSM_ERR_CUDA, "event time");
+    *ms = total / reps;
+    return DSM_OK;
+  };
+  dsm_tuning cur{};
+  dsm_get_tuning(b->ctx[0], &cur);
+  float cur_ms = 0.f;
+  dsm_status st = measure(cur, &cur_ms);
+  if (st == DSM_OK) st = dsm::tuning_search(&cur, &cur_ms, measure);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DSM_OK) return st;
+  return set_all(cur);
 }
 
 dsm_status dsm_batch_sync(dsm_batch* b) {

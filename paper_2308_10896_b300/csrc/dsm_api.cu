@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 #include <atomic>
+#include <functional>
 #include "dsm.h"
 #include "common.cuh"
 #include "kernels.h"
@@ -257,6 +258,36 @@ namespace dsm {
 // Batched scenes: each context keeps its views on the caller's stream.
 void set_serial_views(dsm_ctx* ctx, bool serial) {
   if (ctx) ctx->serial = serial;
+}
+
+// Coordinate search over the kernel shapes: from *cur (timed as *cur_ms by
+// the caller), each knob in turn -- light tile, camera tile, bin depth from
+// {4, 16, 64}, filter shape -- is set to each of its other values and kept
+// when `measure` reports a step at least 2 % faster.
+dsm_status tuning_search(dsm_tuning* cur, float* cur_ms,
+                         const std::function<dsm_status(const dsm_tuning&, float*)>& measure) {
+  const int32_t tiles[2] = {16, 32}, bins[3] = {4, 16, 64}, shapes[2] = {0, 1};
+  for (int knob = 0; knob < 4; ++knob) {
+    const int32_t* vals = knob < 2 ? tiles : (knob == 2 ? bins : shapes);
+    const int nv = knob == 2 ? 3 : 2;
+    const dsm_tuning base = *cur;
+    for (int k = 0; k < nv; ++k) {
+      dsm_tuning cand = base;
+      int32_t* field = knob == 0 ? &cand.light_tile
+                     : knob == 1 ? &cand.camera_tile
+                     : knob == 2 ? &cand.big_tiles : &cand.filter_shape;
+      if (*field == vals[k]) continue;
+      *field = vals[k];
+      float ms = 0.f;
+      const dsm_status s = measure(cand, &ms);
+      if (s != DSM_OK) return s;
+      if (ms < 0.98f * *cur_ms) {
+        *cur = cand;
+        *cur_ms = ms;
+      }
+    }
+  }
+  return DSM_OK;
 }
 }  // namespace dsm
 
@@ -1031,26 +1062,7 @@ dsm_status dsm_autotune(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* lig
   dsm_tuning cur = ctx->tuning;
   float cur_ms = 0.f;
   s = measure(cur, &cur_ms);
-  const int32_t tiles[2] = {16, 32}, bins[3] = {4, 16, 64}, shapes[2] = {0, 1};
-  for (int knob = 0; knob < 4 && s == DSM_OK; ++knob) {
-    const int32_t* vals = knob < 2 ? tiles : (knob == 2 ? bins : shapes);
-    const int nv = knob == 2 ? 3 : 2;
-    const dsm_tuning base = cur;
-    for (int k = 0; k < nv && s == DSM_OK; ++k) {
-      dsm_tuning cand = base;
-      int32_t* field = knob == 0 ? &cand.light_tile
-                     : knob == 1 ? &cand.camera_tile
-                     : knob == 2 ? &cand.big_tiles : &cand.filter_shape;
-      if (*field == vals[k]) continue;
-      *field = vals[k];
-      float ms = 0.f;
-      s = measure(cand, &ms);
-      if (s == DSM_OK && ms < 0.98f * cur_ms) {
-        cur = cand;
-        cur_ms = ms;
-      }
-    }
-  }
+  if (s == DSM_OK) s = dsm::tuning_search(&cur, &cur_ms, measure);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->tuning = cur;

@@ -489,7 +489,8 @@ class Batch:
         return int(self.lib.dsm_batch_kernels_per_step(self.h))
 
     def autotune(self, reps: int = 2):
-        """dsm_autotune of every scene's context (synchronous)."""
+        """Shapes shared by every scene, chosen by timing whole batched steps
+        (dsm_batch_autotune, synchronous)."""
         st = self.lib.dsm_batch_autotune(self.h, ctypes.cast(self.items, ctypes.c_void_p), len(self.scenes),
                                          ctypes.byref(self.params), int(reps))
         if st != DSM_OK:

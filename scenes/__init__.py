@@ -32,7 +32,7 @@ __all__ = [
     "icosphere", "subdivided_box", "ground_quad", "sh_displace", "random_rotation",
     "look_at_perspective", "directional_light", "spot_light", "merge_meshes",
     "config1", "config2", "config3", "config4", "config5", "config_by_name",
-    "tiny_scene", "jitter_vertices", "displaced_target",
+    "tiny_scene", "jitter_vertices", "displaced_target", "minimal_plane",
 ]
 
 
@@ -373,6 +373,31 @@ def tiny_scene(seed: int = 0, res: int = 32, img: int = 32, kind: str = "directi
     return {"name": f"tiny{seed}", "verts": verts, "tris": tris, "tri_mat": mat,
             "albedo": np.array([[0.9, 0.6, 0.4], [0.6, 0.7, 0.8]], np.float32),
             "lights": lights, "camera": cam, "params": _default_params(min_variance=1e-5)}
+
+
+def minimal_plane(res: int = 256, img: int = 128, sigma: float = 1.0, displace=(0.12, 0.0, 0.08),
+                  kind: int = 0) -> dict:
+    """The paper's minimal-plane convergence setup (supplementary Sec. B): a
+    square occluder (2 triangles, side 1, height 1) parallel to a square
+    receiver (side 4, height 0), a directional light orthogonal to both, and a
+    camera between them looking down at the receiver (the occluder is behind
+    it, so the images show only the shadow).  One occluder corner (vertex
+    `moved`) is displaced horizontally by `displace`; "target_verts" holds the
+    undisplaced configuration, whose shadow image is the optimisation target."""
+    occ = np.array([[-0.5, 1.0, -0.5], [0.5, 1.0, -0.5], [0.5, 1.0, 0.5], [-0.5, 1.0, 0.5]], np.float64)
+    occ_t = np.array([[0, 2, 1], [0, 3, 2]], np.int64)          # normal +Y
+    gv, gt = ground_quad(2.0, 0.0)
+    target, tris, mat = merge_meshes([(occ, occ_t, 0), (gv, gt, 1)])
+    moved = 2
+    verts = target.copy()
+    verts[moved] += np.asarray(displace, np.float32)
+    light = directional_light((0.0, -1.0, 0.0), res, ortho_half=1.5, dist=5.0, near=1.0, far=10.0,
+                              sigma=sigma, intensity=(1.0, 1.0, 1.0))
+    cam = look_at_perspective((0.0, 0.9, 0.0), (0.0, 0.0, 0.0), 90.0, img, img, near=0.05, far=10.0)
+    return {"name": "minimal_plane", "verts": verts, "tris": tris, "tri_mat": mat,
+            "albedo": np.array([[0.8, 0.8, 0.8], [0.8, 0.8, 0.8]], np.float32), "lights": [light],
+            "camera": cam, "params": _default_params(min_variance=1e-5, filter_kind=kind),
+            "target_verts": target, "moved": moved}
 
 
 def jitter_vertices(scene: dict, sigma: float, seed: int) -> np.ndarray:
