@@ -35,7 +35,9 @@
 extern "C" {
 #endif
 
-#define DSM_MAX_LIGHTS 8
+#define DSM_MAX_LIGHTS 8         /* lights per call                                     */
+#define DSM_MAX_LIGHT_VIEWS 24   /* shadow-map views of those lights: one per directional
+                                    or spot light, six per point light (cube map)        */
 #define DSM_MAX_CAMERAS 8
 
 typedef enum dsm_status {
@@ -71,10 +73,19 @@ typedef struct dsm_mesh {
  *  type 0, directional: orthographic shadow camera at -dist * normalize(dir),
  *          looking along dir, window +-ortho_half;
  *  type 1, spot: perspective shadow camera at the position looking along dir,
- *          full vertical field of view fov_y_deg.
+ *          full vertical field of view fov_y_deg;
+ *  type 2, point (omnidirectional, Sec. 3: several shadow-map planes arranged
+ *          as a box): a cube map of six perspective faces at the position,
+ *          90-degree field of view, looking along +X, -X, +Y, -Y, +Z, -Z
+ *          (light views in that order), res x res texels each; dir and
+ *          fov_y_deg are unused (zero direction gradient).  Each face is
+ *          antialiased and filtered on its own (the filter boundary applies
+ *          at the face edges) and a point x is shaded by the face of the
+ *          largest component of x - position (ties: x, then y).
  * The map stores the normalised depth d = (z_view - near) / (far - near), with
- * z_view the distance along normalize(dir) (Sec. 3: distance from a plane for a
- * directional light).  Up vector +Y, or +Z when |dir_y| > 0.99 |dir|. */
+ * z_view the distance along normalize(dir) (along the face axis for a cube
+ * face; Sec. 3: distance from a plane for a directional light).  Up vector +Y,
+ * or +Z when |dir_y| > 0.99 |dir|. */
 typedef struct dsm_light {
   int32_t type;
   int32_t res;            /* shadow-map side in texels, 1..16384                   */

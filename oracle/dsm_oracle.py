@@ -47,7 +47,7 @@ GUARD = 1 << 28       # |snapped coordinate| limit; beyond it the triangle is cu
 W_MIN = np.float32(1e-6)
 
 __all__ = [
-    "light_matrix", "clip_pinned", "setup_view", "raster", "edge_adjacency", "silhouette_table",
+    "light_matrix", "light_views", "cube_face", "clip_pinned", "setup_view", "raster", "edge_adjacency", "silhouette_table",
     "barycentrics", "antialias", "filter_weights", "separable_filter", "bilinear",
     "chebyshev", "light_visibility", "vertex_normals", "render", "mse_loss", "render_and_grad",
     "render_cameras_and_grad", "adam_step",
@@ -72,7 +72,34 @@ def _f32(x) -> float:
     return float(np.float32(x))
 
 
-def light_matrix(light: dict, pos: torch.Tensor, direction: torch.Tensor) -> torch.Tensor:
+# Cube faces of a point light, in view order: the fixed viewing axis of each.
+CUBE_AXES = ((1.0, 0.0, 0.0), (-1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, -1.0, 0.0), (0.0, 0.0, 1.0),
+             (0.0, 0.0, -1.0))
+
+
+def light_views(light: dict) -> list:
+    """Shadow-map views of a light: one plane, or for a point light (type 2)
+    the six planes of a box around it (Sec. 3: when the rays from the light
+    cannot be parameterised over one plane, several planes arranged as a box
+    are used).  Returns the cube-face index of each view (None: single view).
+    reading: the faces look along +X, -X, +Y, -Y, +Z, -Z with a 90-degree
+    field of view; each face map is antialiased and filtered on its own."""
+    return list(range(6)) if int(light["type"]) == 2 else [None]
+
+
+def cube_face(d: np.ndarray) -> np.ndarray:
+    """Face of a point light's cube map holding the directions d (n, 3) from
+    the light: the axis of largest |component| and its sign, ties to x, then y.
+    reading: the paper leaves the face selection open; this is the usual
+    major-axis rule."""
+    a = np.abs(d)
+    fx = (a[:, 0] >= a[:, 1]) & (a[:, 0] >= a[:, 2])
+    fy = ~fx & (a[:, 1] >= a[:, 2])
+    return np.where(fx, np.where(d[:, 0] >= 0, 0, 1),
+                    np.where(fy, np.where(d[:, 1] >= 0, 2, 3), np.where(d[:, 2] >= 0, 4, 5)))
+
+
+def light_matrix(light: dict, pos: torch.Tensor, direction: torch.Tensor, face=None) -> torch.Tensor:
     """Light camera of Supplementary Sec. A as a 5x4 float64 matrix Q.
 
     Rows 0-3 map [x, 1] to light clip space; row 4 maps [x, 1] to the
@@ -84,8 +111,12 @@ def light_matrix(light: dict, pos: torch.Tensor, direction: torch.Tensor) -> tor
     directional light is at -dist * f; a spot light looks from ``pos`` along f.
     Up vector +Y, or +Z when |f_y| > 0.99.  Every entry is formed in this exact
     operation order in float64 (``_dot`` left to right, division by the norm)
-    and rounded to float32 only by the caller.
+    and rounded to float32 only by the caller.  A cube face (``face`` of a
+    point light) is the perspective camera at ``pos`` looking along the face
+    axis with c = 1 (90 degrees); the direction parameter does not enter it.
     """
+    if face is not None:
+        direction = torch.tensor(CUBE_AXES[face], dtype=F64)
     f = _normalize(direction)
     if abs(float(f[1].detach())) > 0.99:
         up = torch.tensor([0.0, 0.0, 1.0], dtype=F64)
@@ -112,7 +143,7 @@ def light_matrix(light: dict, pos: torch.Tensor, direction: torch.Tensor) -> tor
         row2 = depth
         row3 = torch.stack([zero, zero, zero, one])
     else:
-        c = 1.0 / math.tan(_f32(light["fov_y_deg"]) * math.pi / 360.0)
+        c = 1.0 if int(light["type"]) == 2 else 1.0 / math.tan(_f32(light["fov_y_deg"]) * math.pi / 360.0)
         A = far / rng
         B = -(far * near) / rng
         row0 = torch.stack([c * r[0], c * r[1], c * r[2], -(c * _dot(r, e))])
@@ -530,6 +561,11 @@ def _substitute(value: torch.Tensor, teacher) -> torch.Tensor:
     return value + (tv - value).detach()
 
 
+def _teacher_view(teacher: dict, key: str, view: int):
+    vals = teacher.get(key)
+    return vals[view] if vals is not None and view < len(vals) else None
+
+
 def shade_pixels(scene: dict, verts: torch.Tensor, light_params: torch.Tensor, albedo: torch.Tensor, maps: list,
                  clipc: torch.Tensor, ids: np.ndarray):
     """Camera pass of Alg. 2 with Lambert shading (suppl. Sec. A) at the
@@ -549,8 +585,16 @@ def shade_pixels(scene: dict, verts: torch.Tensor, light_params: torch.Tensor, a
     radiance = torch.zeros((x.shape[0], 3), dtype=F64)
     vis_all = []
     for li, light in enumerate(scene["lights"]):
-        Q, mom = maps[li]
-        vis = light_visibility(Q, mom, xh, float(P["min_variance"]))
+        views = maps[li] if isinstance(maps[li], list) else [maps[li]]
+        if int(light["type"]) == 2:
+            # the face of the cube map that holds x (a decision, no derivative)
+            face = torch.as_tensor(cube_face((x - light_params[li, 0:3][None, :]).detach().numpy()))
+            vis = torch.zeros((x.shape[0],), dtype=F64)
+            for k, (Q, mom) in enumerate(views):
+                vis = torch.where(face == k, light_visibility(Q, mom, xh, float(P["min_variance"])), vis)
+        else:
+            Q, mom = views[0]
+            vis = light_visibility(Q, mom, xh, float(P["min_variance"]))
         if int(light["type"]) == 0:
             dl = light_params[li, 3:6]
             omega = -(dl / torch.sqrt((dl * dl).sum()))[None, :].expand_as(x)
@@ -567,14 +611,15 @@ def shade_pixels(scene: dict, verts: torch.Tensor, light_params: torch.Tensor, a
 
 def render(scene: dict, verts: torch.Tensor = None, light_params: torch.Tensor = None,
            albedo: torch.Tensor = None, teacher: dict = None, keep: bool = True) -> dict:
-    """Forward pass: Alg. 1 per light, then the camera pass with Alg. 2 and
+    """Forward pass: Alg. 1 per light view (one per directional or spot light,
+    six cube faces per point light), then the camera pass with Alg. 2 and
     Lambert shading, then the final antialiasing.
 
     ``light_params`` is (L, 6) float64: (pos xyz, dir xyz) per light.
     ``teacher`` optionally replaces stage values ('ftilde', 'moments' lists per
-    light, 'color') by given ones while keeping each stage's derivative.
+    light view, 'color') by given ones while keeping each stage's derivative.
     Returns a dict with the image (H, W, 4: RGB and coverage) and every
-    intermediate."""
+    intermediate ('lights' holds one entry per light view)."""
     P = scene["params"]
     tris_np = scene["tris"].astype(np.int64)
     tris = torch.as_tensor(tris_np)
@@ -591,32 +636,37 @@ def render(scene: dict, verts: torch.Tensor = None, light_params: torch.Tensor =
     vh = torch.cat([verts, ones], 1)
     out = {"lights": []}
     maps = []
+    teach = teacher or {}
+    view = 0   # light views in order: a point light's six faces are consecutive
     for li, light in enumerate(scene["lights"]):
-        Q = light_matrix(light, light_params[li, 0:3], light_params[li, 3:6])
-        Q32 = Q.detach().numpy().astype(np.float32)
-        R = int(light["res"])
-        st = setup_view(clip_pinned(Q32[:4], V32), tris_np, R, R)
-        ras = raster(st, tris_np)
-        clip = vh @ Q[:4].T
-        depth = vh @ Q[4]
-        jj, ii, tri, b = barycentrics(clip, tris, ras["ids"])
-        f = (b * depth[tris[tri]]).sum(1)
-        fmap = torch.ones((R, R, 2), dtype=F64)
-        fmap = fmap.index_put((torch.as_tensor(jj), torch.as_tensor(ii)), torch.stack([f, f * f], 1))
-        if P.get("aa_shadow", 1):
-            sil = silhouette_table(adj, st)
-            sx, sy = screen_coords(clip, R, R)
-            ft = antialias(fmap, ras, st, sil, tris_np, sx, sy)
-        else:
-            ft = fmap
-        ft = _substitute(ft, (teacher or {}).get("ftilde", [None] * 8)[li])
-        w = filter_weights(light["sigma"], light["radius"], P.get("filter_kind", 0))
-        mom = separable_filter(ft, w, P.get("filter_boundary", 0))
-        mom = _substitute(mom, (teacher or {}).get("moments", [None] * 8)[li])
-        maps.append((Q, mom))
-        if keep:
-            out["lights"].append({"Q": Q, "Q32": Q32, "setup": st, "raster": ras, "f": fmap,
-                                  "ftilde": ft, "moments": mom, "weights": w})
+        maps.append([])
+        for face in light_views(light):
+            Q = light_matrix(light, light_params[li, 0:3], light_params[li, 3:6], face)
+            Q32 = Q.detach().numpy().astype(np.float32)
+            R = int(light["res"])
+            st = setup_view(clip_pinned(Q32[:4], V32), tris_np, R, R)
+            ras = raster(st, tris_np)
+            clip = vh @ Q[:4].T
+            depth = vh @ Q[4]
+            jj, ii, tri, b = barycentrics(clip, tris, ras["ids"])
+            f = (b * depth[tris[tri]]).sum(1)
+            fmap = torch.ones((R, R, 2), dtype=F64)
+            fmap = fmap.index_put((torch.as_tensor(jj), torch.as_tensor(ii)), torch.stack([f, f * f], 1))
+            if P.get("aa_shadow", 1):
+                sil = silhouette_table(adj, st)
+                sx, sy = screen_coords(clip, R, R)
+                ft = antialias(fmap, ras, st, sil, tris_np, sx, sy)
+            else:
+                ft = fmap
+            ft = _substitute(ft, _teacher_view(teach, "ftilde", view))
+            w = filter_weights(light["sigma"], light["radius"], P.get("filter_kind", 0))
+            mom = separable_filter(ft, w, P.get("filter_boundary", 0))
+            mom = _substitute(mom, _teacher_view(teach, "moments", view))
+            maps[li].append((Q, mom))
+            if keep:
+                out["lights"].append({"Q": Q, "Q32": Q32, "setup": st, "raster": ras, "f": fmap,
+                                      "ftilde": ft, "moments": mom, "weights": w, "light": li, "face": face})
+            view += 1
     cam = scene["camera"]
     Wc, Hc = cam["width"], cam["height"]
     M32 = np.asarray(cam["clip"], np.float32)

@@ -8,7 +8,8 @@ namespace dsm {
 constexpr int kSubpix = 256;          // 8 sub-pixel bits: 24.8 fixed point
 constexpr int kGuard = 1 << 28;       // |snapped coordinate| limit; beyond it a triangle is culled
 constexpr float kWMin = 1e-6f;        // clip w below this culls the triangle
-constexpr int kMaxViews = DSM_MAX_LIGHTS + DSM_MAX_CAMERAS;   // light views, then camera views
+constexpr int kMaxLightViews = DSM_MAX_LIGHT_VIEWS;            // shadow-map views (cube faces count one each)
+constexpr int kMaxViews = kMaxLightViews + DSM_MAX_CAMERAS;     // light views, then camera views
 // Raster tile side 2^tile_log2 pixels: 16 or 32 per view (chosen by the
 // tuning of the context; 32 by default).
 constexpr int kTileLog2Min = 4, kTileLog2Max = 5, kTileLog2Default = 5;
@@ -43,17 +44,19 @@ struct LightDev {
   float fwd[3];       // normalised travel direction
   float dir_norm;     // |dir|
   float pos[3];
-  int type;
+  int type;           // 0 directional, 1 perspective (spot light or a cube face of a point light)
   int res;
   float intensity[3];
+  int face;           // cube face 0..5 (+X, -X, +Y, -Y, +Z, -Z) of a point light, -1 otherwise
+  int user;           // index of the light in the caller's arrays
 };
 
 // Device status word (errors raised by kernels, read by dsm_sync).
 struct DevStatus {
   int capacity_overflow;
   int timeout;
-  int needed_pairs[DSM_MAX_LIGHTS + DSM_MAX_CAMERAS];
-  int big_count[DSM_MAX_LIGHTS + DSM_MAX_CAMERAS];   // triangles of each view flagged as big
+  int needed_pairs[kMaxViews];
+  int big_count[kMaxViews];   // triangles of each view flagged as big
 };
 
 // Contention control for gradient scatters.  A triangle whose pixel bbox spans

@@ -75,15 +75,19 @@ struct dsm_ctx {
   int topo_T = -1, topo_V = -1;
   Buf adj, vf_off, vf_list;
   ViewBufs view[kMaxViews];
-  LightBufs light[DSM_MAX_LIGHTS];
+  LightBufs light[kMaxLightViews];
   Buf lights_dev, viewM, status, vnormal, vnlen, gnormal, gN, gface, gQ, gdirect, red;
   Buf scratch_dverts, scratch_dlight, scratch_dalbedo, filter_tmp;
   DevStatus* hstatus = nullptr;
   // state of the last forward
   bool have_fwd = false;
   dsm_mesh mesh{};
-  dsm_light lights[DSM_MAX_LIGHTS]{};
-  int L = 0, C = 0;
+  dsm_light lights[DSM_MAX_LIGHTS]{};   // the caller's lights
+  int n_user = 0;                        // their number
+  // light views: one per directional or spot light, six (cube faces) per point light
+  int view_user[kMaxLightViews]{};       // caller's light of each light view
+  int view_face[kMaxLightViews]{};       // its cube face, or -1
+  int L = 0, C = 0;                      // light views, cameras
   dsm_camera cams[DSM_MAX_CAMERAS]{};
   dsm_params params{};
   // raster tile sides, big-triangle threshold and filter shape (dsm_autotune)
@@ -132,7 +136,7 @@ struct CamMats {
 
 // One launch that zeroes several buffers: segment blockIdx.y, 16-byte stores
 // over its aligned body, 4-byte stores for an unaligned head and the tail.
-constexpr int kMaxClear = 64;
+constexpr int kMaxClear = 96;
 struct ClearList {
   float* p[kMaxClear];
   long long n[kMaxClear];     // floats
@@ -388,11 +392,15 @@ static dsm_status check_args(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light
     if (cam.width < 1 || cam.height < 1 || cam.width > 16384 || cam.height > 16384)
       return fail(ctx, DSM_ERR_INVALID_ARG, "camera size out of range");
   }
+  int views = 0;
   for (int l = 0; l < n_lights; ++l) {
     const dsm_light& L = lights[l];
-    if (L.type != 0 && L.type != 1) return fail(ctx, DSM_ERR_INVALID_ARG, "unknown light type");
+    if (L.type != 0 && L.type != 1 && L.type != 2) return fail(ctx, DSM_ERR_INVALID_ARG, "unknown light type");
+    views += L.type == 2 ? 6 : 1;
+    if (views > DSM_MAX_LIGHT_VIEWS) return fail(ctx, DSM_ERR_INVALID_ARG, "more than 24 shadow-map views");
     if (L.res < 1 || L.res > 16384) return fail(ctx, DSM_ERR_INVALID_ARG, "shadow-map size out of range");
     if (!(L.far_plane > L.near_plane)) return fail(ctx, DSM_ERR_INVALID_ARG, "far must exceed near");
+    if (L.type != 0 && !(L.near_plane > 0.f)) return fail(ctx, DSM_ERR_INVALID_ARG, "perspective near must be > 0");
     if (L.type == 0 && !(L.ortho_half > 0.f)) return fail(ctx, DSM_ERR_INVALID_ARG, "ortho_half must be positive");
     if (L.type == 1 && !(L.fov_y_deg > 0.f && L.fov_y_deg < 180.f)) return fail(ctx, DSM_ERR_INVALID_ARG, "bad fov");
     if (!(L.sigma > 0.f) && L.radius <= 0) return fail(ctx, DSM_ERR_INVALID_ARG, "filter needs sigma or radius");
@@ -449,7 +457,7 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
 namespace {
 
 // Camera buffer set under recomputation (view[0] is the light set).
-constexpr int kCamSlot = DSM_MAX_LIGHTS;
+constexpr int kCamSlot = kMaxLightViews;
 
 // Buffers of view w (lights 0..L-1, then cameras L..L+C-1).  Under
 // recomputation every light view uses view[0] and every camera view
@@ -470,13 +478,14 @@ bool view_is_light(const dsm_ctx* ctx, int w) { return w < ctx->L; }
 dsm_status prepare_view(dsm_ctx* ctx, int w) {
   const int L = ctx->L;
   const bool light = view_is_light(ctx, w);
-  const int W = light ? ctx->lights[w].res : ctx->cams[w - L].width;
-  const int H = light ? ctx->lights[w].res : ctx->cams[w - L].height;
+  const int W = light ? ctx->lights[ctx->view_user[w]].res : ctx->cams[w - L].width;
+  const int H = light ? ctx->lights[ctx->view_user[w]].res : ctx->cams[w - L].height;
   return ensure_view(ctx, vbuf(ctx, w), W, H, ctx->mesh.n_verts, ctx->mesh.n_tris, light);
 }
 
 dsm_status prepare_light(dsm_ctx* ctx, int l) {
-  const int R = ctx->lights[l].res;
+  const dsm_light& Lu = ctx->lights[ctx->view_user[l]];
+  const int R = Lu.res;
   const size_t R2 = (size_t)R * R * sizeof(float2);
   LightBufs& wk = lwork(ctx, l);
   DSM_CHECK(wk.fmap.ensure(R2));
@@ -485,8 +494,7 @@ dsm_status prepare_light(dsm_ctx* ctx, int l) {
   LightBufs& lb = ctx->light[l];
   DSM_CHECK(lb.mom.ensure(R2));
   lb.res = R;
-  make_filter_args(ctx->lights[l].sigma, ctx->lights[l].radius, ctx->params.filter_kind, ctx->params.filter_boundary,
-                   &lb.fa);
+  make_filter_args(Lu.sigma, Lu.radius, ctx->params.filter_kind, ctx->params.filter_boundary, &lb.fa);
   lb.fa.shape = ctx->tuning.filter_shape;
   return DSM_OK;
 }
@@ -731,9 +739,18 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
   if (s != DSM_OK) return s;
   ctx->have_fwd = false;
   cudaStream_t st = (cudaStream_t)params->stream;
-  const int V = mesh->n_verts, T = mesh->n_tris, L = n_lights, C = n_cams, NV = L + C;
   ctx->mesh = *mesh;
-  for (int l = 0; l < L; ++l) ctx->lights[l] = lights[l];
+  int L = 0;
+  for (int u = 0; u < n_lights; ++u) {
+    ctx->lights[u] = lights[u];
+    const int faces = lights[u].type == 2 ? 6 : 1;
+    for (int f = 0; f < faces; ++f, ++L) {
+      ctx->view_user[L] = u;
+      ctx->view_face[L] = lights[u].type == 2 ? f : -1;
+    }
+  }
+  ctx->n_user = n_lights;
+  const int V = mesh->n_verts, T = mesh->n_tris, C = n_cams, NV = L + C;
   for (int c = 0; c < C; ++c) ctx->cams[c] = cams[c];
   ctx->L = L;
   ctx->C = C;
@@ -745,7 +762,7 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
   uint64_t sig = mix(mix(mix(mix(mix(1, V), T), L), C), ctx->recompute ? 1 : 0);
   sig = mix(mix(mix(sig, ctx->tuning.light_tile), ctx->tuning.camera_tile), ctx->tuning.big_tiles);
   for (int c = 0; c < C; ++c) sig = mix(mix(sig, cams[c].width), cams[c].height);
-  for (int l = 0; l < L; ++l) sig = mix(mix(sig, lights[l].res), lights[l].type);
+  for (int u = 0; u < n_lights; ++u) sig = mix(mix(sig, lights[u].res), lights[u].type);
   const bool sizing = ctx->sized_sig != sig;
   for (int w = 0; w < NV; ++w) {
     s = prepare_view(ctx, w);
@@ -755,7 +772,7 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
     s = prepare_light(ctx, l);
     if (s != DSM_OK) return s;
   }
-  DSM_CHECK(ctx->lights_dev.ensure(sizeof(LightDev) * DSM_MAX_LIGHTS));
+  DSM_CHECK(ctx->lights_dev.ensure(sizeof(LightDev) * kMaxLightViews));
   DSM_CHECK(ctx->viewM.ensure(sizeof(float) * 20 * kMaxViews));
   DSM_CHECK(ctx->vnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->vnlen.ensure(sizeof(float) * std::max(V, 1)));
@@ -764,15 +781,18 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
   LightSetupArgs la{};
   la.n = L;
   for (int l = 0; l < L; ++l) {
-    const dsm_light& Lh = lights[l];
+    const dsm_light& Lh = lights[ctx->view_user[l]];
     LightConst& c = la.c[l];
-    c.type = Lh.type;
+    // a cube face is a perspective view with a 90 degree field of view (c = 1)
+    c.type = Lh.type == 0 ? 0 : 1;
     c.res = Lh.res;
+    c.user = ctx->view_user[l];
+    c.face = ctx->view_face[l];
     c.dist = Lh.dist;
     c.ortho_half = Lh.ortho_half;
     c.near_plane = Lh.near_plane;
     c.far_plane = Lh.far_plane;
-    c.persp_c = Lh.type == 1 ? 1.0 / std::tan((double)Lh.fov_y_deg * M_PI / 360.0) : 0.0;
+    c.persp_c = Lh.type == 2 ? 1.0 : Lh.type == 1 ? 1.0 / std::tan((double)Lh.fov_y_deg * M_PI / 360.0) : 0.0;
     c.intensity[0] = Lh.intensity[0]; c.intensity[1] = Lh.intensity[1]; c.intensity[2] = Lh.intensity[2];
   }
   float* viewM = ctx->viewM.as<float>();
@@ -881,8 +901,8 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
   DSM_CHECK(ctx->gnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->gN.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->gface.ensure(sizeof(float) * 3 * std::max(T, 1)));
-  DSM_CHECK(ctx->gQ.ensure(sizeof(float) * 20 * DSM_MAX_LIGHTS));
-  DSM_CHECK(ctx->gdirect.ensure(sizeof(float) * 3 * DSM_MAX_LIGHTS));
+  DSM_CHECK(ctx->gQ.ensure(sizeof(float) * 20 * kMaxLightViews));
+  DSM_CHECK(ctx->gdirect.ensure(sizeof(float) * 3 * kMaxLightViews));
   const int n_mat_red = mesh.n_materials <= kMaxSharedMat ? mesh.n_materials : 0;
   const int red_stride = 23 * L + 3 * n_mat_red;
   DSM_CHECK(ctx->red.ensure(sizeof(float) * kRedSlots * std::max(red_stride, 1)));
@@ -901,17 +921,17 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     StageTimer t(ctx, ST_BWD_CLEAR, st);
     Clearer cl;
     cl.add(dL_dverts, sizeof(float) * 3 * V);
-    if (L) cl.add(dL_dlight, sizeof(float) * 6 * L);
+    if (ctx->n_user) cl.add(dL_dlight, sizeof(float) * 6 * ctx->n_user);
     cl.add(dL_dalbedo, sizeof(float) * 3 * mesh.n_materials);
     cl.add(ctx->gnormal.p, sizeof(float) * 3 * V);
-    cl.add(ctx->gQ.p, sizeof(float) * 20 * DSM_MAX_LIGHTS);
-    cl.add(ctx->gdirect.p, sizeof(float) * 3 * DSM_MAX_LIGHTS);
+    cl.add(ctx->gQ.p, sizeof(float) * 20 * kMaxLightViews);
+    cl.add(ctx->gdirect.p, sizeof(float) * 3 * kMaxLightViews);
     cl.add(ctx->red.p, sizeof(float) * kRedSlots * red_stride);
     for (int l = 0; l < L; ++l)
       cl.add(ctx->light[l].gm.p, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2));
     if (!ctx->recompute)
       for (int w = 0; w < NV; ++w) clear_view(cl, w);
-    static_assert(7 + DSM_MAX_LIGHTS + 2 * kMaxViews <= kMaxClear, "clear list");
+    static_assert(7 + kMaxLightViews + 2 * kMaxViews <= kMaxClear, "clear list");
     cl.launch(st);
   }
   DSM_CHECK(cudaGetLastError());
@@ -988,8 +1008,8 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
                             ctx->gN.as<float>(), ctx->gface.as<float>(), dL_dverts, st);
     launch_red_reduce(ctx->red.as<float>(), red_stride, L, n_mat_red, ctx->gQ.as<float>(), ctx->gdirect.as<float>(),
                       dL_dalbedo, st);
-    launch_light_grad(ctx->lights_dev.as<LightDev>(), L, ctx->gQ.as<float>(), ctx->gdirect.as<float>(), dL_dlight,
-                      st);
+    launch_light_grad(ctx->lights_dev.as<LightDev>(), L, ctx->n_user, ctx->gQ.as<float>(), ctx->gdirect.as<float>(),
+                      dL_dlight, st);
   }
   DSM_CHECK(cudaGetLastError());
   return DSM_OK;

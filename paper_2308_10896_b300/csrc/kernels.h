@@ -14,8 +14,10 @@ extern std::atomic<unsigned long long> g_kernel_launches;
 inline void count_launches(int n) { g_kernel_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 struct LightConst {
-  int type;
+  int type;                // 0 directional, 1 perspective (spot, or a cube face: persp_c = 1)
   int res;
+  int user;                // the caller's light index (its row of the parameter array)
+  int face;                // cube face 0..5 of a point light (fixed axis direction), -1 otherwise
   double dist, ortho_half, near_plane, far_plane;
   double persp_c;          // 1 / tan(fov / 2), computed on the host in float64
   float intensity[3];
@@ -26,7 +28,7 @@ struct Mat20 {
 };
 
 struct LightSetupArgs {
-  LightConst c[DSM_MAX_LIGHTS];
+  LightConst c[kMaxLightViews];
   int n;
 };
 
@@ -58,8 +60,8 @@ struct ShadeArgs {
   const float4* cam_clip;  // V, camera clip coordinates
   const LightDev* lights;
   int L;
-  const float2* mom[DSM_MAX_LIGHTS];
-  int res[DSM_MAX_LIGHTS];
+  const float2* mom[kMaxLightViews];
+  int res[kMaxLightViews];
   float min_variance;
 };
 
@@ -69,7 +71,7 @@ struct ShadeGradArgs {
   float* gnormal;                     // V x 3, dL/d unit vertex normal
   float4* gclip;                      // V, dL/d camera clip
   float* dalbedo;                     // M x 3
-  float2* gm[DSM_MAX_LIGHTS];         // dL/d(m1, m2) texel maps
+  float2* gm[kMaxLightViews];         // dL/d(m1, m2) texel maps
   float* red;                         // kRedSlots x red_stride: [dQ (L x 20) | direct (L x 3) | albedo (M x 3)]
   int red_stride;
   const int* big;                     // camera view big-triangle index per triangle
@@ -180,8 +182,8 @@ void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const 
                               const DevStatus* status, int view, cudaStream_t st);
 void launch_red_reduce(const float* red, int red_stride, int L, int n_mat_red, float* gQ, float* gdirect,
                        float* dalbedo, cudaStream_t st);
-void launch_light_grad(const LightDev* lights, int L, const float* gQ, const float* gdirect, float* dlight,
-                       cudaStream_t st);
+void launch_light_grad(const LightDev* lights, int L, int n_user, const float* gQ, const float* gdirect,
+                       float* dlight, cudaStream_t st);
 void launch_l2(const float* img, const float* tgt, int64_t n, float* loss, float* grad, cudaStream_t st);
 
 }  // namespace dsm

@@ -110,20 +110,29 @@ template <class T> __device__ __forceinline__ T q_entry(int k, const Frame<T>& F
   return c == 0 ? f.x : c == 1 ? f.y : c == 2 ? f.z : -F.fe;
 }
 
-// One CTA per light.  Warp 0: lane k < 20 forms Q[k] in float64 (the frame is
-// computed by every lane at once) and lane 0 writes the light's other fields;
-// warp 1: lane j < 6 forms all of Q with float32 duals in direction theta_j
-// and writes column j of J.
+// Axis component k of cube face `face` (+X, -X, +Y, -Y, +Z, -Z): the fixed
+// viewing direction of that face of a point light's cube map.
+__device__ __forceinline__ float face_axis(int face, int k) {
+  return (face >> 1) == k ? ((face & 1) ? -1.f : 1.f) : 0.f;
+}
+
+// One CTA per light view.  Warp 0: lane k < 20 forms Q[k] in float64 (the
+// frame is computed by every lane at once) and lane 0 writes the view's other
+// fields; warp 1: lane j < 6 forms all of Q with float32 duals in direction
+// theta_j and writes column j of J.  A cube face takes the light's position
+// and the face axis as its direction (a constant: its J has no direction
+// columns).
 __global__ void light_setup_kernel(const float* __restrict__ params, LightSetupArgs a, LightDev* out,
                                    float* viewM) {
   const int l = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (l >= a.n) return;
   const LightConst& L = a.c[l];
   LightDev& o = out[l];
+  const float* pl = params + L.user * 6;
   if (warp == 0) {
     if (lane >= 20) return;
     R64 th[6];
-    for (int k = 0; k < 6; ++k) th[k] = {(double)params[l * 6 + k]};
+    for (int k = 0; k < 6; ++k) th[k] = {(double)(k >= 3 && L.face >= 0 ? face_axis(L.face, k - 3) : pl[k])};
     const R64 zero{0.0}, one{1.0};
     const Frame<R64> F = light_frame(th, L, zero, one);
     const float q = __double2float_rn(q_entry(lane, F, L, zero, one).v);
@@ -133,14 +142,17 @@ __global__ void light_setup_kernel(const float* __restrict__ params, LightSetupA
       o.fwd[0] = (float)F.f.x.v; o.fwd[1] = (float)F.f.y.v; o.fwd[2] = (float)F.f.z.v;
       const double dx = th[3].v, dy = th[4].v, dz = th[5].v;
       o.dir_norm = (float)sqrt(dx * dx + dy * dy + dz * dz);
-      o.pos[0] = params[l * 6 + 0]; o.pos[1] = params[l * 6 + 1]; o.pos[2] = params[l * 6 + 2];
+      o.pos[0] = pl[0]; o.pos[1] = pl[1]; o.pos[2] = pl[2];
       o.type = L.type;
       o.res = L.res;
       o.intensity[0] = L.intensity[0]; o.intensity[1] = L.intensity[1]; o.intensity[2] = L.intensity[2];
+      o.face = L.face;
+      o.user = L.user;
     }
   } else if (warp == 1 && lane < 6) {
     F1 th[6];
-    for (int k = 0; k < 6; ++k) th[k] = {params[l * 6 + k], k == lane ? 1.f : 0.f};
+    for (int k = 0; k < 6; ++k)
+      th[k] = (k >= 3 && L.face >= 0) ? F1{face_axis(L.face, k - 3), 0.f} : F1{pl[k], k == lane ? 1.f : 0.f};
     const F1 zero{0.f, 0.f}, one{1.f, 0.f};
     const Frame<F1> F = light_frame(th, L, zero, one);
     for (int k = 0; k < 20; ++k) o.J[k * 6 + lane] = q_entry(k, F, L, zero, one).d;

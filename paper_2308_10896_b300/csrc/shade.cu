@@ -220,6 +220,21 @@ __device__ __forceinline__ float3 light_omega(const LightDev& Ld, float3 x, floa
   return make_float3(d.x * il, d.y * il, d.z * il);
 }
 
+// Cube face holding direction d (from a point light to a surface point): the
+// axis of largest magnitude and its sign; ties go to x, then y.
+__device__ __forceinline__ int cube_face(float3 d) {
+  const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+  if (ax >= ay && ax >= az) return d.x >= 0.f ? 0 : 1;
+  if (ay >= az) return d.y >= 0.f ? 2 : 3;
+  return d.z >= 0.f ? 4 : 5;
+}
+
+// Whether light view Ld shades point x: always, except a cube face of a point
+// light, which shades the points of its face only (one face per point).
+__device__ __forceinline__ bool view_shades(const LightDev& Ld, float3 x) {
+  return Ld.face < 0 || cube_face(make_float3(x.x - Ld.pos[0], x.y - Ld.pos[1], x.z - Ld.pos[2])) == Ld.face;
+}
+
 __global__ void shade_kernel(ShadeArgs a, float4* __restrict__ color) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= a.W || j >= a.H) return;
@@ -229,6 +244,7 @@ __global__ void shade_kernel(ShadeArgs a, float4* __restrict__ color) {
   float3 rad = make_float3(0.f, 0.f, 0.f);
   for (int l = 0; l < a.L; ++l) {
     const LightDev& Ld = a.lights[l];
+    if (!view_shades(Ld, s.x)) continue;
     const Look L = lookup(Ld.Q, a.mom[l], a.res[l], s.x, a.min_variance);
     float len;
     const float3 om = light_omega(Ld, s.x, len);
@@ -269,13 +285,13 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[N]) {
 // the albedo gradient per block (slot copies), and writes the per-pixel
 // dL/d world position and dL/d interpolated normal for shade_scatter_kernel.
 __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g) {
-  __shared__ float sQ[DSM_MAX_LIGHTS * 20];
-  __shared__ float sD[DSM_MAX_LIGHTS * 3];
+  __shared__ float sQ[kMaxLightViews * 20];
+  __shared__ float sD[kMaxLightViews * 3];
   __shared__ float sA[kMaxSharedMat * 3];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const bool mat_shared = a.n_mat <= kMaxSharedMat;
-  for (int k = tid; k < DSM_MAX_LIGHTS * 20; k += 256) sQ[k] = 0.f;
-  for (int k = tid; k < DSM_MAX_LIGHTS * 3; k += 256) sD[k] = 0.f;
+  for (int k = tid; k < kMaxLightViews * 20; k += 256) sQ[k] = 0.f;
+  for (int k = tid; k < kMaxLightViews * 3; k += 256) sD[k] = 0.f;
   for (int k = tid; k < kMaxSharedMat * 3; k += 256) sA[k] = 0.f;
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -303,7 +319,7 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
 #pragma unroll
     for (int k = 0; k < 20; ++k) gq[k] = 0.f;
     float3 gdir = make_float3(0.f, 0.f, 0.f);
-    if (act) {
+    if (act && view_shades(a.lights[l], s.x)) {
       const LightDev& Ld = a.lights[l];
       const int R = a.res[l];
       const Look L = lookup(Ld.Q, a.mom[l], R, s.x, a.min_variance);
@@ -562,8 +578,8 @@ __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __res
                                                               int n_lights, VertGradPtrs gp,
                                                               float* __restrict__ dverts, float* __restrict__ red,
                                                               int red_stride) {
-  __shared__ float sQ[DSM_MAX_LIGHTS * 20];
-  for (int k = threadIdx.x; k < DSM_MAX_LIGHTS * 20; k += blockDim.x) sQ[k] = 0.f;
+  __shared__ float sQ[kMaxLightViews * 20];
+  for (int k = threadIdx.x; k < kMaxLightViews * 20; k += blockDim.x) sQ[k] = 0.f;
   __syncthreads();
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const bool ok = v < V;
@@ -601,26 +617,32 @@ __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __res
     if (sQ[k] != 0.f) atomicAdd(&dst[k], sQ[k]);
 }
 
-// dL/d(pos, dir) = J^T dL/dQ + the direct terms of the shading direction omega:
-// directional omega = -dir / |dir|, spot omega = normalize(pos - x).
-__global__ void light_grad_kernel(const LightDev* __restrict__ lights, int L, const float* __restrict__ gQ,
-                                  const float* __restrict__ gdirect, float* __restrict__ dlight) {
-  const int l = blockIdx.x;
+// dL/d(pos, dir) of the caller's light u = sum over its views of J^T dL/dQ
+// plus the direct terms of the shading direction omega: directional
+// omega = -dir / |dir|, spot and point omega = normalize(pos - x).  A point
+// light sums its six cube faces (their J has no direction columns).
+__global__ void light_grad_kernel(const LightDev* __restrict__ lights, int L, int n_user,
+                                  const float* __restrict__ gQ, const float* __restrict__ gdirect,
+                                  float* __restrict__ dlight) {
+  const int u = blockIdx.x;
   const int j = threadIdx.x;
-  if (l >= L || j >= 6) return;
-  const LightDev& Ld = lights[l];
+  if (u >= n_user || j >= 6) return;
   float acc = 0.f;
-  for (int k = 0; k < 20; ++k) acc += gQ[l * 20 + k] * Ld.J[k * 6 + j];
-  const float* gd = gdirect + 3 * l;
-  if (Ld.type == 1) {
-    if (j < 3) acc += gd[j];
-  } else if (j >= 3) {
-    const int c = j - 3;
-    const float* f = Ld.fwd;
-    const float fg = f[0] * gd[0] + f[1] * gd[1] + f[2] * gd[2];
-    acc += -(gd[c] - f[c] * fg) / Ld.dir_norm;
+  for (int l = 0; l < L; ++l) {
+    const LightDev& Ld = lights[l];
+    if (Ld.user != u) continue;
+    for (int k = 0; k < 20; ++k) acc += gQ[l * 20 + k] * Ld.J[k * 6 + j];
+    const float* gd = gdirect + 3 * l;
+    if (Ld.type == 1) {
+      if (j < 3) acc += gd[j];
+    } else if (j >= 3) {
+      const int c = j - 3;
+      const float* f = Ld.fwd;
+      const float fg = f[0] * gd[0] + f[1] * gd[1] + f[2] * gd[2];
+      acc += -(gd[c] - f[c] * fg) / Ld.dir_norm;
+    }
   }
-  dlight[l * 6 + j] = acc;
+  dlight[u * 6 + j] = acc;
 }
 
 __global__ void l2_kernel(const float* __restrict__ img, const float* __restrict__ tgt, int64_t n,
@@ -707,11 +729,11 @@ void launch_red_reduce(const float* red, int red_stride, int L, int n_mat_red, f
   red_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(red, red_stride, L, n_mat_red, gQ, gdirect, dalbedo);
 }
 
-void launch_light_grad(const LightDev* lights, int L, const float* gQ, const float* gdirect, float* dlight,
-                       cudaStream_t st) {
-  if (L == 0) return;
+void launch_light_grad(const LightDev* lights, int L, int n_user, const float* gQ, const float* gdirect,
+                       float* dlight, cudaStream_t st) {
+  if (n_user == 0) return;
   count_launches(1);
-  light_grad_kernel<<<L, 32, 0, st>>>(lights, L, gQ, gdirect, dlight);
+  light_grad_kernel<<<n_user, 32, 0, st>>>(lights, L, n_user, gQ, gdirect, dlight);
 }
 
 void launch_l2(const float* img, const float* tgt, int64_t n, float* loss, float* grad, cudaStream_t st) {

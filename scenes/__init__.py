@@ -30,7 +30,7 @@ import numpy as np
 
 __all__ = [
     "icosphere", "subdivided_box", "ground_quad", "sh_displace", "random_rotation",
-    "look_at_perspective", "directional_light", "spot_light", "merge_meshes",
+    "look_at_perspective", "directional_light", "spot_light", "point_light", "merge_meshes",
     "config1", "config2", "config3", "config4", "config5", "config_by_name",
     "tiny_scene", "jitter_vertices", "displaced_target", "minimal_plane",
 ]
@@ -124,6 +124,20 @@ def ground_quad(half: float, y: float) -> tuple[np.ndarray, np.ndarray]:
     return v, t
 
 
+def ground_grid(half: float, y: float, n: int) -> tuple[np.ndarray, np.ndarray]:
+    """Square receiver at height y split into n x n quads (2 n^2 triangles),
+    normal +Y.  Scenes lit by a point light use it: a view drops a triangle
+    with a vertex behind its eye plane, so no triangle may be larger than the
+    light's near distance (then only points that no cube face shades are lost)."""
+    g = np.linspace(-half, half, n + 1)
+    X, Z = np.meshgrid(g, g, indexing="xy")
+    v = np.stack([X.ravel(), np.full(X.size, y), Z.ravel()], 1)
+    idx = np.arange((n + 1) ** 2).reshape(n + 1, n + 1)
+    a, b, c, d = idx[:-1, :-1].ravel(), idx[:-1, 1:].ravel(), idx[1:, 1:].ravel(), idx[1:, :-1].ravel()
+    t = np.concatenate([np.stack([a, c, b], 1), np.stack([a, d, c], 1)])   # normal (0, +1, 0)
+    return v, t
+
+
 def _real_sh_basis(n: np.ndarray) -> np.ndarray:
     """Real spherical-harmonic polynomials of degree 1..3 (15 functions,
     unnormalised) evaluated at unit vectors n (N, 3)."""
@@ -209,6 +223,16 @@ def spot_light(position, direction, res, fov_y_deg, near, far, sigma,
     """Spot light: perspective shadow camera at the light position facing dir."""
     return {"type": 1, "pos": np.asarray(position, np.float32), "dir": np.asarray(direction, np.float32),
             "res": int(res), "fov_y_deg": float(fov_y_deg), "ortho_half": 0.0, "dist": 0.0,
+            "near": float(near), "far": float(far), "intensity": np.asarray(intensity, np.float32),
+            "sigma": float(sigma), "radius": int(radius)}
+
+
+def point_light(position, res, near, far, sigma, intensity=(1.0, 1.0, 1.0), radius=0) -> dict:
+    """Omnidirectional point light: a cube shadow map of six 90-degree
+    perspective faces at the light position (res x res texels per face).  The
+    direction slot of its parameters is unused."""
+    return {"type": 2, "pos": np.asarray(position, np.float32), "dir": np.array([0.0, -1.0, 0.0], np.float32),
+            "res": int(res), "fov_y_deg": 90.0, "ortho_half": 0.0, "dist": 0.0,
             "near": float(near), "far": float(far), "intensity": np.asarray(intensity, np.float32),
             "sigma": float(sigma), "radius": int(radius)}
 
@@ -357,11 +381,14 @@ def tiny_scene(seed: int = 0, res: int = 32, img: int = 32, kind: str = "directi
     rng = np.random.default_rng(77_000 + seed)
     sv, st = icosphere(freq)
     sv = sv @ random_rotation(rng).T * 0.6 + np.array([0.1, 1.0, -0.1])
-    gv, gt = ground_quad(2.0, 0.0)
+    gv, gt = ground_grid(2.0, 0.0, 16) if kind in ("point", "mixed3") else ground_quad(2.0, 0.0)
     verts, tris, mat = merge_meshes([(sv, st, 0), (gv, gt, 1)])
     lights = []
     for li in range(n_lights):
-        if kind == "spot" or (kind == "mixed" and li % 2 == 1):
+        if kind == "point" or (kind == "mixed3" and li == 2):
+            p = np.array([1.0, 1.6, 0.8]) + rng.uniform(-0.1, 0.1, 3)   # the shadow spans three cube faces
+            lights.append(point_light(p, res, near=0.3, far=8.0, sigma=1.0, intensity=(0.8, 0.8, 0.8)))
+        elif kind == "spot" or (kind in ("mixed", "mixed3") and li % 2 == 1):
             p = np.array([0.6, 4.0, 0.5]) + rng.uniform(-0.3, 0.3, 3)
             lights.append(spot_light(p, -p / np.linalg.norm(p), res, 80.0, near=0.5, far=8.0,
                                      sigma=1.0, intensity=(0.8, 0.8, 0.8)))

@@ -63,7 +63,9 @@ class GpuRun:
         self.r = dsm.Renderer(scene)
         self.image = self.r.forward()
         self.r.ctx.sync()
-        self.L = len(scene["lights"])
+        # light views: one per directional or spot light, six cube faces per point light
+        self.view_light = [l for l, Lt in enumerate(scene["lights"]) for _ in range(6 if Lt["type"] == 2 else 1)]
+        self.L = len(self.view_light)
         self.target = target
         if target is not None:
             tgt = torch.as_tensor(np.asarray(target, np.float32), device="cuda").contiguous()
@@ -75,7 +77,7 @@ class GpuRun:
 
     def view_size(self, w):
         if w < self.L:
-            R = self.scene["lights"][w]["res"]
+            R = self.scene["lights"][self.view_light[w]]["res"]
             return R, R
         return self.scene["camera"]["width"], self.scene["camera"]["height"]
 
@@ -92,7 +94,7 @@ class GpuRun:
         return si[:, 0].astype(np.int64), si[:, 1].astype(np.int64), s[:, 2].numpy(), si[:, 3]
 
     def light_map(self, what, l):
-        R = self.scene["lights"][l]["res"]
+        R = self.scene["lights"][self.view_light[l]]["res"]
         return self.r.ctx.debug(what, l, (R, R, 2)).cpu().numpy()
 
     def color(self):

@@ -27,6 +27,8 @@ SCENES = {
     "tiny_mixed": lambda: scenes.tiny_scene(2, res=33, img=40, kind="mixed", n_lights=2),
     "tiny_freq3": lambda: _ragged_camera(scenes.tiny_scene(4, res=70, img=64, freq=3), 64, 50),
     "config1": scenes.config1,
+    "tiny_point": lambda: scenes.tiny_scene(5, res=32, img=48, kind="point"),
+    "tiny_mixed3": lambda: _ragged_camera(scenes.tiny_scene(6, res=40, img=44, kind="mixed3", n_lights=3), 44, 37),
 }
 
 _cache = {}
@@ -91,7 +93,7 @@ def test_shadow_map_antialias_stagewise(case):
     for l, L in enumerate(ref["lights"]):
         fg = gpu.light_map(gpu.dsm.DBG_F, l)
         ftg = gpu.light_map(gpu.dsm.DBG_FTILDE, l)
-        R = sc["lights"][l]["res"]
+        R = sc["lights"][L["light"]]["res"]
         vh = torch.cat([torch.as_tensor(sc["verts"], dtype=F64), torch.ones((len(sc["verts"]), 1), dtype=F64)], 1)
         clip = vh @ L["Q"].detach()[:4].T
         sx, sy = O.screen_coords(clip, R, R)

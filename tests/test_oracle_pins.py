@@ -669,3 +669,63 @@ def test_minimal_plane_needs_antialiased_shadow_map():
     err_no, g_no, _ = _minimal_plane_descent(0, 20)
     assert abs(err_no - 1.0) < 1e-9
     assert np.linalg.norm(g_no) < 1e-12 * np.linalg.norm(g_aa)
+
+
+# ----------------------------------------------------------------------------- point lights (cube maps)
+def test_cube_faces_closed_form():
+    """Each cube face of a point light at p is the 90-degree perspective view
+    along its axis: a point x of the face's region projects inside the face
+    (|u|, |v| <= 1, w > 0), the face-centre direction to (0, 0), and its depth
+    is (|major component of x - p| - near) / (far - near)."""
+    light = scenes.point_light((0.3, 1.1, -0.4), 64, near=0.2, far=9.0, sigma=1.0)
+    p = torch.as_tensor(light["pos"], dtype=F64)
+    rng = np.random.default_rng(11)
+    d = rng.normal(size=(400, 3)) * rng.uniform(0.5, 4.0, (400, 1))
+    faces = O.cube_face(d)
+    assert set(faces.tolist()) == set(range(6))
+    x = torch.as_tensor(d, dtype=F64) + p
+    xh = torch.cat([x, torch.ones((400, 1), dtype=F64)], 1)
+    near, far = float(np.float32(0.2)), float(np.float32(9.0))
+    for k in range(6):
+        Q = O.light_matrix(light, p, torch.tensor([0.0, -1.0, 0.0], dtype=F64), face=k)
+        sel = faces == k
+        cl = xh[sel] @ Q[:4].T
+        assert (cl[:, 3] > 0).all()
+        assert (cl[:, 0].abs() <= cl[:, 3] * (1 + 1e-12)).all() and (cl[:, 1].abs() <= cl[:, 3] * (1 + 1e-12)).all()
+        major = np.abs(d[sel]).max(1)
+        np.testing.assert_allclose((xh[sel] @ Q[4]).numpy(), (major - near) / (far - near), rtol=1e-12, atol=1e-12)
+        centre = torch.cat([p + torch.tensor(O.CUBE_AXES[k], dtype=F64), torch.ones(1, dtype=F64)])
+        cc = Q[:4] @ centre
+        assert abs(float(cc[0] / cc[3])) < 1e-12 and abs(float(cc[1] / cc[3])) < 1e-12
+        # the direction parameter does not enter a face
+        Q2 = O.light_matrix(light, p, torch.tensor([0.3, 0.2, 0.9], dtype=F64), face=k)
+        assert torch.equal(Q, Q2)
+
+
+def test_point_light_over_scene_equals_spot_light():
+    """With every shaded point in the -Y face of the cube, a point light is a
+    spot light at the same position looking down with a 90-degree field of
+    view (same camera up to the rounding of 1 / tan 45 degrees)."""
+    sc = scenes.tiny_scene(5, res=40, img=40, kind="point")
+    sc["lights"][0]["pos"] = np.array([0.1, 3.5, -0.1], np.float32)
+    spot = dict(sc)
+    spot["lights"] = [scenes.spot_light(sc["lights"][0]["pos"], (0.0, -1.0, 0.0), 40, 90.0, near=0.3, far=8.0,
+                                        sigma=1.0, intensity=(0.8, 0.8, 0.8))]
+    tgt = np.zeros((40, 40, 4))
+    a = O.render_and_grad(sc, tgt)
+    b = O.render_and_grad(spot, tgt)
+    assert len([L for L in a["lights"] if (L["raster"]["ids"] > 0).any()]) >= 1
+    np.testing.assert_allclose(a["image"].detach().numpy(), b["image"].detach().numpy(), atol=1e-9)
+    np.testing.assert_allclose(a["grad_verts"].numpy(), b["grad_verts"].numpy(), atol=1e-9, rtol=1e-6)
+    np.testing.assert_allclose(a["grad_light"].numpy()[0, :3], b["grad_light"].numpy()[0, :3], atol=1e-9, rtol=1e-6)
+    assert np.all(a["grad_light"].numpy()[0, 3:] == 0.0)
+
+
+@pytest.mark.parametrize("kind,seed", [("point", 5), ("mixed3", 6)])
+def test_central_fd_point_lights(kind, seed):
+    """Finite differences through cube maps: the shadow spans three faces of
+    the cube (the face choice is a decision, piecewise constant)."""
+    sc = scenes.tiny_scene(seed, res=32, img=32, kind=kind, n_lights=3 if kind == "mixed3" else 1)
+    tgt = O.render(sc, verts=torch.as_tensor(scenes.jitter_vertices(sc, 0.03, seed + 10), dtype=F64),
+                   keep=False)["image"].detach()
+    _fd_check(sc, tgt, seed, h_vert=1e-6, h_light=1e-6, tol=1e-3)
