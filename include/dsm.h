@@ -116,6 +116,12 @@ typedef struct dsm_params {
   int32_t recompute_in_backward; /* 0: keep every view's buffers from forward to backward;
                                    * 1: views share one light and one camera buffer set and
                                    * the backward rebuilds what it reads (see dsm_render_cameras) */
+  int32_t moments;          /* pre-filtered moment family: 0 variance shadow maps (f, f^2);
+                             * 1 exponential variance shadow maps (w, w^2), w = exp(c f):
+                             * the same antialiasing and filter, the Chebyshev bound on the
+                             * warped depth exp(c d) with the floor min_variance (c exp(c d))^2
+                             * (less light bleeding where occluder depths vary)          */
+  float   exponent;         /* c of moments = 1, in (0, 40] (w^2 stays finite in float32)   */
   void*   stream;           /* cudaStream_t; NULL = legacy default stream                   */
 } dsm_params;
 

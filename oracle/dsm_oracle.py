@@ -49,7 +49,7 @@ W_MIN = np.float32(1e-6)
 __all__ = [
     "light_matrix", "light_views", "cube_face", "clip_pinned", "setup_view", "raster", "edge_adjacency", "silhouette_table",
     "barycentrics", "antialias", "filter_weights", "separable_filter", "bilinear",
-    "chebyshev", "light_visibility", "vertex_normals", "render", "mse_loss", "render_and_grad",
+    "chebyshev", "moment_encode", "warp_exponent", "light_visibility", "vertex_normals", "render", "mse_loss", "render_and_grad",
     "render_cameras_and_grad", "adam_step",
 ]
 
@@ -507,12 +507,15 @@ def bilinear(m: torch.Tensor, s: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
             + ((1 - fs) * ft)[:, None] * m[j1c, i0c] + (fs * ft)[:, None] * m[j1c, i1c])
 
 
-def chebyshev(d: torch.Tensor, m1: torch.Tensor, m2: torch.Tensor, min_variance: float) -> torch.Tensor:
+def chebyshev(d: torch.Tensor, m1: torch.Tensor, m2: torch.Tensor, min_variance) -> torch.Tensor:
     """Modified one-sided Chebyshev (Cantelli) visibility of Sec. 3 / Alg. 2:
     1 if d <= mu, else sigma^2 / (sigma^2 + (d - mu)^2), mu = m1,
-    sigma^2 = max(m2 - m1^2, min_variance).  reading: the variance floor is
-    standard variance-shadow-map practice; the paper does not state it."""
-    var = torch.clamp(m2 - m1 * m1, min=min_variance)
+    sigma^2 = max(m2 - m1^2, min_variance) (a number, or one per point).
+    reading: the variance floor is standard variance-shadow-map practice; the
+    paper does not state it."""
+    raw = m2 - m1 * m1
+    floor = torch.as_tensor(min_variance, dtype=F64).expand_as(raw)
+    var = torch.where(raw >= floor, raw, floor)
     delta = d - m1
     lit = delta <= 0
     dpos = torch.where(lit, torch.zeros_like(delta), delta)
@@ -520,12 +523,26 @@ def chebyshev(d: torch.Tensor, m1: torch.Tensor, m2: torch.Tensor, min_variance:
     return torch.where(lit, torch.ones_like(var), var / denom)
 
 
-def light_visibility(Q: torch.Tensor, mom: torch.Tensor, xh: torch.Tensor, min_variance: float) -> torch.Tensor:
+def moment_encode(f: torch.Tensor, exponent: float = 0.0) -> torch.Tensor:
+    """The two moment channels of depth samples f: (w, w^2) with w = f
+    (variance shadow maps, Sec. 3) or w = exp(c f) for the exponential warp
+    (c = exponent > 0), one of the other pre-filtered families the paper
+    suggests against light bleeding (its discussion of limitations).
+    reading: exponential variance shadow maps with the positive warp only."""
+    w = torch.exp(exponent * f) if exponent > 0 else f
+    return torch.stack([w, w * w], -1)
+
+
+def light_visibility(Q: torch.Tensor, mom: torch.Tensor, xh: torch.Tensor, min_variance: float,
+                     exponent: float = 0.0) -> torch.Tensor:
     """Alg. 2 (ComputeVisibility) at homogeneous world points xh (n, 4):
     u = L(x) from the light clip matrix Q[0:4], texel coordinates
     s = (0.5 u_x + 0.5) R - 0.5 and t = (0.5 - 0.5 u_y) R - 0.5, bilinear (m1, m2),
     d = Q[4] . xh, then the Chebyshev visibility.
-    reading: points behind the light or outside its window are lit (v = 1)."""
+    reading: points behind the light or outside its window are lit (v = 1).
+    With the exponential warp (exponent c > 0) the receiver depth is compared
+    as exp(c d) and the floor is min_variance (c exp(c d))^2 (reading: the
+    depth-unit floor carried by the warp's slope at the receiver)."""
     R = mom.shape[0]
     cl = xh @ Q[:4].T
     d = xh @ Q[4]
@@ -537,7 +554,11 @@ def light_visibility(Q: torch.Tensor, mom: torch.Tensor, xh: torch.Tensor, min_v
     t = (0.5 - 0.5 * v) * R - 0.5
     zero = torch.zeros_like(s)
     mm = bilinear(mom, torch.where(inside, s, zero), torch.where(inside, t, zero))
-    vis = chebyshev(d, mm[:, 0], mm[:, 1], min_variance)
+    if exponent > 0:
+        dw = torch.exp(exponent * d)
+        vis = chebyshev(dw, mm[:, 0], mm[:, 1], min_variance * (exponent * dw) ** 2)
+    else:
+        vis = chebyshev(d, mm[:, 0], mm[:, 1], min_variance)
     return torch.where(inside, vis, torch.ones_like(vis))
 
 
@@ -561,6 +582,12 @@ def _substitute(value: torch.Tensor, teacher) -> torch.Tensor:
     return value + (tv - value).detach()
 
 
+def warp_exponent(params: dict) -> float:
+    """Exponent c of the moments' warp: params 'moments' = 1 selects the
+    exponential family with c = params 'exponent'; 0 (default) is VSM."""
+    return float(np.float32(params.get("exponent", 0.0))) if int(params.get("moments", 0)) == 1 else 0.0
+
+
 def _teacher_view(teacher: dict, key: str, view: int):
     vals = teacher.get(key)
     return vals[view] if vals is not None and view < len(vals) else None
@@ -582,6 +609,7 @@ def shade_pixels(scene: dict, verts: torch.Tensor, light_params: torch.Tensor, a
     n = (b[:, :, None] * vn[tv]).sum(1)
     n = n / torch.sqrt((n * n).sum(1, keepdim=True))
     xh = torch.cat([x, torch.ones((x.shape[0], 1), dtype=F64)], 1)
+    ec = warp_exponent(P)
     radiance = torch.zeros((x.shape[0], 3), dtype=F64)
     vis_all = []
     for li, light in enumerate(scene["lights"]):
@@ -591,10 +619,10 @@ def shade_pixels(scene: dict, verts: torch.Tensor, light_params: torch.Tensor, a
             face = torch.as_tensor(cube_face((x - light_params[li, 0:3][None, :]).detach().numpy()))
             vis = torch.zeros((x.shape[0],), dtype=F64)
             for k, (Q, mom) in enumerate(views):
-                vis = torch.where(face == k, light_visibility(Q, mom, xh, float(P["min_variance"])), vis)
+                vis = torch.where(face == k, light_visibility(Q, mom, xh, float(P["min_variance"]), ec), vis)
         else:
             Q, mom = views[0]
-            vis = light_visibility(Q, mom, xh, float(P["min_variance"]))
+            vis = light_visibility(Q, mom, xh, float(P["min_variance"]), ec)
         if int(light["type"]) == 0:
             dl = light_params[li, 3:6]
             omega = -(dl / torch.sqrt((dl * dl).sum()))[None, :].expand_as(x)
@@ -650,8 +678,10 @@ def render(scene: dict, verts: torch.Tensor = None, light_params: torch.Tensor =
             depth = vh @ Q[4]
             jj, ii, tri, b = barycentrics(clip, tris, ras["ids"])
             f = (b * depth[tris[tri]]).sum(1)
-            fmap = torch.ones((R, R, 2), dtype=F64)
-            fmap = fmap.index_put((torch.as_tensor(jj), torch.as_tensor(ii)), torch.stack([f, f * f], 1))
+            ec = warp_exponent(P)
+            # background texels hold the encoding of f = 1
+            fmap = moment_encode(torch.ones((R, R), dtype=F64), ec)
+            fmap = fmap.index_put((torch.as_tensor(jj), torch.as_tensor(ii)), moment_encode(f, ec))
             if P.get("aa_shadow", 1):
                 sil = silhouette_table(adj, st)
                 sx, sy = screen_coords(clip, R, R)

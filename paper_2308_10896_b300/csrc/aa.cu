@@ -397,12 +397,13 @@ __global__ void __launch_bounds__(256) aa_backward4_list_kernel(AAArgs a, const 
 
 // Adjoint of the shadow-map antialiasing at the listed texels: dL/d(f, f^2)
 // (the pair t-gradients go to the light-space clip coordinates of the edge
-// endpoints), folded into dL/df = g.x + 2 f g.y (f^2 = f f).  The filter
-// transpose already wrote dL/df at every other texel.
+// endpoints), folded into dL/df by moment_fold (the product rule of the
+// second channel, times the warp's slope).  The filter transpose already
+// wrote dL/df at every other texel.
 __global__ void __launch_bounds__(256) sm_aa_adjoint_list_kernel(AAArgs a, const float2* __restrict__ fmap,
                                                                  const float2* __restrict__ gft,
                                                                  float4* __restrict__ gclip,
-                                                                 float* __restrict__ gf_out, AAWork w) {
+                                                                 float* __restrict__ gf_out, float ec, AAWork w) {
   for_listed_pairs(w, [&](int k, int d, bool act) {
     float2 g = make_float2(0.f, 0.f), g_p = g;
     int p = 0;
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(256) sm_aa_adjoint_list_kernel(AAArgs a, const
     g = vadd(g, shfl_xor_v(g, 2));
     if (act && d == 0) {
       const float2 gc = vadd(g_p, g);
-      gf_out[p] = gc.x + 2.f * fmap[p].x * gc.y;
+      gf_out[p] = moment_fold(gc, fmap[p].x, ec);
     }
   });
 }
@@ -551,9 +552,9 @@ void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, uint8
   aa_forward_list_kernel<float4><<<kListGrid, 256, 0, st>>>(a, color, out, w);
 }
 void launch_sm_aa_adjoint_list(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
-                               const AAWork& w, cudaStream_t st) {
+                               float ec, const AAWork& w, cudaStream_t st) {
   count_launches(1);
-  sm_aa_adjoint_list_kernel<<<kListGrid, 256, 0, st>>>(a, fmap, gft, gclip, gf_out, w);
+  sm_aa_adjoint_list_kernel<<<kListGrid, 256, 0, st>>>(a, fmap, gft, gclip, gf_out, ec, w);
 }
 
 void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* depth, float4* gclip,

@@ -102,6 +102,21 @@ __device__ __forceinline__ float2 screen_of(float4 c, int W, int H) {
 }
 
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+// Moment channels of a shadow-map depth sample f: (w, w^2) with w = f
+// (variance shadow maps) or w = exp(ec f) (exponential variance shadow maps,
+// ec > 0: the exponent c of the warp).
+__device__ __forceinline__ float2 moment_encode(float f, float ec) {
+  const float w = ec > 0.f ? expf(ec * f) : f;
+  return make_float2(w, w * w);
+}
+
+// dL/df of a texel from the gradient g of its channels (w, w^2): the product
+// rule of w^2 = w w, times dw/df (1, or ec w for the exponential warp).
+__device__ __forceinline__ float moment_fold(float2 g, float w, float ec) {
+  const float gw = g.x + 2.f * w * g.y;
+  return ec > 0.f ? gw * (ec * w) : gw;
+}
+
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 f2scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) {

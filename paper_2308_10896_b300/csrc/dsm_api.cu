@@ -412,6 +412,9 @@ static dsm_status check_args(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light
   if (params->recompute_in_backward != 0 && params->recompute_in_backward != 1)
     return fail(ctx, DSM_ERR_INVALID_ARG, "recompute_in_backward");
   if (!(params->min_variance >= 0.f)) return fail(ctx, DSM_ERR_INVALID_ARG, "min_variance");
+  if (params->moments != 0 && params->moments != 1) return fail(ctx, DSM_ERR_INVALID_ARG, "moments");
+  if (params->moments == 1 && !(params->exponent > 0.f && params->exponent <= 40.f))
+    return fail(ctx, DSM_ERR_INVALID_ARG, "exponent of the exponential moments outside (0, 40]");
   return DSM_OK;
 }
 
@@ -508,6 +511,9 @@ dsm_status grow_list(dsm_ctx* ctx, ViewBufs& v, long long need) {
   return DSM_OK;
 }
 
+// Exponent of the moments' warp (0: variance shadow maps).
+float warp_exponent(const dsm_ctx* ctx) { return ctx->params.moments == 1 ? ctx->params.exponent : 0.f; }
+
 AAArgs aa_args(const dsm_ctx* ctx, ViewBufs& v) {
   return AAArgs{v.gbuf.as<float4>(), v.W, v.H, ctx->mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(),
                 v.clip.as<float4>()};
@@ -558,7 +564,8 @@ void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
   StageTimer t(ctx, ST_RASTER, st);
   launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,
                 v.bs.tile_log2, v.W, v.H, v.clip.as<float4>(), ctx->mesh.tris, v.gbuf.as<float4>(),
-                light ? v.depth.as<float>() : nullptr, light ? lwork(ctx, w).fmap.as<float2>() : nullptr, st);
+                light ? v.depth.as<float>() : nullptr, light ? lwork(ctx, w).fmap.as<float2>() : nullptr,
+                warp_exponent(ctx), st);
 }
 
 // Alg. 1 after the raster: antialiasing of f, f^2 at the listed texels, then
@@ -595,6 +602,7 @@ ShadeArgs shade_args(dsm_ctx* ctx, int c) {
   sa.lights = ctx->lights_dev.as<LightDev>(); sa.L = ctx->L;
   for (int l = 0; l < ctx->L; ++l) { sa.mom[l] = ctx->light[l].mom.as<float2>(); sa.res[l] = ctx->light[l].res; }
   sa.min_variance = ctx->params.min_variance;
+  sa.ec = warp_exponent(ctx);
   return sa;
 }
 
@@ -674,13 +682,13 @@ void light_backward(dsm_ctx* ctx, int l, cudaStream_t st) {
   {
     StageTimer t(ctx, ST_BWD_FILTER, st);
     launch_filter_adjoint(lb.gm.as<float2>(), wk.tmp.as<float2>(), wk.gft.as<float2>(), v.W, lb.fa, st,
-                          wk.fmap.as<float2>(), wk.tmp.as<float>());
+                          wk.fmap.as<float2>(), wk.tmp.as<float>(), warp_exponent(ctx));
   }
   {
     StageTimer t(ctx, ST_BWD_SM_AA, st);
     if (ctx->params.aa_shadow)
       launch_sm_aa_adjoint_list(aa, wk.fmap.as<float2>(), wk.gft.as<float2>(), v.gclip.as<float4>(),
-                                wk.tmp.as<float>(), v.aa_work(), st);
+                                wk.tmp.as<float>(), warp_exponent(ctx), v.aa_work(), st);
   }
   StageTimer t(ctx, ST_BWD_SM_INTERP, st);
   BigArgs big{v.big_index.as<int>(), v.big_tri.as<int>(), v.big_acc.as<float>(), ctx->status.as<DevStatus>(), l};

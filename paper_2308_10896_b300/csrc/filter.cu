@@ -147,12 +147,14 @@ __device__ __forceinline__ void tap_run(const float2* src, int step, const Filte
 // Extras of the shadow-map path (NULL for a plain filter):
 //   forward: the input is (f, f^2) except where hflag marks a texel whose
 //     antialiased value the antialiasing pass wrote into patch;
-//   adjoint: also writes dL/df = g.x + 2 f g.y of the output g (f from fmap).
+//   adjoint: also writes dL/df of the output g (moment_fold of g with the
+//     first channel of fmap and the warp exponent ec).
 struct FilterExtras {
   const uint8_t* hflag;
   const float2* patch;
   const float2* fmap;
   float* gf;
+  float ec;
 };
 
 template <int kR, bool kAdjoint>
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(256) filter_tile_kernel(const float2* __restri
         if (gy < R) {
           const size_t q = (size_t)gy * R + gx;
           out[q] = acc[u];
-          if (kAdjoint && ex.gf) ex.gf[q] = acc[u].x + 2.f * ex.fmap[q].x * acc[u].y;
+          if (kAdjoint && ex.gf) ex.gf[q] = moment_fold(acc[u], ex.fmap[q].x, ex.ec);
         }
       }
     }
@@ -249,9 +251,9 @@ __global__ void compose_kernel(const float2* __restrict__ fmap, const uint8_t* _
   if (p < n) out[p] = hflag[p] ? patch[p] : fmap[p];
 }
 __global__ void fold_kernel(const float2* __restrict__ fmap, const float2* __restrict__ g, float* __restrict__ gf,
-                            int n) {
+                            int n, float ec) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) gf[p] = g[p].x + 2.f * fmap[p].x * g[p].y;
+  if (p < n) gf[p] = moment_fold(g[p], fmap[p].x, ec);
 }
 static_assert(kFT * kFT == 256 * kYRun, "one y-pass run per thread");
 static_assert(TileGeom<kFRmax>::S * (kFT / kXRun) <= 256, "one x-pass pass over the threads for every radius");
@@ -280,7 +282,7 @@ void launch_compose(const float2* fmap, const uint8_t* hflag, const float2* patc
 
 void launch_filter(const float2* in, float2* tmp, float2* out, int R, const FilterArgs& fa, cudaStream_t st,
                    const uint8_t* hflag, const float2* patch) {
-  const FilterExtras ex{hflag, patch, nullptr, nullptr};
+  const FilterExtras ex{hflag, patch, nullptr, nullptr, 0.f};
   if (fa.shape == 0 && launch_tiled_r<1>(false, in, out, R, fa, ex, st)) return;
   dim3 b(32, 8), g((R + 31) / 32, (R + 7) / 8);
   if (hflag) {
@@ -297,8 +299,8 @@ void launch_filter(const float2* in, float2* tmp, float2* out, int R, const Filt
 }
 
 void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, const FilterArgs& fa,
-                           cudaStream_t st, const float2* fmap, float* gf) {
-  const FilterExtras ex{nullptr, nullptr, fmap, gf};
+                           cudaStream_t st, const float2* fmap, float* gf, float ec) {
+  const FilterExtras ex{nullptr, nullptr, fmap, gf, ec};
   if (fa.shape == 0 && launch_tiled_r<1>(true, gout, gin, R, fa, ex, st)) return;
   dim3 b(32, 8), g((R + 31) / 32, (R + 7) / 8);
   count_launches(1);
@@ -308,7 +310,7 @@ void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, 
   if (gf) {
     const int n = R * R;
     count_launches(1);
-    fold_kernel<<<(n + 255) / 256, 256, 0, st>>>(fmap, gin, gf, n);
+    fold_kernel<<<(n + 255) / 256, 256, 0, st>>>(fmap, gin, gf, n, ec);
   }
 }
 

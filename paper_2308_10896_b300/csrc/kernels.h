@@ -63,6 +63,7 @@ struct ShadeArgs {
   const float2* mom[kMaxLightViews];
   int res[kMaxLightViews];
   float min_variance;
+  float ec;                           // exponential warp of the moments (0: variance shadow maps)
 };
 
 struct ShadeGradArgs {
@@ -138,7 +139,7 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int*
 // of every texel, f interpolated from the per-vertex light depths.
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
                    int tile_log2, int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth,
-                   float2* fmap, cudaStream_t st);
+                   float2* fmap, float ec, cudaStream_t st);
 
 // shadow-map interpolation and antialiasing
 // Antialiasing (detection + list passes, see aa.cu).
@@ -147,7 +148,7 @@ void launch_aa_forward2_list(const AAArgs& a, const float2* color, float2* out, 
 void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, uint8_t* hflag, const AAWork& w,
                         cudaStream_t st);
 void launch_sm_aa_adjoint_list(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
-                               const AAWork& w, cudaStream_t st);
+                               float ec, const AAWork& w, cudaStream_t st);
 void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
                          const uint8_t* hflag, const AAWork& w, cudaStream_t st);
 void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* depth, float4* gclip,
@@ -164,8 +165,10 @@ void launch_filter(const float2* in, float2* tmp, float2* out, int R, const Filt
 void launch_compose(const float2* fmap, const uint8_t* hflag, const float2* patch, float2* out, int n,
                     cudaStream_t st);
 // gin = G^T gout; with gf (shadow-map path) also dL/df = gin.x + 2 f gin.y.
+// With fmap and gf: also writes gf = dL/df of every texel from the result
+// (moment_fold with the warp exponent ec).
 void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, const FilterArgs& fa, cudaStream_t st,
-                           const float2* fmap = nullptr, float* gf = nullptr);
+                           const float2* fmap = nullptr, float* gf = nullptr, float ec = 0.f);
 
 // normals, shading, vertex gradients
 void launch_vertex_normals(const float* verts, int V, const int* tris, const int* vf_off, const int* vf_list,

@@ -544,7 +544,8 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
                                                      const int* __restrict__ list, int capacity, int tilesX,
                                                      int W, int H, const float4* __restrict__ clip,
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf,
-                                                     const float* __restrict__ depth, float2* __restrict__ fmap) {
+                                                     const float* __restrict__ depth, float2* __restrict__ fmap,
+                                                     float ec) {
   constexpr int kTile = 1 << kTL;
   constexpr int kPix = kTile * kTile;
   static_assert(kTile <= 32, "tile-local coordinates are packed in 5 bits");
@@ -668,7 +669,7 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
       }
     }
     gbuf[(size_t)j * W + i] = out;
-    if (fmap) fmap[(size_t)j * W + i] = make_float2(f, f * f);
+    if (fmap) fmap[(size_t)j * W + i] = moment_encode(f, ec);
   }
 }
 
@@ -725,14 +726,14 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int*
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
                    int tile_log2, int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth,
-                   float2* fmap, cudaStream_t st) {
+                   float2* fmap, float ec, cudaStream_t st) {
   count_launches(1);
   if (tile_log2 == 4)
     raster_kernel<4><<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf,
-                                                      depth, fmap);
+                                                      depth, fmap, ec);
   else
     raster_kernel<5><<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf,
-                                                      depth, fmap);
+                                                      depth, fmap, ec);
 }
 
 }  // namespace dsm

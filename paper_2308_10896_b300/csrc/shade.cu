@@ -163,10 +163,14 @@ __device__ __forceinline__ void surf_from(const float4 g, const TriCache& c, Sur
 }
 
 // Lookup of Alg. 2 for one light at world point x: clip, depth d, texel
-// coordinates, bilinear (m1, m2), visibility.
+// coordinates, bilinear (m1, m2), visibility.  With the exponential warp
+// (ec > 0) the receiver depth is compared as dw = exp(ec d) and the variance
+// floor is min_var (ec dw)^2 (the depth-unit floor carried by the warp's
+// slope at the receiver).
 struct Look {
   float4 clip;
   float d;
+  float dw;              // receiver depth in the moments' encoding
   int inside;
   int i0, j0;            // floor of the texel coordinates
   float fs, ft;
@@ -178,11 +182,12 @@ struct Look {
 };
 
 __device__ __forceinline__ Look lookup(const float* Q, const float2* __restrict__ mom, int R, float3 x,
-                                       float min_var) {
+                                       float min_var, float ec) {
   Look L;
   L.clip = make_float4(Q[0] * x.x + Q[1] * x.y + Q[2] * x.z + Q[3], Q[4] * x.x + Q[5] * x.y + Q[6] * x.z + Q[7],
                        Q[8] * x.x + Q[9] * x.y + Q[10] * x.z + Q[11], Q[12] * x.x + Q[13] * x.y + Q[14] * x.z + Q[15]);
   L.d = Q[16] * x.x + Q[17] * x.y + Q[18] * x.z + Q[19];
+  L.dw = ec > 0.f ? expf(ec * L.d) : L.d;
   L.vis = 1.f;
   L.inside = 0;
   if (!(L.clip.w > 0.f)) return L;
@@ -202,9 +207,10 @@ __device__ __forceinline__ Look lookup(const float* Q, const float2* __restrict_
   L.m = make_float2(w00 * m00.x + w01 * m01.x + w10 * m10.x + w11 * m11.x,
                     w00 * m00.y + w01 * m01.y + w10 * m10.y + w11 * m11.y);
   const float raw = fmaf(-L.m.x, L.m.x, L.m.y);
-  L.var_clamped = !(raw >= min_var);
-  L.var = L.var_clamped ? min_var : raw;
-  L.delta = L.d - L.m.x;
+  const float floor_var = ec > 0.f ? min_var * (ec * L.dw) * (ec * L.dw) : min_var;
+  L.var_clamped = !(raw >= floor_var);
+  L.var = L.var_clamped ? floor_var : raw;
+  L.delta = L.dw - L.m.x;
   L.vis = L.delta <= 0.f ? 1.f : L.var / (L.var + L.delta * L.delta);
   return L;
 }
@@ -245,7 +251,7 @@ __global__ void shade_kernel(ShadeArgs a, float4* __restrict__ color) {
   for (int l = 0; l < a.L; ++l) {
     const LightDev& Ld = a.lights[l];
     if (!view_shades(Ld, s.x)) continue;
-    const Look L = lookup(Ld.Q, a.mom[l], a.res[l], s.x, a.min_variance);
+    const Look L = lookup(Ld.Q, a.mom[l], a.res[l], s.x, a.min_variance, a.ec);
     float len;
     const float3 om = light_omega(Ld, s.x, len);
     const float lam = fmaxf(s.n.x * om.x + s.n.y * om.y + s.n.z * om.z, 0.f);
@@ -322,7 +328,7 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
     if (act && view_shades(a.lights[l], s.x)) {
       const LightDev& Ld = a.lights[l];
       const int R = a.res[l];
-      const Look L = lookup(Ld.Q, a.mom[l], R, s.x, a.min_variance);
+      const Look L = lookup(Ld.Q, a.mom[l], R, s.x, a.min_variance, a.ec);
       float len;
       const float3 om = light_omega(Ld, s.x, len);
       const float ndo = s.n.x * om.x + s.n.y * om.y + s.n.z * om.z;
@@ -350,12 +356,15 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
         const float iS2 = 1.f / (S * S);
         const float dv_dvar = L.delta * L.delta * iS2;
         const float dv_ddelta = -2.f * L.var * L.delta * iS2;
-        const float gd = gvis * dv_ddelta;
-        float gm1 = -gd, gm2 = 0.f;
+        const float gdelta = gvis * dv_ddelta;
+        float gm1 = -gdelta, gm2 = 0.f, gdw = gdelta;
         if (!L.var_clamped) {
           gm1 += gvis * dv_dvar * (-2.f * L.m.x);
           gm2 = gvis * dv_dvar;
+        } else if (a.ec > 0.f) {
+          gdw += gvis * dv_dvar * (2.f * a.min_variance * a.ec * a.ec * L.dw);   // the floor follows dw
         }
+        const float gd = a.ec > 0.f ? gdw * (a.ec * L.dw) : gdw;   // dL/d depth
         const int i0 = min(max(L.i0, 0), R - 1), i1 = min(max(L.i0 + 1, 0), R - 1);
         const int j0c = min(max(L.j0, 0), R - 1), j1c = min(max(L.j0 + 1, 0), R - 1);
         const float w00 = (1.f - L.fs) * (1.f - L.ft), w01 = L.fs * (1.f - L.ft), w10 = (1.f - L.fs) * L.ft,

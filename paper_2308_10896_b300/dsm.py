@@ -60,7 +60,8 @@ class Camera(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("min_variance", ctypes.c_float), ("filter_kind", ctypes.c_int32),
                 ("filter_boundary", ctypes.c_int32), ("aa_shadow", ctypes.c_int32), ("aa_final", ctypes.c_int32),
-                ("recompute_in_backward", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("recompute_in_backward", ctypes.c_int32), ("moments", ctypes.c_int32), ("exponent", ctypes.c_float),
+                ("stream", ctypes.c_void_p)]
 
 
 class Tuning(ctypes.Structure):
@@ -183,6 +184,8 @@ def params_struct(p: dict, stream=None) -> Params:
     q.aa_shadow = int(p.get("aa_shadow", 1))
     q.aa_final = int(p.get("aa_final", 1))
     q.recompute_in_backward = int(p.get("recompute_in_backward", 0))
+    q.moments = int(p.get("moments", 0))
+    q.exponent = float(p.get("exponent", 0.0))
     q.stream = _stream_ptr(stream)
     return q
 

@@ -729,3 +729,56 @@ def test_central_fd_point_lights(kind, seed):
     tgt = O.render(sc, verts=torch.as_tensor(scenes.jitter_vertices(sc, 0.03, seed + 10), dtype=F64),
                    keep=False)["image"].detach()
     _fd_check(sc, tgt, seed, h_vert=1e-6, h_light=1e-6, tol=1e-3)
+
+
+# ----------------------------------------------------------------------------- exponential moments (EVSM)
+def test_exponential_moments_reduce_light_bleeding():
+    """Two occluders at depths z1 < z2 cover a receiver at d > z2 half each
+    (the classic bleeding case).  The visibility is the Chebyshev bound on the
+    mixture's moments, written out here for the plain and the warped depths;
+    the exponential warp lowers the bleeding (the exact visibility is 0)."""
+    z1, z2, d, a = 0.2, 0.5, 0.52, 0.5
+
+    def bound(x1, x2, xd):
+        mu = a * x1 + (1 - a) * x2
+        var = a * (1 - a) * (x2 - x1) ** 2
+        return var / (var + (xd - mu) ** 2), mu, a * x1 * x1 + (1 - a) * x2 * x2
+
+    p_vsm, m1, m2 = bound(z1, z2, d)
+    got = O.chebyshev(torch.tensor([d], dtype=F64), torch.tensor([m1], dtype=F64), torch.tensor([m2], dtype=F64), 0.0)
+    assert abs(float(got[0]) - p_vsm) < 1e-12 and p_vsm > 0.4
+    prev = p_vsm
+    for c in (10.0, 20.0, 40.0):
+        w = np.exp(c * np.array([z1, z2, d]))
+        p_exp, m1, m2 = bound(*w)
+        enc = O.moment_encode(torch.tensor([z1, z2], dtype=F64), c)
+        mom = a * enc[0] + (1 - a) * enc[1]
+        assert abs(float(mom[0]) - m1) <= 1e-12 * m1 and abs(float(mom[1]) - m2) <= 1e-12 * m2
+        got = O.chebyshev(torch.tensor([w[2]], dtype=F64), mom[0:1], mom[1:2], 0.0)
+        assert abs(float(got[0]) - p_exp) < 1e-9
+        assert p_exp < prev
+        prev = p_exp
+    assert prev < 0.1
+
+
+def test_exponential_moments_constant_map_and_lit_points():
+    """With the warp, a receiver at or in front of the occluders is lit
+    exactly (v = 1 where exp(c d) <= m1), and a constant map keeps its
+    moments under the filter (the warp is applied before filtering)."""
+    c = 10.0
+    enc = O.moment_encode(torch.full((6, 6), 0.4, dtype=F64), c)
+    w = O.filter_weights(1.5, 0)
+    filt = O.separable_filter(enc, w, 0)
+    assert torch.allclose(filt, enc, rtol=1e-13)
+    m1, m2 = filt[..., 0].reshape(-1), filt[..., 1].reshape(-1)
+    dw = torch.exp(c * torch.full_like(m1, 0.39))
+    assert torch.all(O.chebyshev(dw, m1, m2, 1e-6 * (c * dw) ** 2) == 1.0)
+
+
+@pytest.mark.parametrize("kind,seed", [("mixed", 7), ("point", 8)])
+def test_central_fd_exponential_moments(kind, seed):
+    sc = scenes.tiny_scene(seed, res=32, img=32, kind=kind, n_lights=2 if kind == "mixed" else 1)
+    sc["params"] = dict(sc["params"], moments=1, exponent=10.0)
+    tgt = O.render(sc, verts=torch.as_tensor(scenes.jitter_vertices(sc, 0.03, seed + 10), dtype=F64),
+                   keep=False)["image"].detach()
+    _fd_check(sc, tgt, seed, h_vert=1e-6, h_light=1e-6, tol=1e-3)
