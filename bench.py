@@ -313,12 +313,44 @@ def run_ours(args):
     sc, desc = make_workload(args.workload, rank)
     import scenes
     r = dsm.Renderer(sc, device=f"cuda:{local}")
-    stream = torch.cuda.current_stream(dev)
     # target: the same scene with vertices jittered (rendered once, before timing)
     verts_t = torch.as_tensor(scenes.jitter_vertices(sc, 0.01, 99 + rank), device=dev).contiguous()
     target = r.forward(verts=verts_t).clone()
-    # kernel shapes for this scene (timed outside the measured region)
-    tuning = r.autotune(reps=3)[0] if not args.no_autotune else r.ctx.get_tuning()
+    # The step as the library records it: forward, L2 loss and backward of the
+    # frame captured once into a CUDA graph (dsm_batch_step with one scene, its
+    # views on their own streams) and replayed once per step.
+    b = dsm.Batch([sc], [target.cpu().numpy()], device=f"cuda:{local}")
+    b.step()
+    if not args.no_autotune:          # kernel shapes, timed as whole recorded steps
+        b.autotune(reps=3)
+    tuning = b.tunings()[0]
+    r.ctx.set_tuning(**tuning)
+    stream = b.stream
+    for _ in range(max(args.warmup, 0)):
+        b.step()
+    stream.synchronize()
+    b.sync()
+
+    # ---- timed region (device time, CUDA events on the replay stream)
+    sampler = ClockSampler(local) if not args.no_clocks else None
+    time.sleep(0.3 if sampler else 0.0)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    launches = b.kernels_per_step() * args.steps
+    clocks = sampler.stop() if sampler else None
+    b.sync()
+    sec = e0.elapsed_time(e1) / 1e3
+    sec_max, frames = aggregate(sec, args.steps, world, dev)
+    value = frames / sec_max
+
+    # ---- the same step without the graph: one library call per stage group
     loss = torch.zeros(1, device=dev)
     gimg = torch.empty_like(target)
     image = torch.empty_like(target)
@@ -336,27 +368,14 @@ def run_ours(args):
         step()
     r.ctx.sync()
     torch.cuda.synchronize(dev)
-
-    # ---- timed region (device time, CUDA events on the caller's stream; the
-    # library forks per-view streams internally and joins them back)
-    sampler = ClockSampler(local) if not args.no_clocks else None
-    time.sleep(0.3 if sampler else 0.0)
-    launches0 = dsm.kernel_launches()
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    cur = torch.cuda.current_stream(dev)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(cur)
     for _ in range(args.steps):
         step()
-    e1.record(stream)
+    g1.record(cur)
     torch.cuda.synchronize(dev)
-    barrier(world)
-    launches = dsm.kernel_launches() - launches0
-    clocks = sampler.stop() if sampler else None
-    r.ctx.sync()
-    sec = e0.elapsed_time(e1) / 1e3
-    sec_max, frames = aggregate(sec, args.steps, world, dev)
-    value = frames / sec_max
+    eager_ms = g0.elapsed_time(g1) / args.steps
 
     # ---- roofline timed region: the same steps with per-stage CUDA events;
     # while stage timing is on the library runs the views serially, so every
@@ -369,29 +388,26 @@ def run_ours(args):
     prof = r.ctx.profile_read()
     r.ctx.profile(False)
     r.ctx.sync()
-    # ---- end to end through the public API with host buffers (H2D inputs, D2H results)
-    # the step's inputs (vertices, light parameters, albedo) packed in one pinned
-    # host buffer and uploaded with one copy
-    parts = [torch.as_tensor(sc["verts"], dtype=torch.float32).reshape(-1), r.light_params.cpu().reshape(-1),
-             r.albedo.cpu().reshape(-1)]
-    h_in = torch.cat(parts).pin_memory()
-    d_in = torch.empty_like(h_in, device=dev)
-    n0, n1 = parts[0].numel(), parts[0].numel() + parts[1].numel()
-    d_verts = d_in[:n0].view(r.verts.shape)
-    d_lp = d_in[n0:n1].view(r.light_params.shape)
-    d_alb = d_in[n1:].view(r.albedo.shape)
+    # ---- end to end through the public API with host buffers: every step
+    # uploads the vertices, light parameters and albedo from pinned host memory
+    # into the recorded step's input buffers, replays it and reads the loss back
+    d = b.scenes[0]
+    h_parts = [torch.as_tensor(sc["verts"], dtype=torch.float32).contiguous().pin_memory(),
+               d["light_params"].cpu().pin_memory(), d["albedo"].cpu().pin_memory()]
+    d_parts = [d["verts"], d["light_params"], d["albedo"]]
     h_loss = torch.empty(1, pin_memory=True)
-    h2d = h_in.numel() * 4
+    h2d = sum(t.numel() * 4 for t in h_parts)
     d2h = 4
 
     def e2e_step():
-        d_in.copy_(h_in, non_blocking=True)
-        r.forward(verts=d_verts, light_params=d_lp, albedo=d_alb, image=image)
-        dsm.l2_loss_grad(image, target, loss, gimg)
-        r.backward(gimg, dverts, dlight, dalbedo)
-        # the gradients stay on the device for an optimiser there; the host
-        # reads the step's loss before it issues the next step
-        h_loss.copy_(loss, non_blocking=True)
+        with torch.cuda.stream(stream):
+            for hd, dd in zip(h_parts, d_parts):
+                dd.copy_(hd, non_blocking=True)
+        b.step()
+        with torch.cuda.stream(stream):
+            # the gradients stay on the device for an optimiser there; the host
+            # reads the step's loss before it issues the next step
+            h_loss.copy_(d["loss"], non_blocking=True)
         stream.synchronize()
 
     for _ in range(max(1, args.warmup)):
@@ -407,6 +423,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     barrier(world)
     e2e_sec, e2e_frames = aggregate(q0.elapsed_time(q1) / 1e3, k_e2e, world, dev)
+    b.close()
 
     # ---- roofline of the dominant stage (event timing of the roofline region)
     peak, peak_kind = load_peaks()
@@ -423,7 +440,10 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(sec_max * 1e3 / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator)",
-        "config": dict(workload_config(args.workload, sc, desc), tuning=tuning),
+        "config": dict(workload_config(args.workload, sc, desc), tuning=tuning,
+                       step="forward + L2 loss + backward recorded once as a CUDA graph (dsm_batch_step, one "
+                            "scene) and replayed per step"),
+        "eager_ms_per_step": round(eager_ms, 4),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "algorithmic_bytes_per_step": int(sb[dom]),

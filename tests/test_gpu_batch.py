@@ -96,3 +96,29 @@ def test_batch_autotune_keeps_results():
         assert torch.equal(d["image"].cpu(), img), f"scene {k}: image differs"
         assert _rel(d["dverts"].cpu(), dv) <= 1e-4
     b.close()
+
+
+def test_single_scene_batch_records_its_view_streams():
+    """A batch of one scene records its views on their own streams (fork and
+    join events inside the graph): same images as single renders, gradients up
+    to atomic order, and replays follow changed vertex buffers."""
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    sc = scenes.tiny_scene(14, res=48, img=40, kind="mixed3", n_lights=3)
+    r = dsm.Renderer(sc)
+    jit = torch.as_tensor(scenes.jitter_vertices(sc, 0.01, 81), device="cuda")
+    target = r.forward(verts=jit).clone().cpu().numpy()
+    b = dsm.Batch([sc], [target])
+    d = b.scenes[0]
+    for step in range(3):
+        if step == 2:
+            with torch.cuda.stream(b.stream):
+                d["verts"].mul_(0.99)
+        b.step()
+        b.stream.synchronize()
+        b.sync()
+        img, loss, dv, dl, da = _single(dsm, sc, d["verts"].clone(), torch.as_tensor(target, device="cuda"))
+        assert torch.equal(d["image"].cpu(), img), f"step {step}: image differs"
+        assert abs(float(d["loss"].item()) - loss) <= 1e-6 * abs(loss) + 1e-12
+        assert _rel(d["dverts"].cpu(), dv) <= 1e-4 and _rel(d["dlight"][:3].cpu(), dl) <= 1e-4
+    b.close()
