@@ -471,13 +471,15 @@ __device__ __forceinline__ float key_depth(uint64_t key) {
 }
 
 // Shared-memory form of a setup record inside one tile: for each edge e the
-// orientation-normalised edge function at the tile's first pixel centre, E0_e,
-// and its steps per pixel along x and y, A_e = -s dy_e 256 and B_e = s dx_e 256
-// (all int64, so E_e(x, y) = E0_e + x A_e + y B_e is the exact integer edge
-// function of Eq. 1's coverage test), then z[3], 2A (float), triangle, flags.
-// The stride is odd so that records of different lanes sit in different banks.
-constexpr int kRecE0 = 0, kRecA = 6, kRecB = 12, kRecZ = 18, kRecA2 = 21, kRecTri = 22, kRecFlags = 23;
-constexpr int kRecStride = 25;
+// orientation-normalised edge function at the tile's first pixel centre, E0_e
+// (int64), and the edge's orientation-normalised snapped extent (dx_e, dy_e)
+// (int32: snapped coordinates lie within +-2^28), so that
+// E_e(x, y) = E0_e + 256 (y dx_e - x dy_e) is the exact integer edge function
+// of Eq. 1's coverage test at tile pixel (x, y); then z[3], 2A (float),
+// triangle, flags.  19 words; the stride is odd so that records of different
+// lanes sit in different banks.
+constexpr int kRecE0 = 0, kRecD = 6, kRecZ = 12, kRecA2 = 15, kRecTri = 16, kRecFlags = 17;
+constexpr int kRecStride = 19;
 
 __device__ __forceinline__ long long rec_ll(const int* w, int o) {
   return (long long)(((unsigned long long)(unsigned)w[o + 1] << 32) | (unsigned)w[o]);
@@ -488,15 +490,15 @@ __device__ __forceinline__ void rec_set_ll(int* w, int o, long long v) {
 }
 
 __device__ __forceinline__ void rec_stage(const TriSetup& r, long long Px0, long long Py0, int* w) {
-  const long long sg = (r.flags & 8) ? -1 : 1;
+  const int sg = (r.flags & 8) ? -1 : 1;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int a = e == 0 ? 1 : (e == 1 ? 2 : 0);
     const int b = e == 0 ? 2 : (e == 1 ? 0 : 1);
-    const long long dx = sg * (long long)(r.X[b] - r.X[a]), dy = sg * (long long)(r.Y[b] - r.Y[a]);
-    rec_set_ll(w, kRecE0 + 2 * e, dx * (Py0 - r.Y[a]) - dy * (Px0 - r.X[a]));
-    rec_set_ll(w, kRecA + 2 * e, -dy * kSubpix);
-    rec_set_ll(w, kRecB + 2 * e, dx * kSubpix);
+    const int dx = sg * (r.X[b] - r.X[a]), dy = sg * (r.Y[b] - r.Y[a]);
+    rec_set_ll(w, kRecE0 + 2 * e, (long long)dx * (Py0 - r.Y[a]) - (long long)dy * (Px0 - r.X[a]));
+    w[kRecD + 2 * e] = dx;
+    w[kRecD + 2 * e + 1] = dy;
   }
   w[kRecZ] = __float_as_int(r.z[0]);
   w[kRecZ + 1] = __float_as_int(r.z[1]);
@@ -513,8 +515,8 @@ __device__ __forceinline__ uint64_t cover_key(const int* w, int x, int y) {
   long long E[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    const long long v = rec_ll(w, kRecE0 + 2 * e) + (long long)x * rec_ll(w, kRecA + 2 * e) +
-                        (long long)y * rec_ll(w, kRecB + 2 * e);
+    const long long v = rec_ll(w, kRecE0 + 2 * e) +
+                        256LL * ((long long)y * w[kRecD + 2 * e] - (long long)x * w[kRecD + 2 * e + 1]);
     E[e] = v;
     if (!((v > 0) || (v == 0 && ((flags >> e) & 1)))) return ~0ull;
   }
