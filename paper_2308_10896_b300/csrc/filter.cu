@@ -168,6 +168,17 @@ __global__ void __launch_bounds__(256) filter_tile_kernel(const float2* __restri
   const int ox = blockIdx.x * kFT, oy = blockIdx.y * kFT;
   const int tid = threadIdx.x;
   const bool clamp = fa.boundary == 0;
+  // the adjoint's fold reads f at this thread's outputs: loaded first, so the
+  // loads are in flight during the staging and both passes
+  float fpre[kYRun];
+  if (kAdjoint) {
+    const int col = tid % kFT, r0 = (tid / kFT) * kYRun;
+#pragma unroll
+    for (int u = 0; u < kYRun; ++u) {
+      const int gy = oy + r0 + u, gx = ox + col;
+      fpre[u] = (ex.gf && gx < R && gy < R) ? ex.fmap[(size_t)gy * R + gx].x : 0.f;
+    }
+  }
   // 1. stage the input: every load of the thread is issued before the first
   // shared-memory store
   constexpr int kStage = (S * S + 255) / 256;
@@ -237,7 +248,7 @@ __global__ void __launch_bounds__(256) filter_tile_kernel(const float2* __restri
         if (gy < R) {
           const size_t q = (size_t)gy * R + gx;
           out[q] = acc[u];
-          if (kAdjoint && ex.gf) ex.gf[q] = moment_fold(acc[u], ex.fmap[q].x, ex.ec);
+          if (kAdjoint && ex.gf) ex.gf[q] = moment_fold(acc[u], fpre[u], ex.ec);
         }
       }
     }
