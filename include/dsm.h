@@ -310,6 +310,16 @@ typedef struct dsm_batch_item {
   float*            dL_dverts;     /* device, n_verts x 3, written (NULL: skipped)  */
   float*            dL_dlight;     /* device, n_lights x 6, written (NULL: skipped) */
   float*            dL_dalbedo;    /* device, n_materials x 3, written (NULL: skip) */
+  /* Optional host staging, pinned host memory (cudaHostAlloc / registered),
+   * NULL to skip each.  The step first copies host_verts into mesh.verts,
+   * host_light_params into light_params and host_albedo into mesh.albedo
+   * (the same sizes; those device buffers are overwritten), and ends by
+   * copying the loss into host_loss (1 float), all inside the recorded step:
+   * a host loop then needs only dsm_batch_step and a stream synchronisation. */
+  const void*       host_verts;
+  const void*       host_light_params;
+  const void*       host_albedo;
+  void*             host_loss;
 } dsm_batch_item;
 
 /* Create a batch for up to n scenes (n contexts and streams); destroy frees

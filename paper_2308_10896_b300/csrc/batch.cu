@@ -6,6 +6,7 @@
 // step with a given set of buffers runs eagerly, which sizes every context,
 // and then records the same step into one CUDA graph; later steps with the
 // same buffers replay the graph with a single launch.
+#include <algorithm>
 #include <cstring>
 #include <functional>
 #include <string>
@@ -69,6 +70,15 @@ dsm_status issue_step(dsm_batch* b, const dsm_batch_item* items, int n, const ds
     if (cudaStreamWaitEvent(s, b->ev_fork, 0) != cudaSuccess) return DSM_ERR_CUDA;
     dsm_params p = *params;
     p.stream = s;
+    // the step's inputs from pinned host memory (copies inside the recorded step)
+    const struct { const void* src; const void* dst; size_t bytes; } up[3] = {
+        {it.host_verts, it.mesh.verts, sizeof(float) * 3 * (size_t)std::max(it.mesh.n_verts, 0)},
+        {it.host_light_params, it.light_params, sizeof(float) * 6 * (size_t)std::max(it.n_lights, 0)},
+        {it.host_albedo, it.mesh.albedo, sizeof(float) * 3 * (size_t)std::max(it.mesh.n_materials, 0)}};
+    for (const auto& u : up)
+      if (u.src && u.dst && u.bytes &&
+          cudaMemcpyAsync(const_cast<void*>(u.dst), u.src, u.bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return batch_fail(b, DSM_ERR_CUDA, "input upload of scene " + std::to_string(i));
     dsm_status st =
         dsm_render(b->ctx[i], &it.mesh, it.lights, it.light_params, it.n_lights, &it.camera, &p, it.image);
     if (st != DSM_OK) return batch_fail(b, st, std::string("scene ") + std::to_string(i) + ": " +
@@ -79,6 +89,8 @@ dsm_status issue_step(dsm_batch* b, const dsm_batch_item* items, int n, const ds
     st = dsm_render_backward(b->ctx[i], it.dL_dimage, it.dL_dverts, it.dL_dlight, it.dL_dalbedo);
     if (st != DSM_OK) return batch_fail(b, st, std::string("scene ") + std::to_string(i) + ": " +
                                                    dsm_last_error(b->ctx[i]));
+    if (it.host_loss && cudaMemcpyAsync(it.host_loss, it.loss, sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return batch_fail(b, DSM_ERR_CUDA, "loss download of scene " + std::to_string(i));
     if (cudaEventRecord(b->ev_join[i], s) != cudaSuccess) return DSM_ERR_CUDA;
     if (cudaStreamWaitEvent(origin, b->ev_join[i], 0) != cudaSuccess) return DSM_ERR_CUDA;
   }

@@ -76,7 +76,9 @@ class BatchItem(ctypes.Structure):
     _fields_ = [("mesh", Mesh), ("lights", ctypes.c_void_p), ("light_params", ctypes.c_void_p),
                 ("n_lights", ctypes.c_int32), ("camera", Camera), ("image", ctypes.c_void_p),
                 ("target", ctypes.c_void_p), ("loss", ctypes.c_void_p), ("dL_dimage", ctypes.c_void_p),
-                ("dL_dverts", ctypes.c_void_p), ("dL_dlight", ctypes.c_void_p), ("dL_dalbedo", ctypes.c_void_p)]
+                ("dL_dverts", ctypes.c_void_p), ("dL_dlight", ctypes.c_void_p), ("dL_dalbedo", ctypes.c_void_p),
+                ("host_verts", ctypes.c_void_p), ("host_light_params", ctypes.c_void_p),
+                ("host_albedo", ctypes.c_void_p), ("host_loss", ctypes.c_void_p)]
 
 
 _lib = None
@@ -490,6 +492,21 @@ class Batch:
 
     def kernels_per_step(self) -> int:
         return int(self.lib.dsm_batch_kernels_per_step(self.h))
+
+    def set_host_io(self, i: int, verts=None, light_params=None, albedo=None, loss=None):
+        """Pinned host tensors that scene i's recorded step uploads first
+        (vertices, light parameters, albedo) and the loss it downloads last;
+        None leaves that copy out.  The next step records a new graph."""
+        for t in (verts, light_params, albedo, loss):
+            if t is not None and (t.is_cuda or not t.is_pinned() or not t.is_contiguous()):
+                raise ValueError("host staging tensors must be contiguous pinned host memory")
+        it = self.items[i]
+        self._host = getattr(self, "_host", {})
+        self._host[i] = (verts, light_params, albedo, loss)
+        it.host_verts = verts.data_ptr() if verts is not None else None
+        it.host_light_params = light_params.data_ptr() if light_params is not None else None
+        it.host_albedo = albedo.data_ptr() if albedo is not None else None
+        it.host_loss = loss.data_ptr() if loss is not None else None
 
     def autotune(self, reps: int = 2):
         """Shapes shared by every scene, chosen by timing whole batched steps
