@@ -122,3 +122,36 @@ def test_single_scene_batch_records_its_view_streams():
         assert abs(float(d["loss"].item()) - loss) <= 1e-6 * abs(loss) + 1e-12
         assert _rel(d["dverts"].cpu(), dv) <= 1e-4 and _rel(d["dlight"][:3].cpu(), dl) <= 1e-4
     b.close()
+
+
+def test_host_staging_inside_the_recorded_step():
+    """Pinned host inputs are uploaded by the recorded step itself and the
+    loss is downloaded by it: new host values are picked up by a replay, and
+    the result equals a step on the same values uploaded by hand."""
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    sc = scenes.tiny_scene(15, res=40, img=36, kind="mixed", n_lights=2)
+    r = dsm.Renderer(sc)
+    target = r.forward(verts=torch.as_tensor(scenes.jitter_vertices(sc, 0.01, 5), device="cuda")).clone()
+    b = dsm.Batch([sc], [target.cpu().numpy()])
+    d = b.scenes[0]
+    h_verts = torch.as_tensor(sc["verts"], dtype=torch.float32).contiguous().pin_memory()
+    h_lp = d["light_params"].cpu().contiguous().pin_memory()
+    h_alb = d["albedo"].cpu().contiguous().pin_memory()
+    h_loss = torch.full((1,), -1.0).pin_memory()
+    b.set_host_io(0, verts=h_verts, light_params=h_lp, albedo=h_alb, loss=h_loss)
+    for step in range(3):
+        h_verts.mul_(1.0 + 0.01 * step)       # new host values before every step
+        h_alb.mul_(0.98)
+        b.step()
+        b.stream.synchronize()
+        b.sync()
+        assert torch.equal(d["verts"].cpu(), h_verts) and torch.equal(d["albedo"].cpu(), h_alb)
+        img, loss, dv, dl, da = _single(dsm, dict(sc, albedo=h_alb.numpy()), h_verts.cuda(), target)
+        assert torch.equal(d["image"].cpu(), img), f"step {step}: image differs"
+        assert float(h_loss[0]) == float(d["loss"].item())
+        assert abs(float(h_loss[0]) - loss) <= 1e-6 * abs(loss) + 1e-12
+        assert _rel(d["dverts"].cpu(), dv) <= 1e-4
+    with pytest.raises(ValueError):
+        b.set_host_io(0, verts=torch.zeros(3))   # not pinned
+    b.close()
