@@ -508,34 +508,49 @@ __device__ __forceinline__ void rec_stage(const TriSetup& r, long long Px0, long
   w[kRecFlags] = r.flags;
 }
 
-// Coverage of tile pixel (x, y) by a staged record: integer edge functions
-// with the top-left rule; returns the depth key or ~0.
-__device__ __forceinline__ uint64_t cover_key(const int* w, int x, int y) {
+// Coverage of the span of pixels xs..xe of row y by a staged record: the
+// edge functions at (xs, y), then one int64 step per pixel along x.
+constexpr int kSpan = 4;
+template <int kTileT>
+__device__ __forceinline__ void cover_span(const int* w, int xs, int xe, int y, unsigned long long* sbest) {
   const int flags = w[kRecFlags];
-  long long E[3];
+  long long E[3], S[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    const long long v = rec_ll(w, kRecE0 + 2 * e) +
-                        256LL * ((long long)y * w[kRecD + 2 * e] - (long long)x * w[kRecD + 2 * e + 1]);
-    E[e] = v;
-    if (!((v > 0) || (v == 0 && ((flags >> e) & 1)))) return ~0ull;
+    const int dx = w[kRecD + 2 * e], dy = w[kRecD + 2 * e + 1];
+    E[e] = rec_ll(w, kRecE0 + 2 * e) + 256LL * ((long long)y * dx - (long long)xs * dy);
+    S[e] = -256LL * dy;
   }
-  const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(ll_to_float(E[0]), __int_as_float(w[kRecZ])),
-                                                __fmul_rn(ll_to_float(E[1]), __int_as_float(w[kRecZ + 1]))),
-                                      __fmul_rn(ll_to_float(E[2]), __int_as_float(w[kRecZ + 2]))),
-                            __int_as_float(w[kRecA2]));
-  return depth_key(z, w[kRecTri]);
+#pragma unroll
+  for (int k = 0; k < kSpan; ++k) {
+    if (xs + k <= xe) {
+      bool in = true;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) in = in && ((E[e] > 0) || (E[e] == 0 && ((flags >> e) & 1)));
+      if (in) {
+        const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(ll_to_float(E[0]), __int_as_float(w[kRecZ])),
+                                                      __fmul_rn(ll_to_float(E[1]), __int_as_float(w[kRecZ + 1]))),
+                                            __fmul_rn(ll_to_float(E[2]), __int_as_float(w[kRecZ + 2]))),
+                                  __int_as_float(w[kRecA2]));
+        atomicMin(&sbest[y * kTileT + xs + k], (unsigned long long)depth_key(z, w[kRecTri]));
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) E[e] += S[e];
+  }
 }
 
-// One 256-thread CTA per tile of kTile x kTile pixels (kTile = 2^kTL, 16 or 32).  The tile's triangle list is read 256
-// records at a time.  Every record contributes its bbox-in-tile pixels as work
-// items; a block prefix sum turns them into one flat list that all threads
-// stride over (balanced whatever the triangle sizes), and each covered pixel
-// centre folds (depth key, triangle) into the pixel's shared-memory 64-bit
-// minimum.  The minimum is order independent, so the result is deterministic.
-// Items are handed out kChunk at a time: every record marks the chunk
-// position where it starts (or position 0 when it began earlier), and a block
-// prefix maximum turns the marks into the owning record of every item.
+// One 256-thread CTA per tile of kTile x kTile pixels (kTile = 2^kTL, 16 or
+// 32).  The tile's triangle list is read 256 records at a time.  Every record
+// contributes the spans of its bbox-in-tile (kSpan pixels of one row each) as
+// work items; a block prefix sum turns them into one flat list that all
+// threads stride over (balanced whatever the triangle sizes), and each
+// covered pixel centre folds (depth key, triangle) into the pixel's
+// shared-memory 64-bit minimum.  The minimum is order independent, so the
+// result is deterministic.  Items are handed out kChunk at a time: every
+// record marks the chunk position where it starts (or position 0 when it
+// began earlier), and a block prefix maximum turns the marks into the owning
+// record of every item.
 // Each pixel then writes one 16-byte G-buffer texel: id + 1,
 // perspective-correct b0, b1, depth key.
 constexpr int kChunk = 1024;
@@ -553,9 +568,9 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
   static_assert(kTile <= 32, "tile-local coordinates are packed in 5 bits");
   __shared__ int sq[256 * kRecStride];
   __shared__ unsigned long long sbest[kPix];
-  __shared__ int spre[257];          // exclusive prefix of the work items per record
+  __shared__ int spre[257];          // exclusive prefix of the work items (spans) per record
   __shared__ int sbox[256];          // bbox in tile: x0 | x1 << 5 | y0 << 10 | y1 << 15 (tile-local)
-  __shared__ int sinv[256];          // ceil(2^16 / bbox width)
+  __shared__ int sinv[256];          // ceil(2^16 / spans per bbox row)
   __shared__ unsigned short sown[kChunk];   // owning record + 1 of each item of the chunk
   __shared__ int swarp[8];
   const int tile = blockIdx.x;
@@ -574,7 +589,7 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
       const int i0 = max(r.ibox & 0xffff, ti0), i1 = min((int)((unsigned)r.ibox >> 16), ti0 + kTile - 1);
       const int j0 = max(r.jbox & 0xffff, tj0), j1 = min((int)((unsigned)r.jbox >> 16), tj0 + kTile - 1);
       if (i0 <= i1 && j0 <= j1) {
-        const int wd = i1 - i0 + 1;
+        const int wd = (i1 - i0 + kSpan) / kSpan;   // spans per row
         area = wd * (j1 - j0 + 1);
         box = (i0 - ti0) | ((i1 - ti0) << 5) | ((j0 - tj0) << 10) | ((j1 - tj0) << 15);
         inv = (65536 + wd - 1) / wd;
@@ -643,11 +658,10 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
         const int rec = sown[q] - 1;
         const int b = sbox[rec];
         const int x0 = b & 31, x1 = (b >> 5) & 31, y0 = (b >> 10) & 31;
-        const int it = c0 + q - spre[rec], wd = x1 - x0 + 1;
-        const int qy = (it * sinv[rec]) >> 16;   // it / wd (exact for it < 1024, wd <= 32)
-        const int x = x0 + (it - qy * wd), y = y0 + qy;
-        const uint64_t key = cover_key(sq + rec * kRecStride, x, y);
-        if (key != ~0ull) atomicMin(&sbest[y * kTile + x], (unsigned long long)key);
+        const int it = c0 + q - spre[rec], wd = (x1 - x0 + kSpan) / kSpan;
+        const int qy = (it * sinv[rec]) >> 16;   // it / wd (exact for it <= 256 spans, wd <= 8)
+        const int xs = x0 + kSpan * (it - qy * wd), y = y0 + qy;
+        cover_span<kTile>(sq + rec * kRecStride, xs, min(xs + kSpan - 1, x1), y, sbest);
       }
       __syncthreads();
     }
