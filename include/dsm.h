@@ -192,8 +192,11 @@ typedef struct dsm_tuning {
   int32_t big_tiles;     /* bin depth: a triangle whose bbox spans at least this many tiles is
                             binned by the big-triangle kernel (tiles spread over many blocks) and
                             its backward sums go to private copies; 2..4096                       */
-  int32_t filter_shape;  /* 0: both filter passes in one kernel on 32x32 output tiles (radius <=
-                            15, larger radii take two passes); 1: two 1-D passes                  */
+  int32_t filter_shape;  /* 0: input tiles staged by the TMA in a persistent double-buffered kernel
+                            (radius <= 8, map side a multiple of 16, no antialiased patch to
+                            substitute; otherwise shape 2); 1: two 1-D passes; 2: both passes
+                            in one kernel on 32x32 output tiles with plain loads (radius <= 15,
+                            larger radii take two passes)                                       */
 } dsm_tuning;
 
 /* Set / read the shapes used by the next calls on ctx.  DSM_ERR_INVALID_ARG
@@ -206,7 +209,7 @@ dsm_status dsm_get_tuning(dsm_ctx* ctx, dsm_tuning* tuning);
  * backward, whose gradients go to context scratch) for candidate shapes and
  * keeps the fastest on ctx.  Coordinate search from the current shapes: each
  * knob in turn (light tile, camera tile, bin depth from {4, 16, 64}, filter
- * shape) is set to each of its other values and kept when the step gets
+ * shape from {0, 1, 2}) is set to each of its other values and kept when the step gets
  * faster; each candidate runs one untimed step (sizing) and `reps` timed
  * steps (1..100) with CUDA events on params->stream.  Synchronous.  best and
  * best_ms (host, may be NULL) receive the chosen shapes and their time per

@@ -270,10 +270,10 @@ void set_serial_views(dsm_ctx* ctx, bool serial) {
 // when `measure` reports a step at least 2 % faster.
 dsm_status tuning_search(dsm_tuning* cur, float* cur_ms,
                          const std::function<dsm_status(const dsm_tuning&, float*)>& measure) {
-  const int32_t tiles[2] = {16, 32}, bins[3] = {4, 16, 64}, shapes[2] = {0, 1};
+  const int32_t tiles[2] = {16, 32}, bins[3] = {4, 16, 64}, shapes[3] = {0, 1, 2};
   for (int knob = 0; knob < 4; ++knob) {
     const int32_t* vals = knob < 2 ? tiles : (knob == 2 ? bins : shapes);
-    const int nv = knob == 2 ? 3 : 2;
+    const int nv = knob >= 2 ? 3 : 2;
     const dsm_tuning base = *cur;
     for (int k = 0; k < nv; ++k) {
       dsm_tuning cand = base;
@@ -586,7 +586,7 @@ void light_maps(dsm_ctx* ctx, int l, cudaStream_t st) {
   }
   StageTimer t(ctx, ST_FILTER, st);
   launch_filter(wk.fmap.as<float2>(), wk.tmp.as<float2>(), lb.mom.as<float2>(), v.W, lb.fa, st,
-                aa ? v.hflag.as<uint8_t>() : nullptr, wk.ftilde.as<float2>());
+                aa ? v.hflag.as<uint8_t>() : nullptr, wk.ftilde.as<float2>(), ctx->status.as<DevStatus>());
 }
 
 ShadeArgs shade_args(dsm_ctx* ctx, int c) {
@@ -682,7 +682,7 @@ void light_backward(dsm_ctx* ctx, int l, cudaStream_t st) {
   {
     StageTimer t(ctx, ST_BWD_FILTER, st);
     launch_filter_adjoint(lb.gm.as<float2>(), wk.tmp.as<float2>(), wk.gft.as<float2>(), v.W, lb.fa, st,
-                          wk.fmap.as<float2>(), wk.tmp.as<float>(), warp_exponent(ctx));
+                          wk.fmap.as<float2>(), wk.tmp.as<float>(), warp_exponent(ctx), ctx->status.as<DevStatus>());
   }
   {
     StageTimer t(ctx, ST_BWD_SM_AA, st);
@@ -1032,7 +1032,7 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
 
 static bool tuning_ok(const dsm_tuning& t) {
   return (t.light_tile == 16 || t.light_tile == 32) && (t.camera_tile == 16 || t.camera_tile == 32) &&
-         t.big_tiles >= 2 && t.big_tiles <= 4096 && (t.filter_shape == 0 || t.filter_shape == 1);
+         t.big_tiles >= 2 && t.big_tiles <= 4096 && t.filter_shape >= 0 && t.filter_shape <= 2;
 }
 
 dsm_status dsm_set_tuning(dsm_ctx* ctx, const dsm_tuning* tuning) {
@@ -1117,8 +1117,9 @@ dsm_status dsm_filter_moments(dsm_ctx* ctx, const float* in, float* out, int32_t
   DSM_CHECK(ctx->filter_tmp.ensure((size_t)res * res * sizeof(float2)));
   FilterArgs fa;
   make_filter_args(sigma, radius, kind, boundary, &fa);
+  fa.shape = ctx->tuning.filter_shape;
   launch_filter(reinterpret_cast<const float2*>(in), ctx->filter_tmp.as<float2>(), reinterpret_cast<float2*>(out), res,
-                fa, (cudaStream_t)stream);
+                fa, (cudaStream_t)stream, nullptr, nullptr, ctx->status.as<DevStatus>());
   DSM_CHECK(cudaGetLastError());
   return DSM_OK;
 }
@@ -1132,8 +1133,10 @@ dsm_status dsm_filter_moments_adjoint(dsm_ctx* ctx, const float* gout, float* gi
   DSM_CHECK(ctx->filter_tmp.ensure((size_t)res * res * sizeof(float2)));
   FilterArgs fa;
   make_filter_args(sigma, radius, kind, boundary, &fa);
+  fa.shape = ctx->tuning.filter_shape;
   launch_filter_adjoint(reinterpret_cast<const float2*>(gout), ctx->filter_tmp.as<float2>(),
-                        reinterpret_cast<float2*>(gin), res, fa, (cudaStream_t)stream);
+                        reinterpret_cast<float2*>(gin), res, fa, (cudaStream_t)stream, nullptr, nullptr, 0.f,
+                        ctx->status.as<DevStatus>());
   DSM_CHECK(cudaGetLastError());
   return DSM_OK;
 }

@@ -144,18 +144,6 @@ __device__ __forceinline__ void tap_run(const float2* src, int step, const Filte
   }
 }
 
-// Extras of the shadow-map path (NULL for a plain filter):
-//   forward: the input is (f, f^2) except where hflag marks a texel whose
-//     antialiased value the antialiasing pass wrote into patch;
-//   adjoint: also writes dL/df of the output g (moment_fold of g with the
-//     first channel of fmap and the warp exponent ec).
-struct FilterExtras {
-  const uint8_t* hflag;
-  const float2* patch;
-  const float2* fmap;
-  float* gf;
-  float ec;
-};
 
 template <int kR, bool kAdjoint>
 __global__ void __launch_bounds__(256) filter_tile_kernel(const float2* __restrict__ in, float2* __restrict__ out,
@@ -292,9 +280,13 @@ void launch_compose(const float2* fmap, const uint8_t* hflag, const float2* patc
 }
 
 void launch_filter(const float2* in, float2* tmp, float2* out, int R, const FilterArgs& fa, cudaStream_t st,
-                   const uint8_t* hflag, const float2* patch) {
+                   const uint8_t* hflag, const float2* patch, DevStatus* status) {
   const FilterExtras ex{hflag, patch, nullptr, nullptr, 0.f};
-  if (fa.shape == 0 && launch_tiled_r<1>(false, in, out, R, fa, ex, st)) return;
+  // the TMA path stages whole tiles; the listed texels' substitution would then
+  // wait on a patch load per tile, which costs more than the plain loads that
+  // fetch the patch beside the tile, so it takes only the plain filter
+  if (fa.shape == 0 && !hflag && launch_filter_tma(false, in, out, R, fa, ex, status, st)) return;
+  if (fa.shape != 1 && launch_tiled_r<1>(false, in, out, R, fa, ex, st)) return;
   dim3 b(32, 8), g((R + 31) / 32, (R + 7) / 8);
   if (hflag) {
     // the substituted input is composed into `out` first (the passes read it back)
@@ -310,9 +302,10 @@ void launch_filter(const float2* in, float2* tmp, float2* out, int R, const Filt
 }
 
 void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, const FilterArgs& fa,
-                           cudaStream_t st, const float2* fmap, float* gf, float ec) {
+                           cudaStream_t st, const float2* fmap, float* gf, float ec, DevStatus* status) {
   const FilterExtras ex{nullptr, nullptr, fmap, gf, ec};
-  if (fa.shape == 0 && launch_tiled_r<1>(true, gout, gin, R, fa, ex, st)) return;
+  if (fa.shape == 0 && launch_filter_tma(true, gout, gin, R, fa, ex, status, st)) return;
+  if (fa.shape != 1 && launch_tiled_r<1>(true, gout, gin, R, fa, ex, st)) return;
   dim3 b(32, 8), g((R + 31) / 32, (R + 7) / 8);
   count_launches(1);
   filter_pass_kernel<true, true><<<g, b, 0, st>>>(gout, tmp, R, fa);

@@ -38,7 +38,22 @@ struct FilterArgs {
   float fold[33];          // fold[i] = sum of w over taps that leave the map by more than i texels
   int r;
   int boundary;            // 0 clamp, 1 zero
-  int shape;               // 0 one fused tile kernel (radius <= 15, else two passes), 1 two 1-D passes
+  int shape;               // 0 TMA-staged persistent kernel (radius <= 8, side a multiple of 16, and no
+                           //   antialiased patch to substitute; else 2),
+                           // 1 two 1-D passes, 2 one fused tile kernel with plain loads (radius <= 15, else 1)
+};
+
+// Extras of the shadow-map path (NULL for a plain filter):
+//   forward: the input is (f, f^2) except where hflag marks a texel whose
+//     antialiased value the antialiasing pass wrote into patch;
+//   adjoint: also writes dL/df of the output g (moment_fold of g with the
+//     first channel of fmap and the warp exponent ec).
+struct FilterExtras {
+  const uint8_t* hflag;
+  const float2* patch;
+  const float2* fmap;
+  float* gf;
+  float ec;
 };
 
 // Binning and raster shape of one view: tile side 2^tile_log2 pixels, and the
@@ -158,8 +173,13 @@ void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* dep
 void make_filter_args(double sigma, int radius, int kind, int boundary, FilterArgs* fa);
 // m = G g; with hflag (shadow-map path) g is (f, f^2) except at flagged texels,
 // where the antialiasing pass left (f~, (f^2)~) in patch.
+// The TMA-staged filter (filter_tma.cu); false when the map or the radius does
+// not qualify (the caller then takes another shape).  A bounded wait that runs
+// out sets status->timeout.
+bool launch_filter_tma(bool adjoint, const float2* in, float2* out, int R, const FilterArgs& fa,
+                       const FilterExtras& ex, DevStatus* status, cudaStream_t st);
 void launch_filter(const float2* in, float2* tmp, float2* out, int R, const FilterArgs& fa, cudaStream_t st,
-                   const uint8_t* hflag = nullptr, const float2* patch = nullptr);
+                   const uint8_t* hflag = nullptr, const float2* patch = nullptr, DevStatus* status = nullptr);
 // out = hflag ? patch : fmap per texel (the antialiased shadow map, materialised
 // on request).
 void launch_compose(const float2* fmap, const uint8_t* hflag, const float2* patch, float2* out, int n,
@@ -168,7 +188,8 @@ void launch_compose(const float2* fmap, const uint8_t* hflag, const float2* patc
 // With fmap and gf: also writes gf = dL/df of every texel from the result
 // (moment_fold with the warp exponent ec).
 void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, const FilterArgs& fa, cudaStream_t st,
-                           const float2* fmap = nullptr, float* gf = nullptr, float ec = 0.f);
+                           const float2* fmap = nullptr, float* gf = nullptr, float ec = 0.f,
+                           DevStatus* status = nullptr);
 
 // normals, shading, vertex gradients
 void launch_vertex_normals(const float* verts, int V, const int* tris, const int* vf_off, const int* vf_list,

@@ -78,3 +78,38 @@ def test_filter_rejects_bad_arguments():
         with pytest.raises(dsm.DsmError):
             ctx.filter_moments_adjoint(a, b, *args)
     ctx.close()
+
+
+TMA_CASES = [  # res, sigma, radius, kind, boundary: sides that are multiples of 16 take the TMA path
+    (64, 2.0, 0, 0, 0),
+    (48, 1.5, 3, 0, 1),
+    (96, 2.0, 5, 1, 0),
+    (160, 3.0, 8, 0, 0),
+    (32, 1.0, 7, 0, 0),
+    (2048, 2.0, 0, 0, 0),
+    (2048, 1.0, 1, 1, 1),
+]
+
+
+@pytest.mark.parametrize("res,sigma,radius,kind,boundary", TMA_CASES)
+def test_filter_shapes_are_bit_identical(res, sigma, radius, kind, boundary):
+    """The TMA-staged kernel (shape 0), the fused kernel with plain loads
+    (shape 2) and the two 1-D passes (shape 1): the forward results are
+    bit-identical, the transposes of the tiled kernels too (the two-pass
+    transpose applies y then x, so it agrees to rounding)."""
+    g = torch.Generator().manual_seed(7000 + res + radius)
+    x = torch.rand((res, res, 2), generator=g).cuda().contiguous()
+    y = (torch.rand((res, res, 2), generator=g) - 0.5).cuda().contiguous()
+    ctx = _ctx()
+    out = {}
+    for shape in (0, 2, 1):
+        ctx.set_tuning(filter_shape=shape)
+        m = torch.full_like(x, float("nan"))
+        gin = torch.full_like(y, float("nan"))
+        ctx.filter_moments(x, m, sigma, radius, kind, boundary)
+        ctx.filter_moments_adjoint(y, gin, sigma, radius, kind, boundary)
+        ctx.sync()
+        out[shape] = (m.cpu(), gin.cpu())
+    assert torch.equal(out[0][0], out[2][0]) and torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[2][1])
+    assert torch.allclose(out[0][1], out[1][1], rtol=1e-5, atol=1e-6)

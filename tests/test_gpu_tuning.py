@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 SHAPES = [dict(light_tile=16, camera_tile=16, big_tiles=16, filter_shape=0),
           dict(light_tile=32, camera_tile=16, big_tiles=4, filter_shape=1),
           dict(light_tile=16, camera_tile=32, big_tiles=64, filter_shape=1),
-          dict(light_tile=32, camera_tile=32, big_tiles=2, filter_shape=0)]
+          dict(light_tile=32, camera_tile=32, big_tiles=2, filter_shape=0),
+          dict(light_tile=32, camera_tile=16, big_tiles=16, filter_shape=2)]
 
 
 def _ragged(sc, W, H):
@@ -64,7 +65,7 @@ def test_bad_shapes_rejected():
     from paper_2308_10896_b300 import dsm
     torch.cuda.set_device(0)
     r = dsm.Renderer(SCENES["tiny_mixed"]())
-    for bad in (dict(light_tile=8), dict(camera_tile=64), dict(big_tiles=1), dict(filter_shape=2)):
+    for bad in (dict(light_tile=8), dict(camera_tile=64), dict(big_tiles=1), dict(filter_shape=3)):
         with pytest.raises(dsm.DsmError):
             r.ctx.set_tuning(**bad)
 
@@ -77,7 +78,7 @@ def test_autotune_picks_valid_shapes_and_keeps_results():
     ref = _step(dsm, r, 5)
     best, ms = r.autotune(reps=2)
     assert best["light_tile"] in (16, 32) and best["camera_tile"] in (16, 32)
-    assert best["big_tiles"] in (4, 16, 64) and best["filter_shape"] in (0, 1)
+    assert best["big_tiles"] in (4, 16, 64) and best["filter_shape"] in (0, 1, 2)
     assert ms > 0.0
     assert r.ctx.get_tuning() == best
     got = _step(dsm, r, 5)
