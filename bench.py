@@ -20,7 +20,6 @@ import json
 import math
 import os
 import statistics
-import subprocess
 import sys
 import time
 
@@ -139,69 +138,76 @@ def load_peaks():
 
 
 # ----------------------------------------------------------------------------- clocks
+class _Nvml:
+    """The few read-only NVML queries the clock record needs, through the
+    driver's libnvidia-ml (ctypes)."""
+    CLOCK_SM = 1
+    # clock event reason bits (nvml.h)
+    REASONS = (("sw_power_cap", 0x4), ("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20),
+               ("hw_thermal_slowdown", 0x40))
+
+    def __init__(self, uuid: str):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.lib, self.ct = lib, ctypes
+        self.h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML device with the CUDA device's UUID")
+        self._reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+
+    def clock(self, fn="nvmlDeviceGetClockInfo"):
+        v = self.ct.c_uint()
+        if getattr(self.lib, fn)(self.h, self.CLOCK_SM, self.ct.byref(v)) != 0:
+            raise RuntimeError(fn)
+        return v.value
+
+    def reasons(self):
+        v = self.ct.c_ulonglong()
+        if self._reasons(self.h, self.ct.byref(v)) != 0:
+            raise RuntimeError("clock event reasons")
+        return [name for name, bit in self.REASONS if v.value & bit]
+
+
 class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    """SM clock and throttle reasons of the benchmark's GPU, read through NVML
+    by a background thread every 10 ms while the timed region runs (read only;
+    no setting is changed)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, device_index: int):
-        self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
-        idx = self._smi_index(device_index)
-        if idx is None:
-            return
-        try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-i", str(idx), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
-        except Exception:
-            self.proc = None
-
-    @staticmethod
-    def _smi_index(dev):
+    def __init__(self, device_index: int, period_s: float = 0.01):
+        import threading
+        self.samples, self.thread = [], None
         try:
             import torch
-            uuid = str(torch.cuda.get_device_properties(dev).uuid)
-            out = subprocess.run(["nvidia-smi", "--query-gpu=index,uuid", "--format=csv,noheader"],
-                                 capture_output=True, text=True, timeout=20).stdout
-            for line in out.strip().splitlines():
-                i, u = [x.strip() for x in line.split(",")]
-                if uuid.replace("GPU-", "") in u:
-                    return int(i)
-            return dev
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            nv = _Nvml(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+            self.max_mhz = nv.clock("nvmlDeviceGetMaxClockInfo")
         except Exception:
-            return None
+            return
+        self.stop_flag = threading.Event()
+
+        def run():
+            while not self.stop_flag.is_set():
+                try:
+                    self.samples.append((nv.clock(), nv.reasons()))
+                except Exception:
+                    pass
+                self.stop_flag.wait(period_s)
+
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
 
     def stop(self):
-        if self.proc is None:
+        if self.thread is None:
             return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.fh.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
+        self.stop_flag.set()
+        self.thread.join(timeout=5)
+        if not self.samples:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted({r for _, rs in self.samples for r in rs}), "samples": len(self.samples)}
 
 
 # ----------------------------------------------------------------------------- distributed
@@ -333,7 +339,6 @@ def run_ours(args):
 
     # ---- timed region (device time, CUDA events on the replay stream)
     sampler = ClockSampler(local) if not args.no_clocks else None
-    time.sleep(0.3 if sampler else 0.0)
     barrier(world)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -639,7 +644,6 @@ def run_reconstruction(args):
         r.ctx.sync()
         reset()
         sampler = ClockSampler(0) if (mode == 1 and not args.no_clocks) else None
-        time.sleep(0.3 if sampler else 0.0)
         n0 = dsm.kernel_launches()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -354,6 +354,15 @@ const char* dsm_batch_last_error(dsm_batch* b);
  * overflow, timeouts) raised since the last dsm_sync. */
 dsm_status dsm_sync(dsm_ctx* ctx);
 
+/* Check of the failure path of the bounded device waits (the TMA-staged
+ * filter waits on mbarriers with an iteration limit): one CTA on the
+ * context's stream waits on an mbarrier.  With arrive = 1 a thread completes
+ * the phase and the wait ends; with arrive = 0 nothing completes it, the wait
+ * gives up after a short limit and records a timeout, which the next dsm_sync
+ * reports as DSM_ERR_TIMEOUT.  No fault is raised and the context stays
+ * usable.  DSM_ERR_CUDA on a launch error. */
+dsm_status dsm_bounded_wait_probe(dsm_ctx* ctx, int32_t arrive);
+
 /* One-line description of the last error on ctx (static storage, never NULL). */
 const char* dsm_last_error(dsm_ctx* ctx);
 

@@ -1158,6 +1158,13 @@ dsm_status dsm_sync(dsm_ctx* ctx) {
   return DSM_OK;
 }
 
+dsm_status dsm_bounded_wait_probe(dsm_ctx* ctx, int32_t arrive) {
+  if (!ctx) return DSM_ERR_INVALID_ARG;
+  launch_bounded_wait_probe(ctx->status.as<DevStatus>(), arrive != 0, ctx->stream);
+  DSM_CHECK(cudaGetLastError());
+  return DSM_OK;
+}
+
 dsm_status dsm_profile_enable(dsm_ctx* ctx, int32_t enable) {
   if (!ctx) return DSM_ERR_INVALID_ARG;
   ctx->prof = enable != 0;

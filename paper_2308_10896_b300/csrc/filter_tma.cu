@@ -349,7 +349,29 @@ bool launch_tma_dispatch(const float2* in, float2* out, int R, const FilterArgs&
   return launch_tma_r<kR, kAdjoint>(in, out, R, fa, ex, status, st);
 }
 
+// Probe of the bounded wait: one CTA waits on an mbarrier whose phase
+// completes only when `arrive` is set; otherwise the wait gives up after
+// `limit` polls and records a timeout in the status word.
+__global__ void bounded_wait_probe_kernel(DevStatus* status, int arrive, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+  bool done = false;
+  for (long long it = 0; it < limit && !done; ++it) done = mbar_try_wait(&bar, 0);
+  if (!__syncthreads_and(done) && threadIdx.x == 0) atomicExch(&status->timeout, 1);
+}
+
 }  // namespace
+
+void launch_bounded_wait_probe(DevStatus* status, bool arrive, cudaStream_t st) {
+  count_launches(1);
+  bounded_wait_probe_kernel<<<1, 32, 0, st>>>(status, arrive ? 1 : 0, 4096);
+}
 
 bool launch_filter_tma(bool adjoint, const float2* in, float2* out, int R, const FilterArgs& fa,
                        const FilterExtras& ex, DevStatus* status, cudaStream_t st) {

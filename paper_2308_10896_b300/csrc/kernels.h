@@ -178,6 +178,9 @@ void make_filter_args(double sigma, int radius, int kind, int boundary, FilterAr
 // out sets status->timeout.
 bool launch_filter_tma(bool adjoint, const float2* in, float2* out, int R, const FilterArgs& fa,
                        const FilterExtras& ex, DevStatus* status, cudaStream_t st);
+// One CTA waiting on an mbarrier with the bounded wait of the TMA filter;
+// without `arrive` nothing completes the phase and the wait records a timeout.
+void launch_bounded_wait_probe(DevStatus* status, bool arrive, cudaStream_t st);
 void launch_filter(const float2* in, float2* tmp, float2* out, int R, const FilterArgs& fa, cudaStream_t st,
                    const uint8_t* hflag = nullptr, const float2* patch = nullptr, DevStatus* status = nullptr);
 // out = hflag ? patch : fmap per texel (the antialiased shadow map, materialised

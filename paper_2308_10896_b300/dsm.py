@@ -31,7 +31,7 @@ EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_
             "dsm_batch_create", "dsm_batch_destroy", "dsm_batch_context", "dsm_batch_step", "dsm_batch_sync",
             "dsm_batch_kernels_per_step", "dsm_batch_last_error", "dsm_render_cameras",
             "dsm_render_cameras_backward", "dsm_memory_bytes", "dsm_adam_step", "dsm_set_tuning",
-            "dsm_get_tuning", "dsm_autotune", "dsm_batch_autotune"]
+            "dsm_get_tuning", "dsm_autotune", "dsm_batch_autotune", "dsm_bounded_wait_probe"]
 
 
 class DsmError(RuntimeError):
@@ -129,6 +129,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                           ctypes.POINTER(Params), ctypes.POINTER(P), I32, ctypes.POINTER(Tuning),
                           ctypes.POINTER(ctypes.c_float)], I32),
         "dsm_batch_autotune": ([P, P, I32, P, I32], I32),
+        "dsm_bounded_wait_probe": ([P, I32], I32),
         "dsm_adam_step": ([P, P, P, P, I64, I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P],
                           I32),
     }
@@ -278,6 +279,10 @@ class Context:
 
     def sync(self):
         self._check(self.lib.dsm_sync(self.h), self.h)
+
+    def bounded_wait_probe(self, arrive: bool):
+        """One CTA waiting on an mbarrier (see dsm_bounded_wait_probe)."""
+        self._check(self.lib.dsm_bounded_wait_probe(self.h, 1 if arrive else 0), self.h)
 
     def profile(self, enable: bool):
         self._check(self.lib.dsm_profile_enable(self.h, 1 if enable else 0), self.h)

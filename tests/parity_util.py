@@ -53,7 +53,7 @@ def grad_close(gpu, ref, what, rel=1e-3):
     return l2
 
 
-class GpuRun:
+class GpuFrame:
     """Forward (and optionally backward) of the CUDA path on one scene."""
 
     def __init__(self, scene: dict, target=None):

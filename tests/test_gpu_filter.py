@@ -113,3 +113,24 @@ def test_filter_shapes_are_bit_identical(res, sigma, radius, kind, boundary):
     assert torch.equal(out[0][0], out[2][0]) and torch.equal(out[0][0], out[1][0])
     assert torch.equal(out[0][1], out[2][1])
     assert torch.allclose(out[0][1], out[1][1], rtol=1e-5, atol=1e-6)
+
+
+def test_bounded_wait_records_timeout_and_context_survives():
+    """The bounded-wait failure path without a GPU fault: a wait that nothing
+    completes gives up, dsm_sync reports DSM_ERR_TIMEOUT, and the context then
+    renders the same frame as before."""
+    import scenes
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    r = dsm.Renderer(scenes.tiny_scene(3, res=64, img=32))
+    img0 = r.forward().clone()
+    r.ctx.sync()
+    r.ctx.bounded_wait_probe(arrive=True)
+    r.ctx.sync()
+    r.ctx.bounded_wait_probe(arrive=False)
+    with pytest.raises(dsm.DsmError) as err:
+        r.ctx.sync()
+    assert err.value.status == dsm.DSM_ERR_TIMEOUT
+    img1 = r.forward().clone()
+    r.ctx.sync()
+    assert torch.equal(img0, img1)

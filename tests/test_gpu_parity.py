@@ -11,7 +11,7 @@ import torch
 
 import scenes
 from oracle import dsm_oracle as O
-from parity_util import ATOL, F64, GpuRun, assert_close, grad_close, oracle_target
+from parity_util import ATOL, F64, GpuFrame, assert_close, grad_close, oracle_target
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +45,7 @@ def _case(name):
     if name not in _cache:
         sc = SCENES[name]()
         tgt = oracle_target(sc, 0.01, 7)
-        gpu = GpuRun(sc, tgt)
+        gpu = GpuFrame(sc, tgt)
         ref = O.render(sc)
         _cache[name] = (sc, tgt, gpu, ref)
     return _cache[name]

@@ -369,7 +369,7 @@ def test_two_depth_vsm_equals_pcf():
 
 
 def test_single_triangle_shadow_outline():
-    """North-star closed form: a triangle parallel above the ground under a
+    """Closed form: a triangle parallel above the ground under a
     perpendicular directional light casts its vertical projection: the
     integral of (1 - v) over the ground equals the triangle's area up to the
     smoothing of its perimeter; deep inside v ~ 0, far outside v = 1."""
