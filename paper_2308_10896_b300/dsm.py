@@ -393,15 +393,47 @@ class Renderer:
                                 [camera_struct(c) for c in cameras], params_struct(self.params_dict, stream), images)
         return images
 
-    def autotune(self, cameras: list | None = None, reps: int = 3, stream=None):
+    def shape_class(self, cameras: list | None = None) -> str:
+        """Key of the autotuner's cache: triangle count (rounded to a power of
+        two), light view sizes, camera sizes and the recompute mode."""
+        cams = cameras if cameras is not None else [self.camera_dict]
+        t = 1 << max(0, int(self.tris.shape[0]) - 1).bit_length()
+        lights = ",".join(f"{l.type}:{l.res}" for l in self.lights)
+        views = ",".join(f"{int(c['width'])}x{int(c['height'])}" for c in cams)
+        return f"T{t}|L{lights}|C{views}|R{int(self.params_dict.get('recompute_in_backward', 0))}"
+
+    def autotune(self, cameras: list | None = None, reps: int = 3, stream=None, cache: str | None = None):
         """Choose the kernel shapes of this renderer's context by timing
         forward + backward steps of its scene (dsm_autotune); returns the
-        chosen shapes and the time per step in ms."""
+        chosen shapes and the time per step in ms (None when taken from the
+        cache).  With `cache` (a JSON file path) the shapes chosen for this
+        scene's shape class are read from it when present, and stored in it
+        after a search otherwise."""
+        import json
+        key = self.shape_class(cameras)
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                known = json.load(f)
+            if key in known:
+                self.ctx.set_tuning(**known[key])
+                return self.ctx.get_tuning(), None
         cams = cameras if cameras is not None else [self.camera_dict]
         images = [torch.empty((int(c["height"]), int(c["width"]), 4), dtype=torch.float32, device=self.device)
                   for c in cams]
-        return self.ctx.autotune(self.mesh_struct(), self.lights, self.light_params, [camera_struct(c) for c in cams],
-                                 params_struct(self.params_dict, stream), images, reps)
+        best, ms = self.ctx.autotune(self.mesh_struct(), self.lights, self.light_params,
+                                     [camera_struct(c) for c in cams], params_struct(self.params_dict, stream),
+                                     images, reps)
+        if cache:
+            known = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    known = json.load(f)
+            known[key] = best
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(known, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return best, ms
 
     def backward_cameras(self, dL_dimages: list, dverts=None, dlight=None, dalbedo=None):
         """Backward of the last forward_cameras for the loss summed over the cameras."""

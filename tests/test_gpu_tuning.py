@@ -84,3 +84,18 @@ def test_autotune_picks_valid_shapes_and_keeps_results():
     got = _step(dsm, r, 5)
     assert torch.equal(got[0], ref[0])
     assert _rel(got[1], ref[1]) <= 1e-4
+
+
+def test_autotune_cache_round_trip(tmp_path):
+    """Shapes found by the search are stored under the scene's shape class and
+    read back by the next renderer of that class without a search."""
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    cache = str(tmp_path / "shapes.json")
+    r = dsm.Renderer(SCENES["tiny_mixed"]())
+    best, ms = r.autotune(reps=1, cache=cache)
+    assert ms is not None and ms > 0.0
+    r2 = dsm.Renderer(SCENES["tiny_mixed"]())
+    r2.ctx.set_tuning(light_tile=16, camera_tile=16, big_tiles=4, filter_shape=1)
+    got, ms2 = r2.autotune(reps=1, cache=cache)
+    assert ms2 is None and got == best and r2.ctx.get_tuning() == best
