@@ -32,7 +32,7 @@ __all__ = [
     "icosphere", "subdivided_box", "ground_quad", "sh_displace", "random_rotation",
     "look_at_perspective", "directional_light", "spot_light", "point_light", "merge_meshes",
     "config1", "config2", "config3", "config4", "config5", "config_by_name",
-    "tiny_scene", "jitter_vertices", "displaced_target", "minimal_plane",
+    "tiny_scene", "jitter_vertices", "displaced_target", "minimal_plane", "tessellated_occluder",
 ]
 
 
@@ -425,6 +425,27 @@ def minimal_plane(res: int = 256, img: int = 128, sigma: float = 1.0, displace=(
             "albedo": np.array([[0.8, 0.8, 0.8], [0.8, 0.8, 0.8]], np.float32), "lights": [light],
             "camera": cam, "params": _default_params(min_variance=1e-5, filter_kind=kind),
             "target_verts": target, "moved": moved}
+
+
+def tessellated_occluder(n: int = 256, angle_deg: float = 7.0, res: int = 256, img: int = 128,
+                         sigma: float = 1.0, kind: int = 0) -> dict:
+    """The paper's Jacobian setup (supplementary Sec. B): the minimal-plane
+    scene with the occluder split into n x n quads (2 n^2 triangles; n = 256
+    gives the paper's ~130k faces) and slightly rotated about the vertical
+    axis.  "occluder" holds the occluder's vertex indices."""
+    ov, ot = ground_grid(0.5, 1.0, n)
+    a = math.radians(angle_deg)
+    rot = np.array([[math.cos(a), 0.0, math.sin(a)], [0.0, 1.0, 0.0], [-math.sin(a), 0.0, math.cos(a)]])
+    ov = (ov - np.array([0.0, 1.0, 0.0])) @ rot.T + np.array([0.0, 1.0, 0.0])
+    gv, gt = ground_quad(2.0, 0.0)
+    verts, tris, mat = merge_meshes([(ov, ot, 0), (gv, gt, 1)])
+    light = directional_light((0.0, -1.0, 0.0), res, ortho_half=1.5, dist=5.0, near=1.0, far=10.0,
+                              sigma=sigma, intensity=(1.0, 1.0, 1.0))
+    cam = look_at_perspective((0.0, 0.9, 0.0), (0.0, 0.0, 0.0), 90.0, img, img, near=0.05, far=10.0)
+    return {"name": "tessellated_occluder", "verts": verts, "tris": tris, "tri_mat": mat,
+            "albedo": np.array([[0.8, 0.8, 0.8], [0.8, 0.8, 0.8]], np.float32), "lights": [light],
+            "camera": cam, "params": _default_params(min_variance=1e-5, filter_kind=kind),
+            "occluder": np.arange(len(ov))}
 
 
 def jitter_vertices(scene: dict, sigma: float, seed: int) -> np.ndarray:

@@ -782,3 +782,33 @@ def test_central_fd_exponential_moments(kind, seed):
     tgt = O.render(sc, verts=torch.as_tensor(scenes.jitter_vertices(sc, 0.03, seed + 10), dtype=F64),
                    keep=False)["image"].detach()
     _fd_check(sc, tgt, seed, h_vert=1e-6, h_light=1e-6, tol=1e-3)
+
+
+def test_tessellated_occluder_jacobian_is_sparse():
+    """Sec. 5: with triangles smaller than a shadow-map texel the antialiasing
+    misses primitive boundaries.  The oracle's gradient of a weighted image
+    sum with respect to the occluder's translation equals the small-step
+    difference quotient (the derivative of the method as implemented) for
+    both occluders, but against the one-texel difference quotient (which
+    averages over the method's events) it holds for a coarse occluder and is
+    far too small for a tessellated one."""
+    texel = 3.0 / 64
+    ratios = {}
+    for n in (4, 64):
+        sc = scenes.tessellated_occluder(n=n, res=64, img=32)
+        occ = sc["occluder"]
+        W = np.random.default_rng(3).normal(size=(32, 32, 4))
+        V0 = sc["verts"].astype(np.float64)
+
+        def L(t):
+            v = V0.copy()
+            v[occ, 0] += t
+            return float((O.render(sc, verts=torch.as_tensor(v), keep=False)["image"].detach().numpy() * W).sum())
+
+        v = torch.as_tensor(V0).clone().requires_grad_(True)
+        g, = torch.autograd.grad((O.render(sc, verts=v, keep=False)["image"] * torch.as_tensor(W)).sum(), [v])
+        ad = float(g[occ, 0].sum())
+        fd_small = (L(1e-6) - L(-1e-6)) / 2e-6
+        assert abs(fd_small - ad) <= 1e-6 * abs(ad)
+        ratios[n] = ad / ((L(texel) - L(-texel)) / (2 * texel))
+    assert 0.8 < ratios[4] < 1.3 and ratios[64] < 0.5, ratios
