@@ -28,6 +28,7 @@
 #include "dsm.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace dsm {
 namespace {
@@ -36,7 +37,6 @@ constexpr int kFT = 32;        // output tile side
 constexpr int kXRun = 8;       // x-pass outputs per thread
 constexpr int kYRun = 4;       // y-pass outputs per thread
 constexpr int kTmaRmax = 8;    // largest radius staged by the TMA (shared memory)
-constexpr long long kSpinLimit = 1LL << 22;
 
 template <int kR>
 struct TmaGeom {
@@ -52,44 +52,6 @@ struct TmaGeom {
   static constexpr int MID = S * PM * 8;
   static constexpr size_t smem = 1024 + 2 * (size_t)BUF + 2 * (size_t)HBOX + MID + 16;
 };
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n"
-      "  .reg .pred p;\n"
-      "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "  selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the phase `parity` of an mbarrier to complete.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-      : "memory");
-}
 
 // Byte offset of staged texel (column c, row s) in a staging buffer: box c / 16,
 // row s of 128 bytes, 16-byte chunk (c % 16) / 2 XOR (s % 8).
@@ -276,42 +238,17 @@ __global__ void __launch_bounds__(256) filter_tma_kernel(const __grid_constant__
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-bool encode_map(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int elem_bytes, int R, int box_w,
-                int box_h, CUtensorMapSwizzle swizzle) {
-  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)R, (cuuint64_t)R};
-  const cuuint64_t strides[1] = {(cuuint64_t)R * elem_bytes};
-  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int kR, bool kAdjoint>
 bool launch_tma_r(const float2* in, float2* out, int R, const FilterArgs& fa, const FilterExtras& ex,
                   DevStatus* status, cudaStream_t st) {
   using G = TmaGeom<kR>;
   const bool flags = !kAdjoint && ex.hflag != nullptr;
   alignas(64) CUtensorMap map_in, map_flag;
-  if (!encode_map(&map_in, in, CU_TENSOR_MAP_DATA_TYPE_UINT64, 8, R, 16, G::S, CU_TENSOR_MAP_SWIZZLE_128B))
+  if (!encode_map(&map_in, in, CU_TENSOR_MAP_DATA_TYPE_UINT64, 8, R, R, 16, G::S, CU_TENSOR_MAP_SWIZZLE_128B))
     return false;
   if (flags) {
-    if (!encode_map(&map_flag, ex.hflag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, R, G::HW, G::S, CU_TENSOR_MAP_SWIZZLE_NONE))
+    if (!encode_map(&map_flag, ex.hflag, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, R, R, G::HW, G::S,
+                    CU_TENSOR_MAP_SWIZZLE_NONE))
       return false;
   } else {
     map_flag = map_in;   // not read
