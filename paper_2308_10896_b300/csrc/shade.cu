@@ -325,6 +325,7 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
 #pragma unroll
     for (int k = 0; k < 20; ++k) gq[k] = 0.f;
     float3 gdir = make_float3(0.f, 0.f, 0.f);
+    bool has_q = false;
     if (act && view_shades(a.lights[l], s.x)) {
       const LightDev& Ld = a.lights[l];
       const int R = a.res[l];
@@ -352,6 +353,7 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
         }
       }
       if (L.inside && L.delta > 0.f && gvis != 0.f) {
+        has_q = true;
         const float S = L.var + L.delta * L.delta;
         const float iS2 = 1.f / (S * S);
         const float dv_dvar = L.delta * L.delta * iS2;
@@ -400,8 +402,24 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
       }
     }
     // rows 0, 1, 3 and the depth row of dL/dQ (row 2 is zero: the lookup never
-    // reads clip z) and the direct light term, one warp reduce-scatter
-    {
+    // reads clip z) and the direct light term, one warp reduce-scatter; a warp
+    // without a shadowed lookup has only the direct term to sum
+    if (!__any_sync(kFull, has_q)) {
+      float d0 = gdir.x, d1 = gdir.y, d2 = gdir.z;
+      if (__any_sync(kFull, d0 != 0.f || d1 != 0.f || d2 != 0.f)) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          d0 += __shfl_xor_sync(kFull, d0, o);
+          d1 += __shfl_xor_sync(kFull, d1, o);
+          d2 += __shfl_xor_sync(kFull, d2, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+          if (d0 != 0.f) atomicAdd(&sD[l * 3], d0);
+          if (d1 != 0.f) atomicAdd(&sD[l * 3 + 1], d1);
+          if (d2 != 0.f) atomicAdd(&sD[l * 3 + 2], d2);
+        }
+      }
+    } else {
       float v[32];
 #pragma unroll
       for (int k = 0; k < 8; ++k) v[k] = gq[k];
