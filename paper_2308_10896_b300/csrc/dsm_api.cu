@@ -81,6 +81,9 @@ struct dsm_ctx {
   DevStatus* hstatus = nullptr;
   // state of the last forward
   bool have_fwd = false;
+  // the forward already zeroed every light's dL/dm accumulator (on the light's
+  // stream, beside the camera shading); the first backward after it need not
+  bool gm_zeroed = false;
   dsm_mesh mesh{};
   dsm_light lights[DSM_MAX_LIGHTS]{};   // the caller's lights
   int n_user = 0;                        // their number
@@ -496,6 +499,7 @@ dsm_status prepare_light(dsm_ctx* ctx, int l) {
   DSM_CHECK(wk.tmp.ensure(R2));
   LightBufs& lb = ctx->light[l];
   DSM_CHECK(lb.mom.ensure(R2));
+  DSM_CHECK(lb.gm.ensure(R2));
   lb.res = R;
   make_filter_args(Lu.sigma, Lu.radius, ctx->params.filter_kind, ctx->params.filter_boundary, &lb.fa);
   lb.fa.shape = ctx->tuning.filter_shape;
@@ -746,6 +750,7 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
   dsm_status s = check_args(ctx, mesh, lights, light_params, n_lights, cams, n_cams, params, images);
   if (s != DSM_OK) return s;
   ctx->have_fwd = false;
+  ctx->gm_zeroed = false;
   cudaStream_t st = (cudaStream_t)params->stream;
   ctx->mesh = *mesh;
   int L = 0;
@@ -855,7 +860,11 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
     for (int w = 0; w < NV; ++w) {
       cudaStream_t vst = view_stream(ctx, w, st);
       raster_view(ctx, w, vst);
-      if (w < L) light_maps(ctx, w, vst);
+      if (w < L) {
+        light_maps(ctx, w, vst);
+        const LightBufs& lb = ctx->light[w];
+        DSM_CHECK(cudaMemsetAsync(lb.gm.p, 0, (size_t)lb.res * lb.res * sizeof(float2), vst));
+      }
     }
     DSM_CHECK(join_views(ctx, st, 0, NV));
     DSM_CHECK(cudaGetLastError());
@@ -868,6 +877,7 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
     if (C > 1) DSM_CHECK(join_views(ctx, st, L, NV));
   }
   DSM_CHECK(cudaGetLastError());
+  ctx->gm_zeroed = !ctx->recompute;
   ctx->sized_sig = sig;
   ctx->have_fwd = true;
   return DSM_OK;
@@ -935,8 +945,10 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     cl.add(ctx->gQ.p, sizeof(float) * 20 * kMaxLightViews);
     cl.add(ctx->gdirect.p, sizeof(float) * 3 * kMaxLightViews);
     cl.add(ctx->red.p, sizeof(float) * kRedSlots * red_stride);
-    for (int l = 0; l < L; ++l)
-      cl.add(ctx->light[l].gm.p, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2));
+    if (!ctx->gm_zeroed)
+      for (int l = 0; l < L; ++l)
+        cl.add(ctx->light[l].gm.p, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2));
+    ctx->gm_zeroed = false;   // this backward accumulates into them
     if (!ctx->recompute)
       for (int w = 0; w < NV; ++w) clear_view(cl, w);
     static_assert(7 + kMaxLightViews + 2 * kMaxViews <= kMaxClear, "clear list");

@@ -196,3 +196,20 @@ def test_adam_step_against_oracle():
     assert np.all(np.abs(v.cpu().double().numpy() - vo) <= 1e-6 * scale ** 2 + 1e-5 * np.abs(vo))
     with pytest.raises(dsm.DsmError):
         dsm.adam_step(p, m, m, v, 0)
+
+
+def test_second_backward_after_one_forward():
+    """The forward zeroes the shadow-map gradient accumulators for the first
+    backward; a second backward of the same forward zeroes them itself and
+    gives the same gradients (up to the order of float atomics)."""
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    sc, cams = _scene()
+    r = dsm.Renderer(sc)
+    imgs = r.forward_cameras(cams)
+    gimgs = _grads(21, cams)
+    first = [t.clone() for t in r.backward_cameras(gimgs)]
+    second = [t.clone() for t in r.backward_cameras(gimgs)]
+    torch.cuda.synchronize()
+    for a, b, name in zip(first, second, ("verts", "light", "albedo")):
+        assert _rel(b.cpu(), a.cpu()) <= 1e-5, f"dL/d{name} differs on the second backward"
