@@ -478,6 +478,12 @@ __device__ __forceinline__ float key_depth(uint64_t key) {
 // of Eq. 1's coverage test at tile pixel (x, y); then z[3], 2A (float),
 // triangle, flags.  19 words; the stride is odd so that records of different
 // lanes sit in different banks.
+// E0_e is stored biased by the top-left rule, E0_e - (1 - tl_e): the pixel is
+// covered iff every biased edge function is >= 0 (E > 0, or E = 0 on a
+// top-left edge), which one sign test of their bitwise OR decides.  Records
+// whose biased edge functions stay within int32 over the whole tile (every
+// triangle a few tiles across) are flagged kRecSmall and stepped in int32;
+// the coverage and the depth key are the same integers either way.
 constexpr int kRecE0 = 0, kRecD = 6, kRecZ = 12, kRecA2 = 15, kRecTri = 16, kRecFlags = 17;
 constexpr int kRecStride = 19;
 
@@ -489,51 +495,69 @@ __device__ __forceinline__ void rec_set_ll(int* w, int o, long long v) {
   w[o + 1] = (int)(unsigned)((unsigned long long)v >> 32);
 }
 
+constexpr int kRecSmall = 32;   // the biased edge functions fit int32 over the tile
+constexpr int kSpan = 4;
 __device__ __forceinline__ void rec_stage(const TriSetup& r, long long Px0, long long Py0, int* w) {
   const int sg = (r.flags & 8) ? -1 : 1;
+  bool small = true;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int a = e == 0 ? 1 : (e == 1 ? 2 : 0);
     const int b = e == 0 ? 2 : (e == 1 ? 0 : 1);
     const int dx = sg * (r.X[b] - r.X[a]), dy = sg * (r.Y[b] - r.Y[a]);
-    rec_set_ll(w, kRecE0 + 2 * e, (long long)dx * (Py0 - r.Y[a]) - (long long)dy * (Px0 - r.X[a]));
+    // biased by the top-left rule: covered iff E'_e = E_e - (1 - tl_e) >= 0
+    const long long E0 = (long long)dx * (Py0 - r.Y[a]) - (long long)dy * (Px0 - r.X[a]) - (((r.flags >> e) & 1) ^ 1);
+    rec_set_ll(w, kRecE0 + 2 * e, E0);
     w[kRecD + 2 * e] = dx;
     w[kRecD + 2 * e + 1] = dy;
+    // |E| over tile pixels x <= 31 + kSpan (a span steps once past its end), y <= 31
+    small = small && llabs(E0) + 256LL * (31LL * llabs((long long)dx) + (31LL + kSpan) * llabs((long long)dy)) <
+                         (1LL << 31);
   }
   w[kRecZ] = __float_as_int(r.z[0]);
   w[kRecZ + 1] = __float_as_int(r.z[1]);
   w[kRecZ + 2] = __float_as_int(r.z[2]);
   w[kRecA2] = __float_as_int(r.a2f);
   w[kRecTri] = r.tri;
-  w[kRecFlags] = r.flags;
+  w[kRecFlags] = r.flags | (small ? kRecSmall : 0);
 }
 
 // Coverage of the span of pixels xs..xe of row y by a staged record: the
-// edge functions at (xs, y), then one int64 step per pixel along x.
-constexpr int kSpan = 4;
-template <int kTileT>
+// biased edge functions at (xs, y), then one step per pixel along x; a pixel
+// is covered iff no biased edge function is negative (one sign test of their
+// OR).  TE is int when the record's edge functions fit int32 over the tile.
+template <typename TE>
+__device__ __forceinline__ float edge_float(TE v);
+template <>
+__device__ __forceinline__ float edge_float<int>(int v) { return __int2float_rn(v); }
+template <>
+__device__ __forceinline__ float edge_float<long long>(long long v) { return ll_to_float(v); }
+
+template <typename TE, int kTileT>
 __device__ __forceinline__ void cover_span(const int* w, int xs, int xe, int y, unsigned long long* sbest) {
   const int flags = w[kRecFlags];
-  long long E[3], S[3];
+  TE E[3], S[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int dx = w[kRecD + 2 * e], dy = w[kRecD + 2 * e + 1];
-    E[e] = rec_ll(w, kRecE0 + 2 * e) + 256LL * ((long long)y * dx - (long long)xs * dy);
-    S[e] = -256LL * dy;
+    if constexpr (sizeof(TE) == 4)
+      E[e] = w[kRecE0 + 2 * e] + 256 * (y * dx - xs * dy);
+    else
+      E[e] = rec_ll(w, kRecE0 + 2 * e) + 256LL * ((long long)y * dx - (long long)xs * dy);
+    S[e] = -256 * (TE)dy;
   }
 #pragma unroll
   for (int k = 0; k < kSpan; ++k) {
-    if (xs + k <= xe) {
-      bool in = true;
-#pragma unroll
-      for (int e = 0; e < 3; ++e) in = in && ((E[e] > 0) || (E[e] == 0 && ((flags >> e) & 1)));
-      if (in) {
-        const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(ll_to_float(E[0]), __int_as_float(w[kRecZ])),
-                                                      __fmul_rn(ll_to_float(E[1]), __int_as_float(w[kRecZ + 1]))),
-                                            __fmul_rn(ll_to_float(E[2]), __int_as_float(w[kRecZ + 2]))),
-                                  __int_as_float(w[kRecA2]));
+    if (xs + k <= xe && (E[0] | E[1] | E[2]) >= 0) {
+      // the unbiased edge functions weight the corner depths (Eq. 1's key)
+      const float e0 = edge_float<TE>(E[0] + (TE)((flags & 1) ^ 1));
+      const float e1 = edge_float<TE>(E[1] + (TE)(((flags >> 1) & 1) ^ 1));
+      const float e2 = edge_float<TE>(E[2] + (TE)(((flags >> 2) & 1) ^ 1));
+      const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(e0, __int_as_float(w[kRecZ])),
+                                                    __fmul_rn(e1, __int_as_float(w[kRecZ + 1]))),
+                                          __fmul_rn(e2, __int_as_float(w[kRecZ + 2]))),
+                                __int_as_float(w[kRecA2]));
         atomicMin(&sbest[y * kTileT + xs + k], (unsigned long long)depth_key(z, w[kRecTri]));
-      }
     }
 #pragma unroll
     for (int e = 0; e < 3; ++e) E[e] += S[e];
@@ -661,7 +685,9 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
         const int it = c0 + q - spre[rec], wd = (x1 - x0 + kSpan) / kSpan;
         const int qy = (it * sinv[rec]) >> 16;   // it / wd (exact for it <= 256 spans, wd <= 8)
         const int xs = x0 + kSpan * (it - qy * wd), y = y0 + qy;
-        cover_span<kTile>(sq + rec * kRecStride, xs, min(xs + kSpan - 1, x1), y, sbest);
+        const int* rw = sq + rec * kRecStride;
+        if (rw[kRecFlags] & kRecSmall) cover_span<int, kTile>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
+        else cover_span<long long, kTile>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
       }
       __syncthreads();
     }
