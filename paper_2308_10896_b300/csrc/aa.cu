@@ -465,20 +465,15 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
   float4 cc[3];
   float cd[3];
   // prefetch of row j0
-  float4 g_next = make_float4(0.f, 0.f, 0.f, 0.f);
-  float gf_next = 0.f;
-  if (col_ok && j0 < a.H) {
-    g_next = a.gbuf[(size_t)j0 * a.W + i];
-    gf_next = gf_map[(size_t)j0 * a.W + i];
-  }
+  // the texel gradients of the strip first; a G-buffer texel is read only
+  // where its gradient is nonzero
+  float gfs[kStrip];
+#pragma unroll
+  for (int s = 0; s < kStrip; ++s) gfs[s] = (col_ok && j0 + s < a.H) ? gf_map[(size_t)(j0 + s) * a.W + i] : 0.f;
   for (int s = 0; s < kStrip; ++s) {
     const int j = j0 + s;
-    const float4 g = g_next;
-    const float gf = gf_next;
-    if (col_ok && j + 1 < a.H && s + 1 < kStrip) {
-      g_next = a.gbuf[(size_t)(j + 1) * a.W + i];
-      gf_next = gf_map[(size_t)(j + 1) * a.W + i];
-    }
+    const float gf = gfs[s];
+    const float4 g = gf != 0.f ? a.gbuf[(size_t)j * a.W + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     float c[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) c[k] = 0.f;
