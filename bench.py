@@ -393,6 +393,13 @@ def run_ours(args):
     prof = r.ctx.profile_read()
     r.ctx.profile(False)
     r.ctx.sync()
+    # ---- the raster's integer work per view of the last frame (outside every timed region)
+    n_views = sum(6 if Lt["type"] == 2 else 1 for Lt in sc["lights"]) + 1
+    work = [r.ctx.raster_stats(w) for w in range(n_views)]
+    tests = sum(x["pixel_tests"] for x in work)
+    raster_work = {"per_view": work, "pixel_tests_per_step": tests, "edge_steps_per_step": 3 * tests,
+                   "note": "views: lights (cube faces) then the camera; each pixel test steps three "
+                           "integer edge functions"}
     # ---- end to end through the public API with host buffers: every step
     # uploads the vertices, light parameters and albedo from pinned host memory
     # into the recorded step's input buffers and downloads the loss; the copies
@@ -452,6 +459,8 @@ def run_ours(args):
                      "timed_steps": k_prof},
         "stages": stages,
         "frame_algorithmic_GBps": round(sum(sb.values()) * value / world / 1e9, 1),
+        "raster_work": dict(raster_work, pixel_tests_per_s=round(tests * value / world)),
+        "l2_bytes": int(torch.cuda.get_device_properties(dev).L2_cache_size),
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": {"value": round(e2e_frames / e2e_sec, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),

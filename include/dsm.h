@@ -183,6 +183,17 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
 /* Device memory held by ctx (its scratch and saved state), in bytes. */
 uint64_t dsm_memory_bytes(dsm_ctx* ctx);
 
+/* Integer work of the raster of view `view` (lights' views first, then the
+ * cameras, as in dsm_render_cameras) in the last forward on ctx, counted from
+ * the tile lists and setup records that raster read (Eq. 1's coverage test):
+ * out[0] tile-triangle pairs, out[1] spans of 4 pixels of one row (the raster's
+ * work items), out[2] pixel-centre coverage tests (three edge-function steps
+ * each).  out: host array of 3.  A diagnostic: launches one kernel on the last
+ * forward's stream and synchronises it.  DSM_ERR_NO_FORWARD without a forward;
+ * DSM_ERR_INVALID_ARG for a view out of range or a recomputing context (its
+ * views share one buffer set). */
+dsm_status dsm_raster_stats(dsm_ctx* ctx, int32_t view, int64_t* out);
+
 /* ---- Kernel shapes of a context.  The results do not depend on them (the
  * raster is exact and order independent; the filter is the same sums), only
  * the speed does.  Defaults: 32, 32, 16, 0. */

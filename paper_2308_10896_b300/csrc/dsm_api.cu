@@ -77,7 +77,7 @@ struct dsm_ctx {
   ViewBufs view[kMaxViews];
   LightBufs light[kMaxLightViews];
   Buf lights_dev, viewM, status, vnormal, vnlen, gnormal, gN, gface, gQ, gdirect, red;
-  Buf scratch_dverts, scratch_dlight, scratch_dalbedo, filter_tmp;
+  Buf scratch_dverts, scratch_dlight, scratch_dalbedo, filter_tmp, stats;
   DevStatus* hstatus = nullptr;
   // state of the last forward
   bool have_fwd = false;
@@ -1253,13 +1253,34 @@ dsm_status dsm_debug_copy(dsm_ctx* ctx, int32_t what, int32_t index, void* dst, 
   return DSM_OK;
 }
 
+dsm_status dsm_raster_stats(dsm_ctx* ctx, int32_t view, int64_t* out) {
+  if (!ctx || !out) return DSM_ERR_INVALID_ARG;
+  if (!ctx->have_fwd) return fail(ctx, DSM_ERR_NO_FORWARD, "raster stats without a forward");
+  if (ctx->recompute)
+    return fail(ctx, DSM_ERR_INVALID_ARG, "raster stats need the stored mode (recomputation shares view buffers)");
+  if (view < 0 || view >= ctx->L + ctx->C) return fail(ctx, DSM_ERR_INVALID_ARG, "raster stats: view out of range");
+  ViewBufs& v = vbuf(ctx, view);
+  cudaStream_t st = ctx->stream;
+  constexpr size_t kBytes = 3 * sizeof(unsigned long long);
+  DSM_CHECK(ctx->stats.ensure(kBytes));
+  DSM_CHECK(cudaMemsetAsync(ctx->stats.p, 0, kBytes, st));
+  launch_raster_stats(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,
+                      v.bs.tile_log2, ctx->stats.as<unsigned long long>(), st);
+  DSM_CHECK(cudaGetLastError());
+  unsigned long long h[3];
+  DSM_CHECK(cudaMemcpyAsync(h, ctx->stats.p, kBytes, cudaMemcpyDeviceToHost, st));
+  DSM_CHECK(cudaStreamSynchronize(st));
+  for (int k = 0; k < 3; ++k) out[k] = (int64_t)h[k];
+  return DSM_OK;
+}
+
 uint64_t dsm_memory_bytes(dsm_ctx* ctx) {
   if (!ctx) return 0;
   uint64_t n = 0;
   const Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->status,
                        &ctx->vnormal, &ctx->vnlen, &ctx->gnormal, &ctx->gN, &ctx->gface, &ctx->gQ, &ctx->gdirect,
                        &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo, &ctx->filter_tmp,
-                       &ctx->red};
+                       &ctx->red, &ctx->stats};
   for (const Buf* b : bufs) n += b->cap;
   for (const auto& v : ctx->view) {
     const Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,

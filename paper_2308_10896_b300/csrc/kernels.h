@@ -150,6 +150,10 @@ void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cu
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, const int* offset,
                      int* list, int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
                      cudaStream_t st);
+// Raster work counts of one view into out[0..2] (added): tile-triangle pairs,
+// spans, pixel-centre coverage tests.
+void launch_raster_stats(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX,
+                         int tilesY, int tile_log2, unsigned long long* out, cudaStream_t st);
 // Light views (fmap != NULL) also write the shadow-map depth sample (f, f^2)
 // of every texel, f interpolated from the per-vertex light depths.
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,

@@ -715,6 +715,42 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
   }
 }
 
+// ------------------------------------------------------------------ work counts
+// The raster's integer work for one view, from the same lists and records the
+// raster reads: tile-triangle pairs, spans of kSpan pixels (its work items) and
+// pixel-centre coverage tests (three edge-function steps each).  One warp per
+// tile; a diagnostic, off the frame's path.
+__global__ void raster_stats_kernel(const TriSetup* __restrict__ setup, const int* __restrict__ offset,
+                                    const int* __restrict__ list, int capacity, int n_tiles, int tilesX, int tl,
+                                    unsigned long long* __restrict__ out) {
+  const int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (tile >= n_tiles) return;
+  const int ts = 1 << tl;
+  const int ti0 = (tile % tilesX) * ts, tj0 = (tile / tilesX) * ts;
+  const int beg = min(offset[tile], capacity), end = min(offset[n_tiles + tile], capacity);
+  unsigned long long pairs = 0, spans = 0, tests = 0;
+  for (int k = beg + lane; k < end; k += 32) {
+    const TriSetup r = setup[list[k]];
+    const int i0 = max(r.ibox & 0xffff, ti0), i1 = min((int)((unsigned)r.ibox >> 16), ti0 + ts - 1);
+    const int j0 = max(r.jbox & 0xffff, tj0), j1 = min((int)((unsigned)r.jbox >> 16), tj0 + ts - 1);
+    if (i0 > i1 || j0 > j1) continue;
+    pairs += 1;
+    spans += (unsigned long long)((i1 - i0 + kSpan) / kSpan) * (j1 - j0 + 1);
+    tests += (unsigned long long)(i1 - i0 + 1) * (j1 - j0 + 1);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    pairs += __shfl_xor_sync(kFull, pairs, o);
+    spans += __shfl_xor_sync(kFull, spans, o);
+    tests += __shfl_xor_sync(kFull, tests, o);
+  }
+  if (lane == 0 && pairs) {
+    atomicAdd(&out[0], pairs);
+    atomicAdd(&out[1], spans);
+    atomicAdd(&out[2], tests);
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM,
                         cudaStream_t st) {
@@ -776,6 +812,14 @@ void launch_raster(const TriSetup* setup, const int* offset, const int* list, in
   else
     raster_kernel<5><<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf,
                                                       depth, fmap, ec);
+}
+
+void launch_raster_stats(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX,
+                         int tilesY, int tile_log2, unsigned long long* out, cudaStream_t st) {
+  const int n = tilesX * tilesY;
+  if (n == 0) return;
+  count_launches(1);
+  raster_stats_kernel<<<(n + 7) / 8, 256, 0, st>>>(setup, offset, list, capacity, n, tilesX, tile_log2, out);
 }
 
 }  // namespace dsm

@@ -31,7 +31,8 @@ EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_
             "dsm_batch_create", "dsm_batch_destroy", "dsm_batch_context", "dsm_batch_step", "dsm_batch_sync",
             "dsm_batch_kernels_per_step", "dsm_batch_last_error", "dsm_render_cameras",
             "dsm_render_cameras_backward", "dsm_memory_bytes", "dsm_adam_step", "dsm_set_tuning",
-            "dsm_get_tuning", "dsm_autotune", "dsm_batch_autotune", "dsm_bounded_wait_probe"]
+            "dsm_get_tuning", "dsm_autotune", "dsm_batch_autotune", "dsm_bounded_wait_probe",
+            "dsm_raster_stats"]
 
 
 class DsmError(RuntimeError):
@@ -123,6 +124,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                 ctypes.POINTER(Params), ctypes.POINTER(P)], I32),
         "dsm_render_cameras_backward": ([P, ctypes.POINTER(P), P, P, P], I32),
         "dsm_memory_bytes": ([P], ctypes.c_uint64),
+        "dsm_raster_stats": ([P, I32, P], I32),
         "dsm_set_tuning": ([P, ctypes.POINTER(Tuning)], I32),
         "dsm_get_tuning": ([P, ctypes.POINTER(Tuning)], I32),
         "dsm_autotune": ([P, ctypes.POINTER(Mesh), ctypes.POINTER(Light), P, I32, ctypes.POINTER(Camera), I32,
@@ -246,6 +248,12 @@ class Context:
     def memory_bytes(self) -> int:
         """Device memory held by this context (scratch and saved state)."""
         return int(self.lib.dsm_memory_bytes(self.h))
+
+    def raster_stats(self, view: int) -> dict:
+        """Raster work of one view in the last forward (see dsm_raster_stats)."""
+        out = (ctypes.c_int64 * 3)()
+        self._check(self.lib.dsm_raster_stats(self.h, int(view), ctypes.cast(out, ctypes.c_void_p)), self.h)
+        return {"pairs": int(out[0]), "spans": int(out[1]), "pixel_tests": int(out[2])}
 
     def set_tuning(self, light_tile=32, camera_tile=32, big_tiles=16, filter_shape=0):
         t = Tuning(light_tile, camera_tile, big_tiles, filter_shape)
