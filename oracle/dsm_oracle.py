@@ -637,6 +637,11 @@ def shade_pixels(scene: dict, verts: torch.Tensor, light_params: torch.Tensor, a
     return jj, ii, albedo[mat] * radiance, vis_all
 
 
+def _light_params(scene: dict) -> np.ndarray:
+    """(L, 6) float64: position and direction of every light (L may be 0)."""
+    return np.array([np.concatenate([l["pos"], l["dir"]]) for l in scene["lights"]], np.float64).reshape(-1, 6)
+
+
 def render(scene: dict, verts: torch.Tensor = None, light_params: torch.Tensor = None,
            albedo: torch.Tensor = None, teacher: dict = None, keep: bool = True) -> dict:
     """Forward pass: Alg. 1 per light view (one per directional or spot light,
@@ -654,8 +659,7 @@ def render(scene: dict, verts: torch.Tensor = None, light_params: torch.Tensor =
     if verts is None:
         verts = torch.as_tensor(scene["verts"], dtype=F64)
     if light_params is None:
-        light_params = torch.as_tensor(np.stack([np.concatenate([l["pos"], l["dir"]]) for l in scene["lights"]]),
-                                       dtype=F64)
+        light_params = torch.as_tensor(_light_params(scene), dtype=F64)
     if albedo is None:
         albedo = torch.as_tensor(scene["albedo"], dtype=F64)
     V32 = verts.detach().numpy().astype(np.float32)
@@ -731,7 +735,7 @@ def render_and_grad(scene: dict, target, teacher: dict = None, verts=None, light
     the light parameters (pos xyz, dir xyz per light) and the albedo table."""
     v = torch.as_tensor(scene["verts"] if verts is None else verts, dtype=F64).clone().requires_grad_(True)
     if light_params is None:
-        light_params = np.stack([np.concatenate([l["pos"], l["dir"]]) for l in scene["lights"]])
+        light_params = _light_params(scene)
     lp = torch.as_tensor(light_params, dtype=F64).clone().requires_grad_(True)
     al = torch.as_tensor(scene["albedo"], dtype=F64).clone().requires_grad_(True)
     out = render(scene, v, lp, al, teacher=teacher)
@@ -748,8 +752,7 @@ def render_cameras_and_grad(scene: dict, cameras: list, targets: list, verts=Non
     ``teachers`` optionally gives ``render``'s teacher per camera.  Returns
     the images, the summed loss and its gradients."""
     v = torch.as_tensor(scene["verts"] if verts is None else verts, dtype=F64).clone().requires_grad_(True)
-    lp = torch.as_tensor(np.stack([np.concatenate([l["pos"], l["dir"]]) for l in scene["lights"]]),
-                         dtype=F64).clone().requires_grad_(True)
+    lp = torch.as_tensor(_light_params(scene), dtype=F64).clone().requires_grad_(True)
     al = torch.as_tensor(scene["albedo"], dtype=F64).clone().requires_grad_(True)
     images, loss = [], 0.0
     for c, (cam, tgt) in enumerate(zip(cameras, targets)):

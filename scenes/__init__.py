@@ -448,6 +448,36 @@ def tessellated_occluder(n: int = 256, angle_deg: float = 7.0, res: int = 256, i
             "occluder": np.arange(len(ov))}
 
 
+def with_degenerate_triangles(scene: dict) -> dict:
+    """A copy of ``scene`` with triangles the setup must cull or treat as
+    edge cases, appended after the original ones (ids unchanged):
+    - (a, a, b) on an edge of the first object: zero snapped area in every
+      view, and a third triangle on edge (a, b), which makes it non-manifold
+      (a silhouette edge of the triangles beside it);
+    - a triangle with one corner behind the camera (w < near in the camera
+      view, an ordinary triangle for the lights);
+    - a triangle far outside every view.
+    The degenerate triangle reuses existing vertices, so every vertex still
+    has a well-defined area-weighted normal."""
+    sc = dict(scene)
+    v = np.asarray(scene["verts"], np.float32)
+    t = np.asarray(scene["tris"], np.int32)
+    m = np.asarray(scene["tri_mat"], np.int32)
+    a, b = int(t[0, 0]), int(t[0, 1])
+    cam_eye = np.asarray(scene["camera"].get("eye", (0.0, 3.0, 4.0)), np.float32)
+    behind = cam_eye + np.float32(1.5) * (cam_eye - np.array([0.0, 0.5, 0.0], np.float32)) / np.linalg.norm(
+        cam_eye - np.array([0.0, 0.5, 0.0], np.float32))
+    extra_v = np.array([behind, [0.8, 0.05, 0.9], [-0.6, 0.05, 0.7],
+                        [60.0, 40.0, 60.0], [61.0, 40.0, 60.0], [60.0, 41.0, 60.0]], np.float32)
+    V = len(v)
+    extra_t = np.array([[a, a, b], [V, V + 1, V + 2], [V + 3, V + 4, V + 5]], np.int32)
+    sc["verts"] = np.concatenate([v, extra_v]).astype(np.float32)
+    sc["tris"] = np.concatenate([t, extra_t]).astype(np.int32)
+    sc["tri_mat"] = np.concatenate([m, np.zeros(3, np.int32)]).astype(np.int32)
+    sc["name"] = scene.get("name", "scene") + "_degenerate"
+    return sc
+
+
 def jitter_vertices(scene: dict, sigma: float, seed: int) -> np.ndarray:
     """Seeded vertex perturbation used to make a target render."""
     rng = np.random.default_rng(seed)

@@ -36,6 +36,13 @@ SCENES = {
     "tiny_mixed3": lambda: _ragged_camera(scenes.tiny_scene(6, res=40, img=44, kind="mixed3", n_lights=3), 44, 37),
     "tiny_mixed_evsm": lambda: _evsm(scenes.tiny_scene(7, res=40, img=40, kind="mixed", n_lights=2), 10.0),
     "tiny_point_evsm": lambda: _evsm(scenes.tiny_scene(8, res=32, img=40, kind="point"), 20.0),
+    # culled and degenerate triangles: zero area, a non-manifold edge, a corner behind the camera, off-screen
+    "tiny_degenerate": lambda: scenes.with_degenerate_triangles(
+        scenes.tiny_scene(10, res=40, img=44, kind="mixed", n_lights=2)),
+    # the smallest sizes: one-texel maps and a one-pixel camera; three-texel maps and a 5x3 camera
+    "tiny_res1": lambda: dict(scenes.tiny_scene(11, res=1, img=1, kind="mixed", n_lights=2),
+                              camera=scenes.look_at_perspective((0.0, 3.0, 4.0), (0.1, 1.0, -0.1), 45.0, 1, 1)),
+    "tiny_res3": lambda: _ragged_camera(scenes.tiny_scene(12, res=3, img=5, kind="mixed", n_lights=2), 5, 3),
 }
 
 _cache = {}
