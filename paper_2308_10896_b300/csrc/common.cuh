@@ -57,6 +57,8 @@ struct DevStatus {
   int timeout;
   int needed_pairs[kMaxViews];
   int big_count[kMaxViews];   // triangles of each view flagged as big
+  int units[kMaxViews];       // raster work units of each view (record batches of its tiles)
+  int split[kMaxViews];       // tiles of each view raster by several units (key slots in use)
 };
 
 // Contention control for gradient scatters.  A triangle whose pixel bbox spans

@@ -56,7 +56,14 @@ struct ViewBufs {
   Buf color, gcolor, pgrad;     // camera views: colour before the final antialiasing, its adjoint, pixel gradients
   int list_cap = 0;
   BinShape bs{kTileLog2Default, kBigTilesDefault};
+  // raster work units and the key slots of tiles split over several units
+  Buf units, tile_slot, tile_done, skey;
+  int units_cap = 0, slot_cap = 0;
   AAWork aa_work() { return AAWork{aa_list.as<int>(), aa_ctr.as<int>()}; }
+  RasterUnits raster_units() {
+    return RasterUnits{units.as<int2>(), units_cap, tile_slot.as<int>(), slot_cap, tile_done.as<int>(),
+                       skey.as<unsigned long long>()};
+  }
 };
 
 struct LightBufs {
@@ -329,7 +336,7 @@ void dsm_destroy(dsm_ctx* ctx) {
   for (auto& v : ctx->view) {
     Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
                  &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr,
-                 &v.hflag, &v.color, &v.gcolor, &v.pgrad};
+                 &v.hflag, &v.color, &v.gcolor, &v.pgrad, &v.units, &v.tile_slot, &v.tile_done, &v.skey};
     for (Buf* b : vb) b->release();
   }
   for (auto& l : ctx->light) {
@@ -421,6 +428,23 @@ static dsm_status check_args(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light
   return DSM_OK;
 }
 
+// Raster work units for the view's tiles and list capacity.  The per-tile
+// counters and the key slots start at zero and every frame leaves them so;
+// they are zeroed here when (re)allocated, never while a frame is recorded.
+static dsm_status ensure_units(dsm_ctx* ctx, ViewBufs& v, bool reset = false) {
+  const size_t tiles = (size_t)v.tilesX * v.tilesY;
+  v.units_cap = (int)(tiles + (size_t)v.list_cap / kRasterBatch + 1);
+  v.slot_cap = v.list_cap / (kRasterBatch + 1) + 1;
+  DSM_CHECK(v.units.ensure((size_t)v.units_cap * sizeof(int2)));
+  DSM_CHECK(v.tile_slot.ensure(tiles * 4));
+  const size_t done_cap = v.tile_done.cap, key_cap = v.skey.cap;
+  DSM_CHECK(v.tile_done.ensure(tiles * 4));
+  DSM_CHECK(v.skey.ensure((size_t)v.slot_cap * 1024 * sizeof(unsigned long long)));
+  if (reset || v.tile_done.cap != done_cap) DSM_CHECK(cudaMemset(v.tile_done.p, 0, v.tile_done.cap));
+  if (reset || v.skey.cap != key_cap) DSM_CHECK(cudaMemset(v.skey.p, 0, v.skey.cap));
+  return DSM_OK;
+}
+
 static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, int T, bool is_light) {
   v.W = W;
   v.H = H;
@@ -457,7 +481,7 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
     DSM_CHECK(v.list.ensure(cap * 4));
     v.list_cap = (int)cap;
   }
-  return DSM_OK;
+  return ensure_units(ctx, v);
 }
 
 namespace {
@@ -512,7 +536,8 @@ dsm_status grow_list(dsm_ctx* ctx, ViewBufs& v, long long need) {
   if (cap > 0x7fffffffLL) return fail(ctx, DSM_ERR_CAPACITY, "tile list above 2^31 entries");
   DSM_CHECK(v.list.ensure((size_t)cap * 4));
   v.list_cap = (int)cap;
-  return DSM_OK;
+  // (a frame that overflowed the old list may have left tiles unmerged)
+  return ensure_units(ctx, v, true);
 }
 
 // Exponent of the moments' warp (0: variance shadow maps).
@@ -569,7 +594,7 @@ void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
   launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,
                 v.bs.tile_log2, v.W, v.H, v.clip.as<float4>(), ctx->mesh.tris, v.gbuf.as<float4>(),
                 light ? v.depth.as<float>() : nullptr, light ? lwork(ctx, w).fmap.as<float2>() : nullptr,
-                warp_exponent(ctx), st);
+                warp_exponent(ctx), v.raster_units(), ds, w, st);
 }
 
 // Alg. 1 after the raster: antialiasing of f, f^2 at the listed texels, then
@@ -1285,7 +1310,7 @@ uint64_t dsm_memory_bytes(dsm_ctx* ctx) {
   for (const auto& v : ctx->view) {
     const Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
                        &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr,
-                       &v.hflag, &v.color, &v.gcolor, &v.pgrad};
+                       &v.hflag, &v.color, &v.gcolor, &v.pgrad, &v.units, &v.tile_slot, &v.tile_done, &v.skey};
     for (const Buf* b : vb) n += b->cap;
   }
   for (const auto& l : ctx->light) {

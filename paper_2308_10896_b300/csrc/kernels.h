@@ -144,6 +144,20 @@ void launch_setup_all(const float* verts, int V, const int* tris, int T, const i
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, cudaStream_t st);
 void launch_bin_count(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, DevStatus* status,
                       int view, int* big_index, int* big_tri, cudaStream_t st);
+// Raster work units of one view.  A tile's list is rastered kRasterBatch
+// records per unit (one CTA each); a tile of several units merges their
+// per-pixel minimum keys in a key slot (global 64-bit maxima of the inverted
+// keys, 0 = empty) and its last unit to finish writes the G-buffer, then
+// empties the slot and its counter again.
+constexpr int kRasterBatch = 1024;   // records per unit (four batches of 256)
+struct RasterUnits {
+  int2* units;                 // (tile, batch) per unit, units_cap entries
+  int units_cap;               // tiles + list capacity / kRasterBatch + 1 (an upper bound)
+  int* tile_slot;              // key slot of a tile of several units, or -1
+  int slot_cap;                // list capacity / (kRasterBatch + 1) + 1 (an upper bound)
+  int* tile_done;              // units finished per tile (zero between frames)
+  unsigned long long* skey;    // slot_cap x 1024 inverted keys (zero between frames)
+};
 // Segment of every tile in the view's triangle list (begin, end) from the
 // per-tile counts; clears the counts for the fill pass.
 void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st);
@@ -158,7 +172,7 @@ void launch_raster_stats(const TriSetup* setup, const int* offset, const int* li
 // of every texel, f interpolated from the per-vertex light depths.
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
                    int tile_log2, int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth,
-                   float2* fmap, float ec, cudaStream_t st);
+                   float2* fmap, float ec, const RasterUnits& ru, DevStatus* status, int view, cudaStream_t st);
 
 // shadow-map interpolation and antialiasing
 // Antialiasing (detection + list passes, see aa.cu).

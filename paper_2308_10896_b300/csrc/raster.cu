@@ -274,6 +274,8 @@ __global__ void tri_setup_all_kernel(const int* __restrict__ tris, int T, ViewSe
   if (t < kMaxViews) {
     status->big_count[t] = 0;
     status->needed_pairs[t] = 0;
+    status->units[t] = 0;
+    status->split[t] = 0;
   }
   if (t < a.n && a.aa_count[t]) *a.aa_count[t] = 0;
   if (t >= T) return;
@@ -451,6 +453,35 @@ __global__ void alloc_kernel(int* __restrict__ count, int n, int* __restrict__ o
   }
 }
 
+// Raster work units of the tiles, from their list segments: one unit per
+// kRasterBatch records (at least one per tile), handed out by one atomic per
+// warp on status->units, and a key slot for a tile of several units.  (The
+// bounds hold whenever the list fits its capacity; a frame that overflows it
+// is reported and only has to stay in bounds.)
+__global__ void units_kernel(const int* __restrict__ offset, int n, DevStatus* status, int view, RasterUnits ru) {
+  const int tile = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+  const int nb = tile < n ? max(1, (offset[n + tile] - offset[tile] + kRasterBatch - 1) / kRasterBatch) : 0;
+  int incl = nb;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += u;
+  }
+  int base = 0;
+  if (lane == 31 && incl > 0) base = atomicAdd(&status->units[view], incl);
+  base = __shfl_sync(kFull, base, 31);
+  if (tile < n) {
+    const int u0 = base + incl - nb;
+    for (int b = 0; b < nb && u0 + b < ru.units_cap; ++b) ru.units[u0 + b] = make_int2(tile, b);
+    int slot = -1;
+    if (nb > 1) {
+      slot = atomicAdd(&status->split[view], 1);
+      if (slot >= ru.slot_cap) slot = -1;
+    }
+    ru.tile_slot[tile] = slot;
+  }
+}
+
 // ------------------------------------------------------------------ tile rasteriser
 // Coverage of pixel centre (Px, Py) by a setup record: integer edge functions
 // with the top-left rule; returns the depth key or ~0.  The record is read as
@@ -583,10 +614,11 @@ template <int kTL>
 __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restrict__ setup,
                                                      const int* __restrict__ offset,
                                                      const int* __restrict__ list, int capacity, int tilesX,
-                                                     int W, int H, const float4* __restrict__ clip,
+                                                     int n_tiles, int W, int H, const float4* __restrict__ clip,
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf,
                                                      const float* __restrict__ depth, float2* __restrict__ fmap,
-                                                     float ec) {
+                                                     float ec, RasterUnits ru, const DevStatus* __restrict__ status,
+                                                     int view) {
   constexpr int kTile = 1 << kTL;
   constexpr int kPix = kTile * kTile;
   static_assert(kTile <= 32, "tile-local coordinates are packed in 5 bits");
@@ -597,18 +629,28 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
   __shared__ int sinv[256];          // ceil(2^16 / spans per bbox row)
   __shared__ unsigned short sown[kChunk];   // owning record + 1 of each item of the chunk
   __shared__ int swarp[8];
-  const int tile = blockIdx.x;
+  __shared__ int slast;
+  // this CTA's work unit: records [beg, lim) of one tile
+  if ((int)blockIdx.x >= min(status->units[view], ru.units_cap)) return;
+  const int2 unit = ru.units[blockIdx.x];
+  const int tile = unit.x, batch = unit.y;
+  const int o0 = offset[tile], o1 = offset[n_tiles + tile];
+  const int nb = max(1, (o1 - o0 + kRasterBatch - 1) / kRasterBatch);
+  const int slot = nb > 1 ? ru.tile_slot[tile] : -1;
+  if (nb > 1 && slot < 0 && batch > 0) return;   // no key slot: the tile's first unit takes all its records
+  // slots past the list capacity were never written (the fill pass flagged the overflow)
+  const int end = min(o1, capacity);
+  const int beg = min(slot >= 0 ? o0 + kRasterBatch * batch : o0, end);
+  const int lim = slot >= 0 ? min(end, beg + kRasterBatch) : end;
   const int ti = tile % tilesX, tj = tile / tilesX;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ti0 = ti * kTile, tj0 = tj * kTile;
   const long long Px0 = (long long)ti0 * kSubpix + 128, Py0 = (long long)tj0 * kSubpix + 128;
   for (int q = tid; q < kPix; q += 256) sbest[q] = ~0ull;
-  // slots past the list capacity were never written (the fill pass flagged the overflow)
-  const int beg = min(offset[tile], capacity), end = min(offset[gridDim.x + tile], capacity);
-  for (int base = beg; base < end; base += 256) {
+  for (int base = beg; base < lim; base += 256) {
     const int k = base + tid;
     int area = 0, box = 0, inv = 0;
-    if (k < end) {
+    if (k < lim) {
       const TriSetup r = setup[list[k]];
       const int i0 = max(r.ibox & 0xffff, ti0), i1 = min((int)((unsigned)r.ibox >> 16), ti0 + kTile - 1);
       const int j0 = max(r.jbox & 0xffff, tj0), j1 = min((int)((unsigned)r.jbox >> 16), tj0 + kTile - 1);
@@ -691,6 +733,27 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
       }
       __syncthreads();
     }
+  }
+  if (slot >= 0) {
+    // fold this unit's minima into the tile's key slot; the last unit of the
+    // tile takes the merged keys (and empties the slot for the next frame)
+    unsigned long long* kb = ru.skey + (size_t)slot * 1024;
+    for (int px = tid; px < kPix; px += 256) {
+      const unsigned long long v = sbest[px];
+      if (v != ~0ull) atomicMax(&kb[px], ~v);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) slast = atomicAdd(&ru.tile_done[tile], 1) == nb - 1;
+    __syncthreads();
+    if (!slast) return;
+    __threadfence();
+    for (int px = tid; px < kPix; px += 256) {
+      sbest[px] = ~__ldcg(&kb[px]);
+      kb[px] = 0ull;
+    }
+    if (tid == 0) ru.tile_done[tile] = 0;
+    __syncthreads();
   }
   for (int px = tid; px < kPix; px += 256) {
     const int i = ti0 + (px & (kTile - 1)), j = tj0 + (px >> kTL);
@@ -804,14 +867,16 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int*
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
                    int tile_log2, int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth,
-                   float2* fmap, float ec, cudaStream_t st) {
-  count_launches(1);
+                   float2* fmap, float ec, const RasterUnits& ru, DevStatus* status, int view, cudaStream_t st) {
+  const int n = tilesX * tilesY;
+  count_launches(2);
+  units_kernel<<<(n + 255) / 256, 256, 0, st>>>(offset, n, status, view, ru);
   if (tile_log2 == 4)
-    raster_kernel<4><<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf,
-                                                      depth, fmap, ec);
+    raster_kernel<4><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, tris, gbuf,
+                                                  depth, fmap, ec, ru, status, view);
   else
-    raster_kernel<5><<<tilesX * tilesY, 256, 0, st>>>(setup, offset, list, capacity, tilesX, W, H, clip, tris, gbuf,
-                                                      depth, fmap, ec);
+    raster_kernel<5><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, tris, gbuf,
+                                                  depth, fmap, ec, ru, status, view);
 }
 
 void launch_raster_stats(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX,

@@ -43,6 +43,9 @@ SCENES = {
     "tiny_res1": lambda: dict(scenes.tiny_scene(11, res=1, img=1, kind="mixed", n_lights=2),
                               camera=scenes.look_at_perspective((0.0, 3.0, 4.0), (0.1, 1.0, -0.1), 45.0, 1, 1)),
     "tiny_res3": lambda: _ragged_camera(scenes.tiny_scene(12, res=3, img=5, kind="mixed", n_lights=2), 5, 3),
+    # a dense sphere (2880 triangles within a few tiles): tiles of thousands of records, rastered by
+    # several work units whose minima merge in a key slot
+    "tiny_dense": lambda: scenes.tiny_scene(16, res=64, img=48, kind="mixed", n_lights=2, freq=12),
 }
 
 _cache = {}
