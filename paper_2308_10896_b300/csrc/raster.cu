@@ -595,8 +595,10 @@ __device__ __forceinline__ void cover_span(const int* w, int xs, int xe, int y, 
   }
 }
 
-// One 256-thread CTA per tile of kTile x kTile pixels (kTile = 2^kTL, 16 or
-// 32).  The tile's triangle list is read 256 records at a time.  Every record
+// One 256-thread CTA per work unit: up to kRasterBatch records of the list of
+// one tile of kTile x kTile pixels (kTile = 2^kTL, 16 or 32); a tile with
+// more records has several units, which merge their minima in the tile's key
+// slot.  The unit's records are read 256 at a time.  Every record
 // contributes the spans of its bbox-in-tile (kSpan pixels of one row each) as
 // work items; a block prefix sum turns them into one flat list that all
 // threads stride over (balanced whatever the triangle sizes), and each

@@ -120,3 +120,41 @@ def test_maximum_views_bit_exact():
     sc5, _ = _four_point_lights(5)
     with pytest.raises(dsm.DsmError):
         dsm.Renderer(sc5).forward_cameras(cams[:1])
+
+
+def test_list_overflow_reported_and_recovered():
+    """A frame whose tile-triangle pairs exceed the lists sized by an earlier
+    frame of the same mesh is reported (DSM_ERR_CAPACITY at the next sync,
+    every write of the frame kept in bounds); rendering again re-sizes and
+    gives the G-buffers and image of a fresh context.  (A sphere of 180
+    triangles grown 4x about its centre: 1175 -> 4563 pairs in the 1024^2
+    light view, against lists of 3436 entries.)"""
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    sc = scenes.tiny_scene(18, res=1024, img=64, kind="directional", n_lights=1, freq=3)
+    shape = dict(light_tile=32, camera_tile=32, big_tiles=64)
+    r = dsm.Renderer(sc)
+    r.ctx.set_tuning(**shape)
+    r.forward()
+    r.ctx.sync()
+    pairs_before = r.ctx.raster_stats(0)["pairs"]
+    big = np.asarray(sc["verts"], np.float32).copy()
+    centre = np.array([0.1, 1.0, -0.1], np.float32)
+    big[:-4] = (big[:-4] - centre) * 4.0 + centre          # the sphere; the last four are the ground
+    vbig = torch.as_tensor(big, device="cuda")
+    r.forward(verts=vbig)
+    with pytest.raises(dsm.DsmError) as err:
+        r.ctx.sync()
+    assert err.value.status == dsm.DSM_ERR_CAPACITY
+    img = r.forward(verts=vbig).cpu()
+    r.ctx.sync()
+    fresh = dsm.Renderer(dict(sc, verts=big))
+    fresh.ctx.set_tuning(**shape)
+    img_f = fresh.forward().cpu()
+    fresh.ctx.sync()
+    assert fresh.ctx.raster_stats(0)["pairs"] > pairs_before
+    for w, (W, H) in enumerate([(1024, 1024), (64, 64)]):
+        a = r.ctx.debug(dsm.DBG_GBUF, w, (H, W, 4)).cpu()
+        b = fresh.ctx.debug(dsm.DBG_GBUF, w, (H, W, 4)).cpu()
+        assert torch.equal(a, b), f"view {w}"
+    assert torch.equal(img, img_f)
