@@ -981,6 +981,16 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
   }
   DSM_CHECK(cudaGetLastError());
 
+  // ---- normals: dL/dn of the cameras' pixels onto the vertices.  Its inputs
+  // come from the cameras' adjoints; it adds to dverts with plain
+  // read-modify-writes, so it runs on st after the camera scatters and before
+  // the vertex gather.
+  auto normals = [&]() {
+    StageTimer t(ctx, ST_BWD_VERTEX, st);
+    launch_normals_backward(mesh.verts, V, mesh.tris, T, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
+                            ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), ctx->gnormal.as<float>(),
+                            ctx->gN.as<float>(), ctx->gface.as<float>(), dL_dverts, st);
+  };
   if (ctx->recompute) {
     // ---- the filtered moment maps again (every camera's shading adjoint reads all of them)
     ctx->stage_override = ST_BWD_RECOMPUTE;
@@ -1024,6 +1034,7 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
       StageTimer t(ctx, ST_BWD_VERTEX, st);
       vertex_backward_views(ctx, l, 1, dL_dverts, red_stride, st);
     }
+    normals();
   } else {
     // ---- per camera: final antialiasing adjoint and the shading adjoint
     DSM_CHECK(ensure_streams(ctx));
@@ -1040,17 +1051,16 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     for (int l = 0; l < L; ++l) light_backward(ctx, l, view_stream(ctx, l, st));
     for (int c = 0; c < C; ++c)
       camera_scatter(ctx, c, dL_dverts, dL_dalbedo, red_stride, C > 1 ? view_stream(ctx, L + c, st) : st);
-    DSM_CHECK(join_views(ctx, st, 0, L));
     if (C > 1) DSM_CHECK(join_views(ctx, st, L, NV));
+    normals();   // beside the light views' adjoints
+    DSM_CHECK(join_views(ctx, st, 0, L));
     StageTimer t(ctx, ST_BWD_VERTEX, st);
     vertex_backward_views(ctx, 0, NV, dL_dverts, red_stride, st);
   }
-  // ---- normals, lights
+  // ---- the light matrices' and direct terms' block sums (the vertex gather
+  // adds the light views' share), then the lights' parameters
   {
     StageTimer t(ctx, ST_BWD_VERTEX, st);
-    launch_normals_backward(mesh.verts, V, mesh.tris, T, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
-                            ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), ctx->gnormal.as<float>(),
-                            ctx->gN.as<float>(), ctx->gface.as<float>(), dL_dverts, st);
     launch_red_reduce(ctx->red.as<float>(), red_stride, L, n_mat_red, ctx->gQ.as<float>(), ctx->gdirect.as<float>(),
                       dL_dalbedo, st);
     launch_light_grad(ctx->lights_dev.as<LightDev>(), L, ctx->n_user, ctx->gQ.as<float>(), ctx->gdirect.as<float>(),
