@@ -109,7 +109,7 @@ struct dsm_ctx {
   uint64_t sized_sig = 0;
   // internal streams: one per view (lights, then cameras), fork/join events
   cudaStream_t vs[kMaxViews] = {};
-  cudaEvent_t ev_fork = nullptr, ev_bfork = nullptr, ev_join[kMaxViews] = {};
+  cudaEvent_t ev_fork = nullptr, ev_bfork = nullptr, ev_sil = nullptr, ev_join[kMaxViews] = {};
   // per-stage timing (stage_override >= 0 books every stage under that one)
   bool prof = false;
   int stage_override = -1;
@@ -230,6 +230,7 @@ cudaError_t ensure_streams(dsm_ctx* c) {
     if ((e = cudaStreamCreateWithFlags(&v, cudaStreamNonBlocking)) != cudaSuccess) return e;
   if ((e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
   if ((e = cudaEventCreateWithFlags(&c->ev_bfork, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&c->ev_sil, cudaEventDisableTiming)) != cudaSuccess) return e;
   for (auto& ev : c->ev_join)
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -348,6 +349,7 @@ void dsm_destroy(dsm_ctx* ctx) {
   for (auto v : ctx->vs) if (v) cudaStreamDestroy(v);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_bfork) cudaEventDestroy(ctx->ev_bfork);
+  if (ctx->ev_sil) cudaEventDestroy(ctx->ev_sil);
   for (auto e : ctx->ev_join) if (e) cudaEventDestroy(e);
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   delete ctx;
@@ -550,7 +552,7 @@ AAArgs aa_args(const dsm_ctx* ctx, ViewBufs& v) {
 
 // Transform, triangle setup and silhouettes of views [w0, w0 + n) in one fused
 // pass, which also empties their tile counters and antialiasing lists.
-void setup_views(dsm_ctx* ctx, int w0, int n, cudaStream_t st) {
+ViewSetupArgs view_setup_args(dsm_ctx* ctx, int w0, int n) {
   ViewSetupArgs va{};
   va.n = n;
   for (int k = 0; k < n; ++k) {
@@ -566,9 +568,17 @@ void setup_views(dsm_ctx* ctx, int w0, int n, cudaStream_t st) {
     va.count[k] = v.count.as<int>();
     va.aa_count[k] = v.aa_ctr.as<int>();
   }
+  return va;
+}
+
+void setup_views(dsm_ctx* ctx, int w0, int n, cudaStream_t st, bool silhouettes = true) {
   const dsm_mesh& m = ctx->mesh;
-  launch_setup_all(m.verts, m.n_verts, m.tris, m.n_tris, ctx->adj.as<int>(), ctx->viewM.as<float>() + 20 * w0, va,
-                   ctx->status.as<DevStatus>(), st);
+  launch_setup_all(m.verts, m.n_verts, m.tris, m.n_tris, ctx->adj.as<int>(), ctx->viewM.as<float>() + 20 * w0,
+                   view_setup_args(ctx, w0, n), ctx->status.as<DevStatus>(), silhouettes, st);
+}
+
+void silhouette_views(dsm_ctx* ctx, int w0, int n, cudaStream_t st) {
+  launch_silhouettes_all(ctx->adj.as<int>(), ctx->mesh.n_tris, view_setup_args(ctx, w0, n), st);
 }
 
 void bin_count_view(dsm_ctx* ctx, int w, cudaStream_t st) {
@@ -856,8 +866,9 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
       }
     }
   } else {
-    // every view at once: transform, triangle setup, silhouettes
-    setup_views(ctx, 0, NV, st);
+    // every view at once: transform, triangle setup (the silhouettes follow
+    // beside the binning: only the antialiasing reads them)
+    setup_views(ctx, 0, NV, st, false);
     t_setup.stop();
     // ---- per view on its own stream: bin count, scan (the views are independent until shading)
     DSM_CHECK(ensure_streams(ctx));
@@ -869,6 +880,11 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
                             ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), cst);
     }
     for (int w = 0; w < NV; ++w) bin_count_view(ctx, w, view_stream(ctx, w, st));
+    {
+      StageTimer ts(ctx, ST_SETUP, st);
+      silhouette_views(ctx, 0, NV, st);
+    }
+    DSM_CHECK(cudaEventRecord(ctx->ev_sil, st));
     DSM_CHECK(cudaGetLastError());
     if (sizing) {
       // first frame of this scene size: read the pair counts once and size the lists
@@ -886,6 +902,7 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
       cudaStream_t vst = view_stream(ctx, w, st);
       raster_view(ctx, w, vst);
       if (w < L) {
+        if (vst != st) DSM_CHECK(cudaStreamWaitEvent(vst, ctx->ev_sil, 0));
         light_maps(ctx, w, vst);
         const LightBufs& lb = ctx->light[w];
         DSM_CHECK(cudaMemsetAsync(lb.gm.p, 0, (size_t)lb.res * lb.res * sizeof(float2), vst));

@@ -137,10 +137,13 @@ struct ViewSetupArgs {
   int* count[kMaxViews];          // tile counters, zeroed by the setup
   int* aa_count[kMaxViews];       // antialiasing work-list counters, zeroed by the setup
 };
-// Transform, triangle setup and silhouettes of every view; also zeroes the tile
-// counters and the big-triangle counts for the binning that follows.
+// Transform, triangle setup and (when `silhouettes`) silhouettes of every
+// view; also zeroes the tile counters and the big-triangle counts for the
+// binning that follows.  The silhouettes (needed only by the antialiasing) may
+// instead follow later through launch_silhouettes_all.
 void launch_setup_all(const float* verts, int V, const int* tris, int T, const int* adj, const float* viewM,
-                      const ViewSetupArgs& a, DevStatus* status, cudaStream_t st);
+                      const ViewSetupArgs& a, DevStatus* status, bool silhouettes, cudaStream_t st);
+void launch_silhouettes_all(const int* adj, int T, const ViewSetupArgs& a, cudaStream_t st);
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, cudaStream_t st);
 void launch_bin_count(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, DevStatus* status,
                       int view, int* big_index, int* big_tri, cudaStream_t st);

@@ -824,17 +824,20 @@ void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* 
 }
 
 void launch_setup_all(const float* verts, int V, const int* tris, int T, const int* adj, const float* viewM,
-                      const ViewSetupArgs& a, DevStatus* status, cudaStream_t st) {
+                      const ViewSetupArgs& a, DevStatus* status, bool silhouettes, cudaStream_t st) {
   if (V > 0) {
     count_launches(1);
     transform_all_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, viewM, a);
   }
   count_launches(1);
   tri_setup_all_kernel<<<std::max((T + 255) / 256, 64), 256, 0, st>>>(tris, T, a, status);
-  if (T > 0) {
-    count_launches(1);
-    silhouette_all_kernel<<<(T + 255) / 256, 256, 0, st>>>(adj, T, a);
-  }
+  if (silhouettes) launch_silhouettes_all(adj, T, a, st);
+}
+
+void launch_silhouettes_all(const int* adj, int T, const ViewSetupArgs& a, cudaStream_t st) {
+  if (T == 0) return;
+  count_launches(1);
+  silhouette_all_kernel<<<(T + 255) / 256, 256, 0, st>>>(adj, T, a);
 }
 
 void launch_bin_count(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, DevStatus* status,
