@@ -587,7 +587,8 @@ void bin_count_view(dsm_ctx* ctx, int w, cudaStream_t st) {
   StageTimer t(ctx, ST_SETUP, st);
   launch_bin_count(v.setup.as<TriSetup>(), ctx->mesh.n_tris, v.tilesX, v.bs, v.count.as<int>(), ds, w,
                    v.big_index.as<int>(), v.big_tri.as<int>(), st);
-  launch_scan(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), ds, w, st);
+  launch_scan(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), ds, w, v.setup.as<TriSetup>(),
+              v.big_tri.as<int>(), v.tilesX, v.bs.tile_log2, st);
 }
 
 // Bin fill and raster of view w (a light view also writes f, f^2).
@@ -599,6 +600,8 @@ void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
     StageTimer t(ctx, ST_BIN_FILL, st);
     launch_bin_fill(v.setup.as<TriSetup>(), ctx->mesh.n_tris, v.tilesX, v.bs, v.count.as<int>(), v.offset.as<int>(),
                     v.list.as<int>(), v.list_cap, ds, w, v.big_index.as<int>(), v.big_tri.as<int>(), st);
+    launch_units(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,
+                 v.bs.tile_log2, v.raster_units(), ds, w, v.big_tri.as<int>(), v.count.as<int>(), st);
   }
   StageTimer t(ctx, ST_RASTER, st);
   launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,

@@ -163,7 +163,8 @@ struct RasterUnits {
 };
 // Segment of every tile in the view's triangle list (begin, end) from the
 // per-tile counts; clears the counts for the fill pass.
-void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st);
+void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, const TriSetup* setup,
+                 const int* big_tri, int tilesX, int tile_log2, cudaStream_t st);
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, const int* offset,
                      int* list, int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
                      cudaStream_t st);
@@ -176,6 +177,12 @@ void launch_raster_stats(const TriSetup* setup, const int* offset, const int* li
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
                    int tile_log2, int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth,
                    float2* fmap, float ec, const RasterUnits& ru, DevStatus* status, int view, cudaStream_t st);
+// After the fill pass (filled: its per-tile counts of ordinary triangles):
+// appends each tile's big triangles to its segment and hands out the raster
+// work units and key slots.
+void launch_units(const TriSetup* setup, const int* offset, int* list, int capacity, int tilesX, int tilesY,
+                  int tile_log2, const RasterUnits& ru, DevStatus* status, int view, const int* big_tri,
+                  const int* filled, cudaStream_t st);
 
 // shadow-map interpolation and antialiasing
 // Antialiasing (detection + list passes, see aa.cu).

@@ -330,7 +330,7 @@ __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX
     }
     big_index[t] = b;
   }
-  // big triangles are binned by bin_big_kernel, spread over the whole grid
+  // big triangles are binned per tile by the segment and work-unit passes
   if (t < T && n >= bs.big_tiles && big_index[t] >= 0) n = 0;
   int incl = n;
 #pragma unroll
@@ -396,47 +396,32 @@ __device__ __forceinline__ bool tile_may_cover(const TriSetup& r, int tx, int ty
   return true;
 }
 
-// Binning of the big triangles: blockIdx.y strides over the triangles, the
-// tiles of a bbox are spread over gridDim.x blocks; tiles it cannot cover are
-// skipped.
-constexpr int kBigGridX = 64, kBigGridY = 2;
-template <bool kFill>
-__global__ void bin_big_kernel(const TriSetup* __restrict__ setup, const int* __restrict__ big_tri,
-                               const DevStatus* __restrict__ status, int view, int tilesX, int tl,
-                               int* __restrict__ counter, const int* __restrict__ offset, int* __restrict__ list,
-                               int capacity, DevStatus* wstatus) {
-  const int nb = min(status->big_count[view], kMaxBig);
-  for (int b = blockIdx.y; b < nb; b += gridDim.y) {
-    const int t = big_tri[b];
-    const TriSetup r = setup[t];
-    const int i0 = r.ibox & 0xffff, i1 = (unsigned)r.ibox >> 16, j0 = r.jbox & 0xffff, j1 = (unsigned)r.jbox >> 16;
-    const int tx0 = i0 >> tl, ty0 = j0 >> tl;
-    const int ntx = (i1 >> tl) - tx0 + 1, nty = (j1 >> tl) - ty0 + 1;
-    const int n = ntx * nty;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-      const int tx = tx0 + q % ntx, ty = ty0 + q / ntx;
-      if (!tile_may_cover(r, tx, ty, tl)) continue;
-      const int tile = ty * tilesX + tx;
-      if (!kFill) {
-        atomicAdd(&counter[tile], 1);
-      } else {
-        const int slot = offset[tile] + atomicAdd(&counter[tile], 1);
-        if (slot < capacity) list[slot] = t;
-        else atomicExch(&wstatus->capacity_overflow, 1);
-      }
-    }
-  }
+// Whether big triangle r may cover tile (tx, ty): inside its bbox's tile
+// range and not excluded by the corner test.  The big triangles (at most
+// kMaxBig per view, listed by the count pass) are binned per tile by the
+// segment and work-unit passes instead of per triangle.
+__device__ __forceinline__ bool big_covers_tile(const TriSetup& r, int tx, int ty, int tl) {
+  const int i0 = r.ibox & 0xffff, i1 = (unsigned)r.ibox >> 16, j0 = r.jbox & 0xffff, j1 = (unsigned)r.jbox >> 16;
+  if (tx < (i0 >> tl) || tx > (i1 >> tl) || ty < (j0 >> tl) || ty > (j1 >> tl)) return false;
+  return tile_may_cover(r, tx, ty, tl);
 }
 
-// List segments of the tiles: tile k owns [offset[k], offset[n + k]) of the
+// List segments of the tiles (their ordinary triangles counted by the count
+// pass, their big ones here): tile k owns [offset[k], offset[n + k]) of the
 // view's triangle list.  Segments are handed out by one atomic per warp on the
 // view's running total (status->needed_pairs, zeroed by the setup), so they
 // are not in tile order (nothing depends on that order).  Also clears the
 // counters for the fill pass; the running total tells the host the list size.
 __global__ void alloc_kernel(int* __restrict__ count, int n, int* __restrict__ offset, DevStatus* status,
-                             int view) {
+                             int view, const TriSetup* __restrict__ setup, const int* __restrict__ big_tri,
+                             int tilesX, int tl) {
   const int tile = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
-  const int c = tile < n ? count[tile] : 0;
+  int c = 0;
+  if (tile < n) {
+    c = count[tile];
+    const int nbig = min(status->big_count[view], kMaxBig);
+    for (int b = 0; b < nbig; ++b) c += big_covers_tile(setup[big_tri[b]], tile % tilesX, tile / tilesX, tl);
+  }
   int incl = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -458,8 +443,23 @@ __global__ void alloc_kernel(int* __restrict__ count, int n, int* __restrict__ o
 // warp on status->units, and a key slot for a tile of several units.  (The
 // bounds hold whenever the list fits its capacity; a frame that overflows it
 // is reported and only has to stay in bounds.)
-__global__ void units_kernel(const int* __restrict__ offset, int n, DevStatus* status, int view, RasterUnits ru) {
+__global__ void units_kernel(const int* __restrict__ offset, int n, DevStatus* status, int view, RasterUnits ru,
+                             const TriSetup* __restrict__ setup, const int* __restrict__ big_tri,
+                             const int* __restrict__ filled, int* __restrict__ list, int capacity, int tilesX,
+                             int tl) {
   const int tile = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+  if (tile < n) {
+    // the tile's big triangles follow its ordinary ones in its segment
+    int k = offset[tile] + filled[tile];
+    const int nbig = min(status->big_count[view], kMaxBig);
+    for (int b = 0; b < nbig; ++b) {
+      const int t = big_tri[b];
+      if (!big_covers_tile(setup[t], tile % tilesX, tile / tilesX, tl)) continue;
+      if (k < capacity) list[k] = t;
+      else atomicExch(&status->capacity_overflow, 1);
+      ++k;
+    }
+  }
   const int nb = tile < n ? max(1, (offset[n + tile] - offset[tile] + kRasterBatch - 1) / kRasterBatch) : 0;
   int incl = nb;
 #pragma unroll
@@ -846,15 +846,12 @@ void launch_bin_count(const TriSetup* setup, int T, int tilesX, BinShape bs, int
   count_launches(1);
   bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, bs, counter, nullptr, nullptr, 0, status,
                                                      view, big_index, big_tri);
-  count_launches(1);
-  bin_big_kernel<false><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX,
-                                                                     bs.tile_log2, counter, nullptr, nullptr, 0,
-                                                                     status);
 }
 
-void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, cudaStream_t st) {
+void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, const TriSetup* setup,
+                 const int* big_tri, int tilesX, int tile_log2, cudaStream_t st) {
   count_launches(1);
-  alloc_kernel<<<(n + 255) / 256, 256, 0, st>>>(count, n, offset, status, view);
+  alloc_kernel<<<(n + 255) / 256, 256, 0, st>>>(count, n, offset, status, view, setup, big_tri, tilesX, tile_log2);
 }
 
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, const int* offset,
@@ -864,18 +861,22 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int*
   count_launches(1);
   bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, bs, counter, offset, list, capacity, status,
                                                     view, const_cast<int*>(big_index), const_cast<int*>(big_tri));
+}
+
+void launch_units(const TriSetup* setup, const int* offset, int* list, int capacity, int tilesX, int tilesY,
+                  int tile_log2, const RasterUnits& ru, DevStatus* status, int view, const int* big_tri,
+                  const int* filled, cudaStream_t st) {
+  const int n = tilesX * tilesY;
   count_launches(1);
-  bin_big_kernel<true><<<dim3(kBigGridX, kBigGridY), 256, 0, st>>>(setup, big_tri, status, view, tilesX,
-                                                                    bs.tile_log2, counter, offset, list, capacity,
-                                                                    status);
+  units_kernel<<<(n + 255) / 256, 256, 0, st>>>(offset, n, status, view, ru, setup, big_tri, filled, list, capacity,
+                                                tilesX, tile_log2);
 }
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
                    int tile_log2, int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth,
                    float2* fmap, float ec, const RasterUnits& ru, DevStatus* status, int view, cudaStream_t st) {
   const int n = tilesX * tilesY;
-  count_launches(2);
-  units_kernel<<<(n + 255) / 256, 256, 0, st>>>(offset, n, status, view, ru);
+  count_launches(1);
   if (tile_log2 == 4)
     raster_kernel<4><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, tris, gbuf,
                                                   depth, fmap, ec, ru, status, view);
