@@ -201,8 +201,9 @@ typedef struct dsm_tuning {
   int32_t light_tile;    /* raster tile side of the light views, pixels: 16 or 32                 */
   int32_t camera_tile;   /* raster tile side of the camera views: 16 or 32                        */
   int32_t big_tiles;     /* bin depth: a triangle whose bbox spans at least this many tiles is
-                            binned by the big-triangle kernel (tiles spread over many blocks) and
-                            its backward sums go to private copies; 2..4096                       */
+                            "big" (the first 64 of a view): binned per tile, each tile testing
+                            the view's big triangles, and its backward sums go to private
+                            copies; 2..4096                                                       */
   int32_t filter_shape;  /* 0: input tiles staged by the TMA in a persistent double-buffered kernel
                             (radius <= 8, map side a multiple of 16, no antialiased patch to
                             substitute; otherwise shape 2); 1: two 1-D passes; 2: both passes

@@ -63,8 +63,9 @@ struct DevStatus {
 
 // Contention control for gradient scatters.  A triangle whose pixel bbox spans
 // at least big_tiles raster tiles (a binning parameter of the view, default
-// kBigTilesDefault) is "big": it is binned by a kernel that spreads its tiles
-// over many blocks, and in the backward its per-triangle sums go to
+// kBigTilesDefault) is "big": it is binned per tile (each tile tests the
+// view's few big triangles) rather than per triangle, and in the backward its
+// per-triangle sums go to
 // kBigSlots private copies (spread over L2) instead of straight onto its three
 // vertices, and a resolve kernel adds the copies up.  Block-level reductions
 // of the light and albedo gradients likewise go to kRedSlots copies.
