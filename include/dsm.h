@@ -300,7 +300,8 @@ dsm_status dsm_filter_moments_noalloc(const float* in, float* out, int32_t res, 
  *
  * Each scene has its own context (dsm_batch_context: set its topology there
  * before the first step; its debug copies work as usual) and its own stream,
- * with the scene's views serialised on that stream; the scenes overlap.  The
+ * its views on the context's own streams forked from it; the scenes, and the
+ * views within each scene, overlap.  The
  * first step with a given set of items and params runs eagerly (it sizes
  * every context; this is the only step with host synchronisation) and then
  * records the same step into one CUDA graph; a later step whose items

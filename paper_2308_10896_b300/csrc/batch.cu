@@ -1,8 +1,8 @@
 // Batched frames: n independent scenes advanced by one call per step
 // (forward, L2 loss, backward of every scene).  Each scene keeps its own
-// context (its scratch and saved state) and runs on its own stream with its
-// views serialised on that stream; the scenes overlap one another (a batch of
-// one scene keeps its views on their own streams instead).  The first
+// context (its scratch and saved state) and runs on its own stream, its views
+// on the context's own streams forked from it; the scenes overlap one another
+// and so do the views within each scene.  The first
 // step with a given set of buffers runs eagerly, which sizes every context,
 // and then records the same step into one CUDA graph; later steps with the
 // same buffers replay the graph with a single launch.
@@ -15,7 +15,6 @@
 #include "kernels.h"
 
 namespace dsm {
-void set_serial_views(dsm_ctx* ctx, bool serial);
 dsm_status tuning_search(dsm_tuning* cur, float* cur_ms,
                          const std::function<dsm_status(const dsm_tuning&, float*)>& measure);
 }
@@ -112,8 +111,6 @@ dsm_status dsm_batch_create(dsm_batch** out, int32_t n) {
   dsm_status st = DSM_OK;
   for (int i = 0; i < n && st == DSM_OK; ++i) {
     st = dsm_create(&b->ctx[i]);
-    // several scenes overlap one another; a lone scene overlaps its own views
-    if (st == DSM_OK) dsm::set_serial_views(b->ctx[i], n > 1);
     if (st == DSM_OK && cudaStreamCreateWithFlags(&b->ss[i], cudaStreamNonBlocking) != cudaSuccess)
       st = DSM_ERR_CUDA;
     if (st == DSM_OK && cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming) != cudaSuccess)

@@ -113,8 +113,6 @@ struct dsm_ctx {
   // per-stage timing (stage_override >= 0 books every stage under that one)
   bool prof = false;
   int stage_override = -1;
-  // views serialised on the caller's stream (batched scenes overlap one another instead)
-  bool serial = false;
   struct Rec { int stage; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> free_events;
@@ -240,12 +238,12 @@ cudaError_t ensure_streams(dsm_ctx* c) {
 // on (profiling serialises the views so that each stage's events bracket only
 // its own kernels).
 cudaStream_t view_stream(const dsm_ctx* c, int w, cudaStream_t st) {
-  return (c->prof || c->serial) ? st : c->vs[w];
+  return c->prof ? st : c->vs[w];
 }
 
 // The streams of views [w0, w1) wait for the work enqueued so far on st.
 cudaError_t fork_views(dsm_ctx* c, cudaStream_t st, cudaEvent_t ev, int w0, int w1) {
-  if (c->prof || c->serial || w1 <= w0) return cudaSuccess;
+  if (c->prof || w1 <= w0) return cudaSuccess;
   cudaError_t e = cudaEventRecord(ev, st);
   for (int w = w0; w < w1 && e == cudaSuccess; ++w) e = cudaStreamWaitEvent(c->vs[w], ev, 0);
   return e;
@@ -253,7 +251,7 @@ cudaError_t fork_views(dsm_ctx* c, cudaStream_t st, cudaEvent_t ev, int w0, int 
 
 // st waits for the work enqueued so far on the streams of views [w0, w1).
 cudaError_t join_views(dsm_ctx* c, cudaStream_t st, int w0, int w1) {
-  if (c->prof || c->serial) return cudaSuccess;
+  if (c->prof) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   for (int w = w0; w < w1 && e == cudaSuccess; ++w) {
     e = cudaEventRecord(c->ev_join[w], c->vs[w]);
@@ -270,11 +268,6 @@ uint64_t mix(uint64_t h, uint64_t v) {
 }  // namespace
 
 namespace dsm {
-// Batched scenes: each context keeps its views on the caller's stream.
-void set_serial_views(dsm_ctx* ctx, bool serial) {
-  if (ctx) ctx->serial = serial;
-}
-
 // Coordinate search over the kernel shapes: from *cur (timed as *cur_ms by
 // the caller), each knob in turn -- light tile, camera tile, bin depth from
 // {4, 16, 64}, filter shape -- is set to each of its other values and kept
