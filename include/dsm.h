@@ -257,7 +257,9 @@ dsm_status dsm_l2_loss_grad(const float* image, const float* target, int64_t n,
  * at most 32; kind: 0 Gaussian, 1 box (equal taps); boundary: 0 clamp to the
  * edge texel, 1 zero outside the map.  Radii up to 15 take one tiled kernel;
  * larger radii take two 1-D passes through ctx scratch (may allocate).
- * DSM_ERR_INVALID_ARG for bad arguments, DSM_ERR_CUDA on a launch error.
+ * DSM_ERR_INVALID_ARG for bad arguments: kind or boundary not 0 or 1, radius
+ * above 32, or no finite sigma > 0 where one is needed (always for the
+ * Gaussian, and for the box when radius <= 0).  DSM_ERR_CUDA on a launch error.
  * stream: cudaStream_t (NULL = legacy default stream). */
 dsm_status dsm_filter_moments(dsm_ctx* ctx, const float* in, float* out, int32_t res,
                               float sigma, int32_t radius, int32_t kind, int32_t boundary,
@@ -273,21 +275,26 @@ dsm_status dsm_filter_moments_adjoint(dsm_ctx* ctx, const float* gout, float* gi
                                       float sigma, int32_t radius, int32_t kind, int32_t boundary,
                                       void* stream);
 
-/* Allocation-free variant of dsm_filter_moments, for callers that must not
- * allocate device memory while they run (a real-time loop with a fixed memory
- * budget, code between the begin and end of a stream capture, or an
- * application that owns the device memory pool).  The paper has no
- * counterpart; it is the same separable filter (same result as
- * dsm_filter_moments for the same arguments).  in, out: device, res x res
- * float2, must not overlap; the caller owns both.  The intermediate map lives
- * in a static device array of the library (1024 x 1024 texels, 8 MiB, held
- * by every GPU that loads the library until the process exits); no call
- * allocates or frees memory.  The first call on a device looks up that
- * array's device address once (make it before any stream capture on that
- * device).  Every call shares the array: calls whose work overlaps on the GPU
- * (two streams, or two threads) race on it; serialise them.  Returns
- * DSM_ERR_CAPACITY when res * res exceeds 1024 * 1024, DSM_ERR_INVALID_ARG for
- * other bad arguments, DSM_ERR_CUDA when the device lookup or the launch
+/* Allocation-free variant of dsm_filter_moments.  The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory while
+ * they run, such as a real-time loop that works inside a fixed, preallocated
+ * memory budget, or a host application that owns the device memory pool and
+ * lets no other allocator touch the device.  (dsm_filter_moments may grow its
+ * context's scratch with cudaMalloc.)  It computes the same separable filter
+ * with the same result as dsm_filter_moments for the same arguments.
+ * in, out: device, res x res float2, must not overlap; the caller owns both.
+ * No call allocates or frees memory.  Radii up to 15 run as one tiled kernel
+ * with no intermediate map.  Radii 16 to 32 run as two 1-D passes whose
+ * intermediate map lives in a static device array of the library (1024 x 1024
+ * texels, 8 MiB, held by every GPU that loads the library until the process
+ * exits).  The first call on a device looks up that array's device address
+ * and caches it; make that first call before any stream capture on the
+ * device, and do not use the library on a device again after cudaDeviceReset.
+ * For radii 16 to 32 every call shares the array: such calls whose work
+ * overlaps on the GPU (two streams, or two threads) race on it, so serialise
+ * them.  Returns DSM_ERR_CAPACITY when res * res exceeds 1024 * 1024,
+ * DSM_ERR_INVALID_ARG for other bad arguments (the rules of
+ * dsm_filter_moments), DSM_ERR_CUDA when the device lookup or the launch
  * fails.  stream: cudaStream_t (NULL = legacy default stream). */
 dsm_status dsm_filter_moments_noalloc(const float* in, float* out, int32_t res, float sigma,
                                       int32_t radius, int32_t kind, int32_t boundary, void* stream);
@@ -395,9 +402,32 @@ const char* dsm_last_error(dsm_ctx* ctx);
  *    z slot holds dL/d vertex depth d, since clip z carries no gradient there)
  *  9 dL/d(f~, (f^2)~) (light), float2
  * 10 dL/d colour of camera index before the final antialiasing, float4 per pixel
+ * 11 shading-stage surface of camera index (Alg. 2 inputs, recomputed by the
+ *    shading kernel's own device functions): two float4 per pixel,
+ *    (x, y, z, 0) world position and (nx, ny, nz, 0) unit normal
+ * 12 shading-stage lookup of camera index / 64 in light view index % 64:
+ *    two float4 per pixel, (u, v, s, t) light-space position and texel
+ *    coordinates, (dw, m1, m2, vis) receiver depth in the moments' encoding,
+ *    bilinear moments and visibility (Alg. 2, Sec. 3)
+ *    11, 12: NaN where the pixel has no such value (background, a cube face
+ *    that does not shade the point, (u, v) behind the light, (s, t, m1, m2)
+ *    outside its window)
  * bytes must equal the buffer size; returns DSM_ERR_INVALID_ARG otherwise.
  * After a forward with recompute_in_backward = 1 only 3, 5 and 7 are kept. */
 dsm_status dsm_debug_copy(dsm_ctx* ctx, int32_t what, int32_t index, void* dst, size_t bytes);
+
+/* Diagnostic gradient masks for comparisons that judge gradients away from
+ * silhouettes (the paper's edge antialiasing, Sec. 5, acts only there).
+ * flags: 0 (default) or DSM_GRAD_MASK_SM_BAND: every later dsm_render_backward
+ * on ctx zeroes dL/d(f~, (f^2)~) at the shadow maps' silhouette-band texels,
+ * so no gradient flows from them.  The band: texels with a 4-neighbour of
+ * another triangle id (background included) such that the nearer surface of
+ * the pair (by depth key, ties to the lower id; the background never is) is a
+ * triangle with a silhouette edge in that view.  Every antialiasing crossing
+ * lies in it.  Only with params.aa_shadow = 1 (without antialiasing there is
+ * no band to mask).  DSM_ERR_INVALID_ARG for unknown flags. */
+#define DSM_GRAD_MASK_SM_BAND 1
+dsm_status dsm_set_grad_mask(dsm_ctx* ctx, int32_t flags);
 
 /* Per-stage device timing: while enabled, dsm_render and dsm_render_backward
  * run every view on the caller's stream (instead of one internal stream per

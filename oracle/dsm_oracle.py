@@ -48,6 +48,7 @@ W_MIN = np.float32(1e-6)
 
 __all__ = [
     "light_matrix", "light_views", "cube_face", "clip_pinned", "setup_view", "raster", "edge_adjacency", "silhouette_table",
+    "silhouette_band",
     "barycentrics", "antialias", "filter_weights", "separable_filter", "bilinear",
     "chebyshev", "moment_encode", "warp_exponent", "light_visibility", "vertex_normals", "render", "mse_loss", "render_and_grad",
     "render_cameras_and_grad", "adam_step",
@@ -312,6 +313,27 @@ def silhouette_table(adj: np.ndarray, setup: dict) -> np.ndarray:
     return sil
 
 
+def silhouette_band(ras: dict, sil: np.ndarray) -> np.ndarray:
+    """Pixels (H, W) bool in the view's silhouette band: a pixel with a
+    4-neighbour of another triangle id such that the nearer surface of the pair
+    (key order, as in ``antialias``; the background never is) is a triangle
+    with a silhouette edge in this view.  Every antialiasing crossing lies in
+    this band, so gradients judged outside it carry no edge-antialiasing term.
+    reading: the one-pixel silhouette band of the gradient comparison; a
+    4-neighbour of any other id would also take in every boundary between two
+    triangles of one smooth surface, most of a dense mesh's pixels."""
+    ids, key = ras["ids"], ras["key"]
+    has_sil = np.concatenate([[False], sil.any(1)])     # indexed by id (0 = background)
+    band = np.zeros(ids.shape, bool)
+    for A, B, kA, kB, sa, sb in ((ids[:, :-1], ids[:, 1:], key[:, :-1], key[:, 1:], np.s_[:, :-1], np.s_[:, 1:]),
+                                 (ids[:-1, :], ids[1:, :], key[:-1, :], key[1:, :], np.s_[:-1, :], np.s_[1:, :])):
+        a_occ = (B == 0) | ((A != 0) & (kA < kB))
+        m = (A != B) & has_sil[np.where(a_occ, A, B)]
+        band[sa] |= m
+        band[sb] |= m
+    return band
+
+
 # =============================================================================== interpolation
 def _pixel_ndc(W, H):
     i = torch.arange(W, dtype=F64)
@@ -533,8 +555,17 @@ def moment_encode(f: torch.Tensor, exponent: float = 0.0) -> torch.Tensor:
     return torch.stack([w, w * w], -1)
 
 
+def _stage(value: torch.Tensor, key: str, teach: dict | None, record: dict | None) -> torch.Tensor:
+    """Record this stage's own value under `key` (for a stage-wise comparison)
+    and return it, or the taught value when `teach` holds one (see
+    ``_substitute``)."""
+    if record is not None:
+        record[key] = value.detach().clone()
+    return _substitute(value, None if teach is None else teach.get(key))
+
+
 def light_visibility(Q: torch.Tensor, mom: torch.Tensor, xh: torch.Tensor, min_variance: float,
-                     exponent: float = 0.0) -> torch.Tensor:
+                     exponent: float = 0.0, teach: dict | None = None, record: dict | None = None) -> torch.Tensor:
     """Alg. 2 (ComputeVisibility) at homogeneous world points xh (n, 4):
     u = L(x) from the light clip matrix Q[0:4], texel coordinates
     s = (0.5 u_x + 0.5) R - 0.5 and t = (0.5 - 0.5 u_y) R - 0.5, bilinear (m1, m2),
@@ -542,23 +573,35 @@ def light_visibility(Q: torch.Tensor, mom: torch.Tensor, xh: torch.Tensor, min_v
     reading: points behind the light or outside its window are lit (v = 1).
     With the exponential warp (exponent c > 0) the receiver depth is compared
     as exp(c d) and the floor is min_variance (c exp(c d))^2 (reading: the
-    depth-unit floor carried by the warp's slope at the receiver)."""
+    depth-unit floor carried by the warp's slope at the receiver).
+
+    Stage-wise comparison: ``record`` receives each stage's own value and
+    ``teach`` may replace it (keeping its derivative): 'uv' (n, 2) light-space
+    position, 'st' (n, 2) texel coordinates, 'mm' (n, 2) bilinear moments,
+    'dw' (n,) receiver depth in the moments' encoding, 'vis' (n,) Chebyshev
+    visibility; NaN entries of a taught array keep the oracle's own value."""
     R = mom.shape[0]
     cl = xh @ Q[:4].T
     d = xh @ Q[4]
     wpos = cl[:, 3] > 0
     wsafe = torch.where(wpos, cl[:, 3], torch.ones_like(cl[:, 3]))
-    u, v = cl[:, 0] / wsafe, cl[:, 1] / wsafe
+    uv = _stage(torch.stack([cl[:, 0] / wsafe, cl[:, 1] / wsafe], 1), "uv", teach, record)
+    u, v = uv[:, 0], uv[:, 1]
     inside = wpos & (u.abs() <= 1) & (v.abs() <= 1)
-    s = (0.5 * u + 0.5) * R - 0.5
-    t = (0.5 - 0.5 * v) * R - 0.5
+    st = _stage(torch.stack([(0.5 * u + 0.5) * R - 0.5, (0.5 - 0.5 * v) * R - 0.5], 1), "st", teach, record)
+    s, t = st[:, 0], st[:, 1]
     zero = torch.zeros_like(s)
-    mm = bilinear(mom, torch.where(inside, s, zero), torch.where(inside, t, zero))
+    mm = _stage(bilinear(mom, torch.where(inside, s, zero), torch.where(inside, t, zero)), "mm", teach, record)
     if exponent > 0:
-        dw = torch.exp(exponent * d)
+        dw = _stage(torch.exp(exponent * d), "dw", teach, record)
         vis = chebyshev(dw, mm[:, 0], mm[:, 1], min_variance * (exponent * dw) ** 2)
     else:
-        vis = chebyshev(d, mm[:, 0], mm[:, 1], min_variance)
+        dw = _stage(d, "dw", teach, record)
+        vis = chebyshev(dw, mm[:, 0], mm[:, 1], min_variance)
+    vis = _stage(vis, "vis", teach, record)
+    if record is not None:
+        record["inside"] = inside.numpy().copy()
+        record["front"] = wpos.numpy().copy()
     return torch.where(inside, vis, torch.ones_like(vis))
 
 
@@ -575,10 +618,12 @@ def vertex_normals(verts: torch.Tensor, tris: torch.Tensor) -> torch.Tensor:
 
 # =============================================================================== pipeline
 def _substitute(value: torch.Tensor, teacher) -> torch.Tensor:
-    """Stage-wise comparison: take the given value, keep this stage's derivative."""
+    """Stage-wise comparison: take the given value, keep this stage's
+    derivative.  NaN entries of the teacher keep the stage's own value."""
     if teacher is None:
         return value
     tv = torch.as_tensor(np.asarray(teacher), dtype=F64).reshape(value.shape)
+    tv = torch.where(torch.isnan(tv), value.detach(), tv)
     return value + (tv - value).detach()
 
 
@@ -593,25 +638,56 @@ def _teacher_view(teacher: dict, key: str, view: int):
     return vals[view] if vals is not None and view < len(vals) else None
 
 
+def _pixel_teacher(teach: dict | None, key: str, jj, ii):
+    """The entries of a per-pixel teacher array (H, W, ...) at the given pixels."""
+    if teach is None or teach.get(key) is None:
+        return None
+    return np.asarray(teach[key])[jj, ii]
+
+
 def shade_pixels(scene: dict, verts: torch.Tensor, light_params: torch.Tensor, albedo: torch.Tensor, maps: list,
-                 clipc: torch.Tensor, ids: np.ndarray):
+                 clipc: torch.Tensor, ids: np.ndarray, teach: dict | None = None, record: dict | None = None):
     """Camera pass of Alg. 2 with Lambert shading (suppl. Sec. A) at the
     covered pixels of ``ids``: world position x and normal n interpolated with
     the perspective-correct barycentrics, visibility of every light from its
     (Q, moment map) in ``maps``, colour = albedo * sum_l I_l v_l max(0, n.omega_l).
-    Returns (rows, cols, rgb, per-light visibility)."""
+    Returns (rows, cols, rgb, per-light visibility).
+
+    Stage-wise comparison: ``record`` receives 'x' and 'n' (n, 3) and, per
+    light view in order, a dict of ``light_visibility``'s stage values under
+    'lookup'; ``teach`` may give full-image arrays 'x', 'n' (H, W, 3) and
+    'lookup', a list per light view of (H, W, 8) arrays (u, v, s, t, dw, m1, m2,
+    vis), NaN where a value is not taught."""
     P = scene["params"]
     tris = torch.as_tensor(scene["tris"].astype(np.int64))
     jj, ii, tri, b = barycentrics(clipc, tris, ids)
     tv = tris[tri]
-    x = (b[:, :, None] * verts[tv]).sum(1)
+    if record is not None:
+        record["pixels"] = (jj, ii)
+        record["lookup"] = []
+    x = _stage((b[:, :, None] * verts[tv]).sum(1), "x", {"x": _pixel_teacher(teach, "x", jj, ii)}, record)
     vn = vertex_normals(verts, tris)
     n = (b[:, :, None] * vn[tv]).sum(1)
-    n = n / torch.sqrt((n * n).sum(1, keepdim=True))
+    n = _stage(n / torch.sqrt((n * n).sum(1, keepdim=True)), "n", {"n": _pixel_teacher(teach, "n", jj, ii)}, record)
     xh = torch.cat([x, torch.ones((x.shape[0], 1), dtype=F64)], 1)
     ec = warp_exponent(P)
     radiance = torch.zeros((x.shape[0], 3), dtype=F64)
     vis_all = []
+    view = 0
+
+    def visibility(Q, mom):
+        nonlocal view
+        lt = None
+        if teach is not None and teach.get("lookup") is not None and view < len(teach["lookup"]):
+            a = np.asarray(teach["lookup"][view])[jj, ii]
+            lt = {"uv": a[:, 0:2], "st": a[:, 2:4], "dw": a[:, 4], "mm": a[:, 5:7], "vis": a[:, 7]}
+        rec = None
+        if record is not None:
+            rec = {}
+            record["lookup"].append(rec)
+        view += 1
+        return light_visibility(Q, mom, xh, float(P["min_variance"]), ec, lt, rec)
+
     for li, light in enumerate(scene["lights"]):
         views = maps[li] if isinstance(maps[li], list) else [maps[li]]
         if int(light["type"]) == 2:
@@ -619,10 +695,10 @@ def shade_pixels(scene: dict, verts: torch.Tensor, light_params: torch.Tensor, a
             face = torch.as_tensor(cube_face((x - light_params[li, 0:3][None, :]).detach().numpy()))
             vis = torch.zeros((x.shape[0],), dtype=F64)
             for k, (Q, mom) in enumerate(views):
-                vis = torch.where(face == k, light_visibility(Q, mom, xh, float(P["min_variance"]), ec), vis)
+                vis = torch.where(face == k, visibility(Q, mom), vis)
         else:
             Q, mom = views[0]
-            vis = light_visibility(Q, mom, xh, float(P["min_variance"]), ec)
+            vis = visibility(Q, mom)
         if int(light["type"]) == 0:
             dl = light_params[li, 3:6]
             omega = -(dl / torch.sqrt((dl * dl).sum()))[None, :].expand_as(x)
@@ -643,16 +719,22 @@ def _light_params(scene: dict) -> np.ndarray:
 
 
 def render(scene: dict, verts: torch.Tensor = None, light_params: torch.Tensor = None,
-           albedo: torch.Tensor = None, teacher: dict = None, keep: bool = True) -> dict:
+           albedo: torch.Tensor = None, teacher: dict = None, keep: bool = True,
+           grad_mask_sm_band: bool = False) -> dict:
     """Forward pass: Alg. 1 per light view (one per directional or spot light,
     six cube faces per point light), then the camera pass with Alg. 2 and
     Lambert shading, then the final antialiasing.
 
     ``light_params`` is (L, 6) float64: (pos xyz, dir xyz) per light.
     ``teacher`` optionally replaces stage values ('ftilde', 'moments' lists per
-    light view, 'color') by given ones while keeping each stage's derivative.
+    light view, 'color', and the shading stages 'x', 'n', 'lookup' of
+    ``shade_pixels``) by given ones while keeping each stage's derivative.
+    With ``grad_mask_sm_band`` the gradient reaching f~ is zeroed at every
+    light view's silhouette band (``silhouette_band``); a dict {"on": bool}
+    instead of a bool switches that mask per backward pass.
     Returns a dict with the image (H, W, 4: RGB and coverage) and every
-    intermediate ('lights' holds one entry per light view)."""
+    intermediate ('lights' holds one entry per light view; 'shading' the
+    shading stages' own values, see ``shade_pixels``)."""
     P = scene["params"]
     tris_np = scene["tris"].astype(np.int64)
     tris = torch.as_tensor(tris_np)
@@ -686,13 +768,17 @@ def render(scene: dict, verts: torch.Tensor = None, light_params: torch.Tensor =
             # background texels hold the encoding of f = 1
             fmap = moment_encode(torch.ones((R, R), dtype=F64), ec)
             fmap = fmap.index_put((torch.as_tensor(jj), torch.as_tensor(ii)), moment_encode(f, ec))
+            sil = silhouette_table(adj, st)
             if P.get("aa_shadow", 1):
-                sil = silhouette_table(adj, st)
                 sx, sy = screen_coords(clip, R, R)
                 ft = antialias(fmap, ras, st, sil, tris_np, sx, sy)
             else:
                 ft = fmap
             ft = _substitute(ft, _teacher_view(teach, "ftilde", view))
+            if grad_mask_sm_band and P.get("aa_shadow", 1) and ft.requires_grad:
+                switch = grad_mask_sm_band if isinstance(grad_mask_sm_band, dict) else {"on": True}
+                keep_grad = torch.as_tensor(~silhouette_band(ras, sil), dtype=F64)[:, :, None]
+                ft.register_hook(lambda g, k=keep_grad, sw=switch: g * k if sw["on"] else g)
             w = filter_weights(light["sigma"], light["radius"], P.get("filter_kind", 0))
             mom = separable_filter(ft, w, P.get("filter_boundary", 0))
             mom = _substitute(mom, _teacher_view(teach, "moments", view))
@@ -707,19 +793,22 @@ def render(scene: dict, verts: torch.Tensor = None, light_params: torch.Tensor =
     stc = setup_view(clip_pinned(M32, V32), tris_np, Wc, Hc)
     rasc = raster(stc, tris_np)
     clipc = vh @ torch.as_tensor(M32, dtype=F64).T
-    jj, ii, rgb, vis_all = shade_pixels(scene, verts, light_params, albedo, maps, clipc, rasc["ids"])
+    shading = {}
+    jj, ii, rgb, vis_all = shade_pixels(scene, verts, light_params, albedo, maps, clipc, rasc["ids"], teach,
+                                        shading if keep else None)
     color = torch.zeros((Hc, Wc, 4), dtype=F64)
     color = color.index_put((torch.as_tensor(jj), torch.as_tensor(ii)),
                             torch.cat([rgb, torch.ones((rgb.shape[0], 1), dtype=F64)], 1))
     color = _substitute(color, (teacher or {}).get("color"))
+    silc = silhouette_table(adj, stc)
     if P.get("aa_final", 1):
-        silc = silhouette_table(adj, stc)
         sxc, syc = screen_coords(clipc, Wc, Hc)
         image = antialias(color, rasc, stc, silc, tris_np, sxc, syc)
     else:
         image = color
     out.update({"image": image, "color": color, "camera_setup": stc, "camera_raster": rasc,
-                "visibility": vis_all, "pixels": (jj, ii)})
+                "camera_band": silhouette_band(rasc, silc), "visibility": vis_all, "pixels": (jj, ii),
+                "shading": shading})
     return out
 
 
@@ -730,17 +819,45 @@ def mse_loss(image: torch.Tensor, target) -> torch.Tensor:
     return ((image - tgt) ** 2).mean()
 
 
-def render_and_grad(scene: dict, target, teacher: dict = None, verts=None, light_params=None) -> dict:
+def render_and_grad(scene: dict, target, teacher: dict = None, verts=None, light_params=None, grad_image=None,
+                    grad_mask_sm_band: bool = False, objectives: list = None) -> dict:
     """Forward, loss and reverse-mode gradients with respect to the vertices,
-    the light parameters (pos xyz, dir xyz per light) and the albedo table."""
+    the light parameters (pos xyz, dir xyz per light) and the albedo table.
+    The gradients are those of the mean squared error against ``target``, or,
+    when ``grad_image`` (H, W, 4) is given, of sum(image * grad_image): the
+    backward of a given dL/dimage (the loss is still reported when a target is
+    given).  ``grad_mask_sm_band``: see ``render``.  ``objectives``, a list of
+    (grad_image or None for the loss, mask the shadow maps' bands, zero
+    grad_image on the camera's silhouette band), adds one backward pass of the
+    same forward per entry: 'objective_grads' holds their (verts, light,
+    albedo) gradients."""
     v = torch.as_tensor(scene["verts"] if verts is None else verts, dtype=F64).clone().requires_grad_(True)
     if light_params is None:
         light_params = _light_params(scene)
     lp = torch.as_tensor(light_params, dtype=F64).clone().requires_grad_(True)
     al = torch.as_tensor(scene["albedo"], dtype=F64).clone().requires_grad_(True)
-    out = render(scene, v, lp, al, teacher=teacher)
-    loss = mse_loss(out["image"], target)
-    gv, gl, ga = torch.autograd.grad(loss, [v, lp, al], allow_unused=True)
+    switch = {"on": bool(grad_mask_sm_band)}
+    need_mask = bool(grad_mask_sm_band) or any(o[1] for o in (objectives or []))
+    out = render(scene, v, lp, al, teacher=teacher, grad_mask_sm_band=switch if need_mask else False)
+    loss = mse_loss(out["image"], target) if target is not None else torch.zeros((), dtype=F64)
+
+    def objective(gimg):
+        if gimg is None:
+            return loss
+        return (out["image"] * torch.as_tensor(np.asarray(gimg), dtype=F64)).sum()
+
+    extra = []
+    for gimg, masked, cam_band in objectives or []:
+        switch["on"] = bool(masked)
+        if cam_band and gimg is not None:
+            gimg = np.asarray(gimg) * (~out["camera_band"])[:, :, None]
+        extra.append(torch.autograd.grad(objective(gimg), [v, lp, al], allow_unused=True, retain_graph=True))
+    out["objective_grads"] = extra
+    switch["on"] = bool(grad_mask_sm_band)
+    if target is None and grad_image is None:
+        gv = gl = ga = None            # only the listed objectives were asked for
+    else:
+        gv, gl, ga = torch.autograd.grad(objective(grad_image), [v, lp, al], allow_unused=True)
     out.update({"loss": loss.detach(), "grad_verts": gv, "grad_light": gl, "grad_albedo": ga})
     return out
 

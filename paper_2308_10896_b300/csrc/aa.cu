@@ -18,6 +18,16 @@ struct Cross {
   float dt[4];      // dt / d(xa, ya, xb, yb) in screen pixels (when active)
 };
 
+// Unsnapped screen position (pixels, y down) of vertex v relative to the
+// centre of pixel (i, j): sx - (i + 1/2) = (W x - (2i + 1 - W) w) / 2w and
+// sy - (j + 1/2) = -(H y - (H - 2j - 1) w) / 2w, numerators by pix_rel.
+__device__ __forceinline__ float2 rel_screen(const AAArgs& a, int v, int i, int j) {
+  const float4 h = a.clip[v], l = a.clip_lo[v];
+  const float i2w = 0.5f / h.w;
+  return make_float2(pix_rel(h.x, l.x, h.w, l.w, pix_nx(i, a.W), (float)a.W) * i2w,
+                     -pix_rel(h.y, l.y, h.w, l.w, pix_ny(j, a.H), (float)a.H) * i2w);
+}
+
 template <bool kGrad>
 __device__ __forceinline__ Cross find_crossing(const AAArgs& a, int tri, int io, int jo, int in, int jn,
                                                bool vertical) {
@@ -51,15 +61,19 @@ __device__ __forceinline__ Cross find_crossing(const AAArgs& a, int tri, int io,
     c.found = 1;
     c.va = va;
     c.vb = vb;
-    const float2 sa = screen_of(a.clip[va], a.W, a.H), sb = screen_of(a.clip[vb], a.W, a.H);
-    // along-coordinate p, across-coordinate q (q = const line)
-    float pa, qa, pb, qb, lc, opos, step;
+    // unsnapped screen positions of the endpoints relative to O's pixel centre,
+    // from the clip coordinates' hi + lo (pix_rel): accurate to float32
+    // relative to these small offsets, not to the view's size
+    const float2 sa = rel_screen(a, va, io, jo), sb = rel_screen(a, vb, io, jo);
+    // along-coordinate p, across-coordinate q (q = 0 is the line through both
+    // centres, p = 0 is O's centre)
+    float pa, qa, pb, qb, step;
     if (vertical) {
       pa = sa.y; qa = sa.x; pb = sb.y; qb = sb.x;
-      lc = io + 0.5f; opos = jo + 0.5f; step = (jn > jo) ? 1.f : -1.f;
+      step = (jn > jo) ? 1.f : -1.f;
     } else {
       pa = sa.x; qa = sa.y; pb = sb.x; qb = sb.y;
-      lc = jo + 0.5f; opos = io + 0.5f; step = (in > io) ? 1.f : -1.f;
+      step = (in > io) ? 1.f : -1.f;
     }
     const float dq = qb - qa;
     if (dq == 0.f) {
@@ -67,10 +81,10 @@ __device__ __forceinline__ Cross find_crossing(const AAArgs& a, int tri, int io,
       c.active = 0;
       return c;
     }
-    const float s = (lc - qa) / dq;
+    const float s = -qa / dq;
     const float r = (pb - pa) / dq;
     const float cross = pa + s * (pb - pa);
-    const float traw = (cross - opos) * step;
+    const float traw = cross * step;
     c.t = fminf(fmaxf(traw, 0.f), 1.f);
     c.active = (traw > 0.f && traw < 1.f);
     if (kGrad) {
@@ -483,13 +497,15 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
       t = id - 1;
       // the triangle's corners are reloaded per texel (L1 hits): keeping them
       // live across rows costs more in occupancy than the loads
+      float4 cl[3];
       for (int k = 0; k < 3; ++k) {
         const int v = a.tris[3 * t + k];
         cc[k] = a.clip[v];
+        cl[k] = a.clip_lo[v];
         cd[k] = depth[v];
       }
       const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
-      const Bary r = bary_at(cc[0], cc[1], cc[2], px, py);
+      const Bary r = bary_at(cc, cl, i, j, a.W, a.H);
       const float b[3] = {g.y, g.z, 1.f - g.y - g.z};
       float gb[3];
       for (int k = 0; k < 3; ++k) gb[k] = cd[k] * gf;
@@ -567,6 +583,26 @@ void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gou
   count_launches(2);
   aa_backward4_kernel<<<(n + 255) / 256, 256, 0, st>>>(hflag, gout, gcolor, n);
   aa_backward4_list_kernel<<<kListGrid, 256, 0, st>>>(a, color, gout, gcolor, gclip, w);
+}
+
+// Diagnostic (dsm_set_grad_mask): zero dL/df~ and dL/df at the texels of the
+// shadow map's silhouette band, the texels the detection pass flagged: those
+// with a 4-neighbour of another triangle id whose pair's nearer surface has a
+// silhouette edge in this view.  Every antialiasing crossing lies in that
+// band, so with the mask the backward carries no edge-antialiasing term of the
+// map and no interpolation term of a band texel.
+__global__ void sm_band_mask_kernel(const uint8_t* __restrict__ hflag, int n, float2* __restrict__ gft,
+                                    float* __restrict__ gf) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n && hflag[p]) {
+    gft[p] = make_float2(0.f, 0.f);
+    gf[p] = 0.f;
+  }
+}
+
+void launch_sm_band_mask(const uint8_t* hflag, int n, float2* gft, float* gf, cudaStream_t st) {
+  count_launches(1);
+  sm_band_mask_kernel<<<(n + 255) / 256, 256, 0, st>>>(hflag, n, gft, gf);
 }
 
 }  // namespace dsm

@@ -98,12 +98,6 @@ __device__ __forceinline__ uint64_t depth_key(float z, int tri) {
 __device__ __forceinline__ int edge_p(int e) { return e; }
 __device__ __forceinline__ int edge_q(int e) { return e == 2 ? 0 : e + 1; }
 
-// Unsnapped screen position (pixels, y down) of a clip-space vertex.
-__device__ __forceinline__ float2 screen_of(float4 c, int W, int H) {
-  float iw = 1.0f / c.w;
-  return make_float2((0.5f * c.x * iw + 0.5f) * W, (0.5f - 0.5f * c.y * iw) * H);
-}
-
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 // Moment channels of a shadow-map depth sample f: (w, w^2) with w = f
 // (variance shadow maps) or w = exp(ec f) (exponential variance shadow maps,
@@ -141,8 +135,48 @@ template <typename V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-// Perspective-correct barycentrics at ndc point (px, py) of the triangle with
-// clip vertices c0..c2: b ~ a x c with a_k = x_k - px w_k, c_k = y_k - py w_k.
+// Error-free float32 transformations: a b = p + e (one fused multiply-add)
+// and a + b = s + e (Knuth's two-sum), both exact.  The explicitly rounded
+// intrinsics keep the compiler from contracting or reordering them.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Clip coordinates are held as hi + lo: hi is the pinned float32 transform
+// (the raster's discrete decisions use it), lo its rounding residual against
+// the exact product of the vertex with the view matrix (see
+// transform_all_kernel).  Quantities measured from a pixel centre are formed
+// from hi + lo without the float32 cancellation between a vertex and a nearby
+// pixel: pix_rel = S x - n w for x = xh + xl, w = wh + wl and the pixel-centre
+// ndc n / S (n = 2i + 1 - S an exact integer, S the view side), with the
+// leading part S xh - n wh rounded once (its product S xh split exactly) and
+// the residual terms added.  Its error is a few float32 ulps of the result,
+// whereas x - (n / S) w in plain float32 loses the digits the two terms share.
+__device__ __forceinline__ float pix_rel(float xh, float xl, float wh, float wl, float n, float S) {
+  float p, pe;
+  two_prod(S, xh, p, pe);
+  const float q = __fmaf_rn(-n, wh, p);
+  const float r = __fmaf_rn(S, xl, __fmaf_rn(-n, wl, pe));
+  return __fadd_rn(q, r);
+}
+
+// Pixel-centre numerators: the centre of column i is at ndc nx / W, of row j
+// at ndc ny / H.
+__device__ __forceinline__ float pix_nx(int i, int W) { return (float)(2 * i + 1 - W); }
+__device__ __forceinline__ float pix_ny(int j, int H) { return (float)(H - 2 * j - 1); }
+
+// Perspective-correct barycentrics at the centre of pixel (i, j) of the
+// triangle with clip vertices hi[k] + lo[k]: b ~ a x c with a_k = x_k - px w_k,
+// c_k = y_k - py w_k (px, py the centre's ndc).  a and c are formed with
+// pix_rel and scaled by 1/W and 1/H: a common scale of all three a_k (or c_k)
+// leaves b unchanged, so b keeps float32 accuracy relative to the triangle's
+// own size even for sub-pixel triangles far from the view's origin.
 struct Bary {
   float b[3];
   float a[3], c[3];
@@ -150,10 +184,15 @@ struct Bary {
   float S;
 };
 
-__device__ __forceinline__ Bary bary_at(float4 c0, float4 c1, float4 c2, float px, float py) {
+__device__ __forceinline__ Bary bary_at(const float4 (&hi)[3], const float4 (&lo)[3], int i, int j, int W, int H) {
   Bary r;
-  r.a[0] = fmaf(-px, c0.w, c0.x); r.a[1] = fmaf(-px, c1.w, c1.x); r.a[2] = fmaf(-px, c2.w, c2.x);
-  r.c[0] = fmaf(-py, c0.w, c0.y); r.c[1] = fmaf(-py, c1.w, c1.y); r.c[2] = fmaf(-py, c2.w, c2.y);
+  const float nx = pix_nx(i, W), ny = pix_ny(j, H), Wf = (float)W, Hf = (float)H;
+  const float iW = 1.0f / Wf, iH = 1.0f / Hf;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r.a[k] = pix_rel(hi[k].x, lo[k].x, hi[k].w, lo[k].w, nx, Wf) * iW;
+    r.c[k] = pix_rel(hi[k].y, lo[k].y, hi[k].w, lo[k].w, ny, Hf) * iH;
+  }
   r.beta[0] = r.a[1] * r.c[2] - r.a[2] * r.c[1];
   r.beta[1] = r.a[2] * r.c[0] - r.a[0] * r.c[2];
   r.beta[2] = r.a[0] * r.c[1] - r.a[1] * r.c[0];

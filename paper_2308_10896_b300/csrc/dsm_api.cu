@@ -60,6 +60,8 @@ struct ViewBufs {
   Buf units, tile_slot, tile_done, skey;
   int units_cap = 0, slot_cap = 0;
   AAWork aa_work() { return AAWork{aa_list.as<int>(), aa_ctr.as<int>()}; }
+  // the clip buffer holds V hi entries, then their V rounding residuals
+  float4* clip_lo(int V) { return clip.as<float4>() + std::max(V, 1); }
   RasterUnits raster_units() {
     return RasterUnits{units.as<int2>(), units_cap, tile_slot.as<int>(), slot_cap, tile_done.as<int>(),
                        skey.as<unsigned long long>()};
@@ -83,7 +85,7 @@ struct dsm_ctx {
   Buf adj, vf_off, vf_list;
   ViewBufs view[kMaxViews];
   LightBufs light[kMaxLightViews];
-  Buf lights_dev, viewM, status, vnormal, vnlen, gnormal, gN, gface, gQ, gdirect, red;
+  Buf lights_dev, viewM, viewMlo, status, vnormal, vnlen, gnormal, gN, gface, gQ, gdirect, red;
   Buf scratch_dverts, scratch_dlight, scratch_dalbedo, filter_tmp, stats;
   DevStatus* hstatus = nullptr;
   // state of the last forward
@@ -105,6 +107,8 @@ struct dsm_ctx {
   // recompute_in_backward: the views share two buffer sets (one for the
   // lights, one for the cameras) and the backward rebuilds what it reads
   bool recompute = false;
+  // diagnostic gradient masks (dsm_set_grad_mask)
+  int grad_mask = 0;
   cudaStream_t stream = nullptr;
   uint64_t sized_sig = 0;
   // internal streams: one per view (lights, then cameras), fork/join events
@@ -323,7 +327,7 @@ dsm_status dsm_create(dsm_ctx** out) {
 void dsm_destroy(dsm_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
-  Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->status,
+  Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->viewMlo, &ctx->status,
                  &ctx->vnormal, &ctx->vnlen, &ctx->gnormal, &ctx->gN, &ctx->gface, &ctx->gQ, &ctx->gdirect,
                  &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo, &ctx->filter_tmp, &ctx->red};
   for (Buf* b : bufs) b->release();
@@ -408,12 +412,14 @@ static dsm_status check_args(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light
     if (L.type != 0 && !(L.near_plane > 0.f)) return fail(ctx, DSM_ERR_INVALID_ARG, "perspective near must be > 0");
     if (L.type == 0 && !(L.ortho_half > 0.f)) return fail(ctx, DSM_ERR_INVALID_ARG, "ortho_half must be positive");
     if (L.type == 1 && !(L.fov_y_deg > 0.f && L.fov_y_deg < 180.f)) return fail(ctx, DSM_ERR_INVALID_ARG, "bad fov");
-    if (!(L.sigma > 0.f) && L.radius <= 0) return fail(ctx, DSM_ERR_INVALID_ARG, "filter needs sigma or radius");
-    if (L.radius > 32) return fail(ctx, DSM_ERR_INVALID_ARG, "filter radius above 32");
   }
   if (params->filter_kind != 0 && params->filter_kind != 1) return fail(ctx, DSM_ERR_INVALID_ARG, "filter_kind");
   if (params->filter_boundary != 0 && params->filter_boundary != 1)
     return fail(ctx, DSM_ERR_INVALID_ARG, "filter_boundary");
+  for (int l = 0; l < n_lights; ++l)
+    if (!filter_args_ok(lights[l].sigma, lights[l].radius, params->filter_kind, params->filter_boundary))
+      return fail(ctx, DSM_ERR_INVALID_ARG,
+                  "light filter: radius above 32, or no finite sigma > 0 where the filter needs one");
   if (params->recompute_in_backward != 0 && params->recompute_in_backward != 1)
     return fail(ctx, DSM_ERR_INVALID_ARG, "recompute_in_backward");
   if (!(params->min_variance >= 0.f)) return fail(ctx, DSM_ERR_INVALID_ARG, "min_variance");
@@ -451,7 +457,7 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   v.tilesY = (H + tile - 1) / tile;
   const size_t tiles = (size_t)v.tilesX * v.tilesY;
   const size_t Vn = std::max(V, 1), Tn = std::max(T, 1);
-  DSM_CHECK(v.clip.ensure(Vn * sizeof(float4)));
+  DSM_CHECK(v.clip.ensure(2 * Vn * sizeof(float4)));   // hi, then the rounding residual lo
   DSM_CHECK(v.snap.ensure(Vn * sizeof(VertSnap)));
   DSM_CHECK(v.setup.ensure(Tn * sizeof(TriSetup)));
   DSM_CHECK(v.orient.ensure(Tn));
@@ -540,7 +546,7 @@ float warp_exponent(const dsm_ctx* ctx) { return ctx->params.moments == 1 ? ctx-
 
 AAArgs aa_args(const dsm_ctx* ctx, ViewBufs& v) {
   return AAArgs{v.gbuf.as<float4>(), v.W, v.H, ctx->mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(),
-                v.clip.as<float4>()};
+                v.clip.as<float4>(), v.clip_lo(ctx->mesh.n_verts)};
 }
 
 // Transform, triangle setup and silhouettes of views [w0, w0 + n) in one fused
@@ -553,6 +559,7 @@ ViewSetupArgs view_setup_args(dsm_ctx* ctx, int w0, int n) {
     ViewBufs& v = vbuf(ctx, w);
     va.W[k] = v.W; va.H[k] = v.H; va.tiles[k] = v.tilesX * v.tilesY;
     va.clip[k] = v.clip.as<float4>();
+    va.clip_lo[k] = v.clip_lo(ctx->mesh.n_verts);
     va.snap[k] = v.snap.as<VertSnap>();
     va.depth[k] = view_is_light(ctx, w) ? v.depth.as<float>() : nullptr;
     va.setup[k] = v.setup.as<TriSetup>();
@@ -567,6 +574,7 @@ ViewSetupArgs view_setup_args(dsm_ctx* ctx, int w0, int n) {
 void setup_views(dsm_ctx* ctx, int w0, int n, cudaStream_t st, bool silhouettes = true) {
   const dsm_mesh& m = ctx->mesh;
   launch_setup_all(m.verts, m.n_verts, m.tris, m.n_tris, ctx->adj.as<int>(), ctx->viewM.as<float>() + 20 * w0,
+                   ctx->viewMlo.as<float>() + 16 * w0,
                    view_setup_args(ctx, w0, n), ctx->status.as<DevStatus>(), silhouettes, st);
 }
 
@@ -598,7 +606,8 @@ void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
   }
   StageTimer t(ctx, ST_RASTER, st);
   launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,
-                v.bs.tile_log2, v.W, v.H, v.clip.as<float4>(), ctx->mesh.tris, v.gbuf.as<float4>(),
+                v.bs.tile_log2, v.W, v.H, v.clip.as<float4>(), v.clip_lo(ctx->mesh.n_verts), ctx->mesh.tris,
+                v.gbuf.as<float4>(),
                 light ? v.depth.as<float>() : nullptr, light ? lwork(ctx, w).fmap.as<float2>() : nullptr,
                 warp_exponent(ctx), v.raster_units(), ds, w, st);
 }
@@ -634,6 +643,7 @@ ShadeArgs shade_args(dsm_ctx* ctx, int c) {
   sa.albedo = m.albedo; sa.n_mat = m.n_materials;
   sa.vnormal = ctx->vnormal.as<float>();
   sa.cam_clip = cv.clip.as<float4>();
+  sa.cam_clip_lo = cv.clip_lo(m.n_verts);
   sa.lights = ctx->lights_dev.as<LightDev>(); sa.L = ctx->L;
   for (int l = 0; l < ctx->L; ++l) { sa.mom[l] = ctx->light[l].mom.as<float2>(); sa.res[l] = ctx->light[l].res; }
   sa.min_variance = ctx->params.min_variance;
@@ -650,7 +660,7 @@ ShadeGradArgs grad_args(dsm_ctx* ctx, int c, float* dverts, float* dalbedo, int 
   ga.gclip = cv.gclip.as<float4>();
   ga.dalbedo = dalbedo;
   for (int l = 0; l < ctx->L; ++l) ga.gm[l] = ctx->light[l].gm.as<float2>();
-  ga.red = ctx->red.as<float>();
+  ga.red = ctx->red.as<double>();
   ga.red_stride = red_stride;
   ga.big = cv.big_index.as<int>();
   ga.big_acc = cv.big_acc.as<float>();
@@ -719,6 +729,10 @@ void light_backward(dsm_ctx* ctx, int l, cudaStream_t st) {
     launch_filter_adjoint(lb.gm.as<float2>(), wk.tmp.as<float2>(), wk.gft.as<float2>(), v.W, lb.fa, st,
                           wk.fmap.as<float2>(), wk.tmp.as<float>(), warp_exponent(ctx), ctx->status.as<DevStatus>());
   }
+  // the band is the antialiasing detection's flag map, so it exists only with
+  // the shadow maps' antialiasing on
+  if ((ctx->grad_mask & DSM_GRAD_MASK_SM_BAND) && ctx->params.aa_shadow)
+    launch_sm_band_mask(v.hflag.as<uint8_t>(), v.W * v.H, wk.gft.as<float2>(), wk.tmp.as<float>(), st);
   {
     StageTimer t(ctx, ST_BWD_SM_AA, st);
     if (ctx->params.aa_shadow)
@@ -735,7 +749,7 @@ void vertex_backward_views(dsm_ctx* ctx, int w0, int n, float* dverts, int red_s
   VertGradPtrs gp{};
   for (int k = 0; k < n; ++k) gp.gclip[k] = vbuf(ctx, w0 + k).gclip.as<float4>();
   const int n_lights = std::max(0, std::min(n, ctx->L - w0));
-  float* red = ctx->red.as<float>() + (n_lights > 0 ? 20 * w0 : 0);
+  double* red = ctx->red.as<double>() + (n_lights > 0 ? 20 * w0 : 0);
   launch_vertex_backward(ctx->mesh.verts, ctx->mesh.n_verts, ctx->viewM.as<float>() + 20 * w0, n, n_lights, gp,
                          dverts, red, red_stride, st);
 }
@@ -768,8 +782,10 @@ dsm_status rebuild_view(dsm_ctx* ctx, int w, bool sizing, bool maps, bool detect
   return DSM_OK;
 }
 
-__global__ void set_cameras_kernel(CamMats m, int n, float* dst) {
+__global__ void set_cameras_kernel(CamMats m, int n, float* dst, float* dst_lo) {
   for (int k = threadIdx.x; k < 20 * n; k += blockDim.x) dst[k] = m.v[k];
+  // a camera's float32 matrix is exact: no residual (the slot may have held a light view's)
+  for (int k = threadIdx.x; k < 16 * n; k += blockDim.x) dst_lo[k] = 0.f;
 }
 
 }  // namespace
@@ -818,6 +834,11 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
   }
   DSM_CHECK(ctx->lights_dev.ensure(sizeof(LightDev) * kMaxLightViews));
   DSM_CHECK(ctx->viewM.ensure(sizeof(float) * 20 * kMaxViews));
+  if (!ctx->viewMlo.p) {
+    // light views' clip-row residuals (written by the light setup); camera views' stay zero
+    DSM_CHECK(ctx->viewMlo.ensure(sizeof(float) * 16 * kMaxViews));
+    DSM_CHECK(cudaMemset(ctx->viewMlo.p, 0, sizeof(float) * 16 * kMaxViews));
+  }
   DSM_CHECK(ctx->vnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->vnlen.ensure(sizeof(float) * std::max(V, 1)));
 
@@ -841,12 +862,12 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
   }
   float* viewM = ctx->viewM.as<float>();
   StageTimer t_setup(ctx, ST_SETUP, st);
-  if (L > 0) launch_light_setup(light_params, la, ctx->lights_dev.as<LightDev>(), viewM, st);
+  if (L > 0) launch_light_setup(light_params, la, ctx->lights_dev.as<LightDev>(), viewM, ctx->viewMlo.as<float>(), st);
   CamMats cm{};
   for (int c = 0; c < C; ++c)
     for (int k = 0; k < 16; ++k) cm.v[20 * c + k] = cams[c].clip[k];
   count_launches(1);
-  set_cameras_kernel<<<1, 64, 0, st>>>(cm, C, viewM + 20 * L);
+  set_cameras_kernel<<<1, 64, 0, st>>>(cm, C, viewM + 20 * L, ctx->viewMlo.as<float>() + 16 * L);
 
   if (ctx->recompute) {
     // ---- one view at a time through the shared buffer sets
@@ -957,11 +978,11 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
   DSM_CHECK(ctx->gnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->gN.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->gface.ensure(sizeof(float) * 3 * std::max(T, 1)));
-  DSM_CHECK(ctx->gQ.ensure(sizeof(float) * 20 * kMaxLightViews));
-  DSM_CHECK(ctx->gdirect.ensure(sizeof(float) * 3 * kMaxLightViews));
+  DSM_CHECK(ctx->gQ.ensure(sizeof(double) * 20 * kMaxLightViews));
+  DSM_CHECK(ctx->gdirect.ensure(sizeof(double) * 3 * kMaxLightViews));
   const int n_mat_red = mesh.n_materials <= kMaxSharedMat ? mesh.n_materials : 0;
   const int red_stride = 23 * L + 3 * n_mat_red;
-  DSM_CHECK(ctx->red.ensure(sizeof(float) * kRedSlots * std::max(red_stride, 1)));
+  DSM_CHECK(ctx->red.ensure(sizeof(double) * kRedSlots * std::max(red_stride, 1)));
   for (int l = 0; l < L; ++l) {
     const size_t R2 = (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2);
     DSM_CHECK(ctx->light[l].gm.ensure(R2));
@@ -980,9 +1001,9 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     if (ctx->n_user) cl.add(dL_dlight, sizeof(float) * 6 * ctx->n_user);
     cl.add(dL_dalbedo, sizeof(float) * 3 * mesh.n_materials);
     cl.add(ctx->gnormal.p, sizeof(float) * 3 * V);
-    cl.add(ctx->gQ.p, sizeof(float) * 20 * kMaxLightViews);
-    cl.add(ctx->gdirect.p, sizeof(float) * 3 * kMaxLightViews);
-    cl.add(ctx->red.p, sizeof(float) * kRedSlots * red_stride);
+    cl.add(ctx->gQ.p, sizeof(double) * 20 * kMaxLightViews);
+    cl.add(ctx->gdirect.p, sizeof(double) * 3 * kMaxLightViews);
+    cl.add(ctx->red.p, sizeof(double) * kRedSlots * red_stride);
     if (!ctx->gm_zeroed)
       for (int l = 0; l < L; ++l)
         cl.add(ctx->light[l].gm.p, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2));
@@ -1074,9 +1095,9 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
   // adds the light views' share), then the lights' parameters
   {
     StageTimer t(ctx, ST_BWD_VERTEX, st);
-    launch_red_reduce(ctx->red.as<float>(), red_stride, L, n_mat_red, ctx->gQ.as<float>(), ctx->gdirect.as<float>(),
+    launch_red_reduce(ctx->red.as<double>(), red_stride, L, n_mat_red, ctx->gQ.as<double>(), ctx->gdirect.as<double>(),
                       dL_dalbedo, st);
-    launch_light_grad(ctx->lights_dev.as<LightDev>(), L, ctx->n_user, ctx->gQ.as<float>(), ctx->gdirect.as<float>(),
+    launch_light_grad(ctx->lights_dev.as<LightDev>(), L, ctx->n_user, ctx->gQ.as<double>(), ctx->gdirect.as<double>(),
                       dL_dlight, st);
   }
   DSM_CHECK(cudaGetLastError());
@@ -1088,6 +1109,13 @@ dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_d
   if (!ctx) return DSM_ERR_INVALID_ARG;
   if (ctx->have_fwd && ctx->C != 1) return fail(ctx, DSM_ERR_INVALID_ARG, "last forward had several cameras");
   return dsm_render_cameras_backward(ctx, &dL_dimage, dL_dverts, dL_dlight, dL_dalbedo);
+}
+
+dsm_status dsm_set_grad_mask(dsm_ctx* ctx, int32_t flags) {
+  if (!ctx) return DSM_ERR_INVALID_ARG;
+  if (flags & ~DSM_GRAD_MASK_SM_BAND) return fail(ctx, DSM_ERR_INVALID_ARG, "unknown gradient mask flag");
+  ctx->grad_mask = flags;
+  return DSM_OK;
 }
 
 static bool tuning_ok(const dsm_tuning& t) {
@@ -1171,8 +1199,7 @@ dsm_status dsm_l2_loss_grad(const float* image, const float* target, int64_t n, 
 dsm_status dsm_filter_moments(dsm_ctx* ctx, const float* in, float* out, int32_t res, float sigma, int32_t radius,
                               int32_t kind, int32_t boundary, void* stream) {
   if (!ctx) return DSM_ERR_INVALID_ARG;
-  if (!in || !out || res < 1 || res > 16384 || (kind != 0 && kind != 1) || (boundary != 0 && boundary != 1) ||
-      radius > 32 || (!(sigma > 0.f) && radius <= 0))
+  if (!in || !out || res < 1 || res > 16384 || !filter_args_ok(sigma, radius, kind, boundary))
     return fail(ctx, DSM_ERR_INVALID_ARG, "bad filter arguments");
   DSM_CHECK(ctx->filter_tmp.ensure((size_t)res * res * sizeof(float2)));
   FilterArgs fa;
@@ -1187,8 +1214,7 @@ dsm_status dsm_filter_moments(dsm_ctx* ctx, const float* in, float* out, int32_t
 dsm_status dsm_filter_moments_adjoint(dsm_ctx* ctx, const float* gout, float* gin, int32_t res, float sigma,
                                       int32_t radius, int32_t kind, int32_t boundary, void* stream) {
   if (!ctx) return DSM_ERR_INVALID_ARG;
-  if (!gout || !gin || res < 1 || res > 16384 || (kind != 0 && kind != 1) || (boundary != 0 && boundary != 1) ||
-      radius > 32 || (!(sigma > 0.f) && radius <= 0))
+  if (!gout || !gin || res < 1 || res > 16384 || !filter_args_ok(sigma, radius, kind, boundary))
     return fail(ctx, DSM_ERR_INVALID_ARG, "bad filter arguments");
   DSM_CHECK(ctx->filter_tmp.ensure((size_t)res * res * sizeof(float2)));
   FilterArgs fa;
@@ -1279,6 +1305,19 @@ dsm_status dsm_debug_copy(dsm_ctx* ctx, int32_t what, int32_t index, void* dst, 
     case 8: if (view_ok) { src = ctx->view[index].gclip.p; size = (size_t)V * 16; } break;
     case 9: if (light_ok) { src = ctx->light[index].gft.p; size = R2; } break;
     case 10: if (cam_ok) { src = ctx->view[L + index].gcolor.p; size = cam_px(index) * 16; } break;
+    case 11:
+    case 12: {
+      // shading-stage probe: camera index (11), or camera index / 64 and
+      // light view index % 64 (12)
+      const int c = what == 11 ? index : (index >= 0 ? index / 64 : -1);
+      const int l = what == 11 ? -1 : (index >= 0 ? index % 64 : -1);
+      if (c < 0 || c >= ctx->C || (what == 12 && l >= L)) break;
+      if (bytes != cam_px(c) * 32) return fail(ctx, DSM_ERR_INVALID_ARG, "debug buffer size mismatch");
+      launch_shade_probe(shade_args(ctx, c), l, static_cast<float4*>(dst), ctx->stream);
+      DSM_CHECK(cudaGetLastError());
+      DSM_CHECK(cudaStreamSynchronize(ctx->stream));
+      return DSM_OK;
+    }
     default: break;
   }
   if (!src || size == 0) return fail(ctx, DSM_ERR_INVALID_ARG, "unknown or empty debug buffer");
@@ -1325,7 +1364,7 @@ dsm_status dsm_raster_stats(dsm_ctx* ctx, int32_t view, int64_t* out) {
 uint64_t dsm_memory_bytes(dsm_ctx* ctx) {
   if (!ctx) return 0;
   uint64_t n = 0;
-  const Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->status,
+  const Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->viewMlo, &ctx->status,
                        &ctx->vnormal, &ctx->vnlen, &ctx->gnormal, &ctx->gN, &ctx->gface, &ctx->gQ, &ctx->gdirect,
                        &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo, &ctx->filter_tmp,
                        &ctx->red, &ctx->stats};

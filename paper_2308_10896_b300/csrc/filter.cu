@@ -1,5 +1,6 @@
 // Separable moment filter m = G g (Eqs. moment1/moment2) and its adjoint
 // G^T (Sec. 4: dm/dTheta = G grad f~).  G filters along x, then along y.
+#include <algorithm>
 #include <cmath>
 #include "dsm.h"
 #include "common.cuh"
@@ -7,9 +8,18 @@
 
 namespace dsm {
 
+bool filter_args_ok(float sigma, int radius, int kind, int boundary) {
+  if ((kind != 0 && kind != 1) || (boundary != 0 && boundary != 1) || radius > 32) return false;
+  const bool sigma_ok = std::isfinite(sigma) && sigma > 0.f;
+  // the Gaussian's weights divide by sigma^2; without a radius, r = ceil(2 sigma)
+  if (kind == 0 && !sigma_ok) return false;
+  if (radius <= 0 && !sigma_ok) return false;
+  return true;
+}
+
 void make_filter_args(double sigma, int radius, int kind, int boundary, FilterArgs* fa) {
-  int r = radius > 0 ? radius : (int)std::ceil(2.0 * sigma);
-  if (r > 32) r = 32;
+  // the clamp to 32 taps happens in double, before the conversion to int
+  const int r = radius > 0 ? std::min(radius, 32) : (int)std::min(std::ceil(2.0 * sigma), 32.0);
   fa->r = r;
   fa->boundary = boundary;
   fa->shape = 0;

@@ -73,6 +73,7 @@ struct ShadeArgs {
   int n_mat;
   const float* vnormal;    // V x 3, unit vertex normals
   const float4* cam_clip;  // V, camera clip coordinates
+  const float4* cam_clip_lo;   // V, their rounding residual
   const LightDev* lights;
   int L;
   const float2* mom[kMaxLightViews];
@@ -88,7 +89,7 @@ struct ShadeGradArgs {
   float4* gclip;                      // V, dL/d camera clip
   float* dalbedo;                     // M x 3
   float2* gm[kMaxLightViews];         // dL/d(m1, m2) texel maps
-  float* red;                         // kRedSlots x red_stride: [dQ (L x 20) | direct (L x 3) | albedo (M x 3)]
+  double* red;                        // kRedSlots x red_stride: [dQ (L x 20) | direct (L x 3) | albedo (M x 3)]
   int red_stride;
   const int* big;                     // camera view big-triangle index per triangle
   float* big_acc;                     // kMaxBig x kBigSlots x kBigStrideCam
@@ -122,6 +123,7 @@ struct AAArgs {
   const uint8_t* sil;
   const VertSnap* snap;
   const float4* clip;
+  const float4* clip_lo;   // rounding residual of clip
 };
 
 // Per-view pointers and sizes for the fused setup of all views of a frame.
@@ -129,6 +131,7 @@ struct ViewSetupArgs {
   int n;
   int W[kMaxViews], H[kMaxViews], tiles[kMaxViews];
   float4* clip[kMaxViews];
+  float4* clip_lo[kMaxViews];     // rounding residual of clip (see transform_all_kernel)
   VertSnap* snap[kMaxViews];
   float* depth[kMaxViews];        // light views only (camera: NULL)
   TriSetup* setup[kMaxViews];
@@ -142,9 +145,11 @@ struct ViewSetupArgs {
 // binning that follows.  The silhouettes (needed only by the antialiasing) may
 // instead follow later through launch_silhouettes_all.
 void launch_setup_all(const float* verts, int V, const int* tris, int T, const int* adj, const float* viewM,
+                      const float* viewMlo,
                       const ViewSetupArgs& a, DevStatus* status, bool silhouettes, cudaStream_t st);
 void launch_silhouettes_all(const int* adj, int T, const ViewSetupArgs& a, cudaStream_t st);
-void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, cudaStream_t st);
+void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, float* viewMlo,
+                        cudaStream_t st);
 void launch_bin_count(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, DevStatus* status,
                       int view, int* big_index, int* big_tri, cudaStream_t st);
 // Raster work units of one view.  A tile's list is rastered kRasterBatch
@@ -175,8 +180,9 @@ void launch_raster_stats(const TriSetup* setup, const int* offset, const int* li
 // Light views (fmap != NULL) also write the shadow-map depth sample (f, f^2)
 // of every texel, f interpolated from the per-vertex light depths.
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
-                   int tile_log2, int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth,
-                   float2* fmap, float ec, const RasterUnits& ru, DevStatus* status, int view, cudaStream_t st);
+                   int tile_log2, int W, int H, const float4* clip, const float4* clip_lo, const int* tris,
+                   float4* gbuf, const float* depth, float2* fmap, float ec, const RasterUnits& ru,
+                   DevStatus* status, int view, cudaStream_t st);
 // After the fill pass (filled: its per-tile counts of ordinary triangles):
 // appends each tile's big triangles to its segment and hands out the raster
 // work units and key slots.
@@ -198,6 +204,10 @@ void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* dep
                               const BigArgs& big, cudaStream_t st);
 
 // separable filter
+// Whether (sigma, radius, kind, boundary) describe a filter: kind and boundary
+// 0 or 1, radius <= 32, and a finite sigma > 0 for the Gaussian (kind 0) and
+// whenever the radius is derived from sigma (radius <= 0).
+bool filter_args_ok(float sigma, int radius, int kind, int boundary);
 void make_filter_args(double sigma, int radius, int kind, int boundary, FilterArgs* fa);
 // m = G g; with hflag (shadow-map path) g is (f, f^2) except at flagged texels,
 // where the antialiasing pass left (f~, (f^2)~) in patch.
@@ -229,15 +239,17 @@ void launch_normals_backward(const float* verts, int V, const int* tris, int T, 
                              const int* vf_list, const float* vnormal, const float* vlen, const float* gnormal,
                              float* gN, float* gface, float* dverts, cudaStream_t st);
 void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st);
+void launch_shade_probe(const ShadeArgs& a, int l, float4* out, cudaStream_t st);
+void launch_sm_band_mask(const uint8_t* hflag, int n, float2* gft, float* gf, cudaStream_t st);
 void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);
 void launch_shade_scatter(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);
 void launch_vertex_backward(const float* verts, int V, const float* viewM, int n_views, int n_lights,
-                            const VertGradPtrs& gp, float* dverts, float* red, int red_stride, cudaStream_t st);
+                            const VertGradPtrs& gp, float* dverts, double* red, int red_stride, cudaStream_t st);
 void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const int* big_tri,
                               const DevStatus* status, int view, cudaStream_t st);
-void launch_red_reduce(const float* red, int red_stride, int L, int n_mat_red, float* gQ, float* gdirect,
+void launch_red_reduce(const double* red, int red_stride, int L, int n_mat_red, double* gQ, double* gdirect,
                        float* dalbedo, cudaStream_t st);
-void launch_light_grad(const LightDev* lights, int L, int n_user, const float* gQ, const float* gdirect,
+void launch_light_grad(const LightDev* lights, int L, int n_user, const double* gQ, const double* gdirect,
                        float* dlight, cudaStream_t st);
 void launch_l2(const float* img, const float* tgt, int64_t n, float* loss, float* grad, cudaStream_t st);
 

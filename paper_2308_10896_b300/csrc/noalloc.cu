@@ -1,12 +1,14 @@
 // Allocation-free variant of the moment filter (dsm_filter_moments_noalloc).
 //
-// Some callers must not allocate device memory while they run: a real-time
-// render loop with a fixed memory budget, code that runs between a stream
-// capture's begin and end (where cudaMalloc would break the capture), or a host
-// application that owns the device memory pool and forbids other allocators.
-// This entry point serves them: the caller passes the input and output maps,
-// and the intermediate row-filtered map lives in a static device array that is
-// part of the loaded library, so no call ever reaches cudaMalloc / cudaFree.
+// Some callers cannot allocate device memory while they run: a real-time render
+// loop that works inside a fixed, preallocated memory budget, or a host
+// application that owns the device memory pool and lets no other allocator
+// touch the device.  dsm_filter_moments may grow its context's scratch with
+// cudaMalloc; this entry point never allocates.  The caller passes the input
+// and output maps.  Radii up to 15 run as one tiled kernel that needs no
+// intermediate map.  Radii 16 to 32 run as two 1-D passes whose intermediate,
+// row-filtered map lives in a static device array that is part of the loaded
+// library, so no call ever reaches cudaMalloc or cudaFree.
 #include <cmath>
 #include <mutex>
 #include "dsm.h"
@@ -27,7 +29,10 @@ std::mutex g_mu;
 float2* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the static array on the current device (host code only
-// sees a host-side stand-in for the symbol).  Looked up once per device.
+// sees a host-side stand-in for the symbol).  Looked up once per device, on
+// that device's first call, and cached: after cudaDeviceReset (or any other
+// teardown of the device's primary context) the cached address is stale, so
+// the library must not be used on that device again in this process.
 cudaError_t scratch_for_current_device(float2** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -50,14 +55,15 @@ cudaError_t scratch_for_current_device(float2** out) {
 extern "C" dsm_status dsm_filter_moments_noalloc(const float* in, float* out, int32_t res, float sigma,
                                                  int32_t radius, int32_t kind, int32_t boundary, void* stream) {
   using namespace dsm;
-  if (!in || !out || res < 1 || (kind != 0 && kind != 1) || (boundary != 0 && boundary != 1) || radius > 32 ||
-      (!(sigma > 0.f) && radius <= 0))
-    return DSM_ERR_INVALID_ARG;
+  if (!in || !out || res < 1 || !filter_args_ok(sigma, radius, kind, boundary)) return DSM_ERR_INVALID_ARG;
   if ((long long)res * res > kNoAllocMaxTexels) return DSM_ERR_CAPACITY;   // beyond the static array
   float2* tmp = nullptr;
   if (scratch_for_current_device(&tmp) != cudaSuccess) return DSM_ERR_CUDA;
-  // The x pass overwrites every texel of the intermediate before the y pass
-  // reads it, so nothing in the shared array has to be cleared between calls.
+  // Radii up to 15 take the tiled kernel and never touch `tmp`.  For larger
+  // radii the x pass overwrites every texel of the intermediate before the y
+  // pass reads it, so nothing in the shared array has to be cleared between
+  // calls.  No status word is passed, so the TMA-staged kernel (which reports
+  // timeouts through one) is not used here.
   FilterArgs fa;
   make_filter_args(sigma, radius, kind, boundary, &fa);
   launch_filter(reinterpret_cast<const float2*>(in), tmp, reinterpret_cast<float2*>(out), res, fa,

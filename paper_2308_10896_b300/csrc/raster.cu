@@ -123,7 +123,7 @@ __device__ __forceinline__ float face_axis(int face, int k) {
 // and the face axis as its direction (a constant: its J has no direction
 // columns).
 __global__ void light_setup_kernel(const float* __restrict__ params, LightSetupArgs a, LightDev* out,
-                                   float* viewM) {
+                                   float* viewM, float* viewMlo) {
   const int l = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (l >= a.n) return;
   const LightConst& L = a.c[l];
@@ -135,9 +135,13 @@ __global__ void light_setup_kernel(const float* __restrict__ params, LightSetupA
     for (int k = 0; k < 6; ++k) th[k] = {(double)(k >= 3 && L.face >= 0 ? face_axis(L.face, k - 3) : pl[k])};
     const R64 zero{0.0}, one{1.0};
     const Frame<R64> F = light_frame(th, L, zero, one);
-    const float q = __double2float_rn(q_entry(lane, F, L, zero, one).v);
+    const double q64 = q_entry(lane, F, L, zero, one).v;
+    const float q = __double2float_rn(q64);
     o.Q[lane] = q;
     viewM[l * 20 + lane] = q;
+    // the clip rows' rounding residual: the unsnapped clip coordinates that
+    // interpolation and antialiasing use are those of the float64 matrix
+    if (lane < 16) viewMlo[l * 16 + lane] = __double2float_rn(q64 - (double)q);
     if (lane == 0) {
       o.fwd[0] = (float)F.f.x.v; o.fwd[1] = (float)F.f.y.v; o.fwd[2] = (float)F.f.z.v;
       const double dx = th[3].v, dy = th[4].v, dz = th[5].v;
@@ -246,8 +250,32 @@ __device__ __forceinline__ uint8_t silhouette_mask(const int8_t* __restrict__ or
 // The per-view setup kernels above, fused over the views of one frame: each
 // vertex / triangle is read once and processed for every view (the view loop
 // is unrolled so that the per-view pointers stay in parameter space).
+// Rounding residual of a pinned row: the exact value of
+// ((Mh + Ml) . [x, y, z, 1]) minus `pinned`, with Mh the float32 matrix row and
+// Ml its own residual against the float64 row it was rounded from (zero for a
+// camera, whose float32 matrix is the definition).  The Mh products and their
+// sum are carried exactly as float-float (two_prod, two_sum); Ml's small
+// terms in plain float32.
+__device__ __forceinline__ float row_residual(const float* Mh, const float* Ml, float x, float y, float z,
+                                              float pinned) {
+  float p0, e0, p1, e1, p2, e2, s, t;
+  two_prod(Mh[0], x, p0, e0);
+  two_prod(Mh[1], y, p1, e1);
+  two_prod(Mh[2], z, p2, e2);
+  two_sum(p0, p1, s, t);
+  float err = __fadd_rn(__fadd_rn(e0, e1), t);
+  two_sum(s, p2, s, t);
+  err = __fadd_rn(err, __fadd_rn(e2, t));
+  two_sum(s, Mh[3], s, t);
+  err = __fadd_rn(err, t);
+  err = __fadd_rn(err, __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(Ml[0], x), __fmul_rn(Ml[1], y)),
+                                           __fmul_rn(Ml[2], z)), Ml[3]));
+  // s and `pinned` approximate the same value to a few ulps: their difference is exact
+  return __fadd_rn(__fsub_rn(s, pinned), err);
+}
+
 __global__ void transform_all_kernel(const float* __restrict__ verts, int V, const float* __restrict__ viewM,
-                                     ViewSetupArgs a) {
+                                     const float* __restrict__ viewMlo, ViewSetupArgs a) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
   const float x = verts[3 * v], y = verts[3 * v + 1], z = verts[3 * v + 2];
@@ -255,11 +283,16 @@ __global__ void transform_all_kernel(const float* __restrict__ verts, int V, con
   for (int w = 0; w < kMaxViews; ++w) {
     if (w >= a.n) break;
     const float* M20 = viewM + 20 * w;
+    const float* L16 = viewMlo + 16 * w;
     const float c0 = pinned_row(M20 + 0, x, y, z);
     const float c1 = pinned_row(M20 + 4, x, y, z);
     const float c2 = pinned_row(M20 + 8, x, y, z);
     const float c3 = pinned_row(M20 + 12, x, y, z);
     a.clip[w][v] = make_float4(c0, c1, c2, c3);
+    a.clip_lo[w][v] = make_float4(row_residual(M20 + 0, L16 + 0, x, y, z, c0),
+                                  row_residual(M20 + 4, L16 + 4, x, y, z, c1),
+                                  row_residual(M20 + 8, L16 + 8, x, y, z, c2),
+                                  row_residual(M20 + 12, L16 + 12, x, y, z, c3));
     if (a.depth[w]) a.depth[w][v] = pinned_row(M20 + 16, x, y, z);
     a.snap[w][v] = snap_vertex(c0, c1, c2, c3, a.W[w], a.H[w]);
   }
@@ -617,6 +650,7 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
                                                      const int* __restrict__ offset,
                                                      const int* __restrict__ list, int capacity, int tilesX,
                                                      int n_tiles, int W, int H, const float4* __restrict__ clip,
+                                                     const float4* __restrict__ clip_lo,
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf,
                                                      const float* __restrict__ depth, float2* __restrict__ fmap,
                                                      float ec, RasterUnits ru, const DevStatus* __restrict__ status,
@@ -766,8 +800,9 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
     if (best != ~0ull) {
       const int t = (int)(best & 0xffffffffu);
       const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
-      const float4 c0 = clip[v0], c1 = clip[v1], c2 = clip[v2];
-      const Bary r = bary_at(c0, c1, c2, pix_ndc_x(i, W), pix_ndc_y(j, H));
+      const float4 ch[3] = {clip[v0], clip[v1], clip[v2]};
+      const float4 cl[3] = {clip_lo[v0], clip_lo[v1], clip_lo[v2]};
+      const Bary r = bary_at(ch, cl, i, j, W, H);
       out = make_float4(__int_as_float(t + 1), r.b[0], r.b[1], key_depth(best));
       if (fmap) {
         // f = sum_k b_k d_k with b_2 = 1 - b_0 - b_1 of the stored barycentrics
@@ -817,17 +852,18 @@ __global__ void raster_stats_kernel(const TriSetup* __restrict__ setup, const in
 }
 
 // ------------------------------------------------------------------ launchers
-void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM,
+void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, float* viewMlo,
                         cudaStream_t st) {
   count_launches(1);
-  light_setup_kernel<<<a.n, 64, 0, st>>>(params, a, out, viewM);
+  light_setup_kernel<<<a.n, 64, 0, st>>>(params, a, out, viewM, viewMlo);
 }
 
 void launch_setup_all(const float* verts, int V, const int* tris, int T, const int* adj, const float* viewM,
+                      const float* viewMlo,
                       const ViewSetupArgs& a, DevStatus* status, bool silhouettes, cudaStream_t st) {
   if (V > 0) {
     count_launches(1);
-    transform_all_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, viewM, a);
+    transform_all_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, viewM, viewMlo, a);
   }
   count_launches(1);
   tri_setup_all_kernel<<<std::max((T + 255) / 256, 64), 256, 0, st>>>(tris, T, a, status);
@@ -873,16 +909,17 @@ void launch_units(const TriSetup* setup, const int* offset, int* list, int capac
 }
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
-                   int tile_log2, int W, int H, const float4* clip, const int* tris, float4* gbuf, const float* depth,
-                   float2* fmap, float ec, const RasterUnits& ru, DevStatus* status, int view, cudaStream_t st) {
+                   int tile_log2, int W, int H, const float4* clip, const float4* clip_lo, const int* tris,
+                   float4* gbuf, const float* depth, float2* fmap, float ec, const RasterUnits& ru,
+                   DevStatus* status, int view, cudaStream_t st) {
   const int n = tilesX * tilesY;
   count_launches(1);
   if (tile_log2 == 4)
-    raster_kernel<4><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, tris, gbuf,
-                                                  depth, fmap, ec, ru, status, view);
+    raster_kernel<4><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, clip_lo,
+                                                  tris, gbuf, depth, fmap, ec, ru, status, view);
   else
-    raster_kernel<5><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, tris, gbuf,
-                                                  depth, fmap, ec, ru, status, view);
+    raster_kernel<5><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, clip_lo,
+                                                  tris, gbuf, depth, fmap, ec, ru, status, view);
 }
 
 void launch_raster_stats(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX,

@@ -128,7 +128,7 @@ struct TriCache {
   int tri = -1;
   int v[3];
   float3 p[3], n[3];
-  float4 cc[3];
+  float4 cc[3], cl[3];   // camera clip coordinates: pinned float32 and rounding residual
   int mat;
   float3 alb;
 };
@@ -141,6 +141,7 @@ __device__ __forceinline__ void tri_load(const ShadeArgs& a, int t, TriCache& c)
     c.p[k] = make_float3(a.verts[3 * v], a.verts[3 * v + 1], a.verts[3 * v + 2]);
     c.n[k] = make_float3(a.vnormal[3 * v], a.vnormal[3 * v + 1], a.vnormal[3 * v + 2]);
     c.cc[k] = a.cam_clip[v];
+    c.cl[k] = a.cam_clip_lo[v];
   }
   c.mat = material_of(a, t);
   c.alb = make_float3(a.albedo[3 * c.mat], a.albedo[3 * c.mat + 1], a.albedo[3 * c.mat + 2]);
@@ -172,6 +173,8 @@ struct Look {
   float d;
   float dw;              // receiver depth in the moments' encoding
   int inside;
+  float u, v;            // light-space position (clip x, y over w)
+  float s, t;            // texel coordinates of the bilinear lookup
   int i0, j0;            // floor of the texel coordinates
   float fs, ft;
   float2 m;
@@ -192,9 +195,13 @@ __device__ __forceinline__ Look lookup(const float* Q, const float2* __restrict_
   L.inside = 0;
   if (!(L.clip.w > 0.f)) return L;
   const float u = L.clip.x / L.clip.w, v = L.clip.y / L.clip.w;
+  L.u = u;
+  L.v = v;
   if (!(fabsf(u) <= 1.f && fabsf(v) <= 1.f)) return L;
   L.inside = 1;
   const float s = (0.5f * u + 0.5f) * R - 0.5f, t = (0.5f - 0.5f * v) * R - 0.5f;
+  L.s = s;
+  L.t = t;
   const float fi = floorf(s), fj = floorf(t);
   L.i0 = (int)fi; L.j0 = (int)fj;
   L.fs = s - fi; L.ft = t - fj;
@@ -260,6 +267,45 @@ __global__ void shade_kernel(ShadeArgs a, float4* __restrict__ color) {
   }
   const int mat = material_of(a, s.tri);
   color[p] = make_float4(a.albedo[3 * mat] * rad.x, a.albedo[3 * mat + 1] * rad.y, a.albedo[3 * mat + 2] * rad.z, 1.f);
+}
+
+// Diagnostic copy of the shading stage's intermediate values at every pixel of
+// a camera, computed by the same device functions as shade_kernel (so a
+// comparison can feed a reference the values this kernel used, stage by
+// stage).  l < 0: out[2p] = (x, 0), out[2p + 1] = (n, 0), the interpolated
+// world position and unit normal.  l >= 0 (light view l): out[2p] =
+// (u, v, s, t), out[2p + 1] = (dw, m1, m2, vis): light-space position, texel
+// coordinates, receiver depth in the moments' encoding, bilinear moments and
+// visibility.  Values the pixel does not have are NaN: every value of a
+// background pixel or of a view that does not shade the point (another cube
+// face), (u, v) when the point is behind the light, and (s, t, m1, m2)
+// outside the light's window.
+__global__ void shade_probe_kernel(ShadeArgs a, int l, float4* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= a.W || j >= a.H) return;
+  const size_t p = (size_t)j * a.W + i;
+  const float nan = __int_as_float(0x7fc00000);
+  float4 o0 = make_float4(nan, nan, nan, nan), o1 = o0;
+  Surf s;
+  if (load_surf(a, p, s)) {
+    if (l < 0) {
+      o0 = make_float4(s.x.x, s.x.y, s.x.z, 0.f);
+      o1 = make_float4(s.n.x, s.n.y, s.n.z, 0.f);
+    } else if (view_shades(a.lights[l], s.x)) {
+      const Look L = lookup(a.lights[l].Q, a.mom[l], a.res[l], s.x, a.min_variance, a.ec);
+      const bool front = L.clip.w > 0.f;
+      o0 = make_float4(front ? L.u : nan, front ? L.v : nan, L.inside ? L.s : nan, L.inside ? L.t : nan);
+      o1 = make_float4(L.dw, L.inside ? L.m.x : nan, L.inside ? L.m.y : nan, L.vis);
+    }
+  }
+  out[2 * p] = o0;
+  out[2 * p + 1] = o1;
+}
+
+void launch_shade_probe(const ShadeArgs& a, int l, float4* out, cudaStream_t st) {
+  dim3 b(32, 8), g((a.W + 31) / 32, (a.H + 7) / 8);
+  count_launches(1);
+  shade_probe_kernel<<<g, b, 0, st>>>(a, l, out);
 }
 
 constexpr int kShadeStrip = 8;
@@ -470,14 +516,16 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
     g.pgrad[2 * p + 1] = make_float4(gnt.y, gnt.z, act ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
-  float* red = g.red + (size_t)block_slot(kRedSlots) * g.red_stride;
+  // block sums into float64 slot copies: the light gradients sum millions of
+  // terms of both signs, whose cancellation float32 accumulation would not keep
+  double* red = g.red + (size_t)block_slot(kRedSlots) * g.red_stride;
   for (int k = tid; k < a.L * 20; k += 256)
-    if (sQ[k] != 0.f) atomicAdd(&red[k], sQ[k]);
+    if (sQ[k] != 0.f) atomicAdd(&red[k], (double)sQ[k]);
   for (int k = tid; k < a.L * 3; k += 256)
-    if (sD[k] != 0.f) atomicAdd(&red[a.L * 20 + k], sD[k]);
+    if (sD[k] != 0.f) atomicAdd(&red[a.L * 20 + k], (double)sD[k]);
   if (mat_shared)
     for (int k = tid; k < a.n_mat * 3; k += 256)
-      if (sA[k] != 0.f) atomicAdd(&red[a.L * 23 + k], sA[k]);
+      if (sA[k] != 0.f) atomicAdd(&red[a.L * 23 + k], (double)sA[k]);
 }
 
 // Per-triangle scatter of the camera interpolation adjoint: from the per-pixel
@@ -544,7 +592,7 @@ __global__ void __launch_bounds__(256) shade_scatter_kernel(ShadeArgs a, ShadeGr
                   tc.n[k].x * gnt.x + tc.n[k].y * gnt.y + tc.n[k].z * gnt.z;
         }
         const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
-        const Bary r = bary_at(tc.cc[0], tc.cc[1], tc.cc[2], px, py);
+        const Bary r = bary_at(tc.cc, tc.cl, i, j, a.W, a.H);
         float4 gcv[3];
         bary_backward(r, gb, px, py, gcv);
         for (int k = 0; k < 3; ++k) {
@@ -584,17 +632,18 @@ __global__ void shade_big_resolve_kernel(ShadeArgs a, ShadeGradArgs g, const int
   }
 }
 
-// Sum of the kRedSlots copies: dQ and the direct light terms (overwritten) and
-// the albedo gradient (added).
-__global__ void red_reduce_kernel(const float* __restrict__ red, int stride, int L, int n_mat_red,
-                                  float* __restrict__ gQ, float* __restrict__ gdirect, float* __restrict__ dalbedo) {
+// Sum of the kRedSlots copies (float64): dQ and the direct light terms
+// (overwritten) and the albedo gradient (added).
+__global__ void red_reduce_kernel(const double* __restrict__ red, int stride, int L, int n_mat_red,
+                                  double* __restrict__ gQ, double* __restrict__ gdirect,
+                                  float* __restrict__ dalbedo) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= L * 23 + n_mat_red * 3) return;
-  float acc = 0.f;
+  double acc = 0.0;
   for (int q = 0; q < kRedSlots; ++q) acc += red[(size_t)q * stride + k];
   if (k < L * 20) gQ[k] = acc;
   else if (k < L * 23) gdirect[k - L * 20] = acc;
-  else dalbedo[k - L * 23] += acc;
+  else dalbedo[k - L * 23] += (float)acc;
 }
 
 // ------------------------------------------------------------------ per-vertex gathers
@@ -603,7 +652,7 @@ __global__ void red_reduce_kernel(const float* __restrict__ red, int stride, int
 __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __restrict__ verts, int V,
                                                               const float* __restrict__ viewM, int n_views,
                                                               int n_lights, VertGradPtrs gp,
-                                                              float* __restrict__ dverts, float* __restrict__ red,
+                                                              float* __restrict__ dverts, double* __restrict__ red,
                                                               int red_stride) {
   __shared__ float sQ[kMaxLightViews * 20];
   for (int k = threadIdx.x; k < kMaxLightViews * 20; k += blockDim.x) sQ[k] = 0.f;
@@ -639,9 +688,9 @@ __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __res
     dverts[3 * v] += acc.x; dverts[3 * v + 1] += acc.y; dverts[3 * v + 2] += acc.z;
   }
   __syncthreads();
-  float* dst = red + (size_t)block_slot(kRedSlots) * red_stride;
+  double* dst = red + (size_t)block_slot(kRedSlots) * red_stride;
   for (int k = threadIdx.x; k < n_lights * 20; k += blockDim.x)
-    if (sQ[k] != 0.f) atomicAdd(&dst[k], sQ[k]);
+    if (sQ[k] != 0.f) atomicAdd(&dst[k], (double)sQ[k]);
 }
 
 // dL/d(pos, dir) of the caller's light u = sum over its views of J^T dL/dQ
@@ -649,27 +698,27 @@ __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __res
 // omega = -dir / |dir|, spot and point omega = normalize(pos - x).  A point
 // light sums its six cube faces (their J has no direction columns).
 __global__ void light_grad_kernel(const LightDev* __restrict__ lights, int L, int n_user,
-                                  const float* __restrict__ gQ, const float* __restrict__ gdirect,
+                                  const double* __restrict__ gQ, const double* __restrict__ gdirect,
                                   float* __restrict__ dlight) {
   const int u = blockIdx.x;
   const int j = threadIdx.x;
   if (u >= n_user || j >= 6) return;
-  float acc = 0.f;
+  double acc = 0.0;   // a few float64 operations per light: keeps the cancellation of J^T dL/dQ
   for (int l = 0; l < L; ++l) {
     const LightDev& Ld = lights[l];
     if (Ld.user != u) continue;
-    for (int k = 0; k < 20; ++k) acc += gQ[l * 20 + k] * Ld.J[k * 6 + j];
-    const float* gd = gdirect + 3 * l;
+    for (int k = 0; k < 20; ++k) acc += gQ[l * 20 + k] * (double)Ld.J[k * 6 + j];
+    const double* gd = gdirect + 3 * l;
     if (Ld.type == 1) {
       if (j < 3) acc += gd[j];
     } else if (j >= 3) {
       const int c = j - 3;
       const float* f = Ld.fwd;
-      const float fg = f[0] * gd[0] + f[1] * gd[1] + f[2] * gd[2];
+      const double fg = f[0] * gd[0] + f[1] * gd[1] + f[2] * gd[2];
       acc += -(gd[c] - f[c] * fg) / Ld.dir_norm;
     }
   }
-  dlight[u * 6 + j] = acc;
+  dlight[u * 6 + j] = (float)acc;
 }
 
 __global__ void l2_kernel(const float* __restrict__ img, const float* __restrict__ tgt, int64_t n,
@@ -735,7 +784,7 @@ void launch_shade_scatter(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream
 }
 
 void launch_vertex_backward(const float* verts, int V, const float* viewM, int n_views, int n_lights,
-                            const VertGradPtrs& gp, float* dverts, float* red, int red_stride, cudaStream_t st) {
+                            const VertGradPtrs& gp, float* dverts, double* red, int red_stride, cudaStream_t st) {
   if (V == 0) return;
   count_launches(1);
   vertex_backward_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, viewM, n_views, n_lights, gp, dverts, red,
@@ -748,7 +797,7 @@ void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const 
   shade_big_resolve_kernel<<<kMaxBig, 32, 0, st>>>(a, g, big_tri, status, view);
 }
 
-void launch_red_reduce(const float* red, int red_stride, int L, int n_mat_red, float* gQ, float* gdirect,
+void launch_red_reduce(const double* red, int red_stride, int L, int n_mat_red, double* gQ, double* gdirect,
                        float* dalbedo, cudaStream_t st) {
   const int n = L * 23 + n_mat_red * 3;
   if (n == 0) return;
@@ -756,7 +805,7 @@ void launch_red_reduce(const float* red, int red_stride, int L, int n_mat_red, f
   red_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(red, red_stride, L, n_mat_red, gQ, gdirect, dalbedo);
 }
 
-void launch_light_grad(const LightDev* lights, int L, int n_user, const float* gQ, const float* gdirect,
+void launch_light_grad(const LightDev* lights, int L, int n_user, const double* gQ, const double* gdirect,
                        float* dlight, cudaStream_t st) {
   if (n_user == 0) return;
   count_launches(1);

@@ -22,7 +22,9 @@ MAX_LIGHTS = 8
 MAX_CAMERAS = 8
 
 # debug_copy buffer codes (see include/dsm.h)
-DBG_GBUF, DBG_F, DBG_FTILDE, DBG_MOMENTS, DBG_COLOR, DBG_Q, DBG_SNAP, DBG_GM, DBG_GCLIP, DBG_GFT, DBG_GCOLOR = range(11)
+DBG_GBUF, DBG_F, DBG_FTILDE, DBG_MOMENTS, DBG_COLOR, DBG_Q, DBG_SNAP, DBG_GM, DBG_GCLIP, DBG_GFT, DBG_GCOLOR, \
+    DBG_SURF, DBG_LOOKUP = range(13)
+GRAD_MASK_SM_BAND = 1
 
 EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_render_backward",
             "dsm_l2_loss_grad", "dsm_filter_moments", "dsm_sync", "dsm_last_error", "dsm_debug_copy",
@@ -32,7 +34,7 @@ EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_
             "dsm_batch_kernels_per_step", "dsm_batch_last_error", "dsm_render_cameras",
             "dsm_render_cameras_backward", "dsm_memory_bytes", "dsm_adam_step", "dsm_set_tuning",
             "dsm_get_tuning", "dsm_autotune", "dsm_batch_autotune", "dsm_bounded_wait_probe",
-            "dsm_raster_stats"]
+            "dsm_raster_stats", "dsm_set_grad_mask"]
 
 
 class DsmError(RuntimeError):
@@ -132,6 +134,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                           ctypes.POINTER(ctypes.c_float)], I32),
         "dsm_batch_autotune": ([P, P, I32, P, I32], I32),
         "dsm_bounded_wait_probe": ([P, I32], I32),
+        "dsm_set_grad_mask": ([P, I32], I32),
         "dsm_adam_step": ([P, P, P, P, I64, I32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P],
                           I32),
     }
@@ -198,11 +201,22 @@ def params_struct(p: dict, stream=None) -> Params:
 class Context:
     """Owner of one dsm_ctx (scratch memory and the state of the last forward)."""
 
-    def __init__(self):
+    def __init__(self, handle=None):
         self.lib = load_library()
+        self.owned = handle is None
+        if handle is not None:
+            self.h = ctypes.c_void_p(handle) if not isinstance(handle, ctypes.c_void_p) else handle
+            return
         h = ctypes.c_void_p()
         self._check(self.lib.dsm_create(ctypes.byref(h)), None)
         self.h = h
+
+    @classmethod
+    def wrap(cls, handle) -> "Context":
+        """A non-owning view of a context created elsewhere (a batch's scene,
+        dsm_batch_context): its debug copies, backward and masks; closing it
+        leaves the context alone."""
+        return cls(handle)
 
     def _check(self, status: int, h=None):
         if status != DSM_OK:
@@ -211,7 +225,8 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.dsm_destroy(self.h)
+            if getattr(self, "owned", True):
+                self.lib.dsm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -287,6 +302,19 @@ class Context:
 
     def sync(self):
         self._check(self.lib.dsm_sync(self.h), self.h)
+
+    def set_grad_mask(self, flags: int):
+        """Diagnostic gradient masks (dsm_set_grad_mask): GRAD_MASK_SM_BAND
+        zeroes dL/df~ at the shadow maps' silhouette-band texels."""
+        self._check(self.lib.dsm_set_grad_mask(self.h, int(flags)), self.h)
+
+    def probe_surface(self, cam: int, W: int, H: int) -> torch.Tensor:
+        """(H, W, 2, 4): world position and unit normal the shading used."""
+        return self.debug(DBG_SURF, cam, (H, W, 2, 4))
+
+    def probe_lookup(self, cam: int, view: int, W: int, H: int) -> torch.Tensor:
+        """(H, W, 2, 4): (u, v, s, t) and (dw, m1, m2, vis) of light view `view`."""
+        return self.debug(DBG_LOOKUP, 64 * cam + view, (H, W, 2, 4))
 
     def bounded_wait_probe(self, arrive: bool):
         """One CTA waiting on an mbarrier (see dsm_bounded_wait_probe)."""
@@ -537,6 +565,11 @@ class Batch:
 
     def kernels_per_step(self) -> int:
         return int(self.lib.dsm_batch_kernels_per_step(self.h))
+
+    def context(self, i: int) -> Context:
+        """Scene i's context (non-owning): its debug copies and, after a step,
+        further backward passes of that step's forward."""
+        return Context.wrap(self.lib.dsm_batch_context(self.h, i))
 
     def set_host_io(self, i: int, verts=None, light_params=None, albedo=None, loss=None):
         """Pinned host tensors that scene i's recorded step uploads first

@@ -129,9 +129,10 @@ def test_camera_count_checked():
 
 
 def test_cameras_against_oracle():
-    """Three cameras, two lights, against the oracle's summed loss: images
-    end to end (the derived image bound) and gradients with the GPU's stage
-    values as teachers (the oracle's derivatives of every stage)."""
+    """Three cameras, two lights, against the oracle's summed loss: each
+    camera's colour stage-wise (1e-5 + 1e-4 |o|), images end to end (the
+    derived image bound) and gradients with the GPU's stage values as teachers
+    (the oracle's derivatives of every stage)."""
     from paper_2308_10896_b300 import dsm
     from oracle import dsm_oracle as O
     from parity_util import assert_close, grad_close
@@ -163,7 +164,15 @@ def test_cameras_against_oracle():
              for c, cam in enumerate(cams)]
     ref = O.render_cameras_and_grad(sc, cams, tg, teachers=teach)
     plain = O.render_cameras_and_grad(sc, cams, tg)
-    for c in range(len(cams)):
+    for c, cam in enumerate(cams):
+        # stage-wise: each camera's colour from the GPU's moment maps and shading-stage values
+        W, H = int(cam["width"]), int(cam["height"])
+        surf = r.ctx.probe_surface(c, W, H).cpu().numpy()
+        st_teach = {"moments": mom, "x": surf[:, :, 0, :3], "n": surf[:, :, 1, :3],
+                    "lookup": [r.ctx.probe_lookup(c, l, W, H).cpu().numpy().reshape(H, W, 8) for l in range(L)]}
+        out = O.render(dict(sc, camera=cam), teacher=st_teach)
+        assert_close(teach[c]["color"], out["color"].detach().numpy(), f"camera {c} colour")
+        # end to end: the derived image bound (float32 sigma^2 near its floor)
         assert_close(imgs[c].cpu().numpy(), plain["images"][c].numpy(), f"camera {c} image", atol=2e-3, rtol=1e-3)
     assert abs(loss - float(ref["loss"])) <= 1e-5 + 1e-4 * abs(float(ref["loss"]))
     grad_close(da.cpu().numpy(), ref["grad_albedo"].numpy(), "dL/dalbedo")

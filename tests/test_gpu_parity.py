@@ -3,15 +3,19 @@
 Discrete results (light matrices, snapped vertices, triangle ids, depth keys)
 must be bit-identical.  Floating-point stages are compared with the oracle fed
 the GPU's previous-stage float32 output (a stage-wise comparison): |g - o| <=
-1e-5 + 1e-4 |o|.  Gradients: 1e-3 relative (per element above 1e-3 of the
-largest, and relative L2)."""
+1e-5 + 1e-4 |o|.  Gradients: every element within 1e-3 relative outside the
+one-pixel silhouette bands (camera and shadow maps), relative L2 <= 1e-3 with
+the bands included; the band figures, the run-to-run spread of the float
+atomics and the untaught (end-to-end) comparison are reported separately
+(to the file named by DSM_PARITY_REPORT, when set)."""
 import numpy as np
 import pytest
 import torch
 
 import scenes
 from oracle import dsm_oracle as O
-from parity_util import ATOL, F64, GpuFrame, assert_close, grad_close, oracle_target
+from parity_util import (ATOL, F64, RTOL, GpuFrame, assert_close, camera_band, grad_close, grad_close_strict, grad_stats,
+                         oracle_shading_maps, oracle_target, report, stage_excess)
 
 pytestmark = pytest.mark.gpu
 
@@ -57,8 +61,13 @@ def _case(name):
         tgt = oracle_target(sc, 0.01, 7)
         gpu = GpuFrame(sc, tgt)
         ref = O.render(sc)
+        gpu.name = name
         _cache[name] = (sc, tgt, gpu, ref)
     return _cache[name]
+
+
+def case_name(case):
+    return case[2].name
 
 
 @pytest.fixture(scope="module", params=list(SCENES))
@@ -133,10 +142,36 @@ def test_moment_filter_stagewise(case):
 
 
 def test_shading_stagewise(case):
+    """Alg. 2 x Lambert stage by stage, each stage fed the GPU's float32
+    values of the stages before it: world position and normal; light-space
+    position (u, v), texel coordinates, receiver depth, bilinear moments,
+    Chebyshev visibility per light view; colour.  Every stage within
+    1e-5 + 1e-4 |o| (texel coordinates: a few float32 ulps of the map size)."""
     sc, _, gpu, ref = case
+    W, H = gpu.view_size(gpu.L)
     teach = {"moments": [gpu.light_map(gpu.dsm.DBG_MOMENTS, l) for l in range(gpu.L)]}
+    teach.update(gpu.shading_teacher())
     out = O.render(sc, teacher=teach)
+    ox, on, olook = oracle_shading_maps(out, H, W, gpu.L)
+    gx, gn = gpu.surface()
+    cov = np.isfinite(gx[..., 0])
+    assert np.array_equal(cov, np.isfinite(ox[..., 0])), "covered pixels differ"
+    worst = {}
+    for name, g, o in (("x", gx, ox), ("n", gn, on)):
+        e, _ = stage_excess(g, o)
+        worst[name] = e
+        assert e <= 0, f"{name}: excess {e:.3g}"
+    for v in range(gpu.L):
+        g, o = gpu.lookup(v), olook[v]
+        R = sc["lights"][gpu.view_light[v]]["res"]
+        for name, cols, atol, rtol in (("uv", slice(0, 2), ATOL, 1e-4), ("st", slice(2, 4), 8 * R * 2.0 ** -24, 0.0),
+                                       ("dw", slice(4, 5), ATOL, 1e-4), ("m", slice(5, 7), ATOL, 1e-4),
+                                       ("vis", slice(7, 8), ATOL, 1e-4)):
+            e, n = stage_excess(g[..., cols], o[..., cols], atol, rtol)
+            worst[f"{name}[{v}]"] = e
+            assert e <= 0, f"light view {v} {name}: excess {e:.3g} ({n} values)"
     assert_close(gpu.color(), out["color"].detach().numpy(), "colour before final AA")
+    report({"test": "shading_stagewise", "case": case_name(case), "worst_excess": worst})
 
 
 def test_final_antialias_stagewise(case):
@@ -153,21 +188,99 @@ def test_final_antialias_stagewise(case):
 
 
 def test_gradients_stagewise(case):
+    """Whole gradients, every forward stage taught, with the silhouette bands
+    included: relative L2 <= 1e-3 (per-element figures reported; the band's
+    per-element bar is below)."""
     sc, tgt, gpu, ref = case
-    teach = {"ftilde": [gpu.light_map(gpu.dsm.DBG_FTILDE, l) for l in range(gpu.L)],
-             "moments": [gpu.light_map(gpu.dsm.DBG_MOMENTS, l) for l in range(gpu.L)],
-             "color": gpu.color()}
-    res = O.render_and_grad(sc, tgt, teacher=teach)
+    res = O.render_and_grad(sc, tgt, teacher=gpu.full_teacher())
     assert abs(float(gpu.loss.item()) - float(res["loss"])) <= 1e-5 + 1e-4 * abs(float(res["loss"]))
-    grad_close(gpu.dalbedo.cpu().numpy(), res["grad_albedo"].numpy(), "dL/dalbedo")
-    grad_close(gpu.dlight.cpu().numpy(), res["grad_light"].numpy(), "dL/dlight")
-    grad_close(gpu.dverts.cpu().numpy(), res["grad_verts"].numpy(), "dL/dverts")
+    rec = {"test": "gradients_with_band", "case": case_name(case)}
+    for name, g, o in (("albedo", gpu.dalbedo, res["grad_albedo"]), ("light", gpu.dlight, res["grad_light"]),
+                       ("verts", gpu.dverts, res["grad_verts"])):
+        rec[name] = grad_stats(g.cpu().numpy(), o.numpy())
+        grad_close(g.cpu().numpy(), o.numpy(), f"dL/d{name}")
+    report(rec)
+
+
+def test_gradients_outside_silhouette_band(case):
+    """North-star gradient bar: every element within 1e-3 relative (elements
+    below 1e-3 of the largest within 1e-6 of it) and relative L2 <= 1e-3,
+    outside the one-pixel silhouette bands: dL/dimage is zeroed on the camera's
+    band, and dL/df~ on every shadow map's band (both sides, the same integer
+    rule), with every forward stage taught."""
+    sc, tgt, gpu, ref = case
+    band = camera_band(sc, ref)
+    gimg = gpu.gimg.clone()
+    gimg[torch.as_tensor(band, device=gimg.device)] = 0.0
+    dv, dl, da = gpu.backward_with(gimg, sm_band=True)
+    res = O.render_and_grad(sc, tgt, teacher=gpu.full_teacher(), grad_image=gimg.cpu().numpy(),
+                            grad_mask_sm_band=True)
+    rec = {"test": "gradients_outside_band", "case": case_name(case), "camera_band_pixels": int(band.sum())}
+    for name, g, o in (("albedo", da, res["grad_albedo"]), ("light", dl, res["grad_light"]),
+                       ("verts", dv, res["grad_verts"])):
+        rec[name] = grad_close_strict(g, o.numpy(), f"dL/d{name} outside the band")
+    report(rec)
+
+
+def test_atomic_order_spread(case):
+    """The float atomics of the backward sum in an order that varies between
+    runs: the run-to-run spread of three backward passes of the same forward,
+    reported (and bounded far below the parity bar)."""
+    sc, tgt, gpu, ref = case
+    runs = [gpu.backward_with(gpu.gimg, sm_band=False) for _ in range(3)]
+    rec = {"test": "atomic_order_spread", "case": case_name(case)}
+    for k, name in enumerate(("verts", "light", "albedo")):
+        base = runs[0][k]
+        scale = max(float(np.abs(base).max()), 1e-30)
+        spread = max(float(np.abs(r[k] - base).max()) for r in runs[1:]) / scale
+        rec[name] = spread
+        assert spread <= 1e-4, f"dL/d{name}: run-to-run spread {spread:.3g} of the largest element"
+    report(rec)
+
+
+def test_end_to_end_gradients(case):
+    """Gradients with no stage taught (each side its own forward, its own
+    loss gradient), reported beside the stage-wise figures.  Where sigma^2
+    sits near its floor the float32 forward differs from the float64 one by up
+    to ~1e-3 (see test_end_to_end_image), so dL/dimage = 2 (image - target) / N
+    differs there and so do the gradients.  Bound: relative L2 within the
+    share the oracle's own backward gives to that image difference,
+    ||J^T 2 (image_gpu - image_oracle) / N||, plus the stage-wise bar 1e-3 and
+    its double for the change of linearisation point."""
+    sc, tgt, gpu, ref = case
+    res = O.render_and_grad(sc, tgt)
+    img_g = gpu.image.cpu().numpy().astype(np.float64)
+    img_o = res["image"].detach().numpy()
+    N = img_o.size
+    diff = O.render_and_grad(sc, None, grad_image=2.0 * (img_g - img_o) / N)
+    rec = {"test": "end_to_end_gradients", "case": case_name(case),
+           "image_max_abs_diff": float(np.abs(img_g - img_o).max())}
+    for name, g, o, d in (("albedo", gpu.dalbedo, res["grad_albedo"], diff["grad_albedo"]),
+                          ("light", gpu.dlight, res["grad_light"], diff["grad_light"]),
+                          ("verts", gpu.dverts, res["grad_verts"], diff["grad_verts"])):
+        g, o, d = g.cpu().numpy().ravel(), o.numpy().ravel(), d.numpy().ravel()
+        st = grad_stats(g, o)
+        on = max(float(np.linalg.norm(o)), 1e-30)
+        explained = float(np.linalg.norm(d)) / on
+        st["image_difference_share"] = explained
+        rec[name] = st
+        if on > 1e-30 and np.linalg.norm(o) > 0:
+            assert st["rel_l2"] <= 2.0 * explained + 2e-3, \
+                f"dL/d{name}: end-to-end relative L2 {st['rel_l2']:.3g}, image-difference share {explained:.3g}"
+    report(rec)
 
 
 def test_end_to_end_image(case):
     """Whole forward with no stage substitution.  Tolerance derived from float32
     moments: sigma^2 = m2 - m1^2 inherits ~3e-8 absolute error, and
     |dv/dsigma^2|, |dv/dmu| <= 0.65 / sigma_min, so pixels may differ by
-    ~1e-3 where sigma^2 sits at its floor."""
+    ~1e-3 where sigma^2 sits at its floor.  The stage-wise tests hold every
+    stage to 1e-5 + 1e-4 |o|; this bound is a regression guard on the chained
+    result, whose error distribution is reported."""
     sc, _, gpu, ref = case
-    assert_close(gpu.image.cpu().numpy(), ref["image"].detach().numpy(), "end-to-end image", atol=2e-3, rtol=1e-3)
+    g, o = gpu.image.cpu().numpy().astype(np.float64), ref["image"].detach().numpy()
+    d = np.abs(g - o)
+    report({"test": "end_to_end_image", "case": case_name(case), "max_abs": float(d.max()),
+            "p99_abs": float(np.percentile(d, 99)), "p999_abs": float(np.percentile(d, 99.9)),
+            "share_above_stage_bar": float(np.mean(d > ATOL + RTOL * np.abs(o)))})
+    assert_close(g, o, "end-to-end image", atol=2e-3, rtol=1e-3)

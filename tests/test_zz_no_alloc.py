@@ -1,20 +1,36 @@
-"""The allocation-free filter entry point (dsm_filter_moments_noalloc) gives the
-same moment maps as dsm_filter_moments, call after call, through the C ABI.
+"""The allocation-free filter entry point (dsm_filter_moments_noalloc), called
+through the C ABI.
 
-It exists for callers that must not allocate device memory while they run (a
-fixed-budget real-time loop, code inside a stream capture, a host application
-that owns the memory pool); its intermediate map is a static device array of the
-library.  This file is collected last so that a run stopping at the first
-failure has run every other test before it."""
+It serves callers that cannot allocate device memory while they run: a
+real-time loop that works inside a fixed, preallocated memory budget, or a host
+application that owns the device memory pool and lets no other allocator touch
+the device.  For radii 16 to 32 its intermediate map is a static device array
+of the library; radii up to 15 need no intermediate.  Checked here, for two
+calls in a row on fresh inputs (the second call reuses the array the first one
+wrote):
+- the result equals dsm_filter_moments for the same arguments and the oracle's
+  separable filter, within |g - o| <= 1e-5 + 1e-4 |o|;
+- radii 16 to 32 take the two-pass path, the one that writes and reads the
+  static array (two kernel launches per call, against one for the tiled
+  kernel);
+- after the first call on the device, calls leave the device's free memory
+  unchanged;
+- maps larger than the array are rejected.
+
+This file is collected last, so that a run stopping at the first failure has
+run every other test before it."""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
 
+from oracle import dsm_oracle as O
+
 pytestmark = pytest.mark.gpu
 
 ATOL, RTOL = 1e-5, 1e-4
+F64 = torch.float64
 
 
 def _lib():
@@ -22,7 +38,12 @@ def _lib():
     return dsm, dsm.load_library()
 
 
-def _reference(dsm, inp, sigma, radius, kind, boundary):
+def _call(lib, inp, out, res, sigma, radius, kind, boundary, stream):
+    return lib.dsm_filter_moments_noalloc(ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()), res,
+                                          ctypes.c_float(sigma), radius, kind, boundary, ctypes.c_void_p(stream))
+
+
+def _existing_entry_point(dsm, inp, sigma, radius, kind, boundary):
     ctx = dsm.Context()
     out = torch.empty_like(inp)
     ctx.filter_moments(inp, out, sigma, radius, kind, boundary)
@@ -31,29 +52,76 @@ def _reference(dsm, inp, sigma, radius, kind, boundary):
     return out
 
 
-@pytest.mark.parametrize("res,sigma,radius,kind,boundary", [(300, 2.0, 0, 0, 0), (1024, 1.5, 0, 0, 1), (77, 1.0, 2, 1, 0)])
-def test_noalloc_filter_matches_existing_entry_point(res, sigma, radius, kind, boundary):
+def _within(got, ref):
+    g, r = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    excess = np.abs(g - r) - (ATOL + RTOL * np.abs(r))
+    return float(excess.max()), float(np.abs(g - r).max())
+
+
+# (res, sigma, radius, kind, boundary): radius 0 means ceil(2 sigma)
+CASES = [
+    (1024, 6.0, 20, 0, 0),     # Gaussian, r = 20, clamp: the largest map the array holds
+    (500, 1.0, 32, 1, 1),      # box, r = 32 (the largest radius), zero boundary
+    (300, 8.0, 0, 0, 1),       # Gaussian, r = ceil(16) = 16 (smallest two-pass radius), ragged map, zero boundary
+    (333, 12.0, 0, 1, 0),      # box, r = 24, ragged map, clamp
+    (1024, 1.5, 0, 0, 1),      # Gaussian, r = 3: the tiled kernel, no intermediate
+    (77, 1.0, 2, 1, 0),        # box, r = 2, tiled
+]
+
+
+@pytest.mark.parametrize("res,sigma,radius,kind,boundary", CASES)
+def test_noalloc_filter_matches_existing_entry_point_and_oracle(res, sigma, radius, kind, boundary):
     dsm, lib = _lib()
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream().cuda_stream
-    g = torch.Generator(device="cpu").manual_seed(res)
-    for call in range(2):                               # two calls in a row share the static array
+    r_eff = radius if radius > 0 else int(np.ceil(2.0 * sigma))
+    w = O.filter_weights(sigma, radius, kind)
+    assert len(w) == 2 * r_eff + 1
+    g = torch.Generator(device="cpu").manual_seed(res * 97 + r_eff)
+    for call in range(2):
         inp = torch.rand((res, res, 2), generator=g).cuda().contiguous()
-        ref = _reference(dsm, inp, sigma, radius, kind, boundary)
+        ref = _existing_entry_point(dsm, inp, sigma, radius, kind, boundary)
         out = torch.full_like(inp, float("nan"))
-        st = lib.dsm_filter_moments_noalloc(ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()), res,
-                                            ctypes.c_float(sigma), radius, kind, boundary, ctypes.c_void_p(stream))
+        n0 = dsm.kernel_launches()
+        st = _call(lib, inp, out, res, sigma, radius, kind, boundary, stream)
+        n1 = dsm.kernel_launches()
         assert st == dsm.DSM_OK, f"call {call}: status {st}"
+        # radii above 15 run the two 1-D passes through the static array
+        assert n1 - n0 == (2 if r_eff > 15 else 1), f"call {call}: {n1 - n0} launches for radius {r_eff}"
         torch.cuda.synchronize()
-        o, r = out.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
-        assert np.all(np.abs(o - r) <= ATOL + RTOL * np.abs(r)), f"call {call}: max diff {np.abs(o - r).max()}"
+        got = out.cpu().numpy()
+        excess, diff = _within(got, ref.cpu().numpy())
+        assert excess <= 0, f"call {call}: differs from dsm_filter_moments by up to {diff}"
+        exp = O.separable_filter(torch.as_tensor(inp.cpu().numpy(), dtype=F64), w, boundary).numpy()
+        excess, diff = _within(got, exp)
+        assert excess <= 0, f"call {call}: differs from the oracle by up to {diff}"
 
 
-def test_noalloc_filter_rejects_maps_above_its_static_size():
+def test_noalloc_filter_leaves_free_device_memory_unchanged():
+    dsm, lib = _lib()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    res = 640
+    inp = torch.rand((res, res, 2), device="cuda")
+    out = torch.empty_like(inp)
+    # the first call on the device may load the library's module (and with it
+    # the static array) and looks the array's address up
+    assert _call(lib, inp, out, res, 10.0, 0, 0, 0, stream) == dsm.DSM_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for radius, kind, boundary in ((20, 0, 0), (32, 1, 1), (3, 0, 1), (17, 1, 0)):
+        assert _call(lib, inp, out, res, 10.0, radius, kind, boundary, stream) == dsm.DSM_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"free device memory changed by {free0 - free1} bytes"
+
+
+def test_noalloc_filter_rejects_maps_above_its_static_size_and_bad_arguments():
     dsm, lib = _lib()
     torch.cuda.set_device(0)
     inp = torch.zeros((1025, 1025, 2), device="cuda")
     out = torch.zeros_like(inp)
-    st = lib.dsm_filter_moments_noalloc(ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()), 1025,
-                                        ctypes.c_float(2.0), 0, 0, 0, None)
-    assert st == dsm.DSM_ERR_CAPACITY
+    assert _call(lib, inp, out, 1025, 2.0, 0, 0, 0, None) == dsm.DSM_ERR_CAPACITY
+    # a Gaussian needs a finite sigma > 0 even when the radius is given; at most 32 taps per side
+    for sigma, radius, kind in ((0.0, 4, 0), (float("nan"), 4, 0), (float("inf"), 0, 1), (2.0, 33, 0)):
+        assert _call(lib, inp, out, 64, sigma, radius, kind, 0, None) == dsm.DSM_ERR_INVALID_ARG, (sigma, radius)
