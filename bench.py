@@ -64,15 +64,19 @@ def workload_config(name, sc, desc):
 
 
 # ----------------------------------------------------------------------------- algorithmic bytes per stage
-def stage_bytes(sc) -> dict:
+def stage_bytes(sc, listed=None) -> dict:
     """Algorithmic DRAM bytes of one call of each timed stage (every
-    materialised buffer counted once; neighbour re-reads not counted)."""
+    materialised buffer counted once; neighbour re-reads not counted).
+    `listed`: per view (lights, then the camera) the pixels on its
+    antialiasing work list (dsm_raster_stats), which the list passes read."""
     V, T = int(sc["verts"].shape[0]), int(sc["tris"].shape[0])
     L = len(sc["lights"])
     Rs = [int(l["res"]) ** 2 for l in sc["lights"]]
     WH = int(sc["camera"]["width"]) * int(sc["camera"]["height"])
     views = L + 1
     texels = sum(Rs)
+    listed = list(listed) if listed is not None else [0] * views
+    sm_listed, cam_listed = sum(listed[:L]), listed[L] if len(listed) > L else 0
     return {
         # transform (12 V in, 32 V out, +4 V depth) and triangle setup (12 T in, 64 T + 2 T out), binning count
         "setup": views * (12 * V + 32 * V + 12 * T + 66 * T + 64 * T) + L * 4 * V,
@@ -80,21 +84,22 @@ def stage_bytes(sc) -> dict:
         # setup records and lists read once, one 16-byte G-buffer texel written per pixel, and per light
         # texel the depth sample (f, f^2), 8 bytes
         "raster": views * (64 * T + 4 * T) + 16 * (texels + WH) + 8 * texels,
-        # detection: G-buffer 16 in, listed-flag byte out (the list pass touches ~1 % of texels: not counted)
-        "sm_antialias": texels * (16 + 1),
+        # detection: G-buffer 16 in, listed-flag byte out; list pass per listed texel:
+        # list entry 4, G-buffer 16, (f, f^2) 8 in, antialiased value 8 out
+        "sm_antialias": texels * (16 + 1) + sm_listed * (4 + 16 + 8 + 8),
         # one tiled pass: (f, f^2) 8 + flag 1 in, moments 8 out
         "filter": texels * (8 + 1 + 8),
         "shade": WH * (16 + 16) + 8 * texels + 24 * V,
-        "final_antialias": WH * (16 + 16 + 16 + 1),
+        "final_antialias": WH * (16 + 16 + 16 + 1) + cam_listed * (4 + 16 + 16 + 16),
         "bwd_clear": 8 * texels + views * 16 * V + 4 * L * V + 24 * V,
-        "bwd_final_antialias": WH * (1 + 16 + 16),
+        "bwd_final_antialias": WH * (1 + 16 + 16) + cam_listed * (4 + 16 + 16 + 16 + 16),
         # per pixel: G-buffer 16 + dL/dcolour 16 in, pgrad 32 out; texel gradient scatter 8 per texel
         "bwd_shade": WH * (16 + 16 + 32) + 8 * texels + 40 * V,
         "bwd_shade_scatter": WH * (16 + 32) + 40 * V,
         # dm 8 + f 8 in, dL/df~ 8 + dL/df 4 out
         "bwd_filter": texels * (8 + 8 + 8 + 4),
-        # list pass only (~1 % of texels): not counted
-        "bwd_sm_antialias": 0,
+        # list pass per listed texel: list entry 4, G-buffer 16, (f, f^2) 8, dL/df~ 8 in, dL/df 4 out
+        "bwd_sm_antialias": sm_listed * (4 + 16 + 8 + 8 + 4),
         # G-buffer 16 + dL/df 4 in, vertex gradients
         "bwd_sm_interp": texels * (16 + 4) + 20 * V * L,
         "bwd_vertex": views * 16 * V + 4 * L * V + 12 * V + 24 * V + 12 * T,
@@ -113,19 +118,38 @@ def source_sha1() -> str:
     return h.hexdigest()
 
 
-def dram_traffic(workload: str, stage: str):
-    """DRAM bytes per step of a stage from the committed ncu capture, or None
-    when the capture is missing or was taken on other kernel sources."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+def kernel_counters(workload: str):
+    """Per-stage ncu counters of one step (profiles/kernel_counters.json), or
+    None when missing or captured on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "kernel_counters.json")
     try:
         with open(path) as f:
-            d = json.load(f).get(workload, {})
+            d = json.load(f).get(workload)
     except Exception:
         return None
-    if d.get("source_sha1") != source_sha1():
+    if not d or d.get("source_sha1") != source_sha1():
         return None
-    v = d.get("bytes_per_step", {}).get(stage)
-    return int(v) if v is not None else None
+    return d["stages"]
+
+
+def stage_bound(c: dict) -> str:
+    """'alu' when the stage's warps issue instructions for a larger share of
+    the time than its DRAM is busy (instruction issue and latency bound), else
+    'hbm'."""
+    issue = c.get("smsp__issue_active.avg.pct_of_peak_sustained_active")
+    dram = c.get("dram__throughput.avg.pct_of_peak_sustained_elapsed")
+    if issue is None or dram is None:
+        return "hbm"
+    return "alu" if issue > dram else "hbm"
+
+
+def dram_traffic(workload: str, stage: str):
+    """DRAM bytes per step of a stage from the committed ncu counters, or None
+    when they are missing or were taken on other kernel sources."""
+    c = kernel_counters(workload)
+    if c is not None and stage in c and "dram__bytes_read.sum" in c[stage]:
+        return int(c[stage]["dram__bytes_read.sum"] + c[stage].get("dram__bytes_write.sum", 0))
+    return None
 
 
 def load_peaks():
@@ -245,66 +269,92 @@ def barrier(world):
 
 
 # ----------------------------------------------------------------------------- oracle timing (CPU baseline)
-def oracle_sample(sc: dict, scale: int, keep_instances: int, seed: int = 0) -> tuple[float, str, int]:
-    """Time the CPU oracle (fwd + bwd) on a bounded sample of the workload and
-    scale it to one full frame.  Sample: the first `keep_instances` objects of
-    the scene plus the ground, shadow maps and camera reduced by `scale` per
-    axis.  Per-triangle raster time scales with the triangle count, the rest
-    with the pixel count.  Returns (estimated seconds per full frame,
-    description, threads)."""
+# Whole frames of the oracle (forward, L2 loss, backward), unchanged, on the
+# host's cores: one frame per worker process (one thread each; the oracle's
+# raster is a Python loop over triangles, so one frame cannot use more cores),
+# as many workers as cores.  Workers are spawned (never forked after the GPU
+# has been used) and build the scene once, before the timed region.
+_ORACLE_STATE = {}
+
+
+def _oracle_worker_init(workload: str, item: int):
+    import torch
+    torch.set_num_threads(1)
+    sc, _ = make_workload(workload, item)
+    _ORACLE_STATE["scene"] = sc
+    _ORACLE_STATE["target"] = np.zeros((int(sc["camera"]["height"]), int(sc["camera"]["width"]), 4))
+
+
+def _oracle_frame(_k: int) -> float:
+    from oracle import dsm_oracle as O
+    t0 = time.perf_counter()
+    O.render_and_grad(_ORACLE_STATE["scene"], _ORACLE_STATE["target"])
+    return time.perf_counter() - t0
+
+
+def _oracle_ready(_k: int) -> int:
+    return os.getpid()
+
+
+def oracle_frames(workload: str, warmup: int, frames: int, procs: int) -> dict:
+    """Wall time of `frames` whole oracle frames on `procs` worker processes
+    (after `warmup` untimed frames); frames/s = frames / wall."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs, initializer=_oracle_worker_init, initargs=(workload, 0)) as pool:
+        pool.map(_oracle_ready, range(procs), chunksize=1)        # every worker started and holds the scene
+        if warmup > 0:
+            pool.map(_oracle_frame, range(warmup), chunksize=1)
+        t0 = time.perf_counter()
+        per_frame = pool.map(_oracle_frame, range(frames), chunksize=1)
+        wall = time.perf_counter() - t0
+    return {"wall_s": wall, "frames": frames, "procs": procs, "frame_s_mean": float(np.mean(per_frame)),
+            "frame_s_max": float(np.max(per_frame))}
+
+
+def oracle_single_thread_frame(workload: str) -> float:
+    """Seconds of one oracle frame on one thread, in this process."""
     import torch
     from oracle import dsm_oracle as O
-    import scenes  # noqa: F401
-    tri_mat = sc["tri_mat"]
-    keep = np.isin(tri_mat, list(range(0, keep_instances + 1)))
-    tris_full = sc["tris"]
-    tris = tris_full[keep]
-    used = np.unique(tris)
-    remap = -np.ones(sc["verts"].shape[0], np.int64)
-    remap[used] = np.arange(len(used))
-    sub = dict(sc)
-    sub["verts"] = sc["verts"][used]
-    sub["tris"] = remap[tris].astype(np.int32)
-    sub["tri_mat"] = tri_mat[keep]
-    sub["lights"] = [dict(l, res=max(8, l["res"] // scale)) for l in sc["lights"]]
-    cam = dict(sc["camera"])
-    cam["width"], cam["height"] = max(8, cam["width"] // scale), max(8, cam["height"] // scale)
-    sub["camera"] = cam
-    raster_time = [0.0]
-    orig = O.raster
-
-    def timed_raster(*a, **k):
-        t0 = time.perf_counter()
-        r = orig(*a, **k)
-        raster_time[0] += time.perf_counter() - t0
-        return r
-
-    O.raster = timed_raster
+    sc, _ = make_workload(workload, 0)
+    target = np.zeros((int(sc["camera"]["height"]), int(sc["camera"]["width"]), 4))
+    n = torch.get_num_threads()
+    torch.set_num_threads(1)
     try:
-        target = np.zeros((cam["height"], cam["width"], 4))
         t0 = time.perf_counter()
-        O.render_and_grad(sub, target)
-        total = time.perf_counter() - t0
+        O.render_and_grad(sc, target)
+        return time.perf_counter() - t0
     finally:
-        O.raster = orig
-    t_tri = raster_time[0]
-    t_pix = max(total - t_tri, 0.0)
-    tri_factor = tris_full.shape[0] / max(1, tris.shape[0])
-    pix_factor = float(scale * scale)
-    est = t_tri * tri_factor + t_pix * pix_factor
-    desc = (f"oracle fwd+bwd on {tris.shape[0]} of {tris_full.shape[0]} triangles (first {keep_instances} objects + "
-            f"ground) at 1/{scale} resolution per axis ({total:.1f} s: raster {t_tri:.1f} s scaled x{tri_factor:.1f}, "
-            f"per-pixel {t_pix:.1f} s scaled x{pix_factor:.0f})")
-    return est, desc, torch.get_num_threads()
+        torch.set_num_threads(n)
 
 
-def choose_sample(budget_s: float):
-    """Sample size for the oracle so that one sample takes about budget_s."""
-    if budget_s >= 20:
-        return 4, 8
-    if budget_s >= 8:
-        return 8, 4
-    return 16, 2
+def host_cores() -> tuple[int, str]:
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return len(os.sched_getaffinity(0)), model
+
+
+def cpu_baseline_record(workload: str, warmup: int, frames: int) -> dict:
+    """The oracle's whole-frame throughput on the host cores, and a one-thread
+    frame of the smallest configuration."""
+    cores, model = host_cores()
+    procs = max(1, min(cores, frames))
+    r = oracle_frames(workload, warmup, frames, procs)
+    one = oracle_single_thread_frame("config1")
+    return {"value": round(r["frames"] / r["wall_s"], 6), "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": (f"{r['frames']} whole {workload} frames (forward, L2 loss, backward; every triangle, full "
+                       f"resolution) on {procs} worker processes of one thread each, {r['wall_s']:.1f} s wall; "
+                       f"mean {r['frame_s_mean']:.1f} s per frame"),
+            "cpu_model": model, "host_cores": cores, "wall_s": round(r["wall_s"], 2),
+            "frame_s_mean": round(r["frame_s_mean"], 2),
+            "config1_single_thread_frame_s": round(one, 3)}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -435,7 +485,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant stage (event timing of the roofline region)
     peak, peak_kind = load_peaks()
-    sb = stage_bytes(sc)
+    sb = stage_bytes(sc, [x["aa_listed"] for x in work])
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_calls = prof[dom]
     achieved = sb[dom] * k_prof / (dom_ms / 1e3) / 1e9
@@ -447,6 +497,38 @@ def run_ours(args):
     dom_launches = max(dom_calls / k_prof, 1.0)
     traffic_step = dram_traffic(args.workload, dom)
     traffic = int(traffic_step / dom_launches) if traffic_step is not None else None
+    hbm_roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu)",
+                "algorithmic_bytes_per_launch": int(sb[dom] / dom_launches),
+                "algorithmic_bytes_per_step": int(sb[dom]),
+                "ms_per_step": round(dom_ms / k_prof, 4), "launches_per_step": dom_calls / k_prof,
+                "timed_steps": k_prof}
+    roofline = hbm_roof
+    counters = kernel_counters(args.workload)
+    if counters and dom in counters and stage_bound(counters[dom]) == "alu":
+        # instruction-issue roofline: warp instructions (ncu, per step) over the
+        # live stage time, against every scheduler issuing one per cycle
+        props = torch.cuda.get_device_properties(dev)
+        mhz = (clocks or {}).get("sm_mhz") or 2032.0
+        issue_peak = props.multi_processor_count * 4 * mhz * 1e6 / 1e9        # G warp-instructions/s
+        inst = counters[dom]["smsp__inst_executed.sum"]
+        ach = inst / (dom_ms / k_prof / 1e3) / 1e9
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 1), "peak": round(issue_peak, 1),
+                    "peak_source": f"{props.multi_processor_count} SMs x 4 schedulers x 1 warp-instruction per cycle "
+                                   f"x {mhz:.0f} MHz (median SM clock of the timed region)",
+                    "unit": "G warp-instructions/s", "frac": round(ach / issue_peak, 4), "traffic": traffic,
+                    "traffic_unit": "DRAM bytes per launch (ncu)",
+                    "warp_instructions_per_step": int(inst),
+                    "issue_active_pct_ncu": counters[dom].get("smsp__issue_active.avg.pct_of_peak_sustained_active"),
+                    "dram_pct_ncu": counters[dom].get("dram__throughput.avg.pct_of_peak_sustained_elapsed"),
+                    "ms_per_step": round(dom_ms / k_prof, 4), "launches_per_step": dom_calls / k_prof,
+                    "timed_steps": k_prof, "hbm": {k: hbm_roof[k] for k in ("achieved", "peak", "unit", "frac",
+                                                                           "algorithmic_bytes_per_launch")}}
+    for k, st in stages.items():
+        if counters and k in counters:
+            st["bound"] = stage_bound(counters[k])
+            st["dram_bytes_per_step_ncu"] = dram_traffic(args.workload, k)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(sec_max * 1e3 / args.steps, 4), "higher_is_better": True,
@@ -455,13 +537,7 @@ def run_ours(args):
                        step="forward + L2 loss + backward recorded once as a CUDA graph (dsm_batch_step, one "
                             "scene) and replayed per step"),
         "eager_ms_per_step": round(eager_ms, 4),
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                     "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu)",
-                     "algorithmic_bytes_per_launch": int(sb[dom] / dom_launches),
-                     "algorithmic_bytes_per_step": int(sb[dom]),
-                     "ms_per_step": round(dom_ms / k_prof, 4), "launches_per_step": dom_calls / k_prof,
-                     "timed_steps": k_prof},
+        "roofline": roofline,
         "stages": stages,
         "frame_algorithmic_GBps": round(sum(sb.values()) * value / world / 1e9, 1),
         "raster_work": dict(raster_work, pixel_tests_per_s=round(tests * value / world)),
@@ -472,10 +548,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h)},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        scale, keep = choose_sample(args.cpu_budget)
-        est, sdesc, threads = oracle_sample(sc, scale, keep)
-        out["cpu_baseline"] = {"value": round(1.0 / est, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
-                               "sample": sdesc}
+        # one wave of whole frames, one per host core
+        out["cpu_baseline"] = cpu_baseline_record(args.workload, 0, host_cores()[0])
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -485,28 +559,30 @@ def run_ours(args):
 
 # ----------------------------------------------------------------------------- reference arm (the oracle)
 def run_reference(args):
+    """The oracle, as it stands, on the host cores: W untimed whole frames,
+    then K timed whole frames (one per worker process, as many workers as
+    cores); value = K / wall, the same measurement as the GPU arm's
+    cpu_baseline."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import torch
     sc, desc = make_workload(args.workload, 0)
-    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
-    scale, keep = choose_sample(budget)
-    for _ in range(args.warmup):
-        oracle_sample(sc, scale, keep)
-    ests, sdesc = [], ""
-    for _ in range(args.steps):
-        est, sdesc, threads = oracle_sample(sc, scale, keep)
-        ests.append(est)
-    sec = float(np.mean(ests)) if ests else float("nan")
-    value = 1.0 / sec if ests else float("nan")
+    cores, model = host_cores()
+    procs = max(1, min(cores, args.steps))
+    r = oracle_frames(args.workload, args.warmup, args.steps, procs)
+    value = r["frames"] / r["wall_s"]
+    base = {"value": round(value, 6), "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": (f"{r['frames']} whole {args.workload} frames (forward, L2 loss, backward; every triangle, "
+                       f"full resolution) on {procs} worker processes of one thread each after {args.warmup} "
+                       f"untimed ones, {r['wall_s']:.1f} s wall; mean {r['frame_s_mean']:.1f} s per frame"),
+            "cpu_model": model, "host_cores": cores, "wall_s": round(r["wall_s"], 2),
+            "frame_s_mean": round(r["frame_s_mean"], 2)}
     out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+           "warmup": args.warmup, "ms_per_step": round(r["wall_s"] * 1e3 / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
            "config": workload_config(args.workload, sc, desc), "impl": "reference",
-           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": torch.get_num_threads(),
-                            "kind": "oracle", "sample": sdesc},
+           "cpu_baseline": base,
            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -721,6 +797,134 @@ def run_reconstruction(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_step(args):
+    """A short eager run for ncu: build the workload's renderer, run
+    `warmup` forward + L2 loss + backward steps and then one more, with no
+    graph, no autotuning, no timing and no CPU work, so that a capture with
+    -k/-c selects the launches of the last step after few launches before
+    them."""
+    import torch
+    import scenes
+    from paper_2308_10896_b300 import dsm
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sc, _ = make_workload(args.workload, 0)
+    r = dsm.Renderer(sc)
+    verts_t = torch.as_tensor(scenes.jitter_vertices(sc, 0.01, 99), device=dev).contiguous()
+    target = r.forward(verts=verts_t).clone()
+    image = torch.empty_like(target)
+    loss = torch.zeros(1, device=dev)
+    gimg = torch.empty_like(target)
+    for k in range(args.warmup + 1):
+        last = k == args.warmup
+        if last:
+            torch.cuda.synchronize(dev)
+            torch.cuda.nvtx.range_push("dsm_profiled_step")   # ncu --nvtx --nvtx-include dsm_profiled_step/
+        n0 = dsm.kernel_launches()
+        r.forward(image=image)
+        dsm.l2_loss_grad(image, target, loss, gimg)
+        r.backward(gimg)
+        per_step = dsm.kernel_launches() - n0
+        if last:
+            torch.cuda.nvtx.range_pop()
+    r.ctx.sync()
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_step": args.workload, "steps": args.warmup + 1,
+                      "library_launches_per_step": per_step}), flush=True)
+
+
+# Kernel name -> profiler stage (the stage whose CUDA events bracket it).
+KERNEL_STAGES = [
+    (r"light_setup_kernel|set_cameras_kernel|transform_all_kernel|tri_setup_all_kernel|silhouette_all_kernel|"
+     r"vertex_normals_kernel|bin_kernel<0>|alloc_kernel", "setup"),
+    (r"bin_kernel<1>|units_kernel", "bin_fill"),
+    (r"raster_kernel<", "raster"),
+    (r"aa_detect_kernel|aa_forward_list_kernel<float2>", "sm_antialias"),
+    (r"filter_tma_kernel<\d+, 0>|filter_tile_kernel<\d+, 0>|filter_pass_kernel<(true|false), false>|compose_kernel",
+     "filter"),
+    (r"shade_kernel", "shade"),
+    (r"aa_forward_kernel<float4>|aa_forward_list_kernel<float4>", "final_antialias"),
+    (r"l2_kernel", "loss"),
+    (r"clear_kernel", "bwd_clear"),
+    (r"aa_backward4_kernel|aa_backward4_list_kernel", "bwd_final_antialias"),
+    (r"shade_backward_kernel", "bwd_shade"),
+    (r"shade_scatter_kernel|shade_big_resolve_kernel", "bwd_shade_scatter"),
+    (r"filter_tma_kernel<\d+, 1>|filter_tile_kernel<\d+, 1>|filter_pass_kernel<(true|false), true>|fold_kernel",
+     "bwd_filter"),
+    (r"sm_aa_adjoint_list_kernel|sm_band_mask_kernel", "bwd_sm_antialias"),
+    (r"sm_interp_adjoint_kernel|sm_big_resolve_kernel", "bwd_sm_interp"),
+    (r"normals_bwd_|vertex_backward_kernel|red_reduce_kernel|light_grad_kernel", "bwd_vertex"),
+]
+
+
+def kernel_stage(name: str):
+    import re
+    for pat, stage in KERNEL_STAGES:
+        if re.search(pat, name):
+            return stage
+    return None
+
+
+def ingest_ncu(csv_paths: list, workload: str, command: str):
+    """Per-stage counters of one step from ncu --csv --metrics logs of
+    `--profile-step` restricted to its profiled step (NVTX range
+    dsm_profiled_step; one log per kernel family) into
+    profiles/kernel_counters.json, keyed by workload and the CUDA sources'
+    hash: time, DRAM bytes, warp instructions and, where captured, L2 hit
+    rate, issue activity and atomics per stage and per kernel."""
+    import csv
+    last = []
+    for path in csv_paths:
+        rows, order = {}, []
+        with open(path) as f:
+            lines = [ln for ln in f if ln.startswith('"')]
+        for rec in csv.DictReader(lines):
+            key = rec["ID"]
+            if key not in rows:
+                rows[key] = {"name": rec["Kernel Name"], "m": {}}
+                order.append(key)
+            try:
+                rows[key]["m"][rec["Metric Name"]] = float(rec["Metric Value"].replace(",", ""))
+            except ValueError:
+                pass
+        last += [rows[k] for k in order if kernel_stage(rows[k]["name"])]
+    stages = {}
+    kernels = {}
+    for r in last:
+        short = r["name"].split("(")[0].replace("void ", "").replace("dsm::", "")
+        kr = kernels.setdefault(short, {"launches": 0, "stage": kernel_stage(r["name"])})
+        kr["launches"] += 1
+        for m, v in r["m"].items():
+            kr.setdefault(m, []).append(v)
+        st = stages.setdefault(kernel_stage(r["name"]), {"launches": 0})
+        st["launches"] += 1
+        t = r["m"].get("gpu__time_duration.sum", 1.0)
+        for m, v in r["m"].items():
+            if m.endswith(".pct") or "pct_of_peak" in m:
+                st.setdefault(m + "__list", []).append((v, t))
+            else:
+                st[m] = st.get(m, 0.0) + v
+    for st in stages.values():
+        # percentages: weighted by each launch's duration
+        for m in [k for k in st if k.endswith("__list")]:
+            vals = st.pop(m)
+            st[m[:-6]] = round(sum(v * t for v, t in vals) / max(sum(t for _, t in vals), 1e-30), 2)
+    path = os.path.join(ROOT, "profiles", "kernel_counters.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except Exception:
+        data = {}
+    for kr in kernels.values():
+        for m in [k for k in kr if isinstance(kr[k], list)]:
+            vals = kr[m]
+            kr[m] = round(float(np.mean(vals)), 2) if (m.endswith(".pct") or "pct_of_peak" in m) else float(sum(vals))
+    data[workload] = {"source_sha1": source_sha1(), "command": command, "stages": stages, "kernels": kernels}
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    return data[workload]
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -732,11 +936,19 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel shapes")
-    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for the CPU baseline")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="eager warm-up steps and one more step for an ncu capture; no timing")
+    ap.add_argument("--ingest-ncu", nargs="+", metavar="CSV",
+                    help="write profiles/kernel_counters.json from ncu --csv logs of --profile-step's profiled step")
+    ap.add_argument("--ncu-command", default="", help="the capture command, recorded with --ingest-ncu")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.ingest_ncu:
+        print(json.dumps(ingest_ncu(args.ingest_ncu, args.workload, args.ncu_command)))
+    elif args.profile_step:
+        run_profile_step(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "config4":
         run_batch(args)

@@ -188,7 +188,10 @@ uint64_t dsm_memory_bytes(dsm_ctx* ctx);
  * the tile lists and setup records that raster read (Eq. 1's coverage test):
  * out[0] tile-triangle pairs, out[1] spans of 4 pixels of one row (the raster's
  * work items), out[2] pixel-centre coverage tests (three edge-function steps
- * each).  out: host array of 3.  A diagnostic: launches one kernel on the last
+ * each), and out[3] the pixels on the view's antialiasing work list (those
+ * with a neighbour pair whose nearer triangle has a silhouette edge; 0 when
+ * that view's antialiasing is off).  out: host array of 4.  A diagnostic:
+ * launches one kernel on the last
  * forward's stream and synchronises it.  DSM_ERR_NO_FORWARD without a forward;
  * DSM_ERR_INVALID_ARG for a view out of range or a recomputing context (its
  * views share one buffer set). */

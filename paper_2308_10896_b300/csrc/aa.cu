@@ -507,8 +507,10 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
       const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
       const Bary r = bary_at(cc, cl, i, j, a.W, a.H);
       const float b[3] = {g.y, g.z, 1.f - g.y - g.z};
+      // f = sum_k b_k d_k: centred dL/db_k = gf sum_j b_j (d_k - d_j)
       float gb[3];
-      for (int k = 0; k < 3; ++k) gb[k] = cd[k] * gf;
+      for (int k = 0; k < 3; ++k)
+        gb[k] = gf * (r.b[0] * (cd[k] - cd[0]) + r.b[1] * (cd[k] - cd[1]) + r.b[2] * (cd[k] - cd[2]));
       float4 gcv[3];
       bary_backward(r, gb, px, py, gcv);
       for (int k = 0; k < 3; ++k) {

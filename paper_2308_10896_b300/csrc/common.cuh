@@ -202,12 +202,16 @@ __device__ __forceinline__ Bary bary_at(const float4 (&hi)[3], const float4 (&lo
   return r;
 }
 
-// Adjoint of bary_at: given dL/db_k, the gradient of the three clip vertices.
-__device__ __forceinline__ void bary_backward(const Bary& r, const float gb[3], float px, float py,
+// Adjoint of bary_at, given the centred gradient gbc_k = dL/db_k - sum_j b_j
+// dL/db_j (the normalisation b = beta / S removes the mean): the gradient of
+// the three clip vertices.  Callers form gbc from differences of vertex
+// attributes, gbc_k = sum_j b_j (dL/db_k - dL/db_j), which stay accurate when
+// the attributes of a small triangle's corners nearly agree (subtracting the
+// mean of nearly equal float32 values would lose those digits).
+__device__ __forceinline__ void bary_backward(const Bary& r, const float gbc[3], float px, float py,
                                               float4 gc[3]) {
   float iS = 1.0f / r.S;
-  float mean = gb[0] * r.b[0] + gb[1] * r.b[1] + gb[2] * r.b[2];
-  float gbeta[3] = {(gb[0] - mean) * iS, (gb[1] - mean) * iS, (gb[2] - mean) * iS};
+  float gbeta[3] = {gbc[0] * iS, gbc[1] * iS, gbc[2] * iS};
   // beta = a x c:  dL/da = c x gbeta,  dL/dc = gbeta x a
   float ga[3] = {r.c[1] * gbeta[2] - r.c[2] * gbeta[1], r.c[2] * gbeta[0] - r.c[0] * gbeta[2],
                  r.c[0] * gbeta[1] - r.c[1] * gbeta[0]};

@@ -1355,9 +1355,13 @@ dsm_status dsm_raster_stats(dsm_ctx* ctx, int32_t view, int64_t* out) {
                       v.bs.tile_log2, ctx->stats.as<unsigned long long>(), st);
   DSM_CHECK(cudaGetLastError());
   unsigned long long h[3];
+  int listed = 0;
   DSM_CHECK(cudaMemcpyAsync(h, ctx->stats.p, kBytes, cudaMemcpyDeviceToHost, st));
+  DSM_CHECK(cudaMemcpyAsync(&listed, v.aa_ctr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   DSM_CHECK(cudaStreamSynchronize(st));
   for (int k = 0; k < 3; ++k) out[k] = (int64_t)h[k];
+  const bool aa_on = view_is_light(ctx, view) ? ctx->params.aa_shadow != 0 : ctx->params.aa_final != 0;
+  out[3] = aa_on ? (int64_t)listed : 0;
   return DSM_OK;
 }
 

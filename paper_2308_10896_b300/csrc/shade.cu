@@ -425,10 +425,12 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
         const float2* mom = a.mom[l];
         const float2 m00 = mom[(size_t)j0c * R + i0], m01 = mom[(size_t)j0c * R + i1];
         const float2 m10 = mom[(size_t)j1c * R + i0], m11 = mom[(size_t)j1c * R + i1];
-        const float d00 = m00.x * gm1 + m00.y * gm2, d01 = m01.x * gm1 + m01.y * gm2;
-        const float d10 = m10.x * gm1 + m10.y * gm2, d11 = m11.x * gm1 + m11.y * gm2;
-        const float gfs = (1.f - L.ft) * (d01 - d00) + L.ft * (d11 - d10);
-        const float gft = (1.f - L.fs) * (d10 - d00) + L.fs * (d11 - d01);
+        // d(bilinear)/ds, /dt from texel differences (neighbouring moments
+        // nearly agree; differencing them first keeps their digits)
+        const float gfs = (1.f - L.ft) * ((m01.x - m00.x) * gm1 + (m01.y - m00.y) * gm2) +
+                          L.ft * ((m11.x - m10.x) * gm1 + (m11.y - m10.y) * gm2);
+        const float gft = (1.f - L.fs) * ((m10.x - m00.x) * gm1 + (m10.y - m00.y) * gm2) +
+                          L.fs * ((m11.x - m01.x) * gm1 + (m11.y - m01.y) * gm2);
         // s = (0.5 u + 0.5) R - 0.5,  t = (0.5 - 0.5 v) R - 0.5,  u = cx / cw,  v = cy / cw
         const float gu = gfs * 0.5f * R, gv = -gft * 0.5f * R;
         const float iw = 1.f / L.clip.w;
@@ -584,15 +586,23 @@ __global__ void __launch_bounds__(256) shade_scatter_kernel(ShadeArgs a, ShadeGr
         if (t != tc.tri) tri_load(a, t, tc);
         const float b[3] = {gb4.y, gb4.z, 1.f - gb4.y - gb4.z};
         const float3 gx = make_float3(q0.x, q0.y, q0.z), gnt = make_float3(q0.w, q1.x, q1.y);
-        float gb[3];
         for (int k = 0; k < 3; ++k) {
           c[3 * k] = b[k] * gx.x; c[3 * k + 1] = b[k] * gx.y; c[3 * k + 2] = b[k] * gx.z;
           c[9 + 3 * k] = b[k] * gnt.x; c[10 + 3 * k] = b[k] * gnt.y; c[11 + 3 * k] = b[k] * gnt.z;
-          gb[k] = tc.p[k].x * gx.x + tc.p[k].y * gx.y + tc.p[k].z * gx.z +
-                  tc.n[k].x * gnt.x + tc.n[k].y * gnt.y + tc.n[k].z * gnt.z;
         }
         const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
         const Bary r = bary_at(tc.cc, tc.cl, i, j, a.W, a.H);
+        // x = sum_k b_k p_k, n~ = sum_k b_k n_k: centred dL/db_k from corner differences
+        float gb[3];
+        for (int k = 0; k < 3; ++k) {
+          float acc = 0.f;
+          for (int q = 0; q < 3; ++q) {
+            const float3 dp = make_float3(tc.p[k].x - tc.p[q].x, tc.p[k].y - tc.p[q].y, tc.p[k].z - tc.p[q].z);
+            const float3 dn = make_float3(tc.n[k].x - tc.n[q].x, tc.n[k].y - tc.n[q].y, tc.n[k].z - tc.n[q].z);
+            acc += r.b[q] * (dp.x * gx.x + dp.y * gx.y + dp.z * gx.z + dn.x * gnt.x + dn.y * gnt.y + dn.z * gnt.z);
+          }
+          gb[k] = acc;
+        }
         float4 gcv[3];
         bary_backward(r, gb, px, py, gcv);
         for (int k = 0; k < 3; ++k) {

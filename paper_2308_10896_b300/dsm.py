@@ -266,9 +266,9 @@ class Context:
 
     def raster_stats(self, view: int) -> dict:
         """Raster work of one view in the last forward (see dsm_raster_stats)."""
-        out = (ctypes.c_int64 * 3)()
+        out = (ctypes.c_int64 * 4)()
         self._check(self.lib.dsm_raster_stats(self.h, int(view), ctypes.cast(out, ctypes.c_void_p)), self.h)
-        return {"pairs": int(out[0]), "spans": int(out[1]), "pixel_tests": int(out[2])}
+        return {"pairs": int(out[0]), "spans": int(out[1]), "pixel_tests": int(out[2]), "aa_listed": int(out[3])}
 
     def set_tuning(self, light_tile=32, camera_tile=32, big_tiles=16, filter_shape=0):
         t = Tuning(light_tile, camera_tile, big_tiles, filter_shape)

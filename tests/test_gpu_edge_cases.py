@@ -43,7 +43,7 @@ def test_empty_mesh():
     assert dv.numel() == 0
     assert not dl.cpu().numpy().any() and not da.cpu().numpy().any()
     for w in range(len(sc["lights"]) + 1):
-        assert r.ctx.raster_stats(w) == {"pairs": 0, "spans": 0, "pixel_tests": 0}
+        assert r.ctx.raster_stats(w) == {"pairs": 0, "spans": 0, "pixel_tests": 0, "aa_listed": 0}
 
 
 def test_no_lights():

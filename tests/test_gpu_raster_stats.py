@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import scenes
+from oracle import dsm_oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -81,10 +82,16 @@ def test_raster_stats_match_brute_force(tile, big_tiles):
     r.forward()
     r.ctx.sync()
     tris = np.asarray(sc["tris"], np.int64)
+    ref = O.render(sc)
+    adj = O.edge_adjacency(tris)
+    rasters = [(L["raster"], L["setup"]) for L in ref["lights"]] + [(ref["camera_raster"], ref["camera_setup"])]
     for w, (M, W, H) in enumerate(_views(sc)):
         got = r.ctx.raster_stats(w)
         exp = _expected(M, W, H, np.asarray(sc["verts"]), tris, tile, big_tiles)
+        # the antialiasing detection lists exactly the silhouette band
+        ras, st = rasters[w]
+        exp["aa_listed"] = int(O.silhouette_band(ras, O.silhouette_table(adj, st)).sum())
         assert got == exp, f"view {w}: {got} != {exp}"
-        assert exp["pairs"] > 0
+        assert exp["pairs"] > 0 and exp["aa_listed"] > 0
     with pytest.raises(dsm.DsmError):
         r.ctx.raster_stats(len(sc["lights"]) + 1)
