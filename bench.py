@@ -587,6 +587,28 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def scene_cost(sc: dict) -> int:
+    """Work estimate of one scene's frame: camera pixels, shadow-map texels of
+    every light and triangles (each drives a setup, a binning and a raster
+    term of the frame)."""
+    cam = int(sc["camera"]["width"]) * int(sc["camera"]["height"])
+    maps = sum(int(l["res"]) ** 2 * (6 if int(l["type"]) == 2 else 1) for l in sc["lights"])
+    return cam + maps + int(sc["tris"].shape[0]) * (len(sc["lights"]) + 1)
+
+
+def partition_scenes(costs: list, world: int) -> list:
+    """Scenes of a batch split over `world` ranks by cost: largest first, each
+    to the rank with the least cost so far (ties to the lower rank).  Returns
+    one sorted list of scene indices per rank; every scene appears once."""
+    loads = [0] * world
+    parts = [[] for _ in range(world)]
+    for k in sorted(range(len(costs)), key=lambda k: (-costs[k], k)):
+        r = min(range(world), key=lambda q: (loads[q], q))
+        parts[r].append(k)
+        loads[r] += costs[k]
+    return [sorted(p) for p in parts]
+
+
 def run_batch(args):
     """Config 4: 64 independent scenes of uneven size, forward + L2 loss +
     backward of every scene per step.  Batched (dsm_batch_step: one CUDA graph
@@ -596,11 +618,16 @@ def run_batch(args):
     import torch
     import scenes
     from paper_2308_10896_b300 import dsm
-    dev = torch.device("cuda", 0)
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    scs = scenes.config4()
-    for sc in scs[1:]:
-        sc["params"] = dict(scs[0]["params"])
+    all_scs = scenes.config4()
+    for sc in all_scs[1:]:
+        sc["params"] = dict(all_scs[0]["params"])
+    # independent scenes: each rank renders its share, balanced by cost, with
+    # no data-path collective (scaling "weak" in scenes per rank)
+    mine = partition_scenes([scene_cost(sc) for sc in all_scs], world)[rank]
+    scs = [all_scs[k] for k in mine]
     targets = []
     for k, sc in enumerate(scs):
         r = dsm.Renderer(sc)
@@ -618,14 +645,18 @@ def run_batch(args):
         b.step()
     b.stream.synchronize()
     b.sync()
+    barrier(world)
+    torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(b.stream)
     for _ in range(args.steps):
         b.step()
     e1.record(b.stream)
     e1.synchronize()
+    barrier(world)
     b.sync()
-    batch_ms = e0.elapsed_time(e1) / args.steps
+    batch_sec, batch_frames = aggregate(e0.elapsed_time(e1) / 1e3, n * args.steps, world, dev)
+    batch_ms = batch_sec * 1e3 / args.steps
     kps = b.kernels_per_step()
     b.close()
     # one render per scene, in turn
@@ -645,6 +676,7 @@ def run_batch(args):
 
     for _ in range(args.warmup):
         serial_step()
+    barrier(world)
     torch.cuda.synchronize(dev)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s0.record()
@@ -652,22 +684,29 @@ def run_batch(args):
         serial_step()
     s1.record()
     s1.synchronize()
-    serial_ms = s0.elapsed_time(s1) / args.steps
-    tris = [int(sc["tris"].shape[0]) for sc in scs]
+    barrier(world)
+    serial_sec, serial_frames = aggregate(s0.elapsed_time(s1) / 1e3, n * args.steps, world, dev)
+    serial_ms = serial_sec * 1e3 / args.steps
+    tris = [int(sc["tris"].shape[0]) for sc in all_scs]
+    if rank != 0:
+        return
     line = {
-        "metric": "batched fwd+bwd scene-frames/s (64 uneven scenes)", "value": round(n * 1e3 / batch_ms, 2),
-        "unit": "scene-frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "metric": "batched fwd+bwd scene-frames/s (64 uneven scenes)",
+        "value": round(batch_frames / batch_sec, 2),
+        "unit": "scene-frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(batch_ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded generator)",
         "config": {"workload": "config4: 64 scenes, one SH-displaced icosphere of 1k-100k triangles each on a ground "
                                "quad, image 256-1024, shadow maps 512-2048, 1-3 directional lights",
-                   "scenes": n, "triangles_total": sum(tris), "triangles_min_max": [min(tris), max(tris)],
+                   "scenes": len(all_scs), "scenes_per_rank_rank0": n,
+                   "partition": "by cost (pixels + texels + triangles x views), largest first to the least-loaded rank",
+                   "triangles_total": sum(tris), "triangles_min_max": [min(tris), max(tris)],
                    "tunings": {"autotuned": not args.no_autotune,
                                "light_tile_16": sum(t["light_tile"] == 16 for t in tunings),
                                "camera_tile_16": sum(t["camera_tile"] == 16 for t in tunings),
                                "filter_two_pass": sum(t["filter_shape"] == 1 for t in tunings),
                                "big_tiles": sorted({t["big_tiles"] for t in tunings})}},
-        "one_call_per_scene": {"value": round(n * 1e3 / serial_ms, 2), "unit": "scene-frames/s",
+        "one_call_per_scene": {"value": round(serial_frames / serial_sec, 2), "unit": "scene-frames/s",
                                "ms_per_step": round(serial_ms, 4)},
         "speedup": round(serial_ms / batch_ms, 3),
         "gpu_launches": kps * args.steps,

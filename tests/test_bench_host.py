@@ -72,3 +72,50 @@ def test_reference_arm_json_contract():
         assert k in d, k
     assert d["impl"] == "reference" and d["e2e"]["h2d_bytes_per_step"] == 0 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+def _partition_worker(rank, world, port, out):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    import scenes
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    costs = [bench.scene_cost(sc) for sc in scenes.config4()]
+    mine = bench.partition_scenes(costs, world)[rank]
+    got = [None] * world
+    dist.all_gather_object(got, mine)
+    out.put((rank, got, costs))
+    dist.destroy_process_group()
+
+
+def test_config4_scene_partition_covers_every_scene_once_gloo():
+    """Config 4's scenes split over two gloo ranks (the multi-GPU batch):
+    each rank computes its own share; together they hold every scene exactly
+    once, with costs within 5 % of each other."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_partition_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = [q.get(timeout=300) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, parts0, costs), (_, parts1, _) = res
+    assert parts0 == parts1                       # every rank derives the same split
+    flat = sorted(k for part in parts0 for k in part)
+    assert flat == list(range(len(costs)))
+    loads = [sum(costs[k] for k in part) for part in parts0]
+    assert max(loads) <= 1.05 * min(loads), loads
+
+
+def test_partition_is_balanced_for_uneven_costs():
+    sys.path.insert(0, ROOT)
+    import bench
+    costs = [100, 1, 1, 1, 50, 49]
+    parts = bench.partition_scenes(costs, 2)
+    assert sorted(parts[0] + parts[1]) == list(range(6))
+    assert sorted(sum(costs[k] for k in p) for p in parts) == [101, 101]
