@@ -19,13 +19,10 @@ struct Cross {
 };
 
 // Unsnapped screen position (pixels, y down) of vertex v relative to the
-// centre of pixel (i, j): sx - (i + 1/2) = (W x - (2i + 1 - W) w) / 2w and
-// sy - (j + 1/2) = -(H y - (H - 2j - 1) w) / 2w, numerators by pix_rel.
+// centre of pixel (i, j), from its float-float screen position.
 __device__ __forceinline__ float2 rel_screen(const AAArgs& a, int v, int i, int j) {
-  const float4 h = a.clip[v], l = a.clip_lo[v];
-  const float i2w = 0.5f / h.w;
-  return make_float2(pix_rel(h.x, l.x, h.w, l.w, pix_nx(i, a.W), (float)a.W) * i2w,
-                     -pix_rel(h.y, l.y, h.w, l.w, pix_ny(j, a.H), (float)a.H) * i2w);
+  const float4 s = a.scr[v];
+  return make_float2(scr_dx(s, i), scr_dy(s, j));
 }
 
 template <bool kGrad>
@@ -62,8 +59,8 @@ __device__ __forceinline__ Cross find_crossing(const AAArgs& a, int tri, int io,
     c.va = va;
     c.vb = vb;
     // unsnapped screen positions of the endpoints relative to O's pixel centre,
-    // from the clip coordinates' hi + lo (pix_rel): accurate to float32
-    // relative to these small offsets, not to the view's size
+    // from their float-float screen positions: accurate to float32 relative to
+    // these small offsets, not to the view's size
     const float2 sa = rel_screen(a, va, io, jo), sb = rel_screen(a, vb, io, jo);
     // along-coordinate p, across-coordinate q (q = 0 is the line through both
     // centres, p = 0 is O's centre)
@@ -497,15 +494,15 @@ __global__ void __launch_bounds__(256) sm_interp_adjoint_kernel(AAArgs a, const 
       t = id - 1;
       // the triangle's corners are reloaded per texel (L1 hits): keeping them
       // live across rows costs more in occupancy than the loads
-      float4 cl[3];
+      float4 cs[3];
       for (int k = 0; k < 3; ++k) {
         const int v = a.tris[3 * t + k];
         cc[k] = a.clip[v];
-        cl[k] = a.clip_lo[v];
+        cs[k] = a.scr[v];
         cd[k] = depth[v];
       }
       const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
-      const Bary r = bary_at(cc, cl, i, j, a.W, a.H);
+      const Bary r = bary_at(cc, cs, i, j, a.W, a.H);
       const float b[3] = {g.y, g.z, 1.f - g.y - g.z};
       // f = sum_k b_k d_k: centred dL/db_k = gf sum_j b_j (d_k - d_j)
       float gb[3];

@@ -148,35 +148,24 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Clip coordinates are held as hi + lo: hi is the pinned float32 transform
-// (the raster's discrete decisions use it), lo its rounding residual against
-// the exact product of the vertex with the view matrix (see
-// transform_all_kernel).  Quantities measured from a pixel centre are formed
-// from hi + lo without the float32 cancellation between a vertex and a nearby
-// pixel: pix_rel = S x - n w for x = xh + xl, w = wh + wl and the pixel-centre
-// ndc n / S (n = 2i + 1 - S an exact integer, S the view side), with the
-// leading part S xh - n wh rounded once (its product S xh split exactly) and
-// the residual terms added.  Its error is a few float32 ulps of the result,
-// whereas x - (n / S) w in plain float32 loses the digits the two terms share.
-__device__ __forceinline__ float pix_rel(float xh, float xl, float wh, float wl, float n, float S) {
-  float p, pe;
-  two_prod(S, xh, p, pe);
-  const float q = __fmaf_rn(-n, wh, p);
-  const float r = __fmaf_rn(S, xl, __fmaf_rn(-n, wl, pe));
-  return __fadd_rn(q, r);
-}
-
-// Pixel-centre numerators: the centre of column i is at ndc nx / W, of row j
-// at ndc ny / H.
-__device__ __forceinline__ float pix_nx(int i, int W) { return (float)(2 * i + 1 - W); }
-__device__ __forceinline__ float pix_ny(int j, int H) { return (float)(H - 2 * j - 1); }
+// Unsnapped screen positions are held per vertex as float-float pairs
+// (sx_hi, sx_lo, sy_hi, sy_lo) with sx = (x / w / 2 + 1/2) W and
+// sy = (1/2 - y / w / 2) H of the exact clip coordinates: the product of the
+// vertex with the view matrix carried exactly, not the pinned float32
+// transform that every discrete decision uses (see transform_all_kernel).
+// An offset from a pixel centre, (sx_hi - (i + 1/2)) + sx_lo, then keeps
+// float32 accuracy relative to the offset itself, even for a vertex ~1000
+// pixels from the view's origin next to that centre.
+__device__ __forceinline__ float scr_dx(float4 scr, int i) { return (scr.x - ((float)i + 0.5f)) + scr.y; }
+__device__ __forceinline__ float scr_dy(float4 scr, int j) { return (scr.z - ((float)j + 0.5f)) + scr.w; }
 
 // Perspective-correct barycentrics at the centre of pixel (i, j) of the
-// triangle with clip vertices hi[k] + lo[k]: b ~ a x c with a_k = x_k - px w_k,
-// c_k = y_k - py w_k (px, py the centre's ndc).  a and c are formed with
-// pix_rel and scaled by 1/W and 1/H: a common scale of all three a_k (or c_k)
-// leaves b unchanged, so b keeps float32 accuracy relative to the triangle's
-// own size even for sub-pixel triangles far from the view's origin.
+// triangle with clip vertices hi[k] (w) and screen positions scr[k]:
+// b ~ a x c with a_k = x_k - px w_k = (2/W) w_k (sx_k - i - 1/2) and
+// c_k = y_k - py w_k = -(2/H) w_k (sy_k - j - 1/2) (px, py the centre's ndc).
+// The offsets come from the float-float screen positions, so b keeps float32
+// accuracy relative to the triangle's own size even for sub-pixel triangles
+// far from the view's origin.
 struct Bary {
   float b[3];
   float a[3], c[3];
@@ -184,14 +173,13 @@ struct Bary {
   float S;
 };
 
-__device__ __forceinline__ Bary bary_at(const float4 (&hi)[3], const float4 (&lo)[3], int i, int j, int W, int H) {
+__device__ __forceinline__ Bary bary_at(const float4 (&hi)[3], const float4 (&scr)[3], int i, int j, int W, int H) {
   Bary r;
-  const float nx = pix_nx(i, W), ny = pix_ny(j, H), Wf = (float)W, Hf = (float)H;
-  const float iW = 1.0f / Wf, iH = 1.0f / Hf;
+  const float sx = 2.0f / (float)W, sy = -2.0f / (float)H;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    r.a[k] = pix_rel(hi[k].x, lo[k].x, hi[k].w, lo[k].w, nx, Wf) * iW;
-    r.c[k] = pix_rel(hi[k].y, lo[k].y, hi[k].w, lo[k].w, ny, Hf) * iH;
+    r.a[k] = scr_dx(scr[k], i) * (hi[k].w * sx);
+    r.c[k] = scr_dy(scr[k], j) * (hi[k].w * sy);
   }
   r.beta[0] = r.a[1] * r.c[2] - r.a[2] * r.c[1];
   r.beta[1] = r.a[2] * r.c[0] - r.a[0] * r.c[2];

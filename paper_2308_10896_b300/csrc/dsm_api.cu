@@ -60,8 +60,8 @@ struct ViewBufs {
   Buf units, tile_slot, tile_done, skey;
   int units_cap = 0, slot_cap = 0;
   AAWork aa_work() { return AAWork{aa_list.as<int>(), aa_ctr.as<int>()}; }
-  // the clip buffer holds V hi entries, then their V rounding residuals
-  float4* clip_lo(int V) { return clip.as<float4>() + std::max(V, 1); }
+  // the clip buffer holds V clip coordinates, then V float-float screen positions
+  float4* scr(int V) { return clip.as<float4>() + std::max(V, 1); }
   RasterUnits raster_units() {
     return RasterUnits{units.as<int2>(), units_cap, tile_slot.as<int>(), slot_cap, tile_done.as<int>(),
                        skey.as<unsigned long long>()};
@@ -457,7 +457,7 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   v.tilesY = (H + tile - 1) / tile;
   const size_t tiles = (size_t)v.tilesX * v.tilesY;
   const size_t Vn = std::max(V, 1), Tn = std::max(T, 1);
-  DSM_CHECK(v.clip.ensure(2 * Vn * sizeof(float4)));   // hi, then the rounding residual lo
+  DSM_CHECK(v.clip.ensure(2 * Vn * sizeof(float4)));   // clip, then the float-float screen positions
   DSM_CHECK(v.snap.ensure(Vn * sizeof(VertSnap)));
   DSM_CHECK(v.setup.ensure(Tn * sizeof(TriSetup)));
   DSM_CHECK(v.orient.ensure(Tn));
@@ -546,7 +546,7 @@ float warp_exponent(const dsm_ctx* ctx) { return ctx->params.moments == 1 ? ctx-
 
 AAArgs aa_args(const dsm_ctx* ctx, ViewBufs& v) {
   return AAArgs{v.gbuf.as<float4>(), v.W, v.H, ctx->mesh.tris, v.sil.as<uint8_t>(), v.snap.as<VertSnap>(),
-                v.clip.as<float4>(), v.clip_lo(ctx->mesh.n_verts)};
+                v.clip.as<float4>(), v.scr(ctx->mesh.n_verts)};
 }
 
 // Transform, triangle setup and silhouettes of views [w0, w0 + n) in one fused
@@ -559,7 +559,7 @@ ViewSetupArgs view_setup_args(dsm_ctx* ctx, int w0, int n) {
     ViewBufs& v = vbuf(ctx, w);
     va.W[k] = v.W; va.H[k] = v.H; va.tiles[k] = v.tilesX * v.tilesY;
     va.clip[k] = v.clip.as<float4>();
-    va.clip_lo[k] = v.clip_lo(ctx->mesh.n_verts);
+    va.scr[k] = v.scr(ctx->mesh.n_verts);
     va.snap[k] = v.snap.as<VertSnap>();
     va.depth[k] = view_is_light(ctx, w) ? v.depth.as<float>() : nullptr;
     va.setup[k] = v.setup.as<TriSetup>();
@@ -606,7 +606,7 @@ void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
   }
   StageTimer t(ctx, ST_RASTER, st);
   launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,
-                v.bs.tile_log2, v.W, v.H, v.clip.as<float4>(), v.clip_lo(ctx->mesh.n_verts), ctx->mesh.tris,
+                v.bs.tile_log2, v.W, v.H, v.clip.as<float4>(), v.scr(ctx->mesh.n_verts), ctx->mesh.tris,
                 v.gbuf.as<float4>(),
                 light ? v.depth.as<float>() : nullptr, light ? lwork(ctx, w).fmap.as<float2>() : nullptr,
                 warp_exponent(ctx), v.raster_units(), ds, w, st);
@@ -643,7 +643,7 @@ ShadeArgs shade_args(dsm_ctx* ctx, int c) {
   sa.albedo = m.albedo; sa.n_mat = m.n_materials;
   sa.vnormal = ctx->vnormal.as<float>();
   sa.cam_clip = cv.clip.as<float4>();
-  sa.cam_clip_lo = cv.clip_lo(m.n_verts);
+  sa.cam_scr = cv.scr(m.n_verts);
   sa.lights = ctx->lights_dev.as<LightDev>(); sa.L = ctx->L;
   for (int l = 0; l < ctx->L; ++l) { sa.mom[l] = ctx->light[l].mom.as<float2>(); sa.res[l] = ctx->light[l].res; }
   sa.min_variance = ctx->params.min_variance;
@@ -921,9 +921,14 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
       if (w < L) {
         if (vst != st) DSM_CHECK(cudaStreamWaitEvent(vst, ctx->ev_sil, 0));
         light_maps(ctx, w, vst);
-        const LightBufs& lb = ctx->light[w];
-        DSM_CHECK(cudaMemsetAsync(lb.gm.p, 0, (size_t)lb.res * lb.res * sizeof(float2), vst));
       }
+    }
+    // the lights' dL/dm accumulators start the first backward empty; zeroed on
+    // the render stream, which holds the (shorter) camera raster, so the
+    // clears run beside the lights' antialiasing and filter
+    for (int l = 0; l < L; ++l) {
+      const LightBufs& lb = ctx->light[l];
+      DSM_CHECK(cudaMemsetAsync(lb.gm.p, 0, (size_t)lb.res * lb.res * sizeof(float2), st));
     }
     DSM_CHECK(join_views(ctx, st, 0, NV));
     DSM_CHECK(cudaGetLastError());

@@ -73,7 +73,7 @@ struct ShadeArgs {
   int n_mat;
   const float* vnormal;    // V x 3, unit vertex normals
   const float4* cam_clip;  // V, camera clip coordinates
-  const float4* cam_clip_lo;   // V, their rounding residual
+  const float4* cam_scr;   // V, float-float unsnapped screen positions (sx hi, lo, sy hi, lo)
   const LightDev* lights;
   int L;
   const float2* mom[kMaxLightViews];
@@ -123,7 +123,7 @@ struct AAArgs {
   const uint8_t* sil;
   const VertSnap* snap;
   const float4* clip;
-  const float4* clip_lo;   // rounding residual of clip
+  const float4* scr;       // V, float-float unsnapped screen positions (sx hi, lo, sy hi, lo)
 };
 
 // Per-view pointers and sizes for the fused setup of all views of a frame.
@@ -131,7 +131,7 @@ struct ViewSetupArgs {
   int n;
   int W[kMaxViews], H[kMaxViews], tiles[kMaxViews];
   float4* clip[kMaxViews];
-  float4* clip_lo[kMaxViews];     // rounding residual of clip (see transform_all_kernel)
+  float4* scr[kMaxViews];         // float-float unsnapped screen positions (see transform_all_kernel)
   VertSnap* snap[kMaxViews];
   float* depth[kMaxViews];        // light views only (camera: NULL)
   TriSetup* setup[kMaxViews];
@@ -180,7 +180,7 @@ void launch_raster_stats(const TriSetup* setup, const int* offset, const int* li
 // Light views (fmap != NULL) also write the shadow-map depth sample (f, f^2)
 // of every texel, f interpolated from the per-vertex light depths.
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
-                   int tile_log2, int W, int H, const float4* clip, const float4* clip_lo, const int* tris,
+                   int tile_log2, int W, int H, const float4* clip, const float4* scr, const int* tris,
                    float4* gbuf, const float* depth, float2* fmap, float ec, const RasterUnits& ru,
                    DevStatus* status, int view, cudaStream_t st);
 // After the fill pass (filled: its per-tile counts of ordinary triangles):

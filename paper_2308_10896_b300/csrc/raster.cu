@@ -274,6 +274,25 @@ __device__ __forceinline__ float row_residual(const float* Mh, const float* Ml, 
   return __fadd_rn(__fsub_rn(s, pinned), err);
 }
 
+// sx = (x / w / 2 + 1/2) S (sign = 1) or sy = (1/2 - y / w / 2) S (sign = -1)
+// of clip coordinates x = xh + xl, w = wh + wl, as a float-float pair: the
+// quotient's remainder is exact (one fused multiply-add), the scalings by 1/2
+// exact, the final products and sums split exactly (two_prod, two_sum).
+__device__ __forceinline__ float2 screen_ff(float xh, float xl, float wh, float wl, float sign, float S) {
+  const float q1 = __fdiv_rn(xh, wh);
+  const float rem = __fadd_rn(__fmaf_rn(-q1, wh, xh), __fmaf_rn(-q1, wl, xl));
+  const float q2 = __fdiv_rn(rem, wh);                    // x / w = q1 + q2
+  float s, e;
+  two_sum(0.5f, __fmul_rn(sign * 0.5f, q1), s, e);         // 1/2 +- q1 / 2
+  e = __fadd_rn(e, __fmul_rn(sign * 0.5f, q2));
+  float p, pe;
+  two_prod(s, S, p, pe);
+  pe = __fmaf_rn(e, S, pe);
+  float hi, lo;
+  two_sum(p, pe, hi, lo);
+  return make_float2(hi, lo);
+}
+
 __global__ void transform_all_kernel(const float* __restrict__ verts, int V, const float* __restrict__ viewM,
                                      const float* __restrict__ viewMlo, ViewSetupArgs a) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -289,10 +308,12 @@ __global__ void transform_all_kernel(const float* __restrict__ verts, int V, con
     const float c2 = pinned_row(M20 + 8, x, y, z);
     const float c3 = pinned_row(M20 + 12, x, y, z);
     a.clip[w][v] = make_float4(c0, c1, c2, c3);
-    a.clip_lo[w][v] = make_float4(row_residual(M20 + 0, L16 + 0, x, y, z, c0),
-                                  row_residual(M20 + 4, L16 + 4, x, y, z, c1),
-                                  row_residual(M20 + 8, L16 + 8, x, y, z, c2),
-                                  row_residual(M20 + 12, L16 + 12, x, y, z, c3));
+    const float l0 = row_residual(M20 + 0, L16 + 0, x, y, z, c0);
+    const float l1 = row_residual(M20 + 4, L16 + 4, x, y, z, c1);
+    const float l3 = row_residual(M20 + 12, L16 + 12, x, y, z, c3);
+    const float2 sx = screen_ff(c0, l0, c3, l3, 1.f, (float)a.W[w]);
+    const float2 sy = screen_ff(c1, l1, c3, l3, -1.f, (float)a.H[w]);
+    a.scr[w][v] = make_float4(sx.x, sx.y, sy.x, sy.y);
     if (a.depth[w]) a.depth[w][v] = pinned_row(M20 + 16, x, y, z);
     a.snap[w][v] = snap_vertex(c0, c1, c2, c3, a.W[w], a.H[w]);
   }
@@ -650,7 +671,7 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
                                                      const int* __restrict__ offset,
                                                      const int* __restrict__ list, int capacity, int tilesX,
                                                      int n_tiles, int W, int H, const float4* __restrict__ clip,
-                                                     const float4* __restrict__ clip_lo,
+                                                     const float4* __restrict__ scr,
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf,
                                                      const float* __restrict__ depth, float2* __restrict__ fmap,
                                                      float ec, RasterUnits ru, const DevStatus* __restrict__ status,
@@ -801,8 +822,8 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
       const int t = (int)(best & 0xffffffffu);
       const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
       const float4 ch[3] = {clip[v0], clip[v1], clip[v2]};
-      const float4 cl[3] = {clip_lo[v0], clip_lo[v1], clip_lo[v2]};
-      const Bary r = bary_at(ch, cl, i, j, W, H);
+      const float4 cs[3] = {scr[v0], scr[v1], scr[v2]};
+      const Bary r = bary_at(ch, cs, i, j, W, H);
       out = make_float4(__int_as_float(t + 1), r.b[0], r.b[1], key_depth(best));
       if (fmap) {
         // f = sum_k b_k d_k with b_2 = 1 - b_0 - b_1 of the stored barycentrics
@@ -909,16 +930,16 @@ void launch_units(const TriSetup* setup, const int* offset, int* list, int capac
 }
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
-                   int tile_log2, int W, int H, const float4* clip, const float4* clip_lo, const int* tris,
+                   int tile_log2, int W, int H, const float4* clip, const float4* scr, const int* tris,
                    float4* gbuf, const float* depth, float2* fmap, float ec, const RasterUnits& ru,
                    DevStatus* status, int view, cudaStream_t st) {
   const int n = tilesX * tilesY;
   count_launches(1);
   if (tile_log2 == 4)
-    raster_kernel<4><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, clip_lo,
+    raster_kernel<4><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, scr,
                                                   tris, gbuf, depth, fmap, ec, ru, status, view);
   else
-    raster_kernel<5><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, clip_lo,
+    raster_kernel<5><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, scr,
                                                   tris, gbuf, depth, fmap, ec, ru, status, view);
 }
 

@@ -128,7 +128,7 @@ struct TriCache {
   int tri = -1;
   int v[3];
   float3 p[3], n[3];
-  float4 cc[3], cl[3];   // camera clip coordinates: pinned float32 and rounding residual
+  float4 cc[3], cs[3];   // camera clip coordinates (pinned float32) and float-float screen positions
   int mat;
   float3 alb;
 };
@@ -141,7 +141,7 @@ __device__ __forceinline__ void tri_load(const ShadeArgs& a, int t, TriCache& c)
     c.p[k] = make_float3(a.verts[3 * v], a.verts[3 * v + 1], a.verts[3 * v + 2]);
     c.n[k] = make_float3(a.vnormal[3 * v], a.vnormal[3 * v + 1], a.vnormal[3 * v + 2]);
     c.cc[k] = a.cam_clip[v];
-    c.cl[k] = a.cam_clip_lo[v];
+    c.cs[k] = a.cam_scr[v];
   }
   c.mat = material_of(a, t);
   c.alb = make_float3(a.albedo[3 * c.mat], a.albedo[3 * c.mat + 1], a.albedo[3 * c.mat + 2]);
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(256) shade_scatter_kernel(ShadeArgs a, ShadeGr
           c[9 + 3 * k] = b[k] * gnt.x; c[10 + 3 * k] = b[k] * gnt.y; c[11 + 3 * k] = b[k] * gnt.z;
         }
         const float px = pix_ndc_x(i, a.W), py = pix_ndc_y(j, a.H);
-        const Bary r = bary_at(tc.cc, tc.cl, i, j, a.W, a.H);
+        const Bary r = bary_at(tc.cc, tc.cs, i, j, a.W, a.H);
         // x = sum_k b_k p_k, n~ = sum_k b_k n_k: centred dL/db_k from corner differences
         float gb[3];
         for (int k = 0; k < 3; ++k) {
