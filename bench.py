@@ -892,7 +892,7 @@ KERNEL_STAGES = [
      "bwd_filter"),
     (r"sm_aa_adjoint_list_kernel|sm_band_mask_kernel", "bwd_sm_antialias"),
     (r"sm_interp_adjoint_kernel|sm_big_resolve_kernel", "bwd_sm_interp"),
-    (r"normals_bwd_|vertex_backward_kernel|red_reduce_kernel|light_grad_kernel", "bwd_vertex"),
+    (r"normals_bwd_|vertex_backward_kernel|light_sums_kernel", "bwd_vertex"),
 ]
 
 

@@ -90,9 +90,11 @@ struct dsm_ctx {
   DevStatus* hstatus = nullptr;
   // state of the last forward
   bool have_fwd = false;
-  // the forward already zeroed every light's dL/dm accumulator (on the light's
-  // stream, beside the camera shading); the first backward after it need not
+  // the forward already zeroed every light's dL/dm accumulator and (stored
+  // mode) the backward's internal accumulators, beside the light views'
+  // chains; the first backward after it need not
   bool gm_zeroed = false;
+  bool acc_zeroed = false;
   dsm_mesh mesh{};
   dsm_light lights[DSM_MAX_LIGHTS]{};   // the caller's lights
   int n_user = 0;                        // their number
@@ -113,6 +115,9 @@ struct dsm_ctx {
   uint64_t sized_sig = 0;
   // internal streams: one per view (lights, then cameras), fork/join events
   cudaStream_t vs[kMaxViews] = {};
+  cudaStream_t aux = nullptr;            // side stream of the backward's output clear
+  cudaEvent_t ev_aux = nullptr, ev_aux_done = nullptr;
+  bool aux_pending = false;              // the shading adjoints wait for ev_aux_done
   cudaEvent_t ev_fork = nullptr, ev_bfork = nullptr, ev_sil = nullptr, ev_join[kMaxViews] = {};
   // per-stage timing (stage_override >= 0 books every stage under that one)
   bool prof = false;
@@ -235,6 +240,9 @@ cudaError_t ensure_streams(dsm_ctx* c) {
   if ((e = cudaEventCreateWithFlags(&c->ev_sil, cudaEventDisableTiming)) != cudaSuccess) return e;
   for (auto& ev : c->ev_join)
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&c->ev_aux_done, cudaEventDisableTiming)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -344,6 +352,9 @@ void dsm_destroy(dsm_ctx* ctx) {
   if (ctx->hstatus) cudaFreeHost(ctx->hstatus);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto v : ctx->vs) if (v) cudaStreamDestroy(v);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
+  if (ctx->ev_aux) cudaEventDestroy(ctx->ev_aux);
+  if (ctx->ev_aux_done) cudaEventDestroy(ctx->ev_aux_done);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_bfork) cudaEventDestroy(ctx->ev_bfork);
   if (ctx->ev_sil) cudaEventDestroy(ctx->ev_sil);
@@ -702,6 +713,7 @@ dsm_status camera_backward(dsm_ctx* ctx, int c, const float* gimage, float* dver
                                 st));
     }
   }
+  if (ctx->aux_pending) DSM_CHECK(cudaStreamWaitEvent(st, ctx->ev_aux_done, 0));   // outputs cleared
   StageTimer t(ctx, ST_BWD_SHADE, st);
   launch_shade_backward(shade_args(ctx, c), grad_args(ctx, c, dverts, dalbedo, red_stride), st);
   return DSM_OK;
@@ -782,6 +794,35 @@ dsm_status rebuild_view(dsm_ctx* ctx, int w, bool sizing, bool maps, bool detect
   return DSM_OK;
 }
 
+// The backward's internal accumulators (vertex-normal gradient, light-matrix
+// block sums, and per view the clip gradients and big-triangle slots), sized
+// for the current frame.
+int red_stride_of(const dsm_ctx* ctx) {
+  const int n_mat_red = ctx->mesh.n_materials <= kMaxSharedMat ? ctx->mesh.n_materials : 0;
+  return 23 * ctx->L + 3 * n_mat_red;
+}
+dsm_status ensure_backward_accumulators(dsm_ctx* ctx) {
+  const int V = ctx->mesh.n_verts;
+  DSM_CHECK(ctx->gnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
+  DSM_CHECK(ctx->gQ.ensure(sizeof(double) * 20 * kMaxLightViews));
+  DSM_CHECK(ctx->gdirect.ensure(sizeof(double) * 3 * kMaxLightViews));
+  DSM_CHECK(ctx->red.ensure(sizeof(double) * kRedSlots * std::max(red_stride_of(ctx), 1)));
+  return DSM_OK;
+}
+void add_backward_accumulators(dsm_ctx* ctx, Clearer& cl) {
+  const int V = ctx->mesh.n_verts;
+  cl.add(ctx->gnormal.p, sizeof(float) * 3 * V);
+  cl.add(ctx->gQ.p, sizeof(double) * 20 * kMaxLightViews);
+  cl.add(ctx->gdirect.p, sizeof(double) * 3 * kMaxLightViews);
+  cl.add(ctx->red.p, sizeof(double) * kRedSlots * red_stride_of(ctx));
+  if (!ctx->recompute)
+    for (int w = 0; w < ctx->L + ctx->C; ++w) {
+      ViewBufs& v = vbuf(ctx, w);
+      cl.add(v.gclip.p, sizeof(float4) * V);
+      cl.add(v.big_acc.p, (size_t)kMaxBig * kBigSlots * (view_is_light(ctx, w) ? kBigStrideSm : kBigStrideCam) * 4);
+    }
+}
+
 __global__ void set_cameras_kernel(CamMats m, int n, float* dst, float* dst_lo) {
   for (int k = threadIdx.x; k < 20 * n; k += blockDim.x) dst[k] = m.v[k];
   // a camera's float32 matrix is exact: no residual (the slot may have held a light view's)
@@ -798,6 +839,7 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
   if (s != DSM_OK) return s;
   ctx->have_fwd = false;
   ctx->gm_zeroed = false;
+  ctx->acc_zeroed = false;
   cudaStream_t st = (cudaStream_t)params->stream;
   ctx->mesh = *mesh;
   int L = 0;
@@ -832,6 +874,8 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
     s = prepare_light(ctx, l);
     if (s != DSM_OK) return s;
   }
+  s = ensure_backward_accumulators(ctx);
+  if (s != DSM_OK) return s;
   DSM_CHECK(ctx->lights_dev.ensure(sizeof(LightDev) * kMaxLightViews));
   DSM_CHECK(ctx->viewM.ensure(sizeof(float) * 20 * kMaxViews));
   if (!ctx->viewMlo.p) {
@@ -923,12 +967,19 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
         light_maps(ctx, w, vst);
       }
     }
-    // the lights' dL/dm accumulators start the first backward empty; zeroed on
-    // the render stream, which holds the (shorter) camera raster, so the
-    // clears run beside the lights' antialiasing and filter
+    // the lights' dL/dm accumulators and the backward's other internal
+    // accumulators start the first backward empty; zeroed on the render
+    // stream, which holds the (shorter) camera raster, so the clears run
+    // beside the lights' antialiasing and filter
     for (int l = 0; l < L; ++l) {
       const LightBufs& lb = ctx->light[l];
       DSM_CHECK(cudaMemsetAsync(lb.gm.p, 0, (size_t)lb.res * lb.res * sizeof(float2), st));
+    }
+    {
+      Clearer cl;
+      add_backward_accumulators(ctx, cl);
+      cl.launch(st);
+      ctx->acc_zeroed = true;
     }
     DSM_CHECK(join_views(ctx, st, 0, NV));
     DSM_CHECK(cudaGetLastError());
@@ -942,6 +993,7 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
   }
   DSM_CHECK(cudaGetLastError());
   ctx->gm_zeroed = !ctx->recompute;
+  ctx->acc_zeroed = ctx->acc_zeroed && !ctx->recompute;
   ctx->sized_sig = sig;
   ctx->have_fwd = true;
   return DSM_OK;
@@ -980,14 +1032,12 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     DSM_CHECK(cv.gcolor.ensure(px * sizeof(float4)));
     DSM_CHECK(cv.pgrad.ensure(px * 2 * sizeof(float4)));
   }
-  DSM_CHECK(ctx->gnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
+  dsm_status sa = ensure_backward_accumulators(ctx);
+  if (sa != DSM_OK) return sa;
   DSM_CHECK(ctx->gN.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->gface.ensure(sizeof(float) * 3 * std::max(T, 1)));
-  DSM_CHECK(ctx->gQ.ensure(sizeof(double) * 20 * kMaxLightViews));
-  DSM_CHECK(ctx->gdirect.ensure(sizeof(double) * 3 * kMaxLightViews));
   const int n_mat_red = mesh.n_materials <= kMaxSharedMat ? mesh.n_materials : 0;
-  const int red_stride = 23 * L + 3 * n_mat_red;
-  DSM_CHECK(ctx->red.ensure(sizeof(double) * kRedSlots * std::max(red_stride, 1)));
+  const int red_stride = red_stride_of(ctx);
   for (int l = 0; l < L; ++l) {
     const size_t R2 = (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2);
     DSM_CHECK(ctx->light[l].gm.ensure(R2));
@@ -998,25 +1048,35 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     cl.add(v.gclip.p, sizeof(float4) * V);
     cl.add(v.big_acc.p, (size_t)kMaxBig * kBigSlots * (view_is_light(ctx, w) ? kBigStrideSm : kBigStrideCam) * 4);
   };
-  // ---- clear accumulators and outputs
+  // ---- clear accumulators and outputs.  After a stored forward the internal
+  // accumulators are already zero and only the caller's outputs are cleared,
+  // on a side stream beside the final antialiasing adjoint (the first writer
+  // of dL/dalbedo is the shading adjoint, which waits for it).
+  const bool side = ctx->acc_zeroed && ctx->gm_zeroed && !ctx->prof;
+  ctx->aux_pending = false;
+  DSM_CHECK(ensure_streams(ctx));
   {
     StageTimer t(ctx, ST_BWD_CLEAR, st);
     Clearer cl;
     cl.add(dL_dverts, sizeof(float) * 3 * V);
     if (ctx->n_user) cl.add(dL_dlight, sizeof(float) * 6 * ctx->n_user);
     cl.add(dL_dalbedo, sizeof(float) * 3 * mesh.n_materials);
-    cl.add(ctx->gnormal.p, sizeof(float) * 3 * V);
-    cl.add(ctx->gQ.p, sizeof(double) * 20 * kMaxLightViews);
-    cl.add(ctx->gdirect.p, sizeof(double) * 3 * kMaxLightViews);
-    cl.add(ctx->red.p, sizeof(double) * kRedSlots * red_stride);
+    if (!ctx->acc_zeroed) add_backward_accumulators(ctx, cl);
     if (!ctx->gm_zeroed)
       for (int l = 0; l < L; ++l)
         cl.add(ctx->light[l].gm.p, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2));
     ctx->gm_zeroed = false;   // this backward accumulates into them
-    if (!ctx->recompute)
-      for (int w = 0; w < NV; ++w) clear_view(cl, w);
+    ctx->acc_zeroed = false;
     static_assert(7 + kMaxLightViews + 2 * kMaxViews <= kMaxClear, "clear list");
-    cl.launch(st);
+    if (side) {
+      DSM_CHECK(cudaEventRecord(ctx->ev_aux, st));
+      DSM_CHECK(cudaStreamWaitEvent(ctx->aux, ctx->ev_aux, 0));
+      cl.launch(ctx->aux);
+      DSM_CHECK(cudaEventRecord(ctx->ev_aux_done, ctx->aux));
+      ctx->aux_pending = true;
+    } else {
+      cl.launch(st);
+    }
   }
   DSM_CHECK(cudaGetLastError());
 
@@ -1100,10 +1160,14 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
   // adds the light views' share), then the lights' parameters
   {
     StageTimer t(ctx, ST_BWD_VERTEX, st);
-    launch_red_reduce(ctx->red.as<double>(), red_stride, L, n_mat_red, ctx->gQ.as<double>(), ctx->gdirect.as<double>(),
-                      dL_dalbedo, st);
-    launch_light_grad(ctx->lights_dev.as<LightDev>(), L, ctx->n_user, ctx->gQ.as<double>(), ctx->gdirect.as<double>(),
-                      dL_dlight, st);
+    launch_light_sums(ctx->red.as<double>(), red_stride, L, n_mat_red, ctx->lights_dev.as<LightDev>(), ctx->n_user,
+                      ctx->gQ.as<double>(), ctx->gdirect.as<double>(), dL_dalbedo, dL_dlight, st);
+  }
+  if (ctx->aux_pending) {
+    // the side stream's clear has been waited for by every shading adjoint;
+    // join it to st as well so that the call's work ends on st
+    DSM_CHECK(cudaStreamWaitEvent(st, ctx->ev_aux_done, 0));
+    ctx->aux_pending = false;
   }
   DSM_CHECK(cudaGetLastError());
   return DSM_OK;

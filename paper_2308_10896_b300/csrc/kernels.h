@@ -247,10 +247,8 @@ void launch_vertex_backward(const float* verts, int V, const float* viewM, int n
                             const VertGradPtrs& gp, float* dverts, double* red, int red_stride, cudaStream_t st);
 void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const int* big_tri,
                               const DevStatus* status, int view, cudaStream_t st);
-void launch_red_reduce(const double* red, int red_stride, int L, int n_mat_red, double* gQ, double* gdirect,
-                       float* dalbedo, cudaStream_t st);
-void launch_light_grad(const LightDev* lights, int L, int n_user, const double* gQ, const double* gdirect,
-                       float* dlight, cudaStream_t st);
+void launch_light_sums(const double* red, int red_stride, int L, int n_mat_red, const LightDev* lights, int n_user,
+                       double* gQ, double* gdirect, float* dalbedo, float* dlight, cudaStream_t st);
 void launch_l2(const float* img, const float* tgt, int64_t n, float* loss, float* grad, cudaStream_t st);
 
 }  // namespace dsm

@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
         gn.x += glam * om.x; gn.y += glam * om.y; gn.z += glam * om.z;
         const float3 gom = make_float3(glam * s.n.x, glam * s.n.y, glam * s.n.z);
         if (Ld.type == 0) {
-          gdir = gom;                    // dL/d omega with omega = -fwd (chained in light_grad_kernel)
+          gdir = gom;                    // dL/d omega with omega = -fwd (chained in light_sums_kernel)
         } else {
           const float d = om.x * gom.x + om.y * gom.y + om.z * gom.z;
           const float il = 1.f / len;
@@ -642,20 +642,6 @@ __global__ void shade_big_resolve_kernel(ShadeArgs a, ShadeGradArgs g, const int
   }
 }
 
-// Sum of the kRedSlots copies (float64): dQ and the direct light terms
-// (overwritten) and the albedo gradient (added).
-__global__ void red_reduce_kernel(const double* __restrict__ red, int stride, int L, int n_mat_red,
-                                  double* __restrict__ gQ, double* __restrict__ gdirect,
-                                  float* __restrict__ dalbedo) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= L * 23 + n_mat_red * 3) return;
-  double acc = 0.0;
-  for (int q = 0; q < kRedSlots; ++q) acc += red[(size_t)q * stride + k];
-  if (k < L * 20) gQ[k] = acc;
-  else if (k < L * 23) gdirect[k - L * 20] = acc;
-  else dalbedo[k - L * 23] += (float)acc;
-}
-
 // ------------------------------------------------------------------ per-vertex gathers
 // dL/dv += M^T dL/dclip for every view (+ depth row for lights);
 // dL/dQ_l += dL/dclip (x) [v, 1] and dL/dd (x) [v, 1].
@@ -703,32 +689,61 @@ __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __res
     if (sQ[k] != 0.f) atomicAdd(&dst[k], (double)sQ[k]);
 }
 
-// dL/d(pos, dir) of the caller's light u = sum over its views of J^T dL/dQ
-// plus the direct terms of the shading direction omega: directional
-// omega = -dir / |dir|, spot and point omega = normalize(pos - x).  A point
-// light sums its six cube faces (their J has no direction columns).
-__global__ void light_grad_kernel(const LightDev* __restrict__ lights, int L, int n_user,
-                                  const double* __restrict__ gQ, const double* __restrict__ gdirect,
-                                  float* __restrict__ dlight) {
-  const int u = blockIdx.x;
-  const int j = threadIdx.x;
-  if (u >= n_user || j >= 6) return;
-  double acc = 0.0;   // a few float64 operations per light: keeps the cancellation of J^T dL/dQ
-  for (int l = 0; l < L; ++l) {
-    const LightDev& Ld = lights[l];
-    if (Ld.user != u) continue;
-    for (int k = 0; k < 20; ++k) acc += gQ[l * 20 + k] * (double)Ld.J[k * 6 + j];
-    const double* gd = gdirect + 3 * l;
-    if (Ld.type == 1) {
-      if (j < 3) acc += gd[j];
-    } else if (j >= 3) {
-      const int c = j - 3;
-      const float* f = Ld.fwd;
-      const double fg = f[0] * gd[0] + f[1] * gd[1] + f[2] * gd[2];
-      acc += -(gd[c] - f[c] * fg) / Ld.dir_norm;
+// One block of 1024 threads, the end of the backward: the kRedSlots float64
+// copies of the light-matrix gradient, the direct light terms and the albedo
+// block sums reduced (four threads per entry, 16 slots each, then two
+// shuffles; dQ and the direct terms overwritten, the albedo added), then
+// dL/d(pos, dir) of every caller light u (one warp per output): the sum over
+// its views of J^T dL/dQ plus the direct terms of the shading direction omega
+// (directional omega = -dir / |dir|, spot and point omega = normalize(pos - x)).
+// A point light sums its six cube faces (their J has no direction columns).
+// float64 keeps the cancellation of both sums; the work is spread over the
+// threads because every float64 operation has a long latency.
+__global__ void __launch_bounds__(1024) light_sums_kernel(const double* __restrict__ red, int stride, int L,
+                                                          int n_mat_red, const LightDev* __restrict__ lights,
+                                                          int n_user, double* __restrict__ gQ,
+                                                          double* __restrict__ gdirect, float* __restrict__ dalbedo,
+                                                          float* __restrict__ dlight) {
+  static_assert(kRedSlots % 4 == 0, "four threads per entry");
+  const int n = L * 23 + n_mat_red * 3;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int base = 0; base < 4 * n; base += blockDim.x) {
+    const int e = base + threadIdx.x, k = e >> 2, part = e & 3;
+    double acc = 0.0;
+    if (k < n)
+      for (int q = part; q < kRedSlots; q += 4) acc += red[(size_t)q * stride + k];
+    acc += __shfl_xor_sync(kFull, acc, 1);
+    acc += __shfl_xor_sync(kFull, acc, 2);
+    if (k < n && part == 0) {
+      if (k < L * 20) gQ[k] = acc;
+      else if (k < L * 23) gdirect[k - L * 20] = acc;
+      else dalbedo[k - L * 23] += (float)acc;
     }
   }
-  dlight[u * 6 + j] = (float)acc;
+  __syncthreads();   // this block's writes of gQ and gdirect are visible to all its threads
+  for (int o = warp; o < n_user * 6; o += nwarps) {
+    const int u = o / 6, j = o - 6 * u;
+    double acc = 0.0;
+    for (int l = 0; l < L; ++l) {
+      const LightDev& Ld = lights[l];
+      if (Ld.user != u) continue;
+      if (lane < 20) acc += gQ[l * 20 + lane] * (double)Ld.J[lane * 6 + j];
+      if (lane == 20) {
+        const double* gd = gdirect + 3 * l;
+        if (Ld.type == 1) {
+          if (j < 3) acc += gd[j];
+        } else if (j >= 3) {
+          const int c = j - 3;
+          const float* f = Ld.fwd;
+          const double fg = f[0] * gd[0] + f[1] * gd[1] + f[2] * gd[2];
+          acc += -(gd[c] - f[c] * fg) / Ld.dir_norm;
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 16; m; m >>= 1) acc += __shfl_xor_sync(kFull, acc, m);
+    if (lane == 0) dlight[u * 6 + j] = (float)acc;
+  }
 }
 
 __global__ void l2_kernel(const float* __restrict__ img, const float* __restrict__ tgt, int64_t n,
@@ -807,19 +822,11 @@ void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const 
   shade_big_resolve_kernel<<<kMaxBig, 32, 0, st>>>(a, g, big_tri, status, view);
 }
 
-void launch_red_reduce(const double* red, int red_stride, int L, int n_mat_red, double* gQ, double* gdirect,
-                       float* dalbedo, cudaStream_t st) {
-  const int n = L * 23 + n_mat_red * 3;
-  if (n == 0) return;
+void launch_light_sums(const double* red, int red_stride, int L, int n_mat_red, const LightDev* lights, int n_user,
+                       double* gQ, double* gdirect, float* dalbedo, float* dlight, cudaStream_t st) {
+  if (L * 23 + n_mat_red * 3 == 0 && n_user == 0) return;
   count_launches(1);
-  red_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(red, red_stride, L, n_mat_red, gQ, gdirect, dalbedo);
-}
-
-void launch_light_grad(const LightDev* lights, int L, int n_user, const double* gQ, const double* gdirect,
-                       float* dlight, cudaStream_t st) {
-  if (n_user == 0) return;
-  count_launches(1);
-  light_grad_kernel<<<n_user, 32, 0, st>>>(lights, L, n_user, gQ, gdirect, dlight);
+  light_sums_kernel<<<1, 1024, 0, st>>>(red, red_stride, L, n_mat_red, lights, n_user, gQ, gdirect, dalbedo, dlight);
 }
 
 void launch_l2(const float* img, const float* tgt, int64_t n, float* loss, float* grad, cudaStream_t st) {
