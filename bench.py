@@ -78,9 +78,11 @@ def stage_bytes(sc, listed=None) -> dict:
     listed = list(listed) if listed is not None else [0] * views
     sm_listed, cam_listed = sum(listed[:L]), listed[L] if len(listed) > L else 0
     return {
-        # transform (12 V in, 32 V out, +4 V depth) and triangle setup (12 T in, 64 T + 2 T out), binning count
-        "setup": views * (12 * V + 32 * V + 12 * T + 66 * T + 64 * T) + L * 4 * V,
-        "bin_fill": views * (64 * T + 4 * T),
+        # transform (12 V in, 32 V out, +4 V depth) and triangle setup (12 T in, 64 T + 2 T out) with the
+        # binning's count pass (4 T big-triangle index out)
+        "setup": views * (12 * V + 32 * V + 12 * T + 66 * T + 4 * T) + L * 4 * V,
+        # fill: the record's flags and bbox words and the big-triangle index in, one list entry per triangle out
+        "bin_fill": views * (12 * T + 4 * T + 4 * T),
         # setup records and lists read once, one 16-byte G-buffer texel written per pixel, and per light
         # texel the depth sample (f, f^2), 8 bytes
         "raster": views * (64 * T + 4 * T) + 16 * (texels + WH) + 8 * texels,
@@ -874,9 +876,9 @@ def run_profile_step(args):
 
 # Kernel name -> profiler stage (the stage whose CUDA events bracket it).
 KERNEL_STAGES = [
-    (r"light_setup_kernel|set_cameras_kernel|transform_all_kernel|tri_setup_all_kernel|silhouette_all_kernel|"
-     r"vertex_normals_kernel|bin_kernel<0>|alloc_kernel", "setup"),
-    (r"bin_kernel<1>|units_kernel", "bin_fill"),
+    (r"light_setup_kernel|transform_all_kernel|setup_bin_kernel|silhouette_all_kernel|"
+     r"vertex_normals_kernel|alloc_units_kernel", "setup"),
+    (r"bin_fill_kernel", "bin_fill"),
     (r"raster_kernel<", "raster"),
     (r"aa_detect_kernel|aa_forward_list_kernel<float2>", "sm_antialias"),
     (r"filter_tma_kernel<\d+, 0>|filter_tile_kernel<\d+, 0>|filter_pass_kernel<(true|false), false>|compose_kernel",

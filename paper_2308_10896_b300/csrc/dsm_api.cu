@@ -85,7 +85,7 @@ struct dsm_ctx {
   Buf adj, vf_off, vf_list;
   ViewBufs view[kMaxViews];
   LightBufs light[kMaxLightViews];
-  Buf lights_dev, viewM, viewMlo, status, vnormal, vnlen, gnormal, gN, gface, gQ, gdirect, red;
+  Buf lights_dev, viewM, viewMlo, status, vnormal, vnlen, gnormal, gpos, gN, gface, gQ, gdirect, red;
   Buf scratch_dverts, scratch_dlight, scratch_dalbedo, filter_tmp, stats;
   DevStatus* hstatus = nullptr;
   // state of the last forward
@@ -145,11 +145,6 @@ dsm_status cuda_fail(dsm_ctx* c, cudaError_t e, const char* where) {
     cudaError_t e__ = (call);                                   \
     if (e__ != cudaSuccess) return cuda_fail(ctx, e__, #call);  \
   } while (0)
-
-// Camera matrices, 20 floats each (the clip matrix, then an unused depth row).
-struct CamMats {
-  float v[20 * DSM_MAX_CAMERAS];
-};
 
 // One launch that zeroes several buffers: segment blockIdx.y, 16-byte stores
 // over its aligned body, 4-byte stores for an unaligned head and the tail.
@@ -336,8 +331,8 @@ void dsm_destroy(dsm_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
   Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->viewMlo, &ctx->status,
-                 &ctx->vnormal, &ctx->vnlen, &ctx->gnormal, &ctx->gN, &ctx->gface, &ctx->gQ, &ctx->gdirect,
-                 &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo, &ctx->filter_tmp, &ctx->red};
+                 &ctx->vnormal, &ctx->vnlen, &ctx->gnormal, &ctx->gpos, &ctx->gN, &ctx->gface, &ctx->gQ, &ctx->gdirect,
+                 &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo, &ctx->filter_tmp, &ctx->red, &ctx->stats};
   for (Buf* b : bufs) b->release();
   for (auto& v : ctx->view) {
     Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
@@ -565,6 +560,7 @@ AAArgs aa_args(const dsm_ctx* ctx, ViewBufs& v) {
 ViewSetupArgs view_setup_args(dsm_ctx* ctx, int w0, int n) {
   ViewSetupArgs va{};
   va.n = n;
+  va.view0 = w0;
   for (int k = 0; k < n; ++k) {
     const int w = w0 + k;
     ViewBufs& v = vbuf(ctx, w);
@@ -578,6 +574,10 @@ ViewSetupArgs view_setup_args(dsm_ctx* ctx, int w0, int n) {
     va.sil[k] = v.sil.as<uint8_t>();
     va.count[k] = v.count.as<int>();
     va.aa_count[k] = v.aa_ctr.as<int>();
+    va.tilesX[k] = v.tilesX;
+    va.bs[k] = v.bs;
+    va.big_index[k] = v.big_index.as<int>();
+    va.big_tri[k] = v.big_tri.as<int>();
   }
   return va;
 }
@@ -593,14 +593,30 @@ void silhouette_views(dsm_ctx* ctx, int w0, int n, cudaStream_t st) {
   launch_silhouettes_all(ctx->adj.as<int>(), ctx->mesh.n_tris, view_setup_args(ctx, w0, n), st);
 }
 
-void bin_count_view(dsm_ctx* ctx, int w, cudaStream_t st) {
+// List segments of view w's tiles; with `write`, also its big triangles' list
+// entries and the raster work units.
+void alloc_view(dsm_ctx* ctx, int w, bool write, cudaStream_t st) {
   ViewBufs& v = vbuf(ctx, w);
-  DevStatus* ds = ctx->status.as<DevStatus>();
   StageTimer t(ctx, ST_SETUP, st);
-  launch_bin_count(v.setup.as<TriSetup>(), ctx->mesh.n_tris, v.tilesX, v.bs, v.count.as<int>(), ds, w,
-                   v.big_index.as<int>(), v.big_tri.as<int>(), st);
-  launch_scan(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), ds, w, v.setup.as<TriSetup>(),
-              v.big_tri.as<int>(), v.tilesX, v.bs.tile_log2, st);
+  launch_alloc_units(v.count.as<int>(), v.tilesX * v.tilesY, v.offset.as<int>(), ctx->status.as<DevStatus>(), w,
+                     v.setup.as<TriSetup>(), v.big_tri.as<int>(), v.tilesX, v.bs.tile_log2, v.list.as<int>(),
+                     v.list_cap, v.raster_units(), write, st);
+}
+
+// First frame of a scene size: the list capacities from the segments' totals
+// (one host read), then the segments again with the list entries and units.
+// The views' streams have been joined into st.
+dsm_status size_lists(dsm_ctx* ctx, int w0, int n, cudaStream_t st) {
+  DSM_CHECK(cudaMemcpyAsync(ctx->hstatus, ctx->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  DSM_CHECK(cudaStreamSynchronize(st));
+  DevStatus* ds = ctx->status.as<DevStatus>();
+  for (int w = w0; w < w0 + n; ++w) {
+    dsm_status s = grow_list(ctx, vbuf(ctx, w), ctx->hstatus->needed_pairs[w]);
+    if (s != DSM_OK) return s;
+    DSM_CHECK(cudaMemsetAsync(&ds->needed_pairs[w], 0, sizeof(int), st));
+    alloc_view(ctx, w, true, st);
+  }
+  return DSM_OK;
 }
 
 // Bin fill and raster of view w (a light view also writes f, f^2).
@@ -611,9 +627,7 @@ void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
   {
     StageTimer t(ctx, ST_BIN_FILL, st);
     launch_bin_fill(v.setup.as<TriSetup>(), ctx->mesh.n_tris, v.tilesX, v.bs, v.count.as<int>(), v.offset.as<int>(),
-                    v.list.as<int>(), v.list_cap, ds, w, v.big_index.as<int>(), v.big_tri.as<int>(), st);
-    launch_units(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,
-                 v.bs.tile_log2, v.raster_units(), ds, w, v.big_tri.as<int>(), v.count.as<int>(), st);
+                    v.list.as<int>(), v.list_cap, ds, v.big_index.as<int>(), st);
   }
   StageTimer t(ctx, ST_RASTER, st);
   launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,
@@ -662,12 +676,12 @@ ShadeArgs shade_args(dsm_ctx* ctx, int c) {
   return sa;
 }
 
-ShadeGradArgs grad_args(dsm_ctx* ctx, int c, float* dverts, float* dalbedo, int red_stride) {
+ShadeGradArgs grad_args(dsm_ctx* ctx, int c, float* dalbedo, int red_stride) {
   ViewBufs& cv = vbuf(ctx, ctx->L + c);
   ShadeGradArgs ga{};
   ga.gcolor = cv.gcolor.as<float4>();
-  ga.dverts = dverts;
-  ga.gnormal = ctx->gnormal.as<float>();
+  ga.gpos = ctx->gpos.as<float4>();
+  ga.gnormal = ctx->gnormal.as<float4>();
   ga.gclip = cv.gclip.as<float4>();
   ga.dalbedo = dalbedo;
   for (int l = 0; l < ctx->L; ++l) ga.gm[l] = ctx->light[l].gm.as<float2>();
@@ -700,7 +714,7 @@ dsm_status camera_colour(dsm_ctx* ctx, int c, float* image, cudaStream_t st) {
 
 // Camera c, backward: final antialiasing adjoint, then the shading adjoint
 // (dL/dm into every light's gm, per-pixel gradients for the scatter).
-dsm_status camera_backward(dsm_ctx* ctx, int c, const float* gimage, float* dverts, float* dalbedo, int red_stride,
+dsm_status camera_backward(dsm_ctx* ctx, int c, const float* gimage, float* dalbedo, int red_stride,
                            cudaStream_t st) {
   ViewBufs& cv = vbuf(ctx, ctx->L + c);
   {
@@ -715,15 +729,15 @@ dsm_status camera_backward(dsm_ctx* ctx, int c, const float* gimage, float* dver
   }
   if (ctx->aux_pending) DSM_CHECK(cudaStreamWaitEvent(st, ctx->ev_aux_done, 0));   // outputs cleared
   StageTimer t(ctx, ST_BWD_SHADE, st);
-  launch_shade_backward(shade_args(ctx, c), grad_args(ctx, c, dverts, dalbedo, red_stride), st);
+  launch_shade_backward(shade_args(ctx, c), grad_args(ctx, c, dalbedo, red_stride), st);
   return DSM_OK;
 }
 
 // Camera c, backward: the per-pixel gradients scattered to the triangle corners.
-void camera_scatter(dsm_ctx* ctx, int c, float* dverts, float* dalbedo, int red_stride, cudaStream_t st) {
+void camera_scatter(dsm_ctx* ctx, int c, float* dalbedo, int red_stride, cudaStream_t st) {
   StageTimer t(ctx, ST_BWD_SHADE_SCATTER, st);
   const ShadeArgs sa = shade_args(ctx, c);
-  const ShadeGradArgs ga = grad_args(ctx, c, dverts, dalbedo, red_stride);
+  const ShadeGradArgs ga = grad_args(ctx, c, dalbedo, red_stride);
   launch_shade_scatter(sa, ga, st);
   launch_shade_big_resolve(sa, ga, vbuf(ctx, ctx->L + c).big_tri.as<int>(), ctx->status.as<DevStatus>(), ctx->L + c,
                            st);
@@ -776,11 +790,9 @@ dsm_status rebuild_view(dsm_ctx* ctx, int w, bool sizing, bool maps, bool detect
     StageTimer t(ctx, ST_SETUP, st);
     setup_views(ctx, w, 1, st);
   }
-  bin_count_view(ctx, w, st);
+  alloc_view(ctx, w, !sizing, st);
   if (sizing) {
-    DSM_CHECK(cudaMemcpyAsync(ctx->hstatus, ctx->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-    DSM_CHECK(cudaStreamSynchronize(st));
-    s = grow_list(ctx, vbuf(ctx, w), ctx->hstatus->needed_pairs[w]);
+    s = size_lists(ctx, w, 1, st);
     if (s != DSM_OK) return s;
   }
   raster_view(ctx, w, st);
@@ -794,16 +806,18 @@ dsm_status rebuild_view(dsm_ctx* ctx, int w, bool sizing, bool maps, bool detect
   return DSM_OK;
 }
 
-// The backward's internal accumulators (vertex-normal gradient, light-matrix
-// block sums, and per view the clip gradients and big-triangle slots), sized
-// for the current frame.
+// The backward's internal accumulators (the cameras' vertex-normal and
+// vertex-position gradients as float4 per vertex, so that the scatter adds each
+// with one 16-byte atomic; light-matrix block sums; and per view the clip
+// gradients and big-triangle slots), sized for the current frame.
 int red_stride_of(const dsm_ctx* ctx) {
   const int n_mat_red = ctx->mesh.n_materials <= kMaxSharedMat ? ctx->mesh.n_materials : 0;
   return 23 * ctx->L + 3 * n_mat_red;
 }
 dsm_status ensure_backward_accumulators(dsm_ctx* ctx) {
   const int V = ctx->mesh.n_verts;
-  DSM_CHECK(ctx->gnormal.ensure(sizeof(float) * 3 * std::max(V, 1)));
+  DSM_CHECK(ctx->gnormal.ensure(sizeof(float4) * std::max(V, 1)));
+  DSM_CHECK(ctx->gpos.ensure(sizeof(float4) * std::max(V, 1)));
   DSM_CHECK(ctx->gQ.ensure(sizeof(double) * 20 * kMaxLightViews));
   DSM_CHECK(ctx->gdirect.ensure(sizeof(double) * 3 * kMaxLightViews));
   DSM_CHECK(ctx->red.ensure(sizeof(double) * kRedSlots * std::max(red_stride_of(ctx), 1)));
@@ -811,7 +825,8 @@ dsm_status ensure_backward_accumulators(dsm_ctx* ctx) {
 }
 void add_backward_accumulators(dsm_ctx* ctx, Clearer& cl) {
   const int V = ctx->mesh.n_verts;
-  cl.add(ctx->gnormal.p, sizeof(float) * 3 * V);
+  cl.add(ctx->gnormal.p, sizeof(float4) * V);
+  cl.add(ctx->gpos.p, sizeof(float4) * V);
   cl.add(ctx->gQ.p, sizeof(double) * 20 * kMaxLightViews);
   cl.add(ctx->gdirect.p, sizeof(double) * 3 * kMaxLightViews);
   cl.add(ctx->red.p, sizeof(double) * kRedSlots * red_stride_of(ctx));
@@ -821,12 +836,6 @@ void add_backward_accumulators(dsm_ctx* ctx, Clearer& cl) {
       cl.add(v.gclip.p, sizeof(float4) * V);
       cl.add(v.big_acc.p, (size_t)kMaxBig * kBigSlots * (view_is_light(ctx, w) ? kBigStrideSm : kBigStrideCam) * 4);
     }
-}
-
-__global__ void set_cameras_kernel(CamMats m, int n, float* dst, float* dst_lo) {
-  for (int k = threadIdx.x; k < 20 * n; k += blockDim.x) dst[k] = m.v[k];
-  // a camera's float32 matrix is exact: no residual (the slot may have held a light view's)
-  for (int k = threadIdx.x; k < 16 * n; k += blockDim.x) dst_lo[k] = 0.f;
 }
 
 }  // namespace
@@ -906,12 +915,10 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
   }
   float* viewM = ctx->viewM.as<float>();
   StageTimer t_setup(ctx, ST_SETUP, st);
-  if (L > 0) launch_light_setup(light_params, la, ctx->lights_dev.as<LightDev>(), viewM, ctx->viewMlo.as<float>(), st);
   CamMats cm{};
   for (int c = 0; c < C; ++c)
     for (int k = 0; k < 16; ++k) cm.v[20 * c + k] = cams[c].clip[k];
-  count_launches(1);
-  set_cameras_kernel<<<1, 64, 0, st>>>(cm, C, viewM + 20 * L, ctx->viewMlo.as<float>() + 16 * L);
+  launch_light_setup(light_params, la, ctx->lights_dev.as<LightDev>(), viewM, ctx->viewMlo.as<float>(), cm, C, st);
 
   if (ctx->recompute) {
     // ---- one view at a time through the shared buffer sets
@@ -927,11 +934,12 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
       }
     }
   } else {
-    // every view at once: transform, triangle setup (the silhouettes follow
-    // beside the binning: only the antialiasing reads them)
+    // every view at once: transform, triangle setup with the binning's count
+    // pass (the silhouettes follow beside the segments: only the antialiasing
+    // reads them)
     setup_views(ctx, 0, NV, st, false);
     t_setup.stop();
-    // ---- per view on its own stream: bin count, scan (the views are independent until shading)
+    // ---- per view on its own stream: list segments and work units (the views are independent until shading)
     DSM_CHECK(ensure_streams(ctx));
     DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, 0, NV));
     {
@@ -940,7 +948,7 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
       launch_vertex_normals(mesh->verts, V, mesh->tris, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
                             ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), cst);
     }
-    for (int w = 0; w < NV; ++w) bin_count_view(ctx, w, view_stream(ctx, w, st));
+    for (int w = 0; w < NV; ++w) alloc_view(ctx, w, !sizing, view_stream(ctx, w, st));
     {
       StageTimer ts(ctx, ST_SETUP, st);
       silhouette_views(ctx, 0, NV, st);
@@ -950,12 +958,8 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
     if (sizing) {
       // first frame of this scene size: read the pair counts once and size the lists
       DSM_CHECK(join_views(ctx, st, 0, NV));
-      DSM_CHECK(cudaMemcpyAsync(ctx->hstatus, ctx->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-      DSM_CHECK(cudaStreamSynchronize(st));
-      for (int w = 0; w < NV; ++w) {
-        s = grow_list(ctx, ctx->view[w], ctx->hstatus->needed_pairs[w]);
-        if (s != DSM_OK) return s;
-      }
+      s = size_lists(ctx, 0, NV, st);
+      if (s != DSM_OK) return s;
       DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, 0, NV));
     }
     // ---- per view: bin fill, raster; per light: Alg. 1 (f, f^2 -> antialias -> filter)
@@ -1067,7 +1071,7 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
         cl.add(ctx->light[l].gm.p, (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2));
     ctx->gm_zeroed = false;   // this backward accumulates into them
     ctx->acc_zeroed = false;
-    static_assert(7 + kMaxLightViews + 2 * kMaxViews <= kMaxClear, "clear list");
+    static_assert(8 + kMaxLightViews + 2 * kMaxViews <= kMaxClear, "clear list");
     if (side) {
       DSM_CHECK(cudaEventRecord(ctx->ev_aux, st));
       DSM_CHECK(cudaStreamWaitEvent(ctx->aux, ctx->ev_aux, 0));
@@ -1080,15 +1084,15 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
   }
   DSM_CHECK(cudaGetLastError());
 
-  // ---- normals: dL/dn of the cameras' pixels onto the vertices.  Its inputs
-  // come from the cameras' adjoints; it adds to dverts with plain
-  // read-modify-writes, so it runs on st after the camera scatters and before
-  // the vertex gather.
+  // ---- normals: dL/dn of the cameras' pixels onto the vertices, with the
+  // cameras' position gradients.  Its inputs come from the cameras' adjoints;
+  // it adds to dverts with plain read-modify-writes, so it runs on st after
+  // the camera scatters and before the vertex gather.
   auto normals = [&]() {
     StageTimer t(ctx, ST_BWD_VERTEX, st);
     launch_normals_backward(mesh.verts, V, mesh.tris, T, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
-                            ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), ctx->gnormal.as<float>(),
-                            ctx->gN.as<float>(), ctx->gface.as<float>(), dL_dverts, st);
+                            ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), ctx->gnormal.as<float4>(),
+                            ctx->gpos.as<float4>(), ctx->gN.as<float>(), ctx->gface.as<float>(), dL_dverts, st);
   };
   if (ctx->recompute) {
     // ---- the filtered moment maps again (every camera's shading adjoint reads all of them)
@@ -1111,9 +1115,9 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
         clear_view(cl, L + c);
         cl.launch(st);
       }
-      s = camera_backward(ctx, c, dL_dimages[c], dL_dverts, dL_dalbedo, red_stride, st);
+      s = camera_backward(ctx, c, dL_dimages[c], dL_dalbedo, red_stride, st);
       if (s != DSM_OK) return s;
-      camera_scatter(ctx, c, dL_dverts, dL_dalbedo, red_stride, st);
+      camera_scatter(ctx, c, dL_dalbedo, red_stride, st);
       StageTimer t(ctx, ST_BWD_VERTEX, st);
       vertex_backward_views(ctx, L + c, 1, dL_dverts, red_stride, st);
     }
@@ -1139,7 +1143,7 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     DSM_CHECK(ensure_streams(ctx));
     if (C > 1) DSM_CHECK(fork_views(ctx, st, ctx->ev_bfork, L, NV));
     for (int c = 0; c < C; ++c) {
-      dsm_status s = camera_backward(ctx, c, dL_dimages[c], dL_dverts, dL_dalbedo, red_stride,
+      dsm_status s = camera_backward(ctx, c, dL_dimages[c], dL_dalbedo, red_stride,
                                      C > 1 ? view_stream(ctx, L + c, st) : st);
       if (s != DSM_OK) return s;
     }
@@ -1149,7 +1153,7 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     DSM_CHECK(fork_views(ctx, st, ctx->ev_bfork, 0, L));
     for (int l = 0; l < L; ++l) light_backward(ctx, l, view_stream(ctx, l, st));
     for (int c = 0; c < C; ++c)
-      camera_scatter(ctx, c, dL_dverts, dL_dalbedo, red_stride, C > 1 ? view_stream(ctx, L + c, st) : st);
+      camera_scatter(ctx, c, dL_dalbedo, red_stride, C > 1 ? view_stream(ctx, L + c, st) : st);
     if (C > 1) DSM_CHECK(join_views(ctx, st, L, NV));
     normals();   // beside the light views' adjoints
     DSM_CHECK(join_views(ctx, st, 0, L));
@@ -1438,7 +1442,7 @@ uint64_t dsm_memory_bytes(dsm_ctx* ctx) {
   if (!ctx) return 0;
   uint64_t n = 0;
   const Buf* bufs[] = {&ctx->adj, &ctx->vf_off, &ctx->vf_list, &ctx->lights_dev, &ctx->viewM, &ctx->viewMlo, &ctx->status,
-                       &ctx->vnormal, &ctx->vnlen, &ctx->gnormal, &ctx->gN, &ctx->gface, &ctx->gQ, &ctx->gdirect,
+                       &ctx->vnormal, &ctx->vnlen, &ctx->gnormal, &ctx->gpos, &ctx->gN, &ctx->gface, &ctx->gQ, &ctx->gdirect,
                        &ctx->scratch_dverts, &ctx->scratch_dlight, &ctx->scratch_dalbedo, &ctx->filter_tmp,
                        &ctx->red, &ctx->stats};
   for (const Buf* b : bufs) n += b->cap;

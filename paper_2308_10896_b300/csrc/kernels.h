@@ -32,6 +32,11 @@ struct LightSetupArgs {
   int n;
 };
 
+// Camera matrices, 20 floats each (the clip matrix, then an unused depth row).
+struct CamMats {
+  float v[20 * DSM_MAX_CAMERAS];
+};
+
 // Filter weights and the clamp-boundary fold coefficients of the adjoint.
 struct FilterArgs {
   float w[65];             // taps w[k + r], |k| <= r
@@ -84,8 +89,8 @@ struct ShadeArgs {
 
 struct ShadeGradArgs {
   const float4* gcolor;               // dL/d colour before the final antialiasing
-  float* dverts;                      // V x 3
-  float* gnormal;                     // V x 3, dL/d unit vertex normal
+  float4* gpos;                       // V, dL/d vertex position through the camera's interpolation (xyz)
+  float4* gnormal;                    // V, dL/d unit vertex normal (xyz)
   float4* gclip;                      // V, dL/d camera clip
   float* dalbedo;                     // M x 3
   float2* gm[kMaxLightViews];         // dL/d(m1, m2) texel maps
@@ -129,6 +134,7 @@ struct AAArgs {
 // Per-view pointers and sizes for the fused setup of all views of a frame.
 struct ViewSetupArgs {
   int n;
+  int view0;                      // frame view index of entry 0 (the device status is indexed by frame view)
   int W[kMaxViews], H[kMaxViews], tiles[kMaxViews];
   float4* clip[kMaxViews];
   float4* scr[kMaxViews];         // float-float unsnapped screen positions (see transform_all_kernel)
@@ -137,21 +143,27 @@ struct ViewSetupArgs {
   TriSetup* setup[kMaxViews];
   int8_t* orient[kMaxViews];
   uint8_t* sil[kMaxViews];
-  int* count[kMaxViews];          // tile counters, zeroed by the setup
-  int* aa_count[kMaxViews];       // antialiasing work-list counters, zeroed by the setup
+  int* count[kMaxViews];          // tile counters, zeroed by the transform
+  int* aa_count[kMaxViews];       // antialiasing work-list counters, zeroed by the transform
+  int tilesX[kMaxViews];
+  BinShape bs[kMaxViews];
+  int* big_index[kMaxViews];      // per triangle: its index in big_tri, or -1
+  int* big_tri[kMaxViews];        // the view's big triangles (at most kMaxBig)
 };
-// Transform, triangle setup and (when `silhouettes`) silhouettes of every
-// view; also zeroes the tile counters and the big-triangle counts for the
-// binning that follows.  The silhouettes (needed only by the antialiasing) may
-// instead follow later through launch_silhouettes_all.
+// Transform and triangle setup of every view, with the binning's count pass
+// (per-tile counts of the ordinary triangles, the list of big ones) in the
+// setup kernel; the transform first zeroes the tile counters, the view
+// totals of the device status and the antialiasing work lists.  With
+// `silhouettes`, the silhouettes follow (needed only by the antialiasing,
+// they may instead follow later through launch_silhouettes_all).
 void launch_setup_all(const float* verts, int V, const int* tris, int T, const int* adj, const float* viewM,
                       const float* viewMlo,
                       const ViewSetupArgs& a, DevStatus* status, bool silhouettes, cudaStream_t st);
 void launch_silhouettes_all(const int* adj, int T, const ViewSetupArgs& a, cudaStream_t st);
+// The light views' matrices and derivatives (one CTA per light view) and the
+// C camera matrices after them.
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, float* viewMlo,
-                        cudaStream_t st);
-void launch_bin_count(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, DevStatus* status,
-                      int view, int* big_index, int* big_tri, cudaStream_t st);
+                        const CamMats& cams, int C, cudaStream_t st);
 // Raster work units of one view.  A tile's list is rastered kRasterBatch
 // records per unit (one CTA each); a tile of several units merges their
 // per-pixel minimum keys in a key slot (global 64-bit maxima of the inverted
@@ -166,13 +178,19 @@ struct RasterUnits {
   int* tile_done;              // units finished per tile (zero between frames)
   unsigned long long* skey;    // slot_cap x 1024 inverted keys (zero between frames)
 };
-// Segment of every tile in the view's triangle list (begin, end) from the
-// per-tile counts; clears the counts for the fill pass.
-void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, const TriSetup* setup,
-                 const int* big_tri, int tilesX, int tile_log2, cudaStream_t st);
+// Segment of every tile of one view in its triangle list (begin, end): the
+// count pass's ordinary triangles, then the big triangles that may cover the
+// tile.  With `write`, also appends those big triangles to the segments and
+// hands out the raster work units and key slots; without it (a first frame,
+// whose list capacity is sized from the segments' total first), only the
+// segments and their total.
+void launch_alloc_units(const int* count, int n, int* offset, DevStatus* status, int view, const TriSetup* setup,
+                        const int* big_tri, int tilesX, int tile_log2, int* list, int capacity,
+                        const RasterUnits& ru, bool write, cudaStream_t st);
+// Fill pass: the ordinary triangles into their tiles' segments, by taking
+// slots down from the count pass's per-tile counts (which end at zero).
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, const int* offset,
-                     int* list, int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
-                     cudaStream_t st);
+                     int* list, int capacity, DevStatus* status, const int* big_index, cudaStream_t st);
 // Raster work counts of one view into out[0..2] (added): tile-triangle pairs,
 // spans, pixel-centre coverage tests.
 void launch_raster_stats(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX,
@@ -183,12 +201,6 @@ void launch_raster(const TriSetup* setup, const int* offset, const int* list, in
                    int tile_log2, int W, int H, const float4* clip, const float4* scr, const int* tris,
                    float4* gbuf, const float* depth, float2* fmap, float ec, const RasterUnits& ru,
                    DevStatus* status, int view, cudaStream_t st);
-// After the fill pass (filled: its per-tile counts of ordinary triangles):
-// appends each tile's big triangles to its segment and hands out the raster
-// work units and key slots.
-void launch_units(const TriSetup* setup, const int* offset, int* list, int capacity, int tilesX, int tilesY,
-                  int tile_log2, const RasterUnits& ru, DevStatus* status, int view, const int* big_tri,
-                  const int* filled, cudaStream_t st);
 
 // shadow-map interpolation and antialiasing
 // Antialiasing (detection + list passes, see aa.cu).
@@ -235,9 +247,12 @@ void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, 
 // normals, shading, vertex gradients
 void launch_vertex_normals(const float* verts, int V, const int* tris, const int* vf_off, const int* vf_list,
                            float* vnormal, float* vlen, cudaStream_t st);
+// dL/dv of the cameras' interpolation: the unit vertex normals' gradient
+// gnormal through the normalisation and the area-weighted face normals, plus
+// the positions' gradient gpos, added to dverts.
 void launch_normals_backward(const float* verts, int V, const int* tris, int T, const int* vf_off,
-                             const int* vf_list, const float* vnormal, const float* vlen, const float* gnormal,
-                             float* gN, float* gface, float* dverts, cudaStream_t st);
+                             const int* vf_list, const float* vnormal, const float* vlen, const float4* gnormal,
+                             const float4* gpos, float* gN, float* gface, float* dverts, cudaStream_t st);
 void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st);
 void launch_shade_probe(const ShadeArgs& a, int l, float4* out, cudaStream_t st);
 void launch_sm_band_mask(const uint8_t* hflag, int n, float2* gft, float* gf, cudaStream_t st);

@@ -121,11 +121,17 @@ __device__ __forceinline__ float face_axis(int face, int k) {
 // fields; warp 1: lane j < 6 forms all of Q with float32 duals in direction
 // theta_j and writes column j of J.  A cube face takes the light's position
 // and the face axis as its direction (a constant: its J has no direction
-// columns).
+// columns).  The last CTA copies the C camera matrices after the light views'
+// (a camera's float32 matrix is exact: its residual rows are zero).
 __global__ void light_setup_kernel(const float* __restrict__ params, LightSetupArgs a, LightDev* out,
-                                   float* viewM, float* viewMlo) {
+                                   float* viewM, float* viewMlo, CamMats cams, int C) {
   const int l = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (l >= a.n) return;
+  if (l == a.n) {
+    for (int k = threadIdx.x; k < 20 * C; k += blockDim.x) viewM[20 * a.n + k] = cams.v[k];
+    for (int k = threadIdx.x; k < 16 * C; k += blockDim.x) viewMlo[16 * a.n + k] = 0.f;
+    return;
+  }
+  if (l > a.n) return;
   const LightConst& L = a.c[l];
   LightDev& o = out[l];
   const float* pl = params + L.user * 6;
@@ -188,8 +194,8 @@ __device__ __forceinline__ VertSnap snap_vertex(float c0, float c1, float c2, fl
 // Setup record of triangle t in one view from its snapped corners: bbox,
 // orientation-normalised top-left flags, float 2A; orient = sign of 2A (0:
 // culled).
-__device__ __forceinline__ void setup_triangle(int t, VertSnap s0, VertSnap s1, VertSnap s2, int W, int H,
-                                               TriSetup* __restrict__ out, int8_t* __restrict__ orient) {
+__device__ __forceinline__ TriSetup setup_triangle(int t, VertSnap s0, VertSnap s1, VertSnap s2, int W, int H,
+                                                   TriSetup* __restrict__ out, int8_t* __restrict__ orient) {
   long long area2 = (long long)(s1.X - s0.X) * (s2.Y - s0.Y) - (long long)(s1.Y - s0.Y) * (s2.X - s0.X);
   bool culled = !(s0.ok && s1.ok && s2.ok) || area2 == 0;
   int sg = area2 > 0 ? 1 : -1;
@@ -223,6 +229,7 @@ __device__ __forceinline__ void setup_triangle(int t, VertSnap s0, VertSnap s1, 
   r.jbox = (j0 & 0xffff) | (j1 << 16);
   r.flags = flags;
   *out = r;
+  return r;
 }
 
 
@@ -294,8 +301,19 @@ __device__ __forceinline__ float2 screen_ff(float xh, float xl, float wh, float 
 }
 
 __global__ void transform_all_kernel(const float* __restrict__ verts, int V, const float* __restrict__ viewM,
-                                     const float* __restrict__ viewMlo, ViewSetupArgs a) {
+                                     const float* __restrict__ viewMlo, ViewSetupArgs a, DevStatus* status) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  // the binning's tile counters, big-triangle counts and list and unit
+  // totals, and the antialiasing work lists, start this frame empty
+  for (int w = 0; w < a.n; ++w)
+    for (int k = v; k < a.tiles[w]; k += gridDim.x * blockDim.x) a.count[w][k] = 0;
+  if (v < kMaxViews) {
+    status->big_count[v] = 0;
+    status->needed_pairs[v] = 0;
+    status->units[v] = 0;
+    status->split[v] = 0;
+  }
+  if (v < a.n && a.aa_count[v]) *a.aa_count[v] = 0;
   if (v >= V) return;
   const float x = verts[3 * v], y = verts[3 * v + 1], z = verts[3 * v + 2];
 #pragma unroll
@@ -319,28 +337,6 @@ __global__ void transform_all_kernel(const float* __restrict__ verts, int V, con
   }
 }
 
-__global__ void tri_setup_all_kernel(const int* __restrict__ tris, int T, ViewSetupArgs a, DevStatus* status) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  // the binning's tile counters, big-triangle counts and list totals, and the
-  // antialiasing work lists, start this frame empty
-  for (int w = 0; w < a.n; ++w)
-    for (int k = t; k < a.tiles[w]; k += gridDim.x * blockDim.x) a.count[w][k] = 0;
-  if (t < kMaxViews) {
-    status->big_count[t] = 0;
-    status->needed_pairs[t] = 0;
-    status->units[t] = 0;
-    status->split[t] = 0;
-  }
-  if (t < a.n && a.aa_count[t]) *a.aa_count[t] = 0;
-  if (t >= T) return;
-  const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
-#pragma unroll
-  for (int w = 0; w < kMaxViews; ++w) {
-    if (w >= a.n) break;
-    setup_triangle(t, a.snap[w][v0], a.snap[w][v1], a.snap[w][v2], a.W[w], a.H[w], a.setup[w] + t, a.orient[w] + t);
-  }
-}
-
 __global__ void silhouette_all_kernel(const int* __restrict__ adj, int T, ViewSetupArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= T) return;
@@ -353,39 +349,30 @@ __global__ void silhouette_all_kernel(const int* __restrict__ adj, int T, ViewSe
 }
 
 // ------------------------------------------------------------------ binning
+// Tile range of a setup record: its bbox in tiles of side 2^tl (origin tx0,
+// ty0, width ntx); returns the number of tiles (0 for a record with no pixel
+// centre in its bbox).
+__device__ __forceinline__ int tile_range(int flags, int ibox, int jbox, int tl, int& tx0, int& ty0, int& ntx) {
+  if (!(flags & 16)) return 0;
+  const int i0 = ibox & 0xffff, i1 = (unsigned)ibox >> 16, j0 = jbox & 0xffff, j1 = (unsigned)jbox >> 16;
+  tx0 = i0 >> tl;
+  ty0 = j0 >> tl;
+  ntx = (i1 >> tl) - tx0 + 1;
+  return ntx * ((j1 >> tl) - ty0 + 1);
+}
+
 // Warp-cooperative emission of (triangle, tile) pairs: the 32 triangles of a
 // warp pool their tile ranges and the lanes stride over the pooled pairs, so a
-// triangle spanning thousands of tiles is spread over 32 lanes.
+// triangle spanning thousands of tiles is spread over 32 lanes.  Lanes that
+// hit the same tile (neighbouring triangles usually share tiles) take one
+// atomic through their lowest lane.  Count pass: adds to the tile's counter;
+// fill pass: takes list slots of the tile's segment by counting the counter
+// back down (to zero).  Every lane of the warp calls it; n = 0 emits nothing.
 template <bool kFill>
-__global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX, BinShape bs,
-                           int* __restrict__ counter, const int* __restrict__ offset, int* __restrict__ list,
-                           int capacity, DevStatus* status, int view, int* __restrict__ big_index,
-                           int* __restrict__ big_tri) {
-  const int tl = bs.tile_log2;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int lane = threadIdx.x & 31;
-  int n = 0, tx0 = 0, ty0 = 0, ntx = 1;
-  if (t < T) {
-    int flags = setup[t].flags;
-    if (flags & 16) {
-      int ib = setup[t].ibox, jb = setup[t].jbox;
-      int i0 = ib & 0xffff, i1 = (unsigned)ib >> 16, j0 = jb & 0xffff, j1 = (unsigned)jb >> 16;
-      tx0 = i0 >> tl; ty0 = j0 >> tl;
-      ntx = (i1 >> tl) - tx0 + 1;
-      n = ntx * ((j1 >> tl) - ty0 + 1);
-    }
-  }
-  if (!kFill && t < T) {
-    int b = -1;
-    if (n >= bs.big_tiles) {
-      b = atomicAdd(&status->big_count[view], 1);
-      if (b < kMaxBig) big_tri[b] = t;
-      else b = -1;
-    }
-    big_index[t] = b;
-  }
-  // big triangles are binned per tile by the segment and work-unit passes
-  if (t < T && n >= bs.big_tiles && big_index[t] >= 0) n = 0;
+__device__ __forceinline__ void emit_pairs(int t, int n, int tx0, int ty0, int ntx, int tilesX,
+                                           int* __restrict__ counter, const int* __restrict__ offset,
+                                           int* __restrict__ list, int capacity, DevStatus* status) {
+  const int lane = threadIdx.x & 31;
   int incl = n;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -412,8 +399,6 @@ __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX
       int q = p - o_excl;
       tile = (o_ty0 + q / o_ntx) * tilesX + o_tx0 + q % o_ntx;
     }
-    // lanes that hit the same tile (neighbouring triangles usually share
-    // tiles) take one atomic through their lowest lane
     const unsigned peers = __match_any_sync(kFull, tile);
     const int leader = __ffs(peers) - 1;
     const int cnt = __popc(peers);
@@ -421,15 +406,52 @@ __global__ void bin_kernel(const TriSetup* __restrict__ setup, int T, int tilesX
       if (tile >= 0 && lane == leader) atomicAdd(&counter[tile], cnt);
     } else {
       int base_slot = 0;
-      if (tile >= 0 && lane == leader) base_slot = offset[tile] + atomicAdd(&counter[tile], cnt);
+      if (tile >= 0 && lane == leader) base_slot = offset[tile] + atomicSub(&counter[tile], cnt) - cnt;
       base_slot = __shfl_sync(kFull, base_slot, leader);
       if (tile >= 0) {
         const int slot = base_slot + __popc(peers & ((1u << lane) - 1));
-        if (slot < capacity) list[slot] = o_t;
+        if (slot >= 0 && slot < capacity) list[slot] = o_t;
         else atomicExch(&status->capacity_overflow, 1);
       }
     }
   }
+}
+
+// Triangle setup of one view (blockIdx.y) with the binning's count pass: the
+// record stays in registers for the tile counts.  A triangle spanning at least
+// big_tiles tiles is listed as big (at most kMaxBig per view) and binned per
+// tile by alloc_units_kernel instead.
+__global__ void setup_bin_kernel(const int* __restrict__ tris, int T, ViewSetupArgs a, DevStatus* status) {
+  const int w = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const BinShape bs = a.bs[w];
+  int n = 0, tx0 = 0, ty0 = 0, ntx = 1;
+  if (t < T) {
+    const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
+    const VertSnap* snap = a.snap[w];
+    const TriSetup r = setup_triangle(t, snap[v0], snap[v1], snap[v2], a.W[w], a.H[w], a.setup[w] + t,
+                                      a.orient[w] + t);
+    n = tile_range(r.flags, r.ibox, r.jbox, bs.tile_log2, tx0, ty0, ntx);
+    int b = -1;
+    if (n >= bs.big_tiles) {
+      b = atomicAdd(&status->big_count[a.view0 + w], 1);
+      if (b < kMaxBig) a.big_tri[w][b] = t;
+      else b = -1;
+    }
+    a.big_index[w][t] = b;
+    if (b >= 0) n = 0;
+  }
+  emit_pairs<false>(t, n, tx0, ty0, ntx, a.tilesX[w], a.count[w], nullptr, nullptr, 0, status);
+}
+
+// Fill pass of one view: the same pairs as the count pass, into the list.
+__global__ void bin_fill_kernel(const TriSetup* __restrict__ setup, int T, int tilesX, BinShape bs,
+                                int* __restrict__ counter, const int* __restrict__ offset, int* __restrict__ list,
+                                int capacity, DevStatus* status, const int* __restrict__ big_index) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = 0, tx0 = 0, ty0 = 0, ntx = 1;
+  if (t < T && big_index[t] < 0) n = tile_range(setup[t].flags, setup[t].ibox, setup[t].jbox, bs.tile_log2, tx0, ty0, ntx);
+  emit_pairs<true>(t, n, tx0, ty0, ntx, tilesX, counter, offset, list, capacity, status);
 }
 
 // A tile can hold a covered pixel centre of the triangle only if no edge
@@ -452,29 +474,38 @@ __device__ __forceinline__ bool tile_may_cover(const TriSetup& r, int tx, int ty
 
 // Whether big triangle r may cover tile (tx, ty): inside its bbox's tile
 // range and not excluded by the corner test.  The big triangles (at most
-// kMaxBig per view, listed by the count pass) are binned per tile by the
-// segment and work-unit passes instead of per triangle.
+// kMaxBig per view, listed by the count pass) are binned per tile by
+// alloc_units_kernel instead of per triangle.
 __device__ __forceinline__ bool big_covers_tile(const TriSetup& r, int tx, int ty, int tl) {
   const int i0 = r.ibox & 0xffff, i1 = (unsigned)r.ibox >> 16, j0 = r.jbox & 0xffff, j1 = (unsigned)r.jbox >> 16;
   if (tx < (i0 >> tl) || tx > (i1 >> tl) || ty < (j0 >> tl) || ty > (j1 >> tl)) return false;
   return tile_may_cover(r, tx, ty, tl);
 }
 
-// List segments of the tiles (their ordinary triangles counted by the count
-// pass, their big ones here): tile k owns [offset[k], offset[n + k]) of the
-// view's triangle list.  Segments are handed out by one atomic per warp on the
-// view's running total (status->needed_pairs, zeroed by the setup), so they
-// are not in tile order (nothing depends on that order).  Also clears the
-// counters for the fill pass; the running total tells the host the list size.
-__global__ void alloc_kernel(int* __restrict__ count, int n, int* __restrict__ offset, DevStatus* status,
-                             int view, const TriSetup* __restrict__ setup, const int* __restrict__ big_tri,
-                             int tilesX, int tl) {
+// Per tile of one view: its list segment [offset[k], offset[n + k]), the
+// ordinary triangles of the count pass then the big triangles that may cover
+// the tile.  Segments are handed out by one atomic per warp on the view's
+// running total (status->needed_pairs, zeroed by the transform), so they are
+// not in tile order (nothing depends on that order); the total tells the host
+// the list size.  With `write`: the big triangles go into the segment after
+// its ordinary part (which the fill pass takes), and the raster work units
+// follow, one per kRasterBatch records (at least one per tile), handed out by
+// one atomic per warp on status->units, with a key slot for a tile of several
+// units.  (The bounds hold whenever the list fits its capacity; a frame that
+// overflows it is reported and only has to stay in bounds.)
+__global__ void alloc_units_kernel(const int* __restrict__ count, int n, int* __restrict__ offset,
+                                   DevStatus* status, int view, const TriSetup* __restrict__ setup,
+                                   const int* __restrict__ big_tri, int tilesX, int tl, int* __restrict__ list,
+                                   int capacity, RasterUnits ru, bool write) {
   const int tile = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
-  int c = 0;
+  int c_ord = 0, c = 0;
+  unsigned long long covers = 0ull;   // bit b: big triangle b may cover the tile
   if (tile < n) {
-    c = count[tile];
+    c_ord = count[tile];
     const int nbig = min(status->big_count[view], kMaxBig);
-    for (int b = 0; b < nbig; ++b) c += big_covers_tile(setup[big_tri[b]], tile % tilesX, tile / tilesX, tl);
+    for (int b = 0; b < nbig; ++b)
+      if (big_covers_tile(setup[big_tri[b]], tile % tilesX, tile / tilesX, tl)) covers |= 1ull << b;
+    c = c_ord + __popcll(covers);
   }
   int incl = c;
 #pragma unroll
@@ -485,43 +516,28 @@ __global__ void alloc_kernel(int* __restrict__ count, int n, int* __restrict__ o
   int base = 0;
   if (lane == 31 && incl > 0) base = atomicAdd(&status->needed_pairs[view], incl);
   base = __shfl_sync(kFull, base, 31);
+  const int beg = base + incl - c;
   if (tile < n) {
-    offset[tile] = base + incl - c;
+    offset[tile] = beg;
     offset[n + tile] = base + incl;
-    count[tile] = 0;
   }
-}
-
-// Raster work units of the tiles, from their list segments: one unit per
-// kRasterBatch records (at least one per tile), handed out by one atomic per
-// warp on status->units, and a key slot for a tile of several units.  (The
-// bounds hold whenever the list fits its capacity; a frame that overflows it
-// is reported and only has to stay in bounds.)
-__global__ void units_kernel(const int* __restrict__ offset, int n, DevStatus* status, int view, RasterUnits ru,
-                             const TriSetup* __restrict__ setup, const int* __restrict__ big_tri,
-                             const int* __restrict__ filled, int* __restrict__ list, int capacity, int tilesX,
-                             int tl) {
-  const int tile = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+  if (!write) return;   // (uniform over the grid)
   if (tile < n) {
-    // the tile's big triangles follow its ordinary ones in its segment
-    int k = offset[tile] + filled[tile];
-    const int nbig = min(status->big_count[view], kMaxBig);
-    for (int b = 0; b < nbig; ++b) {
-      const int t = big_tri[b];
-      if (!big_covers_tile(setup[t], tile % tilesX, tile / tilesX, tl)) continue;
-      if (k < capacity) list[k] = t;
+    int k = beg + c_ord;
+    for (unsigned long long m = covers; m; m &= m - 1) {
+      if (k < capacity) list[k] = big_tri[__ffsll((long long)m) - 1];
       else atomicExch(&status->capacity_overflow, 1);
       ++k;
     }
   }
-  const int nb = tile < n ? max(1, (offset[n + tile] - offset[tile] + kRasterBatch - 1) / kRasterBatch) : 0;
-  int incl = nb;
+  const int nb = tile < n ? max(1, (c + kRasterBatch - 1) / kRasterBatch) : 0;
+  incl = nb;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int u = __shfl_up_sync(kFull, incl, o);
     if (lane >= o) incl += u;
   }
-  int base = 0;
+  base = 0;
   if (lane == 31 && incl > 0) base = atomicAdd(&status->units[view], incl);
   base = __shfl_sync(kFull, base, 31);
   if (tile < n) {
@@ -667,7 +683,7 @@ __device__ __forceinline__ void cover_span(const int* w, int xs, int xe, int y, 
 constexpr int kChunk = 1024;
 
 template <int kTL>
-__global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restrict__ setup,
+__global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restrict__ setup,
                                                      const int* __restrict__ offset,
                                                      const int* __restrict__ list, int capacity, int tilesX,
                                                      int n_tiles, int W, int H, const float4* __restrict__ clip,
@@ -874,20 +890,21 @@ __global__ void raster_stats_kernel(const TriSetup* __restrict__ setup, const in
 
 // ------------------------------------------------------------------ launchers
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, float* viewMlo,
-                        cudaStream_t st) {
+                        const CamMats& cams, int C, cudaStream_t st) {
   count_launches(1);
-  light_setup_kernel<<<a.n, 64, 0, st>>>(params, a, out, viewM, viewMlo);
+  light_setup_kernel<<<a.n + 1, 64, 0, st>>>(params, a, out, viewM, viewMlo, cams, C);
 }
 
 void launch_setup_all(const float* verts, int V, const int* tris, int T, const int* adj, const float* viewM,
                       const float* viewMlo,
                       const ViewSetupArgs& a, DevStatus* status, bool silhouettes, cudaStream_t st) {
-  if (V > 0) {
-    count_launches(1);
-    transform_all_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, viewM, viewMlo, a);
-  }
+  // (launched for V = 0 too: it zeroes the binning's counters)
   count_launches(1);
-  tri_setup_all_kernel<<<std::max((T + 255) / 256, 64), 256, 0, st>>>(tris, T, a, status);
+  transform_all_kernel<<<std::max((V + 255) / 256, 16), 256, 0, st>>>(verts, V, viewM, viewMlo, a, status);
+  if (T > 0 && a.n > 0) {
+    count_launches(1);
+    setup_bin_kernel<<<dim3((T + 255) / 256, a.n), 256, 0, st>>>(tris, T, a, status);
+  }
   if (silhouettes) launch_silhouettes_all(adj, T, a, st);
 }
 
@@ -897,36 +914,20 @@ void launch_silhouettes_all(const int* adj, int T, const ViewSetupArgs& a, cudaS
   silhouette_all_kernel<<<(T + 255) / 256, 256, 0, st>>>(adj, T, a);
 }
 
-void launch_bin_count(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, DevStatus* status,
-                      int view, int* big_index, int* big_tri, cudaStream_t st) {
-  if (T == 0) return;
+void launch_alloc_units(const int* count, int n, int* offset, DevStatus* status, int view, const TriSetup* setup,
+                        const int* big_tri, int tilesX, int tile_log2, int* list, int capacity,
+                        const RasterUnits& ru, bool write, cudaStream_t st) {
   count_launches(1);
-  bin_kernel<false><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, bs, counter, nullptr, nullptr, 0, status,
-                                                     view, big_index, big_tri);
-}
-
-void launch_scan(int* count, int n, int* offset, DevStatus* status, int view, const TriSetup* setup,
-                 const int* big_tri, int tilesX, int tile_log2, cudaStream_t st) {
-  count_launches(1);
-  alloc_kernel<<<(n + 255) / 256, 256, 0, st>>>(count, n, offset, status, view, setup, big_tri, tilesX, tile_log2);
+  alloc_units_kernel<<<(n + 255) / 256, 256, 0, st>>>(count, n, offset, status, view, setup, big_tri, tilesX,
+                                                      tile_log2, list, capacity, ru, write);
 }
 
 void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int* counter, const int* offset,
-                     int* list, int capacity, DevStatus* status, int view, const int* big_index, const int* big_tri,
-                     cudaStream_t st) {
+                     int* list, int capacity, DevStatus* status, const int* big_index, cudaStream_t st) {
   if (T == 0) return;
   count_launches(1);
-  bin_kernel<true><<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, bs, counter, offset, list, capacity, status,
-                                                    view, const_cast<int*>(big_index), const_cast<int*>(big_tri));
-}
-
-void launch_units(const TriSetup* setup, const int* offset, int* list, int capacity, int tilesX, int tilesY,
-                  int tile_log2, const RasterUnits& ru, DevStatus* status, int view, const int* big_tri,
-                  const int* filled, cudaStream_t st) {
-  const int n = tilesX * tilesY;
-  count_launches(1);
-  units_kernel<<<(n + 255) / 256, 256, 0, st>>>(offset, n, status, view, ru, setup, big_tri, filled, list, capacity,
-                                                tilesX, tile_log2);
+  bin_fill_kernel<<<(T + 255) / 256, 256, 0, st>>>(setup, T, tilesX, bs, counter, offset, list, capacity, status,
+                                                   big_index);
 }
 
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,

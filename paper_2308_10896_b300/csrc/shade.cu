@@ -38,11 +38,12 @@ __global__ void vertex_normals_kernel(const float* __restrict__ verts, int V, co
 // dL/d unnormalised vertex normal N from dL/d unit normal n = N / |N|:
 // (g - n (n.g)) / |N|, with n and |N| saved by the forward.
 __global__ void normals_bwd_vertex_kernel(const float* __restrict__ vn, const float* __restrict__ vlen, int V,
-                                          const float* __restrict__ gn, float* __restrict__ gN) {
+                                          const float4* __restrict__ gn, float* __restrict__ gN) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
   const float l = vlen[v];
-  const float3 g = make_float3(gn[3 * v], gn[3 * v + 1], gn[3 * v + 2]);
+  const float4 g4 = gn[v];
+  const float3 g = make_float3(g4.x, g4.y, g4.z);
   float3 r = g;
   if (l > 0.f) {
     const float il = 1.f / l;
@@ -65,12 +66,15 @@ __global__ void normals_bwd_face_kernel(const int* __restrict__ tris, int T, con
 }
 
 // F = e1 x e2 (e1 = v1 - v0, e2 = v2 - v0):  dL/de1 = e2 x G,  dL/de2 = G x e1.
+// Adds the vertex's face-normal gradient and its position gradient gpos.
 __global__ void normals_bwd_gather_kernel(const float* __restrict__ verts, int V, const int* __restrict__ tris,
                                           const int* __restrict__ off, const int* __restrict__ lst,
-                                          const float* __restrict__ gface, float* __restrict__ dverts) {
+                                          const float* __restrict__ gface, const float4* __restrict__ gpos,
+                                          float* __restrict__ dverts) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
-  float3 acc = make_float3(0.f, 0.f, 0.f);
+  const float4 gp = gpos[v];
+  float3 acc = make_float3(gp.x, gp.y, gp.z);
   for (int k = off[v]; k < off[v + 1]; ++k) {
     const int t = lst[k];
     const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
@@ -537,21 +541,17 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
 // accumulator; big triangles go to their slot copies.
 struct CamScatter {
   const int* tris;
-  float* dverts;
-  float* gnormal;
+  float4* gpos;
+  float4* gnormal;
   float4* gclip;
   float* big_acc;
   int slot;
-  // ordinary triangle: onto its vertices
+  // ordinary triangle: onto its vertices, three 16-byte atomics per vertex
   __device__ __forceinline__ void vertices(int t, const float (&c)[30]) const {
     for (int k = 0; k < 3; ++k) {
       const int v = tris[3 * t + k];
-      atomicAdd(&dverts[3 * v], c[3 * k]);
-      atomicAdd(&dverts[3 * v + 1], c[3 * k + 1]);
-      atomicAdd(&dverts[3 * v + 2], c[3 * k + 2]);
-      atomicAdd(&gnormal[3 * v], c[9 + 3 * k]);
-      atomicAdd(&gnormal[3 * v + 1], c[10 + 3 * k]);
-      atomicAdd(&gnormal[3 * v + 2], c[11 + 3 * k]);
+      atomic_add4(&gpos[v], make_float4(c[3 * k], c[3 * k + 1], c[3 * k + 2], 0.f));
+      atomic_add4(&gnormal[v], make_float4(c[9 + 3 * k], c[10 + 3 * k], c[11 + 3 * k], 0.f));
       atomic_add4(&gclip[v], make_float4(c[18 + 4 * k], c[19 + 4 * k], c[20 + 4 * k], c[21 + 4 * k]));
     }
   }
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(256) shade_scatter_kernel(ShadeArgs a, ShadeGr
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * kShadeStrip;
   const bool col_ok = i < a.W;
-  CamScatter sc{a.tris, g.dverts, g.gnormal, g.gclip, g.big_acc, scatter_slot(kBigSlots)};
+  CamScatter sc{a.tris, g.gpos, g.gnormal, g.gclip, g.big_acc, scatter_slot(kBigSlots)};
   BigRun<30, 1> run;
   big_run_reset(run);
   TriCache tc;
@@ -632,12 +632,8 @@ __global__ void shade_big_resolve_kernel(ShadeArgs a, ShadeGradArgs g, const int
   __syncthreads();
   if (k < 3) {
     const int v = a.tris[3 * big_tri[b] + k];
-    atomicAdd(&g.dverts[3 * v], sum[3 * k]);
-    atomicAdd(&g.dverts[3 * v + 1], sum[3 * k + 1]);
-    atomicAdd(&g.dverts[3 * v + 2], sum[3 * k + 2]);
-    atomicAdd(&g.gnormal[3 * v], sum[9 + 3 * k]);
-    atomicAdd(&g.gnormal[3 * v + 1], sum[10 + 3 * k]);
-    atomicAdd(&g.gnormal[3 * v + 2], sum[11 + 3 * k]);
+    atomic_add4(&g.gpos[v], make_float4(sum[3 * k], sum[3 * k + 1], sum[3 * k + 2], 0.f));
+    atomic_add4(&g.gnormal[v], make_float4(sum[9 + 3 * k], sum[10 + 3 * k], sum[11 + 3 * k], 0.f));
     atomic_add4(&g.gclip[v], make_float4(sum[18 + 4 * k], sum[19 + 4 * k], sum[20 + 4 * k], sum[21 + 4 * k]));
   }
 }
@@ -779,15 +775,16 @@ void launch_vertex_normals(const float* verts, int V, const int* tris, const int
 }
 
 void launch_normals_backward(const float* verts, int V, const int* tris, int T, const int* vf_off,
-                             const int* vf_list, const float* vnormal, const float* vlen, const float* gnormal,
-                             float* gN, float* gface, float* dverts, cudaStream_t st) {
+                             const int* vf_list, const float* vnormal, const float* vlen, const float4* gnormal,
+                             const float4* gpos, float* gN, float* gface, float* dverts, cudaStream_t st) {
   if (V == 0 || T == 0) return;
   count_launches(1);
   normals_bwd_vertex_kernel<<<(V + 255) / 256, 256, 0, st>>>(vnormal, vlen, V, gnormal, gN);
   count_launches(1);
   normals_bwd_face_kernel<<<(T + 255) / 256, 256, 0, st>>>(tris, T, gN, gface);
   count_launches(1);
-  normals_bwd_gather_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, tris, vf_off, vf_list, gface, dverts);
+  normals_bwd_gather_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, tris, vf_off, vf_list, gface, gpos,
+                                                             dverts);
 }
 
 void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st) {
