@@ -83,20 +83,21 @@ def stage_bytes(sc, listed=None) -> dict:
         "setup": views * (12 * V + 32 * V + 12 * T + 66 * T + 4 * T) + L * 4 * V,
         # fill: the record's flags and bbox words and the big-triangle index in, one list entry per triangle out
         "bin_fill": views * (12 * T + 4 * T + 4 * T),
-        # setup records and lists read once, one 16-byte G-buffer texel written per pixel, and per light
-        # texel the depth sample (f, f^2), 8 bytes
-        "raster": views * (64 * T + 4 * T) + 16 * (texels + WH) + 8 * texels,
-        # detection: G-buffer 16 in, listed-flag byte out; list pass per listed texel:
-        # list entry 4, G-buffer 16, (f, f^2) 8 in, antialiased value 8 out
-        "sm_antialias": texels * (16 + 1) + sm_listed * (4 + 16 + 8 + 8),
+        # setup records and lists read once, one 16-byte G-buffer texel and one listed-flag byte written per
+        # pixel, and per light texel the depth sample (f, f^2), 8 bytes
+        "raster": views * (64 * T + 4 * T) + 17 * (texels + WH) + 8 * texels,
+        # list pass per listed texel: list entry 4, G-buffer 16, (f, f^2) 8 in, antialiased value 8 out
+        "sm_antialias": sm_listed * (4 + 16 + 8 + 8),
         # one tiled pass: (f, f^2) 8 + flag 1 in, moments 8 out
         "filter": texels * (8 + 1 + 8),
-        "shade": WH * (16 + 16) + 8 * texels + 24 * V,
-        "final_antialias": WH * (16 + 16 + 16 + 1) + cam_listed * (4 + 16 + 16 + 16),
+        # G-buffer 16 and flag 1 in, colour 16 and image 16 out
+        "shade": WH * (16 + 1 + 16 + 16) + 8 * texels + 24 * V,
+        "final_antialias": cam_listed * (4 + 16 + 16 + 16),
         "bwd_clear": 8 * texels + views * 16 * V + 4 * L * V + 24 * V,
-        "bwd_final_antialias": WH * (1 + 16 + 16) + cam_listed * (4 + 16 + 16 + 16 + 16),
-        # per pixel: G-buffer 16 + dL/dcolour 16 in, pgrad 32 out; texel gradient scatter 8 per texel
-        "bwd_shade": WH * (16 + 16 + 32) + 8 * texels + 40 * V,
+        "bwd_final_antialias": cam_listed * (4 + 16 + 16 + 16 + 16),
+        # per pixel: G-buffer 16 + flag 1 + dL/dimage or dL/dcolour 16 in, pgrad 32 out; texel gradient
+        # scatter 8 per texel
+        "bwd_shade": WH * (16 + 1 + 16 + 32) + 8 * texels + 40 * V,
         "bwd_shade_scatter": WH * (16 + 32) + 40 * V,
         # dm 8 + f 8 in, dL/df~ 8 + dL/df 4 out
         "bwd_filter": texels * (8 + 8 + 8 + 4),
@@ -879,15 +880,15 @@ KERNEL_STAGES = [
     (r"light_setup_kernel|transform_all_kernel|setup_bin_kernel|silhouette_all_kernel|"
      r"vertex_normals_kernel|alloc_units_kernel", "setup"),
     (r"bin_fill_kernel", "bin_fill"),
-    (r"raster_kernel<", "raster"),
-    (r"aa_detect_kernel|aa_forward_list_kernel<float2>", "sm_antialias"),
+    (r"raster_kernel<|aa_seam_kernel", "raster"),
+    (r"aa_forward_list_kernel<float2>", "sm_antialias"),
     (r"filter_tma_kernel<\d+, 0>|filter_tile_kernel<\d+, 0>|filter_pass_kernel<(true|false), false>|compose_kernel",
      "filter"),
     (r"shade_kernel", "shade"),
-    (r"aa_forward_kernel<float4>|aa_forward_list_kernel<float4>", "final_antialias"),
+    (r"aa_forward_list_kernel<float4>", "final_antialias"),
     (r"l2_kernel", "loss"),
     (r"clear_kernel", "bwd_clear"),
-    (r"aa_backward4_kernel|aa_backward4_list_kernel", "bwd_final_antialias"),
+    (r"aa_backward4_list_kernel", "bwd_final_antialias"),
     (r"shade_backward_kernel", "bwd_shade"),
     (r"shade_scatter_kernel|shade_big_resolve_kernel", "bwd_shade_scatter"),
     (r"filter_tma_kernel<\d+, 1>|filter_tile_kernel<\d+, 1>|filter_pass_kernel<(true|false), true>|fold_kernel",

@@ -404,7 +404,10 @@ const char* dsm_last_error(dsm_ctx* ctx);
  *  8 dL/d clip coordinates of view index, float4 per vertex (light views: the
  *    z slot holds dL/d vertex depth d, since clip z carries no gradient there)
  *  9 dL/d(f~, (f^2)~) (light), float2
- * 10 dL/d colour of camera index before the final antialiasing, float4 per pixel
+ * 10 dL/d colour of camera index before the final antialiasing, float4 per pixel,
+ *    at the pixels on the final antialiasing's work list (every other pixel's
+ *    dL/d colour is its dL/d image, which the shading adjoint reads directly;
+ *    the buffer holds no defined value there)
  * 11 shading-stage surface of camera index (Alg. 2 inputs, recomputed by the
  *    shading kernel's own device functions): two float4 per pixel,
  *    (x, y, z, 0) world position and (nx, ny, nz, 0) unit normal

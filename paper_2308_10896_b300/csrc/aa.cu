@@ -141,89 +141,29 @@ __device__ __forceinline__ bool pair_info(const AAArgs& a, int i, int j, int ni,
   return pi.c.found;
 }
 
-// The G-buffer entries a pair decision needs (triangle id, depth key) for a
-// kAAW x kAAH block of pixels and its one-pixel halo, staged in shared memory
-// with coalesced loads: the four neighbours of every pixel are read from here.
-constexpr int kAAW = 32, kAAH = 32, kAAThreadsY = 8;   // tile of a CTA; threads: 32 x 8, 4 rows each
-constexpr int kAARows = kAAH / kAAThreadsY;
-struct GTile {
-  int id[kAAH + 2][kAAW + 2];
-  float z[kAAH + 2][kAAW + 2];
-};
-
-__device__ __forceinline__ void load_gtile(const AAArgs& a, GTile& t, int bx0, int by0) {
-  constexpr int kN = (kAAH + 2) * (kAAW + 2), kThreads = kAAW * kAAThreadsY;
-  constexpr int kIt = (kN + kThreads - 1) / kThreads;
-  const int tid = threadIdx.y * kAAW + threadIdx.x;
-  float2 g[kIt];   // (id bits, depth key); every load issued before the first store
-#pragma unroll
-  for (int it = 0; it < kIt; ++it) {
-    const int k = tid + kThreads * it;
-    const int r = k / (kAAW + 2), c = k - r * (kAAW + 2);
-    const int gi = bx0 - 1 + c, gj = by0 - 1 + r;
-    g[it] = make_float2(0.f, 0.f);
-    if (k < kN && gi >= 0 && gj >= 0 && gi < a.W && gj < a.H) {
-      const float4 v = a.gbuf[(size_t)gj * a.W + gi];
-      g[it] = make_float2(v.x, v.w);
-    }
-  }
-#pragma unroll
-  for (int it = 0; it < kIt; ++it) {
-    const int k = tid + kThreads * it;
-    if (k < kN) {
-      const int r = k / (kAAW + 2), c = k - r * (kAAW + 2);
-      t.id[r][c] = __float_as_int(g[it].x);
-      t.z[r][c] = g[it].y;
-    }
-  }
-}
-
-__device__ __forceinline__ float4 gtile_at(const GTile& t, int lx, int ly) {
-  return make_float4(__int_as_float(t.id[ly][lx]), 0.f, 0.f, t.z[ly][lx]);
-}
-
 // Neighbour d of pixel (i, j): left, right, up, down.
 __device__ __forceinline__ int nb_dx(int d) { return d == 0 ? -1 : d == 1 ? 1 : 0; }
 __device__ __forceinline__ int nb_dy(int d) { return d == 2 ? -1 : d == 3 ? 1 : 0; }
 
-// Antialiasing runs as a detection pass and a list pass.  Only a pair whose
+// Antialiasing runs as a detection step and a list pass.  Only a pair whose
 // occluder triangle has a silhouette edge can have a crossing, and such pairs
 // are few (about 1 % of pixels in the benchmark scenes); the code that finds
-// and differentiates crossings needs many registers.  So a light detection
-// pass (staged G-buffer tile, high occupancy) flags the pixels with such a
-// pair (hflag) and appends them to the view's work list, and the list passes
-// run the full pair logic for the listed pixels only.  Every other pixel's
-// antialiased value is its own value, so the consumers read the unmodified
-// map there: the moment filter substitutes the list pass's values at flagged
-// texels, and the backward's filter transpose writes dL/df directly.  The list
-// depends only on the G-buffer, so the backward reuses the forward's list; the
-// setup of the next frame clears its counter.
-__device__ __forceinline__ bool needs_crossing(const AAArgs& a, const GTile& t, int i, int j, int lx, int ly) {
-  const float4 gp = gtile_at(t, lx, ly);
-  bool heavy = false;
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    const int ni = i + nb_dx(d), nj = j + nb_dy(d);
-    if (ni < 0 || nj < 0 || ni >= a.W || nj >= a.H) continue;
-    const float4 gq = gtile_at(t, lx + nb_dx(d), ly + nb_dy(d));
-    if (gid(gq) == gid(gp)) continue;
-    const int tri = gid(pair_p_occ(i, j, ni, nj, gp, gq) ? gp : gq) - 1;
-    heavy |= a.sil[tri] != 0;
-  }
-  return heavy;
-}
-
-// Warp-aggregated append of `value` for the lanes with `want`; every lane of
-// the warp must call it.
+// and differentiates crossings needs many registers.  So the detection only
+// flags the pixels with such a pair (hflag) and appends them to the view's
+// work list, and the list passes run the full pair logic for the listed
+// pixels only.  The raster detects the pairs inside one of its tiles from the
+// tile's final keys (a pair's occluder is the smaller depth key, the
+// background's key being the largest), and aa_seam_kernel the pairs across
+// tile edges.  Every other pixel's antialiased value is its own value, so the
+// consumers read the unmodified map there: the moment filter substitutes the
+// list pass's values at flagged texels, the camera's shading writes the image
+// at unflagged pixels, the backward's filter transpose writes dL/df directly
+// and the shading adjoint reads dL/dimage there.  The list depends only on the
+// G-buffer, so the backward reuses the forward's list; the transform of the
+// next frame clears its counter.
+// Warp-aggregated append to the view's work list; every lane of the warp must call it.
 __device__ __forceinline__ void list_append(const AAWork& w, bool want, int value) {
-  const unsigned m = __ballot_sync(kFull, want);
-  if (!m) return;
-  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
-  const int leader = __ffs(m) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(w.count, __popc(m));
-  base = __shfl_sync(kFull, base, leader);
-  if (want) w.list[base + __popc(m & ((1u << lane) - 1))] = value;
+  warp_append(w.list, w.count, want, value);
 }
 
 // ------------------------------------------------------------------ forward
@@ -271,52 +211,56 @@ __device__ __forceinline__ void for_listed_pairs(const AAWork& w, Body body) {
   }
 }
 
-// Detection pass (shadow maps): hflag and the work list only.
-__global__ void __launch_bounds__(256) aa_detect_kernel(AAArgs a, uint8_t* __restrict__ hflag, AAWork w) {
-  __shared__ GTile t;
-  const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
-  load_gtile(a, t, bx0, by0);
-  __syncthreads();
-  const int i = bx0 + threadIdx.x;
-#pragma unroll
-  for (int q = 0; q < kAARows; ++q) {
-    const int ly = threadIdx.y + kAAThreadsY * q, j = by0 + ly;
-    const bool in = i < a.W && j < a.H;
-    const size_t p = in ? (size_t)j * a.W + i : 0;
-    const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, ly + 1);
-    if (in) hflag[p] = heavy ? 1 : 0;
-    list_append(w, heavy, (int)p);
-  }
+// Detection across tile seams.  The raster tested the pairs inside each of
+// its tiles (side T = 2^tl) and left each tile's rim (final keys, flagged
+// pixels) in rim; this pass tests the pairs across tile edges from the rims
+// alone and flags and lists the rim pixels the raster left unflagged.  One
+// thread per rim entry: side s (top, bottom, left, right) and position k;
+// the top and bottom rows hold the corners, with both of their neighbours
+// across the tile's edges, and the columns skip them.  A pair of different
+// ids has the smaller key as its occluder (the background's is the largest).
+constexpr int kSeamThreads = 128;
+__device__ __forceinline__ bool seam_pair_heavy(unsigned long long kp, unsigned long long kq,
+                                                const uint32_t* __restrict__ silbits) {
+  const unsigned idp = kp == ~0ull ? 0u : (unsigned)kp + 1u, idq = kq == ~0ull ? 0u : (unsigned)kq + 1u;
+  if (idp == idq) return false;
+  const unsigned occ = (unsigned)(kp < kq ? kp : kq);
+  return (silbits[occ >> 5] >> (occ & 31)) & 1u;
 }
-
-// Detection pass of the final image: also writes out = colour at the pixels
-// without a crossing.
-template <typename V>
-__global__ void __launch_bounds__(256) aa_forward_kernel(AAArgs a, const V* __restrict__ color, V* __restrict__ out,
-                                                         uint8_t* __restrict__ hflag, AAWork w) {
-  __shared__ GTile t;
-  const int bx0 = blockIdx.x * kAAW, by0 = blockIdx.y * kAAH;
-  const int i = bx0 + threadIdx.x;
-  V cp[kAARows];
-#pragma unroll
-  for (int q = 0; q < kAARows; ++q) {
-    const int j = by0 + threadIdx.y + kAAThreadsY * q;
-    cp[q] = (i < a.W && j < a.H) ? color[(size_t)j * a.W + i] : V{};
-  }
-  load_gtile(a, t, bx0, by0);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < kAARows; ++q) {
-    const int ly = threadIdx.y + kAAThreadsY * q, j = by0 + ly;
-    const bool in = i < a.W && j < a.H;
-    const size_t p = in ? (size_t)j * a.W + i : 0;
-    const bool heavy = in && needs_crossing(a, t, i, j, threadIdx.x + 1, ly + 1);
-    if (in) {
-      hflag[p] = heavy ? 1 : 0;
-      if (!heavy) out[p] = cp[q];
+__global__ void __launch_bounds__(kSeamThreads) aa_seam_kernel(int W, int H, int tilesX, int n_tiles, int tl,
+                                                               RimBufs rim, const uint32_t* __restrict__ silbits,
+                                                               uint8_t* __restrict__ hflag, AAWork w) {
+  const int T = 1 << tl;
+  const int g = blockIdx.x * kSeamThreads + threadIdx.x;
+  const int tile = g >> (tl + 2), r = g & (4 * T - 1), side = r >> tl, k = r & (T - 1);
+  const int tx = tile % tilesX, ty = tile / tilesX;
+  const int x = side == 0 || side == 1 ? k : (side == 2 ? 0 : T - 1);
+  const int y = side == 0 ? 0 : (side == 1 ? T - 1 : k);
+  const int i = (tx << tl) + x, j = (ty << tl) + y;
+  const bool in = tile < n_tiles && !(side >= 2 && (k == 0 || k == T - 1)) && i < W && j < H;
+  bool want = false;
+  if (in && !((rim.flags[(size_t)tile * 4 + side] >> k) & 1u)) {
+    const unsigned long long kp = rim.key[(size_t)tile * 4 * T + r];
+    // the neighbour across the edge of side `side`: the facing side of the adjacent tile
+    const int ntx = tx + (side == 2 ? -1 : side == 3 ? 1 : 0), nty = ty + (side == 0 ? -1 : side == 1 ? 1 : 0);
+    const int ni = i + (side == 2 ? -1 : side == 3 ? 1 : 0), nj = j + (side == 0 ? -1 : side == 1 ? 1 : 0);
+    if (ni >= 0 && nj >= 0 && ni < W && nj < H) {
+      const int facing = side ^ 1;   // top <-> bottom, left <-> right
+      const unsigned long long kq = rim.key[((size_t)(nty * tilesX + ntx) * 4 + facing) * T + k];
+      want = seam_pair_heavy(kp, kq, silbits);
     }
-    list_append(w, heavy, (int)p);
+    // a corner of the top or bottom row: also its neighbour across the side edge
+    // (the adjacent tile's same row, its far end)
+    if (side < 2 && (k == 0 || k == T - 1)) {
+      const int d = k == 0 ? -1 : 1;
+      if (i + d >= 0 && i + d < W) {
+        const unsigned long long kq = rim.key[((size_t)(ty * tilesX + tx + d) * 4 + side) * T + (T - 1 - k)];
+        want = want || seam_pair_heavy(kp, kq, silbits);
+      }
+    }
+    if (want) hflag[(size_t)j * W + i] = 1;
   }
+  warp_append(w.list, w.count, want, j * W + i);
 }
 
 template <typename V>
@@ -377,14 +321,6 @@ __device__ __forceinline__ V aa_pair_adjoint(const AAArgs& a, int i, int j, int 
     atomic_add4(&gclip[pi.c.vb], screen_to_clip_grad(cb, dLdt * pi.c.dt[2], dLdt * pi.c.dt[3], a.W, a.H));
   }
   return term;
-}
-
-// Colour adjoint at the pixels without a crossing (hflag from the forward's
-// detection pass): dL/dcolour passes through.
-__global__ void aa_backward4_kernel(const uint8_t* __restrict__ hflag, const float4* __restrict__ gout,
-                                    float4* __restrict__ gcolor, int n) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n && !hflag[p]) gcolor[p] = gout[p];
 }
 
 __global__ void __launch_bounds__(256) aa_backward4_list_kernel(AAArgs a, const float4* __restrict__ color,
@@ -545,20 +481,21 @@ __global__ void sm_big_resolve_kernel(const int* __restrict__ tris, const int* _
 
 constexpr int kListGrid = 148 * 8;   // CTAs of a second pass (grid-stride over the list)
 
-static inline dim3 aa_grid(const AAArgs& a) { return dim3((a.W + kAAW - 1) / kAAW, (a.H + kAAH - 1) / kAAH); }
-
-void launch_aa_detect(const AAArgs& a, uint8_t* hflag, const AAWork& w, cudaStream_t st) {
+void launch_aa_seam(const AAArgs& a, int tilesX, int tilesY, int tile_log2, const RimBufs& rim,
+                    const uint32_t* silbits, uint8_t* hflag, const AAWork& w, cudaStream_t st) {
+  const int n = tilesX * tilesY;
+  if (n == 0) return;
   count_launches(1);
-  aa_detect_kernel<<<aa_grid(a), dim3(kAAW, kAAThreadsY), 0, st>>>(a, hflag, w);
+  const int threads = n << (tile_log2 + 2);
+  aa_seam_kernel<<<(threads + kSeamThreads - 1) / kSeamThreads, kSeamThreads, 0, st>>>(
+      a.W, a.H, tilesX, n, tile_log2, rim, silbits, hflag, w);
 }
 void launch_aa_forward2_list(const AAArgs& a, const float2* color, float2* out, const AAWork& w, cudaStream_t st) {
   count_launches(1);
   aa_forward_list_kernel<float2><<<kListGrid, 256, 0, st>>>(a, color, out, w);
 }
-void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, uint8_t* hflag, const AAWork& w,
-                        cudaStream_t st) {
-  count_launches(2);
-  aa_forward_kernel<float4><<<aa_grid(a), dim3(kAAW, kAAThreadsY), 0, st>>>(a, color, out, hflag, w);
+void launch_aa_forward4_list(const AAArgs& a, const float4* color, float4* out, const AAWork& w, cudaStream_t st) {
+  count_launches(1);
   aa_forward_list_kernel<float4><<<kListGrid, 256, 0, st>>>(a, color, out, w);
 }
 void launch_sm_aa_adjoint_list(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
@@ -576,11 +513,9 @@ void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* dep
   sm_big_resolve_kernel<<<kMaxBig, 32, 0, st>>>(a.tris, big.tri, big.status, big.view, big.acc, gclip);
 }
 
-void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
-                         const uint8_t* hflag, const AAWork& w, cudaStream_t st) {
-  const int n = a.W * a.H;
-  count_launches(2);
-  aa_backward4_kernel<<<(n + 255) / 256, 256, 0, st>>>(hflag, gout, gcolor, n);
+void launch_aa_backward4_list(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor,
+                              float4* gclip, const AAWork& w, cudaStream_t st) {
+  count_launches(1);
   aa_backward4_list_kernel<<<kListGrid, 256, 0, st>>>(a, color, gout, gcolor, gclip, w);
 }
 

@@ -213,6 +213,41 @@ __device__ __forceinline__ void bary_backward(const Bary& r, const float gbc[3],
 __device__ __forceinline__ float pix_ndc_x(int i, int W) { return (float)(2 * i + 1 - W) / (float)W; }
 __device__ __forceinline__ float pix_ndc_y(int j, int H) { return (float)(H - 2 * j - 1) / (float)H; }
 
+// Warp-aggregated append of `value` to list (one atomic on *count per warp)
+// for the lanes with `want`; every lane of the warp must call it.
+__device__ __forceinline__ void warp_append(int* list, int* count, bool want, int value) {
+  const unsigned m = __ballot_sync(kFull, want);
+  if (!m) return;
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(kFull, base, leader);
+  if (want) list[base + __popc(m & ((1u << lane) - 1))] = value;
+}
+
+// The same for up to N values per lane (bit k of `mask`: append v[k]), with
+// one atomic per warp for all of them.
+template <int N>
+__device__ __forceinline__ void warp_append_n(int* list, int* count, unsigned mask, const int (&v)[N]) {
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  const int n = __popc(mask);
+  int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  if (total == 0) return;
+  int base = 0;
+  if (lane == 31) base = atomicAdd(count, total);
+  base = __shfl_sync(kFull, base, 31) + incl - n;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if ((mask >> k) & 1u) list[base++] = v[k];
+}
+
 __device__ __forceinline__ void atomic_add4(float4* p, float4 v) {
   atomicAdd(p, v);
 }

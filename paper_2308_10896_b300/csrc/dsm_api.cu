@@ -48,11 +48,14 @@ struct Buf {
   template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+inline size_t sil_bytes(size_t T) { return (T + 15) / 16 * 16; }
+
 struct ViewBufs {
   int W = 0, H = 0, tilesX = 0, tilesY = 0;
   Buf clip, snap, depth, setup, orient, sil, count, offset, list, gbuf, gclip;
   Buf big_index, big_tri, big_acc;
   Buf aa_list, aa_ctr, hflag;   // antialiasing work list, its counter, per-pixel "listed" flag
+  Buf rim;                      // the raster tiles' rims for the detection's seam pass
   Buf color, gcolor, pgrad;     // camera views: colour before the final antialiasing, its adjoint, pixel gradients
   int list_cap = 0;
   BinShape bs{kTileLog2Default, kBigTilesDefault};
@@ -62,6 +65,12 @@ struct ViewBufs {
   AAWork aa_work() { return AAWork{aa_list.as<int>(), aa_ctr.as<int>()}; }
   // the clip buffer holds V clip coordinates, then V float-float screen positions
   float4* scr(int V) { return clip.as<float4>() + std::max(V, 1); }
+  // the sil buffer holds T silhouette masks, then (16-byte aligned) the packed flags
+  uint32_t* silbits(int T) { return reinterpret_cast<uint32_t*>(sil.as<uint8_t>() + sil_bytes(std::max(T, 1))); }
+  RimBufs rim_bufs() {
+    const size_t keys = (size_t)tilesX * tilesY * 4 * (1 << bs.tile_log2);
+    return RimBufs{rim.as<unsigned long long>(), reinterpret_cast<unsigned*>(rim.as<unsigned long long>() + keys)};
+  }
   RasterUnits raster_units() {
     return RasterUnits{units.as<int2>(), units_cap, tile_slot.as<int>(), slot_cap, tile_done.as<int>(),
                        skey.as<unsigned long long>()};
@@ -337,7 +346,7 @@ void dsm_destroy(dsm_ctx* ctx) {
   for (auto& v : ctx->view) {
     Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
                  &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr,
-                 &v.hflag, &v.color, &v.gcolor, &v.pgrad, &v.units, &v.tile_slot, &v.tile_done, &v.skey};
+                 &v.hflag, &v.rim, &v.color, &v.gcolor, &v.pgrad, &v.units, &v.tile_slot, &v.tile_done, &v.skey};
     for (Buf* b : vb) b->release();
   }
   for (auto& l : ctx->light) {
@@ -467,7 +476,7 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   DSM_CHECK(v.snap.ensure(Vn * sizeof(VertSnap)));
   DSM_CHECK(v.setup.ensure(Tn * sizeof(TriSetup)));
   DSM_CHECK(v.orient.ensure(Tn));
-  DSM_CHECK(v.sil.ensure(Tn));
+  DSM_CHECK(v.sil.ensure(sil_bytes(Tn) + 4 * ((Tn + 31) / 32)));   // masks, then the packed flags
   DSM_CHECK(v.count.ensure(tiles * 4));
   DSM_CHECK(v.offset.ensure(2 * tiles * 4));
   DSM_CHECK(v.gbuf.ensure((size_t)W * H * sizeof(float4)));
@@ -483,6 +492,7 @@ static dsm_status ensure_view(dsm_ctx* ctx, ViewBufs& v, int W, int H, int V, in
   DSM_CHECK(v.aa_list.ensure((size_t)W * H * 4));
   DSM_CHECK(v.aa_ctr.ensure(sizeof(int)));
   DSM_CHECK(v.hflag.ensure((size_t)W * H));
+  DSM_CHECK(v.rim.ensure(tiles * (4 * (size_t)tile * 8 + 4 * 4)));
   if (v.list_cap == 0) {
     const size_t cap = 2 * Tn + 2 * tiles + 1024;
     DSM_CHECK(v.list.ensure(cap * 4));
@@ -572,6 +582,7 @@ ViewSetupArgs view_setup_args(dsm_ctx* ctx, int w0, int n) {
     va.setup[k] = v.setup.as<TriSetup>();
     va.orient[k] = v.orient.as<int8_t>();
     va.sil[k] = v.sil.as<uint8_t>();
+    va.silbits[k] = v.silbits(ctx->mesh.n_tris);
     va.count[k] = v.count.as<int>();
     va.aa_count[k] = v.aa_ctr.as<int>();
     va.tilesX[k] = v.tilesX;
@@ -619,10 +630,18 @@ dsm_status size_lists(dsm_ctx* ctx, int w0, int n, cudaStream_t st) {
   return DSM_OK;
 }
 
-// Bin fill and raster of view w (a light view also writes f, f^2).
+// Whether view w antialiases: a light view its shadow map, a camera its image.
+bool view_aa(const dsm_ctx* ctx, int w) {
+  return view_is_light(ctx, w) ? ctx->params.aa_shadow != 0 : ctx->params.aa_final != 0;
+}
+
+// Bin fill and raster of view w (a light view also writes f, f^2), with the
+// antialiasing detection when the view antialiases (its silhouettes must be
+// complete on st).
 void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
   ViewBufs& v = vbuf(ctx, w);
   const bool light = view_is_light(ctx, w);
+  const bool aa = view_aa(ctx, w);
   DevStatus* ds = ctx->status.as<DevStatus>();
   {
     StageTimer t(ctx, ST_BIN_FILL, st);
@@ -634,7 +653,11 @@ void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
                 v.bs.tile_log2, v.W, v.H, v.clip.as<float4>(), v.scr(ctx->mesh.n_verts), ctx->mesh.tris,
                 v.gbuf.as<float4>(),
                 light ? v.depth.as<float>() : nullptr, light ? lwork(ctx, w).fmap.as<float2>() : nullptr,
-                warp_exponent(ctx), v.raster_units(), ds, w, st);
+                warp_exponent(ctx), v.raster_units(), ds, w, v.silbits(ctx->mesh.n_tris), aa ? v.hflag.as<uint8_t>() : nullptr,
+                v.aa_work(), v.rim_bufs(), st);
+  if (aa)
+    launch_aa_seam(aa_args(ctx, v), v.tilesX, v.tilesY, v.bs.tile_log2, v.rim_bufs(), v.silbits(ctx->mesh.n_tris),
+                   v.hflag.as<uint8_t>(), v.aa_work(), st);
 }
 
 // Alg. 1 after the raster: antialiasing of f, f^2 at the listed texels, then
@@ -647,11 +670,7 @@ void light_maps(dsm_ctx* ctx, int l, cudaStream_t st) {
   const bool aa = ctx->params.aa_shadow != 0;
   {
     StageTimer t(ctx, ST_SM_AA, st);
-    if (aa) {
-      const AAArgs a = aa_args(ctx, v);
-      launch_aa_detect(a, v.hflag.as<uint8_t>(), v.aa_work(), st);
-      launch_aa_forward2_list(a, wk.fmap.as<float2>(), wk.ftilde.as<float2>(), v.aa_work(), st);
-    }
+    if (aa) launch_aa_forward2_list(aa_args(ctx, v), wk.fmap.as<float2>(), wk.ftilde.as<float2>(), v.aa_work(), st);
   }
   StageTimer t(ctx, ST_FILTER, st);
   launch_filter(wk.fmap.as<float2>(), wk.tmp.as<float2>(), lb.mom.as<float2>(), v.W, lb.fa, st,
@@ -676,10 +695,12 @@ ShadeArgs shade_args(dsm_ctx* ctx, int c) {
   return sa;
 }
 
-ShadeGradArgs grad_args(dsm_ctx* ctx, int c, float* dalbedo, int red_stride) {
+ShadeGradArgs grad_args(dsm_ctx* ctx, int c, const float* gimage, float* dalbedo, int red_stride) {
   ViewBufs& cv = vbuf(ctx, ctx->L + c);
   ShadeGradArgs ga{};
   ga.gcolor = cv.gcolor.as<float4>();
+  ga.gimage = reinterpret_cast<const float4*>(gimage);
+  ga.hflag = ctx->params.aa_final ? cv.hflag.as<uint8_t>() : nullptr;
   ga.gpos = ctx->gpos.as<float4>();
   ga.gnormal = ctx->gnormal.as<float4>();
   ga.gclip = cv.gclip.as<float4>();
@@ -693,22 +714,20 @@ ShadeGradArgs grad_args(dsm_ctx* ctx, int c, float* dalbedo, int red_stride) {
   return ga;
 }
 
-// Camera c: Alg. 2 x Lambert into its colour buffer, then (with an image) the
-// final antialiasing into the image.
+// Camera c: Alg. 2 x Lambert into its colour buffer and (with an image) into
+// the image at the pixels the final antialiasing leaves as they are, then the
+// antialiased values of the listed pixels.
 dsm_status camera_colour(dsm_ctx* ctx, int c, float* image, cudaStream_t st) {
   ViewBufs& cv = vbuf(ctx, ctx->L + c);
+  const bool aa = ctx->params.aa_final != 0;
   {
     StageTimer t(ctx, ST_SHADE, st);
-    launch_shade(shade_args(ctx, c), cv.color.as<float4>(), st);
+    launch_shade(shade_args(ctx, c), cv.color.as<float4>(), reinterpret_cast<float4*>(image),
+                 aa ? cv.hflag.as<uint8_t>() : nullptr, st);
   }
-  if (!image) return DSM_OK;
+  if (!image || !aa) return DSM_OK;
   StageTimer t(ctx, ST_FINAL_AA, st);
-  if (ctx->params.aa_final) {
-    launch_aa_forward4(aa_args(ctx, cv), cv.color.as<float4>(), reinterpret_cast<float4*>(image),
-                       cv.hflag.as<uint8_t>(), cv.aa_work(), st);
-  } else {
-    DSM_CHECK(cudaMemcpyAsync(image, cv.color.p, (size_t)cv.W * cv.H * sizeof(float4), cudaMemcpyDeviceToDevice, st));
-  }
+  launch_aa_forward4_list(aa_args(ctx, cv), cv.color.as<float4>(), reinterpret_cast<float4*>(image), cv.aa_work(), st);
   return DSM_OK;
 }
 
@@ -717,19 +736,15 @@ dsm_status camera_colour(dsm_ctx* ctx, int c, float* image, cudaStream_t st) {
 dsm_status camera_backward(dsm_ctx* ctx, int c, const float* gimage, float* dalbedo, int red_stride,
                            cudaStream_t st) {
   ViewBufs& cv = vbuf(ctx, ctx->L + c);
-  {
+  if (ctx->params.aa_final) {
+    // dL/dcolour of the listed pixels; the shading adjoint reads dL/dimage at the others
     StageTimer t(ctx, ST_BWD_FINAL_AA, st);
-    if (ctx->params.aa_final) {
-      launch_aa_backward4(aa_args(ctx, cv), cv.color.as<float4>(), reinterpret_cast<const float4*>(gimage),
-                          cv.gcolor.as<float4>(), cv.gclip.as<float4>(), cv.hflag.as<uint8_t>(), cv.aa_work(), st);
-    } else {
-      DSM_CHECK(cudaMemcpyAsync(cv.gcolor.p, gimage, (size_t)cv.W * cv.H * sizeof(float4), cudaMemcpyDeviceToDevice,
-                                st));
-    }
+    launch_aa_backward4_list(aa_args(ctx, cv), cv.color.as<float4>(), reinterpret_cast<const float4*>(gimage),
+                             cv.gcolor.as<float4>(), cv.gclip.as<float4>(), cv.aa_work(), st);
   }
   if (ctx->aux_pending) DSM_CHECK(cudaStreamWaitEvent(st, ctx->ev_aux_done, 0));   // outputs cleared
   StageTimer t(ctx, ST_BWD_SHADE, st);
-  launch_shade_backward(shade_args(ctx, c), grad_args(ctx, c, dalbedo, red_stride), st);
+  launch_shade_backward(shade_args(ctx, c), grad_args(ctx, c, gimage, dalbedo, red_stride), st);
   return DSM_OK;
 }
 
@@ -737,7 +752,7 @@ dsm_status camera_backward(dsm_ctx* ctx, int c, const float* gimage, float* dalb
 void camera_scatter(dsm_ctx* ctx, int c, float* dalbedo, int red_stride, cudaStream_t st) {
   StageTimer t(ctx, ST_BWD_SHADE_SCATTER, st);
   const ShadeArgs sa = shade_args(ctx, c);
-  const ShadeGradArgs ga = grad_args(ctx, c, dalbedo, red_stride);
+  const ShadeGradArgs ga = grad_args(ctx, c, nullptr, dalbedo, red_stride);
   launch_shade_scatter(sa, ga, st);
   launch_shade_big_resolve(sa, ga, vbuf(ctx, ctx->L + c).big_tri.as<int>(), ctx->status.as<DevStatus>(), ctx->L + c,
                            st);
@@ -781,9 +796,9 @@ void vertex_backward_views(dsm_ctx* ctx, int w0, int n, float* dverts, int red_s
 }
 
 // Under recomputation: view w through its shared buffer set (setup, binning,
-// raster); `maps` also rebuilds a light's filtered moments, `detect` the
-// antialiasing work list.
-dsm_status rebuild_view(dsm_ctx* ctx, int w, bool sizing, bool maps, bool detect, cudaStream_t st) {
+// raster with the antialiasing detection); `maps` also rebuilds a light's
+// filtered moments.
+dsm_status rebuild_view(dsm_ctx* ctx, int w, bool sizing, bool maps, cudaStream_t st) {
   dsm_status s = prepare_view(ctx, w);
   if (s != DSM_OK) return s;
   {
@@ -797,11 +812,6 @@ dsm_status rebuild_view(dsm_ctx* ctx, int w, bool sizing, bool maps, bool detect
   }
   raster_view(ctx, w, st);
   if (maps && view_is_light(ctx, w)) light_maps(ctx, w, st);
-  if (detect) {
-    ViewBufs& v = vbuf(ctx, w);
-    StageTimer t(ctx, view_is_light(ctx, w) ? ST_SM_AA : ST_FINAL_AA, st);
-    launch_aa_detect(aa_args(ctx, v), v.hflag.as<uint8_t>(), v.aa_work(), st);
-  }
   DSM_CHECK(cudaGetLastError());
   return DSM_OK;
 }
@@ -926,7 +936,7 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
                           ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), st);
     t_setup.stop();
     for (int w = 0; w < NV; ++w) {
-      s = rebuild_view(ctx, w, sizing, true, false, st);
+      s = rebuild_view(ctx, w, sizing, true, st);
       if (s != DSM_OK) return s;
       if (w >= L) {
         s = camera_colour(ctx, w - L, images[w - L], st);
@@ -962,14 +972,13 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
       if (s != DSM_OK) return s;
       DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, 0, NV));
     }
-    // ---- per view: bin fill, raster; per light: Alg. 1 (f, f^2 -> antialias -> filter)
+    // ---- per view: bin fill, raster with the antialiasing detection (which
+    // reads the silhouettes); per light: Alg. 1 (f, f^2 -> antialias -> filter)
     for (int w = 0; w < NV; ++w) {
       cudaStream_t vst = view_stream(ctx, w, st);
+      if (vst != st) DSM_CHECK(cudaStreamWaitEvent(vst, ctx->ev_sil, 0));
       raster_view(ctx, w, vst);
-      if (w < L) {
-        if (vst != st) DSM_CHECK(cudaStreamWaitEvent(vst, ctx->ev_sil, 0));
-        light_maps(ctx, w, vst);
-      }
+      if (w < L) light_maps(ctx, w, vst);
     }
     // the lights' dL/dm accumulators and the backward's other internal
     // accumulators start the first backward empty; zeroed on the render
@@ -1098,14 +1107,14 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     // ---- the filtered moment maps again (every camera's shading adjoint reads all of them)
     ctx->stage_override = ST_BWD_RECOMPUTE;
     for (int l = 0; l < L; ++l) {
-      dsm_status s = rebuild_view(ctx, l, false, true, false, st);
+      dsm_status s = rebuild_view(ctx, l, false, true, st);
       if (s != DSM_OK) { ctx->stage_override = -1; return s; }
     }
     ctx->stage_override = -1;
     // ---- per camera: G-buffer and colour again, then its adjoints and its share of dL/dv
     for (int c = 0; c < C; ++c) {
       ctx->stage_override = ST_BWD_RECOMPUTE;
-      dsm_status s = rebuild_view(ctx, L + c, false, false, ctx->params.aa_final != 0, st);
+      dsm_status s = rebuild_view(ctx, L + c, false, false, st);
       if (s == DSM_OK) s = camera_colour(ctx, c, nullptr, st);
       ctx->stage_override = -1;
       if (s != DSM_OK) return s;
@@ -1124,7 +1133,7 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     // ---- per light: G-buffer, f and the antialiasing list again, then its adjoints
     for (int l = 0; l < L; ++l) {
       ctx->stage_override = ST_BWD_RECOMPUTE;
-      dsm_status s = rebuild_view(ctx, l, false, false, ctx->params.aa_shadow != 0, st);
+      dsm_status s = rebuild_view(ctx, l, false, false, st);
       ctx->stage_override = -1;
       if (s != DSM_OK) return s;
       {
@@ -1449,7 +1458,7 @@ uint64_t dsm_memory_bytes(dsm_ctx* ctx) {
   for (const auto& v : ctx->view) {
     const Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
                        &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr,
-                       &v.hflag, &v.color, &v.gcolor, &v.pgrad, &v.units, &v.tile_slot, &v.tile_done, &v.skey};
+                       &v.hflag, &v.rim, &v.color, &v.gcolor, &v.pgrad, &v.units, &v.tile_slot, &v.tile_done, &v.skey};
     for (const Buf* b : vb) n += b->cap;
   }
   for (const auto& l : ctx->light) {

@@ -88,7 +88,12 @@ struct ShadeArgs {
 };
 
 struct ShadeGradArgs {
-  const float4* gcolor;               // dL/d colour before the final antialiasing
+  // dL/d colour before the final antialiasing: gcolor at the pixels flagged by
+  // the camera's antialiasing detection (hflag), dL/dimage gimage elsewhere
+  // (hflag NULL: gimage everywhere)
+  const float4* gcolor;
+  const float4* gimage;
+  const uint8_t* hflag;
   float4* gpos;                       // V, dL/d vertex position through the camera's interpolation (xyz)
   float4* gnormal;                    // V, dL/d unit vertex normal (xyz)
   float4* gclip;                      // V, dL/d camera clip
@@ -115,10 +120,20 @@ struct BigArgs {
 };
 
 // Antialiasing work list of a view: pixel indices appended by the detection
-// pass; the counter is cleared by the setup of each frame.
+// (the raster and the seam pass); the counter is cleared by the transform of
+// each frame.
 struct AAWork {
   int* list;
   int* count;
+};
+
+// The raster tiles' rims for the seam pass of the antialiasing detection:
+// per tile (side T), the final keys of its top row, bottom row, left and right
+// column (4 T entries), and four words with the pixels of each the raster
+// flagged (bit k: entry k of that side).
+struct RimBufs {
+  unsigned long long* key;   // tiles x 4 T
+  unsigned* flags;           // tiles x 4
 };
 
 struct AAArgs {
@@ -143,6 +158,7 @@ struct ViewSetupArgs {
   TriSetup* setup[kMaxViews];
   int8_t* orient[kMaxViews];
   uint8_t* sil[kMaxViews];
+  uint32_t* silbits[kMaxViews];   // the same, one bit per triangle (bit t & 31 of word t >> 5: any silhouette edge)
   int* count[kMaxViews];          // tile counters, zeroed by the transform
   int* aa_count[kMaxViews];       // antialiasing work-list counters, zeroed by the transform
   int tilesX[kMaxViews];
@@ -196,22 +212,31 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int*
 void launch_raster_stats(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX,
                          int tilesY, int tile_log2, unsigned long long* out, cudaStream_t st);
 // Light views (fmap != NULL) also write the shadow-map depth sample (f, f^2)
-// of every texel, f interpolated from the per-vertex light depths.
+// of every texel, f interpolated from the per-vertex light depths.  With
+// hflag (the view's antialiasing on), also the antialiasing detection of the
+// pixel pairs inside each tile (silbits: the view's packed silhouette flags):
+// hflag at every pixel and the flagged pixels appended to aa; the tiles' rims
+// go to rim.
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
                    int tile_log2, int W, int H, const float4* clip, const float4* scr, const int* tris,
                    float4* gbuf, const float* depth, float2* fmap, float ec, const RasterUnits& ru,
-                   DevStatus* status, int view, cudaStream_t st);
+                   DevStatus* status, int view, const uint32_t* silbits, uint8_t* hflag, const AAWork& aa,
+                   const RimBufs& rim, cudaStream_t st);
 
 // shadow-map interpolation and antialiasing
 // Antialiasing (detection + list passes, see aa.cu).
-void launch_aa_detect(const AAArgs& a, uint8_t* hflag, const AAWork& w, cudaStream_t st);
+// The detection's pairs across the edges of the raster's tiles (after the
+// raster of the view, which detects the pairs inside its tiles and leaves
+// their rims in rim).
+void launch_aa_seam(const AAArgs& a, int tilesX, int tilesY, int tile_log2, const RimBufs& rim,
+                    const uint32_t* silbits, uint8_t* hflag, const AAWork& w, cudaStream_t st);
 void launch_aa_forward2_list(const AAArgs& a, const float2* color, float2* out, const AAWork& w, cudaStream_t st);
-void launch_aa_forward4(const AAArgs& a, const float4* color, float4* out, uint8_t* hflag, const AAWork& w,
-                        cudaStream_t st);
+void launch_aa_forward4_list(const AAArgs& a, const float4* color, float4* out, const AAWork& w, cudaStream_t st);
 void launch_sm_aa_adjoint_list(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
                                float ec, const AAWork& w, cudaStream_t st);
-void launch_aa_backward4(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor, float4* gclip,
-                         const uint8_t* hflag, const AAWork& w, cudaStream_t st);
+// dL/dcolour at the listed pixels (every other pixel's is dL/dimage itself).
+void launch_aa_backward4_list(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor,
+                              float4* gclip, const AAWork& w, cudaStream_t st);
 void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* depth, float4* gclip,
                               const BigArgs& big, cudaStream_t st);
 
@@ -253,7 +278,10 @@ void launch_vertex_normals(const float* verts, int V, const int* tris, const int
 void launch_normals_backward(const float* verts, int V, const int* tris, int T, const int* vf_off,
                              const int* vf_list, const float* vnormal, const float* vlen, const float4* gnormal,
                              const float4* gpos, float* gN, float* gface, float* dverts, cudaStream_t st);
-void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st);
+// Colour of every pixel (Alg. 2 x Lambert); with image, also the image at the
+// pixels that hflag leaves unflagged (all of them for hflag NULL), whose
+// antialiased value is their colour.
+void launch_shade(const ShadeArgs& a, float4* color, float4* image, const uint8_t* hflag, cudaStream_t st);
 void launch_shade_probe(const ShadeArgs& a, int l, float4* out, cudaStream_t st);
 void launch_sm_band_mask(const uint8_t* hflag, int n, float2* gft, float* gf, cudaStream_t st);
 void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);

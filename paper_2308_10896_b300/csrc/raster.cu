@@ -339,12 +339,16 @@ __global__ void transform_all_kernel(const float* __restrict__ verts, int V, con
 
 __global__ void silhouette_all_kernel(const int* __restrict__ adj, int T, ViewSetupArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= T) return;
-  const int a0 = adj[3 * t], a1 = adj[3 * t + 1], a2 = adj[3 * t + 2];
+  const bool ok = t < T;
+  const int a0 = ok ? adj[3 * t] : -1, a1 = ok ? adj[3 * t + 1] : -1, a2 = ok ? adj[3 * t + 2] : -1;
 #pragma unroll
   for (int w = 0; w < kMaxViews; ++w) {
     if (w >= a.n) break;
-    a.sil[w][t] = silhouette_mask(a.orient[w], t, a0, a1, a2);
+    const uint8_t m = ok ? silhouette_mask(a.orient[w], t, a0, a1, a2) : 0;
+    if (ok) a.sil[w][t] = m;
+    // the packed copy: one word per warp of 32 consecutive triangles
+    const unsigned bits = __ballot_sync(kFull, m != 0);
+    if ((threadIdx.x & 31) == 0 && t < T) a.silbits[w][t >> 5] = bits;
   }
 }
 
@@ -691,7 +695,8 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restri
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf,
                                                      const float* __restrict__ depth, float2* __restrict__ fmap,
                                                      float ec, RasterUnits ru, const DevStatus* __restrict__ status,
-                                                     int view) {
+                                                     int view, const uint32_t* __restrict__ silbits,
+                                                     uint8_t* __restrict__ hflag, AAWork aa, RimBufs rim) {
   constexpr int kTile = 1 << kTL;
   constexpr int kPix = kTile * kTile;
   static_assert(kTile <= 32, "tile-local coordinates are packed in 5 bits");
@@ -703,6 +708,7 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restri
   __shared__ unsigned short sown[kChunk];   // owning record + 1 of each item of the chunk
   __shared__ int swarp[8];
   __shared__ int slast;
+  __shared__ unsigned srim[4];       // flagged rim pixels of the tile: top row, bottom row, left, right column
   // this CTA's work unit: records [beg, lim) of one tile
   if ((int)blockIdx.x >= min(status->units[view], ru.units_cap)) return;
   const int2 unit = ru.units[blockIdx.x];
@@ -720,6 +726,7 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restri
   const int ti0 = ti * kTile, tj0 = tj * kTile;
   const long long Px0 = (long long)ti0 * kSubpix + 128, Py0 = (long long)tj0 * kSubpix + 128;
   for (int q = tid; q < kPix; q += 256) sbest[q] = ~0ull;
+  if (tid < 4) srim[tid] = 0u;
   for (int base = beg; base < lim; base += 256) {
     const int k = base + tid;
     int area = 0, box = 0, inv = 0;
@@ -828,6 +835,84 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restri
     if (tid == 0) ru.tile_done[tile] = 0;
     __syncthreads();
   }
+  __syncthreads();   // every pixel's final key is visible to the detection
+  // antialiasing detection of the pairs inside the tile (both pixels in the
+  // image): a pair of different ids (the keys' low words: triangle, or all
+  // ones for the background) whose occluder (the smaller key; the
+  // background's is the largest) has a silhouette edge flags both its
+  // pixels.  A detecting thread takes four consecutive pixels of one row,
+  // tests their right and lower pairs (spair: bits 0-3 and 4-7), then ORs in
+  // the pairs of its left and upper neighbours' threads.  The flagged pixels
+  // are listed after the G-buffer writes (one atomic per warp, its latency
+  // behind them); the rim's keys and flags go to rim for the seam pass
+  // (aa_seam_kernel).
+  constexpr int kRowThreads = kTile / 4, kDetThreads = kPix / 4;
+  unsigned hbits = 0u;   // bit q: pixel q of the thread's four is flagged
+  if (hflag) {
+    unsigned char* spair = reinterpret_cast<unsigned char*>(sown);   // (the owner map is free again)
+    auto pair_heavy = [&](unsigned long long kp, unsigned long long kq) -> unsigned {
+      if ((unsigned)kp == (unsigned)kq) return 0u;
+      const unsigned occ = (unsigned)(kp < kq ? kp : kq);
+      return (silbits[occ >> 5] >> (occ & 31)) & 1u;
+    };
+    const int ly = tid / kRowThreads, x0 = (tid % kRowThreads) * 4;
+    const int i0 = ti0 + x0, j = tj0 + ly;
+    unsigned long long k[4];
+    if (tid < kDetThreads) {
+      const unsigned long long* row = sbest + ly * kTile + x0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) k[q] = row[q];
+      const bool down = ly + 1 < kTile && j + 1 < H;
+      unsigned pr = 0u;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool right = (q < 3 || x0 + 4 < kTile) && i0 + q + 1 < W && j < H;
+        if (right) pr |= pair_heavy(k[q], q < 3 ? k[q + 1] : row[4]) << q;
+        if (down && i0 + q < W) pr |= pair_heavy(k[q], row[kTile + q]) << (4 + q);
+      }
+      spair[tid] = (unsigned char)pr;
+    }
+    __syncthreads();
+    if (tid < kDetThreads) {
+      const unsigned me = spair[tid];
+      const unsigned left = x0 > 0 ? spair[tid - 1] : 0u;
+      const unsigned up = ly > 0 ? spair[tid - kRowThreads] : 0u;
+      // pixel q: its right and lower pair, the right pair of pixel q - 1, the lower pair of the pixel above
+      hbits = (me | (me >> 4) | (me << 1) | ((left >> 3) & 1u) | (up >> 4)) & 15u;
+      unsigned inimg = 0u;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) inimg |= (i0 + q < W && j < H ? 1u : 0u) << q;
+      hbits &= inimg;
+      const size_t p0 = (size_t)j * W + i0;
+      if (inimg == 15u && (p0 & 3) == 0) {
+        *reinterpret_cast<unsigned*>(hflag + p0) =
+            (hbits & 1u) | ((hbits & 2u) << 7) | ((hbits & 4u) << 14) | ((hbits & 8u) << 21);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if ((inimg >> q) & 1u) hflag[p0 + q] = (hbits >> q) & 1u;
+      }
+      unsigned long long* rk = rim.key + (size_t)tile * 4 * kTile;
+      if (ly == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rk[x0 + q] = k[q];
+        if (hbits) atomicOr(&srim[0], hbits << x0);
+      }
+      if (ly == kTile - 1) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rk[kTile + x0 + q] = k[q];
+        if (hbits) atomicOr(&srim[1], hbits << x0);
+      }
+      if (x0 == 0) {
+        rk[2 * kTile + ly] = k[0];
+        if (hbits & 1u) atomicOr(&srim[2], 1u << ly);
+      }
+      if (x0 == kTile - 4) {
+        rk[3 * kTile + ly] = k[3];
+        if (hbits & 8u) atomicOr(&srim[3], 1u << ly);
+      }
+    }
+  }
   for (int px = tid; px < kPix; px += 256) {
     const int i = ti0 + (px & (kTile - 1)), j = tj0 + (px >> kTL);
     const uint64_t best = sbest[px];
@@ -849,6 +934,13 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restri
     }
     gbuf[(size_t)j * W + i] = out;
     if (fmap) fmap[(size_t)j * W + i] = moment_encode(f, ec);
+  }
+  if (hflag) {
+    __syncthreads();
+    if (tid < 4) rim.flags[(size_t)tile * 4 + tid] = srim[tid];
+    const int p0 = (tj0 + tid / kRowThreads) * W + ti0 + (tid % kRowThreads) * 4;
+    const int dpix[4] = {p0, p0 + 1, p0 + 2, p0 + 3};
+    warp_append_n<4>(aa.list, aa.count, hbits, dpix);
   }
 }
 
@@ -933,15 +1025,16 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int*
 void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
                    int tile_log2, int W, int H, const float4* clip, const float4* scr, const int* tris,
                    float4* gbuf, const float* depth, float2* fmap, float ec, const RasterUnits& ru,
-                   DevStatus* status, int view, cudaStream_t st) {
+                   DevStatus* status, int view, const uint32_t* silbits, uint8_t* hflag, const AAWork& aa,
+                   const RimBufs& rim, cudaStream_t st) {
   const int n = tilesX * tilesY;
   count_launches(1);
   if (tile_log2 == 4)
     raster_kernel<4><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, scr,
-                                                  tris, gbuf, depth, fmap, ec, ru, status, view);
+                                                  tris, gbuf, depth, fmap, ec, ru, status, view, silbits, hflag, aa, rim);
   else
     raster_kernel<5><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, scr,
-                                                  tris, gbuf, depth, fmap, ec, ru, status, view);
+                                                  tris, gbuf, depth, fmap, ec, ru, status, view, silbits, hflag, aa, rim);
 }
 
 void launch_raster_stats(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX,

@@ -252,12 +252,18 @@ __device__ __forceinline__ bool view_shades(const LightDev& Ld, float3 x) {
   return Ld.face < 0 || cube_face(make_float3(x.x - Ld.pos[0], x.y - Ld.pos[1], x.z - Ld.pos[2])) == Ld.face;
 }
 
-__global__ void shade_kernel(ShadeArgs a, float4* __restrict__ color) {
+__global__ void shade_kernel(ShadeArgs a, float4* __restrict__ color, float4* __restrict__ image,
+                             const uint8_t* __restrict__ hflag) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= a.W || j >= a.H) return;
   const size_t p = (size_t)j * a.W + i;
+  const bool to_image = image && !(hflag && hflag[p]);
   Surf s;
-  if (!load_surf(a, p, s)) { color[p] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
+  if (!load_surf(a, p, s)) {
+    color[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (to_image) image[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
   float3 rad = make_float3(0.f, 0.f, 0.f);
   for (int l = 0; l < a.L; ++l) {
     const LightDev& Ld = a.lights[l];
@@ -270,7 +276,10 @@ __global__ void shade_kernel(ShadeArgs a, float4* __restrict__ color) {
     rad.x += k * Ld.intensity[0]; rad.y += k * Ld.intensity[1]; rad.z += k * Ld.intensity[2];
   }
   const int mat = material_of(a, s.tri);
-  color[p] = make_float4(a.albedo[3 * mat] * rad.x, a.albedo[3 * mat + 1] * rad.y, a.albedo[3 * mat + 2] * rad.z, 1.f);
+  const float4 c = make_float4(a.albedo[3 * mat] * rad.x, a.albedo[3 * mat + 1] * rad.y, a.albedo[3 * mat + 2] * rad.z,
+                               1.f);
+  color[p] = c;
+  if (to_image) image[p] = c;
 }
 
 // Diagnostic copy of the shading stage's intermediate values at every pixel of
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
   const bool inb = i < a.W && j < a.H;
   const size_t p = inb ? (size_t)j * a.W + i : 0;
   const float4 gb4 = inb ? a.gbuf[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 gcol = inb ? g.gcolor[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 gcol = !inb ? make_float4(0.f, 0.f, 0.f, 0.f) : (g.hflag && g.hflag[p]) ? g.gcolor[p] : g.gimage[p];
   const int id = __float_as_int(gb4.x);
   const bool act = inb && id && (gcol.x != 0.f || gcol.y != 0.f || gcol.z != 0.f);
   Surf s;
@@ -787,10 +796,10 @@ void launch_normals_backward(const float* verts, int V, const int* tris, int T, 
                                                              dverts);
 }
 
-void launch_shade(const ShadeArgs& a, float4* color, cudaStream_t st) {
+void launch_shade(const ShadeArgs& a, float4* color, float4* image, const uint8_t* hflag, cudaStream_t st) {
   dim3 b(32, 8);
   count_launches(1);
-  shade_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, color);
+  shade_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, color, image, hflag);
 }
 
 void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st) {

@@ -55,7 +55,10 @@ def test_stage_bytes_model():
     b = bench.stage_bytes(sc)
     R2, WH = 256 * 256, 256 * 256
     assert b["filter"] == R2 * 17 and b["bwd_filter"] == R2 * 28
-    assert b["final_antialias"] == WH * 49
+    # the final antialiasing reads only its listed pixels; the shading writes the colour and the image
+    assert b["final_antialias"] == 0 and b["shade"] == WH * 49 + 8 * R2 + 24 * sc["verts"].shape[0]
+    listed = bench.stage_bytes(sc, [10, 20])
+    assert listed["final_antialias"] == 20 * 52 and listed["sm_antialias"] == 10 * 36
     assert set(b) >= {"raster", "sm_antialias", "shade", "bwd_sm_interp", "bwd_sm_antialias", "bwd_shade", "setup"}
 
 
