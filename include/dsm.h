@@ -154,6 +154,21 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
 dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_dverts,
                                float* dL_dlight, float* dL_dalbedo);
 
+/* Backward pass of the last dsm_render on ctx for the mean squared error
+ * L = sum (image - target)^2 / n over the n = H x W x 4 floats of its image
+ * (the loss of dsm_l2_loss_grad): the same gradients as dsm_l2_loss_grad
+ * followed by dsm_render_backward with its dL/dimage, whose arithmetic it
+ * uses (dL/dimage = 2 / n (image - target), 2 / n rounded to float), without
+ * writing dL/dimage; the kernels that read dL/dimage form it from image and
+ * target.  image: device, the image that dsm_render wrote (unchanged since);
+ * target: device, H x W x 4; loss: device, one float, overwritten with L (the
+ * squared errors summed in float64 over per-block float sums, so it agrees
+ * with dsm_l2_loss_grad's float sum to rounding).  Outputs as in
+ * dsm_render_backward.  DSM_ERR_INVALID_ARG when image, target or loss is
+ * NULL or the last forward had several cameras. */
+dsm_status dsm_render_backward_l2(dsm_ctx* ctx, const float* image, const float* target, float* loss,
+                                  float* dL_dverts, float* dL_dlight, float* dL_dalbedo);
+
 /* Forward pass seen by n_cameras cameras (1..DSM_MAX_CAMERAS) under the same
  * lights: each light's moment maps (Alg. 1) are built once and every camera
  * is shaded with all of them (Alg. 2 + Lambert, final antialiasing).
@@ -303,10 +318,10 @@ dsm_status dsm_filter_moments_noalloc(const float* in, float* out, int32_t res, 
                                       int32_t radius, int32_t kind, int32_t boundary, void* stream);
 
 /* ---- Batched frames.  n independent scenes (each a mesh, lights, a camera and
- * an L2 target) advanced by one call per step: forward, L2 loss
- * (dsm_l2_loss_grad) and backward of every scene.  The paper renders one view
- * at a time and has no batch call; per scene the step is exactly dsm_render,
- * dsm_l2_loss_grad and dsm_render_backward.
+ * an L2 target) advanced by one call per step: forward, L2 loss and backward
+ * of every scene.  The paper renders one view at a time and has no batch
+ * call; per scene the step is exactly dsm_render and dsm_render_backward_l2
+ * (the gradients of dsm_l2_loss_grad followed by dsm_render_backward).
  *
  * Each scene has its own context (dsm_batch_context: set its topology there
  * before the first step; its debug copies work as usual) and its own stream,
@@ -332,7 +347,8 @@ typedef struct dsm_batch_item {
   float*            image;         /* device, H x W x 4, written                   */
   const float*      target;        /* device, H x W x 4                             */
   float*            loss;          /* device, 1 float, written                      */
-  float*            dL_dimage;     /* device, H x W x 4, caller-owned scratch       */
+  float*            dL_dimage;     /* unused (the loss backward forms dL/dimage where
+                                      it reads it); may be NULL                       */
   float*            dL_dverts;     /* device, n_verts x 3, written (NULL: skipped)  */
   float*            dL_dlight;     /* device, n_lights x 6, written (NULL: skipped) */
   float*            dL_dalbedo;    /* device, n_materials x 3, written (NULL: skip) */

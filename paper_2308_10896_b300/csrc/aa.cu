@@ -285,10 +285,11 @@ __global__ void __launch_bounds__(256) aa_forward_list_kernel(AAArgs a, const V*
 // ------------------------------------------------------------------ adjoint
 // dL/dc_p = g_p + the pair terms; the t-gradient of each pair is scattered once
 // (by its left / top pixel) onto the clip coordinates of the edge endpoints.
-// aa_pair_adjoint: the term of pixel (i, j) from its pair in direction d.
-template <typename V>
+// aa_pair_adjoint: the term of pixel (i, j) from its pair in direction d;
+// gout[q] gives the output gradient of pixel q.
+template <typename V, typename G>
 __device__ __forceinline__ V aa_pair_adjoint(const AAArgs& a, int i, int j, int d, float4 gp, V g_p, const V* color,
-                                             const V* gout, float4* gclip) {
+                                             const G& gout, float4* gclip) {
   const int ni = i + nb_dx(d), nj = j + nb_dy(d);
   if (ni < 0 || nj < 0 || ni >= a.W || nj >= a.H) return V{};
   const size_t p = (size_t)j * a.W + i, q = (size_t)nj * a.W + ni;
@@ -324,8 +325,7 @@ __device__ __forceinline__ V aa_pair_adjoint(const AAArgs& a, int i, int j, int 
 }
 
 __global__ void __launch_bounds__(256) aa_backward4_list_kernel(AAArgs a, const float4* __restrict__ color,
-                                                                const float4* __restrict__ gout,
-                                                                float4* __restrict__ gcolor,
+                                                                ImageGrad gout, float4* __restrict__ gcolor,
                                                                 float4* __restrict__ gclip, AAWork w) {
   for_listed_pairs(w, [&](int k, int d, bool act) {
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f), g_p = g;
@@ -513,7 +513,7 @@ void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* dep
   sm_big_resolve_kernel<<<kMaxBig, 32, 0, st>>>(a.tris, big.tri, big.status, big.view, big.acc, gclip);
 }
 
-void launch_aa_backward4_list(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor,
+void launch_aa_backward4_list(const AAArgs& a, const float4* color, const ImageGrad& gout, float4* gcolor,
                               float4* gclip, const AAWork& w, cudaStream_t st) {
   count_launches(1);
   aa_backward4_list_kernel<<<kListGrid, 256, 0, st>>>(a, color, gout, gcolor, gclip, w);

@@ -82,10 +82,8 @@ dsm_status issue_step(dsm_batch* b, const dsm_batch_item* items, int n, const ds
         dsm_render(b->ctx[i], &it.mesh, it.lights, it.light_params, it.n_lights, &it.camera, &p, it.image);
     if (st != DSM_OK) return batch_fail(b, st, std::string("scene ") + std::to_string(i) + ": " +
                                                    dsm_last_error(b->ctx[i]));
-    const int64_t npx = (int64_t)it.camera.width * it.camera.height * 4;
-    st = dsm_l2_loss_grad(it.image, it.target, npx, it.loss, it.dL_dimage, s);
-    if (st != DSM_OK) return batch_fail(b, st, "loss of scene " + std::to_string(i));
-    st = dsm_render_backward(b->ctx[i], it.dL_dimage, it.dL_dverts, it.dL_dlight, it.dL_dalbedo);
+    // the loss and the backward in one (dL/dimage is formed where it is read)
+    st = dsm_render_backward_l2(b->ctx[i], it.image, it.target, it.loss, it.dL_dverts, it.dL_dlight, it.dL_dalbedo);
     if (st != DSM_OK) return batch_fail(b, st, std::string("scene ") + std::to_string(i) + ": " +
                                                    dsm_last_error(b->ctx[i]));
     if (it.host_loss && cudaMemcpyAsync(it.host_loss, it.loss, sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -147,7 +145,7 @@ dsm_ctx* dsm_batch_context(dsm_batch* b, int32_t i) {
 dsm_status dsm_batch_step(dsm_batch* b, const dsm_batch_item* items, int32_t n, const dsm_params* params) {
   if (!b || !items || !params || n < 1 || n > b->n) return DSM_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
-    if (!items[i].image || !items[i].target || !items[i].loss || !items[i].dL_dimage)
+    if (!items[i].image || !items[i].target || !items[i].loss)
       return batch_fail(b, DSM_ERR_INVALID_ARG, "scene " + std::to_string(i) + ": null image/target/loss buffer");
   cudaStream_t origin = (cudaStream_t)params->stream;
   const uint64_t sig = step_signature(items, n, params);

@@ -695,12 +695,19 @@ ShadeArgs shade_args(dsm_ctx* ctx, int c) {
   return sa;
 }
 
-ShadeGradArgs grad_args(dsm_ctx* ctx, int c, const float* gimage, float* dalbedo, int red_stride) {
+// Block-sum slots: dQ (20 per light view), direct terms (3), albedo (3 per
+// material, when their block sums fit shared memory), the squared error (1).
+int n_mat_red_of(const dsm_ctx* ctx) { return ctx->mesh.n_materials <= kMaxSharedMat ? ctx->mesh.n_materials : 0; }
+int loss_index_of(const dsm_ctx* ctx) { return 23 * ctx->L + 3 * n_mat_red_of(ctx); }
+int red_stride_of(const dsm_ctx* ctx) { return loss_index_of(ctx) + 1; }
+
+ShadeGradArgs grad_args(dsm_ctx* ctx, int c, const ImageGrad& gimage, float* dalbedo, int red_stride) {
   ViewBufs& cv = vbuf(ctx, ctx->L + c);
   ShadeGradArgs ga{};
   ga.gcolor = cv.gcolor.as<float4>();
-  ga.gimage = reinterpret_cast<const float4*>(gimage);
+  ga.gimage = gimage;
   ga.hflag = ctx->params.aa_final ? cv.hflag.as<uint8_t>() : nullptr;
+  ga.loss_index = gimage.g ? -1 : loss_index_of(ctx);
   ga.gpos = ctx->gpos.as<float4>();
   ga.gnormal = ctx->gnormal.as<float4>();
   ga.gclip = cv.gclip.as<float4>();
@@ -733,14 +740,14 @@ dsm_status camera_colour(dsm_ctx* ctx, int c, float* image, cudaStream_t st) {
 
 // Camera c, backward: final antialiasing adjoint, then the shading adjoint
 // (dL/dm into every light's gm, per-pixel gradients for the scatter).
-dsm_status camera_backward(dsm_ctx* ctx, int c, const float* gimage, float* dalbedo, int red_stride,
+dsm_status camera_backward(dsm_ctx* ctx, int c, const ImageGrad& gimage, float* dalbedo, int red_stride,
                            cudaStream_t st) {
   ViewBufs& cv = vbuf(ctx, ctx->L + c);
   if (ctx->params.aa_final) {
     // dL/dcolour of the listed pixels; the shading adjoint reads dL/dimage at the others
     StageTimer t(ctx, ST_BWD_FINAL_AA, st);
-    launch_aa_backward4_list(aa_args(ctx, cv), cv.color.as<float4>(), reinterpret_cast<const float4*>(gimage),
-                             cv.gcolor.as<float4>(), cv.gclip.as<float4>(), cv.aa_work(), st);
+    launch_aa_backward4_list(aa_args(ctx, cv), cv.color.as<float4>(), gimage, cv.gcolor.as<float4>(),
+                             cv.gclip.as<float4>(), cv.aa_work(), st);
   }
   if (ctx->aux_pending) DSM_CHECK(cudaStreamWaitEvent(st, ctx->ev_aux_done, 0));   // outputs cleared
   StageTimer t(ctx, ST_BWD_SHADE, st);
@@ -752,7 +759,7 @@ dsm_status camera_backward(dsm_ctx* ctx, int c, const float* gimage, float* dalb
 void camera_scatter(dsm_ctx* ctx, int c, float* dalbedo, int red_stride, cudaStream_t st) {
   StageTimer t(ctx, ST_BWD_SHADE_SCATTER, st);
   const ShadeArgs sa = shade_args(ctx, c);
-  const ShadeGradArgs ga = grad_args(ctx, c, nullptr, dalbedo, red_stride);
+  const ShadeGradArgs ga = grad_args(ctx, c, ImageGrad{}, dalbedo, red_stride);
   launch_shade_scatter(sa, ga, st);
   launch_shade_big_resolve(sa, ga, vbuf(ctx, ctx->L + c).big_tri.as<int>(), ctx->status.as<DevStatus>(), ctx->L + c,
                            st);
@@ -820,10 +827,6 @@ dsm_status rebuild_view(dsm_ctx* ctx, int w, bool sizing, bool maps, cudaStream_
 // vertex-position gradients as float4 per vertex, so that the scatter adds each
 // with one 16-byte atomic; light-matrix block sums; and per view the clip
 // gradients and big-triangle slots), sized for the current frame.
-int red_stride_of(const dsm_ctx* ctx) {
-  const int n_mat_red = ctx->mesh.n_materials <= kMaxSharedMat ? ctx->mesh.n_materials : 0;
-  return 23 * ctx->L + 3 * n_mat_red;
-}
 dsm_status ensure_backward_accumulators(dsm_ctx* ctx) {
   const int V = ctx->mesh.n_verts;
   DSM_CHECK(ctx->gnormal.ensure(sizeof(float4) * std::max(V, 1)));
@@ -1017,13 +1020,35 @@ dsm_status dsm_render(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_light* light
   return dsm_render_cameras(ctx, mesh, lights, light_params, n_lights, cam, 1, params, &image);
 }
 
-dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dimages, float* dL_dverts,
-                                       float* dL_dlight, float* dL_dalbedo) {
+namespace {
+
+// The backward of the last forward from dL/dimage of every camera, or (l2:
+// one camera) from the mean squared error of its image against a target,
+// whose value goes to *l2_loss.
+struct L2Target {
+  const float* image;
+  const float* target;
+  float* loss;
+};
+
+dsm_status backward_impl(dsm_ctx* ctx, const float* const* dL_dimages, const L2Target* l2, float* dL_dverts,
+                         float* dL_dlight, float* dL_dalbedo) {
   if (!ctx) return DSM_ERR_INVALID_ARG;
   if (!ctx->have_fwd) return fail(ctx, DSM_ERR_NO_FORWARD, "backward without a forward");
-  if (!dL_dimages) return fail(ctx, DSM_ERR_INVALID_ARG, "null dL_dimages");
-  for (int c = 0; c < ctx->C; ++c)
-    if (!dL_dimages[c]) return fail(ctx, DSM_ERR_INVALID_ARG, "null dL_dimage");
+  if (l2) {
+    if (ctx->C != 1) return fail(ctx, DSM_ERR_INVALID_ARG, "last forward had several cameras");
+    if (!l2->image || !l2->target || !l2->loss) return fail(ctx, DSM_ERR_INVALID_ARG, "null image, target or loss");
+  } else {
+    if (!dL_dimages) return fail(ctx, DSM_ERR_INVALID_ARG, "null dL_dimages");
+    for (int c = 0; c < ctx->C; ++c)
+      if (!dL_dimages[c]) return fail(ctx, DSM_ERR_INVALID_ARG, "null dL_dimage");
+  }
+  auto image_grad = [&](int c) {
+    if (!l2) return ImageGrad{reinterpret_cast<const float4*>(dL_dimages[c]), nullptr, nullptr, 0.f};
+    const int64_t n = (int64_t)ctx->cams[c].width * ctx->cams[c].height * 4;
+    return ImageGrad{nullptr, reinterpret_cast<const float4*>(l2->image), reinterpret_cast<const float4*>(l2->target),
+                     2.0f / (float)n};
+  };
   cudaStream_t st = ctx->stream;
   const dsm_mesh& mesh = ctx->mesh;
   const int V = mesh.n_verts, T = mesh.n_tris, L = ctx->L, C = ctx->C, NV = L + C;
@@ -1049,7 +1074,7 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
   if (sa != DSM_OK) return sa;
   DSM_CHECK(ctx->gN.ensure(sizeof(float) * 3 * std::max(V, 1)));
   DSM_CHECK(ctx->gface.ensure(sizeof(float) * 3 * std::max(T, 1)));
-  const int n_mat_red = mesh.n_materials <= kMaxSharedMat ? mesh.n_materials : 0;
+  const int n_mat_red = n_mat_red_of(ctx);
   const int red_stride = red_stride_of(ctx);
   for (int l = 0; l < L; ++l) {
     const size_t R2 = (size_t)ctx->light[l].res * ctx->light[l].res * sizeof(float2);
@@ -1124,7 +1149,7 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
         clear_view(cl, L + c);
         cl.launch(st);
       }
-      s = camera_backward(ctx, c, dL_dimages[c], dL_dalbedo, red_stride, st);
+      s = camera_backward(ctx, c, image_grad(c), dL_dalbedo, red_stride, st);
       if (s != DSM_OK) return s;
       camera_scatter(ctx, c, dL_dalbedo, red_stride, st);
       StageTimer t(ctx, ST_BWD_VERTEX, st);
@@ -1152,7 +1177,7 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
     DSM_CHECK(ensure_streams(ctx));
     if (C > 1) DSM_CHECK(fork_views(ctx, st, ctx->ev_bfork, L, NV));
     for (int c = 0; c < C; ++c) {
-      dsm_status s = camera_backward(ctx, c, dL_dimages[c], dL_dalbedo, red_stride,
+      dsm_status s = camera_backward(ctx, c, image_grad(c), dL_dalbedo, red_stride,
                                      C > 1 ? view_stream(ctx, L + c, st) : st);
       if (s != DSM_OK) return s;
     }
@@ -1174,7 +1199,8 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
   {
     StageTimer t(ctx, ST_BWD_VERTEX, st);
     launch_light_sums(ctx->red.as<double>(), red_stride, L, n_mat_red, ctx->lights_dev.as<LightDev>(), ctx->n_user,
-                      ctx->gQ.as<double>(), ctx->gdirect.as<double>(), dL_dalbedo, dL_dlight, st);
+                      ctx->gQ.as<double>(), ctx->gdirect.as<double>(), dL_dalbedo, dL_dlight, l2 ? l2->loss : nullptr,
+                      (int64_t)ctx->cams[0].width * ctx->cams[0].height * 4, st);
   }
   if (ctx->aux_pending) {
     // the side stream's clear has been waited for by every shading adjoint;
@@ -1186,11 +1212,24 @@ dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dima
   return DSM_OK;
 }
 
+}  // namespace
+
+dsm_status dsm_render_cameras_backward(dsm_ctx* ctx, const float* const* dL_dimages, float* dL_dverts,
+                                       float* dL_dlight, float* dL_dalbedo) {
+  return backward_impl(ctx, dL_dimages, nullptr, dL_dverts, dL_dlight, dL_dalbedo);
+}
+
 dsm_status dsm_render_backward(dsm_ctx* ctx, const float* dL_dimage, float* dL_dverts, float* dL_dlight,
                                float* dL_dalbedo) {
   if (!ctx) return DSM_ERR_INVALID_ARG;
   if (ctx->have_fwd && ctx->C != 1) return fail(ctx, DSM_ERR_INVALID_ARG, "last forward had several cameras");
   return dsm_render_cameras_backward(ctx, &dL_dimage, dL_dverts, dL_dlight, dL_dalbedo);
+}
+
+dsm_status dsm_render_backward_l2(dsm_ctx* ctx, const float* image, const float* target, float* loss,
+                                  float* dL_dverts, float* dL_dlight, float* dL_dalbedo) {
+  const L2Target l2{image, target, loss};
+  return backward_impl(ctx, nullptr, &l2, dL_dverts, dL_dlight, dL_dalbedo);
 }
 
 dsm_status dsm_set_grad_mask(dsm_ctx* ctx, int32_t flags) {

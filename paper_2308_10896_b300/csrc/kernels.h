@@ -87,19 +87,38 @@ struct ShadeArgs {
   float ec;                           // exponential warp of the moments (0: variance shadow maps)
 };
 
+// dL/dimage of a camera: given (g), or, for g NULL, that of the mean squared
+// error L = sum (image - target)^2 / n over the n floats of the image, whose
+// gradient 2 / n (image - target) is formed in the arithmetic of
+// dsm_l2_loss_grad (scale = 2 / n rounded to float32, then one product).
+struct ImageGrad {
+  const float4* g;
+  const float4* image;
+  const float4* target;
+  float scale;
+  __device__ __forceinline__ float4 operator[](size_t p) const {
+    if (g) return g[p];
+    const float4 a = image[p], b = target[p];
+    return make_float4(scale * (a.x - b.x), scale * (a.y - b.y), scale * (a.z - b.z), scale * (a.w - b.w));
+  }
+};
+
 struct ShadeGradArgs {
   // dL/d colour before the final antialiasing: gcolor at the pixels flagged by
   // the camera's antialiasing detection (hflag), dL/dimage gimage elsewhere
   // (hflag NULL: gimage everywhere)
   const float4* gcolor;
-  const float4* gimage;
+  ImageGrad gimage;
   const uint8_t* hflag;
+  int loss_index;                     // with the mean squared error: its sum of squares goes to red[loss_index]
+                                      // (per block slot); -1 otherwise
   float4* gpos;                       // V, dL/d vertex position through the camera's interpolation (xyz)
   float4* gnormal;                    // V, dL/d unit vertex normal (xyz)
   float4* gclip;                      // V, dL/d camera clip
   float* dalbedo;                     // M x 3
   float2* gm[kMaxLightViews];         // dL/d(m1, m2) texel maps
-  double* red;                        // kRedSlots x red_stride: [dQ (L x 20) | direct (L x 3) | albedo (M x 3)]
+  double* red;                        // kRedSlots x red_stride: [dQ (L x 20) | direct (L x 3) | albedo (M x 3) |
+                                      //   squared error (1)]
   int red_stride;
   const int* big;                     // camera view big-triangle index per triangle
   float* big_acc;                     // kMaxBig x kBigSlots x kBigStrideCam
@@ -235,7 +254,7 @@ void launch_aa_forward4_list(const AAArgs& a, const float4* color, float4* out, 
 void launch_sm_aa_adjoint_list(const AAArgs& a, const float2* fmap, const float2* gft, float4* gclip, float* gf_out,
                                float ec, const AAWork& w, cudaStream_t st);
 // dL/dcolour at the listed pixels (every other pixel's is dL/dimage itself).
-void launch_aa_backward4_list(const AAArgs& a, const float4* color, const float4* gout, float4* gcolor,
+void launch_aa_backward4_list(const AAArgs& a, const float4* color, const ImageGrad& gout, float4* gcolor,
                               float4* gclip, const AAWork& w, cudaStream_t st);
 void launch_sm_interp_adjoint(const AAArgs& a, const float* gf, const float* depth, float4* gclip,
                               const BigArgs& big, cudaStream_t st);
@@ -290,8 +309,11 @@ void launch_vertex_backward(const float* verts, int V, const float* viewM, int n
                             const VertGradPtrs& gp, float* dverts, double* red, int red_stride, cudaStream_t st);
 void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const int* big_tri,
                               const DevStatus* status, int view, cudaStream_t st);
+// With loss (the mean squared error of a backward against a target): also
+// the loss, the block sums' squared error over the n_img floats of the image.
 void launch_light_sums(const double* red, int red_stride, int L, int n_mat_red, const LightDev* lights, int n_user,
-                       double* gQ, double* gdirect, float* dalbedo, float* dlight, cudaStream_t st);
+                       double* gQ, double* gdirect, float* dalbedo, float* dlight, float* loss, int64_t n_img,
+                       cudaStream_t st);
 void launch_l2(const float* img, const float* tgt, int64_t n, float* loss, float* grad, cudaStream_t st);
 
 }  // namespace dsm

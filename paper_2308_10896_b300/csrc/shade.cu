@@ -353,7 +353,9 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
   __shared__ float sQ[kMaxLightViews * 20];
   __shared__ float sD[kMaxLightViews * 3];
   __shared__ float sA[kMaxSharedMat * 3];
+  __shared__ float sL;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid == 0) sL = 0.f;
   const bool mat_shared = a.n_mat <= kMaxSharedMat;
   for (int k = tid; k < kMaxLightViews * 20; k += 256) sQ[k] = 0.f;
   for (int k = tid; k < kMaxLightViews * 3; k += 256) sD[k] = 0.f;
@@ -363,7 +365,20 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
   const bool inb = i < a.W && j < a.H;
   const size_t p = inb ? (size_t)j * a.W + i : 0;
   const float4 gb4 = inb ? a.gbuf[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 gcol = !inb ? make_float4(0.f, 0.f, 0.f, 0.f) : (g.hflag && g.hflag[p]) ? g.gcolor[p] : g.gimage[p];
+  float4 gcol = make_float4(0.f, 0.f, 0.f, 0.f);
+  float sq = 0.f;   // squared error of the pixel (mean squared error backward)
+  if (inb) {
+    const bool flagged = g.hflag && g.hflag[p];
+    if (g.loss_index >= 0) {
+      const float4 im = g.gimage.image[p], tg = g.gimage.target[p];
+      const float4 d = make_float4(im.x - tg.x, im.y - tg.y, im.z - tg.z, im.w - tg.w);
+      sq = d.x * d.x + d.y * d.y + d.z * d.z + d.w * d.w;
+      const float sc = g.gimage.scale;
+      gcol = flagged ? g.gcolor[p] : make_float4(sc * d.x, sc * d.y, sc * d.z, sc * d.w);
+    } else {
+      gcol = flagged ? g.gcolor[p] : g.gimage[p];
+    }
+  }
   const int id = __float_as_int(gb4.x);
   const bool act = inb && id && (gcol.x != 0.f || gcol.y != 0.f || gcol.z != 0.f);
   Surf s;
@@ -519,6 +534,11 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
     float* dst = mat_shared ? sA : g.dalbedo;
     atomicAdd(&dst[3 * mat], ga.x); atomicAdd(&dst[3 * mat + 1], ga.y); atomicAdd(&dst[3 * mat + 2], ga.z);
   }
+  if (g.loss_index >= 0) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
+    if ((threadIdx.x & 31) == 0 && sq != 0.f) atomicAdd(&sL, sq);
+  }
   // per-pixel dL/dx and dL/d(interpolated normal) for the scatter pass
   if (inb) {
     float3 gnt = make_float3(0.f, 0.f, 0.f);
@@ -541,6 +561,7 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
   if (mat_shared)
     for (int k = tid; k < a.n_mat * 3; k += 256)
       if (sA[k] != 0.f) atomicAdd(&red[a.L * 23 + k], (double)sA[k]);
+  if (g.loss_index >= 0 && tid == 0 && sL != 0.f) atomicAdd(&red[g.loss_index], (double)sL);
 }
 
 // Per-triangle scatter of the camera interpolation adjoint: from the per-pixel
@@ -708,9 +729,10 @@ __global__ void __launch_bounds__(1024) light_sums_kernel(const double* __restri
                                                           int n_mat_red, const LightDev* __restrict__ lights,
                                                           int n_user, double* __restrict__ gQ,
                                                           double* __restrict__ gdirect, float* __restrict__ dalbedo,
-                                                          float* __restrict__ dlight) {
+                                                          float* __restrict__ dlight, float* __restrict__ loss,
+                                                          double inv_n) {
   static_assert(kRedSlots % 4 == 0, "four threads per entry");
-  const int n = L * 23 + n_mat_red * 3;
+  const int n = L * 23 + n_mat_red * 3 + (loss ? 1 : 0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int base = 0; base < 4 * n; base += blockDim.x) {
     const int e = base + threadIdx.x, k = e >> 2, part = e & 3;
@@ -722,7 +744,8 @@ __global__ void __launch_bounds__(1024) light_sums_kernel(const double* __restri
     if (k < n && part == 0) {
       if (k < L * 20) gQ[k] = acc;
       else if (k < L * 23) gdirect[k - L * 20] = acc;
-      else dalbedo[k - L * 23] += (float)acc;
+      else if (k < L * 23 + n_mat_red * 3) dalbedo[k - L * 23] += (float)acc;
+      else *loss = (float)(acc * inv_n);   // the mean squared error
     }
   }
   __syncthreads();   // this block's writes of gQ and gdirect are visible to all its threads
@@ -829,10 +852,12 @@ void launch_shade_big_resolve(const ShadeArgs& a, const ShadeGradArgs& g, const 
 }
 
 void launch_light_sums(const double* red, int red_stride, int L, int n_mat_red, const LightDev* lights, int n_user,
-                       double* gQ, double* gdirect, float* dalbedo, float* dlight, cudaStream_t st) {
-  if (L * 23 + n_mat_red * 3 == 0 && n_user == 0) return;
+                       double* gQ, double* gdirect, float* dalbedo, float* dlight, float* loss, int64_t n_img,
+                       cudaStream_t st) {
+  if (L * 23 + n_mat_red * 3 == 0 && n_user == 0 && !loss) return;
   count_launches(1);
-  light_sums_kernel<<<1, 1024, 0, st>>>(red, red_stride, L, n_mat_red, lights, n_user, gQ, gdirect, dalbedo, dlight);
+  light_sums_kernel<<<1, 1024, 0, st>>>(red, red_stride, L, n_mat_red, lights, n_user, gQ, gdirect, dalbedo, dlight,
+                                        loss, loss ? 1.0 / (double)n_img : 0.0);
 }
 
 void launch_l2(const float* img, const float* tgt, int64_t n, float* loss, float* grad, cudaStream_t st) {

@@ -34,7 +34,7 @@ EXPORTED = ["dsm_create", "dsm_destroy", "dsm_set_topology", "dsm_render", "dsm_
             "dsm_batch_kernels_per_step", "dsm_batch_last_error", "dsm_render_cameras",
             "dsm_render_cameras_backward", "dsm_memory_bytes", "dsm_adam_step", "dsm_set_tuning",
             "dsm_get_tuning", "dsm_autotune", "dsm_batch_autotune", "dsm_bounded_wait_probe",
-            "dsm_raster_stats", "dsm_set_grad_mask"]
+            "dsm_raster_stats", "dsm_set_grad_mask", "dsm_render_backward_l2"]
 
 
 class DsmError(RuntimeError):
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dsm_render": ([P, ctypes.POINTER(Mesh), ctypes.POINTER(Light), P, I32, ctypes.POINTER(Camera),
                         ctypes.POINTER(Params), P], I32),
         "dsm_render_backward": ([P, P, P, P, P], I32),
+        "dsm_render_backward_l2": ([P, P, P, P, P, P, P], I32),
         "dsm_l2_loss_grad": ([P, P, I64, P, P, P], I32),
         "dsm_filter_moments": ([P, P, P, I32, ctypes.c_float, I32, I32, I32, P], I32),
         "dsm_sync": ([P], I32),
@@ -247,6 +248,10 @@ class Context:
     def render_backward(self, dL_dimage, dverts=None, dlight=None, dalbedo=None):
         self._check(self.lib.dsm_render_backward(self.h, _ptr(dL_dimage), _ptr(dverts), _ptr(dlight),
                                                  _ptr(dalbedo)), self.h)
+
+    def render_backward_l2(self, image, target, loss, dverts=None, dlight=None, dalbedo=None):
+        self._check(self.lib.dsm_render_backward_l2(self.h, _ptr(image), _ptr(target), _ptr(loss), _ptr(dverts),
+                                                    _ptr(dlight), _ptr(dalbedo)), self.h)
 
     def render_cameras(self, mesh: Mesh, lights, light_params: torch.Tensor, cameras, params: Params, images):
         arr = (Light * max(1, len(lights)))(*lights)
@@ -415,6 +420,15 @@ class Renderer:
     def backward(self, dL_dimage: torch.Tensor, dverts=None, dlight=None, dalbedo=None):
         dverts, dlight, dalbedo = self._grads(dverts, dlight, dalbedo)
         self.ctx.render_backward(dL_dimage.contiguous(), dverts, dlight, dalbedo)
+        return dverts, dlight[:len(self.lights)], dalbedo
+
+    def backward_l2(self, image: torch.Tensor, target: torch.Tensor, loss: torch.Tensor, dverts=None, dlight=None,
+                    dalbedo=None):
+        """Backward of the mean squared error of the last forward's image
+        against target (dsm_render_backward_l2); loss (one float on the device)
+        receives its value."""
+        dverts, dlight, dalbedo = self._grads(dverts, dlight, dalbedo)
+        self.ctx.render_backward_l2(image.contiguous(), target.contiguous(), loss, dverts, dlight, dalbedo)
         return dverts, dlight[:len(self.lights)], dalbedo
 
     def forward_cameras(self, cameras: list, verts=None, light_params=None, albedo=None, images=None,

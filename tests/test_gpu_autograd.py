@@ -170,3 +170,31 @@ def test_central_difference_of_gpu_forward(name, seed):
             "oracle_fd": fd_o, "oracle_grad_dot_e": dd_o, "rounding_bound": noise, "free_vertices": free})
     assert abs(fd - dd) <= 1e-2 * abs(dd) + noise, f"central difference {fd:.6g} vs grad . e {dd:.6g}"
     assert abs(fd - fd_o) <= 1e-2 * abs(fd_o) + noise, f"GPU central difference {fd:.6g} vs oracle's {fd_o:.6g}"
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_l2_backward_equals_loss_then_backward(name):
+    """dsm_render_backward_l2 (the mean squared error's backward, dL/dimage
+    formed where it is read) against dsm_l2_loss_grad followed by
+    dsm_render_backward: the same loss to float rounding, the same gradients up
+    to the order of the float atomics."""
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    sc = SCENES[name]()
+    tgt = torch.as_tensor(oracle_target(sc, 0.01, 7).astype(np.float32), device="cuda")
+    r = dsm.Renderer(sc)
+    image = r.forward()
+    lbuf = torch.zeros(1, device="cuda")
+    gimg = torch.empty_like(image)
+    dsm.l2_loss_grad(image, tgt, lbuf, gimg)
+    ref = [x.clone() for x in r.backward(gimg)]
+    loss = torch.full((1,), -1.0, device="cuda")
+    got = r.backward_l2(image, tgt, loss)
+    r.ctx.sync()
+    rec = {"test": "l2_backward", "case": name, "loss": float(loss.item()), "loss_ref": float(lbuf.item())}
+    assert abs(float(loss.item()) - float(lbuf.item())) <= 1e-6 * abs(float(lbuf.item())) + 1e-12
+    for nm, a, b in zip(("verts", "light", "albedo"), got, ref):
+        rel = float((a - b).norm() / max(float(b.norm()), 1e-30))
+        rec[nm] = rel
+        assert rel <= 1e-5, f"dL/d{nm}: fused loss backward vs loss then backward, relative L2 {rel:.3g}"
+    report(rec)
