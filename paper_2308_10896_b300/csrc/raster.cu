@@ -304,14 +304,15 @@ __global__ void transform_all_kernel(const float* __restrict__ verts, int V, con
                                      const float* __restrict__ viewMlo, ViewSetupArgs a, DevStatus* status) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   // the binning's tile counters, big-triangle counts and list and unit
-  // totals, and the antialiasing work lists, start this frame empty
+  // totals, and the antialiasing work lists of these views start this frame
+  // empty (other views' entries may be in use by a concurrent setup)
   for (int w = 0; w < a.n; ++w)
     for (int k = v; k < a.tiles[w]; k += gridDim.x * blockDim.x) a.count[w][k] = 0;
-  if (v < kMaxViews) {
-    status->big_count[v] = 0;
-    status->needed_pairs[v] = 0;
-    status->units[v] = 0;
-    status->split[v] = 0;
+  if (v < a.n) {
+    status->big_count[a.view0 + v] = 0;
+    status->needed_pairs[a.view0 + v] = 0;
+    status->units[a.view0 + v] = 0;
+    status->split[a.view0 + v] = 0;
   }
   if (v < a.n && a.aa_count[v]) *a.aa_count[v] = 0;
   if (v >= V) return;

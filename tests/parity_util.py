@@ -33,6 +33,23 @@ def assert_close(gpu, ref, what, atol=ATOL, rtol=RTOL):
         raise AssertionError(f"{what}: excess {worst:.3g} at {idx}: gpu {g} oracle {o}")
 
 
+def loss_tolerance(n: int, loss: float) -> float:
+    """Bound on |a - b| for two float32 evaluations of the mean squared error
+    over n floats: dsm_l2_loss_grad (a float sum per thread over its
+    grid-stride elements, a 256-lane tree of 8 levels, the block sums divided
+    by n and added by float atomics, one per block of at most 148 * 8 blocks)
+    and dsm_render_backward_l2 (four squares per pixel, a warp tree of 5
+    levels, at most 8 float atomics per block, float64 above).  All terms are
+    non-negative, so each float addition along a chain adds at most one unit
+    roundoff u = 2^-24 of the total: |error| <= (additions in the longest
+    chain) u loss per evaluation."""
+    blocks = min((n + 255) // 256, 148 * 8)
+    per_thread = -(-n // (blocks * 256))
+    chain_l2 = per_thread + 1 + 8 + 1 + blocks
+    chain_fused = 4 + 1 + 5 + 8 + 2
+    return (chain_l2 + chain_fused) * 2.0 ** -24 * abs(loss) + 1e-12
+
+
 def report(record: dict):
     """Append one JSON line of measured parity figures to the file named by the
     environment variable DSM_PARITY_REPORT (nothing when it is unset)."""

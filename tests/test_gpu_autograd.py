@@ -14,7 +14,7 @@ import torch
 
 import scenes
 from oracle import dsm_oracle as O
-from parity_util import GpuFrame, camera_band, grad_close_strict, oracle_target, report
+from parity_util import GpuFrame, camera_band, grad_close_strict, loss_tolerance, oracle_target, report
 
 pytestmark = pytest.mark.gpu
 
@@ -176,8 +176,9 @@ def test_central_difference_of_gpu_forward(name, seed):
 def test_l2_backward_equals_loss_then_backward(name):
     """dsm_render_backward_l2 (the mean squared error's backward, dL/dimage
     formed where it is read) against dsm_l2_loss_grad followed by
-    dsm_render_backward: the same loss to float rounding, the same gradients up
-    to the order of the float atomics."""
+    dsm_render_backward: the same loss within the two float sums' rounding
+    bound (parity_util.loss_tolerance), the same gradients up to the order of
+    the float atomics."""
     from paper_2308_10896_b300 import dsm
     torch.cuda.set_device(0)
     sc = SCENES[name]()
@@ -192,7 +193,7 @@ def test_l2_backward_equals_loss_then_backward(name):
     got = r.backward_l2(image, tgt, loss)
     r.ctx.sync()
     rec = {"test": "l2_backward", "case": name, "loss": float(loss.item()), "loss_ref": float(lbuf.item())}
-    assert abs(float(loss.item()) - float(lbuf.item())) <= 1e-6 * abs(float(lbuf.item())) + 1e-12
+    assert abs(float(loss.item()) - float(lbuf.item())) <= loss_tolerance(image.numel(), float(lbuf.item()))
     for nm, a, b in zip(("verts", "light", "albedo"), got, ref):
         rel = float((a - b).norm() / max(float(b.norm()), 1e-30))
         rec[nm] = rel

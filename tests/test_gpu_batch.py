@@ -1,14 +1,17 @@
 """Batched frames (dsm_batch_step): every scene's forward, L2 loss and backward
 in one call, replayed from a CUDA graph after the first step, give the same
 results as rendering each scene on its own (dsm_render, dsm_l2_loss_grad,
-dsm_render_backward): images and losses identical (the forward has no
-order-dependent arithmetic), gradients equal up to the order of float atomics.
+dsm_render_backward): images identical (the forward has no order-dependent
+arithmetic), losses equal within the rounding bound of their two float sums
+(the batch takes the loss from dsm_render_backward_l2), gradients equal up to
+the order of float atomics.
 Device data changed between steps is picked up by the replayed graph."""
 import numpy as np
 import pytest
 import torch
 
 import scenes
+from parity_util import loss_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +65,8 @@ def test_batch_matches_single_renders_and_follows_device_data():
             tgt = torch.as_tensor(targets[k], device="cuda")
             img, loss, dv, dl, da = _single(dsm, sc, d["verts"].clone(), tgt)
             assert torch.equal(d["image"].cpu(), img), f"step {step} scene {k}: image differs"
-            assert abs(float(d["loss"].item()) - loss) <= 1e-6 * abs(loss) + 1e-12, f"step {step} scene {k}: loss"
+            assert abs(float(d["loss"].item()) - loss) <= loss_tolerance(img.numel(), loss), \
+                f"step {step} scene {k}: loss"
             L = len(sc["lights"])
             for name, g, o in (("verts", d["dverts"].cpu(), dv), ("light", d["dlight"][:L].cpu(), dl),
                                ("albedo", d["dalbedo"].cpu(), da)):
@@ -119,7 +123,7 @@ def test_single_scene_batch_records_its_view_streams():
         b.sync()
         img, loss, dv, dl, da = _single(dsm, sc, d["verts"].clone(), torch.as_tensor(target, device="cuda"))
         assert torch.equal(d["image"].cpu(), img), f"step {step}: image differs"
-        assert abs(float(d["loss"].item()) - loss) <= 1e-6 * abs(loss) + 1e-12
+        assert abs(float(d["loss"].item()) - loss) <= loss_tolerance(img.numel(), loss)
         assert _rel(d["dverts"].cpu(), dv) <= 1e-4 and _rel(d["dlight"][:3].cpu(), dl) <= 1e-4
     b.close()
 
@@ -150,7 +154,7 @@ def test_host_staging_inside_the_recorded_step():
         img, loss, dv, dl, da = _single(dsm, dict(sc, albedo=h_alb.numpy()), h_verts.cuda(), target)
         assert torch.equal(d["image"].cpu(), img), f"step {step}: image differs"
         assert float(h_loss[0]) == float(d["loss"].item())
-        assert abs(float(h_loss[0]) - loss) <= 1e-6 * abs(loss) + 1e-12
+        assert abs(float(h_loss[0]) - loss) <= loss_tolerance(img.numel(), loss)
         assert _rel(d["dverts"].cpu(), dv) <= 1e-4
     with pytest.raises(ValueError):
         b.set_host_io(0, verts=torch.zeros(3))   # not pinned
