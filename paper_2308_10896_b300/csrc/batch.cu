@@ -178,7 +178,8 @@ dsm_status dsm_batch_step(dsm_batch* b, const dsm_batch_item* items, int32_t n, 
     return st;
   }
   if (ce != cudaSuccess || !graph) return batch_fail(b, DSM_ERR_CUDA, "end capture");
-  const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+  // node priorities: kernels keep the priority of the stream they were recorded on
+  const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (ie != cudaSuccess) {
     b->exec = nullptr;

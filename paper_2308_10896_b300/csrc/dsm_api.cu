@@ -124,6 +124,12 @@ struct dsm_ctx {
   uint64_t sized_sig = 0;
   // internal streams: one per view (lights, then cameras), fork/join events
   cudaStream_t vs[kMaxViews] = {};
+  // per camera: the final antialiasing adjoint and the shading adjoint of its
+  // listed pixels, beside the shading adjoint's grid pass; at the device's
+  // highest stream priority, so that the listed pixels' pass takes SMs as the
+  // grid pass's CTAs retire instead of waiting for all of them
+  cudaStream_t cside[DSM_MAX_CAMERAS] = {};
+  cudaEvent_t ev_cside[DSM_MAX_CAMERAS] = {}, ev_cside_done[DSM_MAX_CAMERAS] = {};
   cudaStream_t aux = nullptr;            // side stream of the backward's output clear
   cudaEvent_t ev_aux = nullptr, ev_aux_done = nullptr;
   bool aux_pending = false;              // the shading adjoints wait for ev_aux_done
@@ -239,12 +245,20 @@ cudaError_t ensure_streams(dsm_ctx* c) {
   cudaError_t e;
   for (auto& v : c->vs)
     if ((e = cudaStreamCreateWithFlags(&v, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  int least = 0, greatest = 0;
+  if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess) return e;
+  for (int k = 0; k < DSM_MAX_CAMERAS; ++k) {
+    if ((e = cudaStreamCreateWithPriority(&c->cside[k], cudaStreamNonBlocking, greatest)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&c->ev_cside[k], cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&c->ev_cside_done[k], cudaEventDisableTiming)) != cudaSuccess) return e;
+  }
   if ((e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
   if ((e = cudaEventCreateWithFlags(&c->ev_bfork, cudaEventDisableTiming)) != cudaSuccess) return e;
   if ((e = cudaEventCreateWithFlags(&c->ev_sil, cudaEventDisableTiming)) != cudaSuccess) return e;
   for (auto& ev : c->ev_join)
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
-  if ((e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  // (the clear of the caller's outputs: a short launch that the shading adjoint waits for)
+  if ((e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, greatest)) != cudaSuccess) return e;
   if ((e = cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming)) != cudaSuccess) return e;
   if ((e = cudaEventCreateWithFlags(&c->ev_aux_done, cudaEventDisableTiming)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -356,6 +370,11 @@ void dsm_destroy(dsm_ctx* ctx) {
   if (ctx->hstatus) cudaFreeHost(ctx->hstatus);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto v : ctx->vs) if (v) cudaStreamDestroy(v);
+  for (int k = 0; k < DSM_MAX_CAMERAS; ++k) {
+    if (ctx->cside[k]) cudaStreamDestroy(ctx->cside[k]);
+    if (ctx->ev_cside[k]) cudaEventDestroy(ctx->ev_cside[k]);
+    if (ctx->ev_cside_done[k]) cudaEventDestroy(ctx->ev_cside_done[k]);
+  }
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
   if (ctx->ev_aux) cudaEventDestroy(ctx->ev_aux);
   if (ctx->ev_aux_done) cudaEventDestroy(ctx->ev_aux_done);
@@ -743,15 +762,39 @@ dsm_status camera_colour(dsm_ctx* ctx, int c, float* image, cudaStream_t st) {
 dsm_status camera_backward(dsm_ctx* ctx, int c, const ImageGrad& gimage, float* dalbedo, int red_stride,
                            cudaStream_t st) {
   ViewBufs& cv = vbuf(ctx, ctx->L + c);
-  if (ctx->params.aa_final) {
-    // dL/dcolour of the listed pixels; the shading adjoint reads dL/dimage at the others
-    StageTimer t(ctx, ST_BWD_FINAL_AA, st);
-    launch_aa_backward4_list(aa_args(ctx, cv), cv.color.as<float4>(), gimage, cv.gcolor.as<float4>(),
-                             cv.gclip.as<float4>(), cv.aa_work(), st);
+  const ShadeArgs sa = shade_args(ctx, c);
+  const ShadeGradArgs ga = grad_args(ctx, c, gimage, dalbedo, red_stride);
+  // the listed pixels on the camera's side stream: dL/dcolour (the
+  // antialiasing adjoint), then their shading adjoint; beside it the grid
+  // pass, which reads dL/dimage
+  cudaStream_t side = st;
+  if (ctx->params.aa_final && !ctx->prof) {
+    DSM_CHECK(ensure_streams(ctx));
+    side = ctx->cside[c];
+    DSM_CHECK(cudaEventRecord(ctx->ev_cside[c], st));
+    DSM_CHECK(cudaStreamWaitEvent(side, ctx->ev_cside[c], 0));
   }
-  if (ctx->aux_pending) DSM_CHECK(cudaStreamWaitEvent(st, ctx->ev_aux_done, 0));   // outputs cleared
-  StageTimer t(ctx, ST_BWD_SHADE, st);
-  launch_shade_backward(shade_args(ctx, c), grad_args(ctx, c, gimage, dalbedo, red_stride), st);
+  if (ctx->params.aa_final) {
+    StageTimer t(ctx, ST_BWD_FINAL_AA, side);
+    launch_aa_backward4_list(aa_args(ctx, cv), cv.color.as<float4>(), gimage, cv.gcolor.as<float4>(),
+                             cv.gclip.as<float4>(), cv.aa_work(), side);
+  }
+  if (ctx->aux_pending) {   // outputs cleared
+    DSM_CHECK(cudaStreamWaitEvent(st, ctx->ev_aux_done, 0));
+    if (side != st) DSM_CHECK(cudaStreamWaitEvent(side, ctx->ev_aux_done, 0));
+  }
+  {
+    StageTimer t(ctx, ST_BWD_SHADE, st);
+    launch_shade_backward(sa, ga, st);
+  }
+  if (ctx->params.aa_final) {
+    StageTimer t(ctx, ST_BWD_SHADE, side);
+    launch_shade_backward_listed(sa, ga, cv.aa_work(), side);
+  }
+  if (side != st) {
+    DSM_CHECK(cudaEventRecord(ctx->ev_cside_done[c], side));
+    DSM_CHECK(cudaStreamWaitEvent(st, ctx->ev_cside_done[c], 0));
+  }
   return DSM_OK;
 }
 

@@ -303,7 +303,13 @@ void launch_normals_backward(const float* verts, int V, const int* tris, int T, 
 void launch_shade(const ShadeArgs& a, float4* color, float4* image, const uint8_t* hflag, cudaStream_t st);
 void launch_shade_probe(const ShadeArgs& a, int l, float4* out, cudaStream_t st);
 void launch_sm_band_mask(const uint8_t* hflag, int n, float2* gft, float* gf, cudaStream_t st);
+// The shading adjoint in two passes that may run side by side: the grid pass
+// over every pixel that the final antialiasing did not list (and the squared
+// error of every pixel), and the pass over the listed pixels, after the
+// antialiasing adjoint wrote their dL/dcolour.  Without the final
+// antialiasing (g.hflag NULL) the grid pass takes every pixel.
 void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);
+void launch_shade_backward_listed(const ShadeArgs& a, const ShadeGradArgs& g, const AAWork& w, cudaStream_t st);
 void launch_shade_scatter(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st);
 void launch_vertex_backward(const float* verts, int V, const float* viewM, int n_views, int n_lights,
                             const VertGradPtrs& gp, float* dverts, double* red, int red_stride, cudaStream_t st);

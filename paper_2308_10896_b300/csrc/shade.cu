@@ -349,7 +349,8 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[N]) {
 // dL/d(m1, m2) (bilinear adjoint), reduces dL/dQ, the direct light terms and
 // the albedo gradient per block (slot copies), and writes the per-pixel
 // dL/d world position and dL/d interpolated normal for shade_scatter_kernel.
-__global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g) {
+template <bool kListed>
+__global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, ShadeGradArgs g, AAWork w) {
   __shared__ float sQ[kMaxLightViews * 20];
   __shared__ float sD[kMaxLightViews * 3];
   __shared__ float sA[kMaxSharedMat * 3];
@@ -361,23 +362,26 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
   for (int k = tid; k < kMaxLightViews * 3; k += 256) sD[k] = 0.f;
   for (int k = tid; k < kMaxSharedMat * 3; k += 256) sA[k] = 0.f;
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  const bool inb = i < a.W && j < a.H;
-  const size_t p = inb ? (size_t)j * a.W + i : 0;
+  // One pixel (every lane of the warp calls it; inb false: no pixel).  The
+  // grid pass (kListed false) takes every pixel except those on the final
+  // antialiasing's work list, and the squared error of all of them; the list
+  // pass (kListed true) takes the listed ones, whose dL/dcolour the
+  // antialiasing adjoint writes, so that the grid pass need not wait for it.
+  auto pixel = [&](const int i, const int j, const bool inb_) {
+  const size_t p = inb_ ? (size_t)j * a.W + i : 0;
+  const bool flagged = kListed || (inb_ && g.hflag && g.hflag[p]);
+  const bool inb = inb_ && (kListed || !flagged);   // this pass's pixel
   const float4 gb4 = inb ? a.gbuf[p] : make_float4(0.f, 0.f, 0.f, 0.f);
   float4 gcol = make_float4(0.f, 0.f, 0.f, 0.f);
   float sq = 0.f;   // squared error of the pixel (mean squared error backward)
-  if (inb) {
-    const bool flagged = g.hflag && g.hflag[p];
-    if (g.loss_index >= 0) {
-      const float4 im = g.gimage.image[p], tg = g.gimage.target[p];
-      const float4 d = make_float4(im.x - tg.x, im.y - tg.y, im.z - tg.z, im.w - tg.w);
-      sq = d.x * d.x + d.y * d.y + d.z * d.z + d.w * d.w;
-      const float sc = g.gimage.scale;
-      gcol = flagged ? g.gcolor[p] : make_float4(sc * d.x, sc * d.y, sc * d.z, sc * d.w);
-    } else {
-      gcol = flagged ? g.gcolor[p] : g.gimage[p];
-    }
+  if (!kListed && inb_ && g.loss_index >= 0) {
+    const float4 im = g.gimage.image[p], tg = g.gimage.target[p];
+    const float4 d = make_float4(im.x - tg.x, im.y - tg.y, im.z - tg.z, im.w - tg.w);
+    sq = d.x * d.x + d.y * d.y + d.z * d.z + d.w * d.w;
+    const float sc = g.gimage.scale;
+    if (inb) gcol = make_float4(sc * d.x, sc * d.y, sc * d.z, sc * d.w);
+  } else if (inb) {
+    gcol = flagged ? g.gcolor[p] : g.gimage[p];
   }
   const int id = __float_as_int(gb4.x);
   const bool act = inb && id && (gcol.x != 0.f || gcol.y != 0.f || gcol.z != 0.f);
@@ -549,6 +553,18 @@ __global__ void __launch_bounds__(256, 4) shade_backward_kernel(ShadeArgs a, Sha
     }
     g.pgrad[2 * p] = make_float4(gx.x, gx.y, gx.z, gnt.x);
     g.pgrad[2 * p + 1] = make_float4(gnt.y, gnt.z, act ? 1.f : 0.f, 0.f);
+  }
+  };
+  if (!kListed) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    pixel(i, j, i < a.W && j < a.H);
+  } else {
+    const int n = *w.count;
+    for (int k0 = blockIdx.x * 256 + (tid & ~31); k0 < n; k0 += gridDim.x * 256) {
+      const int k = k0 + (tid & 31);
+      const int q = k < n ? w.list[k] : 0;
+      pixel(q % a.W, q / a.W, k < n);
+    }
   }
   __syncthreads();
   // block sums into float64 slot copies: the light gradients sum millions of
@@ -828,7 +844,12 @@ void launch_shade(const ShadeArgs& a, float4* color, float4* image, const uint8_
 void launch_shade_backward(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st) {
   dim3 b(32, 8);
   count_launches(1);
-  shade_backward_kernel<<<grid2(a.W, a.H, b), b, 0, st>>>(a, g);
+  shade_backward_kernel<false><<<grid2(a.W, a.H, b), b, 0, st>>>(a, g, AAWork{});
+}
+
+void launch_shade_backward_listed(const ShadeArgs& a, const ShadeGradArgs& g, const AAWork& w, cudaStream_t st) {
+  count_launches(1);
+  shade_backward_kernel<true><<<148 * 4, 256, 0, st>>>(a, g, w);
 }
 
 void launch_shade_scatter(const ShadeArgs& a, const ShadeGradArgs& g, cudaStream_t st) {
