@@ -408,9 +408,9 @@ def run_ours(args):
     sec_max, frames = aggregate(sec, args.steps, world, dev)
     value = frames / sec_max
 
-    # ---- the same step without the graph: one library call per stage group
+    # ---- the same step without the graph: the forward and the loss backward
+    # (dsm_render_backward_l2, the recorded step's calls) issued one by one
     loss = torch.zeros(1, device=dev)
-    gimg = torch.empty_like(target)
     image = torch.empty_like(target)
     V, L, M = r.verts.shape[0], len(r.lights), r.albedo.shape[0]
     dverts = torch.empty((V, 3), device=dev)
@@ -419,8 +419,7 @@ def run_ours(args):
 
     def step():
         r.forward(image=image)
-        dsm.l2_loss_grad(image, target, loss, gimg)
-        r.backward(gimg, dverts, dlight, dalbedo)
+        r.backward_l2(image, target, loss, dverts, dlight, dalbedo)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -674,8 +673,7 @@ def run_batch(args):
     def serial_step():
         for r, (img, tgt, loss, gimg) in zip(rs, bufs):
             r.forward(image=img)
-            dsm.l2_loss_grad(img, tgt, loss, gimg)
-            r.backward(gimg)
+            r.backward_l2(img, tgt, loss)
 
     for _ in range(args.warmup):
         serial_step()
@@ -841,7 +839,8 @@ def run_reconstruction(args):
 
 def run_profile_step(args):
     """A short eager run for ncu: build the workload's renderer, run
-    `warmup` forward + L2 loss + backward steps and then one more, with no
+    `warmup` forward + L2 loss backward steps (dsm_render_backward_l2, as in
+    the recorded step) and then one more, with no
     graph, no autotuning, no timing and no CPU work, so that a capture with
     -k/-c selects the launches of the last step after few launches before
     them."""
@@ -856,7 +855,6 @@ def run_profile_step(args):
     target = r.forward(verts=verts_t).clone()
     image = torch.empty_like(target)
     loss = torch.zeros(1, device=dev)
-    gimg = torch.empty_like(target)
     for k in range(args.warmup + 1):
         last = k == args.warmup
         if last:
@@ -864,8 +862,7 @@ def run_profile_step(args):
             torch.cuda.nvtx.range_push("dsm_profiled_step")   # ncu --nvtx --nvtx-include dsm_profiled_step/
         n0 = dsm.kernel_launches()
         r.forward(image=image)
-        dsm.l2_loss_grad(image, target, loss, gimg)
-        r.backward(gimg)
+        r.backward_l2(image, target, loss)
         per_step = dsm.kernel_launches() - n0
         if last:
             torch.cuda.nvtx.range_pop()
