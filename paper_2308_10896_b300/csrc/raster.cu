@@ -679,14 +679,12 @@ __device__ __forceinline__ void cover_span(const int* w, int xs, int xe, int y, 
 // threads stride over (balanced whatever the triangle sizes), and each
 // covered pixel centre folds (depth key, triangle) into the pixel's
 // shared-memory 64-bit minimum.  The minimum is order independent, so the
-// result is deterministic.  Items are handed out kChunk at a time: every
-// record marks the chunk position where it starts (or position 0 when it
-// began earlier), and a block prefix maximum turns the marks into the owning
-// record of every item.
+// result is deterministic.  A thread finds the record of its item by a binary
+// search of the records' first items (eight shared-memory reads; records
+// without items share their successor's first item, so the search lands on
+// the one that owns it).
 // Each pixel then writes one 16-byte G-buffer texel: id + 1,
 // perspective-correct b0, b1, depth key.
-constexpr int kChunk = 1024;
-
 template <int kTL>
 __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restrict__ setup,
                                                      const int* __restrict__ offset,
@@ -706,7 +704,7 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restri
   __shared__ int spre[257];          // exclusive prefix of the work items (spans) per record
   __shared__ int sbox[256];          // bbox in tile: x0 | x1 << 5 | y0 << 10 | y1 << 15 (tile-local)
   __shared__ int sinv[256];          // ceil(2^16 / spans per bbox row)
-  __shared__ unsigned short sown[kChunk];   // owning record + 1 of each item of the chunk
+  __shared__ unsigned char spair[kPix];     // the detection's pair map
   __shared__ int swarp[8];
   __shared__ int slast;
   __shared__ unsigned srim[4];       // flagged rim pixels of the tile: top row, bottom row, left, right column
@@ -770,50 +768,22 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restri
     spre[tid] = my_start;
     __syncthreads();
     const int total = spre[256];
-    for (int c0 = 0; c0 < total; c0 += kChunk) {
-      // owner marks: record tid starts at chunk position my_start - c0 (or began before it)
-      for (int q = tid; q < kChunk / 2; q += 256) reinterpret_cast<unsigned*>(sown)[q] = 0u;
-      __syncthreads();
-      if (area > 0 && my_start < c0 + kChunk && my_start + area > c0)
-        sown[max(my_start - c0, 0)] = (unsigned short)(tid + 1);
-      __syncthreads();
-      // block prefix maximum over the chunk (4 consecutive entries per thread)
-      {
-        unsigned short* o = sown + 4 * tid;
-        int m0 = o[0], m1 = max(m0, (int)o[1]), m2 = max(m1, (int)o[2]), m3 = max(m2, (int)o[3]);
-        int inc = m3;
+    // the owner of item q: the last record whose first item is at most q
+    for (int q = tid; q < total; q += 256) {
+      int rec = 0;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int v = __shfl_up_sync(kFull, inc, d);
-          if (lane >= d) inc = max(inc, v);
-        }
-        __syncthreads();   // every thread has read its entries; swarp is free again
-        if (lane == 31) swarp[warp] = inc;
-        __syncthreads();
-        int before = 0;
-        for (int q = 0; q < warp; ++q) before = max(before, swarp[q]);
-        const int lane_before = __shfl_up_sync(kFull, inc, 1);
-        if (lane > 0) before = max(before, lane_before);
-        o[0] = (unsigned short)max(before, m0);
-        o[1] = (unsigned short)max(before, m1);
-        o[2] = (unsigned short)max(before, m2);
-        o[3] = (unsigned short)max(before, m3);
-      }
-      __syncthreads();
-      const int n = min(kChunk, total - c0);
-      for (int q = tid; q < n; q += 256) {
-        const int rec = sown[q] - 1;
-        const int b = sbox[rec];
-        const int x0 = b & 31, x1 = (b >> 5) & 31, y0 = (b >> 10) & 31;
-        const int it = c0 + q - spre[rec], wd = (x1 - x0 + kSpan) / kSpan;
-        const int qy = (it * sinv[rec]) >> 16;   // it / wd (exact for it <= 256 spans, wd <= 8)
-        const int xs = x0 + kSpan * (it - qy * wd), y = y0 + qy;
-        const int* rw = sq + rec * kRecStride;
-        if (rw[kRecFlags] & kRecSmall) cover_span<int, kTile>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
-        else cover_span<long long, kTile>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
-      }
-      __syncthreads();
+      for (int step = 128; step; step >>= 1)
+        if (spre[rec + step] <= q) rec += step;
+      const int b = sbox[rec];
+      const int x0 = b & 31, x1 = (b >> 5) & 31, y0 = (b >> 10) & 31;
+      const int it = q - spre[rec], wd = (x1 - x0 + kSpan) / kSpan;
+      const int qy = (it * sinv[rec]) >> 16;   // it / wd (exact for it <= 256 spans, wd <= 8)
+      const int xs = x0 + kSpan * (it - qy * wd), y = y0 + qy;
+      const int* rw = sq + rec * kRecStride;
+      if (rw[kRecFlags] & kRecSmall) cover_span<int, kTile>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
+      else cover_span<long long, kTile>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
     }
+    __syncthreads();
   }
   if (slot >= 0) {
     // fold this unit's minima into the tile's key slot; the last unit of the
@@ -850,7 +820,6 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restri
   constexpr int kRowThreads = kTile / 4, kDetThreads = kPix / 4;
   unsigned hbits = 0u;   // bit q: pixel q of the thread's four is flagged
   if (hflag) {
-    unsigned char* spair = reinterpret_cast<unsigned char*>(sown);   // (the owner map is free again)
     auto pair_heavy = [&](unsigned long long kp, unsigned long long kq) -> unsigned {
       if ((unsigned)kp == (unsigned)kq) return 0u;
       const unsigned occ = (unsigned)(kp < kq ? kp : kq);
