@@ -60,7 +60,7 @@ struct ViewBufs {
   int list_cap = 0;
   BinShape bs{kTileLog2Default, kBigTilesDefault};
   // raster work units and the key slots of tiles split over several units
-  Buf units, tile_slot, tile_done, skey;
+  Buf units, tile_done, skey;
   int units_cap = 0, slot_cap = 0;
   AAWork aa_work() { return AAWork{aa_list.as<int>(), aa_ctr.as<int>()}; }
   // the clip buffer holds V clip coordinates, then V float-float screen positions
@@ -72,7 +72,7 @@ struct ViewBufs {
     return RimBufs{rim.as<unsigned long long>(), reinterpret_cast<unsigned*>(rim.as<unsigned long long>() + keys)};
   }
   RasterUnits raster_units() {
-    return RasterUnits{units.as<int2>(), units_cap, tile_slot.as<int>(), slot_cap, tile_done.as<int>(),
+    return RasterUnits{units.as<int4>(), units_cap, slot_cap, tile_done.as<int>(),
                        skey.as<unsigned long long>()};
   }
 };
@@ -360,7 +360,7 @@ void dsm_destroy(dsm_ctx* ctx) {
   for (auto& v : ctx->view) {
     Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
                  &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr,
-                 &v.hflag, &v.rim, &v.color, &v.gcolor, &v.pgrad, &v.units, &v.tile_slot, &v.tile_done, &v.skey};
+                 &v.hflag, &v.rim, &v.color, &v.gcolor, &v.pgrad, &v.units, &v.tile_done, &v.skey};
     for (Buf* b : vb) b->release();
   }
   for (auto& l : ctx->light) {
@@ -470,8 +470,7 @@ static dsm_status ensure_units(dsm_ctx* ctx, ViewBufs& v, bool reset = false) {
   const size_t tiles = (size_t)v.tilesX * v.tilesY;
   v.units_cap = (int)(tiles + (size_t)v.list_cap / kRasterBatch + 1);
   v.slot_cap = v.list_cap / (kRasterBatch + 1) + 1;
-  DSM_CHECK(v.units.ensure((size_t)v.units_cap * sizeof(int2)));
-  DSM_CHECK(v.tile_slot.ensure(tiles * 4));
+  DSM_CHECK(v.units.ensure((size_t)v.units_cap * sizeof(int4)));
   const size_t done_cap = v.tile_done.cap, key_cap = v.skey.cap;
   DSM_CHECK(v.tile_done.ensure(tiles * 4));
   DSM_CHECK(v.skey.ensure((size_t)v.slot_cap * 1024 * sizeof(unsigned long long)));
@@ -668,9 +667,8 @@ void raster_view(dsm_ctx* ctx, int w, cudaStream_t st) {
                     v.list.as<int>(), v.list_cap, ds, v.big_index.as<int>(), st);
   }
   StageTimer t(ctx, ST_RASTER, st);
-  launch_raster(v.setup.as<TriSetup>(), v.offset.as<int>(), v.list.as<int>(), v.list_cap, v.tilesX, v.tilesY,
-                v.bs.tile_log2, v.W, v.H, v.clip.as<float4>(), v.scr(ctx->mesh.n_verts), ctx->mesh.tris,
-                v.gbuf.as<float4>(),
+  launch_raster(v.setup.as<TriSetup>(), v.list.as<int>(), v.tilesX, v.bs.tile_log2, v.W, v.H, v.clip.as<float4>(),
+                v.scr(ctx->mesh.n_verts), ctx->mesh.tris, v.gbuf.as<float4>(),
                 light ? v.depth.as<float>() : nullptr, light ? lwork(ctx, w).fmap.as<float2>() : nullptr,
                 warp_exponent(ctx), v.raster_units(), ds, w, v.silbits(ctx->mesh.n_tris), aa ? v.hflag.as<uint8_t>() : nullptr,
                 v.aa_work(), v.rim_bufs(), st);
@@ -1540,7 +1538,7 @@ uint64_t dsm_memory_bytes(dsm_ctx* ctx) {
   for (const auto& v : ctx->view) {
     const Buf* vb[] = {&v.clip, &v.snap, &v.depth, &v.setup, &v.orient, &v.sil, &v.count, &v.offset, &v.list,
                        &v.gbuf, &v.gclip, &v.big_index, &v.big_tri, &v.big_acc, &v.aa_list, &v.aa_ctr,
-                       &v.hflag, &v.rim, &v.color, &v.gcolor, &v.pgrad, &v.units, &v.tile_slot, &v.tile_done, &v.skey};
+                       &v.hflag, &v.rim, &v.color, &v.gcolor, &v.pgrad, &v.units, &v.tile_done, &v.skey};
     for (const Buf* b : vb) n += b->cap;
   }
   for (const auto& l : ctx->light) {

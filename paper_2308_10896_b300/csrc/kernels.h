@@ -206,9 +206,11 @@ void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* 
 // empties the slot and its counter again.
 constexpr int kRasterBatch = 1024;   // records per unit (four batches of 256)
 struct RasterUnits {
-  int2* units;                 // (tile, batch) per unit, units_cap entries
+  // per unit: tile, the list range of its records [begin, end) (-1, -1 for a
+  // unit with nothing to do), and the tile's key slot + 1 (0: none) with the
+  // tile's unit count << 20
+  int4* units;
   int units_cap;               // tiles + list capacity / kRasterBatch + 1 (an upper bound)
-  int* tile_slot;              // key slot of a tile of several units, or -1
   int slot_cap;                // list capacity / (kRasterBatch + 1) + 1 (an upper bound)
   int* tile_done;              // units finished per tile (zero between frames)
   unsigned long long* skey;    // slot_cap x 1024 inverted keys (zero between frames)
@@ -236,11 +238,10 @@ void launch_raster_stats(const TriSetup* setup, const int* offset, const int* li
 // pixel pairs inside each tile (silbits: the view's packed silhouette flags):
 // hflag at every pixel and the flagged pixels appended to aa; the tiles' rims
 // go to rim.
-void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
-                   int tile_log2, int W, int H, const float4* clip, const float4* scr, const int* tris,
-                   float4* gbuf, const float* depth, float2* fmap, float ec, const RasterUnits& ru,
-                   DevStatus* status, int view, const uint32_t* silbits, uint8_t* hflag, const AAWork& aa,
-                   const RimBufs& rim, cudaStream_t st);
+void launch_raster(const TriSetup* setup, const int* list, int tilesX, int tile_log2, int W, int H,
+                   const float4* clip, const float4* scr, const int* tris, float4* gbuf, const float* depth,
+                   float2* fmap, float ec, const RasterUnits& ru, DevStatus* status, int view,
+                   const uint32_t* silbits, uint8_t* hflag, const AAWork& aa, const RimBufs& rim, cudaStream_t st);
 
 // shadow-map interpolation and antialiasing
 // Antialiasing (detection + list passes, see aa.cu).

@@ -496,8 +496,10 @@ __device__ __forceinline__ bool big_covers_tile(const TriSetup& r, int tx, int t
 // its ordinary part (which the fill pass takes), and the raster work units
 // follow, one per kRasterBatch records (at least one per tile), handed out by
 // one atomic per warp on status->units, with a key slot for a tile of several
-// units.  (The bounds hold whenever the list fits its capacity; a frame that
-// overflows it is reported and only has to stay in bounds.)
+// units; each unit carries its record range and the tile's slot and unit
+// count, so the raster starts from one 16-byte entry.  (The bounds hold
+// whenever the list fits its capacity; a frame that overflows it is reported
+// and only has to stay in bounds.)
 __global__ void alloc_units_kernel(const int* __restrict__ count, int n, int* __restrict__ offset,
                                    DevStatus* status, int view, const TriSetup* __restrict__ setup,
                                    const int* __restrict__ big_tri, int tilesX, int tl, int* __restrict__ list,
@@ -547,13 +549,19 @@ __global__ void alloc_units_kernel(const int* __restrict__ count, int n, int* __
   base = __shfl_sync(kFull, base, 31);
   if (tile < n) {
     const int u0 = base + incl - nb;
-    for (int b = 0; b < nb && u0 + b < ru.units_cap; ++b) ru.units[u0 + b] = make_int2(tile, b);
     int slot = -1;
     if (nb > 1) {
       slot = atomicAdd(&status->split[view], 1);
       if (slot >= ru.slot_cap) slot = -1;
     }
-    ru.tile_slot[tile] = slot;
+    // slots past the list capacity were never written (the fill pass flagged the overflow)
+    const int end = min(beg + c, capacity);
+    for (int b = 0; b < nb && u0 + b < ru.units_cap; ++b) {
+      // without a key slot the tile's first unit takes all its records and the others none (-1)
+      const int ub = slot >= 0 ? min(beg + kRasterBatch * b, end) : (b == 0 ? min(beg, end) : -1);
+      const int ue = slot >= 0 ? min(end, ub + kRasterBatch) : (b == 0 ? end : -1);
+      ru.units[u0 + b] = make_int4(tile, ub, ue, (slot + 1) | (nb << 20));
+    }
   }
 }
 
@@ -687,9 +695,8 @@ __device__ __forceinline__ void cover_span(const int* w, int xs, int xe, int y, 
 // perspective-correct b0, b1, depth key.
 template <int kTL>
 __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restrict__ setup,
-                                                     const int* __restrict__ offset,
-                                                     const int* __restrict__ list, int capacity, int tilesX,
-                                                     int n_tiles, int W, int H, const float4* __restrict__ clip,
+                                                     const int* __restrict__ list, int tilesX,
+                                                     int W, int H, const float4* __restrict__ clip,
                                                      const float4* __restrict__ scr,
                                                      const int* __restrict__ tris, float4* __restrict__ gbuf,
                                                      const float* __restrict__ depth, float2* __restrict__ fmap,
@@ -710,16 +717,10 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restri
   __shared__ unsigned srim[4];       // flagged rim pixels of the tile: top row, bottom row, left, right column
   // this CTA's work unit: records [beg, lim) of one tile
   if ((int)blockIdx.x >= min(status->units[view], ru.units_cap)) return;
-  const int2 unit = ru.units[blockIdx.x];
-  const int tile = unit.x, batch = unit.y;
-  const int o0 = offset[tile], o1 = offset[n_tiles + tile];
-  const int nb = max(1, (o1 - o0 + kRasterBatch - 1) / kRasterBatch);
-  const int slot = nb > 1 ? ru.tile_slot[tile] : -1;
-  if (nb > 1 && slot < 0 && batch > 0) return;   // no key slot: the tile's first unit takes all its records
-  // slots past the list capacity were never written (the fill pass flagged the overflow)
-  const int end = min(o1, capacity);
-  const int beg = min(slot >= 0 ? o0 + kRasterBatch * batch : o0, end);
-  const int lim = slot >= 0 ? min(end, beg + kRasterBatch) : end;
+  const int4 unit = ru.units[blockIdx.x];
+  const int tile = unit.x, beg = unit.y, lim = unit.z;
+  const int slot = (unit.w & 0xfffff) - 1, nb = unit.w >> 20;
+  if (lim < 0) return;   // no key slot: the tile's first unit takes all its records
   const int ti = tile % tilesX, tj = tile / tilesX;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ti0 = ti * kTile, tj0 = tj * kTile;
@@ -992,19 +993,17 @@ void launch_bin_fill(const TriSetup* setup, int T, int tilesX, BinShape bs, int*
                                                    big_index);
 }
 
-void launch_raster(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX, int tilesY,
-                   int tile_log2, int W, int H, const float4* clip, const float4* scr, const int* tris,
-                   float4* gbuf, const float* depth, float2* fmap, float ec, const RasterUnits& ru,
-                   DevStatus* status, int view, const uint32_t* silbits, uint8_t* hflag, const AAWork& aa,
-                   const RimBufs& rim, cudaStream_t st) {
-  const int n = tilesX * tilesY;
+void launch_raster(const TriSetup* setup, const int* list, int tilesX, int tile_log2, int W, int H,
+                   const float4* clip, const float4* scr, const int* tris, float4* gbuf, const float* depth,
+                   float2* fmap, float ec, const RasterUnits& ru, DevStatus* status, int view,
+                   const uint32_t* silbits, uint8_t* hflag, const AAWork& aa, const RimBufs& rim, cudaStream_t st) {
   count_launches(1);
   if (tile_log2 == 4)
-    raster_kernel<4><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, scr,
-                                                  tris, gbuf, depth, fmap, ec, ru, status, view, silbits, hflag, aa, rim);
+    raster_kernel<4><<<ru.units_cap, 256, 0, st>>>(setup, list, tilesX, W, H, clip, scr, tris, gbuf, depth, fmap, ec,
+                                                  ru, status, view, silbits, hflag, aa, rim);
   else
-    raster_kernel<5><<<ru.units_cap, 256, 0, st>>>(setup, offset, list, capacity, tilesX, n, W, H, clip, scr,
-                                                  tris, gbuf, depth, fmap, ec, ru, status, view, silbits, hflag, aa, rim);
+    raster_kernel<5><<<ru.units_cap, 256, 0, st>>>(setup, list, tilesX, W, H, clip, scr, tris, gbuf, depth, fmap, ec,
+                                                  ru, status, view, silbits, hflag, aa, rim);
 }
 
 void launch_raster_stats(const TriSetup* setup, const int* offset, const int* list, int capacity, int tilesX,
