@@ -694,7 +694,7 @@ __device__ __forceinline__ void cover_span(const int* w, int xs, int xe, int y, 
 // Each pixel then writes one 16-byte G-buffer texel: id + 1,
 // perspective-correct b0, b1, depth key.
 template <int kTL>
-__global__ void __launch_bounds__(256, 5) raster_kernel(const TriSetup* __restrict__ setup,
+__global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restrict__ setup,
                                                      const int* __restrict__ list, int tilesX,
                                                      int W, int H, const float4* __restrict__ clip,
                                                      const float4* __restrict__ scr,
