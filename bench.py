@@ -874,8 +874,8 @@ def run_profile_step(args):
 
 # Kernel name -> profiler stage (the stage whose CUDA events bracket it).
 KERNEL_STAGES = [
-    (r"light_setup_kernel|transform_all_kernel|setup_bin_kernel|silhouette_all_kernel|"
-     r"vertex_normals_kernel|alloc_units_kernel", "setup"),
+    (r"light_setup_kernel|transform_all_kernel|setup_bin_kernel|silhouette_all_kernel|alloc_units_kernel",
+     "setup"),
     (r"bin_fill_kernel", "bin_fill"),
     (r"raster_kernel<|aa_seam_kernel", "raster"),
     (r"aa_forward_list_kernel<float2>", "sm_antialias"),

@@ -85,6 +85,50 @@ __device__ __forceinline__ int scatter_slot(int n) {
   return (int)((blockIdx.x * 0x9E3779B1u + blockIdx.y * 0x85EBCA77u + threadIdx.y * 0xC2B2AE3Du) >> 16) & (n - 1);
 }
 
+// Face normal cross(v1 - v0, v2 - v0) of triangle t (area-weighted, unnormalised).
+__device__ __forceinline__ float3 face_normal(const float* __restrict__ verts, const int* __restrict__ tris, int t) {
+  const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+  const float3 v0 = make_float3(verts[3 * a], verts[3 * a + 1], verts[3 * a + 2]);
+  const float3 e1 = make_float3(verts[3 * b] - v0.x, verts[3 * b + 1] - v0.y, verts[3 * b + 2] - v0.z);
+  const float3 e2 = make_float3(verts[3 * c] - v0.x, verts[3 * c + 1] - v0.y, verts[3 * c + 2] - v0.z);
+  return make_float3(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
+}
+
+// Vertex normals: the area-weighted sum of the incident face normals of
+// vertex v (faces off[v] .. off[v + 1] of lst), normalised; its length kept
+// for the adjoint.
+struct VertNormalArgs {
+  const float* verts;
+  int V;
+  const int* tris;
+  const int* off;
+  const int* lst;
+  float* vn;
+  float* vlen;
+};
+__device__ __forceinline__ void vertex_normal_at(const VertNormalArgs& a, int v) {
+  float3 s = make_float3(0.f, 0.f, 0.f);
+  for (int k = a.off[v]; k < a.off[v + 1]; ++k) {
+    const float3 f = face_normal(a.verts, a.tris, a.lst[k]);
+    s.x += f.x; s.y += f.y; s.z += f.z;
+  }
+  const float l = sqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
+  const float il = l > 0.f ? 1.f / l : 1.f;
+  a.vn[3 * v] = s.x * il; a.vn[3 * v + 1] = s.y * il; a.vn[3 * v + 2] = s.z * il;
+  a.vlen[v] = l;
+}
+
+// Exact float32 -> float64 widening from the bit fields of the two IEEE 754
+// formats (exponent rebiased by 1023 - 127 = 896, the 23 fraction bits at the
+// top of the 52), on the integer pipes; zeros keep their sign, and subnormal,
+// infinite and NaN inputs take the hardware conversion.
+__device__ __forceinline__ double widen_exact(float v) {
+  const unsigned u = __float_as_uint(v), e = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (e == 0u || e == 0xffu) return (double)v;
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+
 __device__ __forceinline__ uint32_t order_bits(float z) {
   uint32_t u = __float_as_uint(z);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);

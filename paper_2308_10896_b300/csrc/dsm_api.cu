@@ -972,12 +972,13 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
   CamMats cm{};
   for (int c = 0; c < C; ++c)
     for (int k = 0; k < 16; ++k) cm.v[20 * c + k] = cams[c].clip[k];
-  launch_light_setup(light_params, la, ctx->lights_dev.as<LightDev>(), viewM, ctx->viewMlo.as<float>(), cm, C, st);
+  const VertNormalArgs vna{mesh->verts, V, mesh->tris, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
+                           ctx->vnormal.as<float>(), ctx->vnlen.as<float>()};
+  launch_light_setup(light_params, la, ctx->lights_dev.as<LightDev>(), viewM, ctx->viewMlo.as<float>(), cm, C, vna,
+                     st);
 
   if (ctx->recompute) {
     // ---- one view at a time through the shared buffer sets
-    launch_vertex_normals(mesh->verts, V, mesh->tris, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
-                          ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), st);
     t_setup.stop();
     for (int w = 0; w < NV; ++w) {
       s = rebuild_view(ctx, w, sizing, true, st);
@@ -996,12 +997,6 @@ dsm_status dsm_render_cameras(dsm_ctx* ctx, const dsm_mesh* mesh, const dsm_ligh
     // ---- per view on its own stream: list segments and work units (the views are independent until shading)
     DSM_CHECK(ensure_streams(ctx));
     DSM_CHECK(fork_views(ctx, st, ctx->ev_fork, 0, NV));
-    {
-      cudaStream_t cst = view_stream(ctx, L, st);
-      StageTimer tn(ctx, ST_SETUP, cst);
-      launch_vertex_normals(mesh->verts, V, mesh->tris, ctx->vf_off.as<int>(), ctx->vf_list.as<int>(),
-                            ctx->vnormal.as<float>(), ctx->vnlen.as<float>(), cst);
-    }
     for (int w = 0; w < NV; ++w) alloc_view(ctx, w, !sizing, view_stream(ctx, w, st));
     {
       StageTimer ts(ctx, ST_SETUP, st);

@@ -195,10 +195,11 @@ void launch_setup_all(const float* verts, int V, const int* tris, int T, const i
                       const float* viewMlo,
                       const ViewSetupArgs& a, DevStatus* status, bool silhouettes, cudaStream_t st);
 void launch_silhouettes_all(const int* adj, int T, const ViewSetupArgs& a, cudaStream_t st);
-// The light views' matrices and derivatives (one CTA per light view) and the
-// C camera matrices after them.
+// The light views' matrices and derivatives (one CTA per light view), the
+// C camera matrices after them, and in the same launch the vertex normals
+// (vn.V vertices; none when vn.V = 0), which need neither.
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, float* viewMlo,
-                        const CamMats& cams, int C, cudaStream_t st);
+                        const CamMats& cams, int C, const VertNormalArgs& vn, cudaStream_t st);
 // Raster work units of one view.  A tile's list is rastered kRasterBatch
 // records per unit (one CTA each); a tile of several units merges their
 // per-pixel minimum keys in a key slot (global 64-bit maxima of the inverted
@@ -290,8 +291,6 @@ void launch_filter_adjoint(const float2* gout, float2* tmp, float2* gin, int R, 
                            DevStatus* status = nullptr);
 
 // normals, shading, vertex gradients
-void launch_vertex_normals(const float* verts, int V, const int* tris, const int* vf_off, const int* vf_list,
-                           float* vnormal, float* vlen, cudaStream_t st);
 // dL/dv of the cameras' interpolation: the unit vertex normals' gradient
 // gnormal through the normalisation and the area-weighted face normals, plus
 // the positions' gradient gpos, added to dverts.

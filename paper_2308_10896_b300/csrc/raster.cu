@@ -13,17 +13,10 @@ namespace dsm {
 // formed in float64 with explicitly rounded operations (no contraction) in a
 // fixed order and rounded to float32 once.  The derivatives J = dQ/d theta
 // (theta = pos xyz, dir xyz) only feed gradients and use float32 dual numbers.
-struct R64 {   // float64 value, every operation separately rounded
-  double v;
-};
-__device__ __forceinline__ R64 operator+(R64 a, R64 b) { return {__dadd_rn(a.v, b.v)}; }
-__device__ __forceinline__ R64 operator-(R64 a, R64 b) { return {__dsub_rn(a.v, b.v)}; }
-__device__ __forceinline__ R64 operator-(R64 a) { return {-a.v}; }
-__device__ __forceinline__ R64 operator*(R64 a, R64 b) { return {__dmul_rn(a.v, b.v)}; }
-__device__ __forceinline__ R64 operator/(R64 a, R64 b) { return {__ddiv_rn(a.v, b.v)}; }
-__device__ __forceinline__ R64 tsqrt(R64 a) { return {__dsqrt_rn(a.v)}; }
-__device__ __forceinline__ double val(R64 a) { return a.v; }
-
+// The frame and the entries are stated once, as templates over the number
+// type (light_frame, q_entry), which the duals instantiate; the float64
+// values take the same operations spread over a warp's lanes
+// (light_q64_lanes).
 struct F1 {    // float32 value with its derivative w.r.t. one light parameter
   float v, d;
 };
@@ -116,43 +109,131 @@ __device__ __forceinline__ float face_axis(int face, int k) {
   return (face >> 1) == k ? ((face & 1) ? -1.f : 1.f) : 0.f;
 }
 
-// One CTA per light view.  Warp 0: lane k < 20 forms Q[k] in float64 (the
-// frame is computed by every lane at once) and lane 0 writes the view's other
-// fields; warp 1: lane j < 6 forms all of Q with float32 duals in direction
-// theta_j and writes column j of J.  A cube face takes the light's position
-// and the face axis as its direction (a constant: its J has no direction
-// columns).  The last CTA copies the C camera matrices after the light views'
-// (a camera's float32 matrix is exact: its residual rows are zero).
-__global__ void light_setup_kernel(const float* __restrict__ params, LightSetupArgs a, LightDev* out,
-                                   float* viewM, float* viewMlo, CamMats cams, int C) {
+// The float64 frame and Q of one light view, spread over the lanes of one
+// warp.  Every operation is one that light_frame and q_entry state, on the
+// same operands in the same order, each separately rounded (explicit
+// intrinsics, no contraction), so Q is the same to the bit as their float64
+// evaluation; only the lane that performs an operation differs.  float64 issues at a small fraction of the
+// float32 rate here, so the warp's time is its count of float64 instructions:
+// lane i forms component i mod 3 of each frame vector (one division or cross
+// product term per lane where every lane formed all three), the sums of
+// squares and the dot products f.e, r.e, u.e gather their terms from lanes
+// 0-8 by shuffles, and the divisions of all twenty entries, with the spot
+// light's A = far / (far - near) in lane 20 and B = -far near / (far - near)
+// in lane 21, are one lane-parallel division.  thd: this lane's direction
+// component theta[3 + i mod 3]; thp: its position component theta[i mod 3].
+struct LightQ64 {
+  double q;    // Q entry `lane` (lanes < 20)
+  double fc;   // component lane mod 3 of the normalised direction f
+  double n;    // |dir|
+};
+__device__ __forceinline__ double shfl_d(double v, int src) { return __shfl_sync(kFull, v, src); }
+
+__device__ __forceinline__ LightQ64 light_q64_lanes(double thd, double thp, const LightConst& L, int lane) {
+  const int c = lane % 3, c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+  // f = dir / |dir|, |dir| = sqrt((x x + y y) + z z)
+  const double d2 = __dmul_rn(thd, thd);
+  const double n = __dsqrt_rn(__dadd_rn(__dadd_rn(shfl_d(d2, 0), shfl_d(d2, 1)), shfl_d(d2, 2)));
+  const double fc = __ddiv_rn(thd, n);
+  const double fc1 = shfl_d(fc, c1), fc2 = shfl_d(fc, c2);
+  // r = normalize(f x up), up = z when |f.y| > 0.99, else y; (a x b)_c = a_c1 b_c2 - a_c2 b_c1
+  const int upk = fabs(shfl_d(fc, 1)) > 0.99 ? 2 : 1;
+  const double up1 = c1 == upk ? 1.0 : 0.0, up2 = c2 == upk ? 1.0 : 0.0;
+  const double rr = __dsub_rn(__dmul_rn(fc1, up2), __dmul_rn(fc2, up1));
+  const double r2 = __dmul_rn(rr, rr);
+  const double nr = __dsqrt_rn(__dadd_rn(__dadd_rn(shfl_d(r2, 0), shfl_d(r2, 1)), shfl_d(r2, 2)));
+  const double rc = __ddiv_rn(rr, nr);
+  // u = r x f
+  const double uc = __dsub_rn(__dmul_rn(shfl_d(rc, c1), fc2), __dmul_rn(shfl_d(rc, c2), fc1));
+  // eye: -dist f (directional) or the position
+  const double ec = L.type == 0 ? __dmul_rn(-L.dist, fc) : thp;
+  // f.e, r.e, u.e: lanes 0-2, 3-5 and 6-8 hold the products of one each
+  const double pv = __dmul_rn(lane < 3 ? fc : (lane < 6 ? rc : uc), ec);
+  const int g0 = lane < 3 ? 0 : (lane < 6 ? 3 : 6);
+  const double dsum = __dadd_rn(__dadd_rn(shfl_d(pv, g0), shfl_d(pv, g0 + 1)), shfl_d(pv, g0 + 2));
+  const double fe = shfl_d(dsum, 0), re = shfl_d(dsum, 3), ue = shfl_d(dsum, 6);
+  const double nearp = L.near_plane, farp = L.far_plane;
+  const double rng = __dsub_rn(farp, nearp), nfe_near = __dsub_rn(-fe, nearp);
+  // entry k = lane: row k / 4, column cq = k mod 4 (the depth row, k >= 16, has column k - 16)
+  const int k = lane, row = k >> 2, cq = k & 3, ci = cq < 3 ? cq : 0;
+  const double fq = shfl_d(fc, ci), rq = shfl_d(rc, ci), uq = shfl_d(uc, ci);
+  const bool spot = L.type != 0;
+  // the spot light's products before its divisions: c r, c u (rows 0, 1), far near (lane 21)
+  const double pm = __dmul_rn(k == 21 ? farp : L.persp_c,
+                              k == 21 ? nearp : (row == 0 ? (cq < 3 ? rq : re) : (cq < 3 ? uq : ue)));
+  double num = 1.0, den = 1.0;
+  if (k >= 16 && k < 20) {
+    num = cq < 3 ? fq : nfe_near;
+    den = rng;
+  } else if (!spot && k < 12) {
+    num = row == 0 ? (cq < 3 ? rq : -re) : row == 1 ? (cq < 3 ? uq : -ue) : (cq < 3 ? fq : nfe_near);
+    den = row == 2 ? rng : L.ortho_half;
+  } else if (spot && (k == 20 || k == 21)) {
+    num = k == 20 ? farp : -pm;
+    den = rng;
+  }
+  const double qd = __ddiv_rn(num, den);
+  // the spot light's depth row: A f_c, and (-(A f.e)) + B
+  const double A = shfl_d(qd, 20), B = shfl_d(qd, 21);
+  const double am = __dmul_rn(A, cq < 3 ? fq : fe);
+  const double ab = __dadd_rn(-am, B);
+  double q;
+  if (k >= 16) q = qd;
+  else if (!spot) q = row == 3 ? (cq == 3 ? 1.0 : 0.0) : qd;
+  else if (row < 2) q = cq < 3 ? pm : -pm;
+  else if (row == 2) q = cq < 3 ? am : ab;
+  else q = cq < 3 ? fq : -fe;
+  return {q, fc, n};
+}
+
+// One CTA per light view.  Warp 0 forms Q in float64 (light_q64_lanes; lane
+// k < 20 writes Q[k]) and the view's other fields; warp 1: lane j < 6 forms
+// all of Q with float32 duals in direction theta_j and writes column j of J.
+// A cube face takes the light's position and the face axis as its direction
+// (a constant: its J has no direction columns).  CTA a.n copies the C camera
+// matrices after the light views' (a camera's float32 matrix is exact: its
+// residual rows are zero).  The CTAs after it form the vertex normals, one
+// thread per vertex: the light CTAs' float64 chains occupy a few SMs for
+// several microseconds, and in one launch the normals run beside them for
+// certain (as a kernel of their own on another stream they were seen to start
+// only after it).
+constexpr int kLightSetupThreads = 128;
+__global__ void __launch_bounds__(kLightSetupThreads) light_setup_kernel(const float* __restrict__ params,
+                                                                         LightSetupArgs a, LightDev* out,
+                                                                         float* viewM, float* viewMlo, CamMats cams,
+                                                                         int C, VertNormalArgs vn) {
   const int l = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (l > a.n) {
+    const int v = (l - a.n - 1) * kLightSetupThreads + threadIdx.x;
+    if (v < vn.V) vertex_normal_at(vn, v);
+    return;
+  }
   if (l == a.n) {
     for (int k = threadIdx.x; k < 20 * C; k += blockDim.x) viewM[20 * a.n + k] = cams.v[k];
     for (int k = threadIdx.x; k < 16 * C; k += blockDim.x) viewMlo[16 * a.n + k] = 0.f;
     return;
   }
-  if (l > a.n) return;
   const LightConst& L = a.c[l];
   LightDev& o = out[l];
   const float* pl = params + L.user * 6;
   if (warp == 0) {
-    if (lane >= 20) return;
-    R64 th[6];
-    for (int k = 0; k < 6; ++k) th[k] = {(double)(k >= 3 && L.face >= 0 ? face_axis(L.face, k - 3) : pl[k])};
-    const R64 zero{0.0}, one{1.0};
-    const Frame<R64> F = light_frame(th, L, zero, one);
-    const double q64 = q_entry(lane, F, L, zero, one).v;
-    const float q = __double2float_rn(q64);
-    o.Q[lane] = q;
-    viewM[l * 20 + lane] = q;
-    // the clip rows' rounding residual: the unsnapped clip coordinates that
-    // interpolation and antialiasing use are those of the float64 matrix
-    if (lane < 16) viewMlo[l * 16 + lane] = __double2float_rn(q64 - (double)q);
+    const int c = lane % 3;
+    const float thd = L.face >= 0 ? face_axis(L.face, c) : pl[3 + c];
+    const LightQ64 r = light_q64_lanes(widen_exact(thd), widen_exact(pl[c]), L, lane);
+    if (lane < 20) {
+      const float q = __double2float_rn(r.q);
+      o.Q[lane] = q;
+      viewM[l * 20 + lane] = q;
+      // the clip rows' rounding residual: the unsnapped clip coordinates that
+      // interpolation and antialiasing use are those of the float64 matrix
+      if (lane < 16) viewMlo[l * 16 + lane] = __double2float_rn(r.q - widen_exact(q));
+    }
+    if (lane < 3) {
+      o.fwd[lane] = __double2float_rn(r.fc);
+      o.pos[lane] = pl[lane];
+    }
     if (lane == 0) {
-      o.fwd[0] = (float)F.f.x.v; o.fwd[1] = (float)F.f.y.v; o.fwd[2] = (float)F.f.z.v;
-      const double dx = th[3].v, dy = th[4].v, dz = th[5].v;
-      o.dir_norm = (float)sqrt(dx * dx + dy * dy + dz * dz);
-      o.pos[0] = pl[0]; o.pos[1] = pl[1]; o.pos[2] = pl[2];
+      o.dir_norm = __double2float_rn(r.n);
       o.type = L.type;
       o.res = L.res;
       o.intensity[0] = L.intensity[0]; o.intensity[1] = L.intensity[1]; o.intensity[2] = L.intensity[2];
@@ -953,9 +1034,10 @@ __global__ void raster_stats_kernel(const TriSetup* __restrict__ setup, const in
 
 // ------------------------------------------------------------------ launchers
 void launch_light_setup(const float* params, const LightSetupArgs& a, LightDev* out, float* viewM, float* viewMlo,
-                        const CamMats& cams, int C, cudaStream_t st) {
+                        const CamMats& cams, int C, const VertNormalArgs& vn, cudaStream_t st) {
   count_launches(1);
-  light_setup_kernel<<<a.n + 1, 64, 0, st>>>(params, a, out, viewM, viewMlo, cams, C);
+  const int nv = (vn.V + kLightSetupThreads - 1) / kLightSetupThreads;
+  light_setup_kernel<<<a.n + 1 + nv, kLightSetupThreads, 0, st>>>(params, a, out, viewM, viewMlo, cams, C, vn);
 }
 
 void launch_setup_all(const float* verts, int V, const int* tris, int T, const int* adj, const float* viewM,

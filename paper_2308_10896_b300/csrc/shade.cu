@@ -9,31 +9,6 @@
 namespace dsm {
 
 // ------------------------------------------------------------------ vertex normals
-__device__ __forceinline__ float3 face_normal(const float* __restrict__ verts, const int* __restrict__ tris, int t) {
-  const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
-  const float3 v0 = make_float3(verts[3 * a], verts[3 * a + 1], verts[3 * a + 2]);
-  const float3 e1 = make_float3(verts[3 * b] - v0.x, verts[3 * b + 1] - v0.y, verts[3 * b + 2] - v0.z);
-  const float3 e2 = make_float3(verts[3 * c] - v0.x, verts[3 * c + 1] - v0.y, verts[3 * c + 2] - v0.z);
-  return make_float3(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
-}
-
-// Area-weighted sum of the incident face normals (cross(v1 - v0, v2 - v0)), normalised.
-__global__ void vertex_normals_kernel(const float* __restrict__ verts, int V, const int* __restrict__ tris,
-                                      const int* __restrict__ off, const int* __restrict__ lst,
-                                      float* __restrict__ vn, float* __restrict__ vlen) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V) return;
-  float3 s = make_float3(0.f, 0.f, 0.f);
-  for (int k = off[v]; k < off[v + 1]; ++k) {
-    const float3 f = face_normal(verts, tris, lst[k]);
-    s.x += f.x; s.y += f.y; s.z += f.z;
-  }
-  const float l = sqrtf(s.x * s.x + s.y * s.y + s.z * s.z);
-  const float il = l > 0.f ? 1.f / l : 1.f;
-  vn[3 * v] = s.x * il; vn[3 * v + 1] = s.y * il; vn[3 * v + 2] = s.z * il;
-  vlen[v] = l;
-}
-
 // dL/d(unnormalised vertex normal) from dL/d(unit normal).
 // dL/d unnormalised vertex normal N from dL/d unit normal n = N / |N|:
 // (g - n (n.g)) / |N|, with n and |N| saved by the forward.
@@ -733,14 +708,17 @@ __global__ void __launch_bounds__(256) vertex_backward_kernel(const float* __res
 
 // One block of 1024 threads, the end of the backward: the kRedSlots float64
 // copies of the light-matrix gradient, the direct light terms and the albedo
-// block sums reduced (four threads per entry, 16 slots each, then two
-// shuffles; dQ and the direct terms overwritten, the albedo added), then
-// dL/d(pos, dir) of every caller light u (one warp per output): the sum over
-// its views of J^T dL/dQ plus the direct terms of the shading direction omega
-// (directional omega = -dir / |dir|, spot and point omega = normalize(pos - x)).
-// A point light sums its six cube faces (their J has no direction columns).
-// float64 keeps the cancellation of both sums; the work is spread over the
-// threads because every float64 operation has a long latency.
+// block sums reduced (four threads per entry, 16 slots each, all loads issued
+// at once, then two shuffles; dQ and the direct terms overwritten, the albedo
+// added), then dL/d(pos, dir) of every caller light u: four threads
+// per (view l, parameter j) form view l's share J^T dL/dQ (five terms each)
+// plus the direct term of the shading direction omega (directional
+// omega = -dir / |dir|, spot and point omega = normalize(pos - x)), and thread
+// (u, j) adds the shares of u's views in view order (a point light's six cube
+// faces; their J has no direction columns).  float64 keeps the cancellation of
+// both sums.  float64 has a long latency here, so the views' J, direction and
+// type are staged in shared memory first (their loads overlap the slot
+// reduction's) and every float64 chain is kept short.
 __global__ void __launch_bounds__(1024) light_sums_kernel(const double* __restrict__ red, int stride, int L,
                                                           int n_mat_red, const LightDev* __restrict__ lights,
                                                           int n_user, double* __restrict__ gQ,
@@ -748,45 +726,83 @@ __global__ void __launch_bounds__(1024) light_sums_kernel(const double* __restri
                                                           float* __restrict__ dlight, float* __restrict__ loss,
                                                           double inv_n) {
   static_assert(kRedSlots % 4 == 0, "four threads per entry");
+  __shared__ double sred[kMaxLightViews * 23];   // dL/dQ (20 per view), then the direct terms (3 per view)
+  __shared__ double sshare[kMaxLightViews * 6];
+  __shared__ float sJ[kMaxLightViews * 120];
+  __shared__ float sdir[kMaxLightViews * 4];     // fwd xyz, |dir|
+  __shared__ int suser[kMaxLightViews], stype[kMaxLightViews];
+  const int t = threadIdx.x;
+  for (int i = t; i < L * 120; i += blockDim.x) sJ[i] = lights[i / 120].J[i % 120];
+  if (t < L) {
+    const LightDev& Ld = lights[t];
+    suser[t] = Ld.user;
+    stype[t] = Ld.type;
+    sdir[4 * t] = Ld.fwd[0];
+    sdir[4 * t + 1] = Ld.fwd[1];
+    sdir[4 * t + 2] = Ld.fwd[2];
+    sdir[4 * t + 3] = Ld.dir_norm;
+  }
   const int n = L * 23 + n_mat_red * 3 + (loss ? 1 : 0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int base = 0; base < 4 * n; base += blockDim.x) {
-    const int e = base + threadIdx.x, k = e >> 2, part = e & 3;
+    const int e = base + t, k = e >> 2, part = e & 3;
     double acc = 0.0;
     if (k < n)
-      for (int q = part; q < kRedSlots; q += 4) acc += red[(size_t)q * stride + k];
+#pragma unroll
+      for (int q = 0; q < kRedSlots / 4; ++q) acc += red[(size_t)(4 * q + part) * stride + k];
     acc += __shfl_xor_sync(kFull, acc, 1);
     acc += __shfl_xor_sync(kFull, acc, 2);
     if (k < n && part == 0) {
-      if (k < L * 20) gQ[k] = acc;
-      else if (k < L * 23) gdirect[k - L * 20] = acc;
-      else if (k < L * 23 + n_mat_red * 3) dalbedo[k - L * 23] += (float)acc;
-      else *loss = (float)(acc * inv_n);   // the mean squared error
+      if (k < L * 20) {
+        gQ[k] = acc;
+        sred[k] = acc;
+      } else if (k < L * 23) {
+        gdirect[k - L * 20] = acc;
+        sred[k] = acc;
+      } else if (k < L * 23 + n_mat_red * 3) {
+        dalbedo[k - L * 23] += (float)acc;
+      } else {
+        *loss = (float)(acc * inv_n);   // the mean squared error
+      }
     }
   }
-  __syncthreads();   // this block's writes of gQ and gdirect are visible to all its threads
-  for (int o = warp; o < n_user * 6; o += nwarps) {
-    const int u = o / 6, j = o - 6 * u;
+  __syncthreads();   // sred and the staged views
+  {
+    // thread t: view l, parameter j, terms k = part, part + 4, ... of J^T dL/dQ;
+    // part 1 adds the direct term
+    const int l = t / 24, j = (t % 24) >> 2, part = t & 3;
+    const bool ok = t < L * 24;
     double acc = 0.0;
-    for (int l = 0; l < L; ++l) {
-      const LightDev& Ld = lights[l];
-      if (Ld.user != u) continue;
-      if (lane < 20) acc += gQ[l * 20 + lane] * (double)Ld.J[lane * 6 + j];
-      if (lane == 20) {
-        const double* gd = gdirect + 3 * l;
-        if (Ld.type == 1) {
+    if (ok) {
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        const int k = part + 4 * m;
+        acc += sred[l * 20 + k] * widen_exact(sJ[l * 120 + k * 6 + j]);
+      }
+      const double* gd = sred + L * 20 + 3 * l;
+      if (part == 1) {
+        if (stype[l] == 1) {
           if (j < 3) acc += gd[j];
         } else if (j >= 3) {
           const int c = j - 3;
-          const float* f = Ld.fwd;
-          const double fg = f[0] * gd[0] + f[1] * gd[1] + f[2] * gd[2];
-          acc += -(gd[c] - f[c] * fg) / Ld.dir_norm;
+          const float* fw = sdir + 4 * l;
+          const double f0 = widen_exact(fw[0]), f1 = widen_exact(fw[1]), f2 = widen_exact(fw[2]);
+          const double fc = c == 0 ? f0 : (c == 1 ? f1 : f2);
+          const double fg = f0 * gd[0] + f1 * gd[1] + f2 * gd[2];
+          acc += -(gd[c] - fc * fg) / widen_exact(fw[3]);
         }
       }
     }
-#pragma unroll
-    for (int m = 16; m; m >>= 1) acc += __shfl_xor_sync(kFull, acc, m);
-    if (lane == 0) dlight[u * 6 + j] = (float)acc;
+    acc += __shfl_xor_sync(kFull, acc, 1);
+    acc += __shfl_xor_sync(kFull, acc, 2);
+    if (ok && part == 0) sshare[l * 6 + j] = acc;
+  }
+  __syncthreads();   // sshare
+  if (t < n_user * 6) {
+    const int u = t / 6, j = t - 6 * u;
+    double acc = 0.0;
+    for (int l = 0; l < L; ++l)
+      if (suser[l] == u) acc += sshare[l * 6 + j];
+    dlight[t] = (float)acc;
   }
 }
 
@@ -814,13 +830,6 @@ __global__ void l2_kernel(const float* __restrict__ img, const float* __restrict
 
 // ------------------------------------------------------------------ launchers
 static inline dim3 grid2(int W, int H, dim3 b) { return dim3((W + b.x - 1) / b.x, (H + b.y - 1) / b.y); }
-
-void launch_vertex_normals(const float* verts, int V, const int* tris, const int* vf_off, const int* vf_list,
-                           float* vnormal, float* vlen, cudaStream_t st) {
-  if (V == 0) return;
-  count_launches(1);
-  vertex_normals_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, V, tris, vf_off, vf_list, vnormal, vlen);
-}
 
 void launch_normals_backward(const float* verts, int V, const int* tris, int T, const int* vf_off,
                              const int* vf_list, const float* vnormal, const float* vlen, const float4* gnormal,
