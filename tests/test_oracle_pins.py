@@ -136,6 +136,39 @@ def _ortho_screen_matrix(W, H):
     return M
 
 
+def _is_sqrt_rn(s: float, r: float) -> bool:
+    """r is sqrt(s) rounded to nearest: s lies between the squares of the
+    midpoints to r's float64 neighbours (exact rational arithmetic)."""
+    from fractions import Fraction
+    lo, hi = Fraction(math.nextafter(r, 0.0)), Fraction(math.nextafter(r, math.inf))
+    m_lo, m_hi = (lo + Fraction(r)) / 2, (Fraction(r) + hi) / 2
+    return m_lo * m_lo <= Fraction(s) <= m_hi * m_hi
+
+
+def test_frame_norm_is_correctly_rounded():
+    """Supplementary Sec. A light cameras: Q's entries are formed in float64
+    with every operation rounded once, so the frame's norms are IEEE square
+    roots.  Pinned in exact rational arithmetic on random sums of squares and
+    on the light direction whose float64 norm torch.sqrt rounds one ulp off;
+    the derivative is torch.sqrt's."""
+    rng = np.random.default_rng(31)
+    for s in list(rng.uniform(0.25, 4.0, 2000)) + [float.fromhex("0x1.0000007822024p+0"), 1.0, 2.0, 0.5]:
+        r = float(O._sqrt_rn(torch.tensor(s, dtype=F64)))
+        assert _is_sqrt_rn(s, r), s.hex()
+    x = torch.tensor(float.fromhex("0x1.0000007822024p+0"), dtype=F64, requires_grad=True)
+    O._sqrt_rn(x).backward()
+    assert abs(float(x.grad) - 0.5 / math.sqrt(float(x.detach()))) < 1e-15
+    # the direction whose norm exposed it: Q's translation column of rows 0 and 1
+    # (a cancellation, r.e and u.e with e = -dist f) then matches a plain-float
+    # evaluation of the same operations
+    d = np.array([np.float32(-0.80092883), np.float32(-0.49904314), np.float32(-0.33086097)], np.float64)
+    n = math.sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2])
+    assert _is_sqrt_rn((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2], n)
+    f = torch.as_tensor(d, dtype=F64)
+    fo = O._normalize(f).numpy()
+    assert np.array_equal(fo, d / n)
+
+
 def test_top_left_rule_rectangle():
     """A rectangle with corners exactly on pixel centres covers the half-open
     set [i0, i1) x [j0, j1): left/top edges in, right/bottom edges out."""
