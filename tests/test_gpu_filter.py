@@ -67,6 +67,17 @@ def test_filter_and_transpose_match_oracle(res, sigma, radius, kind, boundary):
     ctx.close()
 
 
+# every radius the filter takes (1 to 32: the tiled kernel up to 15, two 1-D
+# passes above), each map side a multiple of 16 (the TMA-staged path, radius up
+# to 8) or ragged, the kinds and boundaries in turn
+SWEEP = [(48 if r % 2 else 37, 0.4 * r + 0.3, r, (r // 2) % 2, (r // 4) % 2) for r in range(1, 33)]
+
+
+@pytest.mark.parametrize("res,sigma,radius,kind,boundary", SWEEP, ids=[f"r{c[2]}" for c in SWEEP])
+def test_filter_radius_sweep_matches_oracle(res, sigma, radius, kind, boundary):
+    test_filter_and_transpose_match_oracle(res, sigma, radius, kind, boundary)
+
+
 def test_filter_rejects_bad_arguments():
     from paper_2308_10896_b300 import dsm
     ctx = _ctx()
