@@ -1,0 +1,125 @@
+"""The rasteriser's ids and depth keys on adversarial geometry, bit for bit
+against the oracle (Eq. 1: the nearest surface per pixel centre, with the
+top-left fill rule and the (depth, triangle) key).
+
+A directional light looking straight down with ortho_half = 4 maps world x
+and z onto a 64 x 64 shadow map by exact float32 operations: a vertex whose x
+and z are multiples of 1/16 snaps exactly onto a texel centre or a texel edge.
+Each scene mixes:
+- a grid of quads split into triangles with alternating diagonals: shared
+  edges through texel centres, every centre covered exactly once;
+- small random triangles on the same dyadic grid at three heights, so that
+  coplanar overlaps tie on depth and the triangle index decides;
+- slivers (one edge a sixteenth of a texel) and a few triangles spanning
+  most of the map (the int64 edge steps, the big-triangle binning);
+and is rastered with 32- and 16-texel tiles, and with every large triangle
+binned as big.  The camera rasters the same soup in perspective, and a
+48 x 48 map (texels of 1/6) gives ragged tiles without exact alignment.
+"""
+import numpy as np
+import pytest
+import torch
+
+import scenes
+from oracle import dsm_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+G = 1.0 / 16.0   # half a texel of the 64 x 64 map
+
+
+def _soup(seed: int):
+    rng = np.random.default_rng(40_000 + seed)
+    verts, tris = [], []
+
+    def tri(a, b, c):
+        base = len(verts)
+        verts.extend([a, b, c])
+        tris.append([base, base + 1, base + 2])
+
+    def snap(v):
+        return np.round(np.asarray(v) / G) * G
+
+    # a 6 x 6 grid of quads of 0.75 x 0.75 at y = 0
+    x0, z0, s = -2.25, -2.25, 0.75
+    for i in range(6):
+        for j in range(6):
+            a = (x0 + i * s, 0.0, z0 + j * s)
+            b = (x0 + (i + 1) * s, 0.0, z0 + j * s)
+            c = (x0 + (i + 1) * s, 0.0, z0 + (j + 1) * s)
+            d = (x0 + i * s, 0.0, z0 + (j + 1) * s)
+            if (i + j) % 2:
+                tri(a, b, c); tri(a, c, d)
+            else:
+                tri(a, b, d); tri(b, c, d)
+    # small dyadic triangles at three heights (coplanar overlaps tie on depth)
+    for _ in range(160):
+        y = float(rng.choice([0.25, 0.5, 0.75]))
+        p = snap(rng.uniform(-3.5, 3.5, 2))
+        q = p + snap(rng.uniform(-0.6, 0.6, 2))
+        r = p + snap(rng.uniform(-0.6, 0.6, 2))
+        tri((p[0], y, p[1]), (q[0], y, q[1]), (r[0], y, r[1]))
+    # slivers: one edge a sixteenth of a texel
+    for _ in range(40):
+        y = float(rng.uniform(0.1, 0.9))
+        p = snap(rng.uniform(-3.5, 3.5, 2))
+        d = rng.choice([-1.0, 1.0], 2) * G / 8
+        q = p + snap(rng.uniform(-1.5, 1.5, 2))
+        tri((p[0], y, p[1]), (p[0] + d[0], y, p[1] + d[1]), (q[0], y, q[1]))
+    # large triangles over most of the map, tilted (depth varies across them)
+    for k in range(4):
+        c = rng.uniform(-0.5, 0.5, 2)
+        tri((c[0] - 3.6, 0.05 * k, c[1] - 3.4), (c[0] + 3.5, 0.3, c[1] - 3.6), (c[0], 0.9 - 0.1 * k, c[1] + 3.6))
+    v = np.asarray(verts, np.float32)
+    t = np.asarray(tris, np.int32)
+    light = scenes.directional_light((0.0, -1.0, 0.0), 64, ortho_half=4.0, dist=8.0, near=1.0, far=16.0, sigma=1.0)
+    ragged = scenes.directional_light((0.3, -1.0, 0.2), 48, ortho_half=4.0, dist=8.0, near=1.0, far=16.0, sigma=1.0)
+    cam = scenes.look_at_perspective((0.3, 5.0, 3.0), (0.0, 0.0, 0.0), 50.0, 48, 40)
+    return {"name": f"soup{seed}", "verts": v, "tris": t, "tri_mat": np.zeros(len(t), np.int32),
+            "albedo": np.array([[0.8, 0.8, 0.8]], np.float32), "lights": [light, ragged], "camera": cam,
+            "params": scenes._default_params()}
+
+
+SHAPES = [(32, 16), (16, 16), (32, 2), (16, 2)]   # (tile side, big_tiles)
+_refs = {}
+
+
+def _ref(seed):
+    if seed not in _refs:
+        sc = _soup(seed)
+        _refs[seed] = (sc, O.render(sc))
+    return _refs[seed]
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("tile,big", SHAPES, ids=[f"tile{t}_big{b}" for t, b in SHAPES])
+def test_adversarial_raster_bit_exact(seed, tile, big):
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    sc, ref = _ref(seed)
+    r = dsm.Renderer(sc)
+    r.ctx.set_tuning(light_tile=tile, camera_tile=tile, big_tiles=big)
+    r.forward()
+    r.ctx.sync()
+    rasters = [L["raster"] for L in ref["lights"]] + [ref["camera_raster"]]
+    sizes = [(L["res"], L["res"]) for L in sc["lights"]] + [(sc["camera"]["width"], sc["camera"]["height"])]
+    for w, (ras, (W, H)) in enumerate(zip(rasters, sizes)):
+        g = r.ctx.debug(dsm.DBG_GBUF, w, (H, W, 4)).cpu()
+        ids = g[..., 0].contiguous().view(torch.int32).numpy().astype(np.int64)
+        zk = g[..., 3].numpy()
+        assert np.array_equal(ids, ras["ids"]), f"view {w}: {int(np.sum(ids != ras['ids']))} ids differ"
+        cov = ids > 0
+        assert np.array_equal(zk[cov].view(np.uint32), ras["zkey"][cov].view(np.uint32)), f"view {w} keys"
+    r.ctx.close()
+
+
+def test_soup_has_exact_ties():
+    """The straight-down light's snapped texel coordinates land on texel
+    centres (shared edges through them) and coplanar triangles overlap."""
+    sc, ref = _ref(0)
+    st = ref["lights"][0]["setup"]
+    X = np.asarray(st["X"], np.int64)
+    assert np.mean((X % 256) == 128) > 0.25     # vertices exactly on a texel centre column
+    assert np.mean((X % 128) == 0) > 0.9        # and nearly all on the half-texel grid
+    ids = ref["lights"][0]["raster"]["ids"]
+    assert (ids > 0).mean() > 0.5
