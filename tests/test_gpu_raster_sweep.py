@@ -123,3 +123,38 @@ def test_soup_has_exact_ties():
     assert np.mean((X % 128) == 0) > 0.9        # and nearly all on the half-texel grid
     ids = ref["lights"][0]["raster"]["ids"]
     assert (ids > 0).mean() > 0.5
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("tile", [32, 16])
+def test_adversarial_antialias_detection(seed, tile):
+    """The antialiasing detection, fused into the raster's epilogue with a seam
+    pass for the pairs across tile edges (which pairs are which depends on the
+    tile side): every view lists exactly as many pixels as the oracle's
+    silhouette band holds, and f~ of each light (taught the GPU's f) matches the
+    oracle's antialiasing at the stage bar."""
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    sc, ref = _ref(seed)
+    r = dsm.Renderer(sc)
+    r.ctx.set_tuning(light_tile=tile, camera_tile=tile)
+    r.forward()
+    r.ctx.sync()
+    tris = np.asarray(sc["tris"], np.int64)
+    adj = O.edge_adjacency(tris)
+    views = [(L["raster"], L["setup"]) for L in ref["lights"]] + [(ref["camera_raster"], ref["camera_setup"])]
+    for w, (ras, st) in enumerate(views):
+        band = O.silhouette_band(ras, O.silhouette_table(adj, st))
+        assert r.ctx.raster_stats(w)["aa_listed"] == int(band.sum()), f"view {w}"
+    for l, L in enumerate(ref["lights"]):
+        R = sc["lights"][L["light"]]["res"]
+        fg = r.ctx.debug(dsm.DBG_F, l, (R, R, 2)).cpu().numpy()
+        ftg = r.ctx.debug(dsm.DBG_FTILDE, l, (R, R, 2)).cpu().numpy()
+        vh = torch.cat([torch.as_tensor(sc["verts"], dtype=torch.float64),
+                        torch.ones((len(sc["verts"]), 1), dtype=torch.float64)], 1)
+        sx, sy = O.screen_coords(vh @ L["Q"].detach()[:4].T, R, R)
+        exp = O.antialias(torch.as_tensor(fg, dtype=torch.float64), L["raster"], L["setup"],
+                          O.silhouette_table(adj, L["setup"]), tris, sx, sy).numpy()
+        bad = np.abs(ftg - exp) > 1e-5 + 1e-4 * np.abs(exp)
+        assert not bad.any(), f"f~ light {l}: {int(bad.sum())} texels off, max {np.abs(ftg - exp).max():.3g}"
+    r.ctx.close()
