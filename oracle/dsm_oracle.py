@@ -619,14 +619,22 @@ def light_visibility(Q: torch.Tensor, mom: torch.Tensor, xh: torch.Tensor, min_v
 
 
 def vertex_normals(verts: torch.Tensor, tris: torch.Tensor) -> torch.Tensor:
-    """Area-weighted sum of face normals cross(v1 - v0, v2 - v0), normalised."""
+    """Area-weighted sum of face normals cross(v1 - v0, v2 - v0), normalised.
+
+    reading: a vertex whose incident faces all have zero area has no normal
+    direction; it keeps the zero vector, and the derivative there is that of
+    the identity.  The square root is taken of a stand-in for those vertices,
+    so that its infinite slope at 0 never multiplies their zero gradient (a
+    NaN in reverse mode)."""
     v0, v1, v2 = verts[tris[:, 0]], verts[tris[:, 1]], verts[tris[:, 2]]
     fn = torch.cross(v1 - v0, v2 - v0, dim=1)
     n = torch.zeros_like(verts)
     for k in range(3):
         n = n.index_add(0, tris[:, k], fn)
-    ln = torch.sqrt((n * n).sum(1, keepdim=True))
-    return n / torch.where(ln > 0, ln, torch.ones_like(ln))
+    s = (n * n).sum(1, keepdim=True)
+    pos = s > 0
+    ln = torch.sqrt(torch.where(pos, s, torch.ones_like(s)))
+    return n / torch.where(pos, ln, torch.ones_like(ln))
 
 
 # =============================================================================== pipeline

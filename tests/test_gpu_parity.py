@@ -50,6 +50,9 @@ SCENES = {
     # a dense sphere (2880 triangles within a few tiles): tiles of thousands of records, rastered by
     # several work units whose minima merge in a key slot
     "tiny_dense": lambda: scenes.tiny_scene(16, res=64, img=48, kind="mixed", n_lights=2, freq=12),
+    # an adversarial triangle soup (test_gpu_raster_sweep): exact texel-centre ties under a straight-down
+    # light, coplanar overlaps, slivers, map-spanning triangles, a ragged second map
+    "soup": lambda: scenes.triangle_soup(0),
 }
 
 _cache = {}

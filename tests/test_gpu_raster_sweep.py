@@ -25,68 +25,13 @@ from oracle import dsm_oracle as O
 
 pytestmark = pytest.mark.gpu
 
-G = 1.0 / 16.0   # half a texel of the 64 x 64 map
-
-
-def _soup(seed: int):
-    rng = np.random.default_rng(40_000 + seed)
-    verts, tris = [], []
-
-    def tri(a, b, c):
-        base = len(verts)
-        verts.extend([a, b, c])
-        tris.append([base, base + 1, base + 2])
-
-    def snap(v):
-        return np.round(np.asarray(v) / G) * G
-
-    # a 6 x 6 grid of quads of 0.75 x 0.75 at y = 0
-    x0, z0, s = -2.25, -2.25, 0.75
-    for i in range(6):
-        for j in range(6):
-            a = (x0 + i * s, 0.0, z0 + j * s)
-            b = (x0 + (i + 1) * s, 0.0, z0 + j * s)
-            c = (x0 + (i + 1) * s, 0.0, z0 + (j + 1) * s)
-            d = (x0 + i * s, 0.0, z0 + (j + 1) * s)
-            if (i + j) % 2:
-                tri(a, b, c); tri(a, c, d)
-            else:
-                tri(a, b, d); tri(b, c, d)
-    # small dyadic triangles at three heights (coplanar overlaps tie on depth)
-    for _ in range(160):
-        y = float(rng.choice([0.25, 0.5, 0.75]))
-        p = snap(rng.uniform(-3.5, 3.5, 2))
-        q = p + snap(rng.uniform(-0.6, 0.6, 2))
-        r = p + snap(rng.uniform(-0.6, 0.6, 2))
-        tri((p[0], y, p[1]), (q[0], y, q[1]), (r[0], y, r[1]))
-    # slivers: one edge a sixteenth of a texel
-    for _ in range(40):
-        y = float(rng.uniform(0.1, 0.9))
-        p = snap(rng.uniform(-3.5, 3.5, 2))
-        d = rng.choice([-1.0, 1.0], 2) * G / 8
-        q = p + snap(rng.uniform(-1.5, 1.5, 2))
-        tri((p[0], y, p[1]), (p[0] + d[0], y, p[1] + d[1]), (q[0], y, q[1]))
-    # large triangles over most of the map, tilted (depth varies across them)
-    for k in range(4):
-        c = rng.uniform(-0.5, 0.5, 2)
-        tri((c[0] - 3.6, 0.05 * k, c[1] - 3.4), (c[0] + 3.5, 0.3, c[1] - 3.6), (c[0], 0.9 - 0.1 * k, c[1] + 3.6))
-    v = np.asarray(verts, np.float32)
-    t = np.asarray(tris, np.int32)
-    light = scenes.directional_light((0.0, -1.0, 0.0), 64, ortho_half=4.0, dist=8.0, near=1.0, far=16.0, sigma=1.0)
-    ragged = scenes.directional_light((0.3, -1.0, 0.2), 48, ortho_half=4.0, dist=8.0, near=1.0, far=16.0, sigma=1.0)
-    cam = scenes.look_at_perspective((0.3, 5.0, 3.0), (0.0, 0.0, 0.0), 50.0, 48, 40)
-    return {"name": f"soup{seed}", "verts": v, "tris": t, "tri_mat": np.zeros(len(t), np.int32),
-            "albedo": np.array([[0.8, 0.8, 0.8]], np.float32), "lights": [light, ragged], "camera": cam,
-            "params": scenes._default_params()}
-
-
 SHAPES = [(32, 16), (16, 16), (32, 2), (16, 2)]   # (tile side, big_tiles)
 _refs = {}
 
 
 def _ref(seed):
     if seed not in _refs:
-        sc = _soup(seed)
+        sc = scenes.triangle_soup(seed)
         _refs[seed] = (sc, O.render(sc))
     return _refs[seed]
 

@@ -565,6 +565,31 @@ def test_vertex_normals_closed_forms():
     assert errs[0] < 2e-2 and errs[1] < 0.6 * errs[0]      # converges to the radial normal
 
 
+def test_vertex_normals_of_zero_area_faces_are_zero_with_finite_derivative():
+    """A vertex whose faces all have zero area (collinear or coincident corners)
+    keeps the zero normal, and reverse mode through it stays finite: its
+    derivative is the identity's, so a zero upstream gradient gives zero.  The
+    other vertices keep their unit normals."""
+    v = torch.tensor([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0],       # a proper triangle
+                      [2.0, 0.0, 0.0], [3.0, 0.0, 0.0], [4.0, 0.0, 0.0],       # collinear corners
+                      [5.0, 1.0, 5.0], [5.0, 1.0, 5.0], [6.0, 1.0, 5.0]],      # two coincident corners
+                     dtype=F64, requires_grad=True)
+    t = torch.tensor([[0, 2, 1], [3, 4, 5], [6, 7, 8]])
+    n = O.vertex_normals(v, t)
+    assert torch.equal(n[3:].detach(), torch.zeros(6, 3, dtype=F64))
+    np.testing.assert_allclose(n[:3].detach().numpy(), [[0.0, 1.0, 0.0]] * 3, atol=1e-15)
+    w = torch.zeros(9, 3, dtype=F64)
+    w[:3] = torch.randn(3, 3, dtype=F64, generator=torch.Generator().manual_seed(3))
+    (n * w).sum().backward()
+    g = v.grad.numpy()
+    assert np.isfinite(g).all() and np.abs(g[3:]).max() == 0.0
+    # an upstream gradient on a zero normal passes through as the identity's
+    v.grad = None
+    n = O.vertex_normals(v, t)
+    n[4].sum().backward()
+    assert np.isfinite(v.grad.numpy()).all()
+
+
 def test_spot_light_lambert_closed_form():
     """Supplementary Sec. A: for a spot light omega = normalize(p - x); on an
     unshadowed plane c = albedo I max(0, n . omega) at the camera ray's hit."""
