@@ -651,13 +651,33 @@ __global__ void alloc_units_kernel(const int* __restrict__ count, int n, int* __
 // with the top-left rule; returns the depth key or ~0.  The record is read as
 // words in TriSetup order (X[3], Y[3], z[3], a2f, ibox, jbox, tri, flags).
 // Correctly rounded int64 -> float32 without the 64-bit conversion (which
-// runs on the slow double-precision pipe): v = h 2^24 + l with h = v >> 24 and
-// 0 <= l < 2^24 both exact in float32, and one fused multiply-add rounds the
-// exact sum h 2^24 + l once, to nearest even.  Exact for |v| < 2^55.
+// runs on the slow double-precision pipe).  For |v| < 2^48: v = h 2^24 + l
+// with h = v >> 24 and 0 <= l < 2^24 both exact in float32, and one fused
+// multiply-add rounds the exact sum once, to nearest even.
 __device__ __forceinline__ float ll_to_float(long long v) {
   const float h = __int2float_rn((int)(v >> 24));
   const float l = __int2float_rn((int)(v & 0xffffff));
   return __fmaf_rn(h, 16777216.f, l);
+}
+// Any int64 (h above is no longer exact in float32 from 2^48 on; edge
+// functions this large need vertices tens of thousands of pixels off
+// screen): IEEE rounding written out on the integer pipes, |v| shifted so
+// that its leading one is bit 63, the top 24 bits kept and rounded to nearest
+// even on the 40 below them.
+__device__ __forceinline__ float ll_to_float_wide(long long v) {
+  if (v == 0) return 0.f;
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll(a);
+  const unsigned long long m = a << lz;
+  unsigned mant = (unsigned)(m >> 40);
+  const unsigned long long rest = m & ((1ull << 40) - 1), half = 1ull << 39;
+  if (rest > half || (rest == half && (mant & 1u))) ++mant;
+  int e = 63 - lz;
+  if (mant == (1u << 24)) {   // the rounding carried into a new leading bit
+    mant >>= 1;
+    ++e;
+  }
+  return __uint_as_float((v < 0 ? 0x80000000u : 0u) | ((unsigned)(e + 127) << 23) | (mant & 0x7fffffu));
 }
 
 __device__ __forceinline__ float key_depth(uint64_t key) {
@@ -691,6 +711,7 @@ __device__ __forceinline__ void rec_set_ll(int* w, int o, long long v) {
 }
 
 constexpr int kRecSmall = 32;   // the biased edge functions fit int32 over the tile
+constexpr int kRecWide = 64;    // 2A >= 2^48: a covered pixel's edge functions (0 <= E_k <= 2A) may exceed 2^48
 constexpr int kSpan = 4;
 __device__ __forceinline__ void rec_stage(const TriSetup& r, long long Px0, long long Py0, int* w) {
   const int sg = (r.flags & 8) ? -1 : 1;
@@ -714,21 +735,21 @@ __device__ __forceinline__ void rec_stage(const TriSetup& r, long long Px0, long
   w[kRecZ + 2] = __float_as_int(r.z[2]);
   w[kRecA2] = __float_as_int(r.a2f);
   w[kRecTri] = r.tri;
-  w[kRecFlags] = r.flags | (small ? kRecSmall : 0);
+  w[kRecFlags] = r.flags | (small ? kRecSmall : 0) | (r.a2f >= 281474976710656.f ? kRecWide : 0);
 }
 
 // Coverage of the span of pixels xs..xe of row y by a staged record: the
 // biased edge functions at (xs, y), then one step per pixel along x; a pixel
 // is covered iff no biased edge function is negative (one sign test of their
 // OR).  TE is int when the record's edge functions fit int32 over the tile.
-template <typename TE>
-__device__ __forceinline__ float edge_float(TE v);
-template <>
-__device__ __forceinline__ float edge_float<int>(int v) { return __int2float_rn(v); }
-template <>
-__device__ __forceinline__ float edge_float<long long>(long long v) { return ll_to_float(v); }
+template <typename TE, bool kWide>
+__device__ __forceinline__ float edge_float(TE v) {
+  if constexpr (sizeof(TE) == 4) return __int2float_rn(v);
+  else if constexpr (kWide) return ll_to_float_wide(v);
+  else return ll_to_float(v);
+}
 
-template <typename TE, int kTileT>
+template <typename TE, int kTileT, bool kWide = false>
 __device__ __forceinline__ void cover_span(const int* w, int xs, int xe, int y, unsigned long long* sbest) {
   const int flags = w[kRecFlags];
   TE E[3], S[3];
@@ -745,9 +766,9 @@ __device__ __forceinline__ void cover_span(const int* w, int xs, int xe, int y, 
   for (int k = 0; k < kSpan; ++k) {
     if (xs + k <= xe && (E[0] | E[1] | E[2]) >= 0) {
       // the unbiased edge functions weight the corner depths (Eq. 1's key)
-      const float e0 = edge_float<TE>(E[0] + (TE)((flags & 1) ^ 1));
-      const float e1 = edge_float<TE>(E[1] + (TE)(((flags >> 1) & 1) ^ 1));
-      const float e2 = edge_float<TE>(E[2] + (TE)(((flags >> 2) & 1) ^ 1));
+      const float e0 = edge_float<TE, kWide>(E[0] + (TE)((flags & 1) ^ 1));
+      const float e1 = edge_float<TE, kWide>(E[1] + (TE)(((flags >> 1) & 1) ^ 1));
+      const float e2 = edge_float<TE, kWide>(E[2] + (TE)(((flags >> 2) & 1) ^ 1));
       const float z = __fdiv_rn(__fadd_rn(__fadd_rn(__fmul_rn(e0, __int_as_float(w[kRecZ])),
                                                     __fmul_rn(e1, __int_as_float(w[kRecZ + 1]))),
                                           __fmul_rn(e2, __int_as_float(w[kRecZ + 2]))),
@@ -862,8 +883,10 @@ __global__ void __launch_bounds__(256, 6) raster_kernel(const TriSetup* __restri
       const int qy = (it * sinv[rec]) >> 16;   // it / wd (exact for it <= 256 spans, wd <= 8)
       const int xs = x0 + kSpan * (it - qy * wd), y = y0 + qy;
       const int* rw = sq + rec * kRecStride;
-      if (rw[kRecFlags] & kRecSmall) cover_span<int, kTile>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
-      else cover_span<long long, kTile>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
+      const int rf = rw[kRecFlags];
+      if (rf & kRecSmall) cover_span<int, kTile>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
+      else if (!(rf & kRecWide)) cover_span<long long, kTile>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
+      else cover_span<long long, kTile, true>(rw, xs, min(xs + kSpan - 1, x1), y, sbest);
     }
     __syncthreads();
   }

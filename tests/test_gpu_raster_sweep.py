@@ -103,3 +103,58 @@ def test_adversarial_antialias_detection(seed, tile):
         bad = np.abs(ftg - exp) > 1e-5 + 1e-4 * np.abs(exp)
         assert not bad.any(), f"f~ light {l}: {int(bad.sum())} texels off, max {np.abs(ftg - exp).max():.3g}"
     r.ctx.close()
+
+
+def _huge_scene():
+    """Two crossing triangles whose corners lie about 25,000 map widths off
+    the map, inside the guard band: their edge functions at the texel centres
+    reach 2^56, beyond the exact range of the raster's fast int64-to-float
+    split (2^48), and the two surfaces' depth keys decide the nearest one."""
+    X, k = 100_000.0, 4e-6
+    # planes y = 0.5 + k x and y = 0.5 + k z, crossing along x = z through the map
+    a = [(-X, -X), (X, -0.9 * X), (0.3 * X, X)]
+    b = [(-0.8 * X, X), (X, 0.7 * X), (-0.2 * X, -X)]
+    verts = np.array([(x, 0.5 + k * x, z) for x, z in a] + [(x, 0.5 + k * z, z) for x, z in b], np.float32)
+    tris = np.array([[0, 2, 1], [3, 5, 4]], np.int32)
+    light = scenes.directional_light((0.0, -1.0, 0.0), 64, ortho_half=4.0, dist=8.0, near=1.0, far=16.0, sigma=1.0)
+    cam = scenes.look_at_perspective((0.3, 5.0, 3.0), (0.0, 0.0, 0.0), 50.0, 32, 24)
+    return {"name": "huge", "verts": verts, "tris": tris, "tri_mat": np.zeros(2, np.int32),
+            "albedo": np.array([[0.8, 0.8, 0.8]], np.float32), "lights": [light], "camera": cam,
+            "params": scenes._default_params()}
+
+
+def test_huge_triangles_reach_wide_edge_functions():
+    """The scene does what it is for: the oracle's edge functions at covered
+    texel centres exceed 2^55, and both triangles win some texels."""
+    sc = _huge_scene()
+    ref = O.render(sc)
+    st, ras = ref["lights"][0]["setup"], ref["lights"][0]["raster"]
+    X, Y = np.asarray(st["X"], np.int64), np.asarray(st["Y"], np.int64)
+    assert np.abs(X).max() < (1 << 28) and np.abs(Y).max() < (1 << 28) and np.abs(X).max() > (1 << 27)
+    ids = ras["ids"]
+    assert set(np.unique(ids)) == {1, 2}
+    t = sc["tris"][0]
+    j, i = np.nonzero(ids == 1)
+    px, py = 256 * i[0] + 128, 256 * j[0] + 128
+    a, b = t[1], t[2]
+    e = (int(X[b]) - int(X[a])) * (py - int(Y[a])) - (int(Y[b]) - int(Y[a])) * (px - int(X[a]))
+    assert abs(e) >= 1 << 55
+
+
+@pytest.mark.parametrize("tile", [32, 16])
+def test_huge_triangles_bit_exact(tile):
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    sc = _huge_scene()
+    ref = O.render(sc)
+    r = dsm.Renderer(sc)
+    r.ctx.set_tuning(light_tile=tile, camera_tile=tile)
+    r.forward()
+    r.ctx.sync()
+    ras = ref["lights"][0]["raster"]
+    g = r.ctx.debug(dsm.DBG_GBUF, 0, (64, 64, 4)).cpu()
+    ids = g[..., 0].contiguous().view(torch.int32).numpy().astype(np.int64)
+    zk = g[..., 3].numpy()
+    assert np.array_equal(ids, ras["ids"]), f"{int(np.sum(ids != ras['ids']))} ids differ"
+    assert np.array_equal(zk.view(np.uint32), ras["zkey"].view(np.uint32)), "keys differ"
+    r.ctx.close()
