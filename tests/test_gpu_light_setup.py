@@ -16,7 +16,6 @@ import torch
 import scenes
 from oracle import dsm_oracle as O
 
-pytestmark = pytest.mark.gpu
 
 F64 = torch.float64
 
@@ -77,6 +76,7 @@ def test_light_sets_fill_the_limits():
     assert max(len(ls) for _, ls in LIGHT_SETS) == 8 and max(views) == 24 and all(v <= 24 for v in views)
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("k", range(len(LIGHT_SETS)), ids=[f"{n}{k}" for k, (n, _) in enumerate(LIGHT_SETS)])
 def test_random_light_matrices_bit_exact(k):
     from paper_2308_10896_b300 import dsm

@@ -23,7 +23,6 @@ import torch
 import scenes
 from oracle import dsm_oracle as O
 
-pytestmark = pytest.mark.gpu
 
 SHAPES = [(32, 16), (16, 16), (32, 2), (16, 2)]   # (tile side, big_tiles)
 _refs = {}
@@ -36,6 +35,7 @@ def _ref(seed):
     return _refs[seed]
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("seed", range(3))
 @pytest.mark.parametrize("tile,big", SHAPES, ids=[f"tile{t}_big{b}" for t, b in SHAPES])
 def test_adversarial_raster_bit_exact(seed, tile, big):
@@ -70,6 +70,7 @@ def test_soup_has_exact_ties():
     assert (ids > 0).mean() > 0.5
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("seed", range(3))
 @pytest.mark.parametrize("tile", [32, 16])
 def test_adversarial_antialias_detection(seed, tile):
@@ -141,6 +142,7 @@ def test_huge_triangles_reach_wide_edge_functions():
     assert abs(e) >= 1 << 55
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("tile", [32, 16])
 def test_huge_triangles_bit_exact(tile):
     from paper_2308_10896_b300 import dsm
