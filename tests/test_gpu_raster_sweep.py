@@ -160,3 +160,37 @@ def test_huge_triangles_bit_exact(tile):
     assert np.array_equal(ids, ras["ids"]), f"{int(np.sum(ids != ras['ids']))} ids differ"
     assert np.array_equal(zk.view(np.uint32), ras["zkey"].view(np.uint32)), "keys differ"
     r.ctx.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("seed", range(2))
+@pytest.mark.parametrize("kind", ["spot", "point"])
+@pytest.mark.parametrize("tile", [32, 16])
+def test_adversarial_soup_under_perspective_lights(seed, kind, tile):
+    """The soups under a perspective light: a spot light above them, or a
+    point light among them whose six cube faces each raster a part (faces
+    that see nothing included); ids and depth keys of every view bit for bit."""
+    from paper_2308_10896_b300 import dsm
+    torch.cuda.set_device(0)
+    sc = scenes.triangle_soup(seed)
+    if kind == "spot":
+        sc["lights"] = [scenes.spot_light((0.4, 6.0, -0.3), (-0.05, -1.0, 0.04), 48, 70.0, near=0.5, far=12.0,
+                                          sigma=1.0)]
+    else:
+        sc["lights"] = [scenes.point_light((0.2, 1.2, -0.1), 40, near=0.05, far=10.0, sigma=1.0)]
+    ref = O.render(sc)
+    r = dsm.Renderer(sc)
+    r.ctx.set_tuning(light_tile=tile, camera_tile=tile)
+    r.forward()
+    r.ctx.sync()
+    R = sc["lights"][0]["res"]
+    views = [(L["raster"], R, R) for L in ref["lights"]] + [(ref["camera_raster"], sc["camera"]["width"],
+                                                              sc["camera"]["height"])]
+    for w, (ras, W, H) in enumerate(views):
+        g = r.ctx.debug(dsm.DBG_GBUF, w, (H, W, 4)).cpu()
+        ids = g[..., 0].contiguous().view(torch.int32).numpy().astype(np.int64)
+        zk = g[..., 3].numpy()
+        assert np.array_equal(ids, ras["ids"]), f"view {w}: {int(np.sum(ids != ras['ids']))} ids differ"
+        cov = ids > 0
+        assert np.array_equal(zk[cov].view(np.uint32), ras["zkey"][cov].view(np.uint32)), f"view {w} keys"
+    r.ctx.close()
