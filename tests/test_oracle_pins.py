@@ -169,6 +169,31 @@ def test_frame_norm_is_correctly_rounded():
     assert np.array_equal(fo, d / n)
 
 
+def test_edge_function_to_float32_is_correctly_rounded():
+    """Eq. 1's depth key interpolates the corner depths with the integer edge
+    functions converted to float32; for triangles far off screen these reach
+    2^58.  The oracle's int64 -> float32 cast rounds each to the nearest
+    float32, ties to even: checked in exact integer arithmetic against both
+    float32 neighbours, on random magnitudes up to 2^62 and on exact ties."""
+    rng = np.random.default_rng(7)
+    vals = []
+    for k in range(24, 63):
+        vals += [int(x) for x in rng.integers(1 << k, 1 << (k + 1), 200, dtype=np.int64)]
+    for k in range(25, 62):        # halfway between two float32 neighbours, both mantissa parities
+        for odd in (0, 1):
+            base = (1 << k) | (odd << (k - 23))
+            vals += [base | (1 << (k - 24)), (base | (1 << (k - 24))) + 1, (base | (1 << (k - 24))) - 1]
+    vals += [-v for v in vals]
+    f = np.asarray(vals, np.int64).astype(np.float32)
+    for v, g in zip(vals, f):
+        gi = int(g)
+        lo, hi = int(np.nextafter(g, np.float32(-np.inf))), int(np.nextafter(g, np.float32(np.inf)))
+        d = abs(v - gi)
+        assert d <= abs(v - lo) and d <= abs(v - hi), v
+        if d == abs(v - lo) or d == abs(v - hi):   # a tie: the even mantissa wins
+            assert (np.float32(g).view(np.uint32) & 1) == 0, v
+
+
 def test_top_left_rule_rectangle():
     """A rectangle with corners exactly on pixel centres covers the half-open
     set [i0, i1) x [j0, j1): left/top edges in, right/bottom edges out."""
